@@ -1,0 +1,275 @@
+/*
+ * tz.h -- C ABI of the GB300 amplitude library for random quantum circuits.
+ *
+ * The library computes output amplitudes a(x) = <x| U_C |0^n> of the random
+ * circuits of Sec. 1 (H layer; t cycles of CZ in 8 rotating patterns with
+ * sqrt(X)/sqrt(Y)/T single-qubit gates; final H layer) by contracting the
+ * circuit's tensor network (Sec. 1: each node a tensor, each hyperedge a
+ * running index) along a contraction tree. A set of k indices is sliced:
+ * the contraction splits into 2^k independent subtasks of equal cost
+ * (Sec. 2) whose partial amplitudes add up to the amplitude (Sec. 1,
+ * "preprocessing" and the agent's sum).
+ *
+ * Conventions for every function:
+ *  - Return value: TZ_OK (0) on success, a negative TZ_E* code on failure.
+ *    No function aborts the process. tz_last_error() returns a message for
+ *    the last failure on the calling thread (valid until the next call).
+ *  - Handles are opaque; the caller owns each handle it receives and frees
+ *    it with the matching tz_*_destroy. Destroy functions accept NULL.
+ *  - The library copies every input array it is given; it keeps no pointer
+ *    to caller memory, except device memory bound as a workspace.
+ *  - The library never allocates device memory. Device memory is supplied
+ *    by the caller (tz_plan_bind_workspace, tz_server_opts.arena).
+ *  - "Device pointer" means memory of the plan's CUDA device; "host
+ *    pointer" means ordinary (pageable or pinned) host memory.
+ *  - Bitstrings are uint8 arrays of n rows x n_qubits columns (row-major),
+ *    each byte 0 or 1; column q is the bit of qubit q.
+ *  - Amplitudes are returned as FP64 complex numbers: 2*n doubles,
+ *    (re, im) interleaved.
+ */
+#ifndef TZ_H
+#define TZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- status */
+#define TZ_OK            0
+#define TZ_EINVAL       -1   /* invalid argument, shape or spec            */
+#define TZ_ENOMEM       -2   /* host allocation failed or workspace too small */
+#define TZ_EHBM_ADMIT   -3   /* server: query does not fit the HBM budget  */
+#define TZ_ECUDA        -4   /* a CUDA runtime call failed                 */
+#define TZ_ETIMEOUT     -5   /* a bounded wait ran out                     */
+#define TZ_EUNSUPPORTED -6   /* valid request the build does not support  */
+#define TZ_EBUSY        -7   /* server: no free slot (try again later)     */
+
+const char *tz_last_error(void);
+
+/* ------------------------------------------------------------ handles */
+typedef struct tz_circuit tz_circuit;
+typedef struct tz_network tz_network;
+typedef struct tz_tree tz_tree;
+typedef struct tz_plan tz_plan;
+typedef struct tz_server tz_server;
+
+/* --------------------------------------------------------- circuits
+ * Sec. 1 (circuit prescription, items 1-4).
+ */
+
+/* Parse a plain-text circuit spec. First non-empty line: the qubit count.
+ * Each further line: `cycle name q0 [q1]`, name in {h, cz, t, x_1_2, y_1_2}
+ * (the GRCS gate names). Lines starting with '#' are skipped. Gates are
+ * applied in line order. text need not be NUL-terminated; len is its length
+ * in bytes. Malformed text, unknown gates, out-of-range or repeated qubits
+ * give TZ_EINVAL. */
+int tz_circuit_from_spec(const char *text, size_t len, tz_circuit **out);
+
+#define TZ_LATTICE_GRID        0   /* rows x cols square lattice           */
+#define TZ_LATTICE_BRISTLECONE 1   /* 72-site diamond, or 70 without (5,0),(5,11) */
+typedef struct {
+  int kind;      /* TZ_LATTICE_*                                         */
+  int rows;      /* grid: rows (>= 1)                                    */
+  int cols;      /* grid: cols (>= 1)                                    */
+  int n_qubits;  /* bristlecone: 70 or 72                                */
+} tz_lattice;
+
+/* Generate a depth 1+t+1 circuit by the prescription of Sec. 1 with the
+ * library's readings: CZ patterns H0,V0,H2,V2,H1,V1,H3,V3 (H_a: couplers
+ * (r,c)-(r,c+1) with c = a + 2(r mod 2) mod 4; V_a: (r,c)-(r+1,c) with
+ * r = a + 2(c mod 2) mod 4); sqrt(X)/sqrt(Y) after a CZ in the previous
+ * cycle, chosen by the top bit of one SplitMix64 draw (seeded with `seed`;
+ * cycle-major, qubit-minor order); T after H/sqrt(X)/sqrt(Y) in the previous
+ * cycle. Qubits are the lattice sites in row-major order. */
+int tz_circuit_generate(const tz_lattice *lat, int depth_t, uint64_t seed, tz_circuit **out);
+
+int tz_circuit_n_qubits(const tz_circuit *c);
+int tz_circuit_n_gates(const tz_circuit *c);
+/* Write the spec text (NUL-terminated) into buf of capacity cap bytes;
+ * *len receives the length without the NUL. If cap is too small, nothing is
+ * written, *len receives the needed length and TZ_EINVAL is returned. */
+int tz_circuit_to_spec(const tz_circuit *c, char *buf, size_t cap, size_t *len);
+void tz_circuit_destroy(tz_circuit *c);
+
+/* --------------------------------------------------------- networks
+ * Sec. 1 (refactoring note): a node holds a tensor, a hyperedge is a running
+ * index. Every index has dimension 2. A qubit's wire contributes one index
+ * per segment: segment j is the stretch after the qubit's j-th non-diagonal
+ * gate (H, sqrt(X), sqrt(Y)). Diagonal gates (T, CZ) create no index: T is
+ * a rank-1 tensor and CZ a rank-2 tensor on the current segment indices.
+ * The input |0> and the output <x_q| are rank-1 tensors. The builder then
+ * merges rank-1 tensors into a neighbour and the last gate of each wire into
+ * its output tensor (exact rewrites). Output tensors carry `batch_log2`
+ * extra open indices (the bitstring batch): one call contracts 2^batch_log2
+ * bitstrings at once.
+ */
+typedef struct {
+  int batch_log2;   /* 0..8: bitstrings contracted together per group    */
+} tz_network_opts;
+
+int tz_network_from_circuit(const tz_circuit *c, const tz_network_opts *opts, tz_network **out);
+int tz_network_n_tensors(const tz_network *net);
+int tz_network_n_indices(const tz_network *net);
+/* Index info: *qubit = owning qubit and *segment = segment number for wire
+ * indices; *qubit = -1 and *segment = bit number for batch indices. */
+int tz_network_index_info(const tz_network *net, int index, int *qubit, int *segment);
+/* Indices of tensor t in storage order (bit p of a linear element offset is
+ * the p-th index). cap = capacity of idx; *rank receives the rank. */
+int tz_network_tensor_indices(const tz_network *net, int t, int32_t *idx, int cap, int *rank);
+void tz_network_destroy(tz_network *net);
+
+/* ------------------------------------------------------ contraction trees
+ * The contraction algorithm of the paper is deferred to its earlier work;
+ * the library builds its own trees: a greedy over pairs that share an index
+ * (cost size(out) - alpha (size(a) + size(b))), with randomised restarts
+ * scored by the estimated GB300 time of the sliced plan.
+ * Trees are lists of SSA pairs: leaves are ids 0..T-1, the i-th pair
+ * creates id T+i. A complete tree has T-1 pairs.
+ */
+typedef struct {
+  int restarts;                 /* randomised greedy trials (>= 1); 1 = plain greedy */
+  uint64_t seed;                /* seed of the randomisation                   */
+  int log2_max_intermediate;    /* slicing target used to score trials (bits)  */
+  int precision;                /* tz_precision used by the time model         */
+} tz_path_opts;
+
+int tz_path_greedy(const tz_network *net, const tz_path_opts *opts, tz_tree **out);
+/* Build a tree from caller pairs (validated: complete, each id used once). */
+int tz_tree_from_pairs(const tz_network *net, const int32_t *pairs, int n_pairs, tz_tree **out);
+/* Copy the pairs out (2 int32 per pair). cap = capacity in pairs. */
+int tz_tree_pairs(const tz_tree *tree, int32_t *pairs, int cap, int *n_pairs);
+void tz_tree_destroy(tz_tree *tree);
+
+/* ------------------------------------------------------------ slicing
+ * Sec. 1 (preprocessing splits the contraction into subtasks). Greedily
+ * picks indices whose fixing lowers the largest intermediate most (ties:
+ * lower total cost) until it is <= 2^log2_max_intermediate elements or k_max
+ * indices are chosen. sliced_edges receives the index ids (capacity k_max);
+ * slice s fixes the i-th listed index to bit i of s. */
+int tz_slice_select(const tz_network *net, const tz_tree *tree, int log2_max_intermediate,
+                    int k_max, int32_t *sliced_edges, int *k_out);
+
+/* ---------------------------------------------------------------- plans */
+#define TZ_C64_SIMT     0   /* complex64, FP32 FMA on CUDA cores (4 real products) */
+#define TZ_TF32X3       1   /* FP32 operands split hi+lo TF32, 3 tcgen05 products  */
+#define TZ_BF16X3       2   /* FP32 operands split hi+lo BF16, 3 tcgen05 products  */
+
+typedef struct {
+  int precision;         /* TZ_C64_SIMT, TZ_TF32X3 or TZ_BF16X3                    */
+  int device;            /* CUDA device ordinal                                     */
+  void *stream;          /* cudaStream_t the plan launches on (NULL = default)     */
+  int small_log2;        /* steps with output and work below this use the direct SIMT kernel (0 = default) */
+  int use_graph;         /* 1: replay the per-group launch sequence as a CUDA graph
+                            (needs a non-NULL stream)                              */
+  int64_t max_bitstrings;/* bitstrings per call the workspace is sized for (0 = 4096) */
+} tz_plan_opts;
+
+typedef struct {
+  int n_steps;                   /* contraction steps (tree pairs)                   */
+  int n_const_steps;             /* steps computed once at bind time                 */
+  int n_gemm_steps;              /* steps on the GEMM path (per group)               */
+  int n_permutes;                /* operand permutes per group                       */
+  int n_launches_per_group;      /* kernel launches per group                        */
+  int k;                         /* sliced indices                                   */
+  int batch_log2;                /* bitstrings per group = 2^batch_log2              */
+  int max_log2;                  /* largest per-group intermediate (bits)            */
+  double flops_per_group;        /* useful real flops per group, 8 per complex MAC   */
+  double gemm_flops_per_group;   /* part of it on the GEMM path                      */
+  double bytes_per_group;        /* algorithmic bytes: operands + results, complex64 */
+  double permute_bytes_per_group;/* extra bytes moved by operand permutes            */
+  size_t workspace_bytes;        /* device workspace the plan needs                  */
+  size_t const_bytes;            /* part of it holding bind-time constants           */
+} tz_plan_stats;
+
+/* Build a plan: classify steps, choose layouts, permutes and kernels, lay
+ * out the device workspace. The network, tree and edge list are copied.
+ * Errors: TZ_EINVAL for an incomplete tree, an edge that is not a wire index
+ * or a repeated edge; TZ_EUNSUPPORTED for a tensor above 2^40 elements. */
+int tz_plan_create(const tz_network *network, const tz_tree *contraction_tree,
+                   const int32_t *sliced_edges, int k, const tz_plan_opts *opts, tz_plan **out);
+int tz_plan_stats_get(const tz_plan *plan, tz_plan_stats *out);
+/* Bind caller-owned device memory (>= workspace_bytes, 256-byte aligned) as
+ * the plan's workspace; uploads the constant tensors and computes the
+ * bind-time steps on the plan's stream (the memory must stay valid until
+ * the plan is destroyed or rebound). TZ_ENOMEM if bytes is too small. */
+int tz_plan_bind_workspace(tz_plan *plan, void *dev_ptr, size_t bytes);
+/* Restrict contractions to slices [lo, hi) of [0, 2^k) (default: all).
+ * Partial ranges give partial sums; ranges add up. */
+int tz_plan_set_slice_range(tz_plan *plan, int64_t lo, int64_t hi);
+/* The (qubit, segment) wire segment of each sliced index, in slice-bit order
+ * (2 int32 per index; cap in pairs). */
+int tz_plan_sliced_segments(const tz_plan *plan, int32_t *qubit_segment, int cap, int *k);
+
+/* Text (JSON) description of the plan: tensors with their storage order,
+ * steps with their GEMM shapes, the launch schedule. Same buffer protocol
+ * as tz_circuit_to_spec. */
+int tz_plan_describe(const tz_plan *plan, char *buf, size_t cap, size_t *len);
+
+/* Amplitudes of n bitstrings (host pointers): copies the bitstrings in,
+ * contracts every group of the slice range, sums partial amplitudes in
+ * FP64, copies 2n doubles out, and synchronises the plan's stream. */
+int tz_contract_amplitudes(tz_plan *plan, const uint8_t *bitstrings, int64_t n, double *out);
+/* Same with device pointers; asynchronous on the plan's stream (no host
+ * synchronisation). d_bitstrings: n x n_qubits uint8; d_out: 2n doubles. */
+int tz_contract_amplitudes_device(tz_plan *plan, const uint8_t *d_bitstrings, int64_t n, double *d_out);
+void tz_plan_destroy(tz_plan *plan);
+
+/* --------------------------------------------------------------- serving
+ * A request loop for amplitude-batch queries over resident plans: plans
+ * stay bound to their workspaces, queries are admitted while their device
+ * footprint fits the budget and a slot is free, and admitted queries run
+ * concurrently on separate streams.
+ */
+typedef struct {
+  size_t hbm_budget;     /* bytes of device memory queries may hold at once         */
+  int max_inflight;      /* concurrent queries (streams), 1..32                      */
+  int device;            /* CUDA device ordinal                                      */
+  void *arena;           /* caller-owned device memory of arena_bytes for query buffers */
+  size_t arena_bytes;
+  int wait_admit;        /* 1: submit queues a query that does not fit yet; 0: TZ_EHBM_ADMIT */
+} tz_server_opts;
+
+int tz_server_create(const tz_server_opts *opts, tz_server **out);
+/* Queue a query (bitstrings copied). *ticket identifies it. */
+int tz_server_submit(tz_server *srv, tz_plan *plan, const uint8_t *bitstrings, int64_t n, uint64_t *ticket);
+/* Non-blocking: *done = 1 and out (2n doubles) filled once the query has
+ * finished; *done = 0 otherwise. A finished ticket is released after a
+ * successful poll. */
+int tz_server_poll(tz_server *srv, uint64_t ticket, double *out, int *done);
+/* Latency statistics (seconds) over finished queries since creation. */
+int tz_server_latency(tz_server *srv, double *p50, double *p99, int64_t *n_done);
+void tz_server_destroy(tz_server *srv);
+
+/* ------------------------------------------------ per-step operations
+ * The kernels of one contraction step, callable alone on device pointers
+ * (asynchronous on `stream`). Used to test and tune the kernels.
+ */
+
+/* Bit permutation of a complex64 tensor of 2^rank elements: output bit p is
+ * input bit perm[p] (out[j] = in[i] where bit perm[p] of i = bit p of j).
+ * rank <= 40; perm must be a permutation of 0..rank-1. */
+int tz_op_permute(const void *in, void *out, int rank, const int32_t *perm, void *stream);
+
+/* Batched complex64 product C[z] = A[z] * B[z]^T, z < batch (the per-step
+ * contraction of Sec. 1's network once operands are laid out):
+ * A[z] is m x k row-major (k contiguous), B[z] is n x k row-major,
+ * C[z] is m x n row-major; z-th matrices at element offsets z*sa, z*sb, z*sc.
+ * precision: TZ_C64_SIMT, TZ_TF32X3 or TZ_BF16X3. The split-precision
+ * modes need device scratch of tz_op_cgemm_scratch_bytes() bytes (256-byte
+ * aligned); TZ_EUNSUPPORTED for shapes they do not handle. */
+int tz_op_cgemm(int precision, int64_t batch, int64_t m, int64_t n, int64_t k,
+                const void *A, int64_t sa, const void *B, int64_t sb, void *C, int64_t sc,
+                void *scratch, size_t scratch_bytes, void *stream);
+int tz_op_cgemm_scratch_bytes(int precision, int64_t batch, int64_t m, int64_t n, int64_t k, size_t *bytes);
+
+/* FP64 accumulation of partial amplitudes: acc[j] += scale * part[j] for
+ * j < n, with part complex64 and acc, scale complex128 (re, im). */
+int tz_op_accumulate(const void *part, double *acc, int64_t n, double scale_re, double scale_im, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TZ_H */

@@ -1,0 +1,389 @@
+// C ABI entry points (include/tz.h): argument checks, error codes, handles.
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+
+#include "plan.h"
+
+struct tz_circuit {
+  tz::Circuit c;
+};
+struct tz_network {
+  tz::Network n;
+};
+struct tz_tree {
+  tz::Pairs pairs;
+};
+
+namespace {
+thread_local std::string g_err;
+void set_error(const std::string &m) { g_err = m; }
+}  // namespace
+
+#define TZ_TRY try {
+#define TZ_CATCH                           \
+  }                                        \
+  catch (const tz::Error &e) {             \
+    set_error(e.what());                   \
+    return e.code;                         \
+  }                                        \
+  catch (const std::bad_alloc &) {         \
+    set_error("host allocation failed");   \
+    return TZ_ENOMEM;                      \
+  }                                        \
+  catch (const std::exception &e) {        \
+    set_error(e.what());                   \
+    return TZ_EINVAL;                      \
+  }                                        \
+  return TZ_OK;
+
+#define REQUIRE(cond, msg) \
+  if (!(cond)) tz::fail(TZ_EINVAL, msg)
+
+extern "C" {
+
+const char *tz_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------------ circuits
+int tz_circuit_from_spec(const char *text, size_t len, tz_circuit **out) {
+  TZ_TRY
+  REQUIRE(out, "out is NULL");
+  *out = nullptr;
+  auto c = std::make_unique<tz_circuit>();
+  c->c = tz::parse_spec(text, len);
+  *out = c.release();
+  TZ_CATCH
+}
+
+int tz_circuit_generate(const tz_lattice *lat, int depth_t, uint64_t seed, tz_circuit **out) {
+  TZ_TRY
+  REQUIRE(lat && out, "NULL argument");
+  *out = nullptr;
+  auto c = std::make_unique<tz_circuit>();
+  c->c = tz::generate_circuit(*lat, depth_t, seed);
+  *out = c.release();
+  TZ_CATCH
+}
+
+int tz_circuit_n_qubits(const tz_circuit *c) { return c ? c->c.n : TZ_EINVAL; }
+int tz_circuit_n_gates(const tz_circuit *c) { return c ? (int)c->c.gates.size() : TZ_EINVAL; }
+
+int tz_circuit_to_spec(const tz_circuit *c, char *buf, size_t cap, size_t *len) {
+  TZ_TRY
+  REQUIRE(c && len, "NULL argument");
+  std::string s = tz::circuit_spec(c->c);
+  *len = s.size();
+  if (!buf || cap < s.size() + 1) tz::fail(TZ_EINVAL, "buffer too small");
+  std::memcpy(buf, s.c_str(), s.size() + 1);
+  TZ_CATCH
+}
+
+void tz_circuit_destroy(tz_circuit *c) { delete c; }
+
+// ------------------------------------------------------------------ networks
+int tz_network_from_circuit(const tz_circuit *c, const tz_network_opts *opts, tz_network **out) {
+  TZ_TRY
+  REQUIRE(c && out, "NULL argument");
+  *out = nullptr;
+  auto n = std::make_unique<tz_network>();
+  n->n = tz::build_network(c->c, opts ? opts->batch_log2 : 0);
+  *out = n.release();
+  TZ_CATCH
+}
+
+int tz_network_n_tensors(const tz_network *net) { return net ? (int)net->n.leaves.size() : TZ_EINVAL; }
+int tz_network_n_indices(const tz_network *net) { return net ? (int)net->n.indices.size() : TZ_EINVAL; }
+
+int tz_network_index_info(const tz_network *net, int index, int *qubit, int *segment) {
+  TZ_TRY
+  REQUIRE(net && qubit && segment, "NULL argument");
+  REQUIRE(index >= 0 && index < (int)net->n.indices.size(), "index out of range");
+  *qubit = net->n.indices[index].qubit;
+  *segment = net->n.indices[index].segment;
+  TZ_CATCH
+}
+
+int tz_network_tensor_indices(const tz_network *net, int t, int32_t *idx, int cap, int *rank) {
+  TZ_TRY
+  REQUIRE(net && rank, "NULL argument");
+  REQUIRE(t >= 0 && t < (int)net->n.leaves.size(), "tensor out of range");
+  const auto &v = net->n.leaves[t].idx;
+  *rank = (int)v.size();
+  REQUIRE(idx && cap >= (int)v.size(), "buffer too small");
+  for (size_t i = 0; i < v.size(); i++) idx[i] = v[i];
+  TZ_CATCH
+}
+
+void tz_network_destroy(tz_network *net) { delete net; }
+
+// ------------------------------------------------------------------ trees
+static tz::CostModel cost_model(int precision) {
+  tz::CostModel cm;
+  cm.precision = precision;
+  return cm;
+}
+
+// Score of a tree: estimated time of all 2^k groups after slicing to the
+// target, plus the bind-time part once.
+static double tree_score(const tz::Network &net, const tz::Pairs &pairs, int log2_max, const tz::CostModel &cm,
+                         int *max_bits) {
+  std::vector<int> sl;
+  if (log2_max > 0) sl = tz::select_slices(net, pairs, log2_max, 40, cm);
+  std::vector<char> flag(net.indices.size(), 0);
+  for (int e : sl) flag[e] = 1;
+  tz::TreeInfo ti = tz::analyse_tree(net, pairs, flag);
+  *max_bits = ti.max_bits;
+  double t = std::ldexp(tz::group_time(ti, cm), (int)sl.size());
+  for (const auto &s : ti.steps)
+    if (!s.var) t += cm.step_time(s);
+  return t;
+}
+
+int tz_path_greedy(const tz_network *net, const tz_path_opts *opts, tz_tree **out) {
+  TZ_TRY
+  REQUIRE(net && out, "NULL argument");
+  *out = nullptr;
+  tz_path_opts o{};
+  o.restarts = 1;
+  if (opts) o = *opts;
+  if (o.restarts < 1) o.restarts = 1;
+  tz::CostModel cm = cost_model(o.precision);
+  uint64_t rng = o.seed ^ 0x5DEECE66DULL;
+  tz::Pairs best;
+  double best_score = 0;
+  int best_bits = 0;
+  for (int trial = 0; trial < o.restarts; trial++) {
+    double alpha = 1.0, temp = 0.0;
+    if (trial > 0) {
+      alpha = 0.5 + 1.0 * ((tz::splitmix64_next(rng) >> 11) * (1.0 / 9007199254740992.0));
+      temp = 0.05 + 1.0 * ((tz::splitmix64_next(rng) >> 11) * (1.0 / 9007199254740992.0));
+    }
+    tz::Pairs pr = tz::greedy_tree(net->n, alpha, temp, tz::splitmix64_next(rng));
+    int mb = 0;
+    double sc = tree_score(net->n, pr, o.log2_max_intermediate, cm, &mb);
+    if (trial == 0 || sc < best_score) {
+      best = pr;
+      best_score = sc;
+      best_bits = mb;
+    }
+  }
+  (void)best_bits;
+  auto t = std::make_unique<tz_tree>();
+  t->pairs = best;
+  *out = t.release();
+  TZ_CATCH
+}
+
+int tz_tree_from_pairs(const tz_network *net, const int32_t *pairs, int n_pairs, tz_tree **out) {
+  TZ_TRY
+  REQUIRE(net && out && (pairs || n_pairs == 0), "NULL argument");
+  *out = nullptr;
+  tz::Pairs pr;
+  for (int i = 0; i < n_pairs; i++) pr.push_back({pairs[2 * i], pairs[2 * i + 1]});
+  tz::validate_tree(net->n, pr);
+  tz::analyse_tree(net->n, pr, {});
+  auto t = std::make_unique<tz_tree>();
+  t->pairs = pr;
+  *out = t.release();
+  TZ_CATCH
+}
+
+int tz_tree_pairs(const tz_tree *tree, int32_t *pairs, int cap, int *n_pairs) {
+  TZ_TRY
+  REQUIRE(tree && n_pairs, "NULL argument");
+  *n_pairs = (int)tree->pairs.size();
+  REQUIRE(pairs && cap >= (int)tree->pairs.size(), "buffer too small");
+  for (size_t i = 0; i < tree->pairs.size(); i++) {
+    pairs[2 * i] = tree->pairs[i].first;
+    pairs[2 * i + 1] = tree->pairs[i].second;
+  }
+  TZ_CATCH
+}
+
+void tz_tree_destroy(tz_tree *tree) { delete tree; }
+
+int tz_slice_select(const tz_network *net, const tz_tree *tree, int log2_max_intermediate, int k_max,
+                    int32_t *sliced_edges, int *k_out) {
+  TZ_TRY
+  REQUIRE(net && tree && k_out, "NULL argument");
+  REQUIRE(k_max >= 0 && k_max <= 40, "k_max must be in 0..40");
+  REQUIRE(sliced_edges || k_max == 0, "NULL sliced_edges");
+  tz::validate_tree(net->n, tree->pairs);
+  std::vector<int> sl = tz::select_slices(net->n, tree->pairs, log2_max_intermediate, k_max, cost_model(TZ_C64_SIMT));
+  for (size_t i = 0; i < sl.size(); i++) sliced_edges[i] = sl[i];
+  *k_out = (int)sl.size();
+  TZ_CATCH
+}
+
+// ------------------------------------------------------------------ plans
+int tz_plan_create(const tz_network *network, const tz_tree *contraction_tree, const int32_t *sliced_edges, int k,
+                   const tz_plan_opts *opts, tz_plan **out) {
+  TZ_TRY
+  REQUIRE(network && contraction_tree && out, "NULL argument");
+  REQUIRE(k >= 0 && (k == 0 || sliced_edges), "bad sliced edge list");
+  *out = nullptr;
+  tz_plan_opts o{};
+  if (opts) o = *opts;
+  std::vector<int> sl(sliced_edges, sliced_edges + k);
+  *out = tz::plan_create(network->n, contraction_tree->pairs, sl, o);
+  TZ_CATCH
+}
+
+int tz_plan_stats_get(const tz_plan *plan, tz_plan_stats *out) {
+  TZ_TRY
+  REQUIRE(plan && out, "NULL argument");
+  *out = plan->stats;
+  TZ_CATCH
+}
+
+int tz_plan_bind_workspace(tz_plan *plan, void *dev_ptr, size_t bytes) {
+  TZ_TRY
+  REQUIRE(plan, "NULL plan");
+  tz::plan_bind(plan, dev_ptr, bytes);
+  TZ_CATCH
+}
+
+int tz_plan_set_slice_range(tz_plan *plan, int64_t lo, int64_t hi) {
+  TZ_TRY
+  REQUIRE(plan, "NULL plan");
+  const int64_t n = int64_t(1) << plan->sliced.size();
+  REQUIRE(0 <= lo && lo < hi && hi <= n, "slice range must satisfy 0 <= lo < hi <= 2^k");
+  plan->lo = lo;
+  plan->hi = hi;
+  TZ_CATCH
+}
+
+int tz_plan_sliced_segments(const tz_plan *plan, int32_t *qubit_segment, int cap, int *k) {
+  TZ_TRY
+  REQUIRE(plan && k, "NULL argument");
+  *k = (int)plan->sliced.size();
+  REQUIRE(qubit_segment || plan->sliced.empty(), "NULL buffer");
+  REQUIRE(cap >= (int)plan->sliced.size(), "buffer too small");
+  for (size_t j = 0; j < plan->sliced.size(); j++) {
+    qubit_segment[2 * j] = plan->net.indices[plan->sliced[j]].qubit;
+    qubit_segment[2 * j + 1] = plan->net.indices[plan->sliced[j]].segment;
+  }
+  TZ_CATCH
+}
+
+static void check_rows(const tz_plan *plan, int64_t n) {
+  REQUIRE(n >= 1, "need at least one bitstring");
+  if (n > plan->max_rows)
+    tz::fail(TZ_EINVAL, "at most " + std::to_string(plan->max_rows) + " bitstrings per call");
+}
+
+int tz_contract_amplitudes(tz_plan *plan, const uint8_t *bitstrings, int64_t n, double *out) {
+  TZ_TRY
+  REQUIRE(plan && bitstrings && out, "NULL argument");
+  check_rows(plan, n);
+  REQUIRE(plan->bound, "plan has no workspace bound");
+  const int nq = plan->net.n_qubits;
+  for (int64_t i = 0; i < n * nq; i++)
+    if (bitstrings[i] > 1) tz::fail(TZ_EINVAL, "bitstring bytes must be 0 or 1");
+  tz::cuda_check(cudaSetDevice(plan->opts.device), "cudaSetDevice");
+  cudaStream_t s = plan->stream;
+  tz::cuda_check(cudaMemcpyAsync(plan->ws + plan->off_bits, bitstrings, (size_t)(n * nq), cudaMemcpyHostToDevice, s),
+                 "copy bitstrings in");
+  tz::plan_run(plan, n);
+  tz::cuda_check(cudaMemcpyAsync(out, plan->ws + plan->off_acc, (size_t)n * 16, cudaMemcpyDeviceToHost, s),
+                 "copy amplitudes out");
+  tz::cuda_check(cudaStreamSynchronize(s), "contract");
+  TZ_CATCH
+}
+
+int tz_contract_amplitudes_device(tz_plan *plan, const uint8_t *d_bitstrings, int64_t n, double *d_out) {
+  TZ_TRY
+  REQUIRE(plan && d_bitstrings && d_out, "NULL argument");
+  check_rows(plan, n);
+  REQUIRE(plan->bound, "plan has no workspace bound");
+  tz::cuda_check(cudaSetDevice(plan->opts.device), "cudaSetDevice");
+  cudaStream_t s = plan->stream;
+  tz::cuda_check(cudaMemcpyAsync(plan->ws + plan->off_bits, d_bitstrings, (size_t)(n * plan->net.n_qubits),
+                                 cudaMemcpyDeviceToDevice, s),
+                 "copy bitstrings in");
+  tz::plan_run(plan, n);
+  tz::cuda_check(cudaMemcpyAsync(d_out, plan->ws + plan->off_acc, (size_t)n * 16, cudaMemcpyDeviceToDevice, s),
+                 "copy amplitudes out");
+  TZ_CATCH
+}
+
+int tz_plan_describe(const tz_plan *plan, char *buf, size_t cap, size_t *len) {
+  TZ_TRY
+  REQUIRE(plan && len, "NULL argument");
+  std::string s = tz::plan_describe(plan);
+  *len = s.size();
+  if (!buf || cap < s.size() + 1) tz::fail(TZ_EINVAL, "buffer too small");
+  std::memcpy(buf, s.c_str(), s.size() + 1);
+  TZ_CATCH
+}
+
+void tz_plan_destroy(tz_plan *plan) { tz::plan_destroy(plan); }
+
+// ------------------------------------------------------------------ ops
+int tz_op_permute(const void *in, void *out, int rank, const int32_t *perm, void *stream) {
+  TZ_TRY
+  REQUIRE(in && out && (perm || rank == 0), "NULL argument");
+  REQUIRE(rank >= 0 && rank <= tz::dev::kMaxBits, "rank must be in 0..40");
+  tz::dev::PermuteArgs a{};
+  a.rank = rank;
+  std::vector<char> seen(rank, 0);
+  for (int p = 0; p < rank; p++) {
+    REQUIRE(perm[p] >= 0 && perm[p] < rank && !seen[perm[p]], "perm is not a permutation");
+    seen[perm[p]] = 1;
+    a.perm[p] = (int8_t)perm[p];
+  }
+  tz::cuda_check(tz::dev::launch_permute((const float2 *)in, (float2 *)out, a, (cudaStream_t)stream), "permute");
+  TZ_CATCH
+}
+
+int tz_op_cgemm_scratch_bytes(int precision, int64_t batch, int64_t m, int64_t n, int64_t k, size_t *bytes) {
+  TZ_TRY
+  REQUIRE(bytes, "NULL argument");
+  REQUIRE(batch >= 1 && m >= 1 && n >= 1 && k >= 1, "sizes must be >= 1");
+  *bytes = 0;
+  if (precision == TZ_TF32X3 || precision == TZ_BF16X3) {
+    if (!tz::dev::cgemm_tc_supported(precision, m, n, k))
+      tz::fail(TZ_EUNSUPPORTED, "shape not supported by the tensor-core product");
+    *bytes = tz::dev::cgemm_tc_scratch_bytes(precision, batch, n, k);
+  } else if (precision != TZ_C64_SIMT) {
+    tz::fail(TZ_EINVAL, "unknown precision");
+  }
+  TZ_CATCH
+}
+
+int tz_op_cgemm(int precision, int64_t batch, int64_t m, int64_t n, int64_t k, const void *A, int64_t sa,
+                const void *B, int64_t sb, void *C, int64_t sc, void *scratch, size_t scratch_bytes, void *stream) {
+  TZ_TRY
+  REQUIRE(A && B && C, "NULL argument");
+  REQUIRE(batch >= 1 && m >= 1 && n >= 1 && k >= 1, "sizes must be >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == TZ_C64_SIMT) {
+    tz::cuda_check(tz::dev::launch_cgemm_simt((const float2 *)A, (const float2 *)B, (float2 *)C, batch, m, n, k, sa,
+                                              sb, sc, s),
+                   "simt gemm");
+  } else if (precision == TZ_TF32X3 || precision == TZ_BF16X3) {
+    if (!tz::dev::cgemm_tc_supported(precision, m, n, k))
+      tz::fail(TZ_EUNSUPPORTED, "shape not supported by the tensor-core product");
+    size_t need = tz::dev::cgemm_tc_scratch_bytes(precision, batch, n, k);
+    REQUIRE(scratch_bytes >= need && (need == 0 || scratch), "scratch too small");
+    tz::cuda_check(tz::dev::launch_cgemm_tc(precision, (const float2 *)A, (const float2 *)B, (float2 *)C, batch, m, n,
+                                            k, sa, sb, sc, scratch, scratch_bytes, s),
+                   "tensor-core gemm");
+  } else {
+    tz::fail(TZ_EINVAL, "unknown precision");
+  }
+  TZ_CATCH
+}
+
+int tz_op_accumulate(const void *part, double *acc, int64_t n, double scale_re, double scale_im, void *stream) {
+  TZ_TRY
+  REQUIRE(part && acc, "NULL argument");
+  REQUIRE(n >= 0, "n must be >= 0");
+  tz::cuda_check(tz::dev::launch_accumulate_plain((const float2 *)part, (double2 *)acc, n, scale_re, scale_im,
+                                                  (cudaStream_t)stream),
+                 "accumulate");
+  TZ_CATCH
+}
+
+}  // extern "C"

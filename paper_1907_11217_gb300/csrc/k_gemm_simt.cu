@@ -1,0 +1,103 @@
+// Batched complex64 product on CUDA cores (FP32 FMA, four real products per
+// complex multiply-add): C[z] = A[z] B[z]^T with A[z] m x k, B[z] n x k and
+// C[z] m x n, all row-major. This is the plain complex64 precision mode and
+// the baseline of the split-precision tensor-core modes.
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace tz {
+namespace dev {
+
+namespace {
+
+template <int BM, int BN, int TM, int TN, int BK>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    cgemm_simt_kernel(const float2 *__restrict__ A, const float2 *__restrict__ B, float2 *__restrict__ C,
+                      int64_t batch, int64_t M, int64_t N, int64_t K, int64_t sA, int64_t sB, int64_t sC) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  constexpr int TX = BN / TN;
+  __shared__ float2 As[BK][BM + 1];
+  __shared__ float2 Bs[BK][BN + 1];
+  const int64_t mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
+  const int64_t tiles = mt * nt * batch;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t z = tile / (mt * nt);
+    const int64_t rem = tile - z * mt * nt;
+    const int64_t m0 = (rem / nt) * BM, n0 = (rem % nt) * BN;
+    const float2 *Az = A + z * sA;
+    const float2 *Bz = B + z * sB;
+    float2 acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; i++)
+#pragma unroll
+      for (int j = 0; j < TN; j++) acc[i][j] = make_float2(0.f, 0.f);
+    for (int64_t k0 = 0; k0 < K; k0 += BK) {
+      for (int l = threadIdx.x; l < BM * BK; l += NT) {
+        const int i = l / BK, kk = l % BK;
+        const int64_t m = m0 + i, k = k0 + kk;
+        As[kk][i] = (m < M && k < K) ? Az[m * K + k] : make_float2(0.f, 0.f);
+      }
+      for (int l = threadIdx.x; l < BN * BK; l += NT) {
+        const int i = l / BK, kk = l % BK;
+        const int64_t n = n0 + i, k = k0 + kk;
+        Bs[kk][i] = (n < N && k < K) ? Bz[n * K + k] : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; kk++) {
+        float2 a[TM], b[TN];
+#pragma unroll
+        for (int i = 0; i < TM; i++) a[i] = As[kk][ty + i * (BM / TM)];
+#pragma unroll
+        for (int j = 0; j < TN; j++) b[j] = Bs[kk][tx + j * TX];
+#pragma unroll
+        for (int i = 0; i < TM; i++)
+#pragma unroll
+          for (int j = 0; j < TN; j++) {
+            acc[i][j].x = fmaf(a[i].x, b[j].x, acc[i][j].x);
+            acc[i][j].x = fmaf(-a[i].y, b[j].y, acc[i][j].x);
+            acc[i][j].y = fmaf(a[i].x, b[j].y, acc[i][j].y);
+            acc[i][j].y = fmaf(a[i].y, b[j].x, acc[i][j].y);
+          }
+      }
+      __syncthreads();
+    }
+    float2 *Cz = C + z * sC;
+#pragma unroll
+    for (int i = 0; i < TM; i++) {
+      const int64_t m = m0 + ty + i * (BM / TM);
+      if (m >= M) continue;
+#pragma unroll
+      for (int j = 0; j < TN; j++) {
+        const int64_t n = n0 + tx + j * TX;
+        if (n < N) Cz[m * N + n] = acc[i][j];
+      }
+    }
+  }
+}
+
+template <int BM, int BN, int TM, int TN, int BK>
+cudaError_t run(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N, int64_t K,
+                int64_t sA, int64_t sB, int64_t sC, cudaStream_t s) {
+  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN) * batch;
+  const int blocks = (int)std::min<int64_t>(tiles, 152 * 64);
+  cgemm_simt_kernel<BM, BN, TM, TN, BK><<<blocks, (BM / TM) * (BN / TN), 0, s>>>(A, B, C, batch, M, N, K, sA, sB,
+                                                                               sC);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_cgemm_simt(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N,
+                              int64_t K, int64_t sA, int64_t sB, int64_t sC, cudaStream_t s) {
+  if (batch <= 0 || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
+  if (N >= 48) return run<64, 64, 4, 4, 8>(A, B, C, batch, M, N, K, sA, sB, sC, s);
+  if (N >= 12) return run<128, 16, 4, 2, 8>(A, B, C, batch, M, N, K, sA, sB, sC, s);
+  if (N >= 3) return run<256, 4, 4, 1, 8>(A, B, C, batch, M, N, K, sA, sB, sC, s);
+  return run<256, 2, 2, 1, 8>(A, B, C, batch, M, N, K, sA, sB, sC, s);
+}
+
+}  // namespace dev
+}  // namespace tz

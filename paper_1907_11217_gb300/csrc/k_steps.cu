@@ -1,0 +1,198 @@
+// Per-group kernels: leaf builder, direct small-step contraction, FP64
+// accumulation of partial amplitudes.
+#include "kernels.h"
+
+namespace tz {
+namespace dev {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+  c.x = fmaf(a.x, b.x, c.x);
+  c.x = fmaf(-a.y, b.y, c.x);
+  c.y = fmaf(a.x, b.y, c.y);
+  c.y = fmaf(a.y, b.x, c.y);
+  return c;
+}
+
+__global__ void init_state_kernel(GroupState *gs, int64_t lo, int64_t hi, int64_t n_rows) {
+  gs->slice = lo;
+  gs->chunk = 0;
+  gs->lo = lo;
+  gs->hi = hi;
+  gs->n_rows = n_rows;
+  gs->groups_done = 0;
+}
+
+cudaError_t launch_init_state(GroupState *gs, int64_t lo, int64_t hi, int64_t n_rows, cudaStream_t s) {
+  init_state_kernel<<<1, 1, 0, s>>>(gs, lo, hi, n_rows);
+  return cudaGetLastError();
+}
+
+// One block per leaf job. Gather: a constant tensor with its sliced bits
+// fixed to the bits of the current slice id (Sec. 1 subtasks). Output: the
+// tensor <x_q| (final gates folded in) for the current chunk of bitstrings.
+__global__ void leaf_kernel(const LeafJob *jobs, const GroupState *gs, const uint8_t *bits, int nq, int g) {
+  const LeafJob &j = jobs[blockIdx.x];
+  const int64_t slice = gs->slice, chunk = gs->chunk, n_rows = gs->n_rows;
+  const int64_t n = int64_t(1) << j.rank;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    if (j.kind == LJ_GATHER) {
+      int64_t so = 0;
+      for (int p = 0; p < j.rank; p++) so |= ((e >> p) & 1) << j.src_pos[p];
+      for (int f = 0; f < j.n_fixed; f++) so |= ((slice >> j.fixed_slice_bit[f]) & 1) << j.fixed_src_pos[f];
+      j.dst[e] = j.src[so];
+    } else {
+      int64_t beta = 0;
+      for (int b = 0; b < g; b++)
+        if (j.beta_dst_pos[b] >= 0) beta |= ((e >> j.beta_dst_pos[b]) & 1) << b;
+      const int64_t row = (chunk << g) | beta;
+      const int x = row < n_rows ? (bits[row * nq + j.qubit] & 1) : 0;
+      int ev = 0;
+      if (j.rc) {
+        if (j.e_dst_pos >= 0)
+          ev = (int)((e >> j.e_dst_pos) & 1);
+        else if (j.e_slice_bit >= 0)
+          ev = (int)((slice >> j.e_slice_bit) & 1);
+      }
+      j.dst[e] = j.M[x * (1 << j.rc) + ev];
+    }
+  }
+}
+
+cudaError_t launch_leaf_build(const LeafJob *jobs, int n_jobs, const GroupState *gs, const uint8_t *bits, int nq,
+                              int g, cudaStream_t s) {
+  leaf_kernel<<<n_jobs, 128, 0, s>>>(jobs, gs, bits, nq, g);
+  return cudaGetLastError();
+}
+
+// Direct contraction of small steps, several independent steps per launch.
+// Each output element is summed by 2^split consecutive threads, each walking
+// its share of the contracted bits in Gray-code order (one offset update per
+// term), then reduced.
+__global__ void __launch_bounds__(256) direct_kernel(const DStep *steps, int n_steps) {
+  __shared__ int s_idx;
+  __shared__ float2 red[256];
+  const int64_t blk = blockIdx.x;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n_steps - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (steps[mid].block_begin <= blk)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    s_idx = lo;
+  }
+  __syncthreads();
+  const DStep &st = steps[s_idx];
+  const int split = st.split;
+  const int64_t item = (blk - st.block_begin) * 256 + threadIdx.x;
+  const int64_t c = item >> split;
+  const int part = (int)(item & ((1 << split) - 1));
+  const bool active = c < (int64_t(1) << st.nC);
+  float2 acc = make_float2(0.f, 0.f);
+  if (active) {
+    int64_t oa = 0, ob = 0;
+    for (int q = 0; q < st.nC; q++) {
+      if (!((c >> q) & 1)) continue;
+      if (st.a_c[q] >= 0) oa += int64_t(1) << st.a_c[q];
+      if (st.b_c[q] >= 0) ob += int64_t(1) << st.b_c[q];
+    }
+    const int nlow = st.nK - split;
+    for (int q = 0; q < split; q++)
+      if ((part >> q) & 1) {
+        oa += int64_t(1) << st.a_k[nlow + q];
+        ob += int64_t(1) << st.b_k[nlow + q];
+      }
+    acc = cmul(st.A[oa], st.B[ob]);
+    const int64_t nt = int64_t(1) << nlow;
+    for (int64_t t = 1; t < nt; t++) {
+      const int q = __ffsll(t) - 1;
+      const bool on = (((t ^ (t >> 1)) >> q) & 1) != 0;
+      const int64_t da = int64_t(1) << st.a_k[q], db = int64_t(1) << st.b_k[q];
+      oa += on ? da : -da;
+      ob += on ? db : -db;
+      acc = cfma(st.A[oa], st.B[ob], acc);
+    }
+  }
+  if (split > 0) {
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (active && part == 0) {
+      for (int q = 1; q < (1 << split); q++) {
+        float2 v = red[threadIdx.x + q];
+        acc.x += v.x;
+        acc.y += v.y;
+      }
+    }
+  }
+  if (active && part == 0) st.C[c] = acc;
+}
+
+cudaError_t launch_direct(const DStep *steps, int n_steps, int64_t total_blocks, cudaStream_t s) {
+  if (n_steps <= 0) return cudaSuccess;
+  if (total_blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  direct_kernel<<<(unsigned)total_blocks, 256, 0, s>>>(steps, n_steps);
+  return cudaGetLastError();
+}
+
+// acc[row] += scale * root[beta] in FP64 for the current chunk; then advance
+// the group state (next slice, wrapping to the next chunk).
+__global__ void accum_kernel(AccumArgs a) {
+  GroupState *gs = a.gs;
+  const int64_t chunk = gs->chunk, n_rows = gs->n_rows;
+  const int nb = 1 << a.g;
+  for (int beta = threadIdx.x; beta < nb; beta += blockDim.x) {
+    int64_t off = 0;
+    for (int j = 0; j < a.g; j++) off |= int64_t((beta >> j) & 1) << a.beta_pos[j];
+    const int64_t row = (chunk << a.g) | beta;
+    if (row < n_rows) {
+      const float2 v = a.root[off];
+      const double vr = v.x, vi = v.y;
+      double2 r = a.acc[row];
+      r.x += a.scale_re * vr - a.scale_im * vi;
+      r.y += a.scale_re * vi + a.scale_im * vr;
+      a.acc[row] = r;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && a.advance) {
+    int64_t sl = gs->slice + 1;
+    if (sl >= gs->hi) {
+      sl = gs->lo;
+      gs->chunk = chunk + 1;
+    }
+    gs->slice = sl;
+    gs->groups_done++;
+  }
+}
+
+cudaError_t launch_accumulate(const AccumArgs &a, cudaStream_t s) {
+  accum_kernel<<<1, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+__global__ void accum_plain_kernel(const float2 *part, double2 *acc, int64_t n, double sre, double sim) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double vr = part[j].x, vi = part[j].y;
+    double2 r = acc[j];
+    r.x += sre * vr - sim * vi;
+    r.y += sre * vi + sim * vr;
+    acc[j] = r;
+  }
+}
+
+cudaError_t launch_accumulate_plain(const float2 *part, double2 *acc, int64_t n, double sre, double sim,
+                                    cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 65536) blocks = 65536;
+  accum_plain_kernel<<<(unsigned)blocks, 256, 0, s>>>(part, acc, n, sre, sim);
+  return cudaGetLastError();
+}
+
+}  // namespace dev
+}  // namespace tz

@@ -1,0 +1,90 @@
+// Device-side descriptors and kernel launchers (host-callable).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace tz {
+namespace dev {
+
+constexpr int kMaxBits = 40;    // largest tensor rank handled (2^40 elements)
+constexpr int kMaxDirect = 32;  // bits of C or K in a direct (SIMT) step
+constexpr int kMaxBatch = 8;    // bitstring batch bits
+
+// Which group (slice, bitstring chunk) the launches of one group work on.
+// Read by the leaf builder and the accumulator; the accumulator advances it
+// so that a captured group sequence can be replayed back to back.
+struct GroupState {
+  int64_t slice, chunk;  // current group
+  int64_t lo, hi;        // slice range
+  int64_t n_rows;        // bitstrings in the call
+  int64_t groups_done;
+  int64_t pad[2];
+};
+
+enum LeafKind { LJ_GATHER = 0, LJ_OUTPUT = 1 };
+// One leaf tensor built per group.
+struct LeafJob {
+  float2 *dst;
+  const float2 *src;      // gather: the full constant tensor
+  int kind, rank;         // rank: bits of dst
+  int n_fixed;            // gather: sliced bits of src
+  int qubit;              // output: qubit
+  int rc;                 // output: circuit indices in the table (0 or 1)
+  int e_dst_pos;          // output: dst bit of the circuit index, -1 if none
+  int e_slice_bit;        // output: slice bit fixing the circuit index, -1 if none
+  int pad0;
+  int8_t src_pos[24];     // gather: src bit of dst bit p
+  int8_t fixed_src_pos[8];
+  int8_t fixed_slice_bit[8];
+  int8_t beta_dst_pos[8]; // output: dst bit of batch bit j, -1 if absent
+  float2 M[4];            // output: table M[x * 2^rc + e]
+};
+
+// One small contraction step computed directly (no operand permute):
+// C[c] = sum_k A[offA(c,k)] * B[offB(c,k)], offsets from bit positions.
+struct DStep {
+  const float2 *A;
+  const float2 *B;
+  float2 *C;
+  int64_t block_begin;  // first block of this step within its launch
+  int nC, nK, split;    // output bits, contracted bits, log2 threads per output
+  int pad0;
+  int8_t a_c[kMaxDirect], b_c[kMaxDirect];  // C bit -> A / B bit (-1 absent)
+  int8_t a_k[kMaxDirect], b_k[kMaxDirect];  // K bit -> A / B bit
+};
+
+struct PermuteArgs {
+  int rank;
+  int8_t perm[kMaxBits];  // out bit p = in bit perm[p]
+};
+
+struct AccumArgs {
+  const float2 *root;
+  double2 *acc;
+  GroupState *gs;
+  int g;                      // batch bits
+  int8_t beta_pos[kMaxBatch]; // root bit of batch bit j
+  double scale_re, scale_im;
+  int advance;                // 1: advance gs to the next group
+};
+
+cudaError_t launch_init_state(GroupState *gs, int64_t lo, int64_t hi, int64_t n_rows, cudaStream_t s);
+cudaError_t launch_leaf_build(const LeafJob *jobs, int n_jobs, const GroupState *gs, const uint8_t *bits, int nq,
+                              int g, cudaStream_t s);
+cudaError_t launch_direct(const DStep *steps, int n_steps, int64_t total_blocks, cudaStream_t s);
+cudaError_t launch_permute(const float2 *in, float2 *out, const PermuteArgs &a, cudaStream_t s);
+cudaError_t launch_cgemm_simt(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N,
+                              int64_t K, int64_t sA, int64_t sB, int64_t sC, cudaStream_t s);
+// Split-precision tensor-core product; returns cudaErrorNotSupported when the
+// shape is outside what the kernel handles (the planner checks first).
+cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M,
+                            int64_t N, int64_t K, int64_t sA, int64_t sB, int64_t sC, void *scratch,
+                            size_t scratch_bytes, cudaStream_t s);
+bool cgemm_tc_supported(int precision, int64_t M, int64_t N, int64_t K);
+size_t cgemm_tc_scratch_bytes(int precision, int64_t batch, int64_t N, int64_t K);
+cudaError_t launch_accumulate(const AccumArgs &a, cudaStream_t s);
+cudaError_t launch_accumulate_plain(const float2 *part, double2 *acc, int64_t n, double sre, double sim,
+                                    cudaStream_t s);
+
+}  // namespace dev
+}  // namespace tz

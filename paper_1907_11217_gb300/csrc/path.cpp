@@ -1,0 +1,313 @@
+// Contraction trees: analysis, the greedy builder, the cost model and the
+// slice selector. The paper defers its own contraction algorithm to its
+// earlier work; these are the library's own.
+#include <algorithm>
+#include <cmath>
+#include <queue>
+#include <unordered_map>
+
+#include "tz_internal.h"
+
+namespace tz {
+
+void validate_tree(const Network &net, const Pairs &pairs) {
+  const int L = (int)net.leaves.size();
+  if (L == 0) fail(TZ_EINVAL, "network has no tensors");
+  if ((int)pairs.size() != L - 1)
+    fail(TZ_EINVAL, "tree must have exactly n_tensors-1 pairs (got " + std::to_string(pairs.size()) + ", want " +
+                        std::to_string(L - 1) + ")");
+  std::vector<char> used(2 * L, 0);
+  for (size_t s = 0; s < pairs.size(); s++) {
+    int a = pairs[s].first, b = pairs[s].second, c = L + (int)s;
+    if (a < 0 || b < 0 || a >= c || b >= c || a == b) fail(TZ_EINVAL, "tree pair " + std::to_string(s) + " is invalid");
+    if (used[a] || used[b]) fail(TZ_EINVAL, "tree uses a node twice (pair " + std::to_string(s) + ")");
+    used[a] = used[b] = 1;
+  }
+}
+
+static std::vector<int> set_union(const std::vector<int> &a, const std::vector<int> &b) {
+  std::vector<int> r;
+  std::set_union(a.begin(), a.end(), b.begin(), b.end(), std::back_inserter(r));
+  return r;
+}
+
+TreeInfo analyse_tree(const Network &net, const Pairs &pairs, const std::vector<char> &sliced) {
+  TreeInfo ti;
+  const int L = (int)net.leaves.size();
+  const int I = (int)net.indices.size();
+  std::vector<int> cnt(I, 0);
+  ti.sets.resize(L + pairs.size());
+  ti.var.assign(L + pairs.size(), 0);
+  for (int l = 0; l < L; l++) {
+    const Leaf &lf = net.leaves[l];
+    bool var = lf.kind == LEAF_OUTPUT;
+    for (int i : lf.idx) {
+      if (!sliced.empty() && sliced[i]) {
+        var = true;
+        continue;
+      }
+      ti.sets[l].push_back(i);
+      cnt[i]++;
+    }
+    std::sort(ti.sets[l].begin(), ti.sets[l].end());
+    ti.var[l] = var;
+    ti.max_bits = std::max(ti.max_bits, (int)ti.sets[l].size());
+  }
+  ti.steps.reserve(pairs.size());
+  for (size_t s = 0; s < pairs.size(); s++) {
+    StepInfo st;
+    st.a = pairs[s].first;
+    st.b = pairs[s].second;
+    st.c = L + (int)s;
+    const auto &A = ti.sets[st.a], &B = ti.sets[st.b];
+    std::vector<int> C;
+    size_t ia = 0, ib = 0;
+    while (ia < A.size() || ib < B.size()) {
+      int i;
+      bool inA, inB;
+      if (ib >= B.size() || (ia < A.size() && A[ia] < B[ib])) {
+        i = A[ia++];
+        inA = true;
+        inB = false;
+      } else if (ia >= A.size() || B[ib] < A[ia]) {
+        i = B[ib++];
+        inA = false;
+        inB = true;
+      } else {
+        i = A[ia];
+        ia++;
+        ib++;
+        inA = inB = true;
+      }
+      if (inA && inB) {
+        cnt[i]--;
+        if (cnt[i] > 1 || net.is_open(i)) {
+          st.batch.push_back(i);
+          C.push_back(i);
+        } else {
+          st.contr.push_back(i);
+          cnt[i] = 0;
+        }
+      } else {
+        if (cnt[i] <= 1 && !net.is_open(i)) fail(TZ_EINVAL, "index held by one tensor only (dangling)");
+        (inA ? st.freeA : st.freeB).push_back(i);
+        C.push_back(i);
+      }
+    }
+    st.var = ti.var[st.a] || ti.var[st.b];
+    ti.var[st.c] = st.var;
+    ti.sets[st.c] = C;
+    ti.max_bits = std::max(ti.max_bits, (int)C.size());
+    ti.steps.push_back(std::move(st));
+  }
+  return ti;
+}
+
+double CostModel::step_time(const StepInfo &s) const {
+  const int all = s.bitsAll();
+  const double macs = std::ldexp(1.0, all);
+  const double bytes = 8.0 * (std::ldexp(1.0, s.bitsA()) + std::ldexp(1.0, s.bitsB()) + std::ldexp(1.0, s.bitsC()));
+  if (all <= small_log2) return small_step_s + bytes / hbm_bps + 8.0 * macs / simt_flops * 0.5;
+  double rate = simt_flops;
+  if (precision != TZ_C64_SIMT) {
+    // the tensor-core path needs a real contraction (k >= 2 complex, m >= 64)
+    int mk = (int)std::max(s.freeA.size(), s.freeB.size());
+    if (s.contr.size() >= 1 && mk >= 6) rate = tc_useful_flops;
+  }
+  return 3.0e-6 + std::max(8.0 * macs / rate, bytes / hbm_bps);
+}
+
+double group_time(const TreeInfo &ti, const CostModel &cm) {
+  double t = 0;
+  for (const StepInfo &s : ti.steps)
+    if (s.var) t += cm.step_time(s);
+  return t;
+}
+
+// ------------------------------------------------------------------ greedy
+Pairs greedy_tree(const Network &net, double alpha, double temperature, uint64_t seed) {
+  const int L = (int)net.leaves.size();
+  const int I = (int)net.indices.size();
+  std::vector<std::vector<int>> sets(L);
+  std::vector<std::vector<int>> holders(I);
+  std::vector<int> cnt(I, 0);
+  for (int l = 0; l < L; l++) {
+    sets[l] = net.leaves[l].idx;
+    std::sort(sets[l].begin(), sets[l].end());
+    for (int i : sets[l]) {
+      cnt[i]++;
+      holders[i].push_back(l);
+    }
+  }
+  std::vector<char> alive(L, 1);
+  uint64_t rng = seed;
+  auto gumbel = [&]() {
+    double u = ((splitmix64_next(rng) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    return -std::log(-std::log(u));
+  };
+  auto out_bits = [&](int a, int b) {
+    const auto &A = sets[a], &B = sets[b];
+    int n = 0;
+    size_t ia = 0, ib = 0;
+    while (ia < A.size() || ib < B.size()) {
+      if (ib >= B.size() || (ia < A.size() && A[ia] < B[ib])) {
+        n++;
+        ia++;
+      } else if (ia >= A.size() || B[ib] < A[ia]) {
+        n++;
+        ib++;
+      } else {
+        int i = A[ia];
+        if (cnt[i] - 1 > 1 || net.is_open(i)) n++;
+        ia++;
+        ib++;
+      }
+    }
+    return n;
+  };
+  struct Cand {
+    double score;
+    int a, b;
+    bool operator<(const Cand &o) const {
+      if (score != o.score) return score > o.score;  // min-heap
+      if (a != o.a) return a > o.a;
+      return b > o.b;
+    }
+  };
+  std::priority_queue<Cand> heap;
+  auto push = [&](int a, int b) {
+    if (a > b) std::swap(a, b);
+    double sc = std::ldexp(1.0, out_bits(a, b)) - alpha * (std::ldexp(1.0, (int)sets[a].size()) +
+                                                           std::ldexp(1.0, (int)sets[b].size()));
+    double lg = (sc >= 0 ? 1.0 : -1.0) * std::log2(1.0 + std::fabs(sc));
+    if (temperature > 0) lg -= temperature * gumbel();
+    heap.push({lg, a, b});
+  };
+  for (int i = 0; i < I; i++) {
+    if (net.is_open(i)) continue;
+    auto &h = holders[i];
+    for (size_t x = 0; x < h.size(); x++)
+      for (size_t y = x + 1; y < h.size(); y++) push(h[x], h[y]);
+  }
+  Pairs pairs;
+  pairs.reserve(L);
+  while (!heap.empty()) {
+    Cand cd_ = heap.top();
+    heap.pop();
+    int a = cd_.a, b = cd_.b;
+    if (!alive[a] || !alive[b]) continue;
+    // merge
+    const auto &A = sets[a], &B = sets[b];
+    std::vector<int> C;
+    size_t ia = 0, ib = 0;
+    while (ia < A.size() || ib < B.size()) {
+      if (ib >= B.size() || (ia < A.size() && A[ia] < B[ib])) {
+        C.push_back(A[ia++]);
+      } else if (ia >= A.size() || B[ib] < A[ia]) {
+        C.push_back(B[ib++]);
+      } else {
+        int i = A[ia];
+        cnt[i]--;
+        if (cnt[i] > 1 || net.is_open(i))
+          C.push_back(i);
+        else
+          cnt[i] = 0;
+        ia++;
+        ib++;
+      }
+    }
+    int c = (int)sets.size();
+    alive[a] = alive[b] = 0;
+    alive.push_back(1);
+    sets.push_back(C);
+    pairs.push_back({a, b});
+    for (int i : C) {
+      auto &h = holders[i];
+      h.erase(std::remove_if(h.begin(), h.end(), [&](int x) { return !alive[x]; }), h.end());
+      h.push_back(c);
+    }
+    std::vector<int> nb;
+    for (int i : C) {
+      if (net.is_open(i)) continue;
+      for (int d : holders[i])
+        if (d != c) nb.push_back(d);
+    }
+    std::sort(nb.begin(), nb.end());
+    nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+    for (int d : nb) push(c, d);
+  }
+  // components left (joined only through open indices): smallest first
+  std::vector<int> rest;
+  for (int x = 0; x < (int)sets.size(); x++)
+    if (alive[x]) rest.push_back(x);
+  while (rest.size() > 1) {
+    std::sort(rest.begin(), rest.end(), [&](int x, int y) {
+      if (sets[x].size() != sets[y].size()) return sets[x].size() < sets[y].size();
+      return x < y;
+    });
+    int a = rest[0], b = rest[1];
+    std::vector<int> C = set_union(sets[a], sets[b]);
+    int c = (int)sets.size();
+    sets.push_back(C);
+    alive[a] = alive[b] = 0;
+    alive.push_back(1);
+    pairs.push_back({a, b});
+    rest.erase(rest.begin(), rest.begin() + 2);
+    rest.push_back(c);
+  }
+  return pairs;
+}
+
+// ------------------------------------------------------------------ slicing
+std::vector<int> select_slices(const Network &net, const Pairs &pairs, int log2_max, int k_max,
+                               const CostModel &cm) {
+  std::vector<char> sliced(net.indices.size(), 0);
+  std::vector<int> out;
+  while ((int)out.size() < k_max) {
+    TreeInfo ti = analyse_tree(net, pairs, sliced);
+    if (ti.max_bits <= log2_max) break;
+    std::vector<int> cands;
+    for (const auto &s : ti.sets)
+      if ((int)s.size() == ti.max_bits)
+        for (int i : s)
+          if (!net.is_open(i)) cands.push_back(i);
+    std::sort(cands.begin(), cands.end());
+    cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+    if (cands.empty()) break;
+    int best = -1;
+    int best_max = 1 << 30;
+    double best_cost = 0;
+    for (int e : cands) {
+      int mx = 0;
+      for (const auto &s : ti.sets) {
+        int b = (int)s.size() - (std::binary_search(s.begin(), s.end(), e) ? 1 : 0);
+        mx = std::max(mx, b);
+      }
+      double cost = 0;
+      for (const StepInfo &st : ti.steps) {
+        if (!st.var && !std::binary_search(ti.sets[st.c].begin(), ti.sets[st.c].end(), e)) {
+          bool inA = std::binary_search(ti.sets[st.a].begin(), ti.sets[st.a].end(), e);
+          bool inB = std::binary_search(ti.sets[st.b].begin(), ti.sets[st.b].end(), e);
+          if (!inA && !inB) continue;  // stays a bind-time step
+        }
+        StepInfo s2 = st;
+        for (auto *v : {&s2.batch, &s2.contr, &s2.freeA, &s2.freeB}) {
+          auto it = std::find(v->begin(), v->end(), e);
+          if (it != v->end()) v->erase(it);
+        }
+        cost += cm.step_time(s2);
+      }
+      cost *= 2.0;  // twice as many slices
+      if (best < 0 || mx < best_max || (mx == best_max && cost < best_cost)) {
+        best = e;
+        best_max = mx;
+        best_cost = cost;
+      }
+    }
+    sliced[best] = 1;
+    out.push_back(best);
+  }
+  return out;
+}
+
+}  // namespace tz

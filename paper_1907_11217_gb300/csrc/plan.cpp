@@ -1,0 +1,806 @@
+// Plans: from (network, tree, sliced indices) to a launch schedule over one
+// device workspace. A group is one slice (Sec. 1: one subtask) for one chunk
+// of 2^batch_log2 bitstrings; every group runs the same launches.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <sstream>
+
+#include "plan.h"
+
+namespace tz {
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int pos_of(const std::vector<int> &lay, int idx) {
+  for (size_t p = 0; p < lay.size(); p++)
+    if (lay[p] == idx) return (int)p;
+  return -1;
+}
+
+// If lay = (perm of g1) ++ (perm of g2) ++ (perm of g3), return true and the
+// three orders as they appear in lay.
+bool groups_ok(const std::vector<int> &lay, const std::vector<int> &g1, const std::vector<int> &g2,
+               const std::vector<int> &g3, std::vector<int> *o1, std::vector<int> *o2, std::vector<int> *o3) {
+  if (lay.size() != g1.size() + g2.size() + g3.size()) return false;
+  size_t p = 0;
+  const std::vector<int> *gs[3] = {&g1, &g2, &g3};
+  std::vector<int> *os[3] = {o1, o2, o3};
+  for (int g = 0; g < 3; g++) {
+    std::vector<int> seg(lay.begin() + p, lay.begin() + p + gs[g]->size());
+    std::vector<int> a = seg, b = *gs[g];
+    std::sort(a.begin(), a.end());
+    std::sort(b.begin(), b.end());
+    if (a != b) return false;
+    if (os[g]) *os[g] = seg;
+    p += gs[g]->size();
+  }
+  return true;
+}
+
+std::vector<int> concat3(const std::vector<int> &a, const std::vector<int> &b, const std::vector<int> &c) {
+  std::vector<int> r = a;
+  r.insert(r.end(), b.begin(), b.end());
+  r.insert(r.end(), c.begin(), c.end());
+  return r;
+}
+
+// Relative order of the members of `set` as they appear in `lay`.
+std::vector<int> rel_order(const std::vector<int> &lay, const std::vector<int> &set) {
+  std::vector<int> r;
+  for (int i : lay)
+    if (std::find(set.begin(), set.end(), i) != set.end()) r.push_back(i);
+  return r;
+}
+
+// First-fit interval allocator over one region.
+struct Interval {
+  int64_t off, size;
+  int death;
+};
+int64_t first_fit(std::vector<Interval> &live, int64_t size, int birth, int death, int64_t *peak) {
+  live.erase(std::remove_if(live.begin(), live.end(), [&](const Interval &x) { return x.death < birth; }),
+             live.end());
+  std::sort(live.begin(), live.end(), [](const Interval &x, const Interval &y) { return x.off < y.off; });
+  int64_t cur = 0;
+  for (const Interval &x : live) {
+    if (x.off - cur >= size) break;
+    cur = std::max(cur, x.off + x.size);
+  }
+  live.push_back({cur, size, death});
+  *peak = std::max(*peak, cur + size);
+  return cur;
+}
+
+}  // namespace
+
+tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<int> &sliced, const tz_plan_opts &o) {
+  validate_tree(net, pairs);
+  const int I = (int)net.indices.size();
+  std::vector<char> flag(I, 0);
+  std::vector<int> slice_bit(I, -1);
+  for (size_t j = 0; j < sliced.size(); j++) {
+    int e = sliced[j];
+    if (e < 0 || e >= I) fail(TZ_EINVAL, "sliced edge id out of range");
+    if (net.is_open(e)) fail(TZ_EINVAL, "a batch index cannot be sliced");
+    if (flag[e]) fail(TZ_EINVAL, "sliced edge listed twice");
+    flag[e] = 1;
+    slice_bit[e] = (int)j;
+  }
+  if (sliced.size() > 40) fail(TZ_EUNSUPPORTED, "more than 40 sliced indices");
+  if (o.precision < TZ_C64_SIMT || o.precision > TZ_BF16X3) fail(TZ_EINVAL, "unknown precision");
+
+  auto p = std::make_unique<tz_plan>();
+  p->net = net;
+  p->pairs = pairs;
+  p->sliced = sliced;
+  p->slice_bit = slice_bit;
+  p->opts = o;
+  if (p->opts.small_log2 <= 0) p->opts.small_log2 = 20;
+  p->opts.small_log2 = std::min(p->opts.small_log2, 26);
+  p->max_rows = o.max_bitstrings > 0 ? o.max_bitstrings : 4096;
+  if (p->max_rows > (int64_t(1) << 24)) fail(TZ_EINVAL, "max_bitstrings above 2^24");
+  p->ti = analyse_tree(net, pairs, flag);
+  const TreeInfo &ti = p->ti;
+  if (ti.max_bits > dev::kMaxBits) fail(TZ_EUNSUPPORTED, "an intermediate tensor exceeds 2^40 elements");
+  const int L = (int)net.leaves.size();
+  const int NS = (int)ti.steps.size();
+  const int g = net.batch_log2;
+
+  // tensors: leaves, then step outputs
+  p->T.resize(L + NS);
+  for (int n = 0; n < L + NS; n++) {
+    p->T[n].var = ti.var[n];
+    if (n < L) p->T[n].leaf = n;
+  }
+  std::vector<int> consumer(L + NS, -1);
+  p->S.resize(NS);
+  for (int s = 0; s < NS; s++) {
+    const StepInfo &st = ti.steps[s];
+    PStep &ps = p->S[s];
+    ps.a = st.a;
+    ps.b = st.b;
+    ps.c = st.c;
+    ps.var = st.var;
+    ps.gemm = st.bitsAll() > p->opts.small_log2 || st.bitsC() > dev::kMaxDirect - 4 ||
+              (int)st.contr.size() > dev::kMaxDirect - 4;
+    consumer[st.a] = consumer[st.b] = s;
+  }
+  p->root = NS > 0 ? L + NS - 1 : 0;
+
+  auto set_of = [&](int node) { return ti.sets[node]; };
+
+  // ---------------------------------------------------------------- layouts
+  auto new_temp = [&](int src, const std::vector<int> &lay) {
+    PTensor t;
+    t.lay = lay;
+    t.var = p->T[src].var;
+    t.fixed = true;
+    p->T.push_back(t);
+    return (int)p->T.size() - 1;
+  };
+  for (int s = 0; s < NS; s++) {
+    const StepInfo &st = ti.steps[s];
+    PStep &ps = p->S[s];
+    if (!ps.gemm) {
+      for (int x : {st.a, st.b})
+        if (!p->T[x].fixed) {
+          p->T[x].lay = set_of(x);
+          p->T[x].fixed = true;
+        }
+      continue;
+    }
+    struct Option {
+      int X, Y;
+      std::vector<int> fX, fY, layX, layY, layC;
+      bool permX, permY;
+      double cost;
+    };
+    std::vector<Option> opts;
+    for (int role = 0; role < 2; role++) {
+      Option op;
+      op.X = role == 0 ? st.a : st.b;
+      op.Y = role == 0 ? st.b : st.a;
+      op.fX = role == 0 ? st.freeA : st.freeB;
+      op.fY = role == 0 ? st.freeB : st.freeA;
+      const PTensor &TX = p->T[op.X], &TY = p->T[op.Y];
+      std::vector<int> ko, bo, fxo, fyo;
+      bool xok = TX.fixed && groups_ok(TX.lay, st.contr, op.fX, st.batch, &ko, &fxo, &bo);
+      std::vector<int> ko2, bo2, fyo2;
+      bool yok = TY.fixed && groups_ok(TY.lay, st.contr, op.fY, st.batch, &ko2, &fyo2, &bo2);
+      if (!xok) {
+        if (yok) {
+          ko = ko2;
+          bo = bo2;
+        } else {
+          ko = st.contr;
+          bo = st.batch;
+        }
+        fxo = TX.fixed ? rel_order(TX.lay, op.fX) : op.fX;
+      }
+      fyo = TY.fixed ? rel_order(TY.lay, op.fY) : op.fY;
+      op.layX = concat3(ko, fxo, bo);
+      op.layY = concat3(ko, fyo, bo);
+      op.layC = concat3(fyo, fxo, bo);
+      op.permX = TX.fixed && TX.lay != op.layX;
+      op.permY = TY.fixed && TY.lay != op.layY;
+      op.cost = 0;
+      if (op.permX && TX.var) op.cost += 16.0 * TX.elems();
+      if (op.permY && TY.var) op.cost += 16.0 * TY.elems();
+      // look ahead: will the consumer have to permute C?
+      int cs = consumer[st.c];
+      if (cs >= 0 && p->S[cs].gemm && st.var) {
+        const StepInfo &pc = ti.steps[cs];
+        std::vector<int> own = st.c == pc.a ? pc.freeA : pc.freeB;
+        if (!groups_ok(op.layC, pc.contr, own, pc.batch, nullptr, nullptr, nullptr))
+          op.cost += 16.0 * std::ldexp(1.0, (int)op.layC.size()) * 0.999;
+      }
+      // prefer the larger operand as the row (M) operand
+      if (op.fX.size() < op.fY.size()) op.cost += 1e-3;
+      opts.push_back(op);
+    }
+    const Option &best = opts[0].cost <= opts[1].cost ? opts[0] : opts[1];
+    ps.opX = best.X;
+    ps.opY = best.Y;
+    if (!p->T[best.X].fixed) {
+      p->T[best.X].lay = best.layX;
+      p->T[best.X].fixed = true;
+    } else if (best.permX) {
+      ps.permX = best.X;
+      ps.opX = new_temp(best.X, best.layX);
+    }
+    if (!p->T[best.Y].fixed) {
+      p->T[best.Y].lay = best.layY;
+      p->T[best.Y].fixed = true;
+    } else if (best.permY) {
+      ps.permY = best.Y;
+      ps.opY = new_temp(best.Y, best.layY);
+    }
+    p->T[st.c].lay = best.layC;
+    p->T[st.c].fixed = true;
+    ps.M = int64_t(1) << best.fX.size();
+    ps.N = int64_t(1) << best.fY.size();
+    ps.K = int64_t(1) << st.contr.size();
+    ps.batch = int64_t(1) << st.batch.size();
+    ps.tc = o.precision != TZ_C64_SIMT && dev::cgemm_tc_supported(o.precision, ps.M, ps.N, ps.K);
+    if (ps.tc) ps.tc_scratch = (int64_t)dev::cgemm_tc_scratch_bytes(o.precision, ps.batch, ps.N, ps.K);
+  }
+  if (!p->T[p->root].fixed) {
+    p->T[p->root].lay = set_of(p->root);
+    p->T[p->root].fixed = true;
+  }
+  for (int n = 0; n < L + NS; n++)
+    if (!p->T[n].fixed) fail(TZ_EINVAL, "internal: tensor without layout");
+  // root must hold exactly the batch indices
+  for (int i : p->T[p->root].lay)
+    if (!net.is_open(i)) fail(TZ_EINVAL, "tree root keeps a wire index: the tree does not contract the network");
+
+  // full constant sources of sliced constant leaves
+  std::vector<int> full_src(L, -1);
+  for (int l = 0; l < L; l++) {
+    const Leaf &lf = net.leaves[l];
+    if (lf.kind != LEAF_CONST || !p->T[l].var) continue;
+    PTensor t;
+    t.lay = lf.idx;
+    t.var = false;
+    t.fixed = true;
+    t.leaf = l;
+    t.full_source = true;
+    p->T.push_back(t);
+    full_src[l] = (int)p->T.size() - 1;
+  }
+
+  // ---------------------------------------------------------------- schedule
+  std::vector<int> level(L + NS, 0);
+  int max_level[2] = {0, 0};
+  for (int s = 0; s < NS; s++) {
+    const StepInfo &st = ti.steps[s];
+    int lv = 0;
+    for (int x : {st.a, st.b})
+      if (x >= L && p->T[x].var == st.var) lv = std::max(lv, level[x]);
+    level[st.c] = lv + 1;
+    p->S[s].level = lv + 1;
+    max_level[st.var] = std::max(max_level[st.var], lv + 1);
+  }
+  std::vector<int> late_const_permutes;  // const operands of var GEMMs: permuted at bind time
+  for (int s = 0; s < NS; s++) {
+    const PStep &ps = p->S[s];
+    if (!ps.var || !ps.gemm) continue;
+    if (ps.permX >= 0 && !p->T[ps.permX].var) late_const_permutes.insert(late_const_permutes.end(), {ps.permX, ps.opX});
+    if (ps.permY >= 0 && !p->T[ps.permY].var) late_const_permutes.insert(late_const_permutes.end(), {ps.permY, ps.opY});
+  }
+  for (int pass = 0; pass < 2; pass++) {
+    bool var = pass == 1;
+    std::vector<Item> &items = var ? p->var_items : p->const_items;
+    if (var) items.push_back({IT_LEAVES});
+    for (int lv = 1; lv <= max_level[var]; lv++) {
+      Item d{IT_DIRECT};
+      d.first = (int)p->dsteps.size();
+      for (int s = 0; s < NS; s++) {
+        PStep &ps = p->S[s];
+        if (ps.var != var || ps.level != lv || ps.gemm) continue;
+        ps.dstep = (int)p->dsteps.size();
+        p->dsteps.push_back(dev::DStep{});
+        p->dstep_tensors.insert(p->dstep_tensors.end(), {ps.a, ps.b, ps.c});
+      }
+      d.count = (int)p->dsteps.size() - d.first;
+      if (d.count) items.push_back(d);
+      for (int s = 0; s < NS; s++) {
+        PStep &ps = p->S[s];
+        if (ps.var != var || ps.level != lv || !ps.gemm) continue;
+        for (int k = 0; k < 2; k++) {
+          int src = k == 0 ? ps.permX : ps.permY, dst = k == 0 ? ps.opX : ps.opY;
+          if (src < 0) continue;
+          if (var && !p->T[src].var) {
+            continue;  // constant operand of a group step: permuted once at bind time
+          } else {
+            Item it{IT_PERMUTE};
+            it.a = src;
+            it.b = dst;
+            items.push_back(it);
+          }
+        }
+        Item it{IT_GEMM};
+        it.a = s;
+        items.push_back(it);
+      }
+    }
+    if (!var) {
+      for (size_t j = 0; j < late_const_permutes.size(); j += 2) {
+        Item it{IT_PERMUTE};
+        it.a = late_const_permutes[j];
+        it.b = late_const_permutes[j + 1];
+        items.push_back(it);
+      }
+    } else {
+      items.push_back({IT_ACCUM});
+    }
+  }
+
+  // ---------------------------------------------------------------- memory
+  // lifetimes in item time; const tensors consumed by var work are persistent
+  const int NT = (int)p->T.size();
+  std::vector<int> birth[2], death[2];
+  for (int pass = 0; pass < 2; pass++) {
+    birth[pass].assign(NT, -1);
+    death[pass].assign(NT, -1);
+  }
+  std::vector<char> persistent(NT, 0);
+  auto use = [&](int pass, int t, int time) {
+    death[pass][t] = std::max(death[pass][t], time);
+    if (pass == 1 && !p->T[t].var) persistent[t] = 1;
+  };
+  for (int pass = 0; pass < 2; pass++) {
+    std::vector<Item> &items = pass ? p->var_items : p->const_items;
+    for (int time = 0; time < (int)items.size(); time++) {
+      const Item &it = items[time];
+      if (it.kind == IT_LEAVES) {
+        for (int l = 0; l < L; l++)
+          if (p->T[l].var) {
+            birth[1][l] = time;
+            if (full_src[l] >= 0) use(1, full_src[l], time);
+          }
+      } else if (it.kind == IT_DIRECT) {
+        for (int d = it.first; d < it.first + it.count; d++) {
+          use(pass, p->dstep_tensors[3 * d], time);
+          use(pass, p->dstep_tensors[3 * d + 1], time);
+          birth[pass][p->dstep_tensors[3 * d + 2]] = time;
+        }
+      } else if (it.kind == IT_PERMUTE) {
+        use(pass, it.a, time);
+        birth[pass][it.b] = time;
+      } else if (it.kind == IT_GEMM) {
+        const PStep &ps = p->S[it.a];
+        use(pass, ps.opX, time);
+        use(pass, ps.opY, time);
+        birth[pass][ps.c] = time;
+      } else if (it.kind == IT_ACCUM) {
+        use(pass, p->root, time);
+      }
+    }
+  }
+  // the root may be a leaf (no steps): built by the leaf builder
+  int64_t const_peak = 0, arena_peak = 0, arena_const_peak = 0;
+  std::vector<Interval> live_var, live_const;
+  // const region: constant leaves used anywhere, full sources, persistent step outputs
+  for (int t = 0; t < NT; t++) {
+    PTensor &pt = p->T[t];
+    if (pt.var) continue;
+    bool is_const_leaf = (t < L) || pt.full_source;
+    bool used = death[0][t] >= 0 || death[1][t] >= 0;
+    if (!used) continue;
+    if (is_const_leaf || persistent[t]) {
+      pt.region = R_CONST;
+      pt.off = const_peak;
+      const_peak = (int64_t)align256(const_peak + pt.bytes());
+    }
+  }
+  // arena: var tensors in the group pass, transient const tensors in the bind
+  // pass (the two overlay each other); requests in birth order
+  for (int pass = 1; pass >= 0; pass--) {
+    struct Req {
+      int birth, death, tensor, step;
+      int64_t size;
+    };
+    std::vector<Req> reqs;
+    for (int t = 0; t < NT; t++) {
+      PTensor &pt = p->T[t];
+      if (pt.region != R_NONE || birth[pass][t] < 0) continue;
+      if ((pass == 1) != pt.var) continue;
+      reqs.push_back(Req{birth[pass][t], std::max(death[pass][t], birth[pass][t]), t, -1, (int64_t)align256((size_t)pt.bytes())});
+    }
+    // tensor-core operand scratch of each GEMM: lives during its item only
+    std::vector<Item> &items = pass ? p->var_items : p->const_items;
+    for (int time = 0; time < (int)items.size(); time++) {
+      if (items[time].kind != IT_GEMM) continue;
+      PStep &ps = p->S[items[time].a];
+      if (ps.tc_scratch <= 0) continue;
+      reqs.push_back(Req{time, time, -1, items[time].a, (int64_t)align256((size_t)ps.tc_scratch)});
+    }
+    std::sort(reqs.begin(), reqs.end(), [](const Req &x, const Req &y) {
+      if (x.birth != y.birth) return x.birth < y.birth;
+      if (x.tensor != y.tensor) return x.tensor < y.tensor;
+      return x.step < y.step;
+    });
+    std::vector<Interval> &live = pass ? live_var : live_const;
+    int64_t *peak = pass ? &arena_peak : &arena_const_peak;
+    for (const Req &r : reqs) {
+      int64_t at = first_fit(live, r.size, r.birth, r.death, peak);
+      if (r.tensor >= 0) {
+        PTensor &pt = p->T[r.tensor];
+        pt.region = R_ARENA;
+        pt.birth = r.birth;
+        pt.death = r.death;
+        pt.off = at;
+      } else {
+        p->S[r.step].tc_scratch_off = at;
+      }
+    }
+  }
+  for (int t = 0; t < NT; t++) {
+    const PTensor &pt = p->T[t];
+    bool needed = death[0][t] >= 0 || death[1][t] >= 0 || birth[0][t] >= 0 || birth[1][t] >= 0;
+    if (needed && pt.region == R_NONE)
+      fail(TZ_EINVAL, "internal: tensor " + std::to_string(t) + " without memory (var " + std::to_string(pt.var) +
+                          ", births " + std::to_string(birth[0][t]) + "/" + std::to_string(birth[1][t]) +
+                          ", deaths " + std::to_string(death[0][t]) + "/" + std::to_string(death[1][t]) + ")");
+  }
+
+  // ---------------------------------------------------------------- tables
+  for (int d = 0; d < (int)p->dsteps.size(); d++) {
+    dev::DStep &ds = p->dsteps[d];
+    const PTensor &A = p->T[p->dstep_tensors[3 * d]];
+    const PTensor &B = p->T[p->dstep_tensors[3 * d + 1]];
+    const PTensor &C = p->T[p->dstep_tensors[3 * d + 2]];
+    std::memset(&ds, 0, sizeof(ds));
+    ds.nC = (int)C.lay.size();
+    std::vector<int> contr;
+    for (int i : A.lay)
+      if (pos_of(C.lay, i) < 0) contr.push_back(i);
+    ds.nK = (int)contr.size();
+    for (int j = 0; j < dev::kMaxDirect; j++) ds.a_c[j] = ds.b_c[j] = ds.a_k[j] = ds.b_k[j] = -1;
+    for (int j = 0; j < ds.nC; j++) {
+      ds.a_c[j] = (int8_t)pos_of(A.lay, C.lay[j]);
+      ds.b_c[j] = (int8_t)pos_of(B.lay, C.lay[j]);
+    }
+    for (int j = 0; j < ds.nK; j++) {
+      ds.a_k[j] = (int8_t)pos_of(A.lay, contr[j]);
+      ds.b_k[j] = (int8_t)pos_of(B.lay, contr[j]);
+      if (ds.b_k[j] < 0) fail(TZ_EINVAL, "internal: summed index missing from one operand");
+    }
+    int want = std::max(0, 12 - ds.nC);
+    ds.split = std::min({ds.nK, want, 8});
+  }
+  for (Item &it : p->var_items) {
+    if (it.kind != IT_DIRECT) continue;
+    int64_t b = 0;
+    for (int d = it.first; d < it.first + it.count; d++) {
+      p->dsteps[d].block_begin = b;
+      b += std::max<int64_t>(1, ((int64_t(1) << (p->dsteps[d].nC + p->dsteps[d].split)) + 255) / 256);
+    }
+    it.blocks = b;
+  }
+  for (Item &it : p->const_items) {
+    if (it.kind != IT_DIRECT) continue;
+    int64_t b = 0;
+    for (int d = it.first; d < it.first + it.count; d++) {
+      p->dsteps[d].block_begin = b;
+      b += std::max<int64_t>(1, ((int64_t(1) << (p->dsteps[d].nC + p->dsteps[d].split)) + 255) / 256);
+    }
+    it.blocks = b;
+  }
+  // leaf jobs
+  for (int l = 0; l < L; l++) {
+    if (!p->T[l].var) continue;
+    const Leaf &lf = net.leaves[l];
+    const PTensor &dst = p->T[l];
+    dev::LeafJob j;
+    std::memset(&j, 0, sizeof(j));
+    j.rank = (int)dst.lay.size();
+    if (j.rank > 24) fail(TZ_EUNSUPPORTED, "leaf tensor above 2^24 elements");
+    for (int x = 0; x < 24; x++) j.src_pos[x] = -1;
+    for (int x = 0; x < 8; x++) j.fixed_src_pos[x] = j.fixed_slice_bit[x] = j.beta_dst_pos[x] = -1;
+    j.e_dst_pos = j.e_slice_bit = -1;
+    if (lf.kind == LEAF_OUTPUT) {
+      j.kind = dev::LJ_OUTPUT;
+      j.qubit = lf.qubit;
+      j.rc = lf.rc;
+      if (lf.rc == 1) {
+        int e = lf.idx[0];
+        if (slice_bit[e] >= 0)
+          j.e_slice_bit = slice_bit[e];
+        else
+          j.e_dst_pos = pos_of(dst.lay, e);
+      }
+      for (int i : lf.idx) {
+        if (!net.is_open(i)) continue;
+        j.beta_dst_pos[net.indices[i].segment] = (int8_t)pos_of(dst.lay, i);
+      }
+      for (int x = 0; x < 2 * (1 << lf.rc) && x < 4; x++)
+        j.M[x] = make_float2((float)lf.data[x].real(), (float)lf.data[x].imag());
+      p->job_tensors.insert(p->job_tensors.end(), {l, -1});
+    } else {
+      j.kind = dev::LJ_GATHER;
+      const PTensor &src = p->T[full_src[l]];
+      for (int x = 0; x < j.rank; x++) j.src_pos[x] = (int8_t)pos_of(src.lay, dst.lay[x]);
+      for (size_t x = 0; x < src.lay.size(); x++) {
+        int e = src.lay[x];
+        if (slice_bit[e] < 0) continue;
+        if (j.n_fixed >= 8) fail(TZ_EUNSUPPORTED, "leaf with more than 8 sliced indices");
+        j.fixed_src_pos[j.n_fixed] = (int8_t)x;
+        j.fixed_slice_bit[j.n_fixed] = (int8_t)slice_bit[e];
+        j.n_fixed++;
+      }
+      p->job_tensors.insert(p->job_tensors.end(), {l, full_src[l]});
+    }
+    p->jobs.push_back(j);
+  }
+
+  // workspace layout
+  size_t off = 0;
+  p->off_dsteps = off;
+  off = align256(off + sizeof(dev::DStep) * std::max<size_t>(1, p->dsteps.size()));
+  p->off_jobs = off;
+  off = align256(off + sizeof(dev::LeafJob) * std::max<size_t>(1, p->jobs.size()));
+  p->off_gs = off;
+  off = align256(off + sizeof(dev::GroupState));
+  p->off_bits = off;
+  off = align256(off + (size_t)p->max_rows * net.n_qubits);
+  p->off_acc = off;
+  off = align256(off + (size_t)p->max_rows * 16);
+  p->off_const = off;
+  p->const_bytes = (size_t)const_peak;
+  off = align256(off + p->const_bytes);
+  p->off_arena = off;
+  p->arena_bytes = (size_t)std::max(arena_peak, arena_const_peak);
+  off = align256(off + p->arena_bytes);
+  p->total_bytes = off;
+
+  // stats
+  tz_plan_stats &stt = p->stats;
+  stt.n_steps = NS;
+  stt.k = (int)sliced.size();
+  stt.batch_log2 = g;
+  stt.max_log2 = ti.max_bits;
+  for (int s = 0; s < NS; s++) {
+    const StepInfo &st = ti.steps[s];
+    if (!st.var) {
+      stt.n_const_steps++;
+      continue;
+    }
+    double fl = 8.0 * std::ldexp(1.0, st.bitsAll());
+    stt.flops_per_group += fl;
+    stt.bytes_per_group +=
+        8.0 * (std::ldexp(1.0, st.bitsA()) + std::ldexp(1.0, st.bitsB()) + std::ldexp(1.0, st.bitsC()));
+    if (p->S[s].gemm) {
+      stt.n_gemm_steps++;
+      stt.gemm_flops_per_group += fl;
+    }
+  }
+  for (const Item &it : p->var_items)
+    if (it.kind == IT_PERMUTE) {
+      stt.n_permutes++;
+      stt.permute_bytes_per_group += 16.0 * p->T[it.a].elems();
+    }
+  stt.n_launches_per_group = (int)p->var_items.size();
+  stt.workspace_bytes = p->total_bytes;
+  stt.const_bytes = p->const_bytes;
+  p->lo = 0;
+  p->hi = int64_t(1) << sliced.size();
+  return p.release();
+}
+
+std::string plan_describe(const tz_plan *p) {
+  std::ostringstream o;
+  o << "{\"tensors\": [";
+  for (size_t t = 0; t < p->T.size(); t++) {
+    const PTensor &x = p->T[t];
+    o << (t ? "," : "") << "{\"id\":" << t << ",\"lay\":[";
+    for (size_t q = 0; q < x.lay.size(); q++) o << (q ? "," : "") << x.lay[q];
+    o << "],\"var\":" << (x.var ? 1 : 0) << ",\"region\":" << x.region << ",\"off\":" << x.off
+      << ",\"leaf\":" << x.leaf << ",\"full\":" << (x.full_source ? 1 : 0) << "}";
+  }
+  o << "],\"steps\":[";
+  for (size_t s = 0; s < p->S.size(); s++) {
+    const PStep &x = p->S[s];
+    o << (s ? "," : "") << "{\"a\":" << x.a << ",\"b\":" << x.b << ",\"c\":" << x.c << ",\"var\":" << x.var
+      << ",\"gemm\":" << x.gemm << ",\"tc\":" << x.tc << ",\"opX\":" << x.opX << ",\"opY\":" << x.opY
+      << ",\"M\":" << x.M << ",\"N\":" << x.N << ",\"K\":" << x.K << ",\"batch\":" << x.batch
+      << ",\"level\":" << x.level << ",\"dstep\":" << x.dstep << ",\"permX\":" << x.permX << ",\"permY\":" << x.permY << "}";
+  }
+  auto items = [&](const std::vector<Item> &v) {
+    o << "[";
+    for (size_t i = 0; i < v.size(); i++)
+      o << (i ? "," : "") << "[" << v[i].kind << "," << v[i].a << "," << v[i].b << "," << v[i].first << ","
+        << v[i].count << "," << v[i].blocks << "]";
+    o << "]";
+  };
+  o << "],\"var_items\":";
+  items(p->var_items);
+  o << ",\"const_items\":";
+  items(p->const_items);
+  o << ",\"root\":" << p->root << ",\"sliced\":[";
+  for (size_t j = 0; j < p->sliced.size(); j++) o << (j ? "," : "") << p->sliced[j];
+  o << "],\"scalar\":[" << p->net.scalar.real() << "," << p->net.scalar.imag() << "],\"leaves\":[";
+  o.precision(17);
+  for (size_t l = 0; l < p->net.leaves.size(); l++) {
+    const Leaf &lf = p->net.leaves[l];
+    o << (l ? "," : "") << "{\"kind\":" << lf.kind << ",\"qubit\":" << lf.qubit << ",\"rc\":" << lf.rc
+      << ",\"idx\":[";
+    for (size_t q = 0; q < lf.idx.size(); q++) o << (q ? "," : "") << lf.idx[q];
+    o << "],\"data\":[";
+    for (size_t q = 0; q < lf.data.size(); q++)
+      o << (q ? "," : "") << "[" << lf.data[q].real() << "," << lf.data[q].imag() << "]";
+    o << "]}";
+  }
+  o << "],\"open\":[";
+  bool first = true;
+  for (size_t i = 0; i < p->net.indices.size(); i++)
+    if (p->net.is_open((int)i)) {
+      o << (first ? "" : ",") << "[" << i << "," << p->net.indices[i].segment << "]";
+      first = false;
+    }
+  o << "]}";
+  return o.str();
+}
+
+// ------------------------------------------------------------------ device
+static void *tensor_ptr(const tz_plan *p, int t) {
+  const PTensor &x = p->T[t];
+  if (x.region == R_CONST) return p->ws + p->off_const + x.off;
+  if (x.region == R_ARENA) return p->ws + p->off_arena + x.off;
+  fail(TZ_EINVAL, "internal: tensor has no memory");
+}
+
+static void run_items(tz_plan *p, const std::vector<Item> &items) {
+  cudaStream_t s = p->stream;
+  auto *gs = reinterpret_cast<dev::GroupState *>(p->ws + p->off_gs);
+  for (const Item &it : items) {
+    switch (it.kind) {
+      case IT_LEAVES:
+        if (!p->jobs.empty())
+          cuda_check(dev::launch_leaf_build(reinterpret_cast<const dev::LeafJob *>(p->ws + p->off_jobs),
+                                            (int)p->jobs.size(), gs,
+                                            reinterpret_cast<const uint8_t *>(p->ws + p->off_bits),
+                                            p->net.n_qubits, p->net.batch_log2, s),
+                     "leaf build");
+        break;
+      case IT_DIRECT:
+        cuda_check(dev::launch_direct(reinterpret_cast<const dev::DStep *>(p->ws + p->off_dsteps) + it.first,
+                                      it.count, it.blocks, s),
+                   "direct steps");
+        break;
+      case IT_PERMUTE: {
+        dev::PermuteArgs a{};
+        const PTensor &src = p->T[it.a], &dst = p->T[it.b];
+        a.rank = (int)dst.lay.size();
+        for (int q = 0; q < a.rank; q++) a.perm[q] = (int8_t)pos_of(src.lay, dst.lay[q]);
+        cuda_check(dev::launch_permute((const float2 *)tensor_ptr(p, it.a), (float2 *)tensor_ptr(p, it.b), a, s),
+                   "permute");
+        break;
+      }
+      case IT_GEMM: {
+        const PStep &ps = p->S[it.a];
+        const float2 *X = (const float2 *)tensor_ptr(p, ps.opX);
+        const float2 *Y = (const float2 *)tensor_ptr(p, ps.opY);
+        float2 *C = (float2 *)tensor_ptr(p, ps.c);
+        if (ps.tc) {
+          void *scr = p->ws + p->off_arena + ps.tc_scratch_off;
+          cuda_check(dev::launch_cgemm_tc(p->opts.precision, X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.M * ps.K,
+                                          ps.N * ps.K, ps.M * ps.N, scr, (size_t)ps.tc_scratch, s),
+                     "tensor-core gemm");
+        } else {
+          cuda_check(dev::launch_cgemm_simt(X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.M * ps.K, ps.N * ps.K,
+                                            ps.M * ps.N, s),
+                     "simt gemm");
+        }
+        break;
+      }
+      case IT_ACCUM: {
+        dev::AccumArgs a{};
+        a.root = (const float2 *)tensor_ptr(p, p->root);
+        a.acc = reinterpret_cast<double2 *>(p->ws + p->off_acc);
+        a.gs = gs;
+        a.g = p->net.batch_log2;
+        for (int j = 0; j < dev::kMaxBatch; j++) a.beta_pos[j] = -1;
+        for (size_t q = 0; q < p->T[p->root].lay.size(); q++) {
+          int i = p->T[p->root].lay[q];
+          a.beta_pos[p->net.indices[i].segment] = (int8_t)q;
+        }
+        a.scale_re = p->net.scalar.real();
+        a.scale_im = p->net.scalar.imag();
+        a.advance = 1;
+        cuda_check(dev::launch_accumulate(a, s), "accumulate");
+        break;
+      }
+    }
+  }
+}
+
+void plan_bind(tz_plan *p, void *ws, size_t bytes) {
+  if (!ws) fail(TZ_EINVAL, "workspace pointer is NULL");
+  if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) fail(TZ_EINVAL, "workspace must be 256-byte aligned");
+  if (bytes < p->total_bytes)
+    fail(TZ_ENOMEM, "workspace too small: need " + std::to_string(p->total_bytes) + " bytes");
+  cuda_check(cudaSetDevice(p->opts.device), "cudaSetDevice");
+  if (p->graph_exec) {
+    cudaGraphExecDestroy(p->graph_exec);
+    p->graph_exec = nullptr;
+  }
+  if (p->graph) {
+    cudaGraphDestroy(p->graph);
+    p->graph = nullptr;
+  }
+  p->ws = static_cast<char *>(ws);
+  p->ws_bytes = bytes;
+  p->stream = static_cast<cudaStream_t>(p->opts.stream);
+  cudaStream_t s = p->stream;
+  // tables with resolved pointers
+  std::vector<dev::DStep> ds = p->dsteps;
+  for (size_t d = 0; d < ds.size(); d++) {
+    ds[d].A = (const float2 *)tensor_ptr(p, p->dstep_tensors[3 * d]);
+    ds[d].B = (const float2 *)tensor_ptr(p, p->dstep_tensors[3 * d + 1]);
+    ds[d].C = (float2 *)tensor_ptr(p, p->dstep_tensors[3 * d + 2]);
+  }
+  std::vector<dev::LeafJob> js = p->jobs;
+  for (size_t j = 0; j < js.size(); j++) {
+    js[j].dst = (float2 *)tensor_ptr(p, p->job_tensors[2 * j]);
+    js[j].src = p->job_tensors[2 * j + 1] >= 0 ? (const float2 *)tensor_ptr(p, p->job_tensors[2 * j + 1]) : nullptr;
+  }
+  if (!ds.empty())
+    cuda_check(cudaMemcpyAsync(p->ws + p->off_dsteps, ds.data(), ds.size() * sizeof(dev::DStep),
+                               cudaMemcpyHostToDevice, s),
+               "upload step tables");
+  if (!js.empty())
+    cuda_check(cudaMemcpyAsync(p->ws + p->off_jobs, js.data(), js.size() * sizeof(dev::LeafJob),
+                               cudaMemcpyHostToDevice, s),
+               "upload leaf tables");
+  // constant leaves, in their planned storage order
+  std::vector<float2> host;
+  for (size_t t = 0; t < p->T.size(); t++) {
+    const PTensor &x = p->T[t];
+    if (x.region != R_CONST || x.leaf < 0) continue;
+    if (x.var) continue;
+    const Leaf &lf = p->net.leaves[x.leaf];
+    host.assign(x.elems(), make_float2(0, 0));
+    std::vector<int> srcpos(x.lay.size());
+    for (size_t q = 0; q < x.lay.size(); q++) srcpos[q] = pos_of(lf.idx, x.lay[q]);
+    for (int64_t e = 0; e < x.elems(); e++) {
+      int64_t so = 0;
+      for (size_t q = 0; q < x.lay.size(); q++) so |= ((e >> q) & 1) << srcpos[q];
+      host[e] = make_float2((float)lf.data[so].real(), (float)lf.data[so].imag());
+    }
+    cuda_check(cudaMemcpyAsync(tensor_ptr(p, (int)t), host.data(), host.size() * sizeof(float2),
+                               cudaMemcpyHostToDevice, s),
+               "upload constants");
+    cuda_check(cudaStreamSynchronize(s), "sync");  // host buffer is reused
+  }
+  run_items(p, p->const_items);
+  cuda_check(cudaStreamSynchronize(s), "bind-time steps");
+  p->bound = true;
+}
+
+void plan_run(tz_plan *p, int64_t n_rows) {
+  if (!p->bound) fail(TZ_EINVAL, "plan has no workspace bound (tz_plan_bind_workspace)");
+  cuda_check(cudaSetDevice(p->opts.device), "cudaSetDevice");
+  cudaStream_t s = p->stream;
+  auto *gs = reinterpret_cast<dev::GroupState *>(p->ws + p->off_gs);
+  cuda_check(cudaMemsetAsync(p->ws + p->off_acc, 0, (size_t)n_rows * 16, s), "clear accumulator");
+  cuda_check(dev::launch_init_state(gs, p->lo, p->hi, n_rows, s), "init group state");
+  const int64_t chunk = int64_t(1) << p->net.batch_log2;
+  const int64_t n_chunks = (n_rows + chunk - 1) / chunk;
+  const int64_t n_groups = n_chunks * (p->hi - p->lo);
+  const bool graph = p->opts.use_graph && s != nullptr;
+  if (graph && !p->graph_exec) {
+    cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+    try {
+      run_items(p, p->var_items);
+    } catch (...) {
+      cudaGraph_t g2;
+      cudaStreamEndCapture(s, &g2);
+      if (g2) cudaGraphDestroy(g2);
+      throw;
+    }
+    cuda_check(cudaStreamEndCapture(s, &p->graph), "end capture");
+    cuda_check(cudaGraphInstantiate(&p->graph_exec, p->graph, 0), "instantiate graph");
+  }
+  for (int64_t gi = 0; gi < n_groups; gi++) {
+    if (graph)
+      cuda_check(cudaGraphLaunch(p->graph_exec, s), "graph launch");
+    else
+      run_items(p, p->var_items);
+  }
+}
+
+void plan_destroy(tz_plan *p) {
+  if (!p) return;
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  delete p;
+}
+
+}  // namespace tz

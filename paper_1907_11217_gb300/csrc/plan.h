@@ -1,0 +1,88 @@
+// Internal plan structure (host side).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+#include "tz_internal.h"
+
+namespace tz {
+
+enum Region { R_NONE = 0, R_CONST = 1, R_ARENA = 2 };
+enum ItemKind { IT_LEAVES = 0, IT_DIRECT = 1, IT_PERMUTE = 2, IT_GEMM = 3, IT_ACCUM = 4 };
+
+struct PTensor {
+  std::vector<int> lay;   // index ids, lay[p] = bit p of the element offset
+  bool var = false;       // recomputed every group
+  bool fixed = false;     // layout decided
+  int region = R_NONE;
+  int64_t off = -1;       // byte offset within its region
+  int birth = -1, death = -1;
+  int leaf = -1;          // network leaf it holds (or the full source of)
+  bool full_source = false;  // full constant source of a sliced leaf
+  int64_t elems() const { return int64_t(1) << lay.size(); }
+  int64_t bytes() const { return elems() * 8; }
+};
+
+struct PStep {
+  int a, b, c;
+  bool var = false, gemm = false, tc = false;
+  int opX = -1, opY = -1;     // tensors fed to the GEMM (after permutes)
+  int permX = -1, permY = -1; // permute sources (or -1)
+  int64_t M = 0, N = 0, K = 0, batch = 0;
+  int level = 0;
+  int dstep = -1;             // index into dsteps (direct steps)
+  int64_t tc_scratch = 0;     // bytes of tensor-core operand scratch
+  int64_t tc_scratch_off = -1;
+};
+
+struct Item {
+  int kind;
+  int a = -1, b = -1;         // PERMUTE: src, dst tensors; GEMM: step
+  int first = 0, count = 0;   // DIRECT: dsteps range
+  int64_t blocks = 0;         // DIRECT: total blocks
+};
+
+}  // namespace tz
+
+struct tz_plan {
+  tz::Network net;
+  tz::Pairs pairs;
+  std::vector<int> sliced;
+  std::vector<int> slice_bit;  // per index: slice bit number or -1
+  tz_plan_opts opts{};
+  tz::TreeInfo ti;
+  std::vector<tz::PTensor> T;
+  std::vector<tz::PStep> S;
+  std::vector<tz::Item> var_items, const_items;
+  std::vector<tz::dev::DStep> dsteps;
+  std::vector<int> dstep_tensors;  // 3 tensor ids per dstep (A, B, C)
+  std::vector<tz::dev::LeafJob> jobs;
+  std::vector<int> job_tensors;    // 2 per job (dst, src or -1)
+  int root = -1;
+  int64_t max_rows = 0;
+  // workspace layout (bytes)
+  size_t off_dsteps = 0, off_jobs = 0, off_gs = 0, off_bits = 0, off_acc = 0, off_const = 0, off_arena = 0;
+  size_t const_bytes = 0, arena_bytes = 0, total_bytes = 0;
+  // device state
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaStream_t stream = nullptr;
+  bool bound = false;
+  int64_t lo = 0, hi = 1;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  tz_plan_stats stats{};
+};
+
+namespace tz {
+tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<int> &sliced, const tz_plan_opts &o);
+void plan_bind(tz_plan *p, void *ws, size_t bytes);
+// Contract all groups for n rows already in the plan's bitstring buffer;
+// leaves the FP64 sums in the plan's accumulator (asynchronous).
+void plan_run(tz_plan *p, int64_t n_rows);
+void plan_destroy(tz_plan *p);
+std::string plan_describe(const tz_plan *p);
+inline void cuda_check(cudaError_t e, const char *what) {
+  if (e != cudaSuccess) fail(TZ_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+}  // namespace tz

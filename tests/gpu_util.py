@@ -1,0 +1,34 @@
+"""Helpers shared by the GPU tests: plan construction through the C ABI and
+the amplitude error measure.
+
+Error measure: amplitudes of an n-qubit random circuit have the
+Porter-Thomas scale 2^(-n/2); FP32 rounding errors of a contraction scale
+with the magnitudes of the summed terms, i.e. with that scale, not with a
+single (possibly tiny) amplitude. The relative error of amplitude j is
+|a_gpu - a_ref| / max(|a_ref|, 2^(-n/2)).
+"""
+import numpy as np
+
+import tz_inputs as ti
+
+
+def rel_err(got, ref, n_qubits):
+    got, ref = np.asarray(got), np.asarray(ref)
+    floor = 2.0 ** (-n_qubits / 2)
+    return float(np.max(np.abs(got - ref) / np.maximum(np.abs(ref), floor)))
+
+
+def make_plan(tz, spec, batch_log2=0, log2_max=0, precision="c64", small_log2=0, restarts=4, seed=1,
+              use_graph=False, stream=None, k_max=40, max_bitstrings=0):
+    c = tz.tz_circuit_from_spec(spec)
+    net = tz.tz_network_from_circuit(c, batch_log2)
+    tree = tz.tz_path_greedy(net, restarts=restarts, seed=seed, log2_max_intermediate=log2_max, precision=precision)
+    sl = tz.tz_slice_select(net, tree, log2_max, k_max) if log2_max > 0 else []
+    plan = tz.tz_plan_create(net, tree, sl, precision=precision, small_log2=small_log2, use_graph=use_graph,
+                             stream=stream, max_bitstrings=max_bitstrings)
+    plan.bind()
+    return plan, net, tree, sl
+
+
+def grid_spec(rows, cols, t, seed):
+    return ti.circuit_to_spec(rows * cols, ti.generate_circuit(ti.grid(rows, cols), t, seed))

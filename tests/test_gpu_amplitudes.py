@@ -1,0 +1,102 @@
+"""Amplitude parity of the whole path on the GPU (C ABI) against the FP64
+oracle (state vector and plain-wire contractor)."""
+import os
+
+import numpy as np
+import pytest
+
+import tz_inputs as ti
+from oracle import statevector as sv
+from oracle import tn
+from tests.gpu_util import grid_spec, make_plan, rel_err
+
+pytestmark = pytest.mark.gpu
+TOL_C64 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def tz():
+    import torch
+    import paper_1907_11217_gb300 as tz
+    assert torch.cuda.is_available()
+    return tz
+
+
+def test_config1_4x4_depth10_single_bitstring(tz):
+    """4x4 grid, depth 1+10+1, seed 1, one bitstring, no slicing, complex64."""
+    spec = grid_spec(4, 4, 10, 1)
+    bits = ti.random_bitstrings(16, 1, 101)
+    plan, *_ = make_plan(tz, spec)
+    got = tz.tz_contract_amplitudes(plan, bits)
+    ref = sv.amplitudes(spec, bits)
+    assert rel_err(got, ref, 16) <= TOL_C64
+
+
+def test_golden_closed_forms(tz):
+    path = os.path.join(os.path.dirname(__file__), "golden", "closed_forms.txt")
+    for ln in open(path):
+        if not ln.strip() or ln.startswith("#"):
+            continue
+        name, spec, bits, re, im = [f.strip() for f in ln.split("|")]
+        spec = spec.replace(";", "\n") + "\n"
+        x = np.array([[int(ch) for ch in bits]], dtype=np.uint8)
+        plan, *_ = make_plan(tz, spec)
+        got = tz.tz_contract_amplitudes(plan, x)[0]
+        assert abs(got - complex(float(re), float(im))) <= 1e-6, name
+
+
+@pytest.mark.parametrize("g", [0, 2, 4])
+@pytest.mark.parametrize("small", [20, 4])
+def test_batched_bitstrings_ragged(tz, g, small):
+    spec = grid_spec(4, 4, 10, 1)
+    bits = ti.random_bitstrings(16, 37, 7)   # 37 rows: a ragged last chunk
+    plan, *_ = make_plan(tz, spec, batch_log2=g, small_log2=small)
+    got = tz.tz_contract_amplitudes(plan, bits)
+    assert rel_err(got, sv.amplitudes(spec, bits), 16) <= TOL_C64
+
+
+@pytest.mark.parametrize("rows,cols,t,seed,log2max,g,small", [
+    (4, 4, 10, 1, 4, 0, 3), (4, 5, 12, 3, 6, 1, 5), (5, 5, 16, 4, 8, 2, 6), (4, 4, 20, 6, 5, 0, 20)])
+def test_sliced_against_statevector(tz, rows, cols, t, seed, log2max, g, small):
+    spec = grid_spec(rows, cols, t, seed)
+    n = rows * cols
+    bits = ti.random_bitstrings(n, 6, seed + 50)
+    plan, net, tree, sl = make_plan(tz, spec, batch_log2=g, log2_max=log2max, small_log2=small)
+    assert len(sl) >= 1
+    got = tz.tz_contract_amplitudes(plan, bits)
+    assert rel_err(got, sv.amplitudes(spec, bits), n) <= TOL_C64
+
+
+def test_slice_ranges_add_up_and_match_oracle_partials(tz):
+    spec = grid_spec(4, 5, 12, 3)
+    bits = ti.random_bitstrings(20, 3, 8)
+    plan, net, tree, sl = make_plan(tz, spec, log2_max=5, small_log2=5)
+    k = len(sl)
+    assert k >= 3
+    full = tz.tz_contract_amplitudes(plan, bits)
+    parts = []
+    for s in range(1 << k):
+        plan.set_slice_range(s, s + 1)
+        parts.append(tz.tz_contract_amplitudes(plan, bits))
+    assert rel_err(np.sum(parts, axis=0), full, 20) <= 1e-6
+    segs = plan.sliced_segments()
+    c = tn.Contractor(spec, sliced=segs)
+    for s in (0, (1 << k) - 1, (1 << k) // 3):
+        ref = np.array([c.partial(x, s) for x in bits])
+        assert rel_err(parts[s], ref, 20) <= TOL_C64
+
+
+def test_device_entry_point_and_graph(tz):
+    import torch
+    spec = grid_spec(4, 4, 10, 1)
+    bits = ti.random_bitstrings(16, 20, 9)
+    stream = torch.cuda.Stream()
+    plan, *_ = make_plan(tz, spec, batch_log2=2, log2_max=4, small_log2=4, use_graph=True, stream=stream)
+    d_bits = torch.from_numpy(bits).cuda()
+    d_out = torch.zeros(40, dtype=torch.float64, device="cuda")
+    for _ in range(2):   # second call replays the captured graph
+        d_out.zero_()
+        tz.tz_contract_amplitudes_device(plan, d_bits, d_out)
+        stream.synchronize()
+        got = d_out.cpu().numpy().view(np.complex128)
+        assert rel_err(got, sv.amplitudes(spec, bits), 16) <= TOL_C64

@@ -1,0 +1,71 @@
+"""Per-kernel parity on the GPU, through the C ABI (tz_op_*), against the
+plain definitions in oracle.linalg."""
+import numpy as np
+import pytest
+
+from oracle import linalg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import paper_1907_11217_gb300 as tz
+    assert torch.cuda.is_available()
+    return tz, torch
+
+
+def c64(torch, rng, shape):
+    x = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
+    return x, torch.from_numpy(x.view(np.float32).copy()).cuda()
+
+
+@pytest.mark.parametrize("rank", [0, 1, 3, 5, 9, 10, 11, 14, 17, 22])
+def test_permute_bit_exact(env, rank):
+    tz, torch = env
+    rng = np.random.default_rng(rank)
+    x, dx = c64(torch, rng, 1 << rank)
+    perms = [list(range(rank)), list(range(rank))[::-1], list(rng.permutation(rank))]
+    if rank > 6:
+        p = list(range(rank))
+        p[:3], p[-3:] = p[-3:], p[:3]
+        perms.append(p)
+    for perm in perms:
+        dy = torch.empty_like(dx)
+        tz.tz_op_permute(dx, dy, perm)
+        torch.cuda.synchronize()
+        y = dy.cpu().numpy().view(np.complex64)
+        assert np.array_equal(y, linalg.bit_permute(x, perm)), perm
+
+
+@pytest.mark.parametrize("batch,m,n,k", [(1, 1, 1, 1), (1, 7, 3, 5), (3, 64, 64, 8), (2, 130, 17, 33),
+                                         (1, 1000, 2, 4), (5, 33, 80, 1), (1, 4096, 16, 64), (16, 256, 256, 256),
+                                         (1, 1, 300, 9)])
+def test_cgemm_simt(env, batch, m, n, k):
+    tz, torch = env
+    rng = np.random.default_rng(m * 7 + n)
+    A, dA = c64(torch, rng, (batch, m, k))
+    B, dB = c64(torch, rng, (batch, n, k))
+    dC = torch.zeros(batch * m * n * 2, dtype=torch.float32, device="cuda")
+    tz.tz_op_cgemm("c64", batch, m, n, k, dA, m * k, dB, n * k, dC, m * n)
+    torch.cuda.synchronize()
+    C = dC.cpu().numpy().view(np.complex64).reshape(batch, m, n)
+    ref = linalg.cgemm(A, B)
+    bound = linalg.cgemm(np.abs(A).astype(np.complex128), np.abs(B).astype(np.complex128)).real
+    # FP32 products summed over k: |err| <= ~ (k + 2) * 2^-24 * sum |a||b| per component
+    assert np.all(np.abs(C - ref) <= 4 * (k + 2) * 2.0 ** -24 * bound + 1e-30)
+
+
+def test_accumulate_fp64(env):
+    tz, torch = env
+    rng = np.random.default_rng(5)
+    part, dpart = c64(torch, rng, 1000)
+    acc0 = (rng.standard_normal(1000) + 1j * rng.standard_normal(1000)) * 1e-12
+    dacc = torch.from_numpy(acc0.view(np.float64).copy()).cuda()
+    s = 0.25 - 0.5j
+    tz.tz_op_accumulate(dpart, dacc, 1000, s)
+    torch.cuda.synchronize()
+    got = dacc.cpu().numpy().view(np.complex128)
+    ref = linalg.accumulate(acc0, part, s)
+    assert np.max(np.abs(got - ref)) <= 1e-15 * np.max(np.abs(ref))

@@ -1,0 +1,145 @@
+"""Host-side checks of the library (no GPU): the C ABI loads and exports
+every declared symbol, the C++ circuit generator matches the seeded input
+generator, and the network/tree/slicing/plan logic keeps its invariants."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import tz_inputs as ti
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def tz():
+    import paper_1907_11217_gb300 as tz
+    tz._lib.lib()
+    return tz
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "tz.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tz_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(tz):
+    import ctypes
+    L = ctypes.CDLL(tz._lib.LIB_PATH)
+    names = declared_symbols()
+    assert len(names) >= 30
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) <= set(tz._lib.SIGNATURES), set(names) - set(tz._lib.SIGNATURES)
+
+
+@pytest.mark.parametrize("lat,kind,args,t,seed", [
+    (ti.grid(4, 4), 0, (4, 4, 0), 10, 1), (ti.grid(7, 7), 0, (7, 7, 0), 32, 2),
+    (ti.bristlecone(70), 1, (0, 0, 70), 32, 3), (ti.bristlecone(72), 1, (0, 0, 72), 20, 9),
+    (ti.grid(3, 5), 0, (3, 5, 0), 17, 12345678901234)])
+def test_cpp_generator_matches_inputs(tz, lat, kind, args, t, seed):
+    c = tz.tz_circuit_generate(kind, args[0], args[1], args[2], t, seed)
+    assert c.to_spec() == ti.circuit_to_spec(lat.n_qubits, ti.generate_circuit(lat, t, seed))
+
+
+def test_spec_roundtrip_and_errors(tz):
+    spec = ti.circuit_to_spec(9, ti.generate_circuit(ti.grid(3, 3), 6, 4))
+    assert tz.tz_circuit_from_spec(spec).to_spec() == spec
+    for bad in ["", "2\n0 h 2\n", "2\n0 cz 0 0\n", "2\n0 foo 1\n", "x\n", "2\n0 h\n", "2\n0 cz 0\n"]:
+        with pytest.raises(tz.TzError) as e:
+            tz.tz_circuit_from_spec(bad)
+        assert e.value.code == -1
+    with pytest.raises(tz.TzError):
+        tz.tz_circuit_generate(1, 0, 0, 71, 10, 1)
+
+
+def test_network_structure(tz):
+    c = tz.tz_circuit_generate_grid(4, 4, 10, 1)
+    for g in (0, 3):
+        net = tz.tz_network_from_circuit(c, g)
+        seen_open = 0
+        for i in range(net.n_indices):
+            q, s = net.index_info(i)
+            if q < 0:
+                seen_open += 1
+                assert 0 <= s < g
+            else:
+                assert 0 <= q < 16 and s >= 1
+        assert seen_open == g
+        # every wire index is held by at least two tensors; batch indices by the 16 outputs
+        holders = {}
+        for t in range(net.n_tensors):
+            for i in net.tensor_indices(t):
+                holders[i] = holders.get(i, 0) + 1
+        for i, h in holders.items():
+            q, _ = net.index_info(i)
+            assert h >= 2 if q >= 0 else h == 16
+    with pytest.raises(tz.TzError):
+        tz.tz_network_from_circuit(c, 9)
+
+
+def test_tree_validation(tz):
+    c = tz.tz_circuit_generate_grid(3, 3, 8, 2)
+    net = tz.tz_network_from_circuit(c, 0)
+    tree = tz.tz_path_greedy(net)
+    pairs = tree.pairs()
+    assert len(pairs) == net.n_tensors - 1
+    tz.tz_tree_from_pairs(net, pairs)
+    with pytest.raises(tz.TzError):
+        tz.tz_tree_from_pairs(net, pairs[:-1])
+    bad = pairs.copy()
+    bad[-1] = bad[0]
+    with pytest.raises(tz.TzError):
+        tz.tz_tree_from_pairs(net, bad)
+
+
+def test_slicing_meets_target_and_equal_cost(tz):
+    """Sec. 2: all subtasks have equal cost -- the same indices are sliced in
+    every subtask, so every group runs the same steps."""
+    c = tz.tz_circuit_generate_grid(5, 5, 16, 4)
+    net = tz.tz_network_from_circuit(c, 0)
+    tree = tz.tz_path_greedy(net, restarts=4, seed=3)
+    full = tz.tz_plan_create(net, tree, []).stats()
+    target = full["max_log2"] - 3
+    sl = tz.tz_slice_select(net, tree, target, 40)
+    assert len(sl) == len(set(sl)) >= 3
+    st = tz.tz_plan_create(net, tree, sl).stats()
+    assert st["max_log2"] <= target < full["max_log2"]
+    assert st["k"] == len(sl)
+    for e in sl:
+        q, s = net.index_info(e)
+        assert q >= 0
+    with pytest.raises(tz.TzError):
+        tz.tz_plan_create(net, tree, [sl[0], sl[0]])
+    with pytest.raises(tz.TzError):
+        tz.tz_plan_create(net, tree, [10 ** 6])
+
+
+def test_plan_stats_and_workspace_sizes(tz):
+    c = tz.tz_circuit_generate_grid(4, 4, 10, 1)
+    net = tz.tz_network_from_circuit(c, 2)
+    tree = tz.tz_path_greedy(net)
+    for prec in ("c64", "tf32x3", "bf16x3"):
+        p = tz.tz_plan_create(net, tree, [], precision=prec, max_bitstrings=64)
+        st = p.stats()
+        assert st["workspace_bytes"] > 0 and st["n_steps"] == net.n_tensors - 1
+        assert st["flops_per_group"] > 0
+        assert '"steps"' in p.describe()
+
+
+def test_bind_rejects_bad_workspace(tz):
+    import ctypes
+    c = tz.tz_circuit_generate_grid(2, 2, 4, 1)
+    net = tz.tz_network_from_circuit(c, 0)
+    p = tz.tz_plan_create(net, tz.tz_path_greedy(net), [])
+    L = tz._lib.lib()
+    assert L.tz_plan_bind_workspace(p.handle, None, 1 << 20) == -1
+    assert L.tz_plan_bind_workspace(p.handle, ctypes.c_void_p(256), 16) == -2
+    assert L.tz_plan_bind_workspace(p.handle, ctypes.c_void_p(257), 1 << 30) == -1
+    out = np.zeros(2)
+    b = np.zeros(4, dtype=np.uint8)
+    assert L.tz_contract_amplitudes(p.handle, b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), 1,
+                                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == -1
+    assert "workspace" in L.tz_last_error().decode()
