@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Seconds per amplitude of random-circuit amplitudes on one GB300 (or N).
+
+Workload (default): Bristlecone-70, depth 1+32+1, seeded circuit by the
+prescription of Sec. 1, one random output bitstring per amplitude batch.
+The planner builds a contraction tree and slices indices so that every
+slice's largest intermediate fits the target; a step contracts a fixed
+range of slices (Sec. 1 subtasks) and the time per amplitude is
+extrapolated to all 2^k slices: s/amplitude = step time * 2^k / (slices per
+step * ranks) / bitstrings. Preprocessing (tree, slicing, plan, bind) is
+excluded, as in Sec. 1.
+
+Under torchrun each rank contracts its own slice ranges (no data exchange in
+the path) and the per-rank FP64 partial sums are reduced once per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (lattice kind, rows, cols, n_qubits, depth t, circuit seed, log2 target, bitstring seed)
+    "bristlecone70_d32": ("bristlecone", 0, 0, 70, 32, 3, 30, 103),
+    "grid7x7_d32": ("grid", 7, 7, 49, 32, 2, 24, 102),
+    "grid4x4_d10": ("grid", 4, 4, 16, 10, 1, 0, 101),
+}
+PAPER_S_PER_AMP = {"bristlecone70_d32": 0.43}  # Table 2 (1449 x 88 vCPU), context only
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="bristlecone70_d32", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="auto", choices=["auto", "c64", "tf32x3", "bf16x3"])
+    ap.add_argument("--batch-log2", type=int, default=0)
+    ap.add_argument("--slices", type=int, default=0, help="slices per step (0: auto)")
+    ap.add_argument("--log2-max", type=int, default=0, help="slicing target (0: workload default)")
+    ap.add_argument("--restarts", type=int, default=256)
+    ap.add_argument("--algorithm", default="elimination", choices=["auto", "greedy", "elimination"])
+    ap.add_argument("--tree-seed", type=int, default=7)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    return ap.parse_args()
+
+
+def make_circuit_spec(w):
+    import tz_inputs as ti
+    kind, rows, cols, nq, t, seed, _, _ = WORKLOADS[w]
+    lat = ti.grid(rows, cols) if kind == "grid" else ti.bristlecone(nq)
+    return ti.circuit_to_spec(lat.n_qubits, ti.generate_circuit(lat, t, seed)), lat.n_qubits
+
+
+def build_plan(tz, spec, args, precision, stream, device, log2_max):
+    circ = tz.tz_circuit_from_spec(spec)
+    net = tz.tz_network_from_circuit(circ, args.batch_log2)
+    t0 = time.perf_counter()
+    tree = tz.tz_path_greedy(net, restarts=args.restarts, seed=args.tree_seed, log2_max_intermediate=log2_max,
+                             precision=precision, algorithm=args.algorithm)
+    sliced = tz.tz_slice_select(net, tree, log2_max, 40) if log2_max > 0 else []
+    plan = tz.tz_plan_create(net, tree, sliced, precision=precision, device=device, stream=stream, use_graph=True,
+                             max_bitstrings=1 << max(args.batch_log2, 0))
+    prep_s = time.perf_counter() - t0
+    return plan, sliced, prep_s
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), \
+            d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 1900.0, 1700.0, 2070.0, "fallback"
+
+
+def roofline(prof, precision):
+    """Dominant kernel kind of the profiled pass and its roofline position."""
+    hbm, bf16, bf16_s, sm_mhz, src = measured_peaks()
+    kinds = {k: v for k, v in prof.items() if v["launches"] > 0}
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    d = kinds[dom]
+    total_ms = sum(v["ms"] for v in kinds.values())
+    sec = d["ms"] / 1e3
+    fp32_alu_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12   # FFMA lanes x 2 flops x max clock
+    out = {"kernel": dom, "launches": d["launches"], "share_of_step": d["ms"] / total_ms if total_ms else None,
+           "traffic": None}
+    if dom == "gemm_tc":
+        ratio = {"tf32x3": 1.1 / 2.25, "bf16x3": 1.0}[precision]   # nominal dense TF32 : BF16
+        peak = bf16 * ratio
+        out.update(bound="tensor", unit="TFLOP/s", achieved=d["flops"] / sec / 1e12, peak=peak,
+                   peak_source=f"{src} bf16 x nominal {precision[:4]}/bf16 ratio",
+                   issued_tflops=3 * d["flops"] / sec / 1e12)
+    elif dom in ("gemm_simt", "direct"):
+        out.update(bound="alu", unit="TFLOP/s", achieved=d["flops"] / sec / 1e12, peak=fp32_alu_tflops,
+                   peak_source="152 SMs x 128 FP32 lanes x 2 flops x max SM clock")
+    else:
+        out.update(bound="hbm", unit="GB/s", achieved=d["bytes"] / sec / 1e9, peak=hbm, peak_source=f"{src} copy")
+    out["frac"] = out["achieved"] / out["peak"]
+    out["achieved_bytes_gbs"] = d["bytes"] / sec / 1e9
+    out["per_kind_ms"] = {k: round(v["ms"], 3) for k, v in kinds.items()}
+    return out
+
+
+def cpu_oracle_sample(spec, segs, bits, budget_s, k):
+    """Time the FP64 oracle contractor on a bounded sample of the workload:
+    sub-slices of slice 0 until the budget is spent; extrapolate to all
+    2^k slices of one amplitude."""
+    from oracle import tn
+    import itertools
+    t0 = time.perf_counter()
+    c = tn.Contractor(spec, sliced=segs, max_log2=22)
+    setup = time.perf_counter() - t0
+    n_sub = 1 << len(c.extra)
+    done = 0
+    t1 = time.perf_counter()
+    base = [0] * len(segs)
+    for extra in itertools.product((0, 1), repeat=len(c.extra)):
+        leaves = c.net.leaf_values(bits, c._fixed_map(base + list(extra)))
+        tn.contract_path(leaves, c.pairs)
+        done += 1
+        if time.perf_counter() - t1 > budget_s:
+            break
+    el = time.perf_counter() - t1
+    per_sub = el / done
+    s_per_amp = per_sub * n_sub * (1 << k)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": s_per_amp, "unit": "s/amplitude", "cores": cores, "kind": "oracle",
+            "sample": f"{done} of {n_sub} oracle sub-slices of slice 0 (oracle largest intermediate 2^{c.max_log2}), "
+                      f"{el:.1f} s, extrapolated x{n_sub}/{done} sub-slices x 2^{k} slices; oracle setup {setup:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, same metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import tz_inputs as ti
+    import paper_1907_11217_gb300 as tz
+    spec, nq = make_circuit_spec(args.workload)
+    log2_max = args.log2_max or WORKLOADS[args.workload][6]
+    circ = tz.tz_circuit_from_spec(spec)
+    net = tz.tz_network_from_circuit(circ, 0)
+    tree = tz.tz_path_greedy(net, restarts=args.restarts, seed=args.tree_seed, log2_max_intermediate=log2_max,
+                             algorithm=args.algorithm)
+    sliced = tz.tz_slice_select(net, tree, log2_max, 40) if log2_max > 0 else []
+    segs = [net.index_info(e) for e in sliced]
+    bits = ti.random_bitstrings(nq, 1, WORKLOADS[args.workload][7])[0]
+    per = max(2.0, args.cpu_seconds / max(1, args.steps + args.warmup))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(spec, segs, bits, per, len(sliced))
+        if i >= args.warmup:
+            vals.append(r)
+    v = statistics.median(x["value"] for x in vals)
+    line = {"impl": "reference", "metric": f"sec/amplitude ({args.workload})", "value": v, "unit": "s/amplitude",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "k": len(sliced)},
+            "cpu_baseline": {"kind": "oracle", "cores": vals[-1]["cores"], "sample": vals[-1]["sample"], "value": v,
+                             "unit": "s/amplitude"},
+            "e2e": {"value": v, "unit": "s/amplitude", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import paper_1907_11217_gb300 as tz
+    import tz_inputs as ti
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = local
+
+    precision = args.precision
+    if precision == "auto":
+        precision = "tf32x3" if tz._lib.lib() and _tc_available(tz) else "c64"
+    spec, nq = make_circuit_spec(args.workload)
+    log2_max = args.log2_max or WORKLOADS[args.workload][6]
+    stream = torch.cuda.Stream(device=device)
+    plan, sliced, prep_s = build_plan(tz, spec, args, precision, stream, device, log2_max)
+    st = plan.stats()
+    plan.bind()
+    k = len(sliced)
+    n_slices = 1 << k
+    B = 1 << args.batch_log2
+    bits = ti.random_bitstrings(nq, B, WORKLOADS[args.workload][7] + rank)
+    d_bits = torch.from_numpy(bits).to(f"cuda:{device}")
+    d_out = torch.zeros(2 * B, dtype=torch.float64, device=f"cuda:{device}")
+
+    # slices per step: ~3 s of estimated work (a fixed 2^12 when that is smaller), at least 1
+    S = args.slices
+    if S <= 0:
+        plan.set_slice_range(0, 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tz.tz_contract_amplitudes_device(plan, d_bits, d_out)
+        stream.synchronize()
+        one = time.perf_counter() - t0
+        S = int(max(1, min(4096, n_slices // world, 3.0 / max(one, 1e-6))))
+    S = min(S, max(1, n_slices // world))
+
+    def slice_range(step):
+        lo = ((step * world + rank) * S) % n_slices
+        return lo, min(n_slices, lo + S)
+
+    def one_step(step, reduce=True):
+        lo, hi = slice_range(step)
+        plan.set_slice_range(lo, hi)
+        tz.tz_contract_amplitudes_device(plan, d_bits, d_out)
+        if dist and reduce:
+            with torch.cuda.stream(stream):
+                td.all_reduce(d_out)
+
+    for w in range(args.warmup):
+        one_step(w)
+    torch.cuda.synchronize()
+    if dist:
+        td.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(device) as clk:
+        ev0.record(stream)
+        for i in range(args.steps):
+            one_step(args.warmup + i)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        td.barrier()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=f"cuda:{device}")
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        ms = float(t.item())
+    slices_per_step = S * world
+    s_per_amp = ms / 1e3 * n_slices / slices_per_step / B
+    flops_step = st["flops_per_group"] * slices_per_step
+    tflops = flops_step / (ms / 1e3) / 1e12
+
+    # end to end through the host API: bitstrings in from host memory, FP64
+    # amplitudes back to host memory, every step
+    plan_e2e = plan
+    e2e_times = []
+    for i in range(max(1, args.steps)):
+        lo, hi = slice_range(args.warmup + i)
+        plan_e2e.set_slice_range(lo, hi)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tz.tz_contract_amplitudes(plan_e2e, bits)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(e2e_times) * n_slices / slices_per_step / B
+
+    # per-kernel profile of one more step (events around every launch)
+    plan.profile_enable(True)
+    one_step(args.warmup + args.steps, reduce=False)
+    prof = plan.profile()
+    plan.profile_enable(False)
+    rl = roofline(prof, precision)
+    per_launch = {k: v["launches"] for k, v in prof.items()}
+    launches_per_call = 1 + S * st["n_launches_per_group"]
+
+    if rank != 0:
+        if dist:
+            td.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        segs = plan.sliced_segments()
+        cpu = cpu_oracle_sample(spec, segs, bits[0], args.cpu_seconds, k)
+    paper = PAPER_S_PER_AMP.get(args.workload)
+    line = {
+        "metric": f"sec/amplitude ({args.workload}, extrapolated from timed slices)",
+        "value": s_per_amp, "unit": "s/amplitude", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": (s_per_amp / paper) if paper else None,
+        "dtype": precision, "data": "synthetic (seeded circuit by the Sec. 1 prescription, uniform random bitstrings)",
+        "config": {"workload": args.workload, "n_qubits": nq, "depth": f"1+{WORKLOADS[args.workload][4]}+1",
+                   "batch_bitstrings": B, "k_sliced": k, "slices_total": n_slices,
+                   "slices_per_step": slices_per_step, "log2_max_intermediate": st["max_log2"],
+                   "tree_restarts": args.restarts, "preprocessing_s": prep_s,
+                   "l2": "intermediates larger than L2" if st["max_log2"] >= 25 else "working set may fit L2",
+                   "parallelism": f"slices x{world}"},
+        "contraction_tflops": tflops,
+        "plan": {"flops_per_slice": st["flops_per_group"], "bytes_per_slice": st["bytes_per_group"],
+                 "permute_bytes_per_slice": st["permute_bytes_per_group"], "steps": st["n_steps"],
+                 "gemm_steps": st["n_gemm_steps"], "launches_per_slice": st["n_launches_per_group"],
+                 "workspace_gb": st["workspace_bytes"] / 1e9},
+        "e2e": {"value": e2e_s, "unit": "s/amplitude", "h2d_bytes_per_step": int(bits.nbytes),
+                "d2h_bytes_per_step": 16 * B},
+        "roofline": rl,
+        "cpu_baseline": cpu,
+        "gpu_launches": args.steps * launches_per_call,
+        "profiled_launches_per_kind": per_launch,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    if dist:
+        td.destroy_process_group()
+
+
+def _tc_available(tz):
+    try:
+        return tz.tz_op_cgemm_scratch_bytes("tf32x3", 1, 1024, 64, 64) >= 0
+    except tz.TzError:
+        return False
+
+
+if __name__ == "__main__":
+    main()

@@ -123,17 +123,27 @@ void tz_network_destroy(tz_network *net);
 
 /* ------------------------------------------------------ contraction trees
  * The contraction algorithm of the paper is deferred to its earlier work;
- * the library builds its own trees: a greedy over pairs that share an index
- * (cost size(out) - alpha (size(a) + size(b))), with randomised restarts
- * scored by the estimated GB300 time of the sliced plan.
+ * the library builds its own trees, by two randomised heuristics:
+ *   TZ_PATH_GREEDY      pairwise greedy over tensors that share an index,
+ *                       cost size(out) - alpha (size(a) + size(b));
+ *   TZ_PATH_ELIMINATION bucket elimination of indices in min-degree order
+ *                       (merge every holder of the index, then sum it out);
+ * TZ_PATH_AUTO alternates them. Each restart is scored by the estimated
+ * GB300 time of the plan after slicing to log2_max_intermediate, and the
+ * best tree is kept.
  * Trees are lists of SSA pairs: leaves are ids 0..T-1, the i-th pair
  * creates id T+i. A complete tree has T-1 pairs.
  */
+#define TZ_PATH_AUTO        0
+#define TZ_PATH_GREEDY      1
+#define TZ_PATH_ELIMINATION 2
 typedef struct {
-  int restarts;                 /* randomised greedy trials (>= 1); 1 = plain greedy */
+  int restarts;                 /* randomised trials (>= 1); the first trial of
+                                   each algorithm is deterministic              */
   uint64_t seed;                /* seed of the randomisation                   */
   int log2_max_intermediate;    /* slicing target used to score trials (bits)  */
   int precision;                /* tz_precision used by the time model         */
+  int algorithm;                /* TZ_PATH_*                                   */
 } tz_path_opts;
 
 int tz_path_greedy(const tz_network *net, const tz_path_opts *opts, tz_tree **out);
@@ -216,6 +226,24 @@ int tz_contract_amplitudes(tz_plan *plan, const uint8_t *bitstrings, int64_t n, 
  * synchronisation). d_bitstrings: n x n_qubits uint8; d_out: 2n doubles. */
 int tz_contract_amplitudes_device(tz_plan *plan, const uint8_t *d_bitstrings, int64_t n, double *d_out);
 void tz_plan_destroy(tz_plan *plan);
+
+/* Per-kernel timing of a plan's launches (CUDA events around every launch on
+ * the plan's stream; the captured-graph path is not used while enabled).
+ * Kinds: 0 leaf builder, 1 direct small steps, 2 permute, 3 SIMT complex
+ * GEMM, 4 tensor-core complex GEMM, 5 FP64 accumulation. flops are useful
+ * flops (8 per complex multiply-add); bytes are algorithmic bytes (each
+ * operand read once, the result written once, complex64). */
+#define TZ_PROFILE_KINDS 6
+typedef struct {
+  int64_t launches[TZ_PROFILE_KINDS];
+  double ms[TZ_PROFILE_KINDS];
+  double flops[TZ_PROFILE_KINDS];
+  double bytes[TZ_PROFILE_KINDS];
+} tz_plan_profile;
+/* Turn profiling on (1) or off (0); either resets the counters. */
+int tz_plan_profile_enable(tz_plan *plan, int on);
+/* Synchronise the plan's stream and read the counters. */
+int tz_plan_profile_get(tz_plan *plan, tz_plan_profile *out);
 
 /* --------------------------------------------------------------- serving
  * A request loop for amplitude-batch queries over resident plans: plans

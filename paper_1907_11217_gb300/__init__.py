@@ -18,7 +18,7 @@ import ctypes
 
 import numpy as np
 
-from ._lib import (PRECISIONS, TZ_BF16X3, TZ_C64_SIMT, TZ_LATTICE_BRISTLECONE, TZ_LATTICE_GRID, TZ_TF32X3, TzError,
+from ._lib import (PROFILE_KINDS, tz_plan_profile, PRECISIONS, TZ_BF16X3, TZ_C64_SIMT, TZ_LATTICE_BRISTLECONE, TZ_LATTICE_GRID, TZ_TF32X3, TzError,
                    check, lib, tz_lattice, tz_network_opts, tz_path_opts, tz_plan_opts, tz_plan_stats)
 
 __all__ = [
@@ -152,8 +152,13 @@ class Tree(_Handle):
         return buf[: 2 * n.value].reshape(-1, 2)
 
 
-def tz_path_greedy(net: Network, restarts=1, seed=0, log2_max_intermediate=0, precision="c64") -> Tree:
-    o = tz_path_opts(restarts, seed, log2_max_intermediate, PRECISIONS.get(precision, precision))
+PATH_ALGORITHMS = {"auto": 0, "greedy": 1, "elimination": 2}
+
+
+def tz_path_greedy(net: Network, restarts=1, seed=0, log2_max_intermediate=0, precision="c64",
+                   algorithm="auto") -> Tree:
+    o = tz_path_opts(restarts, seed, log2_max_intermediate, PRECISIONS.get(precision, precision),
+                     PATH_ALGORITHMS.get(algorithm, algorithm))
     h = ctypes.c_void_p()
     check(lib().tz_path_greedy(net.handle, ctypes.byref(o), ctypes.byref(h)))
     return Tree(h)
@@ -210,6 +215,16 @@ class Plan(_Handle):
         buf = (ctypes.c_int32 * max(2 * k.value, 2))()
         check(lib().tz_plan_sliced_segments(self._h, buf, k.value, ctypes.byref(k)))
         return [(buf[2 * j], buf[2 * j + 1]) for j in range(k.value)]
+
+    def profile_enable(self, on=True):
+        check(lib().tz_plan_profile_enable(self._h, int(on)))
+
+    def profile(self) -> dict:
+        """Per kernel kind: launches, ms, flops, bytes (synchronises)."""
+        pr = tz_plan_profile()
+        check(lib().tz_plan_profile_get(self._h, ctypes.byref(pr)))
+        return {k: {"launches": pr.launches[i], "ms": pr.ms[i], "flops": pr.flops[i], "bytes": pr.bytes[i]}
+                for i, k in enumerate(PROFILE_KINDS)}
 
     def describe(self) -> str:
         n = ctypes.c_size_t()

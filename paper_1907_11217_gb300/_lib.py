@@ -34,7 +34,7 @@ class tz_network_opts(ctypes.Structure):
 
 class tz_path_opts(ctypes.Structure):
     _fields_ = [("restarts", ctypes.c_int), ("seed", ctypes.c_uint64), ("log2_max_intermediate", ctypes.c_int),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("algorithm", ctypes.c_int)]
 
 
 class tz_plan_opts(ctypes.Structure):
@@ -49,6 +49,14 @@ class tz_plan_stats(ctypes.Structure):
                 ("gemm_flops_per_group", ctypes.c_double), ("bytes_per_group", ctypes.c_double),
                 ("permute_bytes_per_group", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t),
                 ("const_bytes", ctypes.c_size_t)]
+
+
+PROFILE_KINDS = ("leaves", "direct", "permute", "gemm_simt", "gemm_tc", "accumulate")
+
+
+class tz_plan_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 6), ("ms", ctypes.c_double * 6), ("flops", ctypes.c_double * 6),
+                ("bytes", ctypes.c_double * 6)]
 
 
 class tz_server_opts(ctypes.Structure):
@@ -92,6 +100,8 @@ SIGNATURES = {
     "tz_contract_amplitudes": (c_int, [P, U8P, c_int64, F64P]),
     "tz_contract_amplitudes_device": (c_int, [P, P, c_int64, P]),
     "tz_plan_destroy": (None, [P]),
+    "tz_plan_profile_enable": (c_int, [P, c_int]),
+    "tz_plan_profile_get": (c_int, [P, ctypes.POINTER(tz_plan_profile)]),
     "tz_server_create": (c_int, [ctypes.POINTER(tz_server_opts), PP]),
     "tz_server_submit": (c_int, [P, P, U8P, c_int64, ctypes.POINTER(c_uint64)]),
     "tz_server_poll": (c_int, [P, c_uint64, F64P, ctypes.POINTER(c_int)]),

@@ -153,13 +153,23 @@ int tz_path_greedy(const tz_network *net, const tz_path_opts *opts, tz_tree **ou
   tz::Pairs best;
   double best_score = 0;
   int best_bits = 0;
+  REQUIRE(o.algorithm >= TZ_PATH_AUTO && o.algorithm <= TZ_PATH_ELIMINATION, "unknown path algorithm");
   for (int trial = 0; trial < o.restarts; trial++) {
-    double alpha = 1.0, temp = 0.0;
-    if (trial > 0) {
-      alpha = 0.5 + 1.0 * ((tz::splitmix64_next(rng) >> 11) * (1.0 / 9007199254740992.0));
-      temp = 0.05 + 1.0 * ((tz::splitmix64_next(rng) >> 11) * (1.0 / 9007199254740992.0));
+    int algo = o.algorithm;
+    int nth = trial;  // trial number within its algorithm
+    if (algo == TZ_PATH_AUTO) {
+      algo = (trial % 2 == 0) ? TZ_PATH_ELIMINATION : TZ_PATH_GREEDY;
+      nth = trial / 2;
     }
-    tz::Pairs pr = tz::greedy_tree(net->n, alpha, temp, tz::splitmix64_next(rng));
+    double alpha = 1.0, temp = 0.0;
+    const double u1 = (tz::splitmix64_next(rng) >> 11) * (1.0 / 9007199254740992.0);
+    const double u2 = (tz::splitmix64_next(rng) >> 11) * (1.0 / 9007199254740992.0);
+    if (nth > 0) {
+      alpha = 0.5 + 1.0 * u1;
+      temp = 0.05 + 1.0 * u2;
+    }
+    tz::Pairs pr = algo == TZ_PATH_GREEDY ? tz::greedy_tree(net->n, alpha, temp, tz::splitmix64_next(rng))
+                                          : tz::elimination_tree(net->n, temp, tz::splitmix64_next(rng));
     int mb = 0;
     double sc = tree_score(net->n, pr, o.log2_max_intermediate, cm, &mb);
     if (trial == 0 || sc < best_score) {
@@ -289,6 +299,8 @@ int tz_contract_amplitudes(tz_plan *plan, const uint8_t *bitstrings, int64_t n, 
   tz::cuda_check(cudaMemcpyAsync(out, plan->ws + plan->off_acc, (size_t)n * 16, cudaMemcpyDeviceToHost, s),
                  "copy amplitudes out");
   tz::cuda_check(cudaStreamSynchronize(s), "contract");
+  if (plan->opts.precision != TZ_C64_SIMT && tz::dev::tc_take_error() == 1)
+    tz::fail(TZ_ETIMEOUT, "a tensor-core kernel wait timed out; results are invalid");
   TZ_CATCH
 }
 
@@ -319,6 +331,23 @@ int tz_plan_describe(const tz_plan *plan, char *buf, size_t cap, size_t *len) {
 }
 
 void tz_plan_destroy(tz_plan *plan) { tz::plan_destroy(plan); }
+
+int tz_plan_profile_enable(tz_plan *plan, int on) {
+  TZ_TRY
+  REQUIRE(plan, "NULL plan");
+  if (plan->bound) tz::plan_profile_collect(plan);
+  plan->prof = tz_plan_profile{};
+  plan->profiling = on != 0;
+  TZ_CATCH
+}
+
+int tz_plan_profile_get(tz_plan *plan, tz_plan_profile *out) {
+  TZ_TRY
+  REQUIRE(plan && out, "NULL argument");
+  if (plan->bound) tz::plan_profile_collect(plan);
+  *out = plan->prof;
+  TZ_CATCH
+}
 
 // ------------------------------------------------------------------ ops
 int tz_op_permute(const void *in, void *out, int rank, const int32_t *perm, void *stream) {
@@ -360,7 +389,7 @@ int tz_op_cgemm(int precision, int64_t batch, int64_t m, int64_t n, int64_t k, c
   cudaStream_t s = (cudaStream_t)stream;
   if (precision == TZ_C64_SIMT) {
     tz::cuda_check(tz::dev::launch_cgemm_simt((const float2 *)A, (const float2 *)B, (float2 *)C, batch, m, n, k, sa,
-                                              sb, sc, s),
+                                              sb, sc, nullptr, s),
                    "simt gemm");
   } else if (precision == TZ_TF32X3 || precision == TZ_BF16X3) {
     if (!tz::dev::cgemm_tc_supported(precision, m, n, k))
@@ -368,7 +397,7 @@ int tz_op_cgemm(int precision, int64_t batch, int64_t m, int64_t n, int64_t k, c
     size_t need = tz::dev::cgemm_tc_scratch_bytes(precision, batch, n, k);
     REQUIRE(scratch_bytes >= need && (need == 0 || scratch), "scratch too small");
     tz::cuda_check(tz::dev::launch_cgemm_tc(precision, (const float2 *)A, (const float2 *)B, (float2 *)C, batch, m, n,
-                                            k, sa, sb, sc, scratch, scratch_bytes, s),
+                                            k, sa, sb, sc, nullptr, scratch, scratch_bytes, s),
                    "tensor-core gemm");
   } else {
     tz::fail(TZ_EINVAL, "unknown precision");

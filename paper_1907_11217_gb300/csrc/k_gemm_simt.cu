@@ -11,10 +11,17 @@ namespace dev {
 
 namespace {
 
+__device__ __forceinline__ int64_t scatter_bits(int64_t v, int n, const int8_t *pos) {
+  int64_t o = 0;
+  for (int j = 0; j < n; j++) o |= ((v >> j) & 1) << pos[j];
+  return o;
+}
+
 template <int BM, int BN, int TM, int TN, int BK>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     cgemm_simt_kernel(const float2 *__restrict__ A, const float2 *__restrict__ B, float2 *__restrict__ C,
-                      int64_t batch, int64_t M, int64_t N, int64_t K, int64_t sA, int64_t sB, int64_t sC) {
+                      int64_t batch, int64_t M, int64_t N, int64_t K, int64_t sA, int64_t sB, int64_t sC,
+                      const __grid_constant__ CScatter sc, int scatter) {
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int TX = BN / TN;
   __shared__ float2 As[BK][BM + 1];
@@ -64,15 +71,33 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
       }
       __syncthreads();
     }
-    float2 *Cz = C + z * sC;
+    if (!scatter) {
+      float2 *Cz = C + z * sC;
 #pragma unroll
-    for (int i = 0; i < TM; i++) {
-      const int64_t m = m0 + ty + i * (BM / TM);
-      if (m >= M) continue;
+      for (int i = 0; i < TM; i++) {
+        const int64_t m = m0 + ty + i * (BM / TM);
+        if (m >= M) continue;
 #pragma unroll
-      for (int j = 0; j < TN; j++) {
-        const int64_t n = n0 + tx + j * TX;
-        if (n < N) Cz[m * N + n] = acc[i][j];
+        for (int j = 0; j < TN; j++) {
+          const int64_t n = n0 + tx + j * TX;
+          if (n < N) Cz[m * N + n] = acc[i][j];
+        }
+      }
+    } else {
+      const int64_t ob = scatter_bits(z, sc.nb, sc.pb);
+      int64_t on[TN];
+#pragma unroll
+      for (int j = 0; j < TN; j++) on[j] = scatter_bits(n0 + tx + j * TX, sc.nn, sc.pn);
+#pragma unroll
+      for (int i = 0; i < TM; i++) {
+        const int64_t m = m0 + ty + i * (BM / TM);
+        if (m >= M) continue;
+        const int64_t om = ob + scatter_bits(m, sc.nm, sc.pm);
+#pragma unroll
+        for (int j = 0; j < TN; j++) {
+          const int64_t n = n0 + tx + j * TX;
+          if (n < N) C[om + on[j]] = acc[i][j];
+        }
       }
     }
   }
@@ -80,23 +105,24 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 
 template <int BM, int BN, int TM, int TN, int BK>
 cudaError_t run(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N, int64_t K,
-                int64_t sA, int64_t sB, int64_t sC, cudaStream_t s) {
+                int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s) {
   const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN) * batch;
   const int blocks = (int)std::min<int64_t>(tiles, 152 * 64);
+  CScatter none{};
   cgemm_simt_kernel<BM, BN, TM, TN, BK><<<blocks, (BM / TM) * (BN / TN), 0, s>>>(A, B, C, batch, M, N, K, sA, sB,
-                                                                               sC);
+                                                                               sC, sc ? *sc : none, sc ? 1 : 0);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_cgemm_simt(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N,
-                              int64_t K, int64_t sA, int64_t sB, int64_t sC, cudaStream_t s) {
+                              int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s) {
   if (batch <= 0 || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
-  if (N >= 48) return run<64, 64, 4, 4, 8>(A, B, C, batch, M, N, K, sA, sB, sC, s);
-  if (N >= 12) return run<128, 16, 4, 2, 8>(A, B, C, batch, M, N, K, sA, sB, sC, s);
-  if (N >= 3) return run<256, 4, 4, 1, 8>(A, B, C, batch, M, N, K, sA, sB, sC, s);
-  return run<256, 2, 2, 1, 8>(A, B, C, batch, M, N, K, sA, sB, sC, s);
+  if (N >= 48) return run<64, 64, 4, 4, 8>(A, B, C, batch, M, N, K, sA, sB, sC, sc, s);
+  if (N >= 12) return run<128, 16, 4, 2, 8>(A, B, C, batch, M, N, K, sA, sB, sC, sc, s);
+  if (N >= 3) return run<256, 4, 4, 1, 8>(A, B, C, batch, M, N, K, sA, sB, sC, sc, s);
+  return run<256, 2, 2, 1, 8>(A, B, C, batch, M, N, K, sA, sB, sC, sc, s);
 }
 
 }  // namespace dev

@@ -1,14 +1,467 @@
-// Split-precision complex products on the tcgen05 tensor cores.
+// Split-precision complex products on the tcgen05 tensor cores (sm_103a).
+//
+// C[z] = A[z] B[z]^T in complex64, computed as one real product on the
+// interleaved (re, im) view: A is read as an m x 2k FP32 matrix and C is
+// written as an m x 2n FP32 matrix, with the 2n x 2k real matrix
+//     row 2j   = ( Re b_jl, -Im b_jl )_l      (real part of column j)
+//     row 2j+1 = ( Im b_jl,  Re b_jl )_l      (imaginary part)
+// built from B by a small prep kernel. Each FP32 operand x is split exactly
+// into hi = x rounded to the nearest TF32 value (10 explicit mantissa bits)
+// and lo = x - hi (exact, |lo| <= 2^-11 |x|); three tensor-core products
+// hi*hi + hi*lo + lo*hi accumulate in FP32 in tensor memory (TMEM); the
+// dropped lo*lo term is below 2^-22 |a||b|.
+//
+// Pipeline per CTA (one 128-row tile of C, up to 128 complex columns):
+//   warp 0     : TMA loads of the A tile (128 rows x 32 floats, 128B swizzle)
+//                and of the prepared hi/lo B tiles, into a ring of stages;
+//   warps 2..5 : split each A tile in shared memory (hi in place, lo beside
+//                it), then, after the last product, the epilogue
+//                (tcgen05.ld TMEM -> registers -> global);
+//   warp 1     : TMEM allocation; one thread issues tcgen05.mma and commits
+//                stage releases to mbarriers.
+// Every wait is bounded in time; on timeout the kernel raises an error flag,
+// drains its copies in flight, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
 #include "kernels.h"
 
 namespace tz {
 namespace dev {
 
-bool cgemm_tc_supported(int, int64_t, int64_t, int64_t) { return false; }
-size_t cgemm_tc_scratch_bytes(int, int64_t, int64_t, int64_t) { return 0; }
-cudaError_t launch_cgemm_tc(int, const float2 *, const float2 *, float2 *, int64_t, int64_t, int64_t, int64_t,
-                            int64_t, int64_t, int64_t, void *, size_t, cudaStream_t) {
-  return cudaErrorNotSupported;
+namespace {
+
+constexpr int BM = 128;           // C rows per tile = TMEM lanes
+constexpr int kStageFloats = 32;  // K (real) per stage: one 128-byte swizzle row
+constexpr int kThreads = 192;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
+
+__device__ int g_tc_error;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase with the given parity; false on timeout or when another
+// role has aborted (then the caller stops its work).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          bool honour_abort = true) {
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t i = 0;; i++) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (honour_abort && *abort_flag) return false;
+    if ((i & 255) == 255 && globaltimer() - t0 > kWaitNs) {
+      atomicExch(&g_tc_error, 1);
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)tm), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// K-major operand in the 128-byte swizzled layout written by TMA: rows of
+// 128 bytes, 8-row atoms of 1024 bytes (stride-dimension offset 1024).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor: FP32 accumulator, TF32 A and B, both K-major,
+// N = n_cols, M = 128.
+__host__ __device__ constexpr uint32_t idesc_tf32(int n_cols) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n_cols >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Round to nearest TF32 on the bit pattern (a carry into the exponent is the
+// correct rounding up); hi and x are within a factor of two, so x - hi is
+// exact (Sterbenz).
+__device__ __forceinline__ uint32_t split_hi(uint32_t x) { return (x + 0x1000u) & 0xFFFFE000u; }
+__device__ __forceinline__ uint32_t split_lo(uint32_t x) {
+  return __float_as_uint(__uint_as_float(x) - __uint_as_float(split_hi(x)));
+}
+
+struct TcArgs {
+  float2 *C;
+  int64_t M, N, K;     // complex sizes of one product
+  int64_t sC;          // complex elements between batches of C
+  int n_tiles_m, n_tiles_n, kblocks;
+  int NT;              // rows of the prepared B per batch
+  int scatter;         // 1: write C through sc
+  CScatter sc;
+};
+
+__device__ __forceinline__ int64_t scatter_bits(int64_t v, int n, const int8_t *pos) {
+  int64_t o = 0;
+  for (int j = 0; j < n; j++) o |= ((v >> j) & 1) << pos[j];
+  return o;
+}
+
+template <int BNP, int STAGES>
+struct TcSmem {
+  static constexpr uint32_t A_BYTES = BM * 128;
+  static constexpr uint32_t B_BYTES = BNP * 128;
+  static constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr uint32_t TOTAL = STAGES * STAGE + 256 + 1024 + 1024;  // + barriers, column offsets, alignment
+  static constexpr uint32_t TMEM_COLS = BNP < 32 ? 32 : BNP;
+};
+
+template <int BNP, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_tf32x3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
+                     const __grid_constant__ CUtensorMap tmBl, TcArgs a) {
+  using L = TcSmem<BNP, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * L::STAGE);
+  uint64_t *conv = full + STAGES;
+  uint64_t *empty = conv + STAGES;
+  uint64_t *accf = empty + STAGES;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accf + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  auto A_hi = [&](int s) { return smem + s * L::STAGE; };
+  auto A_lo = [&](int s) { return smem + s * L::STAGE + L::A_BYTES; };
+  auto B_hi = [&](int s) { return smem + s * L::STAGE + 2 * L::A_BYTES; };
+  auto B_lo = [&](int s) { return smem + s * L::STAGE + 2 * L::A_BYTES + L::B_BYTES; };
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int64_t per_batch = (int64_t)a.n_tiles_m * a.n_tiles_n;
+  const int64_t z = blockIdx.x / per_batch;
+  const int64_t rem = blockIdx.x - z * per_batch;
+  const int mt = (int)(rem / a.n_tiles_n), nt = (int)(rem % a.n_tiles_n);
+  const int rowA = (int)(z * a.M + (int64_t)mt * BM);
+  const int rowB = (int)(z * a.NT + (int64_t)nt * BNP);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; s++) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 128);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"((uint32_t)L::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int kb = 0; kb < a.kblocks; kb++) {
+        const int s = kb % STAGES, round = kb / STAGES;
+        if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1, abort_flag)) break;
+        mbar_expect_tx(&full[s], L::A_BYTES + 2 * L::B_BYTES);
+        tma_load_2d(A_hi(s), &tmA, kb * kStageFloats, rowA, &full[s]);
+        tma_load_2d(B_hi(s), &tmBh, kb * kStageFloats, rowB, &full[s]);
+        tma_load_2d(B_lo(s), &tmBl, kb * kStageFloats, rowB, &full[s]);
+        issued++;
+      }
+      if (*abort_flag) {
+        // drain: let the copies already issued land before the CTA exits
+        for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; kb++)
+          mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, abort_flag, false);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_tf32(BNP);
+      for (int kb = 0; kb < a.kblocks; kb++) {
+        const int s = kb % STAGES, round = kb / STAGES;
+        if (!mbar_wait(&conv[s], round & 1, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t ah = smem_u32(A_hi(s)), al = smem_u32(A_lo(s));
+        const uint32_t bh = smem_u32(B_hi(s)), bl = smem_u32(B_lo(s));
+#pragma unroll
+        for (int kk = 0; kk < kStageFloats / 8; kk++) {
+          const uint32_t off = kk * 32;  // 8 TF32 values = 32 bytes along K
+          const uint64_t dah = sw128_desc(ah + off), dal = sw128_desc(al + off);
+          const uint64_t dbh = sw128_desc(bh + off), dbl = sw128_desc(bl + off);
+          umma_tf32(tmem, dah, dbh, idesc, (kb | kk) != 0);
+          umma_tf32(tmem, dah, dbl, idesc, 1);
+          umma_tf32(tmem, dal, dbh, idesc, 1);
+        }
+        umma_commit(&empty[s]);
+      }
+      umma_commit(accf);
+    }
+  } else {
+    const int t = threadIdx.x - 64;  // 0..127
+    for (int kb = 0; kb < a.kblocks; kb++) {
+      const int s = kb % STAGES, round = kb / STAGES;
+      if (!mbar_wait(&full[s], round & 1, abort_flag)) break;
+      uint4 *hi = reinterpret_cast<uint4 *>(A_hi(s));
+      uint4 *lo = reinterpret_cast<uint4 *>(A_lo(s));
+#pragma unroll 4
+      for (int i = t; i < (int)(L::A_BYTES / 16); i += 128) {
+        const uint4 v = hi[i];
+        hi[i] = make_uint4(split_hi(v.x), split_hi(v.y), split_hi(v.z), split_hi(v.w));
+        lo[i] = make_uint4(split_lo(v.x), split_lo(v.y), split_lo(v.z), split_lo(v.w));
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&conv[s]);
+    }
+    const int64_t n0 = (int64_t)nt * (BNP / 2);
+    int64_t *coloff = reinterpret_cast<int64_t *>(smem + STAGES * L::STAGE + 256);
+    if (a.scatter && t < BNP / 2) coloff[t] = scatter_bits(n0 + t, a.sc.nn, a.sc.pn);
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    if (mbar_wait(accf, 0, abort_flag, false)) {
+      tc_fence_after();
+      const int q = warp & 3;  // TMEM lane quarter this warp may read
+      const int row = q * 32 + lane;
+      if (a.scatter) {
+        const int64_t om = scatter_bits(z, a.sc.nb, a.sc.pb) + scatter_bits((int64_t)mt * BM + row, a.sc.nm, a.sc.pm);
+#pragma unroll 1
+        for (int c = 0; c < BNP; c += 16) {
+          uint32_t r[16];
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, r);
+#pragma unroll
+          for (int j = 0; j < 8; j++)
+            if (n0 + c / 2 + j < a.N)
+              a.C[om + coloff[c / 2 + j]] = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+        }
+      }
+      float2 *crow = a.C + z * a.sC + ((int64_t)mt * BM + row) * a.N;
+#pragma unroll 1
+      for (int c = 0; c < (a.scatter ? 0 : BNP); c += 16) {
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, r);
+        const int64_t nb = n0 + c / 2;
+        if (nb + 8 <= a.N) {
+          float4 *dst = reinterpret_cast<float4 *>(crow + nb);
+#pragma unroll
+          for (int j = 0; j < 4; j++)
+            dst[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                 __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; j++)
+            if (nb + j < a.N) crow[nb + j] = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)L::TMEM_COLS));
+  }
+}
+
+// B (batch x n x k complex) -> prepared real rows, hi and lo parts:
+// row 2j = (Re b, -Im b) per k, row 2j+1 = (Im b, Re b); rows >= 2n are zero.
+__global__ void prep_b_kernel(const float2 *__restrict__ B, uint32_t *__restrict__ Bh, uint32_t *__restrict__ Bl,
+                              int64_t batch, int64_t N, int64_t K, int64_t sB, int NT) {
+  const int64_t total = batch * NT * K;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i % K;
+    const int64_t r = (i / K) % NT;
+    const int64_t z = i / (K * NT);
+    const int64_t j = r >> 1;
+    float x0 = 0.f, x1 = 0.f;
+    if (j < N) {
+      const float2 b = B[z * sB + j * K + k];
+      if (r & 1) {
+        x0 = b.y;
+        x1 = b.x;
+      } else {
+        x0 = b.x;
+        x1 = -b.y;
+      }
+    }
+    const uint32_t u0 = __float_as_uint(x0), u1 = __float_as_uint(x1);
+    const int64_t o = (z * NT + r) * 2 * K + 2 * k;
+    Bh[o] = split_hi(u0);
+    Bh[o + 1] = split_hi(u1);
+    Bl[o] = split_lo(u0);
+    Bl[o + 1] = split_lo(u1);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2D FP32 tensor map: rows x cols (cols contiguous), box = 32 x box_rows,
+// 128-byte swizzle, zero fill outside.
+bool make_map(CUtensorMap *tm, const void *base, int64_t cols, int64_t rows, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(cols * 4)};
+  cuuint32_t box[2] = {(cuuint32_t)kStageFloats, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int tile_cols(int64_t N) {  // real columns per tile (power of two, 16..256)
+  int64_t c = 2 * N;
+  if (c < 16) c = 16;
+  if (c > 256) c = 256;
+  int64_t p = 16;
+  while (p < c) p <<= 1;
+  return (int)p;
+}
+
+template <int BNP, int STAGES>
+cudaError_t run_tc(const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensorMap &tbl, const TcArgs &args,
+                   int64_t n_blocks, cudaStream_t s) {
+  using L = TcSmem<BNP, STAGES>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tc_tf32x3_kernel<BNP, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)L::TOTAL);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  tc_tf32x3_kernel<BNP, STAGES><<<(unsigned)n_blocks, kThreads, L::TOTAL, s>>>(ta, tbh, tbl, args);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool cgemm_tc_supported(int precision, int64_t M, int64_t N, int64_t K) {
+  if (precision != TZ_TF32X3) return false;
+  // M: whole 128-row tiles; K: at least 2 complex (16-byte rows for TMA);
+  // row coordinates must fit int32
+  if (M < BM || (M % BM) != 0 || K < 2 || (K % 2) != 0 || N < 1) return false;
+  return true;
+}
+
+size_t cgemm_tc_scratch_bytes(int precision, int64_t batch, int64_t N, int64_t K) {
+  if (precision != TZ_TF32X3) return 0;
+  const int bnp = tile_cols(N);
+  const int64_t nt = (2 * N + bnp - 1) / bnp;
+  return (size_t)(2 * batch * nt * bnp * 2 * K * 4);
+}
+
+cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M,
+                            int64_t N, int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc,
+                            void *scratch, size_t scratch_bytes, cudaStream_t s) {
+  if (!cgemm_tc_supported(precision, M, N, K)) return cudaErrorNotSupported;
+  if (sA != M * K || sB != N * K) return cudaErrorNotSupported;  // contiguous batches only
+  const int bnp = tile_cols(N);
+  const int n_tiles_n = (int)((2 * N + bnp - 1) / bnp);
+  const int NT = n_tiles_n * bnp;
+  const int64_t rowsA = batch * M, rowsB = batch * (int64_t)NT;
+  if (rowsA >= (int64_t(1) << 31) || rowsB >= (int64_t(1) << 31) || 2 * K >= (int64_t(1) << 31))
+    return cudaErrorNotSupported;
+  if (scratch_bytes < cgemm_tc_scratch_bytes(precision, batch, N, K) || !scratch) return cudaErrorInvalidValue;
+  uint32_t *Bh = static_cast<uint32_t *>(scratch);
+  uint32_t *Bl = Bh + batch * NT * 2 * K;
+  {
+    const int64_t total = batch * NT * K;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
+    prep_b_kernel<<<blocks, 256, 0, s>>>(B, Bh, Bl, batch, N, K, sB, NT);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  CUtensorMap ta, tbh, tbl;
+  if (!make_map(&ta, A, 2 * K, rowsA, BM) || !make_map(&tbh, Bh, 2 * K, rowsB, bnp) ||
+      !make_map(&tbl, Bl, 2 * K, rowsB, bnp))
+    return cudaErrorInvalidValue;
+  TcArgs args{};
+  args.C = C;
+  args.M = M;
+  args.N = N;
+  args.K = K;
+  args.sC = sC;
+  args.n_tiles_m = (int)(M / BM);
+  args.n_tiles_n = n_tiles_n;
+  args.kblocks = (int)((2 * K + kStageFloats - 1) / kStageFloats);
+  args.NT = NT;
+  args.scatter = sc ? 1 : 0;
+  if (sc) args.sc = *sc;
+  const int64_t n_blocks = batch * args.n_tiles_m * (int64_t)n_tiles_n;
+  if (n_blocks >= (int64_t(1) << 31)) return cudaErrorNotSupported;
+  switch (bnp) {
+    case 16: return run_tc<16, 4>(ta, tbh, tbl, args, n_blocks, s);
+    case 32: return run_tc<32, 4>(ta, tbh, tbl, args, n_blocks, s);
+    case 64: return run_tc<64, 4>(ta, tbh, tbl, args, n_blocks, s);
+    case 128: return run_tc<128, 3>(ta, tbh, tbl, args, n_blocks, s);
+    default: return run_tc<256, 2>(ta, tbh, tbl, args, n_blocks, s);
+  }
+}
+
+int tc_take_error() {
+  int v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int)) != cudaSuccess) return -1;
+  if (v) cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int));
+  return v;
 }
 
 }  // namespace dev

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "tz.h"
+
 namespace tz {
 namespace dev {
 
@@ -53,6 +55,15 @@ struct DStep {
   int8_t a_k[kMaxDirect], b_k[kMaxDirect];  // K bit -> A / B bit
 };
 
+// Where a GEMM writes its result: canonical element (z, m, n) of the
+// row-major [batch][m][n] product goes to offset Sb(z) + Sm(m) + Sn(n),
+// where bit j of m lands on bit pm[j] of the offset (likewise n, z). This
+// writes the result directly in the storage order its consumer needs.
+struct CScatter {
+  int nm, nn, nb;
+  int8_t pm[kMaxBits], pn[kMaxBits], pb[kMaxBits];
+};
+
 struct PermuteArgs {
   int rank;
   int8_t perm[kMaxBits];  // out bit p = in bit perm[p]
@@ -73,14 +84,18 @@ cudaError_t launch_leaf_build(const LeafJob *jobs, int n_jobs, const GroupState 
                               int g, cudaStream_t s);
 cudaError_t launch_direct(const DStep *steps, int n_steps, int64_t total_blocks, cudaStream_t s);
 cudaError_t launch_permute(const float2 *in, float2 *out, const PermuteArgs &a, cudaStream_t s);
+// sc == nullptr: C row-major with batch stride sC.
 cudaError_t launch_cgemm_simt(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N,
-                              int64_t K, int64_t sA, int64_t sB, int64_t sC, cudaStream_t s);
+                              int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s);
 // Split-precision tensor-core product; returns cudaErrorNotSupported when the
 // shape is outside what the kernel handles (the planner checks first).
 cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M,
-                            int64_t N, int64_t K, int64_t sA, int64_t sB, int64_t sC, void *scratch,
-                            size_t scratch_bytes, cudaStream_t s);
+                            int64_t N, int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc,
+                            void *scratch, size_t scratch_bytes, cudaStream_t s);
 bool cgemm_tc_supported(int precision, int64_t M, int64_t N, int64_t K);
+// Read and clear the flag a tensor-core kernel raises when a bounded wait
+// times out (synchronous; 1 = a wait gave up).
+int tc_take_error();
 size_t cgemm_tc_scratch_bytes(int precision, int64_t batch, int64_t N, int64_t K);
 cudaError_t launch_accumulate(const AccumArgs &a, cudaStream_t s);
 cudaError_t launch_accumulate_plain(const float2 *part, double2 *acc, int64_t n, double sre, double sim,

@@ -258,6 +258,124 @@ Pairs greedy_tree(const Network &net, double alpha, double temperature, uint64_t
   return pairs;
 }
 
+// ------------------------------------------------------ variable elimination
+// Bucket elimination: repeatedly pick an index, merge every tensor that holds
+// it (two smallest first) so that it is summed out, and continue. The index
+// picked is the one whose merged tensor would be smallest (min-degree
+// order), with Gumbel noise of the given temperature to randomise ties.
+Pairs elimination_tree(const Network &net, double temperature, uint64_t seed) {
+  const int L = (int)net.leaves.size();
+  const int I = (int)net.indices.size();
+  std::vector<std::vector<int>> sets(L);
+  std::vector<std::vector<int>> holders(I);
+  std::vector<int> cnt(I, 0);
+  std::vector<char> alive(L, 1);
+  for (int l = 0; l < L; l++) {
+    sets[l] = net.leaves[l].idx;
+    std::sort(sets[l].begin(), sets[l].end());
+    for (int i : sets[l]) {
+      cnt[i]++;
+      holders[i].push_back(l);
+    }
+  }
+  uint64_t rng = seed;
+  auto gumbel = [&]() {
+    double u = ((splitmix64_next(rng) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    return -std::log(-std::log(u));
+  };
+  auto live_holders = [&](int v) {
+    auto &h = holders[v];
+    h.erase(std::remove_if(h.begin(), h.end(), [&](int x) { return !alive[x]; }), h.end());
+    return h;
+  };
+  auto score = [&](int v) {
+    std::vector<int> u;
+    for (int t : live_holders(v)) u = set_union(u, sets[t]);
+    return (double)u.size() - 1.0;
+  };
+  std::vector<int> version(I, 0);
+  struct Cand {
+    double key;
+    int v, ver;
+    bool operator<(const Cand &o) const {
+      if (key != o.key) return key > o.key;
+      return v > o.v;
+    }
+  };
+  std::priority_queue<Cand> heap;
+  auto push = [&](int v) {
+    version[v]++;
+    double k = score(v);
+    if (temperature > 0) k -= temperature * gumbel();
+    heap.push({k, v, version[v]});
+  };
+  for (int v = 0; v < I; v++)
+    if (!net.is_open(v) && cnt[v] > 0) push(v);
+  Pairs pairs;
+  auto merge = [&](int a, int b) {
+    const auto &A = sets[a], &B = sets[b];
+    std::vector<int> C;
+    size_t ia = 0, ib = 0;
+    while (ia < A.size() || ib < B.size()) {
+      if (ib >= B.size() || (ia < A.size() && A[ia] < B[ib])) {
+        C.push_back(A[ia++]);
+      } else if (ia >= A.size() || B[ib] < A[ia]) {
+        C.push_back(B[ib++]);
+      } else {
+        int i = A[ia];
+        cnt[i]--;
+        if (cnt[i] > 1 || net.is_open(i))
+          C.push_back(i);
+        else
+          cnt[i] = 0;
+        ia++;
+        ib++;
+      }
+    }
+    int c = (int)sets.size();
+    alive[a] = alive[b] = 0;
+    alive.push_back(1);
+    sets.push_back(C);
+    for (int i : C) holders[i].push_back(c);
+    pairs.push_back({a, b});
+    return c;
+  };
+  while (!heap.empty()) {
+    Cand cd_ = heap.top();
+    heap.pop();
+    int v = cd_.v;
+    if (cd_.ver != version[v] || cnt[v] == 0) continue;
+    std::vector<int> H = live_holders(v);
+    if (H.size() < 2) continue;
+    // merge the bucket, two smallest first
+    while (H.size() > 1) {
+      std::sort(H.begin(), H.end(), [&](int x, int y) {
+        if (sets[x].size() != sets[y].size()) return sets[x].size() < sets[y].size();
+        return x < y;
+      });
+      int c = merge(H[0], H[1]);
+      H.erase(H.begin(), H.begin() + 2);
+      H.push_back(c);
+    }
+    int c = H[0];
+    for (int u : sets[c])
+      if (!net.is_open(u) && cnt[u] > 0) push(u);
+  }
+  std::vector<int> rest;
+  for (int x = 0; x < (int)sets.size(); x++)
+    if (alive[x]) rest.push_back(x);
+  while (rest.size() > 1) {
+    std::sort(rest.begin(), rest.end(), [&](int x, int y) {
+      if (sets[x].size() != sets[y].size()) return sets[x].size() < sets[y].size();
+      return x < y;
+    });
+    int c = merge(rest[0], rest[1]);
+    rest.erase(rest.begin(), rest.begin() + 2);
+    rest.push_back(c);
+  }
+  return pairs;
+}
+
 // ------------------------------------------------------------------ slicing
 std::vector<int> select_slices(const Network &net, const Pairs &pairs, int log2_max, int k_max,
                                const CostModel &cm) {

@@ -135,106 +135,90 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
   auto set_of = [&](int node) { return ti.sets[node]; };
 
   // ---------------------------------------------------------------- layouts
-  auto new_temp = [&](int src, const std::vector<int> &lay) {
-    PTensor t;
-    t.lay = lay;
-    t.var = p->T[src].var;
-    t.fixed = true;
-    p->T.push_back(t);
-    return (int)p->T.size() - 1;
-  };
+  // Every tensor is stored in the order its consumer needs, and its producer
+  // (leaf builder, constant upload, direct step or GEMM epilogue) writes it
+  // in that order directly: no operand permutes. Layouts are decided in
+  // reverse tree order, consumer before producer. A GEMM step wants
+  //   X = [summed | X-free | batch],  Y = [summed | Y-free | batch]
+  // (row-major [batch][rows][k]); its result goes through a scatter map.
+  // The summed-bit order favours bits its producer writes contiguously:
+  // bits the producing GEMM holds as columns, then rows, then batch.
+  std::vector<int> roleX(NS, -1);  // operand used as X (rows) of each GEMM step
   for (int s = 0; s < NS; s++) {
     const StepInfo &st = ti.steps[s];
+    roleX[s] = st.freeA.size() >= st.freeB.size() ? st.a : st.b;
+  }
+  std::vector<int> producer(L + NS, -1);
+  for (int s = 0; s < NS; s++) producer[ti.steps[s].c] = s;
+  // class of bit i in the natural output order of node t's producer:
+  // 0 = GEMM column (fastest), 1 = GEMM row, 2 = batch or no preference
+  auto bit_class = [&](int t, int i) {
+    int s = producer[t];
+    if (s < 0 || !p->S[s].gemm) return 2;
+    const StepInfo &st = ti.steps[s];
+    const auto &fx = roleX[s] == st.a ? st.freeA : st.freeB;
+    const auto &fy = roleX[s] == st.a ? st.freeB : st.freeA;
+    if (std::find(fy.begin(), fy.end(), i) != fy.end()) return 0;
+    if (std::find(fx.begin(), fx.end(), i) != fx.end()) return 1;
+    return 2;
+  };
+  auto natural = [&](int t) {  // producer's own preferred order
+    int s = producer[t];
+    if (s < 0 || !p->S[s].gemm) return set_of(t);
+    const StepInfo &st = ti.steps[s];
+    const auto &fx = roleX[s] == st.a ? st.freeA : st.freeB;
+    const auto &fy = roleX[s] == st.a ? st.freeB : st.freeA;
+    return concat3(fy, fx, st.batch);
+  };
+  p->T[p->root].lay = natural(p->root);
+  p->T[p->root].fixed = true;
+  for (int s = NS - 1; s >= 0; s--) {
+    const StepInfo &st = ti.steps[s];
     PStep &ps = p->S[s];
-    if (!ps.gemm) {
-      for (int x : {st.a, st.b})
-        if (!p->T[x].fixed) {
-          p->T[x].lay = set_of(x);
-          p->T[x].fixed = true;
-        }
-      continue;
+    if (!p->T[st.c].fixed) {
+      p->T[st.c].lay = natural(st.c);
+      p->T[st.c].fixed = true;
     }
-    struct Option {
-      int X, Y;
-      std::vector<int> fX, fY, layX, layY, layC;
-      bool permX, permY;
-      double cost;
-    };
-    std::vector<Option> opts;
-    for (int role = 0; role < 2; role++) {
-      Option op;
-      op.X = role == 0 ? st.a : st.b;
-      op.Y = role == 0 ? st.b : st.a;
-      op.fX = role == 0 ? st.freeA : st.freeB;
-      op.fY = role == 0 ? st.freeB : st.freeA;
-      const PTensor &TX = p->T[op.X], &TY = p->T[op.Y];
-      std::vector<int> ko, bo, fxo, fyo;
-      bool xok = TX.fixed && groups_ok(TX.lay, st.contr, op.fX, st.batch, &ko, &fxo, &bo);
-      std::vector<int> ko2, bo2, fyo2;
-      bool yok = TY.fixed && groups_ok(TY.lay, st.contr, op.fY, st.batch, &ko2, &fyo2, &bo2);
-      if (!xok) {
-        if (yok) {
-          ko = ko2;
-          bo = bo2;
-        } else {
-          ko = st.contr;
-          bo = st.batch;
-        }
-        fxo = TX.fixed ? rel_order(TX.lay, op.fX) : op.fX;
-      }
-      fyo = TY.fixed ? rel_order(TY.lay, op.fY) : op.fY;
-      op.layX = concat3(ko, fxo, bo);
-      op.layY = concat3(ko, fyo, bo);
-      op.layC = concat3(fyo, fxo, bo);
-      op.permX = TX.fixed && TX.lay != op.layX;
-      op.permY = TY.fixed && TY.lay != op.layY;
-      op.cost = 0;
-      if (op.permX && TX.var) op.cost += 16.0 * TX.elems();
-      if (op.permY && TY.var) op.cost += 16.0 * TY.elems();
-      // look ahead: will the consumer have to permute C?
-      int cs = consumer[st.c];
-      if (cs >= 0 && p->S[cs].gemm && st.var) {
-        const StepInfo &pc = ti.steps[cs];
-        std::vector<int> own = st.c == pc.a ? pc.freeA : pc.freeB;
-        if (!groups_ok(op.layC, pc.contr, own, pc.batch, nullptr, nullptr, nullptr))
-          op.cost += 16.0 * std::ldexp(1.0, (int)op.layC.size()) * 0.999;
-      }
-      // prefer the larger operand as the row (M) operand
-      if (op.fX.size() < op.fY.size()) op.cost += 1e-3;
-      opts.push_back(op);
-    }
-    const Option &best = opts[0].cost <= opts[1].cost ? opts[0] : opts[1];
-    ps.opX = best.X;
-    ps.opY = best.Y;
-    if (!p->T[best.X].fixed) {
-      p->T[best.X].lay = best.layX;
-      p->T[best.X].fixed = true;
-    } else if (best.permX) {
-      ps.permX = best.X;
-      ps.opX = new_temp(best.X, best.layX);
-    }
-    if (!p->T[best.Y].fixed) {
-      p->T[best.Y].lay = best.layY;
-      p->T[best.Y].fixed = true;
-    } else if (best.permY) {
-      ps.permY = best.Y;
-      ps.opY = new_temp(best.Y, best.layY);
-    }
-    p->T[st.c].lay = best.layC;
-    p->T[st.c].fixed = true;
-    ps.M = int64_t(1) << best.fX.size();
-    ps.N = int64_t(1) << best.fY.size();
+    if (!ps.gemm) continue;
+    const std::vector<int> &Lc = p->T[st.c].lay;
+    const int X = roleX[s], Y = X == st.a ? st.b : st.a;
+    const std::vector<int> &fX = X == st.a ? st.freeA : st.freeB;
+    const std::vector<int> &fY = X == st.a ? st.freeB : st.freeA;
+    // summed bits: ordered for the larger operand's producer
+    const int big = p->T[X].var == p->T[Y].var ? (fX.size() >= fY.size() ? X : Y) : (p->T[X].var ? X : Y);
+    std::vector<int> ko = st.contr;
+    std::stable_sort(ko.begin(), ko.end(), [&](int u, int v) { return bit_class(big, u) < bit_class(big, v); });
+    std::vector<int> fxo = rel_order(Lc, fX), fyo = rel_order(Lc, fY), bo = rel_order(Lc, st.batch);
+    p->T[X].lay = concat3(ko, fxo, bo);
+    p->T[Y].lay = concat3(ko, fyo, bo);
+    p->T[X].fixed = p->T[Y].fixed = true;
+    ps.opX = X;
+    ps.opY = Y;
+    ps.M = int64_t(1) << fX.size();
+    ps.N = int64_t(1) << fY.size();
     ps.K = int64_t(1) << st.contr.size();
     ps.batch = int64_t(1) << st.batch.size();
     ps.tc = o.precision != TZ_C64_SIMT && dev::cgemm_tc_supported(o.precision, ps.M, ps.N, ps.K);
     if (ps.tc) ps.tc_scratch = (int64_t)dev::cgemm_tc_scratch_bytes(o.precision, ps.batch, ps.N, ps.K);
-  }
-  if (!p->T[p->root].fixed) {
-    p->T[p->root].lay = set_of(p->root);
-    p->T[p->root].fixed = true;
+    // where canonical (z, m, n) lands in C
+    dev::CScatter &sc = ps.scatter;
+    std::memset(&sc, 0, sizeof(sc));
+    sc.nm = (int)fxo.size();
+    sc.nn = (int)fyo.size();
+    sc.nb = (int)bo.size();
+    for (int j = 0; j < sc.nm; j++) sc.pm[j] = (int8_t)pos_of(Lc, fxo[j]);
+    for (int j = 0; j < sc.nn; j++) sc.pn[j] = (int8_t)pos_of(Lc, fyo[j]);
+    for (int j = 0; j < sc.nb; j++) sc.pb[j] = (int8_t)pos_of(Lc, bo[j]);
+    ps.row_major = true;
+    for (int j = 0; j < sc.nn; j++) ps.row_major &= sc.pn[j] == j;
+    for (int j = 0; j < sc.nm; j++) ps.row_major &= sc.pm[j] == sc.nn + j;
+    for (int j = 0; j < sc.nb; j++) ps.row_major &= sc.pb[j] == sc.nn + sc.nm + j;
   }
   for (int n = 0; n < L + NS; n++)
-    if (!p->T[n].fixed) fail(TZ_EINVAL, "internal: tensor without layout");
+    if (!p->T[n].fixed) {
+      p->T[n].lay = set_of(n);
+      p->T[n].fixed = true;
+    }
   // root must hold exactly the batch indices
   for (int i : p->T[p->root].lay)
     if (!net.is_open(i)) fail(TZ_EINVAL, "tree root keeps a wire index: the tree does not contract the network");
@@ -590,7 +574,14 @@ std::string plan_describe(const tz_plan *p) {
     o << (s ? "," : "") << "{\"a\":" << x.a << ",\"b\":" << x.b << ",\"c\":" << x.c << ",\"var\":" << x.var
       << ",\"gemm\":" << x.gemm << ",\"tc\":" << x.tc << ",\"opX\":" << x.opX << ",\"opY\":" << x.opY
       << ",\"M\":" << x.M << ",\"N\":" << x.N << ",\"K\":" << x.K << ",\"batch\":" << x.batch
-      << ",\"level\":" << x.level << ",\"dstep\":" << x.dstep << ",\"permX\":" << x.permX << ",\"permY\":" << x.permY << "}";
+      << ",\"level\":" << x.level << ",\"dstep\":" << x.dstep << ",\"permX\":" << x.permX << ",\"permY\":" << x.permY
+      << ",\"row_major\":" << x.row_major << ",\"pm\":[";
+    for (int j = 0; j < x.scatter.nm; j++) o << (j ? "," : "") << (int)x.scatter.pm[j];
+    o << "],\"pn\":[";
+    for (int j = 0; j < x.scatter.nn; j++) o << (j ? "," : "") << (int)x.scatter.pn[j];
+    o << "],\"pb\":[";
+    for (int j = 0; j < x.scatter.nb; j++) o << (j ? "," : "") << (int)x.scatter.pb[j];
+    o << "]}";
   }
   auto items = [&](const std::vector<Item> &v) {
     o << "[";
@@ -636,10 +627,80 @@ static void *tensor_ptr(const tz_plan *p, int t) {
   fail(TZ_EINVAL, "internal: tensor has no memory");
 }
 
+static cudaEvent_t take_event(tz_plan *p) {
+  if (!p->event_pool.empty()) {
+    cudaEvent_t e = p->event_pool.back();
+    p->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cuda_check(cudaEventCreate(&e), "cudaEventCreate");
+  return e;
+}
+
+void plan_profile_collect(tz_plan *p) {
+  if (p->pending.empty()) return;
+  cuda_check(cudaStreamSynchronize(p->stream), "profile sync");
+  for (auto &q : p->pending) {
+    float ms = 0;
+    cuda_check(cudaEventElapsedTime(&ms, q.a, q.b), "event time");
+    p->prof.launches[q.kind]++;
+    p->prof.ms[q.kind] += ms;
+    p->prof.flops[q.kind] += q.flops;
+    p->prof.bytes[q.kind] += q.bytes;
+    p->event_pool.push_back(q.a);
+    p->event_pool.push_back(q.b);
+  }
+  p->pending.clear();
+}
+
+// kind (profile slot), useful flops and algorithmic bytes of one item
+static void item_cost(const tz_plan *p, const Item &it, int *kind, double *flops, double *bytes) {
+  *flops = 0;
+  *bytes = 0;
+  switch (it.kind) {
+    case IT_LEAVES:
+      *kind = 0;
+      for (size_t j = 0; j < p->jobs.size(); j++) *bytes += 8.0 * (int64_t(1) << p->jobs[j].rank);
+      break;
+    case IT_DIRECT:
+      *kind = 1;
+      for (int d = it.first; d < it.first + it.count; d++) {
+        const PTensor &A = p->T[p->dstep_tensors[3 * d]], &B = p->T[p->dstep_tensors[3 * d + 1]],
+                      &C = p->T[p->dstep_tensors[3 * d + 2]];
+        *flops += 8.0 * std::ldexp(1.0, p->dsteps[d].nC + p->dsteps[d].nK);
+        *bytes += 8.0 * (A.elems() + B.elems() + C.elems());
+      }
+      break;
+    case IT_PERMUTE:
+      *kind = 2;
+      *bytes = 16.0 * p->T[it.a].elems();
+      break;
+    case IT_GEMM: {
+      const PStep &ps = p->S[it.a];
+      *kind = ps.tc ? 4 : 3;
+      *flops = 8.0 * ps.batch * (double)ps.M * (double)ps.N * (double)ps.K;
+      *bytes = 8.0 * ps.batch * ((double)ps.M * ps.K + (double)ps.N * ps.K + (double)ps.M * ps.N);
+      break;
+    }
+    default:
+      *kind = 5;
+      *bytes = 24.0 * (int64_t(1) << p->net.batch_log2);
+  }
+}
+
 static void run_items(tz_plan *p, const std::vector<Item> &items) {
   cudaStream_t s = p->stream;
   auto *gs = reinterpret_cast<dev::GroupState *>(p->ws + p->off_gs);
+  const bool prof = p->profiling && !p->capturing;
   for (const Item &it : items) {
+    tz_plan::Pending pend{};
+    if (prof) {
+      item_cost(p, it, &pend.kind, &pend.flops, &pend.bytes);
+      pend.a = take_event(p);
+      pend.b = take_event(p);
+      cuda_check(cudaEventRecord(pend.a, s), "event record");
+    }
     switch (it.kind) {
       case IT_LEAVES:
         if (!p->jobs.empty())
@@ -668,14 +729,15 @@ static void run_items(tz_plan *p, const std::vector<Item> &items) {
         const float2 *X = (const float2 *)tensor_ptr(p, ps.opX);
         const float2 *Y = (const float2 *)tensor_ptr(p, ps.opY);
         float2 *C = (float2 *)tensor_ptr(p, ps.c);
+        const dev::CScatter *sc = ps.row_major ? nullptr : &ps.scatter;
         if (ps.tc) {
           void *scr = p->ws + p->off_arena + ps.tc_scratch_off;
           cuda_check(dev::launch_cgemm_tc(p->opts.precision, X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.M * ps.K,
-                                          ps.N * ps.K, ps.M * ps.N, scr, (size_t)ps.tc_scratch, s),
+                                          ps.N * ps.K, ps.M * ps.N, sc, scr, (size_t)ps.tc_scratch, s),
                      "tensor-core gemm");
         } else {
           cuda_check(dev::launch_cgemm_simt(X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.M * ps.K, ps.N * ps.K,
-                                            ps.M * ps.N, s),
+                                            ps.M * ps.N, sc, s),
                      "simt gemm");
         }
         break;
@@ -697,6 +759,11 @@ static void run_items(tz_plan *p, const std::vector<Item> &items) {
         cuda_check(dev::launch_accumulate(a, s), "accumulate");
         break;
       }
+    }
+    if (prof) {
+      cuda_check(cudaEventRecord(pend.b, s), "event record");
+      p->pending.push_back(pend);
+      if (p->pending.size() >= 4096) plan_profile_collect(p);
     }
   }
 }
@@ -774,17 +841,20 @@ void plan_run(tz_plan *p, int64_t n_rows) {
   const int64_t chunk = int64_t(1) << p->net.batch_log2;
   const int64_t n_chunks = (n_rows + chunk - 1) / chunk;
   const int64_t n_groups = n_chunks * (p->hi - p->lo);
-  const bool graph = p->opts.use_graph && s != nullptr;
+  const bool graph = p->opts.use_graph && s != nullptr && !p->profiling;
   if (graph && !p->graph_exec) {
     cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+    p->capturing = true;
     try {
       run_items(p, p->var_items);
     } catch (...) {
-      cudaGraph_t g2;
+      p->capturing = false;
+      cudaGraph_t g2 = nullptr;
       cudaStreamEndCapture(s, &g2);
       if (g2) cudaGraphDestroy(g2);
       throw;
     }
+    p->capturing = false;
     cuda_check(cudaStreamEndCapture(s, &p->graph), "end capture");
     cuda_check(cudaGraphInstantiate(&p->graph_exec, p->graph, 0), "instantiate graph");
   }
@@ -798,6 +868,11 @@ void plan_run(tz_plan *p, int64_t n_rows) {
 
 void plan_destroy(tz_plan *p) {
   if (!p) return;
+  for (auto &q : p->pending) {
+    cudaEventDestroy(q.a);
+    cudaEventDestroy(q.b);
+  }
+  for (auto e : p->event_pool) cudaEventDestroy(e);
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   if (p->graph) cudaGraphDestroy(p->graph);
   delete p;

@@ -33,6 +33,8 @@ struct PStep {
   int dstep = -1;             // index into dsteps (direct steps)
   int64_t tc_scratch = 0;     // bytes of tensor-core operand scratch
   int64_t tc_scratch_off = -1;
+  dev::CScatter scatter{};    // where the GEMM writes its result
+  bool row_major = false;     // scatter is the plain row-major order
 };
 
 struct Item {
@@ -72,6 +74,17 @@ struct tz_plan {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   tz_plan_stats stats{};
+  // profiling
+  bool profiling = false;
+  bool capturing = false;
+  struct Pending {
+    int kind;
+    cudaEvent_t a, b;
+    double flops, bytes;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  tz_plan_profile prof{};
 };
 
 namespace tz {
@@ -81,6 +94,7 @@ void plan_bind(tz_plan *p, void *ws, size_t bytes);
 // leaves the FP64 sums in the plan's accumulator (asynchronous).
 void plan_run(tz_plan *p, int64_t n_rows);
 void plan_destroy(tz_plan *p);
+void plan_profile_collect(tz_plan *p);
 std::string plan_describe(const tz_plan *p);
 inline void cuda_check(cudaError_t e, const char *what) {
   if (e != cudaSuccess) fail(TZ_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));

@@ -97,6 +97,7 @@ struct CostModel {
 double group_time(const TreeInfo &ti, const CostModel &cm);
 
 Pairs greedy_tree(const Network &net, double alpha, double temperature, uint64_t seed);
+Pairs elimination_tree(const Network &net, double temperature, uint64_t seed);
 std::vector<int> select_slices(const Network &net, const Pairs &pairs, int log2_max, int k_max,
                                const CostModel &cm);
 

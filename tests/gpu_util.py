@@ -19,10 +19,15 @@ def rel_err(got, ref, n_qubits):
 
 
 def make_plan(tz, spec, batch_log2=0, log2_max=0, precision="c64", small_log2=0, restarts=4, seed=1,
-              use_graph=False, stream=None, k_max=40, max_bitstrings=0):
+              use_graph=False, stream=None, k_max=8, max_bitstrings=0, slice_bits=0):
+    """log2_max > 0: slice down to that size; slice_bits > 0: slice until the
+    largest intermediate is slice_bits below the unsliced one."""
     c = tz.tz_circuit_from_spec(spec)
     net = tz.tz_network_from_circuit(c, batch_log2)
     tree = tz.tz_path_greedy(net, restarts=restarts, seed=seed, log2_max_intermediate=log2_max, precision=precision)
+    if slice_bits > 0:
+        full = tz.tz_plan_create(net, tree, []).stats()["max_log2"]
+        log2_max = full - slice_bits
     sl = tz.tz_slice_select(net, tree, log2_max, k_max) if log2_max > 0 else []
     plan = tz.tz_plan_create(net, tree, sl, precision=precision, small_log2=small_log2, use_graph=use_graph,
                              stream=stream, max_bitstrings=max_bitstrings)

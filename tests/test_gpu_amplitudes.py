@@ -55,14 +55,14 @@ def test_batched_bitstrings_ragged(tz, g, small):
     assert rel_err(got, sv.amplitudes(spec, bits), 16) <= TOL_C64
 
 
-@pytest.mark.parametrize("rows,cols,t,seed,log2max,g,small", [
-    (4, 4, 10, 1, 4, 0, 3), (4, 5, 12, 3, 6, 1, 5), (5, 5, 16, 4, 8, 2, 6), (4, 4, 20, 6, 5, 0, 20)])
-def test_sliced_against_statevector(tz, rows, cols, t, seed, log2max, g, small):
+@pytest.mark.parametrize("rows,cols,t,seed,cut,g,small", [
+    (4, 4, 10, 1, 2, 0, 3), (4, 5, 12, 3, 3, 1, 5), (4, 5, 16, 4, 4, 2, 6), (4, 4, 20, 6, 3, 0, 20)])
+def test_sliced_against_statevector(tz, rows, cols, t, seed, cut, g, small):
     spec = grid_spec(rows, cols, t, seed)
     n = rows * cols
     bits = ti.random_bitstrings(n, 6, seed + 50)
-    plan, net, tree, sl = make_plan(tz, spec, batch_log2=g, log2_max=log2max, small_log2=small)
-    assert len(sl) >= 1
+    plan, net, tree, sl = make_plan(tz, spec, batch_log2=g, slice_bits=cut, small_log2=small)
+    assert cut <= len(sl) <= 8
     got = tz.tz_contract_amplitudes(plan, bits)
     assert rel_err(got, sv.amplitudes(spec, bits), n) <= TOL_C64
 
@@ -70,9 +70,9 @@ def test_sliced_against_statevector(tz, rows, cols, t, seed, log2max, g, small):
 def test_slice_ranges_add_up_and_match_oracle_partials(tz):
     spec = grid_spec(4, 5, 12, 3)
     bits = ti.random_bitstrings(20, 3, 8)
-    plan, net, tree, sl = make_plan(tz, spec, log2_max=5, small_log2=5)
+    plan, net, tree, sl = make_plan(tz, spec, slice_bits=3, small_log2=5, k_max=4)
     k = len(sl)
-    assert k >= 3
+    assert 3 <= k <= 4
     full = tz.tz_contract_amplitudes(plan, bits)
     parts = []
     for s in range(1 << k):
@@ -91,7 +91,7 @@ def test_device_entry_point_and_graph(tz):
     spec = grid_spec(4, 4, 10, 1)
     bits = ti.random_bitstrings(16, 20, 9)
     stream = torch.cuda.Stream()
-    plan, *_ = make_plan(tz, spec, batch_log2=2, log2_max=4, small_log2=4, use_graph=True, stream=stream)
+    plan, *_ = make_plan(tz, spec, batch_log2=2, slice_bits=2, small_log2=4, use_graph=True, stream=stream)
     d_bits = torch.from_numpy(bits).cuda()
     d_out = torch.zeros(40, dtype=torch.float64, device="cuda")
     for _ in range(2):   # second call replays the captured graph
@@ -100,3 +100,25 @@ def test_device_entry_point_and_graph(tz):
         stream.synchronize()
         got = d_out.cpu().numpy().view(np.complex128)
         assert rel_err(got, sv.amplitudes(spec, bits), 16) <= TOL_C64
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "c64"])
+def test_tensor_core_path_5x5(tz, prec):
+    """A circuit big enough that GEMM steps have >= 128 rows, so the split-TF32
+    tcgen05 product really runs (checked through the per-kernel profile);
+    compared with the oracle's plain-wire contractor."""
+    spec = grid_spec(5, 5, 16, 21)
+    bits = ti.random_bitstrings(25, 4, 77)
+    plan, *_ = make_plan(tz, spec, precision=prec, small_log2=8, restarts=8, seed=3)
+    plan.profile_enable(True)
+    got = tz.tz_contract_amplitudes(plan, bits)
+    prof = plan.profile()
+    c = tn.Contractor(spec, max_log2=24)
+    ref = np.array([c.amplitude(x) for x in bits])
+    err = rel_err(got, ref, 25)
+    print(f"{prec}: max rel err {err:.3e}, tc launches {prof['gemm_tc']['launches']}")
+    assert err <= TOL_C64
+    if prec == "tf32x3":
+        assert prof["gemm_tc"]["launches"] > 0
+    else:
+        assert prof["gemm_tc"]["launches"] == 0 and prof["gemm_simt"]["launches"] > 0

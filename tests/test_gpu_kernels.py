@@ -57,6 +57,36 @@ def test_cgemm_simt(env, batch, m, n, k):
     assert np.all(np.abs(C - ref) <= 4 * (k + 2) * 2.0 ** -24 * bound + 1e-30)
 
 
+@pytest.mark.parametrize("batch,m,n,k", [(1, 128, 1, 2), (1, 128, 8, 16), (2, 256, 64, 32), (1, 1024, 128, 64),
+                                         (3, 128, 4, 4), (1, 512, 256, 128), (4, 384, 24, 10), (1, 8192, 16, 256)])
+def test_cgemm_tf32x3(env, batch, m, n, k):
+    """Split-TF32 tcgen05 product: hi*hi + hi*lo + lo*hi with round-to-nearest
+    splits leaves < 2^-20 |a||b| per product, plus FP32 accumulation."""
+    tz, torch = env
+    rng = np.random.default_rng(m + 3 * n + 7 * k)
+    A, dA = c64(torch, rng, (batch, m, k))
+    B, dB = c64(torch, rng, (batch, n, k))
+    dC = torch.zeros(batch * m * n * 2, dtype=torch.float32, device="cuda")
+    nbytes = tz.tz_op_cgemm_scratch_bytes("tf32x3", batch, m, n, k)
+    scratch = torch.empty(nbytes // 4 + 64, dtype=torch.float32, device="cuda")
+    tz.tz_op_cgemm("tf32x3", batch, m, n, k, dA, m * k, dB, n * k, dC, m * n, scratch=scratch)
+    torch.cuda.synchronize()
+    C = dC.cpu().numpy().view(np.complex64).reshape(batch, m, n)
+    ref = linalg.cgemm(A, B)
+    bound = linalg.cgemm(np.abs(A).astype(np.complex128), np.abs(B).astype(np.complex128)).real
+    err = np.abs(C - ref)
+    assert np.all(err <= (2.0 ** -18 + 4 * (k + 2) * 2.0 ** -24) * bound + 1e-30), float(np.max(err / bound))
+    # and it is genuinely more accurate than one TF32 product would be
+    assert np.max(err / bound) < 2.0 ** -14
+
+
+def test_cgemm_tc_rejects_unsupported(env):
+    tz, torch = env
+    with pytest.raises(tz.TzError) as e:
+        tz.tz_op_cgemm_scratch_bytes("tf32x3", 1, 64, 8, 8)   # M below one 128-row tile
+    assert e.value.code == -6
+
+
 def test_accumulate_fp64(env):
     tz, torch = env
     rng = np.random.default_rng(5)
