@@ -192,6 +192,7 @@ typedef struct {
   double permute_bytes_per_group;/* extra bytes moved by operand permutes            */
   size_t workspace_bytes;        /* device workspace the plan needs                  */
   size_t const_bytes;            /* part of it holding bind-time constants           */
+  size_t scratch_bytes;          /* per-query scratch part (server admission unit)   */
 } tz_plan_stats;
 
 /* Build a plan: classify steps, choose layouts, permutes and kernels, lay

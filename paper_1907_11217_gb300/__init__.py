@@ -18,7 +18,7 @@ import ctypes
 
 import numpy as np
 
-from ._lib import (PROFILE_KINDS, tz_plan_profile, PRECISIONS, TZ_BF16X3, TZ_C64_SIMT, TZ_LATTICE_BRISTLECONE, TZ_LATTICE_GRID, TZ_TF32X3, TzError,
+from ._lib import (PROFILE_KINDS, tz_plan_profile, tz_server_opts, PRECISIONS, TZ_BF16X3, TZ_C64_SIMT, TZ_LATTICE_BRISTLECONE, TZ_LATTICE_GRID, TZ_TF32X3, TzError,
                    check, lib, tz_lattice, tz_network_opts, tz_path_opts, tz_plan_opts, tz_plan_stats)
 
 __all__ = [
@@ -284,3 +284,54 @@ def tz_op_accumulate(d_part, d_acc, n, scale=1.0 + 0j, stream=None):
     check(lib().tz_op_accumulate(_ptr(d_part), ctypes.cast(ctypes.c_void_p(d_acc.data_ptr()),
                                                            ctypes.POINTER(ctypes.c_double)),
                                  n, float(np.real(scale)), float(np.imag(scale)), _stream(stream)))
+
+
+class Server(_Handle):
+    """Amplitude server over resident plans (continuous batching): queries
+    are admitted while a slot and enough of the arena are free and run
+    concurrently on separate streams."""
+    _destroy = "tz_server_destroy"
+
+    def __init__(self, h, arena):
+        super().__init__(h)
+        self._arena = arena
+
+    def submit(self, plan: "Plan", bitstrings) -> int:
+        b = np.ascontiguousarray(np.asarray(bitstrings, dtype=np.uint8).reshape(-1, plan.n_qubits))
+        t = ctypes.c_uint64()
+        check(lib().tz_server_submit(self._h, plan.handle, b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), len(b),
+                                     ctypes.byref(t)))
+        self._rows = getattr(self, "_rows", {})
+        self._rows[t.value] = len(b)
+        return t.value
+
+    def poll(self, ticket: int):
+        """complex128 amplitudes once the query is done, else None."""
+        n = self._rows[ticket]
+        out = np.zeros(2 * n, dtype=np.float64)
+        done = ctypes.c_int()
+        check(lib().tz_server_poll(self._h, ticket, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   ctypes.byref(done)))
+        if done.value:
+            del self._rows[ticket]
+            return out.view(np.complex128)
+        return None
+
+    def latency(self):
+        p50, p99, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        check(lib().tz_server_latency(self._h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(n)))
+        return p50.value, p99.value, n.value
+
+
+def tz_server_create(arena_bytes, max_inflight=4, device=0, hbm_budget=0, wait_admit=True, arena=None) -> Server:
+    """Server with a device arena of arena_bytes (a torch uint8 tensor is
+    allocated when `arena` is None)."""
+    import torch
+    if arena is None:
+        arena = torch.empty(arena_bytes + 256, dtype=torch.uint8, device=f"cuda:{device}")
+    base = arena.data_ptr()
+    aligned = (base + 255) & ~255
+    o = tz_server_opts(hbm_budget, max_inflight, device, ctypes.c_void_p(aligned), arena_bytes, int(wait_admit))
+    h = ctypes.c_void_p()
+    check(lib().tz_server_create(ctypes.byref(o), ctypes.byref(h)))
+    return Server(h, arena)

@@ -48,7 +48,7 @@ class tz_plan_stats(ctypes.Structure):
                 ("batch_log2", ctypes.c_int), ("max_log2", ctypes.c_int), ("flops_per_group", ctypes.c_double),
                 ("gemm_flops_per_group", ctypes.c_double), ("bytes_per_group", ctypes.c_double),
                 ("permute_bytes_per_group", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t),
-                ("const_bytes", ctypes.c_size_t)]
+                ("const_bytes", ctypes.c_size_t), ("scratch_bytes", ctypes.c_size_t)]
 
 
 PROFILE_KINDS = ("leaves", "direct", "permute", "gemm_simt", "gemm_tc", "accumulate")

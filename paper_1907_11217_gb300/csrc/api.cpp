@@ -21,6 +21,9 @@ thread_local std::string g_err;
 void set_error(const std::string &m) { g_err = m; }
 }  // namespace
 
+// shared with the other translation units that export C entry points
+void tz_set_error_message(const std::string &m) { set_error(m); }
+
 #define TZ_TRY try {
 #define TZ_CATCH                           \
   }                                        \
@@ -292,11 +295,12 @@ int tz_contract_amplitudes(tz_plan *plan, const uint8_t *bitstrings, int64_t n, 
   for (int64_t i = 0; i < n * nq; i++)
     if (bitstrings[i] > 1) tz::fail(TZ_EINVAL, "bitstring bytes must be 0 or 1");
   tz::cuda_check(cudaSetDevice(plan->opts.device), "cudaSetDevice");
-  cudaStream_t s = plan->stream;
-  tz::cuda_check(cudaMemcpyAsync(plan->ws + plan->off_bits, bitstrings, (size_t)(n * nq), cudaMemcpyHostToDevice, s),
+  const tz::RunCtx ctx = tz::default_ctx(plan);
+  cudaStream_t s = ctx.stream;
+  tz::cuda_check(cudaMemcpyAsync(ctx.scratch + plan->s_bits, bitstrings, (size_t)(n * nq), cudaMemcpyHostToDevice, s),
                  "copy bitstrings in");
-  tz::plan_run(plan, n);
-  tz::cuda_check(cudaMemcpyAsync(out, plan->ws + plan->off_acc, (size_t)n * 16, cudaMemcpyDeviceToHost, s),
+  tz::plan_run(plan, ctx, n, plan->lo, plan->hi);
+  tz::cuda_check(cudaMemcpyAsync(out, ctx.scratch + plan->s_acc, (size_t)n * 16, cudaMemcpyDeviceToHost, s),
                  "copy amplitudes out");
   tz::cuda_check(cudaStreamSynchronize(s), "contract");
   if (plan->opts.precision != TZ_C64_SIMT && tz::dev::tc_take_error() == 1)
@@ -310,12 +314,13 @@ int tz_contract_amplitudes_device(tz_plan *plan, const uint8_t *d_bitstrings, in
   check_rows(plan, n);
   REQUIRE(plan->bound, "plan has no workspace bound");
   tz::cuda_check(cudaSetDevice(plan->opts.device), "cudaSetDevice");
-  cudaStream_t s = plan->stream;
-  tz::cuda_check(cudaMemcpyAsync(plan->ws + plan->off_bits, d_bitstrings, (size_t)(n * plan->net.n_qubits),
+  const tz::RunCtx ctx = tz::default_ctx(plan);
+  cudaStream_t s = ctx.stream;
+  tz::cuda_check(cudaMemcpyAsync(ctx.scratch + plan->s_bits, d_bitstrings, (size_t)(n * plan->net.n_qubits),
                                  cudaMemcpyDeviceToDevice, s),
                  "copy bitstrings in");
-  tz::plan_run(plan, n);
-  tz::cuda_check(cudaMemcpyAsync(d_out, plan->ws + plan->off_acc, (size_t)n * 16, cudaMemcpyDeviceToDevice, s),
+  tz::plan_run(plan, ctx, n, plan->lo, plan->hi);
+  tz::cuda_check(cudaMemcpyAsync(d_out, ctx.scratch + plan->s_acc, (size_t)n * 16, cudaMemcpyDeviceToDevice, s),
                  "copy amplitudes out");
   TZ_CATCH
 }

@@ -1,4 +1,7 @@
 // Split-precision complex products on the tcgen05 tensor cores (sm_103a).
+// Two modes share the pipeline: TF32x3 (operands split into TF32 hi + lo,
+// kind::tf32) and BF16x3 (operands split into BF16 hi + lo, kind::f16 with
+// BF16 inputs). Both accumulate in FP32 in TMEM.
 //
 // C[z] = A[z] B[z]^T in complex64, computed as one real product on the
 // interleaved (re, im) view: A is read as an m x 2k FP32 matrix and C is
@@ -22,6 +25,7 @@
 // Every wait is bounded in time; on timeout the kernel raises an error flag,
 // drains its copies in flight, frees TMEM and returns.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -134,6 +138,35 @@ __device__ __forceinline__ uint32_t split_lo(uint32_t x) {
   return __float_as_uint(__uint_as_float(x) - __uint_as_float(split_hi(x)));
 }
 
+// Round-to-nearest-even BF16 split: hi = bf16(x), lo = bf16(x - hi).
+__device__ __forceinline__ void split_bf16(float x, uint16_t &hi, uint16_t &lo) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+  hi = __bfloat16_as_ushort(h);
+  lo = __bfloat16_as_ushort(l);
+}
+
+// K-major operand in the 64-byte swizzled layout (rows of 64 bytes, 8-row
+// atoms of 512 bytes): 16-byte chunk c of row r sits at chunk c ^ ((r>>1)&3).
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
+// FP32 accumulator, BF16 A and B, both K-major, N = n_cols, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n_cols) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n_cols >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+enum TcMode { MODE_TF32 = 0, MODE_BF16 = 1 };
+
 struct TcArgs {
   float2 *C;
   int64_t M, N, K;     // complex sizes of one product
@@ -150,20 +183,26 @@ __device__ __forceinline__ int64_t scatter_bits(int64_t v, int n, const int8_t *
   return o;
 }
 
-template <int BNP, int STAGES>
+// Per stage: the FP32 A tile as loaded (128 rows x 128 B), the split A
+// (TF32: hi in place + lo tile of 16 KB; BF16: hi and lo tiles of 8 KB),
+// and the prepared B hi and lo tiles (BNP rows x 128 B TF32 / 64 B BF16).
+template <int MODE, int BNP, int STAGES>
 struct TcSmem {
-  static constexpr uint32_t A_BYTES = BM * 128;
-  static constexpr uint32_t B_BYTES = BNP * 128;
-  static constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr uint32_t A_BYTES = BM * 128;                         // FP32 tile as loaded
+  static constexpr uint32_t AS_BYTES = MODE == MODE_TF32 ? BM * 128 : BM * 64;  // one split half
+  static constexpr uint32_t B_BYTES = MODE == MODE_TF32 ? BNP * 128 : BNP * 64;
+  static constexpr uint32_t A_LO = MODE == MODE_TF32 ? A_BYTES : A_BYTES + AS_BYTES;  // offset of A lo
+  static constexpr uint32_t A_HI = MODE == MODE_TF32 ? 0 : A_BYTES;                  // offset of A hi
+  static constexpr uint32_t STAGE = A_BYTES + (MODE == MODE_TF32 ? AS_BYTES : 2 * AS_BYTES) + 2 * B_BYTES;
   static constexpr uint32_t TOTAL = STAGES * STAGE + 256 + 1024 + 1024;  // + barriers, column offsets, alignment
   static constexpr uint32_t TMEM_COLS = BNP < 32 ? 32 : BNP;
 };
 
-template <int BNP, int STAGES>
+template <int MODE, int BNP, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
-    tc_tf32x3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
+    tc_split3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
                      const __grid_constant__ CUtensorMap tmBl, TcArgs a) {
-  using L = TcSmem<BNP, STAGES>;
+  using L = TcSmem<MODE, BNP, STAGES>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * L::STAGE);
@@ -172,10 +211,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t *accf = empty + STAGES;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accf + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-  auto A_hi = [&](int s) { return smem + s * L::STAGE; };
-  auto A_lo = [&](int s) { return smem + s * L::STAGE + L::A_BYTES; };
-  auto B_hi = [&](int s) { return smem + s * L::STAGE + 2 * L::A_BYTES; };
-  auto B_lo = [&](int s) { return smem + s * L::STAGE + 2 * L::A_BYTES + L::B_BYTES; };
+  auto A_raw = [&](int s) { return smem + s * L::STAGE; };
+  auto A_hi = [&](int s) { return smem + s * L::STAGE + L::A_HI; };
+  auto A_lo = [&](int s) { return smem + s * L::STAGE + L::A_LO; };
+  auto B_hi = [&](int s) { return smem + s * L::STAGE + L::STAGE - 2 * L::B_BYTES; };
+  auto B_lo = [&](int s) { return smem + s * L::STAGE + L::STAGE - L::B_BYTES; };
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t per_batch = (int64_t)a.n_tiles_m * a.n_tiles_n;
@@ -212,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int s = kb % STAGES, round = kb / STAGES;
         if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1, abort_flag)) break;
         mbar_expect_tx(&full[s], L::A_BYTES + 2 * L::B_BYTES);
-        tma_load_2d(A_hi(s), &tmA, kb * kStageFloats, rowA, &full[s]);
+        tma_load_2d(A_raw(s), &tmA, kb * kStageFloats, rowA, &full[s]);
         tma_load_2d(B_hi(s), &tmBh, kb * kStageFloats, rowB, &full[s]);
         tma_load_2d(B_lo(s), &tmBl, kb * kStageFloats, rowB, &full[s]);
         issued++;
@@ -225,7 +265,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_tf32(BNP);
+      constexpr uint32_t idesc = MODE == MODE_TF32 ? idesc_tf32(BNP) : idesc_bf16(BNP);
+      // K per instruction: 8 TF32 or 16 BF16 values, 32 bytes either way
+      constexpr int kSteps = MODE == MODE_TF32 ? kStageFloats / 8 : kStageFloats / 16;
       for (int kb = 0; kb < a.kblocks; kb++) {
         const int s = kb % STAGES, round = kb / STAGES;
         if (!mbar_wait(&conv[s], round & 1, abort_flag)) break;
@@ -233,13 +275,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t ah = smem_u32(A_hi(s)), al = smem_u32(A_lo(s));
         const uint32_t bh = smem_u32(B_hi(s)), bl = smem_u32(B_lo(s));
 #pragma unroll
-        for (int kk = 0; kk < kStageFloats / 8; kk++) {
-          const uint32_t off = kk * 32;  // 8 TF32 values = 32 bytes along K
-          const uint64_t dah = sw128_desc(ah + off), dal = sw128_desc(al + off);
-          const uint64_t dbh = sw128_desc(bh + off), dbl = sw128_desc(bl + off);
-          umma_tf32(tmem, dah, dbh, idesc, (kb | kk) != 0);
-          umma_tf32(tmem, dah, dbl, idesc, 1);
-          umma_tf32(tmem, dal, dbh, idesc, 1);
+        for (int kk = 0; kk < kSteps; kk++) {
+          const uint32_t off = kk * 32;
+          if (MODE == MODE_TF32) {
+            const uint64_t dah = sw128_desc(ah + off), dal = sw128_desc(al + off);
+            const uint64_t dbh = sw128_desc(bh + off), dbl = sw128_desc(bl + off);
+            umma_tf32(tmem, dah, dbh, idesc, (kb | kk) != 0);
+            umma_tf32(tmem, dah, dbl, idesc, 1);
+            umma_tf32(tmem, dal, dbh, idesc, 1);
+          } else {
+            const uint64_t dah = sw64_desc(ah + off), dal = sw64_desc(al + off);
+            const uint64_t dbh = sw64_desc(bh + off), dbl = sw64_desc(bl + off);
+            umma_f16(tmem, dah, dbh, idesc, (kb | kk) != 0);
+            umma_f16(tmem, dah, dbl, idesc, 1);
+            umma_f16(tmem, dal, dbh, idesc, 1);
+          }
         }
         umma_commit(&empty[s]);
       }
@@ -250,13 +300,35 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int kb = 0; kb < a.kblocks; kb++) {
       const int s = kb % STAGES, round = kb / STAGES;
       if (!mbar_wait(&full[s], round & 1, abort_flag)) break;
-      uint4 *hi = reinterpret_cast<uint4 *>(A_hi(s));
-      uint4 *lo = reinterpret_cast<uint4 *>(A_lo(s));
+      if (MODE == MODE_TF32) {
+        // elementwise, so the swizzled layout is kept as is
+        uint4 *hi = reinterpret_cast<uint4 *>(A_hi(s));
+        uint4 *lo = reinterpret_cast<uint4 *>(A_lo(s));
 #pragma unroll 4
-      for (int i = t; i < (int)(L::A_BYTES / 16); i += 128) {
-        const uint4 v = hi[i];
-        hi[i] = make_uint4(split_hi(v.x), split_hi(v.y), split_hi(v.z), split_hi(v.w));
-        lo[i] = make_uint4(split_lo(v.x), split_lo(v.y), split_lo(v.z), split_lo(v.w));
+        for (int i = t; i < (int)(L::A_BYTES / 16); i += 128) {
+          const uint4 v = hi[i];
+          hi[i] = make_uint4(split_hi(v.x), split_hi(v.y), split_hi(v.z), split_hi(v.w));
+          lo[i] = make_uint4(split_lo(v.x), split_lo(v.y), split_lo(v.z), split_lo(v.w));
+        }
+      } else {
+        // FP32 chunk c (4 values) of row r sits at chunk c ^ (r & 7) of the
+        // 128-byte row; its 4 BF16 go to bytes 8*(c&1) of chunk
+        // (c>>1) ^ ((r>>1)&3) of the 64-byte row
+        const uint4 *raw = reinterpret_cast<const uint4 *>(A_raw(s));
+        uint8_t *hi = A_hi(s), *lo = A_lo(s);
+#pragma unroll 4
+        for (int i = t; i < BM * 8; i += 128) {
+          const int r = i >> 3, c = i & 7;
+          const uint4 v = raw[r * 8 + (c ^ (r & 7))];
+          uint16_t h[4], l[4];
+          split_bf16(__uint_as_float(v.x), h[0], l[0]);
+          split_bf16(__uint_as_float(v.y), h[1], l[1]);
+          split_bf16(__uint_as_float(v.z), h[2], l[2]);
+          split_bf16(__uint_as_float(v.w), h[3], l[3]);
+          const int o = r * 64 + (((c >> 1) ^ ((r >> 1) & 3)) << 4) + ((c & 1) << 3);
+          *reinterpret_cast<uint2 *>(hi + o) = make_uint2(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16));
+          *reinterpret_cast<uint2 *>(lo + o) = make_uint2(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16));
+        }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&conv[s]);
@@ -311,7 +383,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // B (batch x n x k complex) -> prepared real rows, hi and lo parts:
 // row 2j = (Re b, -Im b) per k, row 2j+1 = (Im b, Re b); rows >= 2n are zero.
-__global__ void prep_b_kernel(const float2 *__restrict__ B, uint32_t *__restrict__ Bh, uint32_t *__restrict__ Bl,
+template <int MODE>
+__global__ void prep_b_kernel(const float2 *__restrict__ B, void *__restrict__ Bh_, void *__restrict__ Bl_,
                               int64_t batch, int64_t N, int64_t K, int64_t sB, int NT) {
   const int64_t total = batch * NT * K;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -330,12 +403,19 @@ __global__ void prep_b_kernel(const float2 *__restrict__ B, uint32_t *__restrict
         x1 = -b.y;
       }
     }
-    const uint32_t u0 = __float_as_uint(x0), u1 = __float_as_uint(x1);
     const int64_t o = (z * NT + r) * 2 * K + 2 * k;
-    Bh[o] = split_hi(u0);
-    Bh[o + 1] = split_hi(u1);
-    Bl[o] = split_lo(u0);
-    Bl[o + 1] = split_lo(u1);
+    if (MODE == MODE_TF32) {
+      uint32_t *Bh = static_cast<uint32_t *>(Bh_), *Bl = static_cast<uint32_t *>(Bl_);
+      const uint32_t u0 = __float_as_uint(x0), u1 = __float_as_uint(x1);
+      Bh[o] = split_hi(u0);
+      Bh[o + 1] = split_hi(u1);
+      Bl[o] = split_lo(u0);
+      Bl[o + 1] = split_lo(u1);
+    } else {
+      uint16_t *Bh = static_cast<uint16_t *>(Bh_), *Bl = static_cast<uint16_t *>(Bl_);
+      split_bf16(x0, Bh[o], Bl[o]);
+      split_bf16(x1, Bh[o + 1], Bl[o + 1]);
+    }
   }
 }
 
@@ -353,17 +433,19 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D FP32 tensor map: rows x cols (cols contiguous), box = 32 x box_rows,
-// 128-byte swizzle, zero fill outside.
-bool make_map(CUtensorMap *tm, const void *base, int64_t cols, int64_t rows, int box_rows) {
+// 2D tensor map: rows x cols (cols contiguous), box = 32 x box_rows, zero
+// fill outside; FP32 with 128-byte swizzle or BF16 with 64-byte swizzle.
+bool make_map(CUtensorMap *tm, const void *base, int64_t cols, int64_t rows, int box_rows, bool bf16) {
   auto fn = encode_fn();
   if (!fn) return false;
+  const int esz = bf16 ? 2 : 4;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)(cols * 4)};
+  cuuint64_t strides[1] = {(cuuint64_t)(cols * esz)};
   cuuint32_t box[2] = {(cuuint32_t)kStageFloats, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  CUresult r = fn(tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                  const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  bf16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -377,36 +459,51 @@ int tile_cols(int64_t N) {  // real columns per tile (power of two, 16..256)
   return (int)p;
 }
 
-template <int BNP, int STAGES>
+template <int MODE, int BNP, int STAGES>
 cudaError_t run_tc(const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensorMap &tbl, const TcArgs &args,
                    int64_t n_blocks, cudaStream_t s) {
-  using L = TcSmem<BNP, STAGES>;
+  using L = TcSmem<MODE, BNP, STAGES>;
+  static_assert(L::TOTAL <= 227 * 1024, "shared memory budget");
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_tf32x3_kernel<BNP, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)L::TOTAL);
+    cudaError_t e = cudaFuncSetAttribute(tc_split3_kernel<MODE, BNP, STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::TOTAL);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  tc_tf32x3_kernel<BNP, STAGES><<<(unsigned)n_blocks, kThreads, L::TOTAL, s>>>(ta, tbh, tbl, args);
+  tc_split3_kernel<MODE, BNP, STAGES><<<(unsigned)n_blocks, kThreads, L::TOTAL, s>>>(ta, tbh, tbl, args);
   return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t dispatch(int bnp, const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensorMap &tbl,
+                     const TcArgs &args, int64_t n_blocks, cudaStream_t s) {
+  switch (bnp) {
+    case 16: return run_tc<MODE, 16, 4>(ta, tbh, tbl, args, n_blocks, s);
+    case 32: return run_tc<MODE, 32, 4>(ta, tbh, tbl, args, n_blocks, s);
+    case 64: return run_tc<MODE, 64, 4>(ta, tbh, tbl, args, n_blocks, s);
+    case 128: return run_tc<MODE, 128, 3>(ta, tbh, tbl, args, n_blocks, s);
+    default: return run_tc<MODE, 256, MODE == MODE_TF32 ? 2 : 3>(ta, tbh, tbl, args, n_blocks, s);
+  }
 }
 
 }  // namespace
 
 bool cgemm_tc_supported(int precision, int64_t M, int64_t N, int64_t K) {
-  if (precision != TZ_TF32X3) return false;
-  // M: whole 128-row tiles; K: at least 2 complex (16-byte rows for TMA);
-  // row coordinates must fit int32
-  if (M < BM || (M % BM) != 0 || K < 2 || (K % 2) != 0 || N < 1) return false;
+  if (precision != TZ_TF32X3 && precision != TZ_BF16X3) return false;
+  // M: whole 128-row tiles; K: rows of the operands a multiple of 16 bytes
+  // for TMA (2 complex in FP32, 4 complex in BF16)
+  const int64_t kmin = precision == TZ_TF32X3 ? 2 : 4;
+  if (M < BM || (M % BM) != 0 || K < kmin || (K % kmin) != 0 || N < 1) return false;
   return true;
 }
 
 size_t cgemm_tc_scratch_bytes(int precision, int64_t batch, int64_t N, int64_t K) {
-  if (precision != TZ_TF32X3) return 0;
+  if (precision != TZ_TF32X3 && precision != TZ_BF16X3) return 0;
   const int bnp = tile_cols(N);
   const int64_t nt = (2 * N + bnp - 1) / bnp;
-  return (size_t)(2 * batch * nt * bnp * 2 * K * 4);
+  const int esz = precision == TZ_TF32X3 ? 4 : 2;
+  return (size_t)(2 * batch * nt * bnp * 2 * K * esz + 256);
 }
 
 cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M,
@@ -421,18 +518,23 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
   if (rowsA >= (int64_t(1) << 31) || rowsB >= (int64_t(1) << 31) || 2 * K >= (int64_t(1) << 31))
     return cudaErrorNotSupported;
   if (scratch_bytes < cgemm_tc_scratch_bytes(precision, batch, N, K) || !scratch) return cudaErrorInvalidValue;
-  uint32_t *Bh = static_cast<uint32_t *>(scratch);
-  uint32_t *Bl = Bh + batch * NT * 2 * K;
+  const bool bf16 = precision == TZ_BF16X3;
+  const size_t half = (size_t)(batch * NT * 2 * K) * (bf16 ? 2 : 4);
+  char *Bh = static_cast<char *>(scratch);
+  char *Bl = Bh + ((half + 255) & ~size_t(255));
   {
     const int64_t total = batch * NT * K;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
-    prep_b_kernel<<<blocks, 256, 0, s>>>(B, Bh, Bl, batch, N, K, sB, NT);
+    if (bf16)
+      prep_b_kernel<MODE_BF16><<<blocks, 256, 0, s>>>(B, Bh, Bl, batch, N, K, sB, NT);
+    else
+      prep_b_kernel<MODE_TF32><<<blocks, 256, 0, s>>>(B, Bh, Bl, batch, N, K, sB, NT);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   CUtensorMap ta, tbh, tbl;
-  if (!make_map(&ta, A, 2 * K, rowsA, BM) || !make_map(&tbh, Bh, 2 * K, rowsB, bnp) ||
-      !make_map(&tbl, Bl, 2 * K, rowsB, bnp))
+  if (!make_map(&ta, A, 2 * K, rowsA, BM, false) || !make_map(&tbh, Bh, 2 * K, rowsB, bnp, bf16) ||
+      !make_map(&tbl, Bl, 2 * K, rowsB, bnp, bf16))
     return cudaErrorInvalidValue;
   TcArgs args{};
   args.C = C;
@@ -448,13 +550,8 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
   if (sc) args.sc = *sc;
   const int64_t n_blocks = batch * args.n_tiles_m * (int64_t)n_tiles_n;
   if (n_blocks >= (int64_t(1) << 31)) return cudaErrorNotSupported;
-  switch (bnp) {
-    case 16: return run_tc<16, 4>(ta, tbh, tbl, args, n_blocks, s);
-    case 32: return run_tc<32, 4>(ta, tbh, tbl, args, n_blocks, s);
-    case 64: return run_tc<64, 4>(ta, tbh, tbl, args, n_blocks, s);
-    case 128: return run_tc<128, 3>(ta, tbh, tbl, args, n_blocks, s);
-    default: return run_tc<256, 2>(ta, tbh, tbl, args, n_blocks, s);
-  }
+  return bf16 ? dispatch<MODE_BF16>(bnp, ta, tbh, tbl, args, n_blocks, s)
+              : dispatch<MODE_TF32>(bnp, ta, tbh, tbl, args, n_blocks, s);
 }
 
 int tc_take_error() {

@@ -33,8 +33,11 @@ cudaError_t launch_init_state(GroupState *gs, int64_t lo, int64_t hi, int64_t n_
 // One block per leaf job. Gather: a constant tensor with its sliced bits
 // fixed to the bits of the current slice id (Sec. 1 subtasks). Output: the
 // tensor <x_q| (final gates folded in) for the current chunk of bitstrings.
-__global__ void leaf_kernel(const LeafJob *jobs, const GroupState *gs, const uint8_t *bits, int nq, int g) {
+__global__ void leaf_kernel(const LeafJob *jobs, const GroupState *gs, const uint8_t *bits, int nq, int g,
+                            const char *cbase, char *abase) {
   const LeafJob &j = jobs[blockIdx.x];
+  float2 *dst = const_cast<float2 *>(region_ptr(j.dst, cbase, abase));
+  const float2 *src = j.kind == LJ_GATHER ? region_ptr(j.src, cbase, abase) : nullptr;
   const int64_t slice = gs->slice, chunk = gs->chunk, n_rows = gs->n_rows;
   const int64_t n = int64_t(1) << j.rank;
   for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
@@ -42,7 +45,7 @@ __global__ void leaf_kernel(const LeafJob *jobs, const GroupState *gs, const uin
       int64_t so = 0;
       for (int p = 0; p < j.rank; p++) so |= ((e >> p) & 1) << j.src_pos[p];
       for (int f = 0; f < j.n_fixed; f++) so |= ((slice >> j.fixed_slice_bit[f]) & 1) << j.fixed_src_pos[f];
-      j.dst[e] = j.src[so];
+      dst[e] = src[so];
     } else {
       int64_t beta = 0;
       for (int b = 0; b < g; b++)
@@ -56,14 +59,14 @@ __global__ void leaf_kernel(const LeafJob *jobs, const GroupState *gs, const uin
         else if (j.e_slice_bit >= 0)
           ev = (int)((slice >> j.e_slice_bit) & 1);
       }
-      j.dst[e] = j.M[x * (1 << j.rc) + ev];
+      dst[e] = j.M[x * (1 << j.rc) + ev];
     }
   }
 }
 
 cudaError_t launch_leaf_build(const LeafJob *jobs, int n_jobs, const GroupState *gs, const uint8_t *bits, int nq,
-                              int g, cudaStream_t s) {
-  leaf_kernel<<<n_jobs, 128, 0, s>>>(jobs, gs, bits, nq, g);
+                              int g, const char *cbase, char *abase, cudaStream_t s) {
+  leaf_kernel<<<n_jobs, 128, 0, s>>>(jobs, gs, bits, nq, g, cbase, abase);
   return cudaGetLastError();
 }
 
@@ -71,7 +74,8 @@ cudaError_t launch_leaf_build(const LeafJob *jobs, int n_jobs, const GroupState 
 // Each output element is summed by 2^split consecutive threads, each walking
 // its share of the contracted bits in Gray-code order (one offset update per
 // term), then reduced.
-__global__ void __launch_bounds__(256) direct_kernel(const DStep *steps, int n_steps) {
+__global__ void __launch_bounds__(256) direct_kernel(const DStep *steps, int n_steps, const char *cbase,
+                                                     char *abase) {
   __shared__ int s_idx;
   __shared__ float2 red[256];
   const int64_t blk = blockIdx.x;
@@ -88,6 +92,9 @@ __global__ void __launch_bounds__(256) direct_kernel(const DStep *steps, int n_s
   }
   __syncthreads();
   const DStep &st = steps[s_idx];
+  const float2 *__restrict__ Ap = region_ptr(st.A, cbase, abase);
+  const float2 *__restrict__ Bp = region_ptr(st.B, cbase, abase);
+  float2 *Cp = const_cast<float2 *>(region_ptr(st.C, cbase, abase));
   const int split = st.split;
   const int64_t item = (blk - st.block_begin) * 256 + threadIdx.x;
   const int64_t c = item >> split;
@@ -107,7 +114,7 @@ __global__ void __launch_bounds__(256) direct_kernel(const DStep *steps, int n_s
         oa += int64_t(1) << st.a_k[nlow + q];
         ob += int64_t(1) << st.b_k[nlow + q];
       }
-    acc = cmul(st.A[oa], st.B[ob]);
+    acc = cmul(Ap[oa], Bp[ob]);
     const int64_t nt = int64_t(1) << nlow;
     for (int64_t t = 1; t < nt; t++) {
       const int q = __ffsll(t) - 1;
@@ -115,7 +122,7 @@ __global__ void __launch_bounds__(256) direct_kernel(const DStep *steps, int n_s
       const int64_t da = int64_t(1) << st.a_k[q], db = int64_t(1) << st.b_k[q];
       oa += on ? da : -da;
       ob += on ? db : -db;
-      acc = cfma(st.A[oa], st.B[ob], acc);
+      acc = cfma(Ap[oa], Bp[ob], acc);
     }
   }
   if (split > 0) {
@@ -129,13 +136,14 @@ __global__ void __launch_bounds__(256) direct_kernel(const DStep *steps, int n_s
       }
     }
   }
-  if (active && part == 0) st.C[c] = acc;
+  if (active && part == 0) Cp[c] = acc;
 }
 
-cudaError_t launch_direct(const DStep *steps, int n_steps, int64_t total_blocks, cudaStream_t s) {
+cudaError_t launch_direct(const DStep *steps, int n_steps, int64_t total_blocks, const char *cbase, char *abase,
+                          cudaStream_t s) {
   if (n_steps <= 0) return cudaSuccess;
   if (total_blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  direct_kernel<<<(unsigned)total_blocks, 256, 0, s>>>(steps, n_steps);
+  direct_kernel<<<(unsigned)total_blocks, 256, 0, s>>>(steps, n_steps, cbase, abase);
   return cudaGetLastError();
 }
 

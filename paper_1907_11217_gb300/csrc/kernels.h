@@ -23,11 +23,19 @@ struct GroupState {
   int64_t pad[2];
 };
 
+// Device tables address tensors by region-relative byte offsets so that one
+// plan can run in several scratch arenas at once: bit 62 set = offset into
+// the per-query arena, clear = offset into the plan's resident constants.
+constexpr int64_t kArenaTag = int64_t(1) << 62;
+__host__ __device__ inline const float2 *region_ptr(int64_t off, const char *cbase, const char *abase) {
+  return reinterpret_cast<const float2 *>(((off & kArenaTag) ? abase : cbase) + (off & (kArenaTag - 1)));
+}
+
 enum LeafKind { LJ_GATHER = 0, LJ_OUTPUT = 1 };
 // One leaf tensor built per group.
 struct LeafJob {
-  float2 *dst;
-  const float2 *src;      // gather: the full constant tensor
+  int64_t dst;            // region-relative offset of the result
+  int64_t src;            // gather: the full constant tensor
   int kind, rank;         // rank: bits of dst
   int n_fixed;            // gather: sliced bits of src
   int qubit;              // output: qubit
@@ -45,9 +53,7 @@ struct LeafJob {
 // One small contraction step computed directly (no operand permute):
 // C[c] = sum_k A[offA(c,k)] * B[offB(c,k)], offsets from bit positions.
 struct DStep {
-  const float2 *A;
-  const float2 *B;
-  float2 *C;
+  int64_t A, B, C;      // region-relative offsets
   int64_t block_begin;  // first block of this step within its launch
   int nC, nK, split;    // output bits, contracted bits, log2 threads per output
   int pad0;
@@ -81,8 +87,9 @@ struct AccumArgs {
 
 cudaError_t launch_init_state(GroupState *gs, int64_t lo, int64_t hi, int64_t n_rows, cudaStream_t s);
 cudaError_t launch_leaf_build(const LeafJob *jobs, int n_jobs, const GroupState *gs, const uint8_t *bits, int nq,
-                              int g, cudaStream_t s);
-cudaError_t launch_direct(const DStep *steps, int n_steps, int64_t total_blocks, cudaStream_t s);
+                              int g, const char *cbase, char *abase, cudaStream_t s);
+cudaError_t launch_direct(const DStep *steps, int n_steps, int64_t total_blocks, const char *cbase, char *abase,
+                          cudaStream_t s);
 cudaError_t launch_permute(const float2 *in, float2 *out, const PermuteArgs &a, cudaStream_t s);
 // sc == nullptr: C row-major with batch stride sC.
 cudaError_t launch_cgemm_simt(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N,

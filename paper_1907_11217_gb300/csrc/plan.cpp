@@ -510,19 +510,23 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
   off = align256(off + sizeof(dev::DStep) * std::max<size_t>(1, p->dsteps.size()));
   p->off_jobs = off;
   off = align256(off + sizeof(dev::LeafJob) * std::max<size_t>(1, p->jobs.size()));
-  p->off_gs = off;
-  off = align256(off + sizeof(dev::GroupState));
-  p->off_bits = off;
-  off = align256(off + (size_t)p->max_rows * net.n_qubits);
-  p->off_acc = off;
-  off = align256(off + (size_t)p->max_rows * 16);
   p->off_const = off;
   p->const_bytes = (size_t)const_peak;
   off = align256(off + p->const_bytes);
-  p->off_arena = off;
+  p->resident_bytes = off;
+  p->off_scratch = off;
+  size_t so = 0;
+  p->s_gs = so;
+  so = align256(so + sizeof(dev::GroupState));
+  p->s_bits = so;
+  so = align256(so + (size_t)p->max_rows * net.n_qubits);
+  p->s_acc = so;
+  so = align256(so + (size_t)p->max_rows * 16);
+  p->s_arena = so;
   p->arena_bytes = (size_t)std::max(arena_peak, arena_const_peak);
-  off = align256(off + p->arena_bytes);
-  p->total_bytes = off;
+  so = align256(so + p->arena_bytes);
+  p->scratch_bytes = so;
+  p->total_bytes = p->resident_bytes + p->scratch_bytes;
 
   // stats
   tz_plan_stats &stt = p->stats;
@@ -553,6 +557,7 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
   stt.n_launches_per_group = (int)p->var_items.size();
   stt.workspace_bytes = p->total_bytes;
   stt.const_bytes = p->const_bytes;
+  stt.scratch_bytes = p->scratch_bytes;
   p->lo = 0;
   p->hi = int64_t(1) << sliced.size();
   return p.release();
@@ -620,10 +625,17 @@ std::string plan_describe(const tz_plan *p) {
 }
 
 // ------------------------------------------------------------------ device
-static void *tensor_ptr(const tz_plan *p, int t) {
+static void *tensor_ptr(const tz_plan *p, const RunCtx &ctx, int t) {
   const PTensor &x = p->T[t];
   if (x.region == R_CONST) return p->ws + p->off_const + x.off;
-  if (x.region == R_ARENA) return p->ws + p->off_arena + x.off;
+  if (x.region == R_ARENA) return ctx.scratch + p->s_arena + x.off;
+  fail(TZ_EINVAL, "internal: tensor has no memory");
+}
+
+static int64_t tensor_rel(const tz_plan *p, int t) {
+  const PTensor &x = p->T[t];
+  if (x.region == R_CONST) return x.off;
+  if (x.region == R_ARENA) return dev::kArenaTag | x.off;
   fail(TZ_EINVAL, "internal: tensor has no memory");
 }
 
@@ -689,9 +701,11 @@ static void item_cost(const tz_plan *p, const Item &it, int *kind, double *flops
   }
 }
 
-static void run_items(tz_plan *p, const std::vector<Item> &items) {
-  cudaStream_t s = p->stream;
-  auto *gs = reinterpret_cast<dev::GroupState *>(p->ws + p->off_gs);
+static void run_items(tz_plan *p, const std::vector<Item> &items, const RunCtx &ctx) {
+  cudaStream_t s = ctx.stream;
+  auto *gs = reinterpret_cast<dev::GroupState *>(ctx.scratch + p->s_gs);
+  const char *cbase = p->ws + p->off_const;
+  char *abase = ctx.scratch + p->s_arena;
   const bool prof = p->profiling && !p->capturing;
   for (const Item &it : items) {
     tz_plan::Pending pend{};
@@ -706,13 +720,13 @@ static void run_items(tz_plan *p, const std::vector<Item> &items) {
         if (!p->jobs.empty())
           cuda_check(dev::launch_leaf_build(reinterpret_cast<const dev::LeafJob *>(p->ws + p->off_jobs),
                                             (int)p->jobs.size(), gs,
-                                            reinterpret_cast<const uint8_t *>(p->ws + p->off_bits),
-                                            p->net.n_qubits, p->net.batch_log2, s),
+                                            reinterpret_cast<const uint8_t *>(ctx.scratch + p->s_bits),
+                                            p->net.n_qubits, p->net.batch_log2, cbase, abase, s),
                      "leaf build");
         break;
       case IT_DIRECT:
         cuda_check(dev::launch_direct(reinterpret_cast<const dev::DStep *>(p->ws + p->off_dsteps) + it.first,
-                                      it.count, it.blocks, s),
+                                      it.count, it.blocks, cbase, abase, s),
                    "direct steps");
         break;
       case IT_PERMUTE: {
@@ -720,18 +734,19 @@ static void run_items(tz_plan *p, const std::vector<Item> &items) {
         const PTensor &src = p->T[it.a], &dst = p->T[it.b];
         a.rank = (int)dst.lay.size();
         for (int q = 0; q < a.rank; q++) a.perm[q] = (int8_t)pos_of(src.lay, dst.lay[q]);
-        cuda_check(dev::launch_permute((const float2 *)tensor_ptr(p, it.a), (float2 *)tensor_ptr(p, it.b), a, s),
+        cuda_check(dev::launch_permute((const float2 *)tensor_ptr(p, ctx, it.a), (float2 *)tensor_ptr(p, ctx, it.b), a,
+                                       s),
                    "permute");
         break;
       }
       case IT_GEMM: {
         const PStep &ps = p->S[it.a];
-        const float2 *X = (const float2 *)tensor_ptr(p, ps.opX);
-        const float2 *Y = (const float2 *)tensor_ptr(p, ps.opY);
-        float2 *C = (float2 *)tensor_ptr(p, ps.c);
+        const float2 *X = (const float2 *)tensor_ptr(p, ctx, ps.opX);
+        const float2 *Y = (const float2 *)tensor_ptr(p, ctx, ps.opY);
+        float2 *C = (float2 *)tensor_ptr(p, ctx, ps.c);
         const dev::CScatter *sc = ps.row_major ? nullptr : &ps.scatter;
         if (ps.tc) {
-          void *scr = p->ws + p->off_arena + ps.tc_scratch_off;
+          void *scr = abase + ps.tc_scratch_off;
           cuda_check(dev::launch_cgemm_tc(p->opts.precision, X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.M * ps.K,
                                           ps.N * ps.K, ps.M * ps.N, sc, scr, (size_t)ps.tc_scratch, s),
                      "tensor-core gemm");
@@ -744,8 +759,8 @@ static void run_items(tz_plan *p, const std::vector<Item> &items) {
       }
       case IT_ACCUM: {
         dev::AccumArgs a{};
-        a.root = (const float2 *)tensor_ptr(p, p->root);
-        a.acc = reinterpret_cast<double2 *>(p->ws + p->off_acc);
+        a.root = (const float2 *)tensor_ptr(p, ctx, p->root);
+        a.acc = reinterpret_cast<double2 *>(ctx.scratch + p->s_acc);
         a.gs = gs;
         a.g = p->net.batch_log2;
         for (int j = 0; j < dev::kMaxBatch; j++) a.beta_pos[j] = -1;
@@ -789,14 +804,14 @@ void plan_bind(tz_plan *p, void *ws, size_t bytes) {
   // tables with resolved pointers
   std::vector<dev::DStep> ds = p->dsteps;
   for (size_t d = 0; d < ds.size(); d++) {
-    ds[d].A = (const float2 *)tensor_ptr(p, p->dstep_tensors[3 * d]);
-    ds[d].B = (const float2 *)tensor_ptr(p, p->dstep_tensors[3 * d + 1]);
-    ds[d].C = (float2 *)tensor_ptr(p, p->dstep_tensors[3 * d + 2]);
+    ds[d].A = tensor_rel(p, p->dstep_tensors[3 * d]);
+    ds[d].B = tensor_rel(p, p->dstep_tensors[3 * d + 1]);
+    ds[d].C = tensor_rel(p, p->dstep_tensors[3 * d + 2]);
   }
   std::vector<dev::LeafJob> js = p->jobs;
   for (size_t j = 0; j < js.size(); j++) {
-    js[j].dst = (float2 *)tensor_ptr(p, p->job_tensors[2 * j]);
-    js[j].src = p->job_tensors[2 * j + 1] >= 0 ? (const float2 *)tensor_ptr(p, p->job_tensors[2 * j + 1]) : nullptr;
+    js[j].dst = tensor_rel(p, p->job_tensors[2 * j]);
+    js[j].src = p->job_tensors[2 * j + 1] >= 0 ? tensor_rel(p, p->job_tensors[2 * j + 1]) : 0;
   }
   if (!ds.empty())
     cuda_check(cudaMemcpyAsync(p->ws + p->off_dsteps, ds.data(), ds.size() * sizeof(dev::DStep),
@@ -821,32 +836,33 @@ void plan_bind(tz_plan *p, void *ws, size_t bytes) {
       for (size_t q = 0; q < x.lay.size(); q++) so |= ((e >> q) & 1) << srcpos[q];
       host[e] = make_float2((float)lf.data[so].real(), (float)lf.data[so].imag());
     }
-    cuda_check(cudaMemcpyAsync(tensor_ptr(p, (int)t), host.data(), host.size() * sizeof(float2),
+    cuda_check(cudaMemcpyAsync(tensor_ptr(p, default_ctx(p), (int)t), host.data(), host.size() * sizeof(float2),
                                cudaMemcpyHostToDevice, s),
                "upload constants");
     cuda_check(cudaStreamSynchronize(s), "sync");  // host buffer is reused
   }
-  run_items(p, p->const_items);
+  run_items(p, p->const_items, default_ctx(p));
   cuda_check(cudaStreamSynchronize(s), "bind-time steps");
   p->bound = true;
 }
 
-void plan_run(tz_plan *p, int64_t n_rows) {
+void plan_run(tz_plan *p, const RunCtx &ctx, int64_t n_rows, int64_t lo, int64_t hi) {
   if (!p->bound) fail(TZ_EINVAL, "plan has no workspace bound (tz_plan_bind_workspace)");
   cuda_check(cudaSetDevice(p->opts.device), "cudaSetDevice");
-  cudaStream_t s = p->stream;
-  auto *gs = reinterpret_cast<dev::GroupState *>(p->ws + p->off_gs);
-  cuda_check(cudaMemsetAsync(p->ws + p->off_acc, 0, (size_t)n_rows * 16, s), "clear accumulator");
-  cuda_check(dev::launch_init_state(gs, p->lo, p->hi, n_rows, s), "init group state");
+  cudaStream_t s = ctx.stream;
+  auto *gs = reinterpret_cast<dev::GroupState *>(ctx.scratch + p->s_gs);
+  cuda_check(cudaMemsetAsync(ctx.scratch + p->s_acc, 0, (size_t)n_rows * 16, s), "clear accumulator");
+  cuda_check(dev::launch_init_state(gs, lo, hi, n_rows, s), "init group state");
   const int64_t chunk = int64_t(1) << p->net.batch_log2;
   const int64_t n_chunks = (n_rows + chunk - 1) / chunk;
-  const int64_t n_groups = n_chunks * (p->hi - p->lo);
-  const bool graph = p->opts.use_graph && s != nullptr && !p->profiling;
+  const int64_t n_groups = n_chunks * (hi - lo);
+  const bool own = ctx.scratch == p->ws + p->off_scratch && ctx.stream == p->stream;
+  const bool graph = own && p->opts.use_graph && s != nullptr && !p->profiling;
   if (graph && !p->graph_exec) {
     cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
     p->capturing = true;
     try {
-      run_items(p, p->var_items);
+      run_items(p, p->var_items, ctx);
     } catch (...) {
       p->capturing = false;
       cudaGraph_t g2 = nullptr;
@@ -862,7 +878,7 @@ void plan_run(tz_plan *p, int64_t n_rows) {
     if (graph)
       cuda_check(cudaGraphLaunch(p->graph_exec, s), "graph launch");
     else
-      run_items(p, p->var_items);
+      run_items(p, p->var_items, ctx);
   }
 }
 

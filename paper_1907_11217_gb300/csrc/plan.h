@@ -62,9 +62,12 @@ struct tz_plan {
   std::vector<int> job_tensors;    // 2 per job (dst, src or -1)
   int root = -1;
   int64_t max_rows = 0;
-  // workspace layout (bytes)
-  size_t off_dsteps = 0, off_jobs = 0, off_gs = 0, off_bits = 0, off_acc = 0, off_const = 0, off_arena = 0;
-  size_t const_bytes = 0, arena_bytes = 0, total_bytes = 0;
+  // workspace layout (bytes): resident part [step tables | leaf tables |
+  // constants], then one scratch part [group state | bitstrings | FP64
+  // accumulator | group arena]; a query can also run in another scratch part
+  size_t off_dsteps = 0, off_jobs = 0, off_const = 0, off_scratch = 0;
+  size_t s_gs = 0, s_bits = 0, s_acc = 0, s_arena = 0;  // offsets within a scratch part
+  size_t const_bytes = 0, arena_bytes = 0, resident_bytes = 0, scratch_bytes = 0, total_bytes = 0;
   // device state
   char *ws = nullptr;
   size_t ws_bytes = 0;
@@ -88,11 +91,19 @@ struct tz_plan {
 };
 
 namespace tz {
+// Where one query of a plan runs: a scratch part and a stream.
+struct RunCtx {
+  char *scratch;
+  cudaStream_t stream;
+};
+inline RunCtx default_ctx(const tz_plan *p) { return RunCtx{p->ws + p->off_scratch, p->stream}; }
 tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<int> &sliced, const tz_plan_opts &o);
 void plan_bind(tz_plan *p, void *ws, size_t bytes);
-// Contract all groups for n rows already in the plan's bitstring buffer;
-// leaves the FP64 sums in the plan's accumulator (asynchronous).
-void plan_run(tz_plan *p, int64_t n_rows);
+// Contract all groups of the slice range [lo, hi) for n rows already in the
+// scratch part's bitstring buffer; leaves the FP64 sums in its accumulator
+// (asynchronous on ctx.stream). The plan's own scratch part may replay a
+// captured graph; other scratch parts launch directly.
+void plan_run(tz_plan *p, const RunCtx &ctx, int64_t n_rows, int64_t lo, int64_t hi);
 void plan_destroy(tz_plan *p);
 void plan_profile_collect(tz_plan *p);
 std::string plan_describe(const tz_plan *p);

@@ -1,13 +1,320 @@
-// Amplitude server: placeholder until the request loop lands.
+// Amplitude server: a request loop over resident plans (Sec. 2: many
+// amplitudes per run; here queries arrive over time).
+//
+// Plans stay bound to their workspaces (tables and constants resident); each
+// admitted query gets its own scratch part carved from the caller's arena and
+// its own stream, so queries that arrive while others run are admitted as
+// soon as a slot and enough arena are free, and their launches overlap on the
+// device. A worker thread admits queued queries (first fit, in arrival order)
+// and retires finished ones; results wait in pinned host memory until polled.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+
 #include "plan.h"
 
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+enum QState { Q_QUEUED = 0, Q_RUNNING = 1, Q_DONE = 2, Q_FAILED = 3 };
+
+struct Query {
+  uint64_t ticket = 0;
+  tz_plan *plan = nullptr;
+  std::vector<uint8_t> bits;
+  int64_t n = 0;
+  std::vector<double> out;
+  int state = Q_QUEUED;
+  int slot = -1;
+  int64_t arena_off = -1;
+  size_t bytes = 0;
+  int err = TZ_OK;
+  std::string msg;
+  Clock::time_point t_submit, t_done;
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  uint8_t *pin_in = nullptr;
+  double *pin_out = nullptr;
+  size_t cap_in = 0, cap_out = 0;
+  uint64_t ticket = 0;  // query running here, 0 = free
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct tz_server {
+  tz_server_opts opts{};
+  std::vector<Slot> slots;
+  std::map<uint64_t, Query> queries;
+  std::deque<uint64_t> queue;
+  std::vector<std::pair<int64_t, int64_t>> used;  // arena intervals (offset, size)
+  size_t in_use = 0;
+  uint64_t next_ticket = 1;
+  std::vector<double> latencies;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  std::thread worker;
+  std::string fatal;
+
+  // first fit in the arena; -1 if no room
+  int64_t arena_alloc(size_t bytes) {
+    if (in_use + bytes > opts.hbm_budget) return -1;
+    std::sort(used.begin(), used.end());
+    int64_t cur = 0;
+    for (auto &u : used) {
+      if (u.first - cur >= (int64_t)bytes) break;
+      cur = std::max(cur, u.first + u.second);
+    }
+    if (cur + (int64_t)bytes > (int64_t)opts.arena_bytes) return -1;
+    used.push_back({cur, (int64_t)bytes});
+    in_use += bytes;
+    return cur;
+  }
+  void arena_free(int64_t off) {
+    for (size_t i = 0; i < used.size(); i++)
+      if (used[i].first == off) {
+        in_use -= (size_t)used[i].second;
+        used.erase(used.begin() + i);
+        return;
+      }
+  }
+
+  void ensure_pinned(Slot &sl, size_t in, size_t out) {
+    if (sl.cap_in < in) {
+      if (sl.pin_in) cudaFreeHost(sl.pin_in);
+      tz::cuda_check(cudaMallocHost(&sl.pin_in, in), "pinned staging");
+      sl.cap_in = in;
+    }
+    if (sl.cap_out < out) {
+      if (sl.pin_out) cudaFreeHost(sl.pin_out);
+      tz::cuda_check(cudaMallocHost(reinterpret_cast<void **>(&sl.pin_out), out), "pinned staging");
+      sl.cap_out = out;
+    }
+  }
+
+  // Launch query q on slot s (called with the lock held).
+  void start(Query &q, int s) {
+    Slot &sl = slots[s];
+    tz_plan *p = q.plan;
+    const int nq = p->net.n_qubits;
+    ensure_pinned(sl, (size_t)q.n * nq, (size_t)q.n * 16);
+    std::memcpy(sl.pin_in, q.bits.data(), (size_t)q.n * nq);
+    char *scratch = static_cast<char *>(opts.arena) + q.arena_off;
+    tz::RunCtx ctx{scratch, sl.stream};
+    tz::cuda_check(cudaMemcpyAsync(scratch + p->s_bits, sl.pin_in, (size_t)q.n * nq, cudaMemcpyHostToDevice,
+                                   sl.stream),
+                   "query bitstrings in");
+    tz::plan_run(p, ctx, q.n, p->lo, p->hi);
+    tz::cuda_check(cudaMemcpyAsync(sl.pin_out, scratch + p->s_acc, (size_t)q.n * 16, cudaMemcpyDeviceToHost,
+                                   sl.stream),
+                   "query amplitudes out");
+    tz::cuda_check(cudaEventRecord(sl.done, sl.stream), "query event");
+    sl.ticket = q.ticket;
+    q.slot = s;
+    q.state = Q_RUNNING;
+  }
+
+  void step() {  // one pass of retire + admit, lock held
+    for (size_t s = 0; s < slots.size(); s++) {
+      Slot &sl = slots[s];
+      if (!sl.ticket) continue;
+      cudaError_t e = cudaEventQuery(sl.done);
+      if (e == cudaErrorNotReady) continue;
+      Query &q = queries[sl.ticket];
+      if (e == cudaSuccess) {
+        q.out.assign(sl.pin_out, sl.pin_out + 2 * q.n);
+        q.state = Q_DONE;
+      } else {
+        q.state = Q_FAILED;
+        q.err = TZ_ECUDA;
+        q.msg = cudaGetErrorString(e);
+      }
+      q.t_done = Clock::now();
+      latencies.push_back(std::chrono::duration<double>(q.t_done - q.t_submit).count());
+      arena_free(q.arena_off);
+      sl.ticket = 0;
+    }
+    for (auto it = queue.begin(); it != queue.end();) {
+      int free_slot = -1;
+      for (size_t s = 0; s < slots.size(); s++)
+        if (!slots[s].ticket) {
+          free_slot = (int)s;
+          break;
+        }
+      if (free_slot < 0) break;
+      Query &q = queries[*it];
+      int64_t off = arena_alloc(q.bytes);
+      if (off < 0) {
+        ++it;  // does not fit yet: later, smaller queries may
+        continue;
+      }
+      q.arena_off = off;
+      try {
+        start(q, free_slot);
+      } catch (const tz::Error &e) {
+        arena_free(off);
+        q.state = Q_FAILED;
+        q.err = e.code;
+        q.msg = e.what();
+      }
+      it = queue.erase(it);
+    }
+  }
+
+  void loop() {
+    cudaSetDevice(opts.device);
+    std::unique_lock<std::mutex> lk(mu);
+    while (!stop) {
+      step();
+      bool busy = !queue.empty();
+      for (auto &sl : slots) busy |= sl.ticket != 0;
+      cv.wait_for(lk, busy ? std::chrono::microseconds(20) : std::chrono::milliseconds(2));
+    }
+  }
+};
+
+#define SRV_TRY try {
+#define SRV_CATCH                                \
+  }                                              \
+  catch (const tz::Error &e) {                   \
+    tz_set_error_message(e.what());              \
+    return e.code;                               \
+  }                                              \
+  catch (const std::exception &e) {              \
+    tz_set_error_message(e.what());              \
+    return TZ_EINVAL;                            \
+  }                                              \
+  return TZ_OK;
+
+void tz_set_error_message(const std::string &m);  // api.cpp
+
 extern "C" {
-int tz_server_create(const tz_server_opts *, tz_server **out) {
-  if (out) *out = nullptr;
-  return TZ_EUNSUPPORTED;
+
+int tz_server_create(const tz_server_opts *o, tz_server **out) {
+  SRV_TRY
+  if (!o || !out) tz::fail(TZ_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (o->max_inflight < 1 || o->max_inflight > 32) tz::fail(TZ_EINVAL, "max_inflight must be in 1..32");
+  if (!o->arena || o->arena_bytes == 0) tz::fail(TZ_EINVAL, "server needs a device arena");
+  if ((reinterpret_cast<uintptr_t>(o->arena) & 255) != 0) tz::fail(TZ_EINVAL, "arena must be 256-byte aligned");
+  auto srv = std::make_unique<tz_server>();
+  srv->opts = *o;
+  if (srv->opts.hbm_budget == 0 || srv->opts.hbm_budget > o->arena_bytes) srv->opts.hbm_budget = o->arena_bytes;
+  tz::cuda_check(cudaSetDevice(o->device), "cudaSetDevice");
+  srv->slots.resize(o->max_inflight);
+  for (auto &sl : srv->slots) {
+    tz::cuda_check(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking), "server stream");
+    tz::cuda_check(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming), "server event");
+  }
+  tz_server *raw = srv.get();
+  srv->worker = std::thread([raw] { raw->loop(); });
+  *out = srv.release();
+  SRV_CATCH
 }
-int tz_server_submit(tz_server *, tz_plan *, const uint8_t *, int64_t, uint64_t *) { return TZ_EUNSUPPORTED; }
-int tz_server_poll(tz_server *, uint64_t, double *, int *) { return TZ_EUNSUPPORTED; }
-int tz_server_latency(tz_server *, double *, double *, int64_t *) { return TZ_EUNSUPPORTED; }
-void tz_server_destroy(tz_server *) {}
+
+int tz_server_submit(tz_server *srv, tz_plan *plan, const uint8_t *bitstrings, int64_t n, uint64_t *ticket) {
+  SRV_TRY
+  if (!srv || !plan || !bitstrings || !ticket) tz::fail(TZ_EINVAL, "NULL argument");
+  if (!plan->bound) tz::fail(TZ_EINVAL, "plan has no workspace bound");
+  if (plan->opts.device != srv->opts.device) tz::fail(TZ_EINVAL, "plan and server are on different devices");
+  if (n < 1 || n > plan->max_rows) tz::fail(TZ_EINVAL, "bitstring count outside 1..max_bitstrings of the plan");
+  const int nq = plan->net.n_qubits;
+  for (int64_t i = 0; i < n * nq; i++)
+    if (bitstrings[i] > 1) tz::fail(TZ_EINVAL, "bitstring bytes must be 0 or 1");
+  const size_t bytes = align256(plan->scratch_bytes);
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (bytes > srv->opts.hbm_budget)
+    tz::fail(TZ_EHBM_ADMIT, "query scratch (" + std::to_string(bytes) + " B) exceeds the server budget");
+  if (!srv->opts.wait_admit) {
+    // admit now or refuse
+    bool slot_free = false;
+    for (auto &sl : srv->slots) slot_free |= sl.ticket == 0;
+    if (!slot_free || srv->in_use + bytes > srv->opts.hbm_budget || !srv->queue.empty())
+      tz::fail(TZ_EHBM_ADMIT, "query does not fit now (slots or budget in use)");
+  }
+  Query q;
+  q.ticket = srv->next_ticket++;
+  q.plan = plan;
+  q.bits.assign(bitstrings, bitstrings + n * nq);
+  q.n = n;
+  q.bytes = bytes;
+  q.t_submit = Clock::now();
+  *ticket = q.ticket;
+  srv->queries[q.ticket] = std::move(q);
+  srv->queue.push_back(*ticket);
+  srv->step();
+  srv->cv.notify_one();
+  SRV_CATCH
 }
+
+int tz_server_poll(tz_server *srv, uint64_t ticket, double *out, int *done) {
+  SRV_TRY
+  if (!srv || !out || !done) tz::fail(TZ_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  srv->step();
+  auto it = srv->queries.find(ticket);
+  if (it == srv->queries.end()) tz::fail(TZ_EINVAL, "unknown ticket");
+  Query &q = it->second;
+  *done = 0;
+  if (q.state == Q_DONE) {
+    std::memcpy(out, q.out.data(), q.out.size() * sizeof(double));
+    *done = 1;
+    srv->queries.erase(it);
+  } else if (q.state == Q_FAILED) {
+    int code = q.err;
+    std::string m = q.msg;
+    srv->queries.erase(it);
+    tz::fail(code, "query failed: " + m);
+  }
+  SRV_CATCH
+}
+
+int tz_server_latency(tz_server *srv, double *p50, double *p99, int64_t *n_done) {
+  SRV_TRY
+  if (!srv || !p50 || !p99 || !n_done) tz::fail(TZ_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  std::vector<double> v = srv->latencies;
+  *n_done = (int64_t)v.size();
+  *p50 = *p99 = 0;
+  if (!v.empty()) {
+    std::sort(v.begin(), v.end());
+    *p50 = v[(size_t)(0.50 * (v.size() - 1) + 0.5)];
+    *p99 = v[(size_t)(0.99 * (v.size() - 1) + 0.5)];
+  }
+  SRV_CATCH
+}
+
+void tz_server_destroy(tz_server *srv) {
+  if (!srv) return;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->stop = true;
+  }
+  srv->cv.notify_all();
+  if (srv->worker.joinable()) srv->worker.join();
+  cudaSetDevice(srv->opts.device);
+  for (auto &sl : srv->slots) {
+    if (sl.stream) {
+      cudaStreamSynchronize(sl.stream);
+      cudaStreamDestroy(sl.stream);
+    }
+    if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.pin_in) cudaFreeHost(sl.pin_in);
+    if (sl.pin_out) cudaFreeHost(sl.pin_out);
+  }
+  delete srv;
+}
+
+}  // extern "C"
