@@ -294,6 +294,24 @@ int tz_op_cgemm(int precision, int64_t batch, int64_t m, int64_t n, int64_t k,
                 void *scratch, size_t scratch_bytes, void *stream);
 int tz_op_cgemm_scratch_bytes(int precision, int64_t batch, int64_t m, int64_t n, int64_t k, size_t *bytes);
 
+/* Allocation-free variant of tz_op_cgemm for the split-precision modes
+ * (TZ_TF32X3, TZ_BF16X3). The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc (they hand all device memory
+ * to another allocator, or must not pay for or fail in an allocation in a
+ * latency-critical loop). The same arguments as tz_op_cgemm, without the
+ * scratch buffer: the prepared copy of B goes to a 16 MiB array in device
+ * global memory owned by the library, which every GPU that loads the library
+ * holds until the process exits. Products needing more scratch than that
+ * (tz_op_cgemm_scratch_bytes) return TZ_EINVAL. The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture. All calls
+ * share the array: calls that overlap on the GPU race on it and must be
+ * serialised by the caller. The array keeps the last call's contents;
+ * every call rewrites all of it that it reads. Allocates no device memory. */
+int tz_op_cgemm_static(int precision, int64_t batch, int64_t m, int64_t n, int64_t k,
+                       const void *A, int64_t sa, const void *B, int64_t sb, void *C, int64_t sc,
+                       void *stream);
+
 /* FP64 accumulation of partial amplitudes: acc[j] += scale * part[j] for
  * j < n, with part complex64 and acc, scale complex128 (re, im). */
 int tz_op_accumulate(const void *part, double *acc, int64_t n, double scale_re, double scale_im, void *stream);

@@ -112,6 +112,7 @@ SIGNATURES = {
                             c_size_t, P]),
     "tz_op_cgemm_scratch_bytes": (c_int, [c_int, c_int64, c_int64, c_int64, c_int64, ctypes.POINTER(c_size_t)]),
     "tz_op_accumulate": (c_int, [P, F64P, c_int64, c_double, c_double, P]),
+    "tz_op_cgemm_static": (c_int, [c_int, c_int64, c_int64, c_int64, c_int64, P, c_int64, P, c_int64, P, c_int64, P]),
 }
 
 _lib = None
