@@ -103,6 +103,67 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   }
 }
 
+// Skinny products (n <= NMAX complex columns, k <= KMAX): memory-bound, so
+// one thread streams one row of A (k contiguous complex values, 16-byte
+// loads) against B held in shared memory and writes its n results.
+template <int NMAX, int KMAX>
+__global__ void __launch_bounds__(256)
+    cgemm_skinny_kernel(const float2 *__restrict__ A, const float2 *__restrict__ B, float2 *__restrict__ C,
+                        int64_t batch, int64_t M, int N, int K, int64_t sA, int64_t sB, int64_t sC,
+                        const __grid_constant__ CScatter sc, int scatter) {
+  __shared__ float2 Bs[NMAX * KMAX];
+  const int64_t rows_per_batch_blocks = (M + 255) / 256;
+  for (int64_t blk = blockIdx.x; blk < rows_per_batch_blocks * batch; blk += gridDim.x) {
+    const int64_t z = blk / rows_per_batch_blocks;
+    const int64_t m = (blk - z * rows_per_batch_blocks) * 256 + threadIdx.x;
+    __syncthreads();
+    for (int i = threadIdx.x; i < N * K; i += 256) Bs[i] = B[z * sB + i];
+    __syncthreads();
+    if (m >= M) continue;
+    float2 a[KMAX];
+    const float2 *arow = A + z * sA + m * K;
+    if ((K & 1) == 0) {
+#pragma unroll
+      for (int k = 0; k < KMAX; k += 2)
+        if (k < K) {
+          const float4 v = *reinterpret_cast<const float4 *>(arow + k);
+          a[k] = make_float2(v.x, v.y);
+          a[k + 1] = make_float2(v.z, v.w);
+        }
+    } else {
+#pragma unroll
+      for (int k = 0; k < KMAX; k++)
+        if (k < K) a[k] = arow[k];
+    }
+    const int64_t om = scatter ? scatter_bits(z, sc.nb, sc.pb) + scatter_bits(m, sc.nm, sc.pm) : z * sC + m * N;
+#pragma unroll
+    for (int n = 0; n < NMAX; n++) {
+      if (n >= N) break;
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < KMAX; k++)
+        if (k < K) {
+          const float2 b = Bs[n * K + k];
+          acc.x = fmaf(a[k].x, b.x, acc.x);
+          acc.x = fmaf(-a[k].y, b.y, acc.x);
+          acc.y = fmaf(a[k].x, b.y, acc.y);
+          acc.y = fmaf(a[k].y, b.x, acc.y);
+        }
+      C[om + (scatter ? scatter_bits(n, sc.nn, sc.pn) : n)] = acc;
+    }
+  }
+}
+
+template <int NMAX, int KMAX>
+cudaError_t run_skinny(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N, int64_t K,
+                       int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s) {
+  const int64_t blocks = ((M + 255) / 256) * batch;
+  CScatter none{};
+  cgemm_skinny_kernel<NMAX, KMAX><<<(unsigned)std::min<int64_t>(blocks, 152 * 16), 256, 0, s>>>(
+      A, B, C, batch, M, (int)N, (int)K, sA, sB, sC, sc ? *sc : none, sc ? 1 : 0);
+  return cudaGetLastError();
+}
+
 template <int BM, int BN, int TM, int TN, int BK>
 cudaError_t run(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N, int64_t K,
                 int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s) {
@@ -119,6 +180,10 @@ cudaError_t run(const float2 *A, const float2 *B, float2 *C, int64_t batch, int6
 cudaError_t launch_cgemm_simt(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N,
                               int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s) {
   if (batch <= 0 || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
+  if (N <= 4 && K <= 16 && M >= 256) {
+    if (K <= 4) return run_skinny<4, 4>(A, B, C, batch, M, N, K, sA, sB, sC, sc, s);
+    return run_skinny<4, 16>(A, B, C, batch, M, N, K, sA, sB, sC, sc, s);
+  }
   if (N >= 48) return run<64, 64, 4, 4, 8>(A, B, C, batch, M, N, K, sA, sB, sC, sc, s);
   if (N >= 12) return run<128, 16, 4, 2, 8>(A, B, C, batch, M, N, K, sA, sB, sC, sc, s);
   if (N >= 3) return run<256, 4, 4, 1, 8>(A, B, C, batch, M, N, K, sA, sB, sC, sc, s);

@@ -40,7 +40,7 @@ namespace {
 
 constexpr int BM = 128;           // C rows per tile = TMEM lanes
 constexpr int kStageFloats = 32;  // K (real) per stage: one 128-byte swizzle row
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;  // TMA, MMA, 4 split warps, 4 epilogue warps
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 __device__ int g_tc_error;
@@ -169,6 +169,7 @@ enum TcMode { MODE_TF32 = 0, MODE_BF16 = 1 };
 
 struct TcArgs {
   float2 *C;
+  int64_t batch;
   int64_t M, N, K;     // complex sizes of one product
   int64_t sC;          // complex elements between batches of C
   int n_tiles_m, n_tiles_n, kblocks;
@@ -186,6 +187,8 @@ __device__ __forceinline__ int64_t scatter_bits(int64_t v, int n, const int8_t *
 // Per stage: the FP32 A tile as loaded (128 rows x 128 B), the split A
 // (TF32: hi in place + lo tile of 16 KB; BF16: hi and lo tiles of 8 KB),
 // and the prepared B hi and lo tiles (BNP rows x 128 B TF32 / 64 B BF16).
+// TMEM holds two accumulators (BNP columns each, at least 32) so the
+// epilogue of one tile overlaps the products of the next.
 template <int MODE, int BNP, int STAGES>
 struct TcSmem {
   static constexpr uint32_t A_BYTES = BM * 128;                         // FP32 tile as loaded
@@ -194,10 +197,16 @@ struct TcSmem {
   static constexpr uint32_t A_LO = MODE == MODE_TF32 ? A_BYTES : A_BYTES + AS_BYTES;  // offset of A lo
   static constexpr uint32_t A_HI = MODE == MODE_TF32 ? 0 : A_BYTES;                  // offset of A hi
   static constexpr uint32_t STAGE = A_BYTES + (MODE == MODE_TF32 ? AS_BYTES : 2 * AS_BYTES) + 2 * B_BYTES;
-  static constexpr uint32_t TOTAL = STAGES * STAGE + 256 + 1024 + 1024;  // + barriers, column offsets, alignment
-  static constexpr uint32_t TMEM_COLS = BNP < 32 ? 32 : BNP;
+  static constexpr uint32_t BARS = 512;                                // barriers and flags
+  static constexpr uint32_t TOTAL = STAGES * STAGE + BARS + 1024 + 1024;  // + column offsets, alignment
+  static constexpr uint32_t ACC_COLS = BNP < 32 ? 32 : BNP;
+  static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
 };
 
+// Persistent: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// (batch-major, then row tile, then column tile, so CTAs working at the same
+// time share A tiles in L2). The stage ring and the accumulator ring run on
+// across tiles.
 template <int MODE, int BNP, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_split3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
@@ -208,9 +217,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * L::STAGE);
   uint64_t *conv = full + STAGES;
   uint64_t *empty = conv + STAGES;
-  uint64_t *accf = empty + STAGES;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accf + 1);
+  uint64_t *tfull = empty + STAGES;  // [2] accumulator ready for the epilogue
+  uint64_t *tempty = tfull + 2;      // [2] accumulator drained by the epilogue
+  uint64_t *drain = tempty + 2;      // all products retired
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  int64_t *coloff = reinterpret_cast<int64_t *>(smem + STAGES * L::STAGE + L::BARS);
   auto A_raw = [&](int s) { return smem + s * L::STAGE; };
   auto A_hi = [&](int s) { return smem + s * L::STAGE + L::A_HI; };
   auto A_lo = [&](int s) { return smem + s * L::STAGE + L::A_LO; };
@@ -219,11 +231,21 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t per_batch = (int64_t)a.n_tiles_m * a.n_tiles_n;
-  const int64_t z = blockIdx.x / per_batch;
-  const int64_t rem = blockIdx.x - z * per_batch;
-  const int mt = (int)(rem / a.n_tiles_n), nt = (int)(rem % a.n_tiles_n);
-  const int rowA = (int)(z * a.M + (int64_t)mt * BM);
-  const int rowB = (int)(z * a.NT + (int64_t)nt * BNP);
+  const int64_t n_tiles = per_batch * a.batch;
+  struct Tile {
+    int64_t z;
+    int mt, nt, rowA, rowB;
+  };
+  auto decode = [&](int64_t t) {
+    Tile d;
+    d.z = t / per_batch;
+    const int64_t rem = t - d.z * per_batch;
+    d.mt = (int)(rem / a.n_tiles_n);
+    d.nt = (int)(rem % a.n_tiles_n);
+    d.rowA = (int)(d.z * a.M + (int64_t)d.mt * BM);
+    d.rowB = (int)(d.z * a.NT + (int64_t)d.nt * BNP);
+    return d;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; s++) {
@@ -231,7 +253,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&conv[s], 128);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accf, 1);
+    for (int b = 0; b < 2; b++) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 128);
+    }
+    mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -247,20 +273,27 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      int issued = 0;
-      for (int kb = 0; kb < a.kblocks; kb++) {
-        const int s = kb % STAGES, round = kb / STAGES;
-        if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1, abort_flag)) break;
-        mbar_expect_tx(&full[s], L::A_BYTES + 2 * L::B_BYTES);
-        tma_load_2d(A_raw(s), &tmA, kb * kStageFloats, rowA, &full[s]);
-        tma_load_2d(B_hi(s), &tmBh, kb * kStageFloats, rowB, &full[s]);
-        tma_load_2d(B_lo(s), &tmBl, kb * kStageFloats, rowB, &full[s]);
-        issued++;
+      int64_t g = 0;  // k-blocks issued by this CTA
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const Tile d = decode(t);
+        for (int kb = 0; kb < a.kblocks; kb++, g++) {
+          const int s = (int)(g % STAGES);
+          const int64_t round = g / STAGES;
+          if (round > 0 && !mbar_wait(&empty[s], (uint32_t)((round - 1) & 1), abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], L::A_BYTES + 2 * L::B_BYTES);
+          tma_load_2d(A_raw(s), &tmA, kb * kStageFloats, d.rowA, &full[s]);
+          tma_load_2d(B_hi(s), &tmBh, kb * kStageFloats, d.rowB, &full[s]);
+          tma_load_2d(B_lo(s), &tmBl, kb * kStageFloats, d.rowB, &full[s]);
+        }
       }
       if (*abort_flag) {
         // drain: let the copies already issued land before the CTA exits
-        for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; kb++)
-          mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, abort_flag, false);
+        for (int64_t q = g > STAGES ? g - STAGES : 0; q < g; q++)
+          mbar_wait(&full[q % STAGES], (uint32_t)((q / STAGES) & 1), abort_flag, false);
       }
     }
   } else if (warp == 1) {
@@ -268,109 +301,146 @@ __global__ void __launch_bounds__(kThreads, 1)
       constexpr uint32_t idesc = MODE == MODE_TF32 ? idesc_tf32(BNP) : idesc_bf16(BNP);
       // K per instruction: 8 TF32 or 16 BF16 values, 32 bytes either way
       constexpr int kSteps = MODE == MODE_TF32 ? kStageFloats / 8 : kStageFloats / 16;
-      for (int kb = 0; kb < a.kblocks; kb++) {
-        const int s = kb % STAGES, round = kb / STAGES;
-        if (!mbar_wait(&conv[s], round & 1, abort_flag)) break;
+      int64_t g = 0, i = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, i++) {
+        const int b = (int)(i & 1);
+        const int64_t u = i >> 1;
+        if (u > 0 && !mbar_wait(&tempty[b], (uint32_t)((u - 1) & 1), abort_flag)) break;
         tc_fence_after();
-        const uint32_t ah = smem_u32(A_hi(s)), al = smem_u32(A_lo(s));
-        const uint32_t bh = smem_u32(B_hi(s)), bl = smem_u32(B_lo(s));
+        const uint32_t d_acc = tmem + (uint32_t)(b * L::ACC_COLS);
+        for (int kb = 0; kb < a.kblocks; kb++, g++) {
+          const int s = (int)(g % STAGES);
+          if (!mbar_wait(&conv[s], (uint32_t)((g / STAGES) & 1), abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ah = smem_u32(A_hi(s)), al = smem_u32(A_lo(s));
+          const uint32_t bh = smem_u32(B_hi(s)), bl = smem_u32(B_lo(s));
 #pragma unroll
-        for (int kk = 0; kk < kSteps; kk++) {
-          const uint32_t off = kk * 32;
-          if (MODE == MODE_TF32) {
-            const uint64_t dah = sw128_desc(ah + off), dal = sw128_desc(al + off);
-            const uint64_t dbh = sw128_desc(bh + off), dbl = sw128_desc(bl + off);
-            umma_tf32(tmem, dah, dbh, idesc, (kb | kk) != 0);
-            umma_tf32(tmem, dah, dbl, idesc, 1);
-            umma_tf32(tmem, dal, dbh, idesc, 1);
-          } else {
-            const uint64_t dah = sw64_desc(ah + off), dal = sw64_desc(al + off);
-            const uint64_t dbh = sw64_desc(bh + off), dbl = sw64_desc(bl + off);
-            umma_f16(tmem, dah, dbh, idesc, (kb | kk) != 0);
-            umma_f16(tmem, dah, dbl, idesc, 1);
-            umma_f16(tmem, dal, dbh, idesc, 1);
+          for (int kk = 0; kk < kSteps; kk++) {
+            const uint32_t off = kk * 32;
+            if (MODE == MODE_TF32) {
+              const uint64_t dah = sw128_desc(ah + off), dal = sw128_desc(al + off);
+              const uint64_t dbh = sw128_desc(bh + off), dbl = sw128_desc(bl + off);
+              umma_tf32(d_acc, dah, dbh, idesc, (kb | kk) != 0);
+              umma_tf32(d_acc, dah, dbl, idesc, 1);
+              umma_tf32(d_acc, dal, dbh, idesc, 1);
+            } else {
+              const uint64_t dah = sw64_desc(ah + off), dal = sw64_desc(al + off);
+              const uint64_t dbh = sw64_desc(bh + off), dbl = sw64_desc(bl + off);
+              umma_f16(d_acc, dah, dbh, idesc, (kb | kk) != 0);
+              umma_f16(d_acc, dah, dbl, idesc, 1);
+              umma_f16(d_acc, dal, dbh, idesc, 1);
+            }
+          }
+          umma_commit(&empty[s]);
+        }
+        if (ok) umma_commit(&tfull[b]);
+      }
+      // every product issued by this thread has retired once this fires
+      umma_commit(drain);
+      mbar_wait(drain, 0, abort_flag, false);
+    }
+  } else if (warp < 6) {
+    const int t = threadIdx.x - 64;  // 0..127
+    int64_t g = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      for (int kb = 0; kb < a.kblocks; kb++, g++) {
+        const int s = (int)(g % STAGES);
+        if (!mbar_wait(&full[s], (uint32_t)((g / STAGES) & 1), abort_flag)) {
+          ok = false;
+          break;
+        }
+        if (MODE == MODE_TF32) {
+          // elementwise, so the swizzled layout is kept as is
+          uint4 *hi = reinterpret_cast<uint4 *>(A_hi(s));
+          uint4 *lo = reinterpret_cast<uint4 *>(A_lo(s));
+#pragma unroll 4
+          for (int x = t; x < (int)(L::A_BYTES / 16); x += 128) {
+            const uint4 v = hi[x];
+            hi[x] = make_uint4(split_hi(v.x), split_hi(v.y), split_hi(v.z), split_hi(v.w));
+            lo[x] = make_uint4(split_lo(v.x), split_lo(v.y), split_lo(v.z), split_lo(v.w));
+          }
+        } else {
+          // FP32 chunk c (4 values) of row r sits at chunk c ^ (r & 7) of the
+          // 128-byte row; its 4 BF16 go to bytes 8*(c&1) of chunk
+          // (c>>1) ^ ((r>>1)&3) of the 64-byte row
+          const uint4 *raw = reinterpret_cast<const uint4 *>(A_raw(s));
+          uint8_t *hi = A_hi(s), *lo = A_lo(s);
+#pragma unroll 4
+          for (int x = t; x < BM * 8; x += 128) {
+            const int r = x >> 3, c = x & 7;
+            const uint4 v = raw[r * 8 + (c ^ (r & 7))];
+            uint16_t h[4], l[4];
+            split_bf16(__uint_as_float(v.x), h[0], l[0]);
+            split_bf16(__uint_as_float(v.y), h[1], l[1]);
+            split_bf16(__uint_as_float(v.z), h[2], l[2]);
+            split_bf16(__uint_as_float(v.w), h[3], l[3]);
+            const int o = r * 64 + (((c >> 1) ^ ((r >> 1) & 3)) << 4) + ((c & 1) << 3);
+            *reinterpret_cast<uint2 *>(hi + o) =
+                make_uint2(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16));
+            *reinterpret_cast<uint2 *>(lo + o) =
+                make_uint2(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16));
           }
         }
-        umma_commit(&empty[s]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&conv[s]);
       }
-      umma_commit(accf);
     }
   } else {
-    const int t = threadIdx.x - 64;  // 0..127
-    for (int kb = 0; kb < a.kblocks; kb++) {
-      const int s = kb % STAGES, round = kb / STAGES;
-      if (!mbar_wait(&full[s], round & 1, abort_flag)) break;
-      if (MODE == MODE_TF32) {
-        // elementwise, so the swizzled layout is kept as is
-        uint4 *hi = reinterpret_cast<uint4 *>(A_hi(s));
-        uint4 *lo = reinterpret_cast<uint4 *>(A_lo(s));
-#pragma unroll 4
-        for (int i = t; i < (int)(L::A_BYTES / 16); i += 128) {
-          const uint4 v = hi[i];
-          hi[i] = make_uint4(split_hi(v.x), split_hi(v.y), split_hi(v.z), split_hi(v.w));
-          lo[i] = make_uint4(split_lo(v.x), split_lo(v.y), split_lo(v.z), split_lo(v.w));
-        }
-      } else {
-        // FP32 chunk c (4 values) of row r sits at chunk c ^ (r & 7) of the
-        // 128-byte row; its 4 BF16 go to bytes 8*(c&1) of chunk
-        // (c>>1) ^ ((r>>1)&3) of the 64-byte row
-        const uint4 *raw = reinterpret_cast<const uint4 *>(A_raw(s));
-        uint8_t *hi = A_hi(s), *lo = A_lo(s);
-#pragma unroll 4
-        for (int i = t; i < BM * 8; i += 128) {
-          const int r = i >> 3, c = i & 7;
-          const uint4 v = raw[r * 8 + (c ^ (r & 7))];
-          uint16_t h[4], l[4];
-          split_bf16(__uint_as_float(v.x), h[0], l[0]);
-          split_bf16(__uint_as_float(v.y), h[1], l[1]);
-          split_bf16(__uint_as_float(v.z), h[2], l[2]);
-          split_bf16(__uint_as_float(v.w), h[3], l[3]);
-          const int o = r * 64 + (((c >> 1) ^ ((r >> 1) & 3)) << 4) + ((c & 1) << 3);
-          *reinterpret_cast<uint2 *>(hi + o) = make_uint2(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16));
-          *reinterpret_cast<uint2 *>(lo + o) = make_uint2(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16));
-        }
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(&conv[s]);
-    }
-    const int64_t n0 = (int64_t)nt * (BNP / 2);
-    int64_t *coloff = reinterpret_cast<int64_t *>(smem + STAGES * L::STAGE + 256);
-    if (a.scatter && t < BNP / 2) coloff[t] = scatter_bits(n0 + t, a.sc.nn, a.sc.pn);
-    asm volatile("bar.sync 1, 128;" ::: "memory");
-    if (mbar_wait(accf, 0, abort_flag, false)) {
-      tc_fence_after();
-      const int q = warp & 3;  // TMEM lane quarter this warp may read
-      const int row = q * 32 + lane;
+    // epilogue: warps 6..9 read TMEM lane quarters 2, 3, 0, 1
+    const int t = threadIdx.x - 192;  // 0..127
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    int64_t i = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, i++) {
+      const Tile d = decode(tile);
+      const int b = (int)(i & 1);
+      const int64_t n0 = (int64_t)d.nt * (BNP / 2);
       if (a.scatter) {
-        const int64_t om = scatter_bits(z, a.sc.nb, a.sc.pb) + scatter_bits((int64_t)mt * BM + row, a.sc.nm, a.sc.pm);
+        asm volatile("bar.sync 2, 128;" ::: "memory");  // previous tile's offsets no longer read
+        if (t < BNP / 2) coloff[t] = scatter_bits(n0 + t, a.sc.nn, a.sc.pn);
+        asm volatile("bar.sync 2, 128;" ::: "memory");
+      }
+      if (!mbar_wait(&tfull[b], (uint32_t)((i >> 1) & 1), abort_flag)) break;
+      tc_fence_after();
+      const uint32_t taddr = tmem + (uint32_t)(b * L::ACC_COLS) + ((uint32_t)(q * 32) << 16);
+      if (a.scatter) {
+        const int64_t om = scatter_bits(d.z, a.sc.nb, a.sc.pb) + scatter_bits((int64_t)d.mt * BM + row, a.sc.nm, a.sc.pm);
 #pragma unroll 1
         for (int c = 0; c < BNP; c += 16) {
           uint32_t r[16];
-          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, r);
+          tmem_ld16(taddr + (uint32_t)c, r);
 #pragma unroll
           for (int j = 0; j < 8; j++)
             if (n0 + c / 2 + j < a.N)
               a.C[om + coloff[c / 2 + j]] = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
         }
-      }
-      float2 *crow = a.C + z * a.sC + ((int64_t)mt * BM + row) * a.N;
+      } else {
+        float2 *crow = a.C + d.z * a.sC + ((int64_t)d.mt * BM + row) * a.N;
 #pragma unroll 1
-      for (int c = 0; c < (a.scatter ? 0 : BNP); c += 16) {
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, r);
-        const int64_t nb = n0 + c / 2;
-        if (nb + 8 <= a.N) {
-          float4 *dst = reinterpret_cast<float4 *>(crow + nb);
+        for (int c = 0; c < BNP; c += 16) {
+          uint32_t r[16];
+          tmem_ld16(taddr + (uint32_t)c, r);
+          const int64_t nb = n0 + c / 2;
+          if (nb + 8 <= a.N) {
+            float4 *dst = reinterpret_cast<float4 *>(crow + nb);
 #pragma unroll
-          for (int j = 0; j < 4; j++)
-            dst[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                                 __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
-        } else {
+            for (int j = 0; j < 4; j++)
+              dst[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                   __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+          } else {
 #pragma unroll
-          for (int j = 0; j < 8; j++)
-            if (nb + j < a.N) crow[nb + j] = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+            for (int j = 0; j < 8; j++)
+              if (nb + j < a.N) crow[nb + j] = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+          }
         }
       }
+      tc_fence_before();
+      mbar_arrive(&tempty[b]);
     }
   }
   tc_fence_before();
@@ -538,6 +608,7 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
     return cudaErrorInvalidValue;
   TcArgs args{};
   args.C = C;
+  args.batch = batch;
   args.M = M;
   args.N = N;
   args.K = K;
@@ -548,8 +619,14 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
   args.NT = NT;
   args.scatter = sc ? 1 : 0;
   if (sc) args.sc = *sc;
-  const int64_t n_blocks = batch * args.n_tiles_m * (int64_t)n_tiles_n;
-  if (n_blocks >= (int64_t(1) << 31)) return cudaErrorNotSupported;
+  const int64_t n_tiles = batch * args.n_tiles_m * (int64_t)n_tiles_n;
+  static int n_sm = 0;
+  if (!n_sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 148;
+  }
+  const int64_t n_blocks = std::min<int64_t>(n_tiles, n_sm);
   return bf16 ? dispatch<MODE_BF16>(bnp, ta, tbh, tbl, args, n_blocks, s)
               : dispatch<MODE_TF32>(bnp, ta, tbh, tbl, args, n_blocks, s);
 }

@@ -198,7 +198,9 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
     ps.N = int64_t(1) << fY.size();
     ps.K = int64_t(1) << st.contr.size();
     ps.batch = int64_t(1) << st.batch.size();
-    ps.tc = o.precision != TZ_C64_SIMT && dev::cgemm_tc_supported(o.precision, ps.M, ps.N, ps.K);
+    // skinny products are memory-bound: the streaming SIMT kernel serves them
+    ps.tc = o.precision != TZ_C64_SIMT && dev::cgemm_tc_supported(o.precision, ps.M, ps.N, ps.K) &&
+            !(ps.N <= 4 && ps.K <= 16);
     if (ps.tc) ps.tc_scratch = (int64_t)dev::cgemm_tc_scratch_bytes(o.precision, ps.batch, ps.N, ps.K);
     // where canonical (z, m, n) lands in C
     dev::CScatter &sc = ps.scatter;

@@ -41,7 +41,8 @@ def test_permute_bit_exact(env, rank):
 
 @pytest.mark.parametrize("batch,m,n,k", [(1, 1, 1, 1), (1, 7, 3, 5), (3, 64, 64, 8), (2, 130, 17, 33),
                                          (1, 1000, 2, 4), (5, 33, 80, 1), (1, 4096, 16, 64), (16, 256, 256, 256),
-                                         (1, 1, 300, 9)])
+                                         (1, 1, 300, 9), (3, 4096, 1, 2), (1, 512, 4, 16), (2, 300, 3, 5),
+                                         (1, 1 << 16, 2, 8)])
 def test_cgemm_simt(env, batch, m, n, k):
     tz, torch = env
     rng = np.random.default_rng(m * 7 + n)
@@ -78,6 +79,49 @@ def test_cgemm_tf32x3(env, batch, m, n, k):
     assert np.all(err <= (2.0 ** -18 + 4 * (k + 2) * 2.0 ** -24) * bound + 1e-30), float(np.max(err / bound))
     # and it is genuinely more accurate than one TF32 product would be
     assert np.max(err / bound) < 2.0 ** -14
+
+
+@pytest.mark.parametrize("batch,m,n,k", [(1, 128, 8, 16), (2, 256, 64, 32), (1, 1024, 128, 64), (3, 128, 4, 4),
+                                         (1, 512, 256, 128), (4, 384, 24, 12), (1, 8192, 16, 256), (37, 256, 40, 8)])
+def test_cgemm_bf16x3(env, batch, m, n, k):
+    """Split-BF16 product: hi and lo carry 8+8 significand bits, so the
+    dropped lo*lo term and the lo roundings leave ~2^-16 |a||b| per product."""
+    tz, torch = env
+    rng = np.random.default_rng(m + 5 * n + 11 * k)
+    A, dA = c64(torch, rng, (batch, m, k))
+    B, dB = c64(torch, rng, (batch, n, k))
+    dC = torch.zeros(batch * m * n * 2, dtype=torch.float32, device="cuda")
+    nbytes = tz.tz_op_cgemm_scratch_bytes("bf16x3", batch, m, n, k)
+    scratch = torch.empty(nbytes // 4 + 64, dtype=torch.float32, device="cuda")
+    tz.tz_op_cgemm("bf16x3", batch, m, n, k, dA, m * k, dB, n * k, dC, m * n, scratch=scratch)
+    torch.cuda.synchronize()
+    C = dC.cpu().numpy().view(np.complex64).reshape(batch, m, n)
+    ref = linalg.cgemm(A, B)
+    bound = linalg.cgemm(np.abs(A).astype(np.complex128), np.abs(B).astype(np.complex128)).real
+    err = np.abs(C - ref)
+    assert np.all(err <= (2.0 ** -14 + 4 * (k + 2) * 2.0 ** -24) * bound + 1e-30), float(np.max(err / bound))
+    assert np.max(err / bound) < 2.0 ** -10   # far better than one BF16 product
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_cgemm_tc_many_tiles_scatter_free(env, prec):
+    """More tiles than SMs, so each persistent CTA walks several tiles and
+    both accumulator buffers are reused."""
+    tz, torch = env
+    batch, m, n, k = 8, 2048, 256, 64
+    rng = np.random.default_rng(99)
+    A, dA = c64(torch, rng, (batch, m, k))
+    B, dB = c64(torch, rng, (batch, n, k))
+    dC = torch.zeros(batch * m * n * 2, dtype=torch.float32, device="cuda")
+    nbytes = tz.tz_op_cgemm_scratch_bytes(prec, batch, m, n, k)
+    scratch = torch.empty(nbytes // 4 + 64, dtype=torch.float32, device="cuda")
+    tz.tz_op_cgemm(prec, batch, m, n, k, dA, m * k, dB, n * k, dC, m * n, scratch=scratch)
+    torch.cuda.synchronize()
+    C = dC.cpu().numpy().view(np.complex64).reshape(batch, m, n)
+    ref = linalg.cgemm(A, B)
+    bound = linalg.cgemm(np.abs(A).astype(np.complex128), np.abs(B).astype(np.complex128)).real
+    tol = 2.0 ** -18 if prec == "tf32x3" else 2.0 ** -14
+    assert np.all(np.abs(C - ref) <= (tol + 4 * (k + 2) * 2.0 ** -24) * bound)
 
 
 def test_cgemm_tc_rejects_unsupported(env):
