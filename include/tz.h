@@ -245,6 +245,10 @@ typedef struct {
 int tz_plan_profile_enable(tz_plan *plan, int on);
 /* Synchronise the plan's stream and read the counters. */
 int tz_plan_profile_get(tz_plan *plan, tz_plan_profile *out);
+/* Per launch item of the group schedule, summed over profiled groups:
+ * 6 doubles per item (kind, ms, flops, bytes, step or -1, launches), in
+ * schedule order. cap = capacity in items; *n receives the item count. */
+int tz_plan_profile_items(tz_plan *plan, double *out, int cap, int *n);
 
 /* --------------------------------------------------------------- serving
  * A request loop for amplitude-batch queries over resident plans: plans

@@ -226,6 +226,21 @@ class Plan(_Handle):
         return {k: {"launches": pr.launches[i], "ms": pr.ms[i], "flops": pr.flops[i], "bytes": pr.bytes[i]}
                 for i, k in enumerate(PROFILE_KINDS)}
 
+    def profile_items(self):
+        """Per launch item of a group: dicts with kind, ms, flops, bytes,
+        step (GEMM items) and launches, summed over profiled groups."""
+        n = ctypes.c_int()
+        lib().tz_plan_profile_items(self._h, None, 0, ctypes.byref(n))
+        buf = np.zeros(6 * max(n.value, 1))
+        check(lib().tz_plan_profile_items(self._h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n.value,
+                                          ctypes.byref(n)))
+        out = []
+        for i in range(n.value):
+            k, ms, fl, by, st, cnt = buf[6 * i: 6 * i + 6]
+            out.append({"kind": PROFILE_KINDS[int(k)], "ms": ms, "flops": fl, "bytes": by, "step": int(st),
+                        "launches": int(cnt)})
+        return out
+
     def describe(self) -> str:
         n = ctypes.c_size_t()
         lib().tz_plan_describe(self._h, None, 0, ctypes.byref(n))

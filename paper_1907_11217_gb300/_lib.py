@@ -102,6 +102,7 @@ SIGNATURES = {
     "tz_plan_destroy": (None, [P]),
     "tz_plan_profile_enable": (c_int, [P, c_int]),
     "tz_plan_profile_get": (c_int, [P, ctypes.POINTER(tz_plan_profile)]),
+    "tz_plan_profile_items": (c_int, [P, F64P, c_int, ctypes.POINTER(c_int)]),
     "tz_server_create": (c_int, [ctypes.POINTER(tz_server_opts), PP]),
     "tz_server_submit": (c_int, [P, P, U8P, c_int64, ctypes.POINTER(c_uint64)]),
     "tz_server_poll": (c_int, [P, c_uint64, F64P, ctypes.POINTER(c_int)]),

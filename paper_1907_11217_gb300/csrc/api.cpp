@@ -342,7 +342,31 @@ int tz_plan_profile_enable(tz_plan *plan, int on) {
   REQUIRE(plan, "NULL plan");
   if (plan->bound) tz::plan_profile_collect(plan);
   plan->prof = tz_plan_profile{};
+  plan->item_ms.clear();
+  plan->item_count.clear();
   plan->profiling = on != 0;
+  TZ_CATCH
+}
+
+int tz_plan_profile_items(tz_plan *plan, double *out, int cap, int *n) {
+  TZ_TRY
+  REQUIRE(plan && n, "NULL argument");
+  if (plan->bound) tz::plan_profile_collect(plan);
+  const auto &items = plan->var_items;
+  *n = (int)items.size();
+  REQUIRE(out && cap >= (int)items.size(), "buffer too small");
+  for (size_t i = 0; i < items.size(); i++) {
+    int kind = 0;
+    double fl = 0, by = 0;
+    tz::item_cost_public(plan, (int)i, &kind, &fl, &by);
+    double *o = out + 6 * i;
+    o[0] = kind;
+    o[1] = i < plan->item_ms.size() ? plan->item_ms[i] : 0.0;
+    o[2] = fl;
+    o[3] = by;
+    o[4] = items[i].kind == tz::IT_GEMM ? items[i].a : -1;
+    o[5] = i < plan->item_count.size() ? (double)plan->item_count[i] : 0.0;
+  }
   TZ_CATCH
 }
 

@@ -104,64 +104,120 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 }
 
 // Skinny products (n <= NMAX complex columns, k <= KMAX): memory-bound, so
-// one thread streams one row of A (k contiguous complex values, 16-byte
-// loads) against B held in shared memory and writes its n results.
-template <int NMAX, int KMAX>
+// each thread streams RPT rows of A (k contiguous complex values, 16-byte
+// loads, all issued before any use) against B held in shared memory and
+// writes its n results per row.
+template <int NMAX, int KMAX, int RPT>
 __global__ void __launch_bounds__(256)
     cgemm_skinny_kernel(const float2 *__restrict__ A, const float2 *__restrict__ B, float2 *__restrict__ C,
                         int64_t batch, int64_t M, int N, int K, int64_t sA, int64_t sB, int64_t sC,
                         const __grid_constant__ CScatter sc, int scatter) {
   __shared__ float2 Bs[NMAX * KMAX];
-  const int64_t rows_per_batch_blocks = (M + 255) / 256;
-  for (int64_t blk = blockIdx.x; blk < rows_per_batch_blocks * batch; blk += gridDim.x) {
-    const int64_t z = blk / rows_per_batch_blocks;
-    const int64_t m = (blk - z * rows_per_batch_blocks) * 256 + threadIdx.x;
+  constexpr int ROWS = 256 * RPT;
+  const int64_t blocks_per_batch = (M + ROWS - 1) / ROWS;
+  for (int64_t blk = blockIdx.x; blk < blocks_per_batch * batch; blk += gridDim.x) {
+    const int64_t z = blk / blocks_per_batch;
+    const int64_t m0 = (blk - z * blocks_per_batch) * ROWS + threadIdx.x;
     __syncthreads();
     for (int i = threadIdx.x; i < N * K; i += 256) Bs[i] = B[z * sB + i];
     __syncthreads();
-    if (m >= M) continue;
-    float2 a[KMAX];
-    const float2 *arow = A + z * sA + m * K;
-    if ((K & 1) == 0) {
+    float2 a[RPT][KMAX];
 #pragma unroll
-      for (int k = 0; k < KMAX; k += 2)
-        if (k < K) {
-          const float4 v = *reinterpret_cast<const float4 *>(arow + k);
-          a[k] = make_float2(v.x, v.y);
-          a[k + 1] = make_float2(v.z, v.w);
+    for (int r = 0; r < RPT; r++) {
+      const int64_t m = m0 + r * 256;
+      const float2 *arow = A + z * sA + m * K;
+#pragma unroll
+      for (int k = 0; k < KMAX; k += 2) {
+        if (m < M && k + 1 < K) {
+          const float4 v = __ldcs(reinterpret_cast<const float4 *>(arow + k));
+          a[r][k] = make_float2(v.x, v.y);
+          a[r][k + 1] = make_float2(v.z, v.w);
+        } else if (m < M && k < K) {
+          a[r][k] = arow[k];
         }
-    } else {
-#pragma unroll
-      for (int k = 0; k < KMAX; k++)
-        if (k < K) a[k] = arow[k];
+      }
     }
-    const int64_t om = scatter ? scatter_bits(z, sc.nb, sc.pb) + scatter_bits(m, sc.nm, sc.pm) : z * sC + m * N;
 #pragma unroll
-    for (int n = 0; n < NMAX; n++) {
-      if (n >= N) break;
-      float2 acc = make_float2(0.f, 0.f);
+    for (int r = 0; r < RPT; r++) {
+      const int64_t m = m0 + r * 256;
+      if (m >= M) continue;
+      const int64_t om = scatter ? scatter_bits(z, sc.nb, sc.pb) + scatter_bits(m, sc.nm, sc.pm) : z * sC + m * N;
 #pragma unroll
-      for (int k = 0; k < KMAX; k++)
-        if (k < K) {
-          const float2 b = Bs[n * K + k];
-          acc.x = fmaf(a[k].x, b.x, acc.x);
-          acc.x = fmaf(-a[k].y, b.y, acc.x);
-          acc.y = fmaf(a[k].x, b.y, acc.y);
-          acc.y = fmaf(a[k].y, b.x, acc.y);
-        }
-      C[om + (scatter ? scatter_bits(n, sc.nn, sc.pn) : n)] = acc;
+      for (int n = 0; n < NMAX; n++) {
+        if (n >= N) break;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < KMAX; k++)
+          if (k < K) {
+            const float2 b = Bs[n * K + k];
+            acc.x = fmaf(a[r][k].x, b.x, acc.x);
+            acc.x = fmaf(-a[r][k].y, b.y, acc.x);
+            acc.y = fmaf(a[r][k].x, b.y, acc.y);
+            acc.y = fmaf(a[r][k].y, b.x, acc.y);
+          }
+        C[om + (scatter ? scatter_bits(n, sc.nn, sc.pn) : n)] = acc;
+      }
     }
   }
 }
 
-template <int NMAX, int KMAX>
+template <int NMAX, int KMAX, int RPT>
 cudaError_t run_skinny(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N, int64_t K,
                        int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s) {
-  const int64_t blocks = ((M + 255) / 256) * batch;
+  const int64_t blocks = ((M + 256 * RPT - 1) / (256 * RPT)) * batch;
   CScatter none{};
-  cgemm_skinny_kernel<NMAX, KMAX><<<(unsigned)std::min<int64_t>(blocks, 152 * 16), 256, 0, s>>>(
+  cgemm_skinny_kernel<NMAX, KMAX, RPT><<<(unsigned)std::min<int64_t>(blocks, 152 * 16), 256, 0, s>>>(
       A, B, C, batch, M, (int)N, (int)K, sA, sB, sC, sc ? *sc : none, sc ? 1 : 0);
   return cudaGetLastError();
+}
+
+// Few outputs, long summed index (m*n small, k large): one block per output
+// element streams its A row and B row (both k-contiguous) with 16-byte loads;
+// each thread sums its strided share in FP32, then a tree reduction.
+__global__ void __launch_bounds__(256)
+    cgemm_dot_kernel(const float2 *__restrict__ A, const float2 *__restrict__ B, float2 *__restrict__ C,
+                     int64_t batch, int64_t M, int64_t N, int64_t K, int64_t sA, int64_t sB, int64_t sC,
+                     const __grid_constant__ CScatter sc, int scatter) {
+  __shared__ float2 red[8];
+  const int64_t n_out = batch * M * N;
+  for (int64_t o = blockIdx.x; o < n_out; o += gridDim.x) {
+    const int64_t z = o / (M * N);
+    const int64_t m = (o / N) % M;
+    const int64_t n = o % N;
+    const float4 *a = reinterpret_cast<const float4 *>(A + z * sA + m * K);
+    const float4 *b = reinterpret_cast<const float4 *>(B + z * sB + n * K);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int64_t k = threadIdx.x; k < K / 2; k += blockDim.x) {
+      const float4 va = a[k], vb = b[k];
+      acc.x = fmaf(va.x, vb.x, acc.x);
+      acc.x = fmaf(-va.y, vb.y, acc.x);
+      acc.y = fmaf(va.x, vb.y, acc.y);
+      acc.y = fmaf(va.y, vb.x, acc.y);
+      acc.x = fmaf(va.z, vb.z, acc.x);
+      acc.x = fmaf(-va.w, vb.w, acc.x);
+      acc.y = fmaf(va.z, vb.w, acc.y);
+      acc.y = fmaf(va.w, vb.z, acc.y);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float2 t = red[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+        t.x += red[w].x;
+        t.y += red[w].y;
+      }
+      const int64_t off = scatter ? scatter_bits(z, sc.nb, sc.pb) + scatter_bits(m, sc.nm, sc.pm) +
+                                        scatter_bits(n, sc.nn, sc.pn)
+                                  : z * sC + m * N + n;
+      C[off] = t;
+    }
+  }
 }
 
 template <int BM, int BN, int TM, int TN, int BK>
@@ -180,9 +236,16 @@ cudaError_t run(const float2 *A, const float2 *B, float2 *C, int64_t batch, int6
 cudaError_t launch_cgemm_simt(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N,
                               int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s) {
   if (batch <= 0 || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
+  if (M * N <= 64 && K >= 2048 && (K % 2) == 0) {
+    CScatter none{};
+    const int64_t outs = batch * M * N;
+    cgemm_dot_kernel<<<(unsigned)std::min<int64_t>(outs, 152 * 8), 256, 0, s>>>(A, B, C, batch, M, N, K, sA, sB, sC,
+                                                                             sc ? *sc : none, sc ? 1 : 0);
+    return cudaGetLastError();
+  }
   if (N <= 4 && K <= 16 && M >= 256) {
-    if (K <= 4) return run_skinny<4, 4>(A, B, C, batch, M, N, K, sA, sB, sC, sc, s);
-    return run_skinny<4, 16>(A, B, C, batch, M, N, K, sA, sB, sC, sc, s);
+    if (K <= 4) return run_skinny<4, 4, 4>(A, B, C, batch, M, N, K, sA, sB, sC, sc, s);
+    return run_skinny<4, 16, 2>(A, B, C, batch, M, N, K, sA, sB, sC, sc, s);
   }
   if (N >= 48) return run<64, 64, 4, 4, 8>(A, B, C, batch, M, N, K, sA, sB, sC, sc, s);
   if (N >= 12) return run<128, 16, 4, 2, 8>(A, B, C, batch, M, N, K, sA, sB, sC, sc, s);

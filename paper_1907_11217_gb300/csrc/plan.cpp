@@ -221,6 +221,35 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
       p->T[n].lay = set_of(n);
       p->T[n].fixed = true;
     }
+  // A GEMM epilogue writes its consumer's layout directly only when the two
+  // lowest bits of that layout are bits it writes contiguously (rows across a
+  // warp, or a thread's run of columns); otherwise whole sectors would be
+  // assembled from several CTAs' 8-byte stores. Then it writes row-major and
+  // the tiled permute moves the result (both sides in 256-byte runs).
+  for (int s = 0; s < NS; s++) {
+    PStep &ps = p->S[s];
+    if (!ps.gemm || ps.row_major) continue;
+    const std::vector<int> &Lc = p->T[ps.c].lay;
+    if (Lc.size() < 2) continue;
+    const dev::CScatter &sc = ps.scatter;
+    std::vector<int> good;  // positions in Lc written contiguously
+    const bool skinny = ps.N <= 4 && ps.K <= 16 && ps.M >= 256 && !ps.tc;
+    const int m_run = ps.tc || skinny ? 5 : 2, n_run = ps.tc ? 3 : skinny ? sc.nn : 4;
+    for (int j = 0; j < std::min(sc.nm, m_run); j++) good.push_back(sc.pm[j]);
+    for (int j = 0; j < std::min(sc.nn, n_run); j++) good.push_back(sc.pn[j]);
+    auto has = [&](int pos) { return std::find(good.begin(), good.end(), pos) != good.end(); };
+    if (has(0) && has(1)) continue;
+    PTensor t;
+    t.var = p->T[ps.c].var;
+    t.fixed = true;
+    // row-major [batch][m][n]: n bits lowest, then m, then batch
+    for (int j = 0; j < sc.nn; j++) t.lay.push_back(Lc[sc.pn[j]]);
+    for (int j = 0; j < sc.nm; j++) t.lay.push_back(Lc[sc.pm[j]]);
+    for (int j = 0; j < sc.nb; j++) t.lay.push_back(Lc[sc.pb[j]]);
+    p->T.push_back(t);
+    ps.c_nat = (int)p->T.size() - 1;
+    ps.row_major = true;
+  }
   // root must hold exactly the batch indices
   for (int i : p->T[p->root].lay)
     if (!net.is_open(i)) fail(TZ_EINVAL, "tree root keeps a wire index: the tree does not contract the network");
@@ -293,6 +322,12 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
         Item it{IT_GEMM};
         it.a = s;
         items.push_back(it);
+        if (ps.c_nat >= 0) {
+          Item pm{IT_PERMUTE};
+          pm.a = ps.c_nat;
+          pm.b = ps.c;
+          items.push_back(pm);
+        }
       }
     }
     if (!var) {
@@ -343,7 +378,7 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
         const PStep &ps = p->S[it.a];
         use(pass, ps.opX, time);
         use(pass, ps.opY, time);
-        birth[pass][ps.c] = time;
+        birth[pass][ps.c_nat >= 0 ? ps.c_nat : ps.c] = time;
       } else if (it.kind == IT_ACCUM) {
         use(pass, p->root, time);
       }
@@ -582,7 +617,7 @@ std::string plan_describe(const tz_plan *p) {
       << ",\"gemm\":" << x.gemm << ",\"tc\":" << x.tc << ",\"opX\":" << x.opX << ",\"opY\":" << x.opY
       << ",\"M\":" << x.M << ",\"N\":" << x.N << ",\"K\":" << x.K << ",\"batch\":" << x.batch
       << ",\"level\":" << x.level << ",\"dstep\":" << x.dstep << ",\"permX\":" << x.permX << ",\"permY\":" << x.permY
-      << ",\"row_major\":" << x.row_major << ",\"pm\":[";
+      << ",\"row_major\":" << x.row_major << ",\"c_nat\":" << x.c_nat << ",\"pm\":[";
     for (int j = 0; j < x.scatter.nm; j++) o << (j ? "," : "") << (int)x.scatter.pm[j];
     o << "],\"pn\":[";
     for (int j = 0; j < x.scatter.nn; j++) o << (j ? "," : "") << (int)x.scatter.pn[j];
@@ -662,6 +697,14 @@ void plan_profile_collect(tz_plan *p) {
     p->prof.ms[q.kind] += ms;
     p->prof.flops[q.kind] += q.flops;
     p->prof.bytes[q.kind] += q.bytes;
+    if (q.item >= 0) {
+      if (p->item_ms.size() < p->var_items.size()) {
+        p->item_ms.assign(p->var_items.size(), 0.0);
+        p->item_count.assign(p->var_items.size(), 0);
+      }
+      p->item_ms[q.item] += ms;
+      p->item_count[q.item]++;
+    }
     p->event_pool.push_back(q.a);
     p->event_pool.push_back(q.b);
   }
@@ -703,16 +746,23 @@ static void item_cost(const tz_plan *p, const Item &it, int *kind, double *flops
   }
 }
 
+void item_cost_public(const tz_plan *p, int var_item, int *kind, double *flops, double *bytes) {
+  item_cost(p, p->var_items[var_item], kind, flops, bytes);
+}
+
 static void run_items(tz_plan *p, const std::vector<Item> &items, const RunCtx &ctx) {
   cudaStream_t s = ctx.stream;
   auto *gs = reinterpret_cast<dev::GroupState *>(ctx.scratch + p->s_gs);
   const char *cbase = p->ws + p->off_const;
   char *abase = ctx.scratch + p->s_arena;
   const bool prof = p->profiling && !p->capturing;
-  for (const Item &it : items) {
+  const bool is_var = &items == &p->var_items;
+  for (size_t ii = 0; ii < items.size(); ii++) {
+    const Item &it = items[ii];
     tz_plan::Pending pend{};
     if (prof) {
       item_cost(p, it, &pend.kind, &pend.flops, &pend.bytes);
+      pend.item = is_var ? (int)ii : -1;
       pend.a = take_event(p);
       pend.b = take_event(p);
       cuda_check(cudaEventRecord(pend.a, s), "event record");
@@ -745,7 +795,7 @@ static void run_items(tz_plan *p, const std::vector<Item> &items, const RunCtx &
         const PStep &ps = p->S[it.a];
         const float2 *X = (const float2 *)tensor_ptr(p, ctx, ps.opX);
         const float2 *Y = (const float2 *)tensor_ptr(p, ctx, ps.opY);
-        float2 *C = (float2 *)tensor_ptr(p, ctx, ps.c);
+        float2 *C = (float2 *)tensor_ptr(p, ctx, ps.c_nat >= 0 ? ps.c_nat : ps.c);
         const dev::CScatter *sc = ps.row_major ? nullptr : &ps.scatter;
         if (ps.tc) {
           void *scr = abase + ps.tc_scratch_off;

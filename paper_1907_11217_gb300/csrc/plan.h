@@ -35,6 +35,8 @@ struct PStep {
   int64_t tc_scratch_off = -1;
   dev::CScatter scatter{};    // where the GEMM writes its result
   bool row_major = false;     // scatter is the plain row-major order
+  int c_nat = -1;             // tensor the GEMM writes in row-major order when a
+                              // permute then moves it into c's layout
 };
 
 struct Item {
@@ -84,7 +86,10 @@ struct tz_plan {
     int kind;
     cudaEvent_t a, b;
     double flops, bytes;
+    int item;   // index in var_items, -1 for bind-time items
   };
+  std::vector<double> item_ms;     // per var item, summed over profiled groups
+  std::vector<int64_t> item_count;
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
   tz_plan_profile prof{};
@@ -106,6 +111,7 @@ void plan_bind(tz_plan *p, void *ws, size_t bytes);
 void plan_run(tz_plan *p, const RunCtx &ctx, int64_t n_rows, int64_t lo, int64_t hi);
 void plan_destroy(tz_plan *p);
 void plan_profile_collect(tz_plan *p);
+void item_cost_public(const tz_plan *p, int var_item, int *kind, double *flops, double *bytes);
 std::string plan_describe(const tz_plan *p);
 inline void cuda_check(cudaError_t e, const char *what) {
   if (e != cudaSuccess) fail(TZ_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));

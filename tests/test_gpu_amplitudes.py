@@ -102,23 +102,28 @@ def test_device_entry_point_and_graph(tz):
         assert rel_err(got, sv.amplitudes(spec, bits), 16) <= TOL_C64
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "c64"])
-def test_tensor_core_path_5x5(tz, prec):
-    """A circuit big enough that GEMM steps have >= 128 rows, so the split-TF32
-    tcgen05 product really runs (checked through the per-kernel profile);
-    compared with the oracle's plain-wire contractor."""
-    spec = grid_spec(5, 5, 16, 21)
-    bits = ti.random_bitstrings(25, 4, 77)
-    plan, *_ = make_plan(tz, spec, precision=prec, small_log2=8, restarts=8, seed=3)
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "c64"])
+def test_tensor_core_path_5x6(tz, prec):
+    """5x6 grid, depth 1+20+1, a batch of 64 bitstrings contracted together:
+    the batch indices make the late tensors large enough that GEMM steps
+    with >= 128 rows and >= 8 columns run on the split-precision tcgen05
+    product (checked through the per-kernel profile); compared with the
+    oracle's plain-wire contractor, one bitstring at a time. TF32x3 is held
+    to the complex64 bar; the BF16x3 error is measured and only sanity-bounded."""
+    spec = grid_spec(5, 6, 20, 7)
+    bits = ti.random_bitstrings(30, 64, 77)
+    plan, *_ = make_plan(tz, spec, batch_log2=6, precision=prec, small_log2=8, restarts=8, seed=3,
+                         max_bitstrings=64)
     plan.profile_enable(True)
     got = tz.tz_contract_amplitudes(plan, bits)
     prof = plan.profile()
     c = tn.Contractor(spec, max_log2=24)
     ref = np.array([c.amplitude(x) for x in bits])
-    err = rel_err(got, ref, 25)
+    err = rel_err(got, ref, 30)
     print(f"{prec}: max rel err {err:.3e}, tc launches {prof['gemm_tc']['launches']}")
-    assert err <= TOL_C64
-    if prec == "tf32x3":
-        assert prof["gemm_tc"]["launches"] > 0
-    else:
+    if prec == "c64":
+        assert err <= TOL_C64
         assert prof["gemm_tc"]["launches"] == 0 and prof["gemm_simt"]["launches"] > 0
+    else:
+        assert prof["gemm_tc"]["launches"] > 0
+        assert err <= (TOL_C64 if prec == "tf32x3" else 1e-3)
