@@ -126,15 +126,19 @@ __global__ void __launch_bounds__(256)
     for (int r = 0; r < RPT; r++) {
       const int64_t m = m0 + r * 256;
       const float2 *arow = A + z * sA + m * K;
+      if ((K & 1) == 0) {
+        // K even: every row starts on a 16-byte boundary
 #pragma unroll
-      for (int k = 0; k < KMAX; k += 2) {
-        if (m < M && k + 1 < K) {
-          const float4 v = __ldcs(reinterpret_cast<const float4 *>(arow + k));
-          a[r][k] = make_float2(v.x, v.y);
-          a[r][k + 1] = make_float2(v.z, v.w);
-        } else if (m < M && k < K) {
-          a[r][k] = arow[k];
-        }
+        for (int k = 0; k < KMAX; k += 2)
+          if (m < M && k < K) {
+            const float4 v = __ldcs(reinterpret_cast<const float4 *>(arow + k));
+            a[r][k] = make_float2(v.x, v.y);
+            a[r][k + 1] = make_float2(v.z, v.w);
+          }
+      } else {
+#pragma unroll
+        for (int k = 0; k < KMAX; k++)
+          if (m < M && k < K) a[r][k] = arow[k];
       }
     }
 #pragma unroll

@@ -1,8 +1,12 @@
 // Bit permutation of a complex64 tensor (every index has dimension 2, so a
 // tensor transpose is a permutation of the bits of the element offset).
-// Tiled through shared memory: a tile spans the 5 lowest input bits and the
-// input bits that land on the 5 lowest output bits (topped up to 10 bits),
-// so both the loads and the stores move runs of >= 32 consecutive elements.
+// HBM-bound. A tile spans the 5 lowest input bits, the input bits that land
+// on the 5 lowest output bits, and further low input bits up to 10 bits
+// (1024 elements, 8 KB of shared memory), so loads and stores both move
+// runs of >= 32 consecutive elements (256 bytes per warp access). The
+// tile-local offsets are the same for every tile and are computed once per
+// thread; shared memory is XOR-swizzled (low 5 index bits ^= high 5) so
+// neither the row-wise writes nor the column-wise reads conflict on banks.
 #include <algorithm>
 
 #include "kernels.h"
@@ -14,6 +18,8 @@ namespace {
 
 constexpr int kW = 5;       // bits of a contiguous run on either side
 constexpr int kTile = 10;   // bits of a tile (1024 elements, 8 KB)
+constexpr int kThreads = 256;
+constexpr int kPer = (1 << kTile) / kThreads;  // elements per thread per tile
 
 struct TileMap {
   int r, u;                 // tensor rank, tile bits
@@ -24,6 +30,8 @@ struct TileMap {
   int8_t rout[kMaxBits];    // output bit of tile-index bit j
 };
 
+__device__ __forceinline__ int swz(int e) { return e ^ ((e >> 5) & 31); }
+
 __global__ void permute_small_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, PermuteArgs a) {
   const int64_t n = int64_t(1) << a.rank;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
@@ -33,11 +41,33 @@ __global__ void permute_small_kernel(const float2 *__restrict__ in, float2 *__re
   }
 }
 
-__global__ void __launch_bounds__(256) permute_tiled_kernel(const float2 *__restrict__ in, float2 *__restrict__ out,
-                                                            TileMap m, int64_t n_tiles) {
+// u == kTile (rank >= 10): every thread moves kPer elements per tile.
+__global__ void __launch_bounds__(kThreads) permute_tiled_kernel(const float2 *__restrict__ in,
+                                                                 float2 *__restrict__ out, const __grid_constant__ TileMap m,
+                                                                 int64_t n_tiles) {
   __shared__ float2 tile[1 << kTile];
-  const int nt = 1 << m.u;
-  const int nr = m.r - m.u;
+  // tile-local offsets, identical for every tile
+  int64_t ld_off[kPer], st_off[kPer];
+  int ld_s[kPer], st_s[kPer];
+#pragma unroll
+  for (int i = 0; i < kPer; i++) {
+    const int e = threadIdx.x + i * kThreads;  // load order
+    int64_t o = 0;
+    for (int j = 0; j < kTile; j++) o |= int64_t((e >> j) & 1) << m.uin[j];
+    ld_off[i] = o;
+    ld_s[i] = swz(e);
+    const int f = e;  // store order
+    int64_t oo = 0;
+    int src = 0;
+    for (int j = 0; j < kTile; j++) {
+      const int b = (f >> j) & 1;
+      oo |= int64_t(b) << m.vout[j];
+      src |= b << m.vsrc[j];
+    }
+    st_off[i] = oo;
+    st_s[i] = swz(src);
+  }
+  const int nr = m.r - kTile;
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     int64_t bin = 0, bout = 0;
     for (int j = 0; j < nr; j++) {
@@ -45,22 +75,14 @@ __global__ void __launch_bounds__(256) permute_tiled_kernel(const float2 *__rest
       bin |= b << m.rin[j];
       bout |= b << m.rout[j];
     }
-    for (int e = threadIdx.x; e < nt; e += blockDim.x) {
-      int64_t off = bin;
-      for (int j = 0; j < m.u; j++) off |= int64_t((e >> j) & 1) << m.uin[j];
-      tile[e] = in[off];
-    }
+    float2 v[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; i++) v[i] = __ldcs(in + bin + ld_off[i]);
+#pragma unroll
+    for (int i = 0; i < kPer; i++) tile[ld_s[i]] = v[i];
     __syncthreads();
-    for (int f = threadIdx.x; f < nt; f += blockDim.x) {
-      int64_t off = bout;
-      int e = 0;
-      for (int j = 0; j < m.u; j++) {
-        const int b = (f >> j) & 1;
-        off |= int64_t(b) << m.vout[j];
-        e |= b << m.vsrc[j];
-      }
-      out[off] = tile[e];
-    }
+#pragma unroll
+    for (int i = 0; i < kPer; i++) __stcs(out + bout + st_off[i], tile[st_s[i]]);
     __syncthreads();
   }
 }
@@ -71,7 +93,7 @@ cudaError_t launch_permute(const float2 *in, float2 *out, const PermuteArgs &a, 
   const int r = a.rank;
   if (r < 0 || r > kMaxBits) return cudaErrorInvalidValue;
   const int64_t n = int64_t(1) << r;
-  if (r <= kTile) {
+  if (r < kTile) {
     int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
     permute_small_kernel<<<blocks, 256, 0, s>>>(in, out, a);
     return cudaGetLastError();
@@ -89,7 +111,7 @@ cudaError_t launch_permute(const float2 *in, float2 *out, const PermuteArgs &a, 
     in_tile[b] = true;
   }
   for (int p = 0; p < kW; p++)
-    if (!in_tile[a.perm[p]]) {
+    if (!in_tile[(int)a.perm[p]]) {
       m.uin[u++] = a.perm[p];
       in_tile[(int)a.perm[p]] = true;
     }
@@ -116,8 +138,8 @@ cudaError_t launch_permute(const float2 *in, float2 *out, const PermuteArgs &a, 
       j++;
     }
   const int64_t n_tiles = n >> u;
-  const int blocks = (int)std::min<int64_t>(n_tiles, 152 * 16);
-  permute_tiled_kernel<<<blocks, 256, 0, s>>>(in, out, m, n_tiles);
+  const int blocks = (int)std::min<int64_t>(n_tiles, 152 * 8);
+  permute_tiled_kernel<<<blocks, kThreads, 0, s>>>(in, out, m, n_tiles);
   return cudaGetLastError();
 }
 
