@@ -235,7 +235,83 @@ cudaError_t run(const float2 *A, const float2 *B, float2 *C, int64_t batch, int6
   return cudaGetLastError();
 }
 
+// Skinny products read in place: X and Y in any bit layout (gather maps),
+// C through a scatter map. One thread per row of X; rows are numbered so that
+// the lowest row bits are the lowest bits of X where possible, which keeps
+// the loads of a warp in few sectors.
+template <int NMAX, int KMAX, int RPT>
+__global__ void __launch_bounds__(256)
+    skinny_gather_kernel(const float2 *__restrict__ X, const float2 *__restrict__ Y, float2 *__restrict__ C,
+                         int64_t batch, int64_t M, int N, int K, const __grid_constant__ GatherMap g,
+                         const __grid_constant__ CScatter sc, int scatter) {
+  __shared__ float2 Ys[NMAX * KMAX];
+  __shared__ int64_t xk_off[KMAX];
+  constexpr int ROWS = 256 * RPT;
+  const int64_t blocks_per_batch = (M + ROWS - 1) / ROWS;
+  for (int64_t blk = blockIdx.x; blk < blocks_per_batch * batch; blk += gridDim.x) {
+    const int64_t z = blk / blocks_per_batch;
+    const int64_t m0 = (blk - z * blocks_per_batch) * ROWS + threadIdx.x;
+    const int64_t xb = scatter_bits(z, g.nb, g.xb), yb = scatter_bits(z, g.nb, g.yb);
+    const int64_t cb = scatter ? scatter_bits(z, sc.nb, sc.pb) : z * M * N;
+    __syncthreads();
+    if (threadIdx.x < N * K) {
+      const int n = threadIdx.x / K, k = threadIdx.x % K;
+      Ys[threadIdx.x] = Y[yb + scatter_bits(n, g.nn, g.yn) + scatter_bits(k, g.nk, g.yk)];
+    }
+    if (threadIdx.x < K) xk_off[threadIdx.x] = scatter_bits(threadIdx.x, g.nk, g.xk);
+    __syncthreads();
+    float2 a[RPT][KMAX];
+#pragma unroll
+    for (int r = 0; r < RPT; r++) {
+      const int64_t m = m0 + r * 256;
+      if (m >= M) continue;
+      const float2 *xr = X + xb + scatter_bits(m, g.nm, g.xm);
+#pragma unroll
+      for (int k = 0; k < KMAX; k++)
+        if (k < K) a[r][k] = __ldcs(xr + xk_off[k]);
+    }
+#pragma unroll
+    for (int r = 0; r < RPT; r++) {
+      const int64_t m = m0 + r * 256;
+      if (m >= M) continue;
+      const int64_t om = cb + (scatter ? scatter_bits(m, sc.nm, sc.pm) : m * N);
+#pragma unroll
+      for (int n = 0; n < NMAX; n++) {
+        if (n >= N) break;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < KMAX; k++)
+          if (k < K) {
+            const float2 b = Ys[n * K + k];
+            acc.x = fmaf(a[r][k].x, b.x, acc.x);
+            acc.x = fmaf(-a[r][k].y, b.y, acc.x);
+            acc.y = fmaf(a[r][k].x, b.y, acc.y);
+            acc.y = fmaf(a[r][k].y, b.x, acc.y);
+          }
+        C[om + (scatter ? scatter_bits(n, sc.nn, sc.pn) : n)] = acc;
+      }
+    }
+  }
+}
+
+template <int NMAX, int KMAX, int RPT>
+cudaError_t run_skinny_gather(const float2 *X, const float2 *Y, float2 *C, int64_t batch, int64_t M, int64_t N,
+                              int64_t K, const GatherMap &g, const CScatter *sc, cudaStream_t s) {
+  const int64_t blocks = ((M + 256 * RPT - 1) / (256 * RPT)) * batch;
+  CScatter none{};
+  skinny_gather_kernel<NMAX, KMAX, RPT><<<(unsigned)std::min<int64_t>(blocks, 152 * 16), 256, 0, s>>>(
+      X, Y, C, batch, M, (int)N, (int)K, g, sc ? *sc : none, sc ? 1 : 0);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_cgemm_skinny_gather(const float2 *X, const float2 *Y, float2 *C, int64_t batch, int64_t M,
+                                       int64_t N, int64_t K, const GatherMap &g, const CScatter *sc, cudaStream_t s) {
+  if (batch <= 0 || M <= 0 || N <= 0 || K <= 0 || N > 4 || K > 16) return cudaErrorInvalidValue;
+  if (K <= 4) return run_skinny_gather<4, 4, 4>(X, Y, C, batch, M, N, K, g, sc, s);
+  return run_skinny_gather<4, 16, 2>(X, Y, C, batch, M, N, K, g, sc, s);
+}
 
 cudaError_t launch_cgemm_simt(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N,
                               int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s) {

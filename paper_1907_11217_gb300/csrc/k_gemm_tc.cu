@@ -29,6 +29,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 
 #include "kernels.h"
@@ -175,6 +176,7 @@ struct TcArgs {
   int n_tiles_m, n_tiles_n, kblocks;
   int NT;              // rows of the prepared B per batch
   int scatter;         // 1: write C through sc
+  int tma_store;       // 1: row-major C written by bulk tensor stores (tmC)
   CScatter sc;
 };
 
@@ -198,7 +200,8 @@ struct TcSmem {
   static constexpr uint32_t A_HI = MODE == MODE_TF32 ? 0 : A_BYTES;                  // offset of A hi
   static constexpr uint32_t STAGE = A_BYTES + (MODE == MODE_TF32 ? AS_BYTES : 2 * AS_BYTES) + 2 * B_BYTES;
   static constexpr uint32_t BARS = 512;                                // barriers and flags
-  static constexpr uint32_t TOTAL = STAGES * STAGE + BARS + 1024 + 1024;  // + column offsets, alignment
+  static constexpr uint32_t STAGING = 4 * 2 * 2048;                    // epilogue: 4 warps x 2 x (32 rows x 64 B)
+  static constexpr uint32_t TOTAL = STAGES * STAGE + STAGING + BARS + 1024 + 1024;  // + column offsets, alignment
   static constexpr uint32_t ACC_COLS = BNP < 32 ? 32 : BNP;
   static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
 };
@@ -210,11 +213,11 @@ struct TcSmem {
 template <int MODE, int BNP, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_split3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
-                     const __grid_constant__ CUtensorMap tmBl, TcArgs a) {
+                     const __grid_constant__ CUtensorMap tmBl, const __grid_constant__ CUtensorMap tmC, TcArgs a) {
   using L = TcSmem<MODE, BNP, STAGES>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * L::STAGE);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * L::STAGE + L::STAGING);
   uint64_t *conv = full + STAGES;
   uint64_t *empty = conv + STAGES;
   uint64_t *tfull = empty + STAGES;  // [2] accumulator ready for the epilogue
@@ -222,7 +225,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t *drain = tempty + 2;      // all products retired
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-  int64_t *coloff = reinterpret_cast<int64_t *>(smem + STAGES * L::STAGE + L::BARS);
+  int64_t *coloff = reinterpret_cast<int64_t *>(smem + STAGES * L::STAGE + L::STAGING + L::BARS);
+  uint8_t *staging = smem + STAGES * L::STAGE;  // 1024-aligned
   auto A_raw = [&](int s) { return smem + s * L::STAGE; };
   auto A_hi = [&](int s) { return smem + s * L::STAGE + L::A_HI; };
   auto A_lo = [&](int s) { return smem + s * L::STAGE + L::A_LO; };
@@ -419,6 +423,36 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (n0 + c / 2 + j < a.N)
               a.C[om + coloff[c / 2 + j]] = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
         }
+      } else if (a.tma_store) {
+        // 16 columns (8 complex) at a time: this warp's 32 rows go to its
+        // staging buffer in the 64-byte swizzled layout (16-byte chunk c of
+        // row r at chunk c ^ ((r >> 1) & 3)), then one bulk tensor store.
+        uint8_t *stg = staging + (warp - 6) * 4096;
+        const int y = (int)(d.z * a.M + (int64_t)d.mt * BM + q * 32);
+#pragma unroll 1
+        for (int c = 0; c < BNP; c += 16) {
+          uint32_t r[16];
+          tmem_ld16(taddr + (uint32_t)c, r);
+          if (n0 + c / 2 >= a.N) break;
+          uint8_t *buf = stg + (((c >> 4) & 1) << 11);
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < 4; j++) {
+            const int pc = j ^ ((lane >> 1) & 3);
+            *reinterpret_cast<uint4 *>(buf + lane * 64 + pc * 16) =
+                make_uint4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) {
+            asm volatile(
+                "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"((uint64_t)&tmC),
+                "r"((int)(2 * n0 + c)), "r"(y), "r"(smem_u32(buf))
+                : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          }
+        }
       } else {
         float2 *crow = a.C + d.z * a.sC + ((int64_t)d.mt * BM + row) * a.N;
 #pragma unroll 1
@@ -443,6 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_arrive(&tempty[b]);
     }
   }
+  if (warp >= 6 && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -530,8 +565,8 @@ int tile_cols(int64_t N) {  // real columns per tile (power of two, 16..256)
 }
 
 template <int MODE, int BNP, int STAGES>
-cudaError_t run_tc(const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensorMap &tbl, const TcArgs &args,
-                   int64_t n_blocks, cudaStream_t s) {
+cudaError_t run_tc(const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensorMap &tbl, const CUtensorMap &tc,
+                   const TcArgs &args, int64_t n_blocks, cudaStream_t s) {
   using L = TcSmem<MODE, BNP, STAGES>;
   static_assert(L::TOTAL <= 227 * 1024, "shared memory budget");
   static bool attr = false;
@@ -541,19 +576,19 @@ cudaError_t run_tc(const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensor
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  tc_split3_kernel<MODE, BNP, STAGES><<<(unsigned)n_blocks, kThreads, L::TOTAL, s>>>(ta, tbh, tbl, args);
+  tc_split3_kernel<MODE, BNP, STAGES><<<(unsigned)n_blocks, kThreads, L::TOTAL, s>>>(ta, tbh, tbl, tc, args);
   return cudaGetLastError();
 }
 
 template <int MODE>
 cudaError_t dispatch(int bnp, const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensorMap &tbl,
-                     const TcArgs &args, int64_t n_blocks, cudaStream_t s) {
+                     const CUtensorMap &tc, const TcArgs &args, int64_t n_blocks, cudaStream_t s) {
   switch (bnp) {
-    case 16: return run_tc<MODE, 16, 4>(ta, tbh, tbl, args, n_blocks, s);
-    case 32: return run_tc<MODE, 32, 4>(ta, tbh, tbl, args, n_blocks, s);
-    case 64: return run_tc<MODE, 64, 4>(ta, tbh, tbl, args, n_blocks, s);
-    case 128: return run_tc<MODE, 128, 3>(ta, tbh, tbl, args, n_blocks, s);
-    default: return run_tc<MODE, 256, MODE == MODE_TF32 ? 2 : 3>(ta, tbh, tbl, args, n_blocks, s);
+    case 16: return run_tc<MODE, 16, 4>(ta, tbh, tbl, tc, args, n_blocks, s);
+    case 32: return run_tc<MODE, 32, 4>(ta, tbh, tbl, tc, args, n_blocks, s);
+    case 64: return run_tc<MODE, 64, 4>(ta, tbh, tbl, tc, args, n_blocks, s);
+    case 128: return run_tc<MODE, 128, 3>(ta, tbh, tbl, tc, args, n_blocks, s);
+    default: return run_tc<MODE, 256, MODE == MODE_TF32 ? 2 : 3>(ta, tbh, tbl, tc, args, n_blocks, s);
   }
 }
 
@@ -627,8 +662,23 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
     if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 148;
   }
   const int64_t n_blocks = std::min<int64_t>(n_tiles, n_sm);
-  return bf16 ? dispatch<MODE_BF16>(bnp, ta, tbh, tbl, args, n_blocks, s)
-              : dispatch<MODE_TF32>(bnp, ta, tbh, tbl, args, n_blocks, s);
+  // row-major C with 16-byte aligned rows: bulk tensor stores of 32-row x
+  // 16-float boxes (64-byte swizzle), clipped at the tensor edge
+  CUtensorMap tcm;
+  std::memset(&tcm, 0, sizeof(tcm));
+  if (!sc && sC == M * N && (N % 2) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0) {
+    auto fn = encode_fn();
+    cuuint64_t dims[2] = {(cuuint64_t)(2 * N), (cuuint64_t)(batch * M)};
+    cuuint64_t strides[1] = {(cuuint64_t)(2 * N * 4)};
+    cuuint32_t box[2] = {16, 32};
+    cuuint32_t estr[2] = {1, 1};
+    if (fn && fn(&tcm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, C, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                 CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+      args.tma_store = 1;
+  }
+  return bf16 ? dispatch<MODE_BF16>(bnp, ta, tbh, tbl, tcm, args, n_blocks, s)
+              : dispatch<MODE_TF32>(bnp, ta, tbh, tbl, tcm, args, n_blocks, s);
 }
 
 int tc_take_error() {

@@ -5,8 +5,10 @@
 // (1024 elements, 8 KB of shared memory), so loads and stores both move
 // runs of >= 32 consecutive elements (256 bytes per warp access). The
 // tile-local offsets are the same for every tile and are computed once per
-// thread; shared memory is XOR-swizzled (low 5 index bits ^= high 5) so
-// neither the row-wise writes nor the column-wise reads conflict on banks.
+// thread. Each thread moves pairs of consecutive elements (16-byte global
+// accesses: input bit 0 and output bit 0 are both inside the tile's runs);
+// shared memory is XOR-swizzled on index bits 1..4 (by bits 5..8), which
+// keeps pair partners adjacent and spreads both access orders over banks.
 #include <algorithm>
 
 #include "kernels.h"
@@ -30,7 +32,7 @@ struct TileMap {
   int8_t rout[kMaxBits];    // output bit of tile-index bit j
 };
 
-__device__ __forceinline__ int swz(int e) { return e ^ ((e >> 5) & 31); }
+__device__ __forceinline__ int swz(int e) { return e ^ (((e >> 5) & 15) << 1); }
 
 __global__ void permute_small_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, PermuteArgs a) {
   const int64_t n = int64_t(1) << a.rank;
@@ -41,31 +43,35 @@ __global__ void permute_small_kernel(const float2 *__restrict__ in, float2 *__re
   }
 }
 
-// u == kTile (rank >= 10): every thread moves kPer elements per tile.
+// u == kTile (rank >= 10): every thread moves kPer elements (kPer/2 pairs)
+// per tile.
 __global__ void __launch_bounds__(kThreads) permute_tiled_kernel(const float2 *__restrict__ in,
-                                                                 float2 *__restrict__ out, const __grid_constant__ TileMap m,
-                                                                 int64_t n_tiles) {
-  __shared__ float2 tile[1 << kTile];
-  // tile-local offsets, identical for every tile
-  int64_t ld_off[kPer], st_off[kPer];
-  int ld_s[kPer], st_s[kPer];
+                                                                 float2 *__restrict__ out,
+                                                                 const __grid_constant__ TileMap m, int64_t n_tiles) {
+  __shared__ __align__(16) float2 tile[1 << kTile];
+  constexpr int kPairs = kPer / 2;
+  // tile-local offsets of each pair, identical for every tile
+  int64_t ld_off[kPairs], st_off[kPairs];
+  int ld_s[kPairs], st_s0[kPairs], st_s1[kPairs];
 #pragma unroll
-  for (int i = 0; i < kPer; i++) {
-    const int e = threadIdx.x + i * kThreads;  // load order
+  for (int i = 0; i < kPairs; i++) {
+    const int e = 2 * (threadIdx.x + i * kThreads);  // load order, even
     int64_t o = 0;
     for (int j = 0; j < kTile; j++) o |= int64_t((e >> j) & 1) << m.uin[j];
     ld_off[i] = o;
     ld_s[i] = swz(e);
-    const int f = e;  // store order
+    const int f = e;  // store order, even
     int64_t oo = 0;
-    int src = 0;
+    int src0 = 0, src1 = 0;
     for (int j = 0; j < kTile; j++) {
-      const int b = (f >> j) & 1;
-      oo |= int64_t(b) << m.vout[j];
-      src |= b << m.vsrc[j];
+      const int b0 = (f >> j) & 1, b1 = ((f + 1) >> j) & 1;
+      oo |= int64_t(b0) << m.vout[j];
+      src0 |= b0 << m.vsrc[j];
+      src1 |= b1 << m.vsrc[j];
     }
     st_off[i] = oo;
-    st_s[i] = swz(src);
+    st_s0[i] = swz(src0);
+    st_s1[i] = swz(src1);
   }
   const int nr = m.r - kTile;
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
@@ -75,14 +81,17 @@ __global__ void __launch_bounds__(kThreads) permute_tiled_kernel(const float2 *_
       bin |= b << m.rin[j];
       bout |= b << m.rout[j];
     }
-    float2 v[kPer];
+    float4 v[kPairs];
 #pragma unroll
-    for (int i = 0; i < kPer; i++) v[i] = __ldcs(in + bin + ld_off[i]);
+    for (int i = 0; i < kPairs; i++) v[i] = __ldcs(reinterpret_cast<const float4 *>(in + bin + ld_off[i]));
 #pragma unroll
-    for (int i = 0; i < kPer; i++) tile[ld_s[i]] = v[i];
+    for (int i = 0; i < kPairs; i++) *reinterpret_cast<float4 *>(&tile[ld_s[i]]) = v[i];
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < kPer; i++) __stcs(out + bout + st_off[i], tile[st_s[i]]);
+    for (int i = 0; i < kPairs; i++) {
+      const float2 a = tile[st_s0[i]], b = tile[st_s1[i]];
+      __stcs(reinterpret_cast<float4 *>(out + bout + st_off[i]), make_float4(a.x, a.y, b.x, b.y));
+    }
     __syncthreads();
   }
 }

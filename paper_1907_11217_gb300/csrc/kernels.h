@@ -70,6 +70,15 @@ struct CScatter {
   int8_t pm[kMaxBits], pn[kMaxBits], pb[kMaxBits];
 };
 
+// Operand maps of a skinny product read in place (no permute): element
+// (z, m, k) of X sits at offset sum of bit j of m << xm[j] (likewise k, z),
+// and element (z, n, k) of Y at the offsets given by yn, yk, yb.
+struct GatherMap {
+  int nm, nn, nk, nb;
+  int8_t xm[kMaxBits], xk[8], xb[kMaxBits];
+  int8_t yn[8], yk[8], yb[kMaxBits];
+};
+
 struct PermuteArgs {
   int rank;
   int8_t perm[kMaxBits];  // out bit p = in bit perm[p]
@@ -94,6 +103,10 @@ cudaError_t launch_permute(const float2 *in, float2 *out, const PermuteArgs &a, 
 // sc == nullptr: C row-major with batch stride sC.
 cudaError_t launch_cgemm_simt(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N,
                               int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s);
+// Skinny product (n <= 4, k <= 16) reading X and Y through gather maps and
+// writing C through sc (nullptr: row-major [batch][m][n]).
+cudaError_t launch_cgemm_skinny_gather(const float2 *X, const float2 *Y, float2 *C, int64_t batch, int64_t M,
+                                       int64_t N, int64_t K, const GatherMap &g, const CScatter *sc, cudaStream_t s);
 // Split-precision tensor-core product; returns cudaErrorNotSupported when the
 // shape is outside what the kernel handles (the planner checks first).
 cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M,

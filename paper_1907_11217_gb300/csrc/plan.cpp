@@ -170,6 +170,22 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
     const auto &fy = roleX[s] == st.a ? st.freeB : st.freeA;
     return concat3(fy, fx, st.batch);
   };
+  // GEMM shapes and kernels, known before any layout
+  for (int s = 0; s < NS; s++) {
+    const StepInfo &st = ti.steps[s];
+    PStep &ps = p->S[s];
+    if (!ps.gemm) continue;
+    const bool xa = roleX[s] == st.a;
+    ps.M = int64_t(1) << (xa ? st.freeA : st.freeB).size();
+    ps.N = int64_t(1) << (xa ? st.freeB : st.freeA).size();
+    ps.K = int64_t(1) << st.contr.size();
+    ps.batch = int64_t(1) << st.batch.size();
+    // skinny products are memory-bound: the streaming SIMT kernel serves them
+    ps.tc = o.precision != TZ_C64_SIMT && dev::cgemm_tc_supported(o.precision, ps.M, ps.N, ps.K) &&
+            !(ps.N <= 4 && ps.K <= 16);
+    ps.skinny = !ps.tc && ps.N <= 4 && ps.K <= 16 && ps.M >= 256;
+    if (ps.tc) ps.tc_scratch = (int64_t)dev::cgemm_tc_scratch_bytes(o.precision, ps.batch, ps.N, ps.K);
+  }
   p->T[p->root].lay = natural(p->root);
   p->T[p->root].fixed = true;
   for (int s = NS - 1; s >= 0; s--) {
@@ -180,6 +196,12 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
       p->T[st.c].fixed = true;
     }
     if (!ps.gemm) continue;
+    if (ps.skinny) {
+      // operands are read in place: their producers keep their own order
+      ps.opX = roleX[s];
+      ps.opY = roleX[s] == st.a ? st.b : st.a;
+      continue;
+    }
     const std::vector<int> &Lc = p->T[st.c].lay;
     const int X = roleX[s], Y = X == st.a ? st.b : st.a;
     const std::vector<int> &fX = X == st.a ? st.freeA : st.freeB;
@@ -194,14 +216,6 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
     p->T[X].fixed = p->T[Y].fixed = true;
     ps.opX = X;
     ps.opY = Y;
-    ps.M = int64_t(1) << fX.size();
-    ps.N = int64_t(1) << fY.size();
-    ps.K = int64_t(1) << st.contr.size();
-    ps.batch = int64_t(1) << st.batch.size();
-    // skinny products are memory-bound: the streaming SIMT kernel serves them
-    ps.tc = o.precision != TZ_C64_SIMT && dev::cgemm_tc_supported(o.precision, ps.M, ps.N, ps.K) &&
-            !(ps.N <= 4 && ps.K <= 16);
-    if (ps.tc) ps.tc_scratch = (int64_t)dev::cgemm_tc_scratch_bytes(o.precision, ps.batch, ps.N, ps.K);
     // where canonical (z, m, n) lands in C
     dev::CScatter &sc = ps.scatter;
     std::memset(&sc, 0, sizeof(sc));
@@ -221,6 +235,46 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
       p->T[n].lay = set_of(n);
       p->T[n].fixed = true;
     }
+  // skinny steps: rows numbered in the order of X's storage (so a warp's loads
+  // stay together), then the gather maps of both operands and the scatter map
+  for (int s = 0; s < NS; s++) {
+    PStep &ps = p->S[s];
+    if (!ps.gemm || !ps.skinny) continue;
+    const StepInfo &st = ti.steps[s];
+    const std::vector<int> &LX = p->T[ps.opX].lay, &LY = p->T[ps.opY].lay, &Lc = p->T[ps.c].lay;
+    const std::vector<int> &fX = ps.opX == st.a ? st.freeA : st.freeB;
+    const std::vector<int> &fY = ps.opX == st.a ? st.freeB : st.freeA;
+    const std::vector<int> fxo = rel_order(LX, fX), ko = rel_order(LX, st.contr), bo = rel_order(LX, st.batch);
+    const std::vector<int> fyo = rel_order(LY, fY);
+    dev::GatherMap &g = ps.gather;
+    std::memset(&g, 0, sizeof(g));
+    g.nm = (int)fxo.size();
+    g.nn = (int)fyo.size();
+    g.nk = (int)ko.size();
+    g.nb = (int)bo.size();
+    for (int j = 0; j < g.nm; j++) g.xm[j] = (int8_t)pos_of(LX, fxo[j]);
+    for (int j = 0; j < g.nk; j++) {
+      g.xk[j] = (int8_t)pos_of(LX, ko[j]);
+      g.yk[j] = (int8_t)pos_of(LY, ko[j]);
+    }
+    for (int j = 0; j < g.nb; j++) {
+      g.xb[j] = (int8_t)pos_of(LX, bo[j]);
+      g.yb[j] = (int8_t)pos_of(LY, bo[j]);
+    }
+    for (int j = 0; j < g.nn; j++) g.yn[j] = (int8_t)pos_of(LY, fyo[j]);
+    dev::CScatter &sc = ps.scatter;
+    std::memset(&sc, 0, sizeof(sc));
+    sc.nm = g.nm;
+    sc.nn = g.nn;
+    sc.nb = g.nb;
+    for (int j = 0; j < sc.nm; j++) sc.pm[j] = (int8_t)pos_of(Lc, fxo[j]);
+    for (int j = 0; j < sc.nn; j++) sc.pn[j] = (int8_t)pos_of(Lc, fyo[j]);
+    for (int j = 0; j < sc.nb; j++) sc.pb[j] = (int8_t)pos_of(Lc, bo[j]);
+    ps.row_major = true;
+    for (int j = 0; j < sc.nn; j++) ps.row_major &= sc.pn[j] == j;
+    for (int j = 0; j < sc.nm; j++) ps.row_major &= sc.pm[j] == sc.nn + j;
+    for (int j = 0; j < sc.nb; j++) ps.row_major &= sc.pb[j] == sc.nn + sc.nm + j;
+  }
   // A GEMM epilogue writes its consumer's layout directly only when the two
   // lowest bits of that layout are bits it writes contiguously (rows across a
   // warp, or a thread's run of columns); otherwise whole sectors would be
@@ -233,7 +287,7 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
     if (Lc.size() < 2) continue;
     const dev::CScatter &sc = ps.scatter;
     std::vector<int> good;  // positions in Lc written contiguously
-    const bool skinny = ps.N <= 4 && ps.K <= 16 && ps.M >= 256 && !ps.tc;
+    const bool skinny = ps.skinny;
     const int m_run = ps.tc || skinny ? 5 : 2, n_run = ps.tc ? 3 : skinny ? sc.nn : 4;
     for (int j = 0; j < std::min(sc.nm, m_run); j++) good.push_back(sc.pm[j]);
     for (int j = 0; j < std::min(sc.nn, n_run); j++) good.push_back(sc.pn[j]);
@@ -617,7 +671,19 @@ std::string plan_describe(const tz_plan *p) {
       << ",\"gemm\":" << x.gemm << ",\"tc\":" << x.tc << ",\"opX\":" << x.opX << ",\"opY\":" << x.opY
       << ",\"M\":" << x.M << ",\"N\":" << x.N << ",\"K\":" << x.K << ",\"batch\":" << x.batch
       << ",\"level\":" << x.level << ",\"dstep\":" << x.dstep << ",\"permX\":" << x.permX << ",\"permY\":" << x.permY
-      << ",\"row_major\":" << x.row_major << ",\"c_nat\":" << x.c_nat << ",\"pm\":[";
+      << ",\"row_major\":" << x.row_major << ",\"c_nat\":" << x.c_nat << ",\"skinny\":" << x.skinny;
+    auto arr = [&](const char *name, const int8_t *v, int n) {
+      o << ",\"" << name << "\":[";
+      for (int j = 0; j < n; j++) o << (j ? "," : "") << (int)v[j];
+      o << "]";
+    };
+    arr("xm", x.gather.xm, x.gather.nm);
+    arr("xk", x.gather.xk, x.gather.nk);
+    arr("xb", x.gather.xb, x.gather.nb);
+    arr("yn", x.gather.yn, x.gather.nn);
+    arr("yk", x.gather.yk, x.gather.nk);
+    arr("yb", x.gather.yb, x.gather.nb);
+    o << ",\"pm\":[";
     for (int j = 0; j < x.scatter.nm; j++) o << (j ? "," : "") << (int)x.scatter.pm[j];
     o << "],\"pn\":[";
     for (int j = 0; j < x.scatter.nn; j++) o << (j ? "," : "") << (int)x.scatter.pn[j];
@@ -797,7 +863,10 @@ static void run_items(tz_plan *p, const std::vector<Item> &items, const RunCtx &
         const float2 *Y = (const float2 *)tensor_ptr(p, ctx, ps.opY);
         float2 *C = (float2 *)tensor_ptr(p, ctx, ps.c_nat >= 0 ? ps.c_nat : ps.c);
         const dev::CScatter *sc = ps.row_major ? nullptr : &ps.scatter;
-        if (ps.tc) {
+        if (ps.skinny) {
+          cuda_check(dev::launch_cgemm_skinny_gather(X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.gather, sc, s),
+                     "skinny gemm");
+        } else if (ps.tc) {
           void *scr = abase + ps.tc_scratch_off;
           cuda_check(dev::launch_cgemm_tc(p->opts.precision, X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.M * ps.K,
                                           ps.N * ps.K, ps.M * ps.N, sc, scr, (size_t)ps.tc_scratch, s),

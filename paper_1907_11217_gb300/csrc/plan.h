@@ -37,6 +37,8 @@ struct PStep {
   bool row_major = false;     // scatter is the plain row-major order
   int c_nat = -1;             // tensor the GEMM writes in row-major order when a
                               // permute then moves it into c's layout
+  bool skinny = false;        // n <= 4, k <= 16: operands read in place
+  dev::GatherMap gather{};    // skinny: where the operands' elements sit
 };
 
 struct Item {

@@ -127,3 +127,21 @@ def test_tensor_core_path_5x6(tz, prec):
     else:
         assert prof["gemm_tc"]["launches"] > 0
         assert err <= (TOL_C64 if prec == "tf32x3" else 1e-3)
+
+
+@pytest.mark.parametrize("rows,cols,t,seed,g,small", [(5, 5, 20, 11, 4, 5), (6, 6, 16, 3, 0, 6)])
+def test_in_place_skinny_steps(tz, rows, cols, t, seed, g, small):
+    """Plans whose skinny products read their operands in the producers'
+    storage order (gather maps) and write through scatter maps, with the
+    remaining operand permutes; against the plain-wire contractor."""
+    import json
+    spec = grid_spec(rows, cols, t, seed)
+    n = rows * cols
+    bits = ti.random_bitstrings(n, 1 << g, seed + 5)
+    plan, *_ = make_plan(tz, spec, batch_log2=g, small_log2=small, restarts=8, seed=3, max_bitstrings=1 << g)
+    d = json.loads(plan.describe())
+    assert sum(s["skinny"] for s in d["steps"]) >= 2
+    got = tz.tz_contract_amplitudes(plan, bits)
+    c = tn.Contractor(spec, max_log2=24)
+    ref = np.array([c.amplitude(x) for x in bits])
+    assert rel_err(got, ref, n) <= TOL_C64
