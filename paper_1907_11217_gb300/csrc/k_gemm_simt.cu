@@ -246,35 +246,57 @@ __global__ void __launch_bounds__(256)
                          const __grid_constant__ CScatter sc, int scatter) {
   __shared__ float2 Ys[NMAX * KMAX];
   __shared__ int64_t xk_off[KMAX];
+  __shared__ int64_t cn_off[NMAX];
+  __shared__ int64_t hi_off[2];  // block-uniform part of the X and C offsets
   constexpr int ROWS = 256 * RPT;
+  static_assert(ROWS == 1024 || ROWS == 512, "rows per block");
+  constexpr int LOW = ROWS == 1024 ? 10 : 9;  // row bits owned by the thread
+  // offsets of this thread's rows within a block: the row index bits below
+  // LOW come from threadIdx and r only, so they are computed once
+  int64_t xlo[RPT], clo[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; r++) {
+    const int64_t m = threadIdx.x + r * 256;
+    xlo[r] = scatter_bits(m, g.nm < LOW ? g.nm : LOW, g.xm);
+    clo[r] = scatter ? scatter_bits(m, sc.nm < LOW ? sc.nm : LOW, sc.pm) : m * N;
+  }
   const int64_t blocks_per_batch = (M + ROWS - 1) / ROWS;
   for (int64_t blk = blockIdx.x; blk < blocks_per_batch * batch; blk += gridDim.x) {
     const int64_t z = blk / blocks_per_batch;
-    const int64_t m0 = (blk - z * blocks_per_batch) * ROWS + threadIdx.x;
-    const int64_t xb = scatter_bits(z, g.nb, g.xb), yb = scatter_bits(z, g.nb, g.yb);
-    const int64_t cb = scatter ? scatter_bits(z, sc.nb, sc.pb) : z * M * N;
+    const int64_t mb = (blk - z * blocks_per_batch) * ROWS;
     __syncthreads();
     if (threadIdx.x < N * K) {
       const int n = threadIdx.x / K, k = threadIdx.x % K;
-      Ys[threadIdx.x] = Y[yb + scatter_bits(n, g.nn, g.yn) + scatter_bits(k, g.nk, g.yk)];
+      Ys[threadIdx.x] = Y[scatter_bits(z, g.nb, g.yb) + scatter_bits(n, g.nn, g.yn) + scatter_bits(k, g.nk, g.yk)];
     }
     if (threadIdx.x < K) xk_off[threadIdx.x] = scatter_bits(threadIdx.x, g.nk, g.xk);
+    if (threadIdx.x >= 64 && threadIdx.x < 64 + N)
+      cn_off[threadIdx.x - 64] = scatter ? scatter_bits(threadIdx.x - 64, sc.nn, sc.pn) : threadIdx.x - 64;
+    if (threadIdx.x == 128) {
+      int64_t xh = scatter_bits(z, g.nb, g.xb), ch = scatter ? scatter_bits(z, sc.nb, sc.pb) : z * M * N;
+      for (int j = LOW; j < g.nm; j++) xh |= ((mb >> j) & 1) << g.xm[j];
+      if (scatter)
+        for (int j = LOW; j < sc.nm; j++) ch |= ((mb >> j) & 1) << sc.pm[j];
+      else
+        ch += mb * N;
+      hi_off[0] = xh;
+      hi_off[1] = ch;
+    }
     __syncthreads();
+    const int64_t xh = hi_off[0], ch = hi_off[1];
     float2 a[RPT][KMAX];
 #pragma unroll
     for (int r = 0; r < RPT; r++) {
-      const int64_t m = m0 + r * 256;
-      if (m >= M) continue;
-      const float2 *xr = X + xb + scatter_bits(m, g.nm, g.xm);
+      if (mb + threadIdx.x + r * 256 >= M) continue;
+      const float2 *xr = X + xh + xlo[r];
 #pragma unroll
       for (int k = 0; k < KMAX; k++)
         if (k < K) a[r][k] = __ldcs(xr + xk_off[k]);
     }
 #pragma unroll
     for (int r = 0; r < RPT; r++) {
-      const int64_t m = m0 + r * 256;
-      if (m >= M) continue;
-      const int64_t om = cb + (scatter ? scatter_bits(m, sc.nm, sc.pm) : m * N);
+      if (mb + threadIdx.x + r * 256 >= M) continue;
+      const int64_t om = ch + clo[r];
 #pragma unroll
       for (int n = 0; n < NMAX; n++) {
         if (n >= N) break;
@@ -288,7 +310,7 @@ __global__ void __launch_bounds__(256)
             acc.y = fmaf(a[r][k].x, b.y, acc.y);
             acc.y = fmaf(a[r][k].y, b.x, acc.y);
           }
-        C[om + (scatter ? scatter_bits(n, sc.nn, sc.pn) : n)] = acc;
+        __stcs(C + om + cn_off[n], acc);
       }
     }
   }

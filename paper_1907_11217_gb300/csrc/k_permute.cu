@@ -73,14 +73,22 @@ __global__ void __launch_bounds__(kThreads) permute_tiled_kernel(const float2 *_
     st_s0[i] = swz(src0);
     st_s1[i] = swz(src1);
   }
+  __shared__ int64_t base[2];
   const int nr = m.r - kTile;
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    int64_t bin = 0, bout = 0;
-    for (int j = 0; j < nr; j++) {
-      const int64_t b = (t >> j) & 1;
-      bin |= b << m.rin[j];
-      bout |= b << m.rout[j];
+    // the tile's base offsets are block-uniform: one thread computes them
+    if (threadIdx.x == 0) {
+      int64_t bin = 0, bout = 0;
+      for (int j = 0; j < nr; j++) {
+        const int64_t b = (t >> j) & 1;
+        bin |= b << m.rin[j];
+        bout |= b << m.rout[j];
+      }
+      base[0] = bin;
+      base[1] = bout;
     }
+    __syncthreads();
+    const int64_t bin = base[0], bout = base[1];
     float4 v[kPairs];
 #pragma unroll
     for (int i = 0; i < kPairs; i++) v[i] = __ldcs(reinterpret_cast<const float4 *>(in + bin + ld_off[i]));
