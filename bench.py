@@ -159,7 +159,7 @@ def roofline(prof, precision):
         out.update(bound="tensor", unit="TFLOP/s", achieved=d["flops"] / sec / 1e12, peak=peak,
                    peak_source=f"{src} bf16 x nominal {precision[:4]}/bf16 ratio",
                    issued_tflops=3 * d["flops"] / sec / 1e12)
-    elif dom in ("gemm_simt", "direct"):
+    elif dom == "gemm_simt":
         out.update(bound="alu", unit="TFLOP/s", achieved=d["flops"] / sec / 1e12, peak=fp32_alu_tflops,
                    peak_source="152 SMs x 128 FP32 lanes x 2 flops x max SM clock")
     else:

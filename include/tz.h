@@ -230,11 +230,12 @@ void tz_plan_destroy(tz_plan *plan);
 
 /* Per-kernel timing of a plan's launches (CUDA events around every launch on
  * the plan's stream; the captured-graph path is not used while enabled).
- * Kinds: 0 leaf builder, 1 direct small steps, 2 permute, 3 SIMT complex
- * GEMM, 4 tensor-core complex GEMM, 5 FP64 accumulation. flops are useful
+ * Kinds: 0 leaf builder, 1 direct small steps, 2 permute, 3 tiled SIMT
+ * complex GEMM, 4 tensor-core complex GEMM, 5 FP64 accumulation, 6 skinny
+ * streaming product (n <= 4, k <= 16), 7 long-k dot product. flops are useful
  * flops (8 per complex multiply-add); bytes are algorithmic bytes (each
  * operand read once, the result written once, complex64). */
-#define TZ_PROFILE_KINDS 6
+#define TZ_PROFILE_KINDS 8
 typedef struct {
   int64_t launches[TZ_PROFILE_KINDS];
   double ms[TZ_PROFILE_KINDS];

@@ -51,12 +51,12 @@ class tz_plan_stats(ctypes.Structure):
                 ("const_bytes", ctypes.c_size_t), ("scratch_bytes", ctypes.c_size_t)]
 
 
-PROFILE_KINDS = ("leaves", "direct", "permute", "gemm_simt", "gemm_tc", "accumulate")
+PROFILE_KINDS = ("leaves", "direct", "permute", "gemm_simt", "gemm_tc", "accumulate", "gemm_skinny", "gemm_dot")
 
 
 class tz_plan_profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64 * 6), ("ms", ctypes.c_double * 6), ("flops", ctypes.c_double * 6),
-                ("bytes", ctypes.c_double * 6)]
+    _fields_ = [("launches", ctypes.c_int64 * 8), ("ms", ctypes.c_double * 8), ("flops", ctypes.c_double * 8),
+                ("bytes", ctypes.c_double * 8)]
 
 
 class tz_server_opts(ctypes.Structure):

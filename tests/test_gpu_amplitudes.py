@@ -123,7 +123,8 @@ def test_tensor_core_path_5x6(tz, prec):
     print(f"{prec}: max rel err {err:.3e}, tc launches {prof['gemm_tc']['launches']}")
     if prec == "c64":
         assert err <= TOL_C64
-        assert prof["gemm_tc"]["launches"] == 0 and prof["gemm_simt"]["launches"] > 0
+        assert prof["gemm_tc"]["launches"] == 0
+        assert prof["gemm_simt"]["launches"] + prof["gemm_skinny"]["launches"] > 0
     else:
         assert prof["gemm_tc"]["launches"] > 0
         assert err <= (TOL_C64 if prec == "tf32x3" else 1e-3)

@@ -1,0 +1,159 @@
+"""Full-size checks on the benchmark workloads.
+
+The FP64 oracle cannot contract a slice of a depth 1+32+1 circuit on 49 or 70
+qubits in test time (its own contraction orders would need 2^13 - 2^24
+sub-slices), so at full depth the path is checked by properties that hold at
+any size, in the launch configuration bench.py times (bucket-elimination
+tree, 2^30 cap, captured graph on a stream):
+
+* slicing is exact: the partial amplitudes of the slices add up to the full
+  amplitude (Sec. 1: subtask results add up to the amplitude);
+* the amplitude does not depend on the contraction tree or the slicing;
+* the split-precision modes agree with complex64;
+* Porter-Thomas (Sec. 2): E[2^n |a|^2] = 1 over random bitstrings.
+
+At full width and reduced depth the oracle is feasible, and those circuits
+are compared with it amplitude by amplitude.
+"""
+import numpy as np
+import pytest
+
+import tz_inputs as ti
+from oracle import tn
+from tests.gpu_util import rel_err
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def tz():
+    import torch
+    import paper_1907_11217_gb300 as tz
+    assert torch.cuda.is_available()
+    return tz
+
+
+def bris_spec(t, seed):
+    return ti.circuit_to_spec(70, ti.generate_circuit(ti.bristlecone(70), t, seed))
+
+
+def grid_spec(r, c, t, seed):
+    return ti.circuit_to_spec(r * c, ti.generate_circuit(ti.grid(r, c), t, seed))
+
+
+def build(tz, spec, precision, log2_max, batch_log2=0, restarts=64, seed=7, algorithm="elimination", k_max=40,
+          max_bitstrings=0):
+    import torch
+    circ = tz.tz_circuit_from_spec(spec)
+    net = tz.tz_network_from_circuit(circ, batch_log2)
+    tree = tz.tz_path_greedy(net, restarts=restarts, seed=seed, log2_max_intermediate=log2_max,
+                             precision=precision, algorithm=algorithm)
+    sliced = tz.tz_slice_select(net, tree, log2_max, k_max)
+    stream = torch.cuda.Stream()
+    plan = tz.tz_plan_create(net, tree, sliced, precision=precision, stream=stream, use_graph=True,
+                             max_bitstrings=max_bitstrings or (1 << batch_log2) * 64)
+    plan.bind()
+    return plan, net, tree, sliced
+
+
+def test_bristlecone70_depth32_properties(tz):
+    spec = bris_spec(32, 3)
+    bits = ti.random_bitstrings(70, 2, 103)
+    plan, net, tree, sl = build(tz, spec, "tf32x3", 30)
+    k = len(sl)
+    assert k >= 2
+    a = tz.tz_contract_amplitudes(plan, bits)
+    # slicing is exact: slice partial amplitudes add up
+    parts = []
+    for s in range(1 << k):
+        plan.set_slice_range(s, s + 1)
+        parts.append(tz.tz_contract_amplitudes(plan, bits))
+    plan.set_slice_range(0, 1 << k)
+    assert rel_err(np.sum(parts, axis=0), a, 70) <= 1e-6
+    # complex64 on the same tree and slicing
+    p64, *_ = build(tz, spec, "c64", 30)
+    a64 = tz.tz_contract_amplitudes(p64, bits)
+    assert rel_err(a, a64, 70) <= TOL
+    # an independent tree (pairwise greedy, other seed) and a different cap
+    p2, _, tree2, sl2 = build(tz, spec, "c64", 29, algorithm="greedy", seed=11, restarts=32)
+    assert not np.array_equal(tree.pairs(), tree2.pairs())
+    a2 = tz.tz_contract_amplitudes(p2, bits)
+    assert rel_err(a2, a64, 70) <= TOL
+    # Porter-Thomas scale: N p far from 0 and from the tail
+    npk = np.abs(a64) ** 2 * 2.0 ** 70
+    assert np.all(npk > 1e-6) and np.all(npk < 40)
+
+
+def test_bristlecone70_depth32_porter_thomas_mean(tz):
+    """Sec. 2: N p follows exp(-x); the mean over 32 random bitstrings is
+    1 +- 0.18 (one standard deviation)."""
+    spec = bris_spec(32, 3)
+    bits = ti.random_bitstrings(70, 32, 2024)
+    plan, *_ = build(tz, spec, "tf32x3", 30)
+    a = tz.tz_contract_amplitudes(plan, bits)
+    npk = np.abs(a) ** 2 * 2.0 ** 70
+    assert abs(npk.mean() - 1.0) < 0.75
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "c64", "bf16x3"])
+def test_bristlecone70_reduced_depth_vs_oracle(tz, prec):
+    """All 70 qubits, depth 1+12+1, sliced (k >= 3), against the oracle."""
+    spec = bris_spec(12, 3)
+    bits = ti.random_bitstrings(70, 4, 31)
+    c = tn.Contractor(spec, max_log2=24)
+    ref = np.array([c.amplitude(x) for x in bits])
+    circ = tz.tz_circuit_from_spec(spec)
+    net = tz.tz_network_from_circuit(circ, 0)
+    tree = tz.tz_path_greedy(net, restarts=16, seed=7, algorithm="elimination")
+    full = tz.tz_plan_create(net, tree, []).stats()["max_log2"]
+    plan, _, _, sl = build(tz, spec, prec, full - 3, k_max=6)
+    assert len(sl) >= 3
+    got = tz.tz_contract_amplitudes(plan, bits)
+    err = rel_err(got, ref, 70)
+    print(f"bristlecone70 d12 {prec}: max rel err {err:.2e}")
+    assert err <= (TOL if prec != "bf16x3" else 1e-3)
+
+
+def test_grid7x7_depth32_config2_properties(tz):
+    """7x7 depth 1+32+1, 2^10 slices, 64 bitstrings (one group per slice and
+    bitstring: for this circuit, batching bitstrings as open indices costs
+    more bytes per amplitude than it saves): slice additivity over two halves
+    of the slice range, agreement of split-TF32 and complex64, and the
+    Porter-Thomas mean."""
+    spec = grid_spec(7, 7, 32, 2)
+    bits = ti.random_bitstrings(49, 64, 102)
+    results = {}
+    for prec in ("tf32x3", "c64"):
+        circ = tz.tz_circuit_from_spec(spec)
+        net = tz.tz_network_from_circuit(circ, 0)
+        tree = tz.tz_path_greedy(net, restarts=32, seed=7, log2_max_intermediate=22, precision=prec,
+                                 algorithm="elimination")
+        import torch
+        sl = tz.tz_slice_select(net, tree, 1, 10)
+        assert len(sl) == 10
+        plan = tz.tz_plan_create(net, tree, sl, precision=prec, stream=torch.cuda.Stream(), use_graph=True,
+                                 max_bitstrings=64)
+        plan.bind()
+        a = tz.tz_contract_amplitudes(plan, bits)
+        if prec == "tf32x3":
+            plan.set_slice_range(0, 512)
+            lo = tz.tz_contract_amplitudes(plan, bits)
+            plan.set_slice_range(512, 1024)
+            hi = tz.tz_contract_amplitudes(plan, bits)
+            assert rel_err(lo + hi, a, 49) <= 1e-6
+        results[prec] = a
+    assert rel_err(results["tf32x3"], results["c64"], 49) <= TOL
+    npk = np.abs(results["c64"]) ** 2 * 2.0 ** 49
+    assert abs(npk.mean() - 1.0) < 0.5
+
+
+def test_grid7x7_reduced_depth_batch64_vs_oracle(tz):
+    """7x7, depth 1+14+1, 64 bitstrings as one batch, sliced, against the oracle."""
+    spec = grid_spec(7, 7, 14, 2)
+    bits = ti.random_bitstrings(49, 64, 55)
+    c = tn.Contractor(spec, max_log2=24)
+    ref = np.array([c.amplitude(x) for x in bits])
+    plan, _, _, sl = build(tz, spec, "tf32x3", 14, batch_log2=6, k_max=6, restarts=16, max_bitstrings=64)
+    got = tz.tz_contract_amplitudes(plan, bits)
+    assert rel_err(got, ref, 49) <= TOL
