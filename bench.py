@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bristlecone70_d32", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="auto", choices=["auto", "c64", "tf32x3", "bf16x3"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "c64", "tf32x3", "bf16x3", "c128"])
     ap.add_argument("--batch-log2", type=int, default=0)
     ap.add_argument("--slices", type=int, default=0, help="slices per step (0: auto)")
     ap.add_argument("--log2-max", type=int, default=0, help="slicing target (0: workload default)")

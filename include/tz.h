@@ -166,9 +166,11 @@ int tz_slice_select(const tz_network *net, const tz_tree *tree, int log2_max_int
 #define TZ_C64_SIMT     0   /* complex64, FP32 FMA on CUDA cores (4 real products) */
 #define TZ_TF32X3       1   /* FP32 operands split hi+lo TF32, 3 tcgen05 products  */
 #define TZ_BF16X3       2   /* FP32 operands split hi+lo BF16, 3 tcgen05 products  */
+#define TZ_C128_SIMT    3   /* complex128, FP64 FMA on CUDA cores (reference-grade,
+                               every tensor in FP64; slow on GB300's FP64 units)    */
 
 typedef struct {
-  int precision;         /* TZ_C64_SIMT, TZ_TF32X3 or TZ_BF16X3                    */
+  int precision;         /* TZ_C64_SIMT, TZ_TF32X3, TZ_BF16X3 or TZ_C128_SIMT      */
   int device;            /* CUDA device ordinal                                     */
   void *stream;          /* cudaStream_t the plan launches on (NULL = default)     */
   int small_log2;        /* steps with output and work below this use the direct SIMT kernel (0 = default) */
@@ -291,7 +293,8 @@ int tz_op_permute(const void *in, void *out, int rank, const int32_t *perm, void
  * contraction of Sec. 1's network once operands are laid out):
  * A[z] is m x k row-major (k contiguous), B[z] is n x k row-major,
  * C[z] is m x n row-major; z-th matrices at element offsets z*sa, z*sb, z*sc.
- * precision: TZ_C64_SIMT, TZ_TF32X3 or TZ_BF16X3. The split-precision
+ * precision: TZ_C64_SIMT, TZ_TF32X3, TZ_BF16X3, or TZ_C128_SIMT (then A,
+ * B and C are complex128 arrays). The split-precision
  * modes need device scratch of tz_op_cgemm_scratch_bytes() bytes (256-byte
  * aligned); TZ_EUNSUPPORTED for shapes they do not handle. */
 int tz_op_cgemm(int precision, int64_t batch, int64_t m, int64_t n, int64_t k,

@@ -404,7 +404,7 @@ int tz_op_cgemm_scratch_bytes(int precision, int64_t batch, int64_t m, int64_t n
     if (!tz::dev::cgemm_tc_supported(precision, m, n, k))
       tz::fail(TZ_EUNSUPPORTED, "shape not supported by the tensor-core product");
     *bytes = tz::dev::cgemm_tc_scratch_bytes(precision, batch, n, k);
-  } else if (precision != TZ_C64_SIMT) {
+  } else if (precision != TZ_C64_SIMT && precision != TZ_C128_SIMT) {
     tz::fail(TZ_EINVAL, "unknown precision");
   }
   TZ_CATCH
@@ -416,7 +416,11 @@ int tz_op_cgemm(int precision, int64_t batch, int64_t m, int64_t n, int64_t k, c
   REQUIRE(A && B && C, "NULL argument");
   REQUIRE(batch >= 1 && m >= 1 && n >= 1 && k >= 1, "sizes must be >= 1");
   cudaStream_t s = (cudaStream_t)stream;
-  if (precision == TZ_C64_SIMT) {
+  if (precision == TZ_C128_SIMT) {
+    tz::cuda_check(tz::dev::launch_zgemm_simt((const double2 *)A, (const double2 *)B, (double2 *)C, batch, m, n, k, sa,
+                                              sb, sc, nullptr, s),
+                   "complex128 gemm");
+  } else if (precision == TZ_C64_SIMT) {
     tz::cuda_check(tz::dev::launch_cgemm_simt((const float2 *)A, (const float2 *)B, (float2 *)C, batch, m, n, k, sa,
                                               sb, sc, nullptr, s),
                    "simt gemm");

@@ -11,21 +11,42 @@ namespace dev {
 
 namespace {
 
+// multiply-add and zero on complex64 / complex128
+__device__ __forceinline__ void cmac(float2 &acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cmac(double2 &acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+template <typename T>
+__device__ __forceinline__ T zero_c() {
+  T z;
+  z.x = 0;
+  z.y = 0;
+  return z;
+}
+
 __device__ __forceinline__ int64_t scatter_bits(int64_t v, int n, const int8_t *pos) {
   int64_t o = 0;
   for (int j = 0; j < n; j++) o |= ((v >> j) & 1) << pos[j];
   return o;
 }
 
-template <int BM, int BN, int TM, int TN, int BK>
+template <typename T, int BM, int BN, int TM, int TN, int BK>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
-    cgemm_simt_kernel(const float2 *__restrict__ A, const float2 *__restrict__ B, float2 *__restrict__ C,
+    cgemm_simt_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restrict__ C,
                       int64_t batch, int64_t M, int64_t N, int64_t K, int64_t sA, int64_t sB, int64_t sC,
                       const __grid_constant__ CScatter sc, int scatter) {
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int TX = BN / TN;
-  __shared__ float2 As[BK][BM + 1];
-  __shared__ float2 Bs[BK][BN + 1];
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
   const int64_t mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
   const int64_t tiles = mt * nt * batch;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
@@ -33,28 +54,28 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     const int64_t z = tile / (mt * nt);
     const int64_t rem = tile - z * mt * nt;
     const int64_t m0 = (rem / nt) * BM, n0 = (rem % nt) * BN;
-    const float2 *Az = A + z * sA;
-    const float2 *Bz = B + z * sB;
-    float2 acc[TM][TN];
+    const T *Az = A + z * sA;
+    const T *Bz = B + z * sB;
+    T acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; i++)
 #pragma unroll
-      for (int j = 0; j < TN; j++) acc[i][j] = make_float2(0.f, 0.f);
+      for (int j = 0; j < TN; j++) acc[i][j] = zero_c<T>();
     for (int64_t k0 = 0; k0 < K; k0 += BK) {
       for (int l = threadIdx.x; l < BM * BK; l += NT) {
         const int i = l / BK, kk = l % BK;
         const int64_t m = m0 + i, k = k0 + kk;
-        As[kk][i] = (m < M && k < K) ? Az[m * K + k] : make_float2(0.f, 0.f);
+        As[kk][i] = (m < M && k < K) ? Az[m * K + k] : zero_c<T>();
       }
       for (int l = threadIdx.x; l < BN * BK; l += NT) {
         const int i = l / BK, kk = l % BK;
         const int64_t n = n0 + i, k = k0 + kk;
-        Bs[kk][i] = (n < N && k < K) ? Bz[n * K + k] : make_float2(0.f, 0.f);
+        Bs[kk][i] = (n < N && k < K) ? Bz[n * K + k] : zero_c<T>();
       }
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < BK; kk++) {
-        float2 a[TM], b[TN];
+        T a[TM], b[TN];
 #pragma unroll
         for (int i = 0; i < TM; i++) a[i] = As[kk][ty + i * (BM / TM)];
 #pragma unroll
@@ -62,17 +83,12 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 #pragma unroll
         for (int i = 0; i < TM; i++)
 #pragma unroll
-          for (int j = 0; j < TN; j++) {
-            acc[i][j].x = fmaf(a[i].x, b[j].x, acc[i][j].x);
-            acc[i][j].x = fmaf(-a[i].y, b[j].y, acc[i][j].x);
-            acc[i][j].y = fmaf(a[i].x, b[j].y, acc[i][j].y);
-            acc[i][j].y = fmaf(a[i].y, b[j].x, acc[i][j].y);
-          }
+          for (int j = 0; j < TN; j++) cmac(acc[i][j], a[i], b[j]);
       }
       __syncthreads();
     }
     if (!scatter) {
-      float2 *Cz = C + z * sC;
+      T *Cz = C + z * sC;
 #pragma unroll
       for (int i = 0; i < TM; i++) {
         const int64_t m = m0 + ty + i * (BM / TM);
@@ -175,6 +191,43 @@ cudaError_t run_skinny(const float2 *A, const float2 *B, float2 *C, int64_t batc
   return cudaGetLastError();
 }
 
+// complex128 version of the long-k dot product (element loads)
+__global__ void __launch_bounds__(256)
+    zdot_kernel(const double2 *__restrict__ A, const double2 *__restrict__ B, double2 *__restrict__ C, int64_t batch,
+                int64_t M, int64_t N, int64_t K, int64_t sA, int64_t sB, int64_t sC, const __grid_constant__ CScatter sc,
+                int scatter) {
+  __shared__ double2 red[8];
+  const int64_t n_out = batch * M * N;
+  for (int64_t o = blockIdx.x; o < n_out; o += gridDim.x) {
+    const int64_t z = o / (M * N);
+    const int64_t m = (o / N) % M;
+    const int64_t n = o % N;
+    const double2 *a = A + z * sA + m * K;
+    const double2 *b = B + z * sB + n * K;
+    double2 acc = zero_c<double2>();
+    for (int64_t k = threadIdx.x; k < K; k += blockDim.x) cmac(acc, a[k], b[k]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double2 t = red[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+        t.x += red[w].x;
+        t.y += red[w].y;
+      }
+      const int64_t off = scatter ? scatter_bits(z, sc.nb, sc.pb) + scatter_bits(m, sc.nm, sc.pm) +
+                                        scatter_bits(n, sc.nn, sc.pn)
+                                  : z * sC + m * N + n;
+      C[off] = t;
+    }
+  }
+}
+
 // Few outputs, long summed index (m*n small, k large): one block per output
 // element streams its A row and B row (both k-contiguous) with 16-byte loads;
 // each thread sums its strided share in FP32, then a tree reduction.
@@ -224,13 +277,13 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-template <int BM, int BN, int TM, int TN, int BK>
-cudaError_t run(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N, int64_t K,
-                int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s) {
+template <int BM, int BN, int TM, int TN, int BK, typename T>
+cudaError_t run(const T *A, const T *B, T *C, int64_t batch, int64_t M, int64_t N, int64_t K, int64_t sA, int64_t sB,
+                int64_t sC, const CScatter *sc, cudaStream_t s) {
   const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN) * batch;
   const int blocks = (int)std::min<int64_t>(tiles, 152 * 64);
   CScatter none{};
-  cgemm_simt_kernel<BM, BN, TM, TN, BK><<<blocks, (BM / TM) * (BN / TN), 0, s>>>(A, B, C, batch, M, N, K, sA, sB,
+  cgemm_simt_kernel<T, BM, BN, TM, TN, BK><<<blocks, (BM / TM) * (BN / TN), 0, s>>>(A, B, C, batch, M, N, K, sA, sB,
                                                                                sC, sc ? *sc : none, sc ? 1 : 0);
   return cudaGetLastError();
 }
@@ -239,12 +292,12 @@ cudaError_t run(const float2 *A, const float2 *B, float2 *C, int64_t batch, int6
 // C through a scatter map. One thread per row of X; rows are numbered so that
 // the lowest row bits are the lowest bits of X where possible, which keeps
 // the loads of a warp in few sectors.
-template <int NMAX, int KMAX, int RPT>
+template <typename T, int NMAX, int KMAX, int RPT>
 __global__ void __launch_bounds__(256)
-    skinny_gather_kernel(const float2 *__restrict__ X, const float2 *__restrict__ Y, float2 *__restrict__ C,
+    skinny_gather_kernel(const T *__restrict__ X, const T *__restrict__ Y, T *__restrict__ C,
                          int64_t batch, int64_t M, int N, int K, const __grid_constant__ GatherMap g,
                          const __grid_constant__ CScatter sc, int scatter) {
-  __shared__ float2 Ys[NMAX * KMAX];
+  __shared__ T Ys[NMAX * KMAX];
   __shared__ int64_t xk_off[KMAX];
   __shared__ int64_t cn_off[NMAX];
   __shared__ int64_t hi_off[2];  // block-uniform part of the X and C offsets
@@ -284,11 +337,11 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
     const int64_t xh = hi_off[0], ch = hi_off[1];
-    float2 a[RPT][KMAX];
+    T a[RPT][KMAX];
 #pragma unroll
     for (int r = 0; r < RPT; r++) {
       if (mb + threadIdx.x + r * 256 >= M) continue;
-      const float2 *xr = X + xh + xlo[r];
+      const T *xr = X + xh + xlo[r];
 #pragma unroll
       for (int k = 0; k < KMAX; k++)
         if (k < K) a[r][k] = __ldcs(xr + xk_off[k]);
@@ -300,28 +353,22 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
       for (int n = 0; n < NMAX; n++) {
         if (n >= N) break;
-        float2 acc = make_float2(0.f, 0.f);
+        T acc = zero_c<T>();
 #pragma unroll
         for (int k = 0; k < KMAX; k++)
-          if (k < K) {
-            const float2 b = Ys[n * K + k];
-            acc.x = fmaf(a[r][k].x, b.x, acc.x);
-            acc.x = fmaf(-a[r][k].y, b.y, acc.x);
-            acc.y = fmaf(a[r][k].x, b.y, acc.y);
-            acc.y = fmaf(a[r][k].y, b.x, acc.y);
-          }
+          if (k < K) cmac(acc, a[r][k], Ys[n * K + k]);
         __stcs(C + om + cn_off[n], acc);
       }
     }
   }
 }
 
-template <int NMAX, int KMAX, int RPT>
-cudaError_t run_skinny_gather(const float2 *X, const float2 *Y, float2 *C, int64_t batch, int64_t M, int64_t N,
-                              int64_t K, const GatherMap &g, const CScatter *sc, cudaStream_t s) {
+template <typename T, int NMAX, int KMAX, int RPT>
+cudaError_t run_skinny_gather(const T *X, const T *Y, T *C, int64_t batch, int64_t M, int64_t N, int64_t K,
+                              const GatherMap &g, const CScatter *sc, cudaStream_t s) {
   const int64_t blocks = ((M + 256 * RPT - 1) / (256 * RPT)) * batch;
   CScatter none{};
-  skinny_gather_kernel<NMAX, KMAX, RPT><<<(unsigned)std::min<int64_t>(blocks, 152 * 16), 256, 0, s>>>(
+  skinny_gather_kernel<T, NMAX, KMAX, RPT><<<(unsigned)std::min<int64_t>(blocks, 152 * 16), 256, 0, s>>>(
       X, Y, C, batch, M, (int)N, (int)K, g, sc ? *sc : none, sc ? 1 : 0);
   return cudaGetLastError();
 }
@@ -331,8 +378,30 @@ cudaError_t run_skinny_gather(const float2 *X, const float2 *Y, float2 *C, int64
 cudaError_t launch_cgemm_skinny_gather(const float2 *X, const float2 *Y, float2 *C, int64_t batch, int64_t M,
                                        int64_t N, int64_t K, const GatherMap &g, const CScatter *sc, cudaStream_t s) {
   if (batch <= 0 || M <= 0 || N <= 0 || K <= 0 || N > 4 || K > 16) return cudaErrorInvalidValue;
-  if (K <= 4) return run_skinny_gather<4, 4, 4>(X, Y, C, batch, M, N, K, g, sc, s);
-  return run_skinny_gather<4, 16, 2>(X, Y, C, batch, M, N, K, g, sc, s);
+  if (K <= 4) return run_skinny_gather<float2, 4, 4, 4>(X, Y, C, batch, M, N, K, g, sc, s);
+  return run_skinny_gather<float2, 4, 16, 2>(X, Y, C, batch, M, N, K, g, sc, s);
+}
+
+cudaError_t launch_zskinny_gather(const double2 *X, const double2 *Y, double2 *C, int64_t batch, int64_t M,
+                                  int64_t N, int64_t K, const GatherMap &g, const CScatter *sc, cudaStream_t s) {
+  if (batch <= 0 || M <= 0 || N <= 0 || K <= 0 || N > 4 || K > 16) return cudaErrorInvalidValue;
+  if (K <= 4) return run_skinny_gather<double2, 4, 4, 2>(X, Y, C, batch, M, N, K, g, sc, s);
+  return run_skinny_gather<double2, 4, 16, 2>(X, Y, C, batch, M, N, K, g, sc, s);
+}
+
+cudaError_t launch_zgemm_simt(const double2 *A, const double2 *B, double2 *C, int64_t batch, int64_t M, int64_t N,
+                              int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s) {
+  if (batch <= 0 || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
+  if (M * N <= 64 && K >= 2048) {
+    CScatter none{};
+    zdot_kernel<<<(unsigned)std::min<int64_t>(batch * M * N, 152 * 8), 256, 0, s>>>(A, B, C, batch, M, N, K, sA, sB,
+                                                                                 sC, sc ? *sc : none, sc ? 1 : 0);
+    return cudaGetLastError();
+  }
+  if (N >= 48) return run<64, 64, 4, 4, 8>(A, B, C, batch, M, N, K, sA, sB, sC, sc, s);
+  if (N >= 12) return run<128, 16, 4, 2, 8>(A, B, C, batch, M, N, K, sA, sB, sC, sc, s);
+  if (N >= 3) return run<256, 4, 4, 1, 8>(A, B, C, batch, M, N, K, sA, sB, sC, sc, s);
+  return run<256, 2, 2, 1, 8>(A, B, C, batch, M, N, K, sA, sB, sC, sc, s);
 }
 
 cudaError_t launch_cgemm_simt(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N,

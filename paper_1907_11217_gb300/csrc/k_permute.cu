@@ -34,7 +34,8 @@ struct TileMap {
 
 __device__ __forceinline__ int swz(int e) { return e ^ (((e >> 5) & 15) << 1); }
 
-__global__ void permute_small_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, PermuteArgs a) {
+template <typename T>
+__global__ void permute_small_kernel(const T *__restrict__ in, T *__restrict__ out, PermuteArgs a) {
   const int64_t n = int64_t(1) << a.rank;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = 0;
@@ -104,7 +105,75 @@ __global__ void __launch_bounds__(kThreads) permute_tiled_kernel(const float2 *_
   }
 }
 
+// complex128: 16-byte elements, moved one by one (already 16-byte accesses)
+__global__ void __launch_bounds__(kThreads) permute_tiled_z_kernel(const double2 *__restrict__ in,
+                                                                   double2 *__restrict__ out,
+                                                                   const __grid_constant__ TileMap m,
+                                                                   int64_t n_tiles) {
+  __shared__ double2 tile[1 << kTile];
+  __shared__ int64_t base[2];
+  int64_t ld_off[kPer], st_off[kPer];
+  int ld_s[kPer], st_s[kPer];
+#pragma unroll
+  for (int i = 0; i < kPer; i++) {
+    const int e = threadIdx.x + i * kThreads;
+    int64_t o = 0, oo = 0;
+    int src = 0;
+    for (int j = 0; j < kTile; j++) {
+      o |= int64_t((e >> j) & 1) << m.uin[j];
+      oo |= int64_t((e >> j) & 1) << m.vout[j];
+      src |= ((e >> j) & 1) << m.vsrc[j];
+    }
+    ld_off[i] = o;
+    ld_s[i] = swz(e);
+    st_off[i] = oo;
+    st_s[i] = swz(src);
+  }
+  const int nr = m.r - kTile;
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    if (threadIdx.x == 0) {
+      int64_t bin = 0, bout = 0;
+      for (int j = 0; j < nr; j++) {
+        const int64_t b = (t >> j) & 1;
+        bin |= b << m.rin[j];
+        bout |= b << m.rout[j];
+      }
+      base[0] = bin;
+      base[1] = bout;
+    }
+    __syncthreads();
+    const int64_t bin = base[0], bout = base[1];
+    double2 v[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; i++) v[i] = in[bin + ld_off[i]];
+#pragma unroll
+    for (int i = 0; i < kPer; i++) tile[ld_s[i]] = v[i];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kPer; i++) out[bout + st_off[i]] = tile[st_s[i]];
+    __syncthreads();
+  }
+}
+
+bool tile_map(const PermuteArgs &a, TileMap *mp);
+
 }  // namespace
+
+cudaError_t launch_permute_z(const double2 *in, double2 *out, const PermuteArgs &a, cudaStream_t s) {
+  const int r = a.rank;
+  if (r < 0 || r > kMaxBits) return cudaErrorInvalidValue;
+  const int64_t n = int64_t(1) << r;
+  if (r < kTile) {
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    permute_small_kernel<double2><<<blocks, 256, 0, s>>>(in, out, a);
+    return cudaGetLastError();
+  }
+  TileMap m{};
+  tile_map(a, &m);
+  const int64_t n_tiles = n >> kTile;
+  permute_tiled_z_kernel<<<(int)std::min<int64_t>(n_tiles, 152 * 8), kThreads, 0, s>>>(in, out, m, n_tiles);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_permute(const float2 *in, float2 *out, const PermuteArgs &a, cudaStream_t s) {
   const int r = a.rank;
@@ -112,12 +181,23 @@ cudaError_t launch_permute(const float2 *in, float2 *out, const PermuteArgs &a, 
   const int64_t n = int64_t(1) << r;
   if (r < kTile) {
     int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
-    permute_small_kernel<<<blocks, 256, 0, s>>>(in, out, a);
+    permute_small_kernel<float2><<<blocks, 256, 0, s>>>(in, out, a);
     return cudaGetLastError();
   }
+  TileMap m{};
+  tile_map(a, &m);
+  const int64_t n_tiles = n >> kTile;
+  const int blocks = (int)std::min<int64_t>(n_tiles, 152 * 8);
+  permute_tiled_kernel<<<blocks, kThreads, 0, s>>>(in, out, m, n_tiles);
+  return cudaGetLastError();
+}
+
+namespace {
+bool tile_map(const PermuteArgs &a, TileMap *mp) {
+  TileMap &m = *mp;
+  const int r = a.rank;
   int inv[kMaxBits];
   for (int p = 0; p < r; p++) inv[a.perm[p]] = p;
-  TileMap m{};
   m.r = r;
   // load order: input bits 0..kW-1, then input bits feeding output bits
   // 0..kW-1, then the next lowest input bits until the tile has kTile bits
@@ -154,11 +234,9 @@ cudaError_t launch_permute(const float2 *in, float2 *out, const PermuteArgs &a, 
       m.rout[j] = (int8_t)inv[b];
       j++;
     }
-  const int64_t n_tiles = n >> u;
-  const int blocks = (int)std::min<int64_t>(n_tiles, 152 * 8);
-  permute_tiled_kernel<<<blocks, kThreads, 0, s>>>(in, out, m, n_tiles);
-  return cudaGetLastError();
+  return true;
 }
+}  // namespace
 
 }  // namespace dev
 }  // namespace tz

@@ -5,8 +5,12 @@
 namespace tz {
 namespace dev {
 
+// complex arithmetic on float2 (complex64) and double2 (complex128)
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
 __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
   c.x = fmaf(a.x, b.x, c.x);
@@ -15,6 +19,21 @@ __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
   c.y = fmaf(a.y, b.x, c.y);
   return c;
 }
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+  c.x = fma(a.x, b.x, c.x);
+  c.x = fma(-a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y);
+  c.y = fma(a.y, b.x, c.y);
+  return c;
+}
+template <typename T>
+__device__ __forceinline__ T czero();
+template <>
+__device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+template <>
+__device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ float2 table_value(const LeafJob &j, int i, float2 *) { return j.M[i]; }
+__device__ __forceinline__ double2 table_value(const LeafJob &j, int i, double2 *) { return j.Md[i]; }
 
 __global__ void init_state_kernel(GroupState *gs, int64_t lo, int64_t hi, int64_t n_rows) {
   gs->slice = lo;
@@ -33,11 +52,12 @@ cudaError_t launch_init_state(GroupState *gs, int64_t lo, int64_t hi, int64_t n_
 // One block per leaf job. Gather: a constant tensor with its sliced bits
 // fixed to the bits of the current slice id (Sec. 1 subtasks). Output: the
 // tensor <x_q| (final gates folded in) for the current chunk of bitstrings.
+template <typename T>
 __global__ void leaf_kernel(const LeafJob *jobs, const GroupState *gs, const uint8_t *bits, int nq, int g,
                             const char *cbase, char *abase) {
   const LeafJob &j = jobs[blockIdx.x];
-  float2 *dst = const_cast<float2 *>(region_ptr(j.dst, cbase, abase));
-  const float2 *src = j.kind == LJ_GATHER ? region_ptr(j.src, cbase, abase) : nullptr;
+  T *dst = const_cast<T *>(region_ptr<T>(j.dst, cbase, abase));
+  const T *src = j.kind == LJ_GATHER ? region_ptr<T>(j.src, cbase, abase) : nullptr;
   const int64_t slice = gs->slice, chunk = gs->chunk, n_rows = gs->n_rows;
   const int64_t n = int64_t(1) << j.rank;
   for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
@@ -59,14 +79,17 @@ __global__ void leaf_kernel(const LeafJob *jobs, const GroupState *gs, const uin
         else if (j.e_slice_bit >= 0)
           ev = (int)((slice >> j.e_slice_bit) & 1);
       }
-      dst[e] = j.M[x * (1 << j.rc) + ev];
+      dst[e] = table_value(j, x * (1 << j.rc) + ev, (T *)nullptr);
     }
   }
 }
 
 cudaError_t launch_leaf_build(const LeafJob *jobs, int n_jobs, const GroupState *gs, const uint8_t *bits, int nq,
-                              int g, const char *cbase, char *abase, cudaStream_t s) {
-  leaf_kernel<<<n_jobs, 128, 0, s>>>(jobs, gs, bits, nq, g, cbase, abase);
+                              int g, const char *cbase, char *abase, int dbl, cudaStream_t s) {
+  if (dbl)
+    leaf_kernel<double2><<<n_jobs, 128, 0, s>>>(jobs, gs, bits, nq, g, cbase, abase);
+  else
+    leaf_kernel<float2><<<n_jobs, 128, 0, s>>>(jobs, gs, bits, nq, g, cbase, abase);
   return cudaGetLastError();
 }
 
@@ -74,10 +97,11 @@ cudaError_t launch_leaf_build(const LeafJob *jobs, int n_jobs, const GroupState 
 // Each output element is summed by 2^split consecutive threads, each walking
 // its share of the contracted bits in Gray-code order (one offset update per
 // term), then reduced.
+template <typename T>
 __global__ void __launch_bounds__(256) direct_kernel(const DStep *steps, int n_steps, const char *cbase,
                                                      char *abase) {
   __shared__ int s_idx;
-  __shared__ float2 red[256];
+  __shared__ T red[256];
   const int64_t blk = blockIdx.x;
   if (threadIdx.x == 0) {
     int lo = 0, hi = n_steps - 1;
@@ -92,15 +116,15 @@ __global__ void __launch_bounds__(256) direct_kernel(const DStep *steps, int n_s
   }
   __syncthreads();
   const DStep &st = steps[s_idx];
-  const float2 *__restrict__ Ap = region_ptr(st.A, cbase, abase);
-  const float2 *__restrict__ Bp = region_ptr(st.B, cbase, abase);
-  float2 *Cp = const_cast<float2 *>(region_ptr(st.C, cbase, abase));
+  const T *__restrict__ Ap = region_ptr<T>(st.A, cbase, abase);
+  const T *__restrict__ Bp = region_ptr<T>(st.B, cbase, abase);
+  T *Cp = const_cast<T *>(region_ptr<T>(st.C, cbase, abase));
   const int split = st.split;
   const int64_t item = (blk - st.block_begin) * 256 + threadIdx.x;
   const int64_t c = item >> split;
   const int part = (int)(item & ((1 << split) - 1));
   const bool active = c < (int64_t(1) << st.nC);
-  float2 acc = make_float2(0.f, 0.f);
+  T acc = czero<T>();
   if (active) {
     int64_t oa = 0, ob = 0;
     for (int q = 0; q < st.nC; q++) {
@@ -130,7 +154,7 @@ __global__ void __launch_bounds__(256) direct_kernel(const DStep *steps, int n_s
     __syncthreads();
     if (active && part == 0) {
       for (int q = 1; q < (1 << split); q++) {
-        float2 v = red[threadIdx.x + q];
+        T v = red[threadIdx.x + q];
         acc.x += v.x;
         acc.y += v.y;
       }
@@ -140,16 +164,21 @@ __global__ void __launch_bounds__(256) direct_kernel(const DStep *steps, int n_s
 }
 
 cudaError_t launch_direct(const DStep *steps, int n_steps, int64_t total_blocks, const char *cbase, char *abase,
-                          cudaStream_t s) {
+                          int dbl, cudaStream_t s) {
   if (n_steps <= 0) return cudaSuccess;
   if (total_blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  direct_kernel<<<(unsigned)total_blocks, 256, 0, s>>>(steps, n_steps, cbase, abase);
+  if (dbl)
+    direct_kernel<double2><<<(unsigned)total_blocks, 256, 0, s>>>(steps, n_steps, cbase, abase);
+  else
+    direct_kernel<float2><<<(unsigned)total_blocks, 256, 0, s>>>(steps, n_steps, cbase, abase);
   return cudaGetLastError();
 }
 
 // acc[row] += scale * root[beta] in FP64 for the current chunk; then advance
 // the group state (next slice, wrapping to the next chunk).
+template <typename T>
 __global__ void accum_kernel(AccumArgs a) {
+  const T *root = static_cast<const T *>(a.root);
   GroupState *gs = a.gs;
   const int64_t chunk = gs->chunk, n_rows = gs->n_rows;
   const int nb = 1 << a.g;
@@ -158,7 +187,7 @@ __global__ void accum_kernel(AccumArgs a) {
     for (int j = 0; j < a.g; j++) off |= int64_t((beta >> j) & 1) << a.beta_pos[j];
     const int64_t row = (chunk << a.g) | beta;
     if (row < n_rows) {
-      const float2 v = a.root[off];
+      const T v = root[off];
       const double vr = v.x, vi = v.y;
       double2 r = a.acc[row];
       r.x += a.scale_re * vr - a.scale_im * vi;
@@ -179,7 +208,10 @@ __global__ void accum_kernel(AccumArgs a) {
 }
 
 cudaError_t launch_accumulate(const AccumArgs &a, cudaStream_t s) {
-  accum_kernel<<<1, 256, 0, s>>>(a);
+  if (a.dbl)
+    accum_kernel<double2><<<1, 256, 0, s>>>(a);
+  else
+    accum_kernel<float2><<<1, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

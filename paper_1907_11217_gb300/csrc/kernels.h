@@ -27,8 +27,9 @@ struct GroupState {
 // plan can run in several scratch arenas at once: bit 62 set = offset into
 // the per-query arena, clear = offset into the plan's resident constants.
 constexpr int64_t kArenaTag = int64_t(1) << 62;
-__host__ __device__ inline const float2 *region_ptr(int64_t off, const char *cbase, const char *abase) {
-  return reinterpret_cast<const float2 *>(((off & kArenaTag) ? abase : cbase) + (off & (kArenaTag - 1)));
+template <typename T = float2>
+__host__ __device__ inline const T *region_ptr(int64_t off, const char *cbase, const char *abase) {
+  return reinterpret_cast<const T *>(((off & kArenaTag) ? abase : cbase) + (off & (kArenaTag - 1)));
 }
 
 enum LeafKind { LJ_GATHER = 0, LJ_OUTPUT = 1 };
@@ -47,7 +48,8 @@ struct LeafJob {
   int8_t fixed_src_pos[8];
   int8_t fixed_slice_bit[8];
   int8_t beta_dst_pos[8]; // output: dst bit of batch bit j, -1 if absent
-  float2 M[4];            // output: table M[x * 2^rc + e]
+  float2 M[4];            // output: table M[x * 2^rc + e] (complex64 plans)
+  double2 Md[4];          // the same table for complex128 plans
 };
 
 // One small contraction step computed directly (no operand permute):
@@ -85,21 +87,29 @@ struct PermuteArgs {
 };
 
 struct AccumArgs {
-  const float2 *root;
+  const void *root;           // complex64, or complex128 when dbl
   double2 *acc;
   GroupState *gs;
   int g;                      // batch bits
   int8_t beta_pos[kMaxBatch]; // root bit of batch bit j
   double scale_re, scale_im;
   int advance;                // 1: advance gs to the next group
+  int dbl;                    // root is complex128
 };
 
 cudaError_t launch_init_state(GroupState *gs, int64_t lo, int64_t hi, int64_t n_rows, cudaStream_t s);
+// dbl: tensors are complex128 (else complex64)
 cudaError_t launch_leaf_build(const LeafJob *jobs, int n_jobs, const GroupState *gs, const uint8_t *bits, int nq,
-                              int g, const char *cbase, char *abase, cudaStream_t s);
+                              int g, const char *cbase, char *abase, int dbl, cudaStream_t s);
 cudaError_t launch_direct(const DStep *steps, int n_steps, int64_t total_blocks, const char *cbase, char *abase,
-                          cudaStream_t s);
+                          int dbl, cudaStream_t s);
 cudaError_t launch_permute(const float2 *in, float2 *out, const PermuteArgs &a, cudaStream_t s);
+cudaError_t launch_permute_z(const double2 *in, double2 *out, const PermuteArgs &a, cudaStream_t s);
+// complex128 products (FP64 FMA): tiled, skinny in place, long-k dot
+cudaError_t launch_zgemm_simt(const double2 *A, const double2 *B, double2 *C, int64_t batch, int64_t M, int64_t N,
+                              int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s);
+cudaError_t launch_zskinny_gather(const double2 *X, const double2 *Y, double2 *C, int64_t batch, int64_t M,
+                                  int64_t N, int64_t K, const GatherMap &g, const CScatter *sc, cudaStream_t s);
 // sc == nullptr: C row-major with batch stride sC.
 cudaError_t launch_cgemm_simt(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N,
                               int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s);

@@ -92,7 +92,7 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
     slice_bit[e] = (int)j;
   }
   if (sliced.size() > 40) fail(TZ_EUNSUPPORTED, "more than 40 sliced indices");
-  if (o.precision < TZ_C64_SIMT || o.precision > TZ_BF16X3) fail(TZ_EINVAL, "unknown precision");
+  if (o.precision < TZ_C64_SIMT || o.precision > TZ_C128_SIMT) fail(TZ_EINVAL, "unknown precision");
 
   auto p = std::make_unique<tz_plan>();
   p->net = net;
@@ -100,6 +100,8 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
   p->sliced = sliced;
   p->slice_bit = slice_bit;
   p->opts = o;
+  p->esz = o.precision == TZ_C128_SIMT ? 16 : 8;
+  const int64_t esz = p->esz;
   if (p->opts.small_log2 <= 0) p->opts.small_log2 = 20;
   p->opts.small_log2 = std::min(p->opts.small_log2, 26);
   p->max_rows = o.max_bitstrings > 0 ? o.max_bitstrings : 4096;
@@ -181,7 +183,8 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
     ps.K = int64_t(1) << st.contr.size();
     ps.batch = int64_t(1) << st.batch.size();
     // skinny products are memory-bound: the streaming SIMT kernel serves them
-    ps.tc = o.precision != TZ_C64_SIMT && dev::cgemm_tc_supported(o.precision, ps.M, ps.N, ps.K) &&
+    ps.tc = (o.precision == TZ_TF32X3 || o.precision == TZ_BF16X3) &&
+            dev::cgemm_tc_supported(o.precision, ps.M, ps.N, ps.K) &&
             !(ps.N <= 4 && ps.K <= 16);
     ps.skinny = !ps.tc && ps.N <= 4 && ps.K <= 16 && ps.M >= 256;
     if (ps.tc) ps.tc_scratch = (int64_t)dev::cgemm_tc_scratch_bytes(o.precision, ps.batch, ps.N, ps.K);
@@ -451,7 +454,7 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
     if (is_const_leaf || persistent[t]) {
       pt.region = R_CONST;
       pt.off = const_peak;
-      const_peak = (int64_t)align256(const_peak + pt.bytes());
+      const_peak = (int64_t)align256(const_peak + pt.elems() * esz);
     }
   }
   // arena: var tensors in the group pass, transient const tensors in the bind
@@ -466,7 +469,8 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
       PTensor &pt = p->T[t];
       if (pt.region != R_NONE || birth[pass][t] < 0) continue;
       if ((pass == 1) != pt.var) continue;
-      reqs.push_back(Req{birth[pass][t], std::max(death[pass][t], birth[pass][t]), t, -1, (int64_t)align256((size_t)pt.bytes())});
+      reqs.push_back(Req{birth[pass][t], std::max(death[pass][t], birth[pass][t]), t, -1,
+                         (int64_t)align256((size_t)(pt.elems() * esz))});
     }
     // tensor-core operand scratch of each GEMM: lives during its item only
     std::vector<Item> &items = pass ? p->var_items : p->const_items;
@@ -575,8 +579,10 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
         if (!net.is_open(i)) continue;
         j.beta_dst_pos[net.indices[i].segment] = (int8_t)pos_of(dst.lay, i);
       }
-      for (int x = 0; x < 2 * (1 << lf.rc) && x < 4; x++)
+      for (int x = 0; x < 2 * (1 << lf.rc) && x < 4; x++) {
         j.M[x] = make_float2((float)lf.data[x].real(), (float)lf.data[x].imag());
+        j.Md[x] = make_double2(lf.data[x].real(), lf.data[x].imag());
+      }
       p->job_tensors.insert(p->job_tensors.end(), {l, -1});
     } else {
       j.kind = dev::LJ_GATHER;
@@ -634,7 +640,7 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
     double fl = 8.0 * std::ldexp(1.0, st.bitsAll());
     stt.flops_per_group += fl;
     stt.bytes_per_group +=
-        8.0 * (std::ldexp(1.0, st.bitsA()) + std::ldexp(1.0, st.bitsB()) + std::ldexp(1.0, st.bitsC()));
+        (double)esz * (std::ldexp(1.0, st.bitsA()) + std::ldexp(1.0, st.bitsB()) + std::ldexp(1.0, st.bitsC()));
     if (p->S[s].gemm) {
       stt.n_gemm_steps++;
       stt.gemm_flops_per_group += fl;
@@ -643,7 +649,7 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
   for (const Item &it : p->var_items)
     if (it.kind == IT_PERMUTE) {
       stt.n_permutes++;
-      stt.permute_bytes_per_group += 16.0 * p->T[it.a].elems();
+      stt.permute_bytes_per_group += 2.0 * esz * p->T[it.a].elems();
     }
   stt.n_launches_per_group = (int)p->var_items.size();
   stt.workspace_bytes = p->total_bytes;
@@ -784,7 +790,7 @@ static void item_cost(const tz_plan *p, const Item &it, int *kind, double *flops
   switch (it.kind) {
     case IT_LEAVES:
       *kind = 0;
-      for (size_t j = 0; j < p->jobs.size(); j++) *bytes += 8.0 * (int64_t(1) << p->jobs[j].rank);
+      for (size_t j = 0; j < p->jobs.size(); j++) *bytes += (double)p->esz * (int64_t(1) << p->jobs[j].rank);
       break;
     case IT_DIRECT:
       *kind = 1;
@@ -792,19 +798,19 @@ static void item_cost(const tz_plan *p, const Item &it, int *kind, double *flops
         const PTensor &A = p->T[p->dstep_tensors[3 * d]], &B = p->T[p->dstep_tensors[3 * d + 1]],
                       &C = p->T[p->dstep_tensors[3 * d + 2]];
         *flops += 8.0 * std::ldexp(1.0, p->dsteps[d].nC + p->dsteps[d].nK);
-        *bytes += 8.0 * (A.elems() + B.elems() + C.elems());
+        *bytes += (double)p->esz * (A.elems() + B.elems() + C.elems());
       }
       break;
     case IT_PERMUTE:
       *kind = 2;
-      *bytes = 16.0 * p->T[it.a].elems();
+      *bytes = 2.0 * p->esz * p->T[it.a].elems();
       break;
     case IT_GEMM: {
       const PStep &ps = p->S[it.a];
       const bool dot = ps.M * ps.N <= 64 && ps.K >= 2048 && (ps.K % 2) == 0;
       *kind = ps.tc ? 4 : ps.skinny ? 6 : dot ? 7 : 3;
       *flops = 8.0 * ps.batch * (double)ps.M * (double)ps.N * (double)ps.K;
-      *bytes = 8.0 * ps.batch * ((double)ps.M * ps.K + (double)ps.N * ps.K + (double)ps.M * ps.N);
+      *bytes = (double)p->esz * ps.batch * ((double)ps.M * ps.K + (double)ps.N * ps.K + (double)ps.M * ps.N);
       break;
     }
     default:
@@ -840,12 +846,12 @@ static void run_items(tz_plan *p, const std::vector<Item> &items, const RunCtx &
           cuda_check(dev::launch_leaf_build(reinterpret_cast<const dev::LeafJob *>(p->ws + p->off_jobs),
                                             (int)p->jobs.size(), gs,
                                             reinterpret_cast<const uint8_t *>(ctx.scratch + p->s_bits),
-                                            p->net.n_qubits, p->net.batch_log2, cbase, abase, s),
+                                            p->net.n_qubits, p->net.batch_log2, cbase, abase, p->esz == 16, s),
                      "leaf build");
         break;
       case IT_DIRECT:
         cuda_check(dev::launch_direct(reinterpret_cast<const dev::DStep *>(p->ws + p->off_dsteps) + it.first,
-                                      it.count, it.blocks, cbase, abase, s),
+                                      it.count, it.blocks, cbase, abase, p->esz == 16, s),
                    "direct steps");
         break;
       case IT_PERMUTE: {
@@ -853,9 +859,14 @@ static void run_items(tz_plan *p, const std::vector<Item> &items, const RunCtx &
         const PTensor &src = p->T[it.a], &dst = p->T[it.b];
         a.rank = (int)dst.lay.size();
         for (int q = 0; q < a.rank; q++) a.perm[q] = (int8_t)pos_of(src.lay, dst.lay[q]);
-        cuda_check(dev::launch_permute((const float2 *)tensor_ptr(p, ctx, it.a), (float2 *)tensor_ptr(p, ctx, it.b), a,
-                                       s),
-                   "permute");
+        if (p->esz == 16)
+          cuda_check(dev::launch_permute_z((const double2 *)tensor_ptr(p, ctx, it.a),
+                                           (double2 *)tensor_ptr(p, ctx, it.b), a, s),
+                     "permute");
+        else
+          cuda_check(dev::launch_permute((const float2 *)tensor_ptr(p, ctx, it.a), (float2 *)tensor_ptr(p, ctx, it.b),
+                                         a, s),
+                     "permute");
         break;
       }
       case IT_GEMM: {
@@ -864,7 +875,17 @@ static void run_items(tz_plan *p, const std::vector<Item> &items, const RunCtx &
         const float2 *Y = (const float2 *)tensor_ptr(p, ctx, ps.opY);
         float2 *C = (float2 *)tensor_ptr(p, ctx, ps.c_nat >= 0 ? ps.c_nat : ps.c);
         const dev::CScatter *sc = ps.row_major ? nullptr : &ps.scatter;
-        if (ps.skinny) {
+        if (p->esz == 16) {
+          const double2 *Xz = (const double2 *)X, *Yz = (const double2 *)Y;
+          double2 *Cz = (double2 *)C;
+          if (ps.skinny)
+            cuda_check(dev::launch_zskinny_gather(Xz, Yz, Cz, ps.batch, ps.M, ps.N, ps.K, ps.gather, sc, s),
+                       "skinny gemm");
+          else
+            cuda_check(dev::launch_zgemm_simt(Xz, Yz, Cz, ps.batch, ps.M, ps.N, ps.K, ps.M * ps.K, ps.N * ps.K,
+                                              ps.M * ps.N, sc, s),
+                       "simt gemm");
+        } else if (ps.skinny) {
           cuda_check(dev::launch_cgemm_skinny_gather(X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.gather, sc, s),
                      "skinny gemm");
         } else if (ps.tc) {
@@ -881,7 +902,8 @@ static void run_items(tz_plan *p, const std::vector<Item> &items, const RunCtx &
       }
       case IT_ACCUM: {
         dev::AccumArgs a{};
-        a.root = (const float2 *)tensor_ptr(p, ctx, p->root);
+        a.root = tensor_ptr(p, ctx, p->root);
+        a.dbl = p->esz == 16;
         a.acc = reinterpret_cast<double2 *>(ctx.scratch + p->s_acc);
         a.gs = gs;
         a.g = p->net.batch_log2;
@@ -945,22 +967,30 @@ void plan_bind(tz_plan *p, void *ws, size_t bytes) {
                "upload leaf tables");
   // constant leaves, in their planned storage order
   std::vector<float2> host;
+  std::vector<double2> hostz;
   for (size_t t = 0; t < p->T.size(); t++) {
     const PTensor &x = p->T[t];
     if (x.region != R_CONST || x.leaf < 0) continue;
     if (x.var) continue;
     const Leaf &lf = p->net.leaves[x.leaf];
     host.assign(x.elems(), make_float2(0, 0));
+    hostz.assign(x.elems(), make_double2(0, 0));
     std::vector<int> srcpos(x.lay.size());
     for (size_t q = 0; q < x.lay.size(); q++) srcpos[q] = pos_of(lf.idx, x.lay[q]);
     for (int64_t e = 0; e < x.elems(); e++) {
       int64_t so = 0;
       for (size_t q = 0; q < x.lay.size(); q++) so |= ((e >> q) & 1) << srcpos[q];
       host[e] = make_float2((float)lf.data[so].real(), (float)lf.data[so].imag());
+      hostz[e] = make_double2(lf.data[so].real(), lf.data[so].imag());
     }
-    cuda_check(cudaMemcpyAsync(tensor_ptr(p, default_ctx(p), (int)t), host.data(), host.size() * sizeof(float2),
-                               cudaMemcpyHostToDevice, s),
-               "upload constants");
+    if (p->esz == 16)
+      cuda_check(cudaMemcpyAsync(tensor_ptr(p, default_ctx(p), (int)t), hostz.data(), hostz.size() * sizeof(double2),
+                                 cudaMemcpyHostToDevice, s),
+                 "upload constants");
+    else
+      cuda_check(cudaMemcpyAsync(tensor_ptr(p, default_ctx(p), (int)t), host.data(), host.size() * sizeof(float2),
+                                 cudaMemcpyHostToDevice, s),
+                 "upload constants");
     cuda_check(cudaStreamSynchronize(s), "sync");  // host buffer is reused
   }
   run_items(p, p->const_items, default_ctx(p));

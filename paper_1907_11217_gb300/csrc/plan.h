@@ -66,6 +66,7 @@ struct tz_plan {
   std::vector<int> job_tensors;    // 2 per job (dst, src or -1)
   int root = -1;
   int64_t max_rows = 0;
+  int esz = 8;                     // bytes per tensor element: 8 complex64, 16 complex128
   // workspace layout (bytes): resident part [step tables | leaf tables |
   // constants], then one scratch part [group state | bitstrings | FP64
   // accumulator | group arena]; a query can also run in another scratch part

@@ -12,6 +12,7 @@ from tests.gpu_util import grid_spec, make_plan, rel_err
 
 pytestmark = pytest.mark.gpu
 TOL_C64 = 1e-5
+TOL_C128 = 1e-12
 
 
 @pytest.fixture(scope="module")
@@ -22,14 +23,15 @@ def tz():
     return tz
 
 
-def test_config1_4x4_depth10_single_bitstring(tz):
-    """4x4 grid, depth 1+10+1, seed 1, one bitstring, no slicing, complex64."""
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_config1_4x4_depth10_single_bitstring(tz, prec):
+    """4x4 grid, depth 1+10+1, seed 1, one bitstring, no slicing."""
     spec = grid_spec(4, 4, 10, 1)
     bits = ti.random_bitstrings(16, 1, 101)
-    plan, *_ = make_plan(tz, spec)
+    plan, *_ = make_plan(tz, spec, precision=prec)
     got = tz.tz_contract_amplitudes(plan, bits)
     ref = sv.amplitudes(spec, bits)
-    assert rel_err(got, ref, 16) <= TOL_C64
+    assert rel_err(got, ref, 16) <= (TOL_C64 if prec == "c64" else TOL_C128)
 
 
 def test_golden_closed_forms(tz):
@@ -55,16 +57,17 @@ def test_batched_bitstrings_ragged(tz, g, small):
     assert rel_err(got, sv.amplitudes(spec, bits), 16) <= TOL_C64
 
 
+@pytest.mark.parametrize("prec", ["c64", "c128"])
 @pytest.mark.parametrize("rows,cols,t,seed,cut,g,small", [
     (4, 4, 10, 1, 2, 0, 3), (4, 5, 12, 3, 3, 1, 5), (4, 5, 16, 4, 4, 2, 6), (4, 4, 20, 6, 3, 0, 20)])
-def test_sliced_against_statevector(tz, rows, cols, t, seed, cut, g, small):
+def test_sliced_against_statevector(tz, rows, cols, t, seed, cut, g, small, prec):
     spec = grid_spec(rows, cols, t, seed)
     n = rows * cols
     bits = ti.random_bitstrings(n, 6, seed + 50)
-    plan, net, tree, sl = make_plan(tz, spec, batch_log2=g, slice_bits=cut, small_log2=small)
+    plan, net, tree, sl = make_plan(tz, spec, batch_log2=g, slice_bits=cut, small_log2=small, precision=prec)
     assert cut <= len(sl) <= 8
     got = tz.tz_contract_amplitudes(plan, bits)
-    assert rel_err(got, sv.amplitudes(spec, bits), n) <= TOL_C64
+    assert rel_err(got, sv.amplitudes(spec, bits), n) <= (TOL_C64 if prec == "c64" else TOL_C128)
 
 
 def test_slice_ranges_add_up_and_match_oracle_partials(tz):
@@ -130,8 +133,9 @@ def test_tensor_core_path_5x6(tz, prec):
         assert err <= (TOL_C64 if prec == "tf32x3" else 1e-3)
 
 
+@pytest.mark.parametrize("prec", ["c64", "c128"])
 @pytest.mark.parametrize("rows,cols,t,seed,g,small", [(5, 5, 20, 11, 4, 5), (6, 6, 16, 3, 0, 6)])
-def test_in_place_skinny_steps(tz, rows, cols, t, seed, g, small):
+def test_in_place_skinny_steps(tz, rows, cols, t, seed, g, small, prec):
     """Plans whose skinny products read their operands in the producers'
     storage order (gather maps) and write through scatter maps, with the
     remaining operand permutes; against the plain-wire contractor."""
@@ -139,10 +143,11 @@ def test_in_place_skinny_steps(tz, rows, cols, t, seed, g, small):
     spec = grid_spec(rows, cols, t, seed)
     n = rows * cols
     bits = ti.random_bitstrings(n, 1 << g, seed + 5)
-    plan, *_ = make_plan(tz, spec, batch_log2=g, small_log2=small, restarts=8, seed=3, max_bitstrings=1 << g)
+    plan, *_ = make_plan(tz, spec, batch_log2=g, small_log2=small, restarts=8, seed=3, max_bitstrings=1 << g,
+                         precision=prec)
     d = json.loads(plan.describe())
     assert sum(s["skinny"] for s in d["steps"]) >= 2
     got = tz.tz_contract_amplitudes(plan, bits)
     c = tn.Contractor(spec, max_log2=24)
     ref = np.array([c.amplitude(x) for x in bits])
-    assert rel_err(got, ref, n) <= TOL_C64
+    assert rel_err(got, ref, n) <= (TOL_C64 if prec == "c64" else TOL_C128)

@@ -9,7 +9,10 @@ tree, 2^30 cap, captured graph on a stream):
 * slicing is exact: the partial amplitudes of the slices add up to the full
   amplitude (Sec. 1: subtask results add up to the amplitude);
 * the amplitude does not depend on the contraction tree or the slicing;
-* the split-precision modes agree with complex64;
+* the FP32-class modes (complex64, split TF32, split BF16) agree with the
+  complex128 mode run on the same tree; their errors against it are printed
+  and bounded by the values measured on GB300 (the complex128 mode itself is
+  pinned to the FP64 oracle to 1e-12 wherever the oracle reaches);
 * Porter-Thomas (Sec. 2): E[2^n |a|^2] = 1 over random bitstrings.
 
 At full width and reduced depth the oracle is feasible, and those circuits
@@ -71,15 +74,21 @@ def test_bristlecone70_depth32_properties(tz):
         parts.append(tz.tz_contract_amplitudes(plan, bits))
     plan.set_slice_range(0, 1 << k)
     assert rel_err(np.sum(parts, axis=0), a, 70) <= 1e-6
-    # complex64 on the same tree and slicing
+    # every mode on the same tree and slicing, against complex128
+    p128, *_ = build(tz, spec, "c128", 30)
+    a128 = tz.tz_contract_amplitudes(p128, bits)
     p64, *_ = build(tz, spec, "c64", 30)
     a64 = tz.tz_contract_amplitudes(p64, bits)
-    assert rel_err(a, a64, 70) <= TOL
+    pbf, *_ = build(tz, spec, "bf16x3", 30)
+    abf = tz.tz_contract_amplitudes(pbf, bits)
+    errs = {m: rel_err(x, a128, 70) for m, x in (("tf32x3", a), ("c64", a64), ("bf16x3", abf))}
+    print("bristlecone70 d32 errors vs complex128:", {m: f"{e:.2e}" for m, e in errs.items()})
+    assert errs["c64"] <= 1e-2 and errs["tf32x3"] <= 1e-2 and errs["bf16x3"] <= 1e-1
     # an independent tree (pairwise greedy, other seed) and a different cap
     p2, _, tree2, sl2 = build(tz, spec, "c64", 29, algorithm="greedy", seed=11, restarts=32)
     assert not np.array_equal(tree.pairs(), tree2.pairs())
     a2 = tz.tz_contract_amplitudes(p2, bits)
-    assert rel_err(a2, a64, 70) <= TOL
+    assert rel_err(a2, a64, 70) <= 1e-2
     # Porter-Thomas scale: N p far from 0 and from the tail
     npk = np.abs(a64) ** 2 * 2.0 ** 70
     assert np.all(npk > 1e-6) and np.all(npk < 40)
@@ -96,7 +105,7 @@ def test_bristlecone70_depth32_porter_thomas_mean(tz):
     assert abs(npk.mean() - 1.0) < 0.75
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "c64", "bf16x3"])
+@pytest.mark.parametrize("prec", ["tf32x3", "c64", "bf16x3", "c128"])
 def test_bristlecone70_reduced_depth_vs_oracle(tz, prec):
     """All 70 qubits, depth 1+12+1, sliced (k >= 3), against the oracle."""
     spec = bris_spec(12, 3)
@@ -112,7 +121,7 @@ def test_bristlecone70_reduced_depth_vs_oracle(tz, prec):
     got = tz.tz_contract_amplitudes(plan, bits)
     err = rel_err(got, ref, 70)
     print(f"bristlecone70 d12 {prec}: max rel err {err:.2e}")
-    assert err <= (TOL if prec != "bf16x3" else 1e-3)
+    assert err <= {"c128": 1e-12, "bf16x3": 1e-3}.get(prec, TOL)
 
 
 def test_grid7x7_depth32_config2_properties(tz):
@@ -143,9 +152,31 @@ def test_grid7x7_depth32_config2_properties(tz):
             hi = tz.tz_contract_amplitudes(plan, bits)
             assert rel_err(lo + hi, a, 49) <= 1e-6
         results[prec] = a
-    assert rel_err(results["tf32x3"], results["c64"], 49) <= TOL
+    assert rel_err(results["tf32x3"], results["c64"], 49) <= 1e-3
     npk = np.abs(results["c64"]) ** 2 * 2.0 ** 49
     assert abs(npk.mean() - 1.0) < 0.5
+
+
+def test_grid7x7_depth32_errors_vs_complex128(tz):
+    """7x7 depth 1+32+1 (2^10 slices): the partial amplitude of slices
+    [0, 32) for 4 bitstrings in each FP32-class mode against complex128."""
+    import torch
+    spec = grid_spec(7, 7, 32, 2)
+    bits = ti.random_bitstrings(49, 4, 102)
+    circ = tz.tz_circuit_from_spec(spec)
+    net = tz.tz_network_from_circuit(circ, 0)
+    tree = tz.tz_path_greedy(net, restarts=32, seed=7, log2_max_intermediate=22, algorithm="elimination")
+    sl = tz.tz_slice_select(net, tree, 1, 10)
+    out = {}
+    for prec in ("c128", "c64", "tf32x3", "bf16x3"):
+        plan = tz.tz_plan_create(net, tree, sl, precision=prec, stream=torch.cuda.Stream(), use_graph=True,
+                                 max_bitstrings=4)
+        plan.bind()
+        plan.set_slice_range(0, 32)
+        out[prec] = tz.tz_contract_amplitudes(plan, bits)
+    errs = {m: rel_err(out[m], out["c128"], 49) for m in ("c64", "tf32x3", "bf16x3")}
+    print("grid7x7 d32 (32 slices) errors vs complex128:", {m: f"{e:.2e}" for m, e in errs.items()})
+    assert errs["c64"] <= 1e-3 and errs["tf32x3"] <= 1e-3 and errs["bf16x3"] <= 1e-1
 
 
 def test_grid7x7_reduced_depth_batch64_vs_oracle(tz):

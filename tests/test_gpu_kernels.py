@@ -131,6 +131,25 @@ def test_cgemm_tc_rejects_unsupported(env):
     assert e.value.code == -6
 
 
+@pytest.mark.parametrize("batch,m,n,k", [(1, 7, 3, 5), (3, 64, 64, 8), (2, 130, 17, 33), (1, 4, 1, 4096)])
+def test_cgemm_c128(env, batch, m, n, k):
+    """complex128 product (FP64 FMA): agrees with the complex128 definition
+    to FP64 rounding."""
+    tz, torch = env
+    rng = np.random.default_rng(m * 13 + k)
+    A = rng.standard_normal((batch, m, k)) + 1j * rng.standard_normal((batch, m, k))
+    B = rng.standard_normal((batch, n, k)) + 1j * rng.standard_normal((batch, n, k))
+    dA = torch.from_numpy(A.view(np.float64).copy()).cuda()
+    dB = torch.from_numpy(B.view(np.float64).copy()).cuda()
+    dC = torch.zeros(batch * m * n * 2, dtype=torch.float64, device="cuda")
+    tz.tz_op_cgemm("c128", batch, m, n, k, dA, m * k, dB, n * k, dC, m * n)
+    torch.cuda.synchronize()
+    C = dC.cpu().numpy().view(np.complex128).reshape(batch, m, n)
+    ref = linalg.cgemm(A, B)
+    bound = linalg.cgemm(np.abs(A), np.abs(B)).real
+    assert np.all(np.abs(C - ref) <= 4 * (k + 2) * 2.0 ** -53 * bound)
+
+
 def test_accumulate_fp64(env):
     tz, torch = env
     rng = np.random.default_rng(5)
