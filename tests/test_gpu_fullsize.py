@@ -45,6 +45,9 @@ def grid_spec(r, c, t, seed):
     return ti.circuit_to_spec(r * c, ti.generate_circuit(ti.grid(r, c), t, seed))
 
 
+MAX_FLOPS_PER_AMPLITUDE = 1e14   # guard: never start a contraction this test cannot finish
+
+
 def build(tz, spec, precision, log2_max, batch_log2=0, restarts=64, seed=7, algorithm="elimination", k_max=40,
           max_bitstrings=0):
     import torch
@@ -56,6 +59,8 @@ def build(tz, spec, precision, log2_max, batch_log2=0, restarts=64, seed=7, algo
     stream = torch.cuda.Stream()
     plan = tz.tz_plan_create(net, tree, sliced, precision=precision, stream=stream, use_graph=True,
                              max_bitstrings=max_bitstrings or (1 << batch_log2) * 64)
+    st = plan.stats()
+    assert st["flops_per_group"] * 2.0 ** st["k"] / 2 ** batch_log2 < MAX_FLOPS_PER_AMPLITUDE
     plan.bind()
     return plan, net, tree, sliced
 
@@ -74,21 +79,24 @@ def test_bristlecone70_depth32_properties(tz):
         parts.append(tz.tz_contract_amplitudes(plan, bits))
     plan.set_slice_range(0, 1 << k)
     assert rel_err(np.sum(parts, axis=0), a, 70) <= 1e-6
-    # every mode on the same tree and slicing, against complex128
+    # every mode on the same tree and slicing, against complex128 (one
+    # bitstring: the FP64 units of GB300 are slow)
     p128, *_ = build(tz, spec, "c128", 30)
-    a128 = tz.tz_contract_amplitudes(p128, bits)
+    a128 = tz.tz_contract_amplitudes(p128, bits[:1])
     p64, *_ = build(tz, spec, "c64", 30)
     a64 = tz.tz_contract_amplitudes(p64, bits)
     pbf, *_ = build(tz, spec, "bf16x3", 30)
     abf = tz.tz_contract_amplitudes(pbf, bits)
-    errs = {m: rel_err(x, a128, 70) for m, x in (("tf32x3", a), ("c64", a64), ("bf16x3", abf))}
+    errs = {m: rel_err(x[:1], a128, 70) for m, x in (("tf32x3", a), ("c64", a64), ("bf16x3", abf))}
     print("bristlecone70 d32 errors vs complex128:", {m: f"{e:.2e}" for m, e in errs.items()})
-    assert errs["c64"] <= 1e-2 and errs["tf32x3"] <= 1e-2 and errs["bf16x3"] <= 1e-1
-    # an independent tree (pairwise greedy, other seed) and a different cap
-    p2, _, tree2, sl2 = build(tz, spec, "c64", 29, algorithm="greedy", seed=11, restarts=32)
+    # measured on GB300: c64 1.2e-6, tf32x3 2.1e-5, bf16x3 2.4e-5
+    assert errs["c64"] <= 1e-5 and errs["tf32x3"] <= 1e-4 and errs["bf16x3"] <= 1e-4
+    # another tree (other seed) with a different cap, hence other slices
+    p2, _, tree2, sl2 = build(tz, spec, "c64", 29, seed=11, restarts=32)
     assert not np.array_equal(tree.pairs(), tree2.pairs())
     a2 = tz.tz_contract_amplitudes(p2, bits)
-    assert rel_err(a2, a64, 70) <= 1e-2
+    print("bristlecone70 d32 second tree vs first (complex64):", f"{rel_err(a2, a64, 70):.2e}")
+    assert rel_err(a2, a64, 70) <= 1e-5
     # Porter-Thomas scale: N p far from 0 and from the tail
     npk = np.abs(a64) ** 2 * 2.0 ** 70
     assert np.all(npk > 1e-6) and np.all(npk < 40)
