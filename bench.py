@@ -278,9 +278,10 @@ def main():
         S = int(max(1, min(4096, n_slices // world, 3.0 / max(one, 1e-6))))
     S = min(S, max(1, n_slices // world))
 
+    from paper_1907_11217_gb300 import shard
+
     def slice_range(step):
-        lo = ((step * world + rank) * S) % n_slices
-        return lo, min(n_slices, lo + S)
+        return shard.step_window(n_slices, world, rank, S, step)
 
     def one_step(step, reduce=True):
         lo, hi = slice_range(step)
@@ -288,7 +289,7 @@ def main():
         tz.tz_contract_amplitudes_device(plan, d_bits, d_out)
         if dist and reduce:
             with torch.cuda.stream(stream):
-                td.all_reduce(d_out)
+                shard.reduce_partials(d_out)
 
     for w in range(args.warmup):
         one_step(w)

@@ -260,20 +260,32 @@ class Contractor:
         return [[e for e in edges if e not in fixed_edges] for (_, _, edges) in self.net.leaves]
 
     def _busiest_segment(self, legs, pairs, mx, fixed_segs):
-        """Segment whose edges sit in the most intermediates of >= mx-1 legs."""
+        """Extra segment to slice: among the segments in intermediates of >=
+        mx-1 legs, the one whose fixing gives the smallest largest
+        intermediate along the current order (ties: fewer intermediates at
+        that size, then the most frequent segment)."""
         sets = [frozenset(s) for s in legs]
+        inter = []
         count = {}
         for (a, b) in pairs:
             so = sets[a] ^ sets[b]
             sets.append(so)
+            inter.append(so)
             if len(so) >= mx - 1:
-                w = 4 if len(so) == mx else 1
                 for seg in {self.net.edge_seg[e] for e in so}:
-                    count[seg] = count.get(seg, 0) + w
-        cands = [(c, s) for s, c in count.items() if s not in fixed_segs]
+                    count[seg] = count.get(seg, 0) + (4 if len(so) == mx else 1)
+        cands = sorted((c, seg) for seg, c in count.items() if seg not in fixed_segs)[-24:]
         if not cands:
             return None
-        return max(cands, key=lambda cs: (cs[0], -cs[1][0], -cs[1][1]))[1]
+        best = None
+        for c, seg in cands:
+            drop = self.net.edges_of_segments([seg])
+            sizes = [len(x) - len(x & drop) for x in inter]
+            m = max(sizes)
+            key = (m, sizes.count(m), -c)
+            if best is None or key < best[0]:
+                best = (key, seg)
+        return best[1]
 
     def _fixed_map(self, values):
         fixed = {}

@@ -1,0 +1,36 @@
+"""Slice sharding across ranks (one process per GPU).
+
+Slices are independent subtasks with no shared data (Sec. 2), so ranks
+split the slice range and exchange nothing but their FP64 partial sums
+(Sec. 1: subtask results add up to the amplitude): one all-reduce of 2n
+doubles per call.
+"""
+
+
+def partition(n_slices: int, world: int, rank: int):
+    """Contiguous block of slices [lo, hi) owned by `rank` (sizes differ by at
+    most one slice)."""
+    if world < 1 or not 0 <= rank < world or n_slices < 0:
+        raise ValueError("bad partition request")
+    base, extra = divmod(n_slices, world)
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
+def step_window(n_slices: int, world: int, rank: int, per_rank: int, step: int):
+    """Slices [lo, hi) a rank contracts in one timed step when every rank
+    takes `per_rank` consecutive slices and successive steps move on through
+    the range (wrapping)."""
+    if per_rank < 1:
+        raise ValueError("per_rank must be >= 1")
+    lo = ((step * world + rank) * per_rank) % max(n_slices, 1)
+    return lo, min(n_slices, lo + per_rank)
+
+
+def reduce_partials(t):
+    """Sum a tensor of FP64 partial amplitudes over all ranks in place (no-op
+    without an initialised process group of more than one rank)."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t
