@@ -173,6 +173,13 @@ int tz_path_greedy(const tz_network *net, const tz_path_opts *opts, tz_tree **ou
     }
     tz::Pairs pr = algo == TZ_PATH_GREEDY ? tz::greedy_tree(net->n, alpha, temp, tz::splitmix64_next(rng))
                                           : tz::elimination_tree(net->n, temp, tz::splitmix64_next(rng));
+    if (o.log2_max_intermediate > 0) {
+      // local three-way rotations under the slicing this tree would get
+      std::vector<int> sl = tz::select_slices(net->n, pr, o.log2_max_intermediate, 40, cm);
+      std::vector<char> flag(net->n.indices.size(), 0);
+      for (int e : sl) flag[e] = 1;
+      pr = tz::rotate_tree(net->n, pr, flag, cm, 16);
+    }
     int mb = 0;
     double sc = tree_score(net->n, pr, o.log2_max_intermediate, cm, &mb);
     if (trial == 0 || sc < best_score) {

@@ -376,6 +376,128 @@ Pairs elimination_tree(const Network &net, double temperature, uint64_t seed) {
   return pairs;
 }
 
+// ------------------------------------------------------- local rotations
+// Three tensors S, Y1, Y2 can be combined as ((S Y1) Y2), ((S Y2) Y1) or
+// ((Y1 Y2) S); the result is the same, the intermediate differs. A pass
+// visits every node whose child is an internal node and keeps the cheapest
+// of the three under the time model (steps that run once at bind time cost
+// nothing per group). Typical win: a large stem absorbing two small branches
+// one after the other is read once instead of twice.
+namespace {
+struct Node {
+  int l = -1, r = -1;
+};
+std::vector<int> keep_of(const std::vector<int> &x, const std::vector<int> &y, const std::vector<int> &z,
+                         const std::vector<int> &out, const Network &net) {
+  std::vector<int> u = set_union(x, y), k;
+  for (int i : u)
+    if (net.is_open(i) || std::binary_search(z.begin(), z.end(), i) || std::binary_search(out.begin(), out.end(), i))
+      k.push_back(i);
+  return k;
+}
+StepInfo classify(const std::vector<int> &x, const std::vector<int> &y, const std::vector<int> &c, bool var) {
+  StepInfo st;
+  for (int i : x) {
+    bool iny = std::binary_search(y.begin(), y.end(), i), inc = std::binary_search(c.begin(), c.end(), i);
+    if (iny)
+      (inc ? st.batch : st.contr).push_back(i);
+    else
+      st.freeA.push_back(i);
+  }
+  for (int i : y)
+    if (!std::binary_search(x.begin(), x.end(), i)) st.freeB.push_back(i);
+  st.var = var;
+  return st;
+}
+}  // namespace
+
+Pairs rotate_tree(const Network &net, const Pairs &pairs, const std::vector<char> &sliced, const CostModel &cm,
+                  int max_passes) {
+  const int L = (int)net.leaves.size();
+  Pairs cur = pairs;
+  for (int pass = 0; pass < max_passes; pass++) {
+    TreeInfo ti = analyse_tree(net, cur, sliced);
+    const int NS = (int)cur.size();
+    std::vector<Node> nd(L + NS);
+    for (int s = 0; s < NS; s++) nd[L + s] = {cur[s].first, cur[s].second};
+    auto cost = [&](const StepInfo &st) { return st.var ? cm.step_time(st) : 0.0; };
+    std::vector<char> touched(L + NS, 0);
+    bool changed = false;
+    for (int q = L; q < L + NS; q++) {
+      if (touched[q]) continue;
+      for (int side = 0; side < 2; side++) {
+        const int p = side == 0 ? nd[q].l : nd[q].r;
+        const int y2 = side == 0 ? nd[q].r : nd[q].l;
+        if (p < L || touched[p]) continue;
+        const int s0 = nd[p].l, y1 = nd[p].r;
+        const auto &S = ti.sets[s0], &Y1 = ti.sets[y1], &Y2 = ti.sets[y2], &Out = ti.sets[q];
+        const bool vS = ti.var[s0], v1 = ti.var[y1], v2 = ti.var[y2];
+        // the three ways: first pair, then the third tensor
+        const int first[3][2] = {{s0, y1}, {s0, y2}, {y1, y2}};
+        const int third[3] = {y2, y1, s0};
+        double best = 0;
+        int best_k = 0;
+        for (int k = 0; k < 3; k++) {
+          const auto &X = ti.sets[first[k][0]], &Y = ti.sets[first[k][1]], &Z = ti.sets[third[k]];
+          const bool vxy = ti.var[first[k][0]] || ti.var[first[k][1]];
+          std::vector<int> w = keep_of(X, Y, Z, Out, net);
+          if (k > 0 && (int)w.size() > ti.max_bits) continue;  // never raise the memory peak
+          double c = cost(classify(X, Y, w, vxy)) + cost(classify(w, Z, Out, vxy || ti.var[third[k]]));
+          if (k == 0 || c < best) {
+            best = c;
+            best_k = k;
+          }
+        }
+        (void)S;
+        (void)Y1;
+        (void)Y2;
+        (void)vS;
+        (void)v1;
+        (void)v2;
+        if (best_k == 0) continue;
+        // keep it only if clearly cheaper than the current arrangement
+        {
+          const auto &X = ti.sets[s0], &Y = ti.sets[y1], &Z = ti.sets[y2];
+          std::vector<int> w = keep_of(X, Y, Z, Out, net);
+          double c0 = cost(classify(X, Y, w, ti.var[s0] || ti.var[y1])) +
+                      cost(classify(w, Z, Out, ti.var[s0] || ti.var[y1] || ti.var[y2]));
+          if (best >= 0.98 * c0) continue;
+        }
+        nd[p] = {first[best_k][0], first[best_k][1]};
+        if (side == 0)
+          nd[q] = {p, third[best_k]};
+        else
+          nd[q] = {third[best_k], p};
+        touched[p] = touched[q] = 1;
+        changed = true;
+        break;
+      }
+    }
+    if (!changed) break;
+    // re-linearise: post-order from the root
+    Pairs out;
+    std::vector<int> newid(L + NS, -1);
+    for (int l = 0; l < L; l++) newid[l] = l;
+    std::vector<std::pair<int, int>> stack;  // (node, state)
+    stack.push_back({L + NS - 1, 0});
+    while (!stack.empty()) {
+      auto [n, st] = stack.back();
+      stack.pop_back();
+      if (n < L) continue;
+      if (st == 0) {
+        stack.push_back({n, 1});
+        stack.push_back({nd[n].r, 0});
+        stack.push_back({nd[n].l, 0});
+      } else {
+        out.push_back({newid[nd[n].l], newid[nd[n].r]});
+        newid[n] = L + (int)out.size() - 1;
+      }
+    }
+    cur = out;
+  }
+  return cur;
+}
+
 // ------------------------------------------------------------------ slicing
 std::vector<int> select_slices(const Network &net, const Pairs &pairs, int log2_max, int k_max,
                                const CostModel &cm) {

@@ -98,6 +98,8 @@ double group_time(const TreeInfo &ti, const CostModel &cm);
 
 Pairs greedy_tree(const Network &net, double alpha, double temperature, uint64_t seed);
 Pairs elimination_tree(const Network &net, double temperature, uint64_t seed);
+Pairs rotate_tree(const Network &net, const Pairs &pairs, const std::vector<char> &sliced, const CostModel &cm,
+                  int max_passes);
 std::vector<int> select_slices(const Network &net, const Pairs &pairs, int log2_max, int k_max,
                                const CostModel &cm);
 
