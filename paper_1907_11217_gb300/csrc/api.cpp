@@ -410,7 +410,7 @@ int tz_op_cgemm_scratch_bytes(int precision, int64_t batch, int64_t m, int64_t n
   if (precision == TZ_TF32X3 || precision == TZ_BF16X3) {
     if (!tz::dev::cgemm_tc_supported(precision, m, n, k))
       tz::fail(TZ_EUNSUPPORTED, "shape not supported by the tensor-core product");
-    *bytes = tz::dev::cgemm_tc_scratch_bytes(precision, batch, n, k);
+    *bytes = tz::dev::cgemm_tc_scratch_bytes(precision, batch, m, n, k);
   } else if (precision != TZ_C64_SIMT && precision != TZ_C128_SIMT) {
     tz::fail(TZ_EINVAL, "unknown precision");
   }
@@ -434,7 +434,7 @@ int tz_op_cgemm(int precision, int64_t batch, int64_t m, int64_t n, int64_t k, c
   } else if (precision == TZ_TF32X3 || precision == TZ_BF16X3) {
     if (!tz::dev::cgemm_tc_supported(precision, m, n, k))
       tz::fail(TZ_EUNSUPPORTED, "shape not supported by the tensor-core product");
-    size_t need = tz::dev::cgemm_tc_scratch_bytes(precision, batch, n, k);
+    size_t need = tz::dev::cgemm_tc_scratch_bytes(precision, batch, m, n, k);
     REQUIRE(scratch_bytes >= need && (need == 0 || scratch), "scratch too small");
     tz::cuda_check(tz::dev::launch_cgemm_tc(precision, (const float2 *)A, (const float2 *)B, (float2 *)C, batch, m, n,
                                             k, sa, sb, sc, nullptr, scratch, scratch_bytes, s),

@@ -15,8 +15,9 @@
 // dropped lo*lo term is below 2^-22 |a||b|.
 //
 // Pipeline per CTA (one 128-row tile of C, up to 128 complex columns):
-//   warp 0     : TMA loads of the A tile (128 rows x 32 floats, 128B swizzle)
-//                and of the prepared hi/lo B tiles, into a ring of stages;
+//   warp 0     : TMA loads of the A tile (TF32: 128 rows x 16 floats, 64B
+//                swizzle; BF16: 128 rows x 32 floats, 128B swizzle) and of
+//                the prepared hi/lo B tiles, into a ring of stages;
 //   warps 2..5 : split each A tile in shared memory (hi in place, lo beside
 //                it), then, after the last product, the epilogue
 //                (tcgen05.ld TMEM -> registers -> global);
@@ -40,7 +41,13 @@ namespace dev {
 namespace {
 
 constexpr int BM = 128;           // C rows per tile = TMEM lanes
-constexpr int kStageFloats = 32;  // K (real) per stage: one 128-byte swizzle row
+// K (real values) per stage, chosen so that the split operands have 64-byte
+// rows: TF32 16 (the FP32 A tile has 64-byte rows too; the small stages make
+// a ring of 4 to 8, which hides the TMA round trip), BF16 32 (the FP32 A
+// tile has 128-byte rows). BF16 stages of 16 values, with 32-byte rows,
+// measured slower.
+template <int MODE>
+__host__ __device__ constexpr int stage_k() { return MODE == 0 ? 16 : 32; }
 constexpr int kThreads = 320;  // TMA, MMA, 4 split warps, 4 epilogue warps
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
@@ -94,13 +101,6 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, in
           smem_u32(dst)),
       "l"((uint64_t)tm), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
-}
-
-// K-major operand in the 128-byte swizzled layout written by TMA: rows of
-// 128 bytes, 8-row atoms of 1024 bytes (stride-dimension offset 1024).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
 // Instruction descriptor: FP32 accumulator, TF32 A and B, both K-major,
@@ -175,8 +175,11 @@ struct TcArgs {
   int64_t sC;          // complex elements between batches of C
   int n_tiles_m, n_tiles_n, kblocks;
   int NT;              // rows of the prepared B per batch
-  int scatter;         // 1: write C through sc
+  int scatter;         // 1: write C through sc; 2: likewise, the three lowest
+                       // bits of C being n bits 0..2 (stores staged per warp)
   int tma_store;       // 1: row-major C written by bulk tensor stores (tmC)
+  int ksplit, kb_per;  // K split into ksplit ranges of kb_per k-blocks; with
+  int64_t split_stride;  // ksplit > 1, range s writes row-major partials at C + s * split_stride
   CScatter sc;
 };
 
@@ -186,16 +189,16 @@ __device__ __forceinline__ int64_t scatter_bits(int64_t v, int n, const int8_t *
   return o;
 }
 
-// Per stage: the FP32 A tile as loaded (128 rows x 128 B), the split A
-// (TF32: hi in place + lo tile of 16 KB; BF16: hi and lo tiles of 8 KB),
-// and the prepared B hi and lo tiles (BNP rows x 128 B TF32 / 64 B BF16).
+// Per stage: the FP32 A tile as loaded (128 rows x 64 B TF32 / 128 B BF16),
+// the split A (TF32: hi in place + lo tile of 8 KB; BF16: hi and lo tiles of
+// 8 KB), and the prepared B hi and lo tiles (BNP rows x 64 B).
 // TMEM holds two accumulators (BNP columns each, at least 32) so the
 // epilogue of one tile overlaps the products of the next.
 template <int MODE, int BNP, int STAGES>
 struct TcSmem {
-  static constexpr uint32_t A_BYTES = BM * 128;                         // FP32 tile as loaded
-  static constexpr uint32_t AS_BYTES = MODE == MODE_TF32 ? BM * 128 : BM * 64;  // one split half
-  static constexpr uint32_t B_BYTES = MODE == MODE_TF32 ? BNP * 128 : BNP * 64;
+  static constexpr uint32_t A_BYTES = BM * stage_k<MODE>() * 4;         // FP32 tile as loaded
+  static constexpr uint32_t AS_BYTES = BM * 64;                          // one split half
+  static constexpr uint32_t B_BYTES = BNP * 64;
   static constexpr uint32_t A_LO = MODE == MODE_TF32 ? A_BYTES : A_BYTES + AS_BYTES;  // offset of A lo
   static constexpr uint32_t A_HI = MODE == MODE_TF32 ? 0 : A_BYTES;                  // offset of A hi
   static constexpr uint32_t STAGE = A_BYTES + (MODE == MODE_TF32 ? AS_BYTES : 2 * AS_BYTES) + 2 * B_BYTES;
@@ -235,13 +238,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t per_batch = (int64_t)a.n_tiles_m * a.n_tiles_n;
-  const int64_t n_tiles = per_batch * a.batch;
+  const int64_t n_tiles = per_batch * a.batch * a.ksplit;
   struct Tile {
     int64_t z;
-    int mt, nt, rowA, rowB;
+    int mt, nt, rowA, rowB, ks, kb0, kb1;
   };
   auto decode = [&](int64_t t) {
     Tile d;
+    d.ks = (int)(t % a.ksplit);
+    t /= a.ksplit;
+    d.kb0 = d.ks * a.kb_per;
+    d.kb1 = min(a.kblocks, d.kb0 + a.kb_per);
     d.z = t / per_batch;
     const int64_t rem = t - d.z * per_batch;
     d.mt = (int)(rem / a.n_tiles_n);
@@ -281,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         const Tile d = decode(t);
-        for (int kb = 0; kb < a.kblocks; kb++, g++) {
+        for (int kb = d.kb0; kb < d.kb1; kb++, g++) {
           const int s = (int)(g % STAGES);
           const int64_t round = g / STAGES;
           if (round > 0 && !mbar_wait(&empty[s], (uint32_t)((round - 1) & 1), abort_flag)) {
@@ -289,9 +296,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           mbar_expect_tx(&full[s], L::A_BYTES + 2 * L::B_BYTES);
-          tma_load_2d(A_raw(s), &tmA, kb * kStageFloats, d.rowA, &full[s]);
-          tma_load_2d(B_hi(s), &tmBh, kb * kStageFloats, d.rowB, &full[s]);
-          tma_load_2d(B_lo(s), &tmBl, kb * kStageFloats, d.rowB, &full[s]);
+          tma_load_2d(A_raw(s), &tmA, kb * stage_k<MODE>(), d.rowA, &full[s]);
+          tma_load_2d(B_hi(s), &tmBh, kb * stage_k<MODE>(), d.rowB, &full[s]);
+          tma_load_2d(B_lo(s), &tmBl, kb * stage_k<MODE>(), d.rowB, &full[s]);
         }
       }
       if (*abort_flag) {
@@ -303,8 +310,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = MODE == MODE_TF32 ? idesc_tf32(BNP) : idesc_bf16(BNP);
-      // K per instruction: 8 TF32 or 16 BF16 values, 32 bytes either way
-      constexpr int kSteps = MODE == MODE_TF32 ? kStageFloats / 8 : kStageFloats / 16;
+      // K per instruction: 8 TF32 or 16 BF16 values, 32 bytes either way;
+      // two instructions per 64-byte row
+      constexpr int kSteps = 2;
       int64_t g = 0, i = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, i++) {
@@ -313,7 +321,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (u > 0 && !mbar_wait(&tempty[b], (uint32_t)((u - 1) & 1), abort_flag)) break;
         tc_fence_after();
         const uint32_t d_acc = tmem + (uint32_t)(b * L::ACC_COLS);
-        for (int kb = 0; kb < a.kblocks; kb++, g++) {
+        const Tile d = decode(t);
+        for (int kb = 0; kb < d.kb1 - d.kb0; kb++, g++) {
           const int s = (int)(g % STAGES);
           if (!mbar_wait(&conv[s], (uint32_t)((g / STAGES) & 1), abort_flag)) {
             ok = false;
@@ -325,15 +334,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int kk = 0; kk < kSteps; kk++) {
             const uint32_t off = kk * 32;
+            const uint64_t dah = sw64_desc(ah + off), dal = sw64_desc(al + off);
+            const uint64_t dbh = sw64_desc(bh + off), dbl = sw64_desc(bl + off);
             if (MODE == MODE_TF32) {
-              const uint64_t dah = sw128_desc(ah + off), dal = sw128_desc(al + off);
-              const uint64_t dbh = sw128_desc(bh + off), dbl = sw128_desc(bl + off);
               umma_tf32(d_acc, dah, dbh, idesc, (kb | kk) != 0);
               umma_tf32(d_acc, dah, dbl, idesc, 1);
               umma_tf32(d_acc, dal, dbh, idesc, 1);
             } else {
-              const uint64_t dah = sw64_desc(ah + off), dal = sw64_desc(al + off);
-              const uint64_t dbh = sw64_desc(bh + off), dbl = sw64_desc(bl + off);
               umma_f16(d_acc, dah, dbh, idesc, (kb | kk) != 0);
               umma_f16(d_acc, dah, dbl, idesc, 1);
               umma_f16(d_acc, dal, dbh, idesc, 1);
@@ -352,7 +359,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     int64_t g = 0;
     bool ok = true;
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-      for (int kb = 0; kb < a.kblocks; kb++, g++) {
+      const Tile d = decode(tile);
+      for (int kb = 0; kb < d.kb1 - d.kb0; kb++, g++) {
         const int s = (int)(g % STAGES);
         if (!mbar_wait(&full[s], (uint32_t)((g / STAGES) & 1), abort_flag)) {
           ok = false;
@@ -412,7 +420,37 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!mbar_wait(&tfull[b], (uint32_t)((i >> 1) & 1), abort_flag)) break;
       tc_fence_after();
       const uint32_t taddr = tmem + (uint32_t)(b * L::ACC_COLS) + ((uint32_t)(q * 32) << 16);
-      if (a.scatter) {
+      if (a.scatter == 2) {
+        // a warp's 32 rows x 8 complex go through its staging buffer (16-byte
+        // chunk j of row r at chunk j ^ ((r >> 1) & 3), so both sides are
+        // free of bank conflicts); then each store instruction writes 8 rows
+        // x 64 contiguous bytes (lane: row 8 u + lane / 4, pair lane % 4)
+        const int64_t om = scatter_bits(d.z, a.sc.nb, a.sc.pb) + scatter_bits((int64_t)d.mt * BM + row, a.sc.nm, a.sc.pm);
+        int64_t om_u[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) om_u[u] = __shfl_sync(0xffffffffu, om, 8 * u + (lane >> 2));
+        uint8_t *stg = staging + (warp - 6) * 4096;
+#pragma unroll 1
+        for (int c = 0; c < BNP; c += 16) {
+          uint32_t r[16];
+          tmem_ld16(taddr + (uint32_t)c, r);
+          if (n0 + c / 2 >= a.N) break;  // N is a multiple of 8 here
+          uint8_t *buf = stg + (((c >> 4) & 1) << 11);
+#pragma unroll
+          for (int j = 0; j < 4; j++)
+            *reinterpret_cast<uint4 *>(buf + lane * 64 + ((j ^ ((lane >> 1) & 3)) << 4)) =
+                make_uint4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+          __syncwarp();
+          const int64_t col = coloff[c / 2] + 2 * (lane & 3);
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            const int rr = 8 * u + (lane >> 2);
+            const uint4 v =
+                *reinterpret_cast<const uint4 *>(buf + rr * 64 + (((lane & 3) ^ ((rr >> 1) & 3)) << 4));
+            *reinterpret_cast<uint4 *>(a.C + om_u[u] + col) = v;
+          }
+        }
+      } else if (a.scatter) {
         const int64_t om = scatter_bits(d.z, a.sc.nb, a.sc.pb) + scatter_bits((int64_t)d.mt * BM + row, a.sc.nm, a.sc.pm);
 #pragma unroll 1
         for (int c = 0; c < BNP; c += 16) {
@@ -454,7 +492,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       } else {
-        float2 *crow = a.C + d.z * a.sC + ((int64_t)d.mt * BM + row) * a.N;
+        float2 *crow = a.C + d.ks * a.split_stride + d.z * a.sC + ((int64_t)d.mt * BM + row) * a.N;
 #pragma unroll 1
         for (int c = 0; c < BNP; c += 16) {
           uint32_t r[16];
@@ -524,6 +562,23 @@ __global__ void prep_b_kernel(const float2 *__restrict__ B, void *__restrict__ B
   }
 }
 
+// Sum of the ksplit row-major partials of a split-K product, in a fixed order
+// (so results do not depend on scheduling), written to row-major C whose
+// batches are sC apart.
+__global__ void split_reduce_kernel(const float2 *__restrict__ P, float2 *__restrict__ C, int ksplit,
+                                    int64_t split_stride, int64_t MN, int64_t sC) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < split_stride;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float2 v = P[e];
+    for (int s = 1; s < ksplit; s++) {
+      const float2 w = P[s * split_stride + e];
+      v.x += w.x;
+      v.y += w.y;
+    }
+    C[(e / MN) * sC + e % MN] = v;
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
@@ -538,19 +593,21 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D tensor map: rows x cols (cols contiguous), box = 32 x box_rows, zero
-// fill outside; FP32 with 128-byte swizzle or BF16 with 64-byte swizzle.
-bool make_map(CUtensorMap *tm, const void *base, int64_t cols, int64_t rows, int box_rows, bool bf16) {
+// 2D tensor map: rows x cols (cols contiguous), box = box_cols x box_rows,
+// zero fill outside; box rows of 128 bytes (128-byte swizzle) or 64 bytes
+// (64-byte swizzle).
+bool make_map(CUtensorMap *tm, const void *base, int64_t cols, int64_t rows, int box_cols, int box_rows, bool bf16) {
   auto fn = encode_fn();
   if (!fn) return false;
   const int esz = bf16 ? 2 : 4;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(cols * esz)};
-  cuuint32_t box[2] = {(cuuint32_t)kStageFloats, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                   const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  bf16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  box_cols * esz == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -583,12 +640,15 @@ cudaError_t run_tc(const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensor
 template <int MODE>
 cudaError_t dispatch(int bnp, const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensorMap &tbl,
                      const CUtensorMap &tc, const TcArgs &args, int64_t n_blocks, cudaStream_t s) {
+  // stages: TF32 as many as fit beside the epilogue staging (at most 8);
+  // BF16 as measured best
+  constexpr bool T = MODE == MODE_TF32;
   switch (bnp) {
-    case 16: return run_tc<MODE, 16, 4>(ta, tbh, tbl, tc, args, n_blocks, s);
-    case 32: return run_tc<MODE, 32, 4>(ta, tbh, tbl, tc, args, n_blocks, s);
-    case 64: return run_tc<MODE, 64, 4>(ta, tbh, tbl, tc, args, n_blocks, s);
-    case 128: return run_tc<MODE, 128, 3>(ta, tbh, tbl, tc, args, n_blocks, s);
-    default: return run_tc<MODE, 256, MODE == MODE_TF32 ? 2 : 3>(ta, tbh, tbl, tc, args, n_blocks, s);
+    case 16: return run_tc<MODE, 16, T ? 8 : 4>(ta, tbh, tbl, tc, args, n_blocks, s);
+    case 32: return run_tc<MODE, 32, T ? 8 : 4>(ta, tbh, tbl, tc, args, n_blocks, s);
+    case 64: return run_tc<MODE, 64, T ? 8 : 4>(ta, tbh, tbl, tc, args, n_blocks, s);
+    case 128: return run_tc<MODE, 128, T ? 6 : 3>(ta, tbh, tbl, tc, args, n_blocks, s);
+    default: return run_tc<MODE, 256, T ? 4 : 3>(ta, tbh, tbl, tc, args, n_blocks, s);
   }
 }
 
@@ -603,12 +663,29 @@ bool cgemm_tc_supported(int precision, int64_t M, int64_t N, int64_t K) {
   return true;
 }
 
-size_t cgemm_tc_scratch_bytes(int precision, int64_t batch, int64_t N, int64_t K) {
+// K ranges per product: products with fewer tiles than half the 152 SMs of
+// GB300 and a long K split K so that the ranges fill the SMs, each range at
+// least 32 k-blocks and the partials at most 64 MiB. A function of the shape
+// alone, so scratch sized by a plan covers every launch (a launch writing C
+// through a scatter map does not split).
+static int split_k(int precision, int64_t batch, int64_t M, int64_t N, int64_t K) {
+  const int bnp = tile_cols(N);
+  const int64_t tiles = batch * (M / BM) * ((2 * N + bnp - 1) / bnp);
+  const int sk = precision == TZ_BF16X3 ? stage_k<MODE_BF16>() : stage_k<MODE_TF32>();
+  const int64_t kblocks = (2 * K + sk - 1) / sk;
+  int64_t s = std::min<int64_t>({16, 152 / std::max<int64_t>(tiles, 1), kblocks / 32});
+  while (s > 1 && s * batch * M * N * 8 > (int64_t(64) << 20)) s--;
+  return s < 2 ? 1 : (int)s;
+}
+
+size_t cgemm_tc_scratch_bytes(int precision, int64_t batch, int64_t M, int64_t N, int64_t K) {
   if (precision != TZ_TF32X3 && precision != TZ_BF16X3) return 0;
   const int bnp = tile_cols(N);
   const int64_t nt = (2 * N + bnp - 1) / bnp;
   const int esz = precision == TZ_TF32X3 ? 4 : 2;
-  return (size_t)(2 * batch * nt * bnp * 2 * K * esz + 256);
+  const size_t half = ((size_t)(batch * nt * bnp * 2 * K * esz) + 255) & ~size_t(255);
+  const int ks = split_k(precision, batch, M, N, K);
+  return 2 * half + (ks > 1 ? (size_t)(ks * batch * M * N * 8) : 0) + 256;
 }
 
 cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M,
@@ -622,7 +699,7 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
   const int64_t rowsA = batch * M, rowsB = batch * (int64_t)NT;
   if (rowsA >= (int64_t(1) << 31) || rowsB >= (int64_t(1) << 31) || 2 * K >= (int64_t(1) << 31))
     return cudaErrorNotSupported;
-  if (scratch_bytes < cgemm_tc_scratch_bytes(precision, batch, N, K) || !scratch) return cudaErrorInvalidValue;
+  if (scratch_bytes < cgemm_tc_scratch_bytes(precision, batch, M, N, K) || !scratch) return cudaErrorInvalidValue;
   const bool bf16 = precision == TZ_BF16X3;
   const size_t half = (size_t)(batch * NT * 2 * K) * (bf16 ? 2 : 4);
   char *Bh = static_cast<char *>(scratch);
@@ -638,8 +715,9 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
     if (e != cudaSuccess) return e;
   }
   CUtensorMap ta, tbh, tbl;
-  if (!make_map(&ta, A, 2 * K, rowsA, BM, false) || !make_map(&tbh, Bh, 2 * K, rowsB, bnp, bf16) ||
-      !make_map(&tbl, Bl, 2 * K, rowsB, bnp, bf16))
+  const int sk = bf16 ? stage_k<MODE_BF16>() : stage_k<MODE_TF32>();
+  if (!make_map(&ta, A, 2 * K, rowsA, sk, BM, false) || !make_map(&tbh, Bh, 2 * K, rowsB, sk, bnp, bf16) ||
+      !make_map(&tbl, Bl, 2 * K, rowsB, sk, bnp, bf16))
     return cudaErrorInvalidValue;
   TcArgs args{};
   args.C = C;
@@ -650,11 +728,23 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
   args.sC = sC;
   args.n_tiles_m = (int)(M / BM);
   args.n_tiles_n = n_tiles_n;
-  args.kblocks = (int)((2 * K + kStageFloats - 1) / kStageFloats);
+  args.kblocks = (int)((2 * K + sk - 1) / sk);
+  const int ks = sc ? 1 : split_k(precision, batch, M, N, K);
+  args.ksplit = ks;
+  args.kb_per = (args.kblocks + ks - 1) / ks;
+  args.split_stride = batch * M * N;
+  float2 *P = nullptr;  // split-K partials, after the prepared B
+  if (ks > 1) P = reinterpret_cast<float2 *>(Bl + ((half + 255) & ~size_t(255)));
   args.NT = NT;
   args.scatter = sc ? 1 : 0;
-  if (sc) args.sc = *sc;
-  const int64_t n_tiles = batch * args.n_tiles_m * (int64_t)n_tiles_n;
+  if (sc) {
+    args.sc = *sc;
+    // n bits 0..2 lowest in C, C 16-byte aligned: whole 64-byte runs per row
+    if (sc->nn >= 3 && sc->pn[0] == 0 && sc->pn[1] == 1 && sc->pn[2] == 2 &&
+        (reinterpret_cast<uintptr_t>(C) & 15) == 0)
+      args.scatter = 2;
+  }
+  const int64_t n_tiles = batch * args.n_tiles_m * (int64_t)n_tiles_n * ks;
   static int n_sm = 0;
   if (!n_sm) {
     int dev = 0;
@@ -666,7 +756,12 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
   // 16-float boxes (64-byte swizzle), clipped at the tensor edge
   CUtensorMap tcm;
   std::memset(&tcm, 0, sizeof(tcm));
-  if (!sc && sC == M * N && (N % 2) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0) {
+  if (ks > 1) {
+    // partials row-major in scratch; the reduce kernel writes C
+    args.C = P;
+    args.sC = M * N;
+    args.scatter = 0;
+  } else if (!sc && sC == M * N && (N % 2) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0) {
     auto fn = encode_fn();
     cuuint64_t dims[2] = {(cuuint64_t)(2 * N), (cuuint64_t)(batch * M)};
     cuuint64_t strides[1] = {(cuuint64_t)(2 * N * 4)};
@@ -677,8 +772,13 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
       args.tma_store = 1;
   }
-  return bf16 ? dispatch<MODE_BF16>(bnp, ta, tbh, tbl, tcm, args, n_blocks, s)
-              : dispatch<MODE_TF32>(bnp, ta, tbh, tbl, tcm, args, n_blocks, s);
+  cudaError_t e = bf16 ? dispatch<MODE_BF16>(bnp, ta, tbh, tbl, tcm, args, n_blocks, s)
+                       : dispatch<MODE_TF32>(bnp, ta, tbh, tbl, tcm, args, n_blocks, s);
+  if (e != cudaSuccess || ks == 1) return e;
+  const int64_t total = batch * M * N;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+  split_reduce_kernel<<<blocks, 256, 0, s>>>(P, C, ks, total, M * N, sC);
+  return cudaGetLastError();
 }
 
 int tc_take_error() {

@@ -58,7 +58,7 @@ extern "C" int tz_op_cgemm_static(int precision, int64_t batch, int64_t m, int64
       tz::fail(TZ_EINVAL, "tz_op_cgemm_static serves the split-precision modes (TZ_TF32X3, TZ_BF16X3)");
     if (!tz::dev::cgemm_tc_supported(precision, m, n, k))
       tz::fail(TZ_EUNSUPPORTED, "shape not supported by the tensor-core product");
-    const size_t need = tz::dev::cgemm_tc_scratch_bytes(precision, batch, n, k);
+    const size_t need = tz::dev::cgemm_tc_scratch_bytes(precision, batch, m, n, k);
     if (need > kStaticScratchBytes)
       tz::fail(TZ_EINVAL, "product needs " + std::to_string(need) + " bytes of scratch; the static scratch holds " +
                               std::to_string(kStaticScratchBytes) + " (use tz_op_cgemm with caller scratch)");

@@ -126,7 +126,9 @@ bool cgemm_tc_supported(int precision, int64_t M, int64_t N, int64_t K);
 // Read and clear the flag a tensor-core kernel raises when a bounded wait
 // times out (synchronous; 1 = a wait gave up).
 int tc_take_error();
-size_t cgemm_tc_scratch_bytes(int precision, int64_t batch, int64_t N, int64_t K);
+// Device scratch of one tensor-core product: the prepared hi/lo copies of B
+// and, for products that split K across CTAs, the partial results.
+size_t cgemm_tc_scratch_bytes(int precision, int64_t batch, int64_t M, int64_t N, int64_t K);
 cudaError_t launch_accumulate(const AccumArgs &a, cudaStream_t s);
 cudaError_t launch_accumulate_plain(const float2 *part, double2 *acc, int64_t n, double sre, double sim,
                                     cudaStream_t s);

@@ -187,7 +187,7 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
             dev::cgemm_tc_supported(o.precision, ps.M, ps.N, ps.K) &&
             !(ps.N <= 4 && ps.K <= 16);
     ps.skinny = !ps.tc && ps.N <= 4 && ps.K <= 16 && ps.M >= 256;
-    if (ps.tc) ps.tc_scratch = (int64_t)dev::cgemm_tc_scratch_bytes(o.precision, ps.batch, ps.N, ps.K);
+    if (ps.tc) ps.tc_scratch = (int64_t)dev::cgemm_tc_scratch_bytes(o.precision, ps.batch, ps.M, ps.N, ps.K);
   }
   p->T[p->root].lay = natural(p->root);
   p->T[p->root].fixed = true;

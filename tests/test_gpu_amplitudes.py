@@ -151,3 +151,27 @@ def test_in_place_skinny_steps(tz, rows, cols, t, seed, g, small, prec):
     c = tn.Contractor(spec, max_log2=24)
     ref = np.array([c.amplitude(x) for x in bits])
     assert rel_err(got, ref, n) <= (TOL_C64 if prec == "c64" else TOL_C128)
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_tensor_core_scatter_epilogue_n_low(tz, prec):
+    """7x7 grid, depth 1+16+1, 64 bitstrings as one batch: the plan has a
+    tensor-core step whose output layout puts three column (n) bits lowest,
+    written through the staged per-warp epilogue; all 64 amplitudes against
+    the oracle's contractor."""
+    import json
+    spec = grid_spec(7, 7, 16, 2)
+    bits = ti.random_bitstrings(49, 64, 77)
+    c = tz.tz_circuit_from_spec(spec)
+    net = tz.tz_network_from_circuit(c, 6)
+    tree = tz.tz_path_greedy(net, restarts=16, seed=7, algorithm="elimination", precision="tf32x3")
+    plan = tz.tz_plan_create(net, tree, [], precision=prec, max_bitstrings=64)
+    steps = json.loads(plan.describe())["steps"]
+    assert any(s.get("gemm") and s.get("tc") and not s["row_major"] and s["pn"][:3] == [0, 1, 2] for s in steps)
+    plan.bind()
+    got = tz.tz_contract_amplitudes(plan, bits)
+    oc = tn.Contractor(spec, max_log2=24)
+    ref = np.array([oc.amplitude(x) for x in bits])
+    err = rel_err(got, ref, 49)
+    print(f"grid7x7 d16 batch64 {prec}: max rel err {err:.3e}")
+    assert err <= (TOL_C64 if prec == "tf32x3" else 1e-3)

@@ -124,6 +124,33 @@ def test_cgemm_tc_many_tiles_scatter_free(env, prec):
     assert np.all(np.abs(C - ref) <= (tol + 4 * (k + 2) * 2.0 ** -24) * bound)
 
 
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("batch,m,n,k", [(2, 128, 16, 4096), (64, 128, 32, 2048), (1, 256, 8, 1024)])
+def test_cgemm_tc_split_k(env, prec, batch, m, n, k):
+    """Few output tiles and a long K: the product splits K across CTAs (2 to
+    16 ranges for these shapes) and sums the partials in a fixed order, so two
+    runs agree bit for bit."""
+    tz, torch = env
+    rng = np.random.default_rng(batch + m + n + k)
+    A, dA = c64(torch, rng, (batch, m, k))
+    B, dB = c64(torch, rng, (batch, n, k))
+    nbytes = tz.tz_op_cgemm_scratch_bytes(prec, batch, m, n, k)
+    scratch = torch.empty(nbytes // 4 + 64, dtype=torch.float32, device="cuda")
+    outs = []
+    for _ in range(2):
+        dC = torch.full((batch * m * n * 2,), float("nan"), dtype=torch.float32, device="cuda")
+        tz.tz_op_cgemm(prec, batch, m, n, k, dA, m * k, dB, n * k, dC, m * n, scratch=scratch)
+        torch.cuda.synchronize()
+        outs.append(dC.cpu().numpy().view(np.complex64).reshape(batch, m, n))
+    assert np.array_equal(outs[0], outs[1])
+    C = outs[0]
+    ref = linalg.cgemm(A, B)
+    bound = linalg.cgemm(np.abs(A).astype(np.complex128), np.abs(B).astype(np.complex128)).real
+    tol = 2.0 ** -18 if prec == "tf32x3" else 2.0 ** -14
+    err = np.abs(C - ref)
+    assert np.all(err <= (tol + 4 * (k + 2) * 2.0 ** -24) * bound), float(np.max(err / bound))
+
+
 def test_cgemm_tc_rejects_unsupported(env):
     tz, torch = env
     with pytest.raises(tz.TzError) as e:
