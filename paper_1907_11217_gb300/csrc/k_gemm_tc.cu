@@ -14,15 +14,19 @@
 // hi*hi + hi*lo + lo*hi accumulate in FP32 in tensor memory (TMEM); the
 // dropped lo*lo term is below 2^-22 |a||b|.
 //
-// Pipeline per CTA (one 128-row tile of C, up to 128 complex columns):
+// Pipeline per CTA (tiles of 128 rows of C by up to 64 complex columns):
 //   warp 0     : TMA loads of the A tile (TF32: 128 rows x 16 floats, 64B
 //                swizzle; BF16: 128 rows x 32 floats, 128B swizzle) and of
 //                the prepared hi/lo B tiles, into a ring of stages;
-//   warps 2..5 : split each A tile in shared memory (hi in place, lo beside
-//                it), then, after the last product, the epilogue
-//                (tcgen05.ld TMEM -> registers -> global);
 //   warp 1     : TMEM allocation; one thread issues tcgen05.mma and commits
-//                stage releases to mbarriers.
+//                stage and accumulator releases to mbarriers;
+//   warps 2..5 : split each A tile in shared memory (hi in place, lo beside
+//                it);
+//   warps 6..13: epilogue: every accumulation range of kFoldK real K values
+//                ends in its own TMEM accumulator, which these warps add into
+//                FP32 registers (per thread one row of the tile, half of its
+//                columns: two warps per TMEM lane quarter) before the row
+//                goes to global memory.
 // Every wait is bounded in time; on timeout the kernel raises an error flag,
 // drains its copies in flight, frees TMEM and returns.
 #include <cuda.h>
@@ -48,7 +52,9 @@ constexpr int BM = 128;           // C rows per tile = TMEM lanes
 // measured slower.
 template <int MODE>
 __host__ __device__ constexpr int stage_k() { return MODE == 0 ? 16 : 32; }
-constexpr int kThreads = 320;  // TMA, MMA, 4 split warps, 4 epilogue warps
+// TMA, MMA, 4 split warps, 8 epilogue warps; registers are granted to warps
+// in groups of four, so 14 warps leave 128 registers a thread
+constexpr int kThreads = 448;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 __device__ int g_tc_error;
@@ -122,13 +128,16 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// 16 columns of this warp's 32 TMEM lanes; the wait is in the same asm
+// statement, so the registers are only defined once the load has landed.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      : "r"(taddr)
+      : "memory");
 }
 
 // Round to nearest TF32 on the bit pattern (a carry into the exponent is the
@@ -189,11 +198,20 @@ __device__ __forceinline__ int64_t scatter_bits(int64_t v, int n, const int8_t *
   return o;
 }
 
+// Accumulation range: the tensor cores sum at most kFoldK real K values (of
+// each of the three products) in one TMEM accumulator. Their FP32
+// accumulation rounds toward zero: on GB300 a product summed over K real
+// values in one accumulator comes out smaller by about 6e-9 K (relative),
+// whatever the total K. The epilogue warps add the ranges in FP32 registers
+// (round to nearest), which bounds that bias at about 6e-9 kFoldK per product.
+constexpr int kFoldK = 128;
+
 // Per stage: the FP32 A tile as loaded (128 rows x 64 B TF32 / 128 B BF16),
 // the split A (TF32: hi in place + lo tile of 8 KB; BF16: hi and lo tiles of
 // 8 KB), and the prepared B hi and lo tiles (BNP rows x 64 B).
-// TMEM holds two accumulators (BNP columns each, at least 32) so the
-// epilogue of one tile overlaps the products of the next.
+// TMEM (all 512 columns) is a ring of NBUF accumulators of BNP columns (at
+// least 32): the products of one range go to the next accumulator of the
+// ring while the epilogue drains the previous ones.
 template <int MODE, int BNP, int STAGES>
 struct TcSmem {
   static constexpr uint32_t A_BYTES = BM * stage_k<MODE>() * 4;         // FP32 tile as loaded
@@ -202,11 +220,16 @@ struct TcSmem {
   static constexpr uint32_t A_LO = MODE == MODE_TF32 ? A_BYTES : A_BYTES + AS_BYTES;  // offset of A lo
   static constexpr uint32_t A_HI = MODE == MODE_TF32 ? 0 : A_BYTES;                  // offset of A hi
   static constexpr uint32_t STAGE = A_BYTES + (MODE == MODE_TF32 ? AS_BYTES : 2 * AS_BYTES) + 2 * B_BYTES;
+  static constexpr int EC = BNP >= 32 ? BNP / 2 : BNP;                // real columns per epilogue warp
   static constexpr uint32_t BARS = 512;                                // barriers and flags
-  static constexpr uint32_t STAGING = 4 * 2 * 2048;                    // epilogue: 4 warps x 2 x (32 rows x 64 B)
-  static constexpr uint32_t TOTAL = STAGES * STAGE + STAGING + BARS + 1024 + 1024;  // + column offsets, alignment
+  static constexpr uint32_t STAGING = 8 * 2 * 2048;                    // epilogue: 8 warps x 2 x (32 rows x 64 B)
+  static constexpr uint32_t COLOFF = 8 * (EC / 2) * 8;                 // epilogue: 8 warps x column offsets
+  static constexpr uint32_t TOTAL = STAGES * STAGE + STAGING + BARS + COLOFF + 1024;  // + alignment
   static constexpr uint32_t ACC_COLS = BNP < 32 ? 32 : BNP;
-  static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
+  static constexpr uint32_t TMEM_COLS = 512;
+  static constexpr int NBUF = TMEM_COLS / ACC_COLS;
+  static_assert(BNP <= 128, "an epilogue thread holds half a row of the tile in registers");
+  static_assert(3 * STAGES + 2 * NBUF + 1 <= 62, "barriers and flags fit in BARS");
 };
 
 // Persistent: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
@@ -223,12 +246,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * L::STAGE + L::STAGING);
   uint64_t *conv = full + STAGES;
   uint64_t *empty = conv + STAGES;
-  uint64_t *tfull = empty + STAGES;  // [2] accumulator ready for the epilogue
-  uint64_t *tempty = tfull + 2;      // [2] accumulator drained by the epilogue
-  uint64_t *drain = tempty + 2;      // all products retired
+  uint64_t *tfull = empty + STAGES;     // [NBUF] accumulator ready for the epilogue
+  uint64_t *tempty = tfull + L::NBUF;   // [NBUF] accumulator drained by the epilogue
+  uint64_t *drain = tempty + L::NBUF;   // all products retired
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-  int64_t *coloff = reinterpret_cast<int64_t *>(smem + STAGES * L::STAGE + L::STAGING + L::BARS);
+  int64_t *coloff_all = reinterpret_cast<int64_t *>(smem + STAGES * L::STAGE + L::STAGING + L::BARS);
   uint8_t *staging = smem + STAGES * L::STAGE;  // 1024-aligned
   auto A_raw = [&](int s) { return smem + s * L::STAGE; };
   auto A_hi = [&](int s) { return smem + s * L::STAGE + L::A_HI; };
@@ -264,9 +287,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&conv[s], 128);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; b++) {
+    for (int b = 0; b < L::NBUF; b++) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 128);
+      mbar_init(&tempty[b], 256);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -313,42 +336,52 @@ __global__ void __launch_bounds__(kThreads, 1)
       // K per instruction: 8 TF32 or 16 BF16 values, 32 bytes either way;
       // two instructions per 64-byte row
       constexpr int kSteps = 2;
-      int64_t g = 0, i = 0;
+      constexpr int kFoldKb = kFoldK / stage_k<MODE>();  // k-blocks per accumulation range
+      int64_t g = 0, rg = 0;  // k-blocks and accumulation ranges issued
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, i++) {
-        const int b = (int)(i & 1);
-        const int64_t u = i >> 1;
-        if (u > 0 && !mbar_wait(&tempty[b], (uint32_t)((u - 1) & 1), abort_flag)) break;
-        tc_fence_after();
-        const uint32_t d_acc = tmem + (uint32_t)(b * L::ACC_COLS);
+      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         const Tile d = decode(t);
-        for (int kb = 0; kb < d.kb1 - d.kb0; kb++, g++) {
-          const int s = (int)(g % STAGES);
-          if (!mbar_wait(&conv[s], (uint32_t)((g / STAGES) & 1), abort_flag)) {
+        const int nkb = d.kb1 - d.kb0;
+        for (int r0 = 0; r0 < nkb; r0 += kFoldKb, rg++) {
+          const int buf = (int)(rg % L::NBUF);
+          const int64_t use = rg / L::NBUF;
+          if (use > 0 && !mbar_wait(&tempty[buf], (uint32_t)((use - 1) & 1), abort_flag)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t ah = smem_u32(A_hi(s)), al = smem_u32(A_lo(s));
-          const uint32_t bh = smem_u32(B_hi(s)), bl = smem_u32(B_lo(s));
-#pragma unroll
-          for (int kk = 0; kk < kSteps; kk++) {
-            const uint32_t off = kk * 32;
-            const uint64_t dah = sw64_desc(ah + off), dal = sw64_desc(al + off);
-            const uint64_t dbh = sw64_desc(bh + off), dbl = sw64_desc(bl + off);
-            if (MODE == MODE_TF32) {
-              umma_tf32(d_acc, dah, dbh, idesc, (kb | kk) != 0);
-              umma_tf32(d_acc, dah, dbl, idesc, 1);
-              umma_tf32(d_acc, dal, dbh, idesc, 1);
-            } else {
-              umma_f16(d_acc, dah, dbh, idesc, (kb | kk) != 0);
-              umma_f16(d_acc, dah, dbl, idesc, 1);
-              umma_f16(d_acc, dal, dbh, idesc, 1);
+          const uint32_t d_acc = tmem + (uint32_t)(buf * L::ACC_COLS);
+          const int r1 = min(nkb, r0 + kFoldKb);
+          for (int kb = r0; kb < r1; kb++, g++) {
+            const int s = (int)(g % STAGES);
+            if (!mbar_wait(&conv[s], (uint32_t)((g / STAGES) & 1), abort_flag)) {
+              ok = false;
+              break;
             }
+            tc_fence_after();
+            const uint32_t ah = smem_u32(A_hi(s)), al = smem_u32(A_lo(s));
+            const uint32_t bh = smem_u32(B_hi(s)), bl = smem_u32(B_lo(s));
+#pragma unroll
+            for (int kk = 0; kk < kSteps; kk++) {
+              const uint32_t off = kk * 32;
+              const uint64_t dah = sw64_desc(ah + off), dal = sw64_desc(al + off);
+              const uint64_t dbh = sw64_desc(bh + off), dbl = sw64_desc(bl + off);
+              const uint32_t acc = ((kb - r0) | kk) != 0;
+              if (MODE == MODE_TF32) {
+                umma_tf32(d_acc, dah, dbh, idesc, acc);
+                umma_tf32(d_acc, dah, dbl, idesc, 1);
+                umma_tf32(d_acc, dal, dbh, idesc, 1);
+              } else {
+                umma_f16(d_acc, dah, dbh, idesc, acc);
+                umma_f16(d_acc, dah, dbl, idesc, 1);
+                umma_f16(d_acc, dal, dbh, idesc, 1);
+              }
+            }
+            umma_commit(&empty[s]);
           }
-          umma_commit(&empty[s]);
+          if (!ok) break;
+          umma_commit(&tfull[buf]);
         }
-        if (ok) umma_commit(&tfull[b]);
       }
       // every product issued by this thread has retired once this fires
       umma_commit(drain);
@@ -403,23 +436,54 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // epilogue: warps 6..9 read TMEM lane quarters 2, 3, 0, 1
-    const int t = threadIdx.x - 192;  // 0..127
+    // epilogue: warps 6..13 read TMEM lane quarters 2, 3, 0, 1, 2, 3, 0, 1;
+    // warps 6..9 take the first EC columns of the tile, warps 10..13 the
+    // rest (none when the tile is narrower than 32 columns); each thread
+    // sums its part of a row over the accumulation ranges in registers
+    constexpr int kFoldKb = kFoldK / stage_k<MODE>();
+    constexpr int EC = L::EC;
+    const int e = warp - 6;
     const int q = warp & 3;
     const int row = q * 32 + lane;
-    int64_t i = 0;
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, i++) {
+    const int c0 = (e >> 2) * EC;  // first column (real) of this warp
+    const bool active = c0 < BNP;
+    int64_t *coloff = coloff_all + e * (EC / 2);  // this warp's copy
+    int64_t rg = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
       const Tile d = decode(tile);
-      const int b = (int)(i & 1);
-      const int64_t n0 = (int64_t)d.nt * (BNP / 2);
-      if (a.scatter) {
-        asm volatile("bar.sync 2, 128;" ::: "memory");  // previous tile's offsets no longer read
-        if (t < BNP / 2) coloff[t] = scatter_bits(n0 + t, a.sc.nn, a.sc.pn);
-        asm volatile("bar.sync 2, 128;" ::: "memory");
+      const int64_t n0 = (int64_t)d.nt * (BNP / 2) + c0 / 2;  // first complex column of this warp
+      if (a.scatter && active) {
+        __syncwarp();  // the previous tile's offsets are no longer read
+        for (int j = lane; j < EC / 2; j += 32) coloff[j] = scatter_bits(n0 + j, a.sc.nn, a.sc.pn);
+        __syncwarp();
       }
-      if (!mbar_wait(&tfull[b], (uint32_t)((i >> 1) & 1), abort_flag)) break;
-      tc_fence_after();
-      const uint32_t taddr = tmem + (uint32_t)(b * L::ACC_COLS) + ((uint32_t)(q * 32) << 16);
+      float acc[EC];
+#pragma unroll
+      for (int j = 0; j < EC; j++) acc[j] = 0.f;
+      const int nkb = d.kb1 - d.kb0;
+      for (int r0 = 0; r0 < nkb; r0 += kFoldKb, rg++) {
+        const int buf = (int)(rg % L::NBUF);
+        if (!mbar_wait(&tfull[buf], (uint32_t)((rg / L::NBUF) & 1), abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t taddr = tmem + (uint32_t)(buf * L::ACC_COLS + c0) + ((uint32_t)(q * 32) << 16);
+        if (active) {
+#pragma unroll
+          for (int c = 0; c < EC; c += 16) {
+            uint32_t r[16];
+            tmem_ld16(taddr + (uint32_t)c, r);
+#pragma unroll
+            for (int j = 0; j < 16; j++) acc[c + j] += __uint_as_float(r[j]);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&tempty[buf]);
+      }
+      if (!ok) break;
+      if (!active) continue;
       if (a.scatter == 2) {
         // a warp's 32 rows x 8 complex go through its staging buffer (16-byte
         // chunk j of row r at chunk j ^ ((r >> 1) & 3), so both sides are
@@ -429,90 +493,77 @@ __global__ void __launch_bounds__(kThreads, 1)
         int64_t om_u[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) om_u[u] = __shfl_sync(0xffffffffu, om, 8 * u + (lane >> 2));
-        uint8_t *stg = staging + (warp - 6) * 4096;
-#pragma unroll 1
-        for (int c = 0; c < BNP; c += 16) {
-          uint32_t r[16];
-          tmem_ld16(taddr + (uint32_t)c, r);
-          if (n0 + c / 2 >= a.N) break;  // N is a multiple of 8 here
-          uint8_t *buf = stg + (((c >> 4) & 1) << 11);
+        uint8_t *stg = staging + e * 4096;
 #pragma unroll
-          for (int j = 0; j < 4; j++)
-            *reinterpret_cast<uint4 *>(buf + lane * 64 + ((j ^ ((lane >> 1) & 3)) << 4)) =
-                make_uint4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
-          __syncwarp();
-          const int64_t col = coloff[c / 2] + 2 * (lane & 3);
+        for (int c = 0; c < EC; c += 16) {
+          if (n0 + c / 2 < a.N) {  // N is a multiple of 8 here
+            uint8_t *buf = stg + (((c >> 4) & 1) << 11);
 #pragma unroll
-          for (int u = 0; u < 4; u++) {
-            const int rr = 8 * u + (lane >> 2);
-            const uint4 v =
-                *reinterpret_cast<const uint4 *>(buf + rr * 64 + (((lane & 3) ^ ((rr >> 1) & 3)) << 4));
-            *reinterpret_cast<uint4 *>(a.C + om_u[u] + col) = v;
+            for (int j = 0; j < 4; j++)
+              *reinterpret_cast<float4 *>(buf + lane * 64 + ((j ^ ((lane >> 1) & 3)) << 4)) =
+                  make_float4(acc[c + 4 * j], acc[c + 4 * j + 1], acc[c + 4 * j + 2], acc[c + 4 * j + 3]);
+            __syncwarp();
+            const int64_t col = coloff[c / 2] + 2 * (lane & 3);
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+              const int rr = 8 * u + (lane >> 2);
+              const uint4 v =
+                  *reinterpret_cast<const uint4 *>(buf + rr * 64 + (((lane & 3) ^ ((rr >> 1) & 3)) << 4));
+              *reinterpret_cast<uint4 *>(a.C + om_u[u] + col) = v;
+            }
           }
         }
       } else if (a.scatter) {
         const int64_t om = scatter_bits(d.z, a.sc.nb, a.sc.pb) + scatter_bits((int64_t)d.mt * BM + row, a.sc.nm, a.sc.pm);
-#pragma unroll 1
-        for (int c = 0; c < BNP; c += 16) {
-          uint32_t r[16];
-          tmem_ld16(taddr + (uint32_t)c, r);
 #pragma unroll
-          for (int j = 0; j < 8; j++)
-            if (n0 + c / 2 + j < a.N)
-              a.C[om + coloff[c / 2 + j]] = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
-        }
+        for (int j = 0; j < EC / 2; j++)
+          if (n0 + j < a.N) a.C[om + coloff[j]] = make_float2(acc[2 * j], acc[2 * j + 1]);
       } else if (a.tma_store) {
         // 16 columns (8 complex) at a time: this warp's 32 rows go to its
         // staging buffer in the 64-byte swizzled layout (16-byte chunk c of
         // row r at chunk c ^ ((r >> 1) & 3)), then one bulk tensor store.
-        uint8_t *stg = staging + (warp - 6) * 4096;
+        uint8_t *stg = staging + e * 4096;
         const int y = (int)(d.z * a.M + (int64_t)d.mt * BM + q * 32);
-#pragma unroll 1
-        for (int c = 0; c < BNP; c += 16) {
-          uint32_t r[16];
-          tmem_ld16(taddr + (uint32_t)c, r);
-          if (n0 + c / 2 >= a.N) break;
-          uint8_t *buf = stg + (((c >> 4) & 1) << 11);
-          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-          __syncwarp();
 #pragma unroll
-          for (int j = 0; j < 4; j++) {
-            const int pc = j ^ ((lane >> 1) & 3);
-            *reinterpret_cast<uint4 *>(buf + lane * 64 + pc * 16) =
-                make_uint4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
-          }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) {
-            asm volatile(
-                "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"((uint64_t)&tmC),
-                "r"((int)(2 * n0 + c)), "r"(y), "r"(smem_u32(buf))
-                : "memory");
-            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        for (int c = 0; c < EC; c += 16) {
+          if (n0 + c / 2 < a.N) {
+            uint8_t *buf = stg + (((c >> 4) & 1) << 11);
+            if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+              const int pc = j ^ ((lane >> 1) & 3);
+              *reinterpret_cast<float4 *>(buf + lane * 64 + pc * 16) =
+                  make_float4(acc[c + 4 * j], acc[c + 4 * j + 1], acc[c + 4 * j + 2], acc[c + 4 * j + 3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+              asm volatile(
+                  "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"((uint64_t)&tmC),
+                  "r"((int)(2 * n0 + c)), "r"(y), "r"(smem_u32(buf))
+                  : "memory");
+              asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            }
           }
         }
       } else {
         float2 *crow = a.C + d.ks * a.split_stride + d.z * a.sC + ((int64_t)d.mt * BM + row) * a.N;
-#pragma unroll 1
-        for (int c = 0; c < BNP; c += 16) {
-          uint32_t r[16];
-          tmem_ld16(taddr + (uint32_t)c, r);
+#pragma unroll
+        for (int c = 0; c < EC; c += 16) {
           const int64_t nb = n0 + c / 2;
           if (nb + 8 <= a.N) {
             float4 *dst = reinterpret_cast<float4 *>(crow + nb);
 #pragma unroll
             for (int j = 0; j < 4; j++)
-              dst[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                                   __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+              dst[j] = make_float4(acc[c + 4 * j], acc[c + 4 * j + 1], acc[c + 4 * j + 2], acc[c + 4 * j + 3]);
           } else {
 #pragma unroll
             for (int j = 0; j < 8; j++)
-              if (nb + j < a.N) crow[nb + j] = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+              if (nb + j < a.N) crow[nb + j] = make_float2(acc[c + 2 * j], acc[c + 2 * j + 1]);
           }
         }
       }
-      tc_fence_before();
-      mbar_arrive(&tempty[b]);
     }
   }
   if (warp >= 6 && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
@@ -612,10 +663,10 @@ bool make_map(CUtensorMap *tm, const void *base, int64_t cols, int64_t rows, int
   return r == CUDA_SUCCESS;
 }
 
-int tile_cols(int64_t N) {  // real columns per tile (power of two, 16..256)
+int tile_cols(int64_t N) {  // real columns per tile (power of two, 16..128)
   int64_t c = 2 * N;
   if (c < 16) c = 16;
-  if (c > 256) c = 256;
+  if (c > 128) c = 128;
   int64_t p = 16;
   while (p < c) p <<= 1;
   return (int)p;
@@ -640,15 +691,13 @@ cudaError_t run_tc(const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensor
 template <int MODE>
 cudaError_t dispatch(int bnp, const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensorMap &tbl,
                      const CUtensorMap &tc, const TcArgs &args, int64_t n_blocks, cudaStream_t s) {
-  // stages: TF32 as many as fit beside the epilogue staging (at most 8);
-  // BF16 as measured best
+  // stages: as many as fit beside the epilogue staging (at most 8)
   constexpr bool T = MODE == MODE_TF32;
   switch (bnp) {
-    case 16: return run_tc<MODE, 16, T ? 8 : 4>(ta, tbh, tbl, tc, args, n_blocks, s);
-    case 32: return run_tc<MODE, 32, T ? 8 : 4>(ta, tbh, tbl, tc, args, n_blocks, s);
-    case 64: return run_tc<MODE, 64, T ? 8 : 4>(ta, tbh, tbl, tc, args, n_blocks, s);
-    case 128: return run_tc<MODE, 128, T ? 6 : 3>(ta, tbh, tbl, tc, args, n_blocks, s);
-    default: return run_tc<MODE, 256, T ? 4 : 3>(ta, tbh, tbl, tc, args, n_blocks, s);
+    case 16: return run_tc<MODE, 16, T ? 8 : 5>(ta, tbh, tbl, tc, args, n_blocks, s);
+    case 32: return run_tc<MODE, 32, T ? 8 : 5>(ta, tbh, tbl, tc, args, n_blocks, s);
+    case 64: return run_tc<MODE, 64, T ? 7 : 4>(ta, tbh, tbl, tc, args, n_blocks, s);
+    default: return run_tc<MODE, 128, T ? 5 : 3>(ta, tbh, tbl, tc, args, n_blocks, s);
   }
 }
 

@@ -11,8 +11,9 @@ tree, 2^30 cap, captured graph on a stream):
 * the amplitude does not depend on the contraction tree or the slicing;
 * the FP32-class modes (complex64, split TF32, split BF16) agree with the
   complex128 mode run on the same tree; their errors against it are printed
-  and bounded by the values measured on GB300 (the complex128 mode itself is
-  pinned to the FP64 oracle to 1e-12 wherever the oracle reaches);
+  and held to 1e-5 (complex64, split TF32) and 3e-5 (split BF16) (the
+  complex128 mode itself is pinned to the FP64 oracle to 1e-12 wherever the
+  oracle reaches);
 * Porter-Thomas (Sec. 2): E[2^n |a|^2] = 1 over random bitstrings.
 
 At full width and reduced depth the oracle is feasible, and those circuits
@@ -80,7 +81,9 @@ def test_bristlecone70_depth32_properties(tz):
     for s in range(1 << k):
         ps.set_slice_range(s, s + 1)
         parts.append(tz.tz_contract_amplitudes(ps, bits))
-    assert rel_err(np.sum(parts, axis=0), a, 70) <= 1e-4
+    add = rel_err(np.sum(parts, axis=0), a, 70)
+    print(f"bristlecone70 d32 slices (k={k}) sum vs unsliced (split TF32): {add:.2e}")
+    assert add <= 3e-5
     # every mode on the same tree and slicing, against complex128 (one
     # bitstring: the FP64 units of GB300 are slow)
     p128, *_ = build(tz, spec, "c128", 30)
@@ -91,8 +94,8 @@ def test_bristlecone70_depth32_properties(tz):
     abf = tz.tz_contract_amplitudes(pbf, bits)
     errs = {m: rel_err(x[:1], a128, 70) for m, x in (("tf32x3", a), ("c64", a64), ("bf16x3", abf))}
     print("bristlecone70 d32 errors vs complex128:", {m: f"{e:.2e}" for m, e in errs.items()})
-    # measured on GB300: c64 1.2e-6, tf32x3 2.1e-5, bf16x3 2.4e-5
-    assert errs["c64"] <= 1e-5 and errs["tf32x3"] <= 1e-4 and errs["bf16x3"] <= 1e-4
+    # measured on GB300: c64 3.3e-6, tf32x3 7.6e-6, bf16x3 9.0e-6
+    assert errs["c64"] <= 1e-5 and errs["tf32x3"] <= 1e-5 and errs["bf16x3"] <= 3e-5
     # another tree (other seed) with a different cap, hence other slices
     p2, _, tree2, sl2 = build(tz, spec, "c64", 29, seed=11, restarts=32)
     assert not np.array_equal(tree.pairs(), tree2.pairs())
@@ -162,7 +165,9 @@ def test_grid7x7_depth32_config2_properties(tz):
             hi = tz.tz_contract_amplitudes(plan, bits)
             assert rel_err(lo + hi, a, 49) <= 1e-6
         results[prec] = a
-    assert rel_err(results["tf32x3"], results["c64"], 49) <= 1e-3
+    agree = rel_err(results["tf32x3"], results["c64"], 49)
+    print(f"grid7x7 d32 split TF32 vs complex64: {agree:.2e}")
+    assert agree <= 2e-5
     npk = np.abs(results["c64"]) ** 2 * 2.0 ** 49
     assert abs(npk.mean() - 1.0) < 0.5
 
@@ -186,7 +191,8 @@ def test_grid7x7_depth32_errors_vs_complex128(tz):
         out[prec] = tz.tz_contract_amplitudes(plan, bits)
     errs = {m: rel_err(out[m], out["c128"], 49) for m in ("c64", "tf32x3", "bf16x3")}
     print("grid7x7 d32 (32 slices) errors vs complex128:", {m: f"{e:.2e}" for m, e in errs.items()})
-    assert errs["c64"] <= 1e-3 and errs["tf32x3"] <= 1e-3 and errs["bf16x3"] <= 1e-1
+    # measured on GB300: c64 6.8e-7, tf32x3 2.2e-6, bf16x3 6.3e-6
+    assert errs["c64"] <= 1e-5 and errs["tf32x3"] <= 1e-5 and errs["bf16x3"] <= 3e-5
 
 
 def test_grid7x7_reduced_depth_batch64_vs_oracle(tz):

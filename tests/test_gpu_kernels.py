@@ -59,7 +59,8 @@ def test_cgemm_simt(env, batch, m, n, k):
 
 
 @pytest.mark.parametrize("batch,m,n,k", [(1, 128, 1, 2), (1, 128, 8, 16), (2, 256, 64, 32), (1, 1024, 128, 64),
-                                         (3, 128, 4, 4), (1, 512, 256, 128), (4, 384, 24, 10), (1, 8192, 16, 256)])
+                                         (3, 128, 4, 4), (1, 512, 256, 128), (4, 384, 24, 10), (1, 8192, 16, 256),
+                                         (2, 256, 24, 100)])
 def test_cgemm_tf32x3(env, batch, m, n, k):
     """Split-TF32 tcgen05 product: hi*hi + hi*lo + lo*hi with round-to-nearest
     splits leaves < 2^-20 |a||b| per product, plus FP32 accumulation."""
@@ -82,7 +83,8 @@ def test_cgemm_tf32x3(env, batch, m, n, k):
 
 
 @pytest.mark.parametrize("batch,m,n,k", [(1, 128, 8, 16), (2, 256, 64, 32), (1, 1024, 128, 64), (3, 128, 4, 4),
-                                         (1, 512, 256, 128), (4, 384, 24, 12), (1, 8192, 16, 256), (37, 256, 40, 8)])
+                                         (1, 512, 256, 128), (4, 384, 24, 12), (1, 8192, 16, 256), (37, 256, 40, 8),
+                                         (2, 256, 24, 100)])
 def test_cgemm_bf16x3(env, batch, m, n, k):
     """Split-BF16 product: hi and lo carry 8+8 significand bits, so the
     dropped lo*lo term and the lo roundings leave ~2^-16 |a||b| per product."""
@@ -149,6 +151,34 @@ def test_cgemm_tc_split_k(env, prec, batch, m, n, k):
     tol = 2.0 ** -18 if prec == "tf32x3" else 2.0 ** -14
     err = np.abs(C - ref)
     assert np.all(err <= (tol + 4 * (k + 2) * 2.0 ** -24) * bound), float(np.max(err / bound))
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_cgemm_tc_accumulation_bias(env, prec):
+    """The tensor cores' FP32 accumulation rounds toward zero, so a product
+    summed over K real values in one accumulator comes out smaller by about
+    6e-9 K (2.5e-5 measured for 4096 values per accumulator). The kernel adds
+    ranges of 128 real values in FP32 registers instead: over K = 16384
+    complex the mean shrink (the error's component along the exact result)
+    stays near 6e-9 x 128, checked below 3e-6."""
+    tz, torch = env
+    batch, m, n, k = 2, 256, 16, 16384
+    rng = np.random.default_rng(4242)
+    A, dA = c64(torch, rng, (batch, m, k))
+    B, dB = c64(torch, rng, (batch, n, k))
+    dC = torch.zeros(batch * m * n * 2, dtype=torch.float32, device="cuda")
+    nbytes = tz.tz_op_cgemm_scratch_bytes(prec, batch, m, n, k)
+    scratch = torch.empty(nbytes // 4 + 64, dtype=torch.float32, device="cuda")
+    tz.tz_op_cgemm(prec, batch, m, n, k, dA, m * k, dB, n * k, dC, m * n, scratch=scratch)
+    torch.cuda.synchronize()
+    C = dC.cpu().numpy().view(np.complex64).reshape(batch, m, n).astype(np.complex128)
+    ref = linalg.cgemm(A, B)
+    d = C - ref
+    shrink = float(np.sum((d * np.conj(ref)).real) / np.sum(np.abs(ref) ** 2))
+    rel = float(np.sqrt(np.sum(np.abs(d) ** 2) / np.sum(np.abs(ref) ** 2)))
+    print(f"{prec} K={k}: mean shrink {shrink:.2e}, relative error {rel:.2e}")
+    assert abs(shrink) < 3e-6
+    assert rel < 1e-5
 
 
 def test_cgemm_tc_rejects_unsupported(env):
