@@ -18,10 +18,13 @@
 //   warp 0     : TMA loads of the A tile (TF32: 128 rows x 16 floats, 64B
 //                swizzle; BF16: 128 rows x 32 floats, 128B swizzle) and of
 //                the prepared hi/lo B tiles, into a ring of stages;
-//   warp 1     : TMEM allocation; one thread issues tcgen05.mma and commits
-//                stage and accumulator releases to mbarriers;
-//   warps 2..5 : split each A tile in shared memory (hi in place, lo beside
-//                it);
+//   warp 1     : TMEM allocation; one thread issues tcgen05.mma (A from
+//                TMEM, B from shared memory) and commits stage, A-slot and
+//                accumulator releases to mbarriers;
+//   warps 2..5 : split each A tile: one row a thread, read from shared
+//                memory, split in registers, written as hi and lo to a ring
+//                of A slots in TMEM (tcgen05.st); so shared memory carries
+//                only the raw A and the B operands;
 //   warps 6..13: epilogue: every accumulation range of kFoldK real K values
 //                ends in its own TMEM accumulator, which these warps add into
 //                FP32 registers (per thread one row of the tile, half of its
@@ -87,25 +90,47 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 // Wait for the phase with the given parity; false on timeout or when another
 // role has aborted (then the caller stops its work).
+// The clock is read only every 256 unsuccessful polls (a wait that succeeds
+// at once costs one try_wait): the time limit counts from the first of them.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
                                           bool honour_abort = true) {
-  const unsigned long long t0 = globaltimer();
+  unsigned long long t0 = 0;
   for (uint32_t i = 0;; i++) {
     if (mbar_try_wait(bar, parity)) return true;
     if (honour_abort && *abort_flag) return false;
-    if ((i & 255) == 255 && globaltimer() - t0 > kWaitNs) {
-      atomicExch(&g_tc_error, 1);
-      *abort_flag = 1;
-      return false;
+    if ((i & 255) == 255) {
+      const unsigned long long now = globaltimer();
+      if (t0 == 0) {
+        t0 = now;
+      } else if (now - t0 > kWaitNs) {
+        atomicExch(&g_tc_error, 1);
+        *abort_flag = 1;
+        return false;
+      }
     }
   }
 }
 
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *bar) {
+// L2 policies for the TMA loads: B tiles are read by every row tile, so they
+// are kept (evict last); A tiles are read by the few CTAs of one row tile at
+// about the same time, then not again (evict first).
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *bar,
+                                            uint64_t policy) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          smem_u32(dst)),
-      "l"((uint64_t)tm), "r"(x), "r"(y), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, "
+      "%3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)tm), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(policy)
       : "memory");
 }
 
@@ -115,11 +140,44 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int n_cols) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n_cols >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
-__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+// A from tensor memory (lane = row of A; one 32-bit column per TF32 value,
+// or per pair of BF16 values with the lower k in the low half), B from
+// shared memory.
+__device__ __forceinline__ void umma_tf32_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc,
+                                             uint32_t accum) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::
+          "r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(idesc), "r"(accum));
+}
+__device__ __forceinline__ void umma_f16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc,
+                                            uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::
+          "r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(idesc), "r"(accum));
+}
+// The same tile delivered to the shared memory of every CTA of the cluster in
+// mask, at the same offsets, each completing on its own barrier at bar.
+__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *bar,
+                                               uint16_t mask, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster.L2::cache_hint "
+      "[%0], [%1, {%2, %3}], [%4], %5, %6;" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)tm), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask), "l"(policy)
+      : "memory");
+}
+// Arrive on the barrier at bar in every CTA of the cluster in mask once the
+// products issued so far have completed.
+__device__ __forceinline__ void umma_commit_mc(uint64_t *bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -127,6 +185,17 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 columns of this warp's 32 TMEM lanes from registers (completion: tmem_st_wait).
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // 16 columns of this warp's 32 TMEM lanes; the wait is in the same asm
 // statement, so the registers are only defined once the load has landed.
@@ -148,6 +217,15 @@ __device__ __forceinline__ uint32_t split_lo(uint32_t x) {
   return __float_as_uint(__uint_as_float(x) - __uint_as_float(split_hi(x)));
 }
 
+// Two values at once (x0: lower k, in the low half of each result):
+// hi = bf16(x) and lo = bf16(x - hi), both rounded to nearest even; the BF16
+// hi values are widened back to FP32 by placing their bits in the top half.
+__device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(x1), "f"(x0));
+  const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xFFFF0000u);
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(x1 - h1), "f"(x0 - h0));
+}
+
 // Round-to-nearest-even BF16 split: hi = bf16(x), lo = bf16(x - hi).
 __device__ __forceinline__ void split_bf16(float x, uint16_t &hi, uint16_t &lo) {
   const __nv_bfloat16 h = __float2bfloat16_rn(x);
@@ -166,13 +244,6 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
 // FP32 accumulator, BF16 A and B, both K-major, N = n_cols, M = 128.
 __host__ __device__ constexpr uint32_t idesc_bf16(int n_cols) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n_cols >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum));
 }
 
 enum TcMode { MODE_TF32 = 0, MODE_BF16 = 1 };
@@ -206,20 +277,17 @@ __device__ __forceinline__ int64_t scatter_bits(int64_t v, int n, const int8_t *
 // (round to nearest), which bounds that bias at about 6e-9 kFoldK per product.
 constexpr int kFoldK = 128;
 
-// Per stage: the FP32 A tile as loaded (128 rows x 64 B TF32 / 128 B BF16),
-// the split A (TF32: hi in place + lo tile of 8 KB; BF16: hi and lo tiles of
-// 8 KB), and the prepared B hi and lo tiles (BNP rows x 64 B).
-// TMEM (all 512 columns) is a ring of NBUF accumulators of BNP columns (at
-// least 32): the products of one range go to the next accumulator of the
-// ring while the epilogue drains the previous ones.
+// Per stage (shared memory): the FP32 A tile as loaded (128 rows x 64 B TF32 /
+// 128 B BF16) and the prepared B hi and lo tiles (BNP rows x 64 B).
+// TMEM (all 512 columns): a ring of ASLOTS split A tiles (32 columns each:
+// hi, then lo) in the top columns, below it a ring of NBUF accumulators of
+// BNP columns (at least 32): the products of one range go to the next
+// accumulator of the ring while the epilogue drains the previous ones.
 template <int MODE, int BNP, int STAGES>
 struct TcSmem {
   static constexpr uint32_t A_BYTES = BM * stage_k<MODE>() * 4;         // FP32 tile as loaded
-  static constexpr uint32_t AS_BYTES = BM * 64;                          // one split half
   static constexpr uint32_t B_BYTES = BNP * 64;
-  static constexpr uint32_t A_LO = MODE == MODE_TF32 ? A_BYTES : A_BYTES + AS_BYTES;  // offset of A lo
-  static constexpr uint32_t A_HI = MODE == MODE_TF32 ? 0 : A_BYTES;                  // offset of A hi
-  static constexpr uint32_t STAGE = A_BYTES + (MODE == MODE_TF32 ? AS_BYTES : 2 * AS_BYTES) + 2 * B_BYTES;
+  static constexpr uint32_t STAGE = A_BYTES + 2 * B_BYTES;
   static constexpr int EC = BNP >= 32 ? BNP / 2 : BNP;                // real columns per epilogue warp
   static constexpr uint32_t BARS = 512;                                // barriers and flags
   static constexpr uint32_t STAGING = 8 * 2 * 2048;                    // epilogue: 8 warps x 2 x (32 rows x 64 B)
@@ -227,16 +295,23 @@ struct TcSmem {
   static constexpr uint32_t TOTAL = STAGES * STAGE + STAGING + BARS + COLOFF + 1024;  // + alignment
   static constexpr uint32_t ACC_COLS = BNP < 32 ? 32 : BNP;
   static constexpr uint32_t TMEM_COLS = 512;
-  static constexpr int NBUF = TMEM_COLS / ACC_COLS;
+  static constexpr int ASLOTS = 4;
+  static constexpr uint32_t A_COL0 = TMEM_COLS - ASLOTS * 32;
+  static constexpr int NBUF = A_COL0 / ACC_COLS;
   static_assert(BNP <= 128, "an epilogue thread holds half a row of the tile in registers");
-  static_assert(3 * STAGES + 2 * NBUF + 1 <= 62, "barriers and flags fit in BARS");
+  static_assert(3 * STAGES + 2 * NBUF + ASLOTS + 1 <= 62, "barriers and flags fit in BARS");
 };
 
 // Persistent: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // (batch-major, then row tile, then column tile, so CTAs working at the same
 // time share A tiles in L2). The stage ring and the accumulator ring run on
 // across tiles.
-template <int MODE, int BNP, int STAGES>
+// CL = 2: clusters of two CTAs take row tiles 2p and 2p + 1 of the same
+// column tile in step; each CTA loads half of every B tile and multicasts it
+// to both, which halves the B traffic from L2. A stage's B buffer is then
+// written by both CTAs, so each CTA's products release the stage in both
+// (empty barriers count two arrivals).
+template <int MODE, int BNP, int STAGES, int CL>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_split3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
                      const __grid_constant__ CUtensorMap tmBl, const __grid_constant__ CUtensorMap tmC, TcArgs a) {
@@ -249,19 +324,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t *tfull = empty + STAGES;     // [NBUF] accumulator ready for the epilogue
   uint64_t *tempty = tfull + L::NBUF;   // [NBUF] accumulator drained by the epilogue
   uint64_t *drain = tempty + L::NBUF;   // all products retired
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+  uint64_t *aempty = drain + 1;         // [ASLOTS] TMEM A slot read by its products
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(aempty + L::ASLOTS);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   int64_t *coloff_all = reinterpret_cast<int64_t *>(smem + STAGES * L::STAGE + L::STAGING + L::BARS);
   uint8_t *staging = smem + STAGES * L::STAGE;  // 1024-aligned
   auto A_raw = [&](int s) { return smem + s * L::STAGE; };
-  auto A_hi = [&](int s) { return smem + s * L::STAGE + L::A_HI; };
-  auto A_lo = [&](int s) { return smem + s * L::STAGE + L::A_LO; };
-  auto B_hi = [&](int s) { return smem + s * L::STAGE + L::STAGE - 2 * L::B_BYTES; };
-  auto B_lo = [&](int s) { return smem + s * L::STAGE + L::STAGE - L::B_BYTES; };
+  auto B_hi = [&](int s) { return smem + s * L::STAGE + L::A_BYTES; };
+  auto B_lo = [&](int s) { return smem + s * L::STAGE + L::A_BYTES + L::B_BYTES; };
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int64_t per_batch = (int64_t)a.n_tiles_m * a.n_tiles_n;
+  uint32_t rank = 0;  // CTA rank in the cluster
+  if (CL > 1) asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  // work units: tiles (CL = 1) or pairs of row tiles (CL = 2)
+  const int64_t per_batch = (int64_t)(a.n_tiles_m / CL) * a.n_tiles_n;
   const int64_t n_tiles = per_batch * a.batch * a.ksplit;
+  const int64_t t_first = blockIdx.x / CL, t_step = gridDim.x / CL;
   struct Tile {
     int64_t z;
     int mt, nt, rowA, rowB, ks, kb0, kb1;
@@ -274,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     d.kb1 = min(a.kblocks, d.kb0 + a.kb_per);
     d.z = t / per_batch;
     const int64_t rem = t - d.z * per_batch;
-    d.mt = (int)(rem / a.n_tiles_n);
+    d.mt = (int)(rem / a.n_tiles_n) * CL + (int)rank;
     d.nt = (int)(rem % a.n_tiles_n);
     d.rowA = (int)(d.z * a.M + (int64_t)d.mt * BM);
     d.rowB = (int)(d.z * a.NT + (int64_t)d.nt * BNP);
@@ -285,13 +363,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int s = 0; s < STAGES; s++) {
       mbar_init(&full[s], 1);
       mbar_init(&conv[s], 128);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], CL);
     }
     for (int b = 0; b < L::NBUF; b++) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], 256);
     }
     mbar_init(drain, 1);
+    for (int b = 0; b < L::ASLOTS; b++) mbar_init(&aempty[b], 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -302,14 +381,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
+  if (CL > 1) cluster_sync();  // the peer's barriers are initialised before any multicast
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
     if (lane == 0) {
+      const uint64_t keep = l2_evict_last(), stream = l2_evict_first();
       int64_t g = 0;  // k-blocks issued by this CTA
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+      for (int64_t t = t_first; t < n_tiles && ok; t += t_step) {
         const Tile d = decode(t);
         for (int kb = d.kb0; kb < d.kb1; kb++, g++) {
           const int s = (int)(g % STAGES);
@@ -319,9 +400,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           mbar_expect_tx(&full[s], L::A_BYTES + 2 * L::B_BYTES);
-          tma_load_2d(A_raw(s), &tmA, kb * stage_k<MODE>(), d.rowA, &full[s]);
-          tma_load_2d(B_hi(s), &tmBh, kb * stage_k<MODE>(), d.rowB, &full[s]);
-          tma_load_2d(B_lo(s), &tmBl, kb * stage_k<MODE>(), d.rowB, &full[s]);
+          tma_load_2d(A_raw(s), &tmA, kb * stage_k<MODE>(), d.rowA, &full[s], stream);
+          if (CL == 1) {
+            tma_load_2d(B_hi(s), &tmBh, kb * stage_k<MODE>(), d.rowB, &full[s], keep);
+            tma_load_2d(B_lo(s), &tmBl, kb * stage_k<MODE>(), d.rowB, &full[s], keep);
+          } else {
+            // this CTA's half of the B rows, to both CTAs (the maps' boxes are BNP / CL rows)
+            const uint32_t off = rank * (BNP / CL) * 64;
+            const uint16_t mask = (uint16_t)((1u << CL) - 1);
+            tma_load_2d_mc(B_hi(s) + off, &tmBh, kb * stage_k<MODE>(), d.rowB + (int)rank * (BNP / CL), &full[s],
+                           mask, keep);
+            tma_load_2d_mc(B_lo(s) + off, &tmBl, kb * stage_k<MODE>(), d.rowB + (int)rank * (BNP / CL), &full[s],
+                           mask, keep);
+          }
         }
       }
       if (*abort_flag) {
@@ -339,7 +430,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       constexpr int kFoldKb = kFoldK / stage_k<MODE>();  // k-blocks per accumulation range
       int64_t g = 0, rg = 0;  // k-blocks and accumulation ranges issued
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+      for (int64_t t = t_first; t < n_tiles && ok; t += t_step) {
         const Tile d = decode(t);
         const int nkb = d.kb1 - d.kb0;
         for (int r0 = 0; r0 < nkb; r0 += kFoldKb, rg++) {
@@ -359,25 +450,29 @@ __global__ void __launch_bounds__(kThreads, 1)
               break;
             }
             tc_fence_after();
-            const uint32_t ah = smem_u32(A_hi(s)), al = smem_u32(A_lo(s));
+            const int slot = (int)(g % L::ASLOTS);
+            const uint32_t ah = tmem + L::A_COL0 + (uint32_t)(slot * 32), al = ah + 16;
             const uint32_t bh = smem_u32(B_hi(s)), bl = smem_u32(B_lo(s));
 #pragma unroll
             for (int kk = 0; kk < kSteps; kk++) {
-              const uint32_t off = kk * 32;
-              const uint64_t dah = sw64_desc(ah + off), dal = sw64_desc(al + off);
-              const uint64_t dbh = sw64_desc(bh + off), dbl = sw64_desc(bl + off);
+              // 8 TMEM columns and 32 bytes of each B row per instruction
+              const uint64_t dbh = sw64_desc(bh + kk * 32), dbl = sw64_desc(bl + kk * 32);
               const uint32_t acc = ((kb - r0) | kk) != 0;
               if (MODE == MODE_TF32) {
-                umma_tf32(d_acc, dah, dbh, idesc, acc);
-                umma_tf32(d_acc, dah, dbl, idesc, 1);
-                umma_tf32(d_acc, dal, dbh, idesc, 1);
+                umma_tf32_ts(d_acc, ah + kk * 8, dbh, idesc, acc);
+                umma_tf32_ts(d_acc, ah + kk * 8, dbl, idesc, 1);
+                umma_tf32_ts(d_acc, al + kk * 8, dbh, idesc, 1);
               } else {
-                umma_f16(d_acc, dah, dbh, idesc, acc);
-                umma_f16(d_acc, dah, dbl, idesc, 1);
-                umma_f16(d_acc, dal, dbh, idesc, 1);
+                umma_f16_ts(d_acc, ah + kk * 8, dbh, idesc, acc);
+                umma_f16_ts(d_acc, ah + kk * 8, dbl, idesc, 1);
+                umma_f16_ts(d_acc, al + kk * 8, dbh, idesc, 1);
               }
             }
-            umma_commit(&empty[s]);
+            if (CL == 1)
+              umma_commit(&empty[s]);
+            else
+              umma_commit_mc(&empty[s], (uint16_t)((1u << CL) - 1));
+            umma_commit(&aempty[slot]);
           }
           if (!ok) break;
           umma_commit(&tfull[buf]);
@@ -388,50 +483,53 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_wait(drain, 0, abort_flag, false);
     }
   } else if (warp < 6) {
-    const int t = threadIdx.x - 64;  // 0..127
+    // split warps: warp w takes TMEM lane quarter w % 4, one row of A a thread
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16) + L::A_COL0;
     int64_t g = 0;
     bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    for (int64_t tile = t_first; tile < n_tiles && ok; tile += t_step) {
       const Tile d = decode(tile);
       for (int kb = 0; kb < d.kb1 - d.kb0; kb++, g++) {
         const int s = (int)(g % STAGES);
-        if (!mbar_wait(&full[s], (uint32_t)((g / STAGES) & 1), abort_flag)) {
+        const int slot = (int)(g % L::ASLOTS);
+        const int64_t use = g / L::ASLOTS;
+        if ((use > 0 && !mbar_wait(&aempty[slot], (uint32_t)((use - 1) & 1), abort_flag)) ||
+            !mbar_wait(&full[s], (uint32_t)((g / STAGES) & 1), abort_flag)) {
           ok = false;
           break;
         }
+        tc_fence_after();
+        uint32_t hi[16], lo[16];
         if (MODE == MODE_TF32) {
-          // elementwise, so the swizzled layout is kept as is
-          uint4 *hi = reinterpret_cast<uint4 *>(A_hi(s));
-          uint4 *lo = reinterpret_cast<uint4 *>(A_lo(s));
-#pragma unroll 4
-          for (int x = t; x < (int)(L::A_BYTES / 16); x += 128) {
-            const uint4 v = hi[x];
-            hi[x] = make_uint4(split_hi(v.x), split_hi(v.y), split_hi(v.z), split_hi(v.w));
-            lo[x] = make_uint4(split_lo(v.x), split_lo(v.y), split_lo(v.z), split_lo(v.w));
+          // 16 floats: 16-byte chunk c of the row at chunk c ^ ((row >> 1) & 3)
+          const uint4 *src = reinterpret_cast<const uint4 *>(A_raw(s) + row * 64);
+#pragma unroll
+          for (int c = 0; c < 4; c++) {
+            const uint4 v = src[c ^ ((row >> 1) & 3)];
+            const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+              hi[4 * c + j] = split_hi(x[j]);
+              lo[4 * c + j] = __float_as_uint(__uint_as_float(x[j]) - __uint_as_float(hi[4 * c + j]));
+            }
           }
         } else {
-          // FP32 chunk c (4 values) of row r sits at chunk c ^ (r & 7) of the
-          // 128-byte row; its 4 BF16 go to bytes 8*(c&1) of chunk
-          // (c>>1) ^ ((r>>1)&3) of the 64-byte row
-          const uint4 *raw = reinterpret_cast<const uint4 *>(A_raw(s));
-          uint8_t *hi = A_hi(s), *lo = A_lo(s);
-#pragma unroll 4
-          for (int x = t; x < BM * 8; x += 128) {
-            const int r = x >> 3, c = x & 7;
-            const uint4 v = raw[r * 8 + (c ^ (r & 7))];
-            uint16_t h[4], l[4];
-            split_bf16(__uint_as_float(v.x), h[0], l[0]);
-            split_bf16(__uint_as_float(v.y), h[1], l[1]);
-            split_bf16(__uint_as_float(v.z), h[2], l[2]);
-            split_bf16(__uint_as_float(v.w), h[3], l[3]);
-            const int o = r * 64 + (((c >> 1) ^ ((r >> 1) & 3)) << 4) + ((c & 1) << 3);
-            *reinterpret_cast<uint2 *>(hi + o) =
-                make_uint2(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16));
-            *reinterpret_cast<uint2 *>(lo + o) =
-                make_uint2(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16));
+          // 32 floats: chunk c of the row at chunk c ^ (row & 7); BF16 pairs
+          // packed with the lower k in the low half
+          const uint4 *src = reinterpret_cast<const uint4 *>(A_raw(s) + row * 128);
+#pragma unroll
+          for (int c = 0; c < 8; c++) {
+            const uint4 v = src[c ^ (row & 7)];
+            split_bf16x2(__uint_as_float(v.x), __uint_as_float(v.y), hi[2 * c], lo[2 * c]);
+            split_bf16x2(__uint_as_float(v.z), __uint_as_float(v.w), hi[2 * c + 1], lo[2 * c + 1]);
           }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tmem_st16(tq + (uint32_t)(slot * 32), hi);
+        tmem_st16(tq + (uint32_t)(slot * 32 + 16), lo);
+        tmem_st_wait();
+        tc_fence_before();
         mbar_arrive(&conv[s]);
       }
     }
@@ -450,7 +548,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int64_t *coloff = coloff_all + e * (EC / 2);  // this warp's copy
     int64_t rg = 0;
     bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    for (int64_t tile = t_first; tile < n_tiles && ok; tile += t_step) {
       const Tile d = decode(tile);
       const int64_t n0 = (int64_t)d.nt * (BNP / 2) + c0 / 2;  // first complex column of this warp
       if (a.scatter && active) {
@@ -569,6 +667,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp >= 6 && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   tc_fence_before();
   __syncthreads();
+  // the peer's products have arrived on this CTA's barriers (they retired
+  // before its MMA thread got here) before either CTA exits
+  if (CL > 1) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)L::TMEM_COLS));
@@ -672,32 +773,66 @@ int tile_cols(int64_t N) {  // real columns per tile (power of two, 16..128)
   return (int)p;
 }
 
-template <int MODE, int BNP, int STAGES>
+// Launches the persistent kernel on at most one CTA (CL = 1) or one cluster
+// (CL = 2) per work unit, as many as are resident at once.
+template <int MODE, int BNP, int STAGES, int CL>
 cudaError_t run_tc(const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensorMap &tbl, const CUtensorMap &tc,
-                   const TcArgs &args, int64_t n_blocks, cudaStream_t s) {
+                   const TcArgs &args, int64_t n_units, cudaStream_t s) {
   using L = TcSmem<MODE, BNP, STAGES>;
   static_assert(L::TOTAL <= 227 * 1024, "shared memory budget");
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_split3_kernel<MODE, BNP, STAGES>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::TOTAL);
+  auto kernel = tc_split3_kernel<MODE, BNP, STAGES, CL>;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  static int resident = 0;  // CTAs (CL = 1) or clusters (CL = 2) resident at once
+  if (!resident) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::TOTAL);
     if (e != cudaSuccess) return e;
-    attr = true;
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 148;
+    int r = n_sm / CL;
+    if (CL > 1) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(r * CL));
+      cfg.blockDim = dim3(kThreads);
+      cfg.dynamicSmemBytes = L::TOTAL;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int c = 0;
+      e = cudaOccupancyMaxActiveClusters(&c, kernel, &cfg);
+      if (e != cudaSuccess) return e;
+      if (c > 0) r = std::min(r, c);
+    }
+    resident = r;
   }
-  tc_split3_kernel<MODE, BNP, STAGES><<<(unsigned)n_blocks, kThreads, L::TOTAL, s>>>(ta, tbh, tbl, tc, args);
-  return cudaGetLastError();
+  const int64_t units = std::min<int64_t>(n_units, resident);
+  if (CL == 1) {
+    kernel<<<(unsigned)units, kThreads, L::TOTAL, s>>>(ta, tbh, tbl, tc, args);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(units * CL));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = L::TOTAL;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, ta, tbh, tbl, tc, args);
 }
 
-template <int MODE>
+template <int MODE, int CL>
 cudaError_t dispatch(int bnp, const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensorMap &tbl,
-                     const CUtensorMap &tc, const TcArgs &args, int64_t n_blocks, cudaStream_t s) {
+                     const CUtensorMap &tc, const TcArgs &args, int64_t n_units, cudaStream_t s) {
   // stages: as many as fit beside the epilogue staging (at most 8)
   constexpr bool T = MODE == MODE_TF32;
   switch (bnp) {
-    case 16: return run_tc<MODE, 16, T ? 8 : 5>(ta, tbh, tbl, tc, args, n_blocks, s);
-    case 32: return run_tc<MODE, 32, T ? 8 : 5>(ta, tbh, tbl, tc, args, n_blocks, s);
-    case 64: return run_tc<MODE, 64, T ? 7 : 4>(ta, tbh, tbl, tc, args, n_blocks, s);
-    default: return run_tc<MODE, 128, T ? 5 : 3>(ta, tbh, tbl, tc, args, n_blocks, s);
+    case 16: return run_tc<MODE, 16, 8, CL>(ta, tbh, tbl, tc, args, n_units, s);
+    case 32: return run_tc<MODE, 32, 8, CL>(ta, tbh, tbl, tc, args, n_units, s);
+    case 64: return run_tc<MODE, 64, T ? 8 : 7, CL>(ta, tbh, tbl, tc, args, n_units, s);
+    default: return run_tc<MODE, 128, T ? 7 : 5, CL>(ta, tbh, tbl, tc, args, n_units, s);
   }
 }
 
@@ -765,8 +900,10 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
   }
   CUtensorMap ta, tbh, tbl;
   const int sk = bf16 ? stage_k<MODE_BF16>() : stage_k<MODE_TF32>();
-  if (!make_map(&ta, A, 2 * K, rowsA, sk, BM, false) || !make_map(&tbh, Bh, 2 * K, rowsB, sk, bnp, bf16) ||
-      !make_map(&tbl, Bl, 2 * K, rowsB, sk, bnp, bf16))
+  // pairs of row tiles share their B tiles when the row tiles pair up
+  const int cl = ((M / BM) % 2) == 0 ? 2 : 1;
+  if (!make_map(&ta, A, 2 * K, rowsA, sk, BM, false) || !make_map(&tbh, Bh, 2 * K, rowsB, sk, bnp / cl, bf16) ||
+      !make_map(&tbl, Bl, 2 * K, rowsB, sk, bnp / cl, bf16))
     return cudaErrorInvalidValue;
   TcArgs args{};
   args.C = C;
@@ -793,14 +930,7 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
         (reinterpret_cast<uintptr_t>(C) & 15) == 0)
       args.scatter = 2;
   }
-  const int64_t n_tiles = batch * args.n_tiles_m * (int64_t)n_tiles_n * ks;
-  static int n_sm = 0;
-  if (!n_sm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 148;
-  }
-  const int64_t n_blocks = std::min<int64_t>(n_tiles, n_sm);
+  const int64_t n_units = batch * (args.n_tiles_m / cl) * (int64_t)n_tiles_n * ks;
   // row-major C with 16-byte aligned rows: bulk tensor stores of 32-row x
   // 16-float boxes (64-byte swizzle), clipped at the tensor edge
   CUtensorMap tcm;
@@ -821,8 +951,13 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
       args.tma_store = 1;
   }
-  cudaError_t e = bf16 ? dispatch<MODE_BF16>(bnp, ta, tbh, tbl, tcm, args, n_blocks, s)
-                       : dispatch<MODE_TF32>(bnp, ta, tbh, tbl, tcm, args, n_blocks, s);
+  cudaError_t e;
+  if (cl == 2)
+    e = bf16 ? dispatch<MODE_BF16, 2>(bnp, ta, tbh, tbl, tcm, args, n_units, s)
+             : dispatch<MODE_TF32, 2>(bnp, ta, tbh, tbl, tcm, args, n_units, s);
+  else
+    e = bf16 ? dispatch<MODE_BF16, 1>(bnp, ta, tbh, tbl, tcm, args, n_units, s)
+             : dispatch<MODE_TF32, 1>(bnp, ta, tbh, tbl, tcm, args, n_units, s);
   if (e != cudaSuccess || ks == 1) return e;
   const int64_t total = batch * M * N;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
