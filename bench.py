@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--algorithm", default="elimination", choices=["auto", "greedy", "elimination"])
     ap.add_argument("--tree-seed", type=int, default=7)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip timing the same workload in the other precision modes")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     return ap.parse_args()
 
@@ -142,6 +144,15 @@ def measured_peaks():
     return 6800.0, 1900.0, 1700.0, 2070.0, "fallback"
 
 
+# DRAM bytes (read + write) per useful flop of the tensor-core product, from
+# one ncu capture of the dominant Bristlecone-70 shape (M 16384, N 1024,
+# K 2048, batch 1; profiles/tc_split3_*_m16384_n1024_k2048.md). A launch's
+# traffic grows with its flops for this kernel (row tiles re-read B), so the
+# per-launch traffic of a step is scaled from it. Must be re-captured whenever
+# the kernel changes.
+TC_DRAM_BYTES_PER_FLOP = {"tf32x3": 1.315e9 / 2.749e11, "bf16x3": 0.432e9 / 2.749e11}
+
+
 def roofline(prof, precision):
     """Dominant kernel kind of the profiled pass and its roofline position."""
     hbm, bf16, bf16_s, sm_mhz, src = measured_peaks()
@@ -159,6 +170,10 @@ def roofline(prof, precision):
         out.update(bound="tensor", unit="TFLOP/s", achieved=d["flops"] / sec / 1e12, peak=peak,
                    peak_source=f"{src} bf16 x nominal {precision[:4]}/bf16 ratio",
                    issued_tflops=3 * d["flops"] / sec / 1e12)
+        if precision in TC_DRAM_BYTES_PER_FLOP:
+            out["traffic"] = TC_DRAM_BYTES_PER_FLOP[precision] * d["flops"] / d["launches"]
+            out["traffic_note"] = ("bytes per launch, scaled by flops from an ncu capture of the dominant shape "
+                                   "at batch 1")
     elif dom == "gemm_simt":
         out.update(bound="alu", unit="TFLOP/s", achieved=d["flops"] / sec / 1e12, peak=fp32_alu_tflops,
                    peak_source="152 SMs x 128 FP32 lanes x 2 flops x max SM clock")
@@ -252,7 +267,7 @@ def main():
 
     precision = args.precision
     if precision == "auto":
-        precision = "tf32x3" if tz._lib.lib() and _tc_available(tz) else "c64"
+        precision = "bf16x3" if tz._lib.lib() and _tc_available(tz) else "c64"
     spec, nq = make_circuit_spec(args.workload)
     log2_max = args.log2_max or WORKLOADS[args.workload][6]
     stream = torch.cuda.Stream(device=device)
@@ -339,13 +354,48 @@ def main():
     per_launch = {k: v["launches"] for k, v in prof.items()}
     launches_per_call = 1 + S * st["n_launches_per_group"]
 
+    # the same workload in the other modes (split precision against complex64),
+    # each with its own tree and plan, timed over the same slice windows
+    compare = None
+    segs = plan.sliced_segments()
+    if world == 1 and not args.no_compare:
+        compare = {}
+        plan.close()  # free its workspace before the other plans bind theirs
+        for other in ("c64", "bf16x3", "tf32x3"):
+            if other == precision:
+                continue
+            p2, _, _ = build_plan(tz, spec, args, other, stream, device, log2_max)
+            st2 = p2.stats()
+            p2.bind()
+            k2 = st2["k"]
+            n2 = 1 << k2
+            S2 = max(1, min(S, n2))
+
+            def step2(i):
+                lo = (i * S2) % n2
+                p2.set_slice_range(lo, min(n2, lo + S2))
+                tz.tz_contract_amplitudes_device(p2, d_bits, d_out)
+
+            step2(0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(2):
+                step2(1 + i)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms2 = e0.elapsed_time(e1) / 2
+            compare[other] = {"s_per_amplitude": ms2 / 1e3 * n2 / S2 / B,
+                              "contraction_tflops": st2["flops_per_group"] * S2 / (ms2 / 1e3) / 1e12,
+                              "k_sliced": k2}
+            p2.close()
+
     if rank != 0:
         if dist:
             td.destroy_process_group()
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        segs = plan.sliced_segments()
         cpu = cpu_oracle_sample(spec, segs, bits[0], args.cpu_seconds, k)
     paper = PAPER_S_PER_AMP.get(args.workload)
     line = {
@@ -368,6 +418,7 @@ def main():
         "e2e": {"value": e2e_s, "unit": "s/amplitude", "h2d_bytes_per_step": int(bits.nbytes),
                 "d2h_bytes_per_step": 16 * B},
         "roofline": rl,
+        "compare": compare,
         "cpu_baseline": cpu,
         "gpu_launches": args.steps * launches_per_call,
         "profiled_launches_per_kind": per_launch,

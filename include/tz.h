@@ -296,7 +296,12 @@ int tz_op_permute(const void *in, void *out, int rank, const int32_t *perm, void
  * precision: TZ_C64_SIMT, TZ_TF32X3, TZ_BF16X3, or TZ_C128_SIMT (then A,
  * B and C are complex128 arrays). The split-precision
  * modes need device scratch of tz_op_cgemm_scratch_bytes() bytes (256-byte
- * aligned); TZ_EUNSUPPORTED for shapes they do not handle. */
+ * aligned): the hi/lo copies of B in the real view, and the partial products
+ * when a long K is split across CTAs (summed in a fixed order, so results do
+ * not depend on scheduling); they accumulate in FP32 over ranges of 128 real
+ * K values, added in FP32 with round to nearest. TZ_EUNSUPPORTED for shapes
+ * they do not handle (m not a multiple of 128; k odd for TF32, not a multiple
+ * of 4 for BF16). */
 int tz_op_cgemm(int precision, int64_t batch, int64_t m, int64_t n, int64_t k,
                 const void *A, int64_t sa, const void *B, int64_t sb, void *C, int64_t sc,
                 void *scratch, size_t scratch_bytes, void *stream);

@@ -157,28 +157,6 @@ __device__ __forceinline__ void umma_f16_ts(uint32_t tmem_d, uint32_t tmem_a, ui
           "r"(tmem_d),
       "r"(tmem_a), "l"(b), "r"(idesc), "r"(accum));
 }
-// The same tile delivered to the shared memory of every CTA of the cluster in
-// mask, at the same offsets, each completing on its own barrier at bar.
-__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *bar,
-                                               uint16_t mask, uint64_t policy) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster.L2::cache_hint "
-      "[%0], [%1, {%2, %3}], [%4], %5, %6;" ::"r"(smem_u32(dst)),
-      "l"((uint64_t)tm), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask), "l"(policy)
-      : "memory");
-}
-// Arrive on the barrier at bar in every CTA of the cluster in mask once the
-// products issued so far have completed.
-__device__ __forceinline__ void umma_commit_mc(uint64_t *bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -306,12 +284,7 @@ struct TcSmem {
 // (batch-major, then row tile, then column tile, so CTAs working at the same
 // time share A tiles in L2). The stage ring and the accumulator ring run on
 // across tiles.
-// CL = 2: clusters of two CTAs take row tiles 2p and 2p + 1 of the same
-// column tile in step; each CTA loads half of every B tile and multicasts it
-// to both, which halves the B traffic from L2. A stage's B buffer is then
-// written by both CTAs, so each CTA's products release the stage in both
-// (empty barriers count two arrivals).
-template <int MODE, int BNP, int STAGES, int CL>
+template <int MODE, int BNP, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_split3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
                      const __grid_constant__ CUtensorMap tmBl, const __grid_constant__ CUtensorMap tmC, TcArgs a) {
@@ -334,12 +307,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto B_lo = [&](int s) { return smem + s * L::STAGE + L::A_BYTES + L::B_BYTES; };
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  uint32_t rank = 0;  // CTA rank in the cluster
-  if (CL > 1) asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
-  // work units: tiles (CL = 1) or pairs of row tiles (CL = 2)
-  const int64_t per_batch = (int64_t)(a.n_tiles_m / CL) * a.n_tiles_n;
+  const int64_t per_batch = (int64_t)a.n_tiles_m * a.n_tiles_n;
   const int64_t n_tiles = per_batch * a.batch * a.ksplit;
-  const int64_t t_first = blockIdx.x / CL, t_step = gridDim.x / CL;
   struct Tile {
     int64_t z;
     int mt, nt, rowA, rowB, ks, kb0, kb1;
@@ -352,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     d.kb1 = min(a.kblocks, d.kb0 + a.kb_per);
     d.z = t / per_batch;
     const int64_t rem = t - d.z * per_batch;
-    d.mt = (int)(rem / a.n_tiles_n) * CL + (int)rank;
+    d.mt = (int)(rem / a.n_tiles_n);
     d.nt = (int)(rem % a.n_tiles_n);
     d.rowA = (int)(d.z * a.M + (int64_t)d.mt * BM);
     d.rowB = (int)(d.z * a.NT + (int64_t)d.nt * BNP);
@@ -363,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int s = 0; s < STAGES; s++) {
       mbar_init(&full[s], 1);
       mbar_init(&conv[s], 128);
-      mbar_init(&empty[s], CL);
+      mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < L::NBUF; b++) {
       mbar_init(&tfull[b], 1);
@@ -381,7 +350,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (CL > 1) cluster_sync();  // the peer's barriers are initialised before any multicast
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -390,7 +358,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint64_t keep = l2_evict_last(), stream = l2_evict_first();
       int64_t g = 0;  // k-blocks issued by this CTA
       bool ok = true;
-      for (int64_t t = t_first; t < n_tiles && ok; t += t_step) {
+      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         const Tile d = decode(t);
         for (int kb = d.kb0; kb < d.kb1; kb++, g++) {
           const int s = (int)(g % STAGES);
@@ -401,18 +369,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           mbar_expect_tx(&full[s], L::A_BYTES + 2 * L::B_BYTES);
           tma_load_2d(A_raw(s), &tmA, kb * stage_k<MODE>(), d.rowA, &full[s], stream);
-          if (CL == 1) {
-            tma_load_2d(B_hi(s), &tmBh, kb * stage_k<MODE>(), d.rowB, &full[s], keep);
-            tma_load_2d(B_lo(s), &tmBl, kb * stage_k<MODE>(), d.rowB, &full[s], keep);
-          } else {
-            // this CTA's half of the B rows, to both CTAs (the maps' boxes are BNP / CL rows)
-            const uint32_t off = rank * (BNP / CL) * 64;
-            const uint16_t mask = (uint16_t)((1u << CL) - 1);
-            tma_load_2d_mc(B_hi(s) + off, &tmBh, kb * stage_k<MODE>(), d.rowB + (int)rank * (BNP / CL), &full[s],
-                           mask, keep);
-            tma_load_2d_mc(B_lo(s) + off, &tmBl, kb * stage_k<MODE>(), d.rowB + (int)rank * (BNP / CL), &full[s],
-                           mask, keep);
-          }
+          tma_load_2d(B_hi(s), &tmBh, kb * stage_k<MODE>(), d.rowB, &full[s], keep);
+          tma_load_2d(B_lo(s), &tmBl, kb * stage_k<MODE>(), d.rowB, &full[s], keep);
         }
       }
       if (*abort_flag) {
@@ -430,7 +388,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       constexpr int kFoldKb = kFoldK / stage_k<MODE>();  // k-blocks per accumulation range
       int64_t g = 0, rg = 0;  // k-blocks and accumulation ranges issued
       bool ok = true;
-      for (int64_t t = t_first; t < n_tiles && ok; t += t_step) {
+      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         const Tile d = decode(t);
         const int nkb = d.kb1 - d.kb0;
         for (int r0 = 0; r0 < nkb; r0 += kFoldKb, rg++) {
@@ -468,10 +426,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 umma_f16_ts(d_acc, al + kk * 8, dbh, idesc, 1);
               }
             }
-            if (CL == 1)
-              umma_commit(&empty[s]);
-            else
-              umma_commit_mc(&empty[s], (uint16_t)((1u << CL) - 1));
+            umma_commit(&empty[s]);
             umma_commit(&aempty[slot]);
           }
           if (!ok) break;
@@ -489,7 +444,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16) + L::A_COL0;
     int64_t g = 0;
     bool ok = true;
-    for (int64_t tile = t_first; tile < n_tiles && ok; tile += t_step) {
+    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
       const Tile d = decode(tile);
       for (int kb = 0; kb < d.kb1 - d.kb0; kb++, g++) {
         const int s = (int)(g % STAGES);
@@ -548,7 +503,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int64_t *coloff = coloff_all + e * (EC / 2);  // this warp's copy
     int64_t rg = 0;
     bool ok = true;
-    for (int64_t tile = t_first; tile < n_tiles && ok; tile += t_step) {
+    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
       const Tile d = decode(tile);
       const int64_t n0 = (int64_t)d.nt * (BNP / 2) + c0 / 2;  // first complex column of this warp
       if (a.scatter && active) {
@@ -667,9 +622,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp >= 6 && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   tc_fence_before();
   __syncthreads();
-  // the peer's products have arrived on this CTA's barriers (they retired
-  // before its MMA thread got here) before either CTA exits
-  if (CL > 1) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)L::TMEM_COLS));
@@ -773,66 +725,37 @@ int tile_cols(int64_t N) {  // real columns per tile (power of two, 16..128)
   return (int)p;
 }
 
-// Launches the persistent kernel on at most one CTA (CL = 1) or one cluster
-// (CL = 2) per work unit, as many as are resident at once.
-template <int MODE, int BNP, int STAGES, int CL>
+// Launches the persistent kernel on at most one CTA per tile, as many as are
+// resident at once (one per SM).
+template <int MODE, int BNP, int STAGES>
 cudaError_t run_tc(const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensorMap &tbl, const CUtensorMap &tc,
-                   const TcArgs &args, int64_t n_units, cudaStream_t s) {
+                   const TcArgs &args, int64_t n_tiles, cudaStream_t s) {
   using L = TcSmem<MODE, BNP, STAGES>;
   static_assert(L::TOTAL <= 227 * 1024, "shared memory budget");
-  auto kernel = tc_split3_kernel<MODE, BNP, STAGES, CL>;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = CL;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  static int resident = 0;  // CTAs (CL = 1) or clusters (CL = 2) resident at once
+  auto kernel = tc_split3_kernel<MODE, BNP, STAGES>;
+  static int resident = 0;
   if (!resident) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::TOTAL);
     if (e != cudaSuccess) return e;
     int dev = 0, n_sm = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 148;
-    int r = n_sm / CL;
-    if (CL > 1) {
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3((unsigned)(r * CL));
-      cfg.blockDim = dim3(kThreads);
-      cfg.dynamicSmemBytes = L::TOTAL;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      int c = 0;
-      e = cudaOccupancyMaxActiveClusters(&c, kernel, &cfg);
-      if (e != cudaSuccess) return e;
-      if (c > 0) r = std::min(r, c);
-    }
-    resident = r;
+    resident = n_sm;
   }
-  const int64_t units = std::min<int64_t>(n_units, resident);
-  if (CL == 1) {
-    kernel<<<(unsigned)units, kThreads, L::TOTAL, s>>>(ta, tbh, tbl, tc, args);
-    return cudaGetLastError();
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(units * CL));
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = L::TOTAL;
-  cfg.stream = s;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, ta, tbh, tbl, tc, args);
+  kernel<<<(unsigned)std::min<int64_t>(n_tiles, resident), kThreads, L::TOTAL, s>>>(ta, tbh, tbl, tc, args);
+  return cudaGetLastError();
 }
 
-template <int MODE, int CL>
+template <int MODE>
 cudaError_t dispatch(int bnp, const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensorMap &tbl,
-                     const CUtensorMap &tc, const TcArgs &args, int64_t n_units, cudaStream_t s) {
+                     const CUtensorMap &tc, const TcArgs &args, int64_t n_tiles, cudaStream_t s) {
   // stages: as many as fit beside the epilogue staging (at most 8)
   constexpr bool T = MODE == MODE_TF32;
   switch (bnp) {
-    case 16: return run_tc<MODE, 16, 8, CL>(ta, tbh, tbl, tc, args, n_units, s);
-    case 32: return run_tc<MODE, 32, 8, CL>(ta, tbh, tbl, tc, args, n_units, s);
-    case 64: return run_tc<MODE, 64, T ? 8 : 7, CL>(ta, tbh, tbl, tc, args, n_units, s);
-    default: return run_tc<MODE, 128, T ? 7 : 5, CL>(ta, tbh, tbl, tc, args, n_units, s);
+    case 16: return run_tc<MODE, 16, 8>(ta, tbh, tbl, tc, args, n_tiles, s);
+    case 32: return run_tc<MODE, 32, 8>(ta, tbh, tbl, tc, args, n_tiles, s);
+    case 64: return run_tc<MODE, 64, T ? 8 : 7>(ta, tbh, tbl, tc, args, n_tiles, s);
+    default: return run_tc<MODE, 128, T ? 7 : 5>(ta, tbh, tbl, tc, args, n_tiles, s);
   }
 }
 
@@ -860,6 +783,10 @@ static int split_k(int precision, int64_t batch, int64_t M, int64_t N, int64_t K
   int64_t s = std::min<int64_t>({16, 152 / std::max<int64_t>(tiles, 1), kblocks / 32});
   while (s > 1 && s * batch * M * N * 8 > (int64_t(64) << 20)) s--;
   return s < 2 ? 1 : (int)s;
+}
+
+int cgemm_tc_launches(int precision, int64_t batch, int64_t M, int64_t N, int64_t K, bool scatter) {
+  return 2 + (!scatter && split_k(precision, batch, M, N, K) > 1 ? 1 : 0);
 }
 
 size_t cgemm_tc_scratch_bytes(int precision, int64_t batch, int64_t M, int64_t N, int64_t K) {
@@ -900,10 +827,8 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
   }
   CUtensorMap ta, tbh, tbl;
   const int sk = bf16 ? stage_k<MODE_BF16>() : stage_k<MODE_TF32>();
-  // pairs of row tiles share their B tiles when the row tiles pair up
-  const int cl = ((M / BM) % 2) == 0 ? 2 : 1;
-  if (!make_map(&ta, A, 2 * K, rowsA, sk, BM, false) || !make_map(&tbh, Bh, 2 * K, rowsB, sk, bnp / cl, bf16) ||
-      !make_map(&tbl, Bl, 2 * K, rowsB, sk, bnp / cl, bf16))
+  if (!make_map(&ta, A, 2 * K, rowsA, sk, BM, false) || !make_map(&tbh, Bh, 2 * K, rowsB, sk, bnp, bf16) ||
+      !make_map(&tbl, Bl, 2 * K, rowsB, sk, bnp, bf16))
     return cudaErrorInvalidValue;
   TcArgs args{};
   args.C = C;
@@ -930,7 +855,7 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
         (reinterpret_cast<uintptr_t>(C) & 15) == 0)
       args.scatter = 2;
   }
-  const int64_t n_units = batch * (args.n_tiles_m / cl) * (int64_t)n_tiles_n * ks;
+  const int64_t n_tiles = batch * args.n_tiles_m * (int64_t)n_tiles_n * ks;
   // row-major C with 16-byte aligned rows: bulk tensor stores of 32-row x
   // 16-float boxes (64-byte swizzle), clipped at the tensor edge
   CUtensorMap tcm;
@@ -951,13 +876,8 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
       args.tma_store = 1;
   }
-  cudaError_t e;
-  if (cl == 2)
-    e = bf16 ? dispatch<MODE_BF16, 2>(bnp, ta, tbh, tbl, tcm, args, n_units, s)
-             : dispatch<MODE_TF32, 2>(bnp, ta, tbh, tbl, tcm, args, n_units, s);
-  else
-    e = bf16 ? dispatch<MODE_BF16, 1>(bnp, ta, tbh, tbl, tcm, args, n_units, s)
-             : dispatch<MODE_TF32, 1>(bnp, ta, tbh, tbl, tcm, args, n_units, s);
+  cudaError_t e = bf16 ? dispatch<MODE_BF16>(bnp, ta, tbh, tbl, tcm, args, n_tiles, s)
+                       : dispatch<MODE_TF32>(bnp, ta, tbh, tbl, tcm, args, n_tiles, s);
   if (e != cudaSuccess || ks == 1) return e;
   const int64_t total = batch * M * N;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);

@@ -651,7 +651,18 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
       stt.n_permutes++;
       stt.permute_bytes_per_group += 2.0 * esz * p->T[it.a].elems();
     }
-  stt.n_launches_per_group = (int)p->var_items.size();
+  // kernel launches: one per item, but a tensor-core product also prepares B
+  // and, when it splits K, sums the partials
+  stt.n_launches_per_group = 0;
+  for (const Item &it : p->var_items) {
+    int n = 1;
+    if (it.kind == IT_GEMM) {
+      const PStep &ps = p->S[it.a];
+      if (ps.tc)
+        n = dev::cgemm_tc_launches(p->opts.precision, ps.batch, ps.M, ps.N, ps.K, !ps.row_major);
+    }
+    stt.n_launches_per_group += n;
+  }
   stt.workspace_bytes = p->total_bytes;
   stt.const_bytes = p->const_bytes;
   stt.scratch_bytes = p->scratch_bytes;
