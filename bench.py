@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bristlecone70_d32", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="bristlecone70_d32", choices=sorted(WORKLOADS) + ["serving_mix"])
+    ap.add_argument("--queries", type=int, default=96, help="serving_mix: queries in the Poisson stream")
     ap.add_argument("--precision", default="auto", choices=["auto", "c64", "tf32x3", "bf16x3", "c128"])
     ap.add_argument("--batch-log2", type=int, default=0)
     ap.add_argument("--slices", type=int, default=0, help="slices per step (0: auto)")
@@ -153,6 +154,41 @@ def measured_peaks():
 TC_DRAM_BYTES_PER_FLOP = {"tf32x3": 1.315e9 / 2.749e11, "bf16x3": 0.432e9 / 2.749e11}
 
 
+def plan_roofline(plan, precision, ms_per_group):
+    """Plan-level roofline: T_roof = sum over the per-slice steps of
+    max(hardware flops / peak of the mode, algorithmic bytes / HBM), plus the
+    permutes (read + write at HBM speed); its ratio to the measured time of one
+    group (one slice, one bitstring batch)."""
+    hbm, bf16, _, sm_mhz, src = measured_peaks()
+    simt = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    tc = {"tf32x3": bf16 * 1.1 / 2.25, "bf16x3": bf16}.get(precision)
+    fp64 = simt / 64   # GB300 FP64 CUDA-core rate, 1/64 of FP32
+    d = json.loads(plan.describe())
+    size = [1 << len(t["lay"]) for t in d["tensors"]]
+    lay = [set(t["lay"]) for t in d["tensors"]]
+    esz = 16 if precision == "c128" else 8
+    t = 0.0
+    for st in d["steps"]:
+        if not st["var"]:
+            continue
+        a, b, c = st["a"], st["b"], st["c"]
+        nbytes = esz * (size[a] + size[b] + size[c])
+        if st["gemm"]:
+            fl = 8.0 * st["batch"] * st["M"] * st["N"] * st["K"]
+        else:
+            fl = 8.0 * (1 << len(lay[a] | lay[b]))
+        if st["gemm"] and st["tc"] and tc:
+            tf = 3 * fl / (tc * 1e12)
+        else:
+            tf = fl / ((fp64 if precision == "c128" else simt) * 1e12)
+        t += max(tf, nbytes / (hbm * 1e9))
+    for it in d["var_items"]:
+        if it[0] == 2:  # permute: read and write the tensor
+            t += 2 * esz * size[it[1]] / (hbm * 1e9)
+    return {"t_roof_ms": t * 1e3, "t_measured_ms": ms_per_group, "frac": t * 1e3 / ms_per_group,
+            "peaks": f"{src}: HBM {hbm:.0f} GB/s, tensor {tc or 0:.0f} TF/s, FP32 {simt:.1f} TF/s"}
+
+
 def roofline(prof, precision):
     """Dominant kernel kind of the profiled pass and its roofline position."""
     hbm, bf16, bf16_s, sm_mhz, src = measured_peaks()
@@ -213,6 +249,90 @@ def cpu_oracle_sample(spec, segs, bits, budget_s, k):
                       f"{el:.1f} s, extrapolated x{n_sub}/{done} sub-slices x 2^{k} slices; oracle setup {setup:.1f} s"}
 
 
+def run_serving(args):
+    """Continuous-batching server over resident plans: grids 4x4..7x7 at
+    depths 1+16+1, 1+24+1, 1+32+1; queries of 1..256 bitstrings on uniformly
+    chosen circuits. The saturation rate is measured on a burst; then a Poisson
+    stream at 0.8x that rate gives the sustained amplitudes/s and the server's
+    p50/p99 query latency (submit to completion)."""
+    import torch
+    import paper_1907_11217_gb300 as tz
+    import tz_inputs as ti
+    precision = args.precision if args.precision != "auto" else "bf16x3"
+    torch.cuda.set_device(0)
+    plans = []
+    t0 = time.perf_counter()
+    for (r, c) in ((4, 4), (5, 5), (6, 6), (7, 7)):
+        for t in (16, 24, 32):
+            spec = ti.circuit_to_spec(r * c, ti.generate_circuit(ti.grid(r, c), t, 4))
+            net = tz.tz_network_from_circuit(tz.tz_circuit_from_spec(spec), 6)
+            tree = tz.tz_path_greedy(net, restarts=16, seed=7, log2_max_intermediate=26, precision=precision,
+                                     algorithm="elimination")
+            sliced = tz.tz_slice_select(net, tree, 26, 40)
+            plan = tz.tz_plan_create(net, tree, sliced, precision=precision, max_bitstrings=256)
+            plan.bind()
+            plans.append((plan, r * c, f"{r}x{c}_d{t}", len(sliced)))
+    prep_s = time.perf_counter() - t0
+    scratch = max(p[0].stats()["scratch_bytes"] for p in plans)
+    srv = tz.tz_server_create(arena_bytes=4 * scratch + (1 << 20), max_inflight=4)
+    rng = np.random.default_rng(4)
+
+    def make_queries(n, seed):
+        q = []
+        for i in range(n):
+            j = int(rng.integers(len(plans)))
+            nb = int(rng.integers(1, 257))
+            q.append((j, ti.random_bitstrings(plans[j][1], nb, seed + i)))
+        return q
+
+    def drain(tickets, limit_s=600):
+        done = {}
+        t_end = time.perf_counter() + limit_s
+        while len(done) < len(tickets) and time.perf_counter() < t_end:
+            for t in tickets:
+                if t not in done and srv.poll(t) is not None:
+                    done[t] = time.perf_counter()
+        return done
+
+    # warm-up: every plan once
+    drain([srv.submit(p[0], ti.random_bitstrings(p[1], 4, 7)) for p in plans])
+    # saturation: a burst of queries submitted at once
+    burst = make_queries(args.queries // 2, 10_000)
+    t0 = time.perf_counter()
+    tk = [srv.submit(plans[j][0], b) for j, b in burst]
+    drain(tk)
+    sat = sum(len(b) for _, b in burst) / (time.perf_counter() - t0)
+    # Poisson stream at 0.8x saturation (queries per second from the mean query size)
+    stream = make_queries(args.queries, 20_000)
+    mean_b = np.mean([len(b) for _, b in stream])
+    rate_q = 0.8 * sat / mean_b
+    gaps = rng.exponential(1.0 / rate_q, size=len(stream))
+    srv.close()
+    srv = tz.tz_server_create(arena_bytes=4 * scratch + (1 << 20), max_inflight=4)  # stream-only statistics
+    t0 = time.perf_counter()
+    tickets, t_next = [], t0
+    for (j, b), g in zip(stream, gaps):
+        t_next += g
+        while time.perf_counter() < t_next:
+            pass
+        tickets.append(srv.submit(plans[j][0], b))
+    done = drain(tickets)
+    elapsed = max(done.values()) - t0
+    p50, p99, n_done = srv.latency()
+    amps = sum(len(b) for _, b in stream)
+    line = {"metric": "amplitudes/s (serving mix, Poisson arrivals at 0.8x saturation)",
+            "value": amps / elapsed, "unit": "amplitudes/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": precision, "data": "synthetic (seeded circuits by the Sec. 1 prescription, uniform bitstrings)",
+            "config": {"workload": "serving_mix", "circuits": [p[2] for p in plans], "slices": [p[3] for p in plans],
+                       "bitstrings_per_query": "uniform 1..256", "queries": len(stream),
+                       "arrival_rate_qps": rate_q, "saturation_amps_per_s": sat, "plans_prep_s": prep_s,
+                       "max_inflight": 4},
+            "latency_ms": {"p50": p50 * 1e3, "p99": p99 * 1e3, "queries": n_done},
+            "vs_baseline": None}
+    print(json.dumps(line))
+    srv.close()
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle on the host cores, same metric."""
     rank = int(os.environ.get("RANK", "0"))
@@ -250,6 +370,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "serving_mix":
+        run_serving(args)
         return
     import torch
     import paper_1907_11217_gb300 as tz
@@ -351,6 +474,7 @@ def main():
     prof = plan.profile()
     plan.profile_enable(False)
     rl = roofline(prof, precision)
+    rl["plan_roofline"] = plan_roofline(plan, precision, ms / S)
     per_launch = {k: v["launches"] for k, v in prof.items()}
     launches_per_call = 1 + S * st["n_launches_per_group"]
 

@@ -204,3 +204,19 @@ def test_grid7x7_reduced_depth_batch64_vs_oracle(tz):
     plan, _, _, sl = build(tz, spec, "tf32x3", 14, batch_log2=6, k_max=6, restarts=16, max_bitstrings=64)
     got = tz.tz_contract_amplitudes(plan, bits)
     assert rel_err(got, ref, 49) <= TOL
+
+
+@pytest.mark.parametrize("prec", ["c64", "bf16x3"])
+def test_bristlecone72_reduced_depth_vs_oracle(tz, prec):
+    """Bristlecone-72 (with its two degree-1 qubits), depth 1+12+1: the planner
+    absorbs the degree-1 wires into their neighbours' subtrees; the oracle
+    contracts the 72-qubit network directly. The amplitudes agree."""
+    spec = ti.circuit_to_spec(72, ti.generate_circuit(ti.bristlecone(72), 12, 3))
+    bits = ti.random_bitstrings(72, 4, 37)
+    c = tn.Contractor(spec, max_log2=24)
+    ref = np.array([c.amplitude(x) for x in bits])
+    plan, *_ = build(tz, spec, prec, 30, restarts=16)
+    got = tz.tz_contract_amplitudes(plan, bits)
+    err = rel_err(got, ref, 72)
+    print(f"bristlecone72 d12 {prec}: max rel err {err:.2e}")
+    assert err <= (TOL if prec == "c64" else 3e-5)

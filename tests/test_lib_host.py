@@ -143,3 +143,20 @@ def test_bind_rejects_bad_workspace(tz):
     assert L.tz_contract_amplitudes(p.handle, b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), 1,
                                     out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == -1
     assert "workspace" in L.tz_last_error().decode()
+
+
+@pytest.mark.parametrize("depth,seed", [(20, 3), (24, 5)])
+def test_degree_one_qubits_cost_like_70(tz, depth, seed):
+    """Sec. 1: the two qubits of Bristlecone-72 with one neighbour each add
+    nothing of order to the contraction; the planner absorbs their wires, so
+    a 72-qubit circuit costs about what a 70-qubit one of the same depth does
+    (within a factor of 2 in flops per amplitude)."""
+    import math
+    flops = {}
+    for n in (70, 72):
+        spec = ti.circuit_to_spec(n, ti.generate_circuit(ti.bristlecone(n), depth, seed))
+        net = tz.tz_network_from_circuit(tz.tz_circuit_from_spec(spec), 0)
+        tree = tz.tz_path_greedy(net, restarts=32, seed=7, log2_max_intermediate=30, algorithm="elimination",
+                                 precision="bf16x3")
+        flops[n] = tz.tz_plan_create(net, tree, [], precision="bf16x3").stats()["flops_per_group"]
+    assert abs(math.log2(flops[72]) - math.log2(flops[70])) <= 1.0, flops
