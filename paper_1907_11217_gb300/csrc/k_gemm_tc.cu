@@ -48,13 +48,11 @@ namespace dev {
 namespace {
 
 constexpr int BM = 128;           // C rows per tile = TMEM lanes
-// K (real values) per stage, chosen so that the split operands have 64-byte
-// rows: TF32 16 (the FP32 A tile has 64-byte rows too; the small stages make
-// a ring of 4 to 8, which hides the TMA round trip), BF16 32 (the FP32 A
-// tile has 128-byte rows). BF16 stages of 16 values, with 32-byte rows,
-// measured slower.
+// K (real values) per stage: 32, so that the FP32 A tile has 128-byte rows
+// (whole L2 lines per TMA row; 64-byte rows measured slower) and the split B
+// 128-byte (TF32) or 64-byte (BF16) rows.
 template <int MODE>
-__host__ __device__ constexpr int stage_k() { return MODE == 0 ? 16 : 32; }
+__host__ __device__ constexpr int stage_k() { return 32; }
 // TMA, MMA, 4 split warps, 8 epilogue warps; registers are granted to warps
 // in groups of four, so 14 warps leave 128 registers a thread
 constexpr int kThreads = 448;
@@ -212,6 +210,12 @@ __device__ __forceinline__ void split_bf16(float x, uint16_t &hi, uint16_t &lo) 
   lo = __bfloat16_as_ushort(l);
 }
 
+// K-major operand in the 128-byte swizzled layout (rows of 128 bytes, 8-row
+// atoms of 1024 bytes): 16-byte chunk c of row r sits at chunk c ^ (r & 7).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
 // K-major operand in the 64-byte swizzled layout (rows of 64 bytes, 8-row
 // atoms of 512 bytes): 16-byte chunk c of row r sits at chunk c ^ ((r>>1)&3).
 __device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
@@ -257,14 +261,16 @@ constexpr int kFoldK = 128;
 
 // Per stage (shared memory): the FP32 A tile as loaded (128 rows x 64 B TF32 /
 // 128 B BF16) and the prepared B hi and lo tiles (BNP rows x 64 B).
-// TMEM (all 512 columns): a ring of ASLOTS split A tiles (32 columns each:
+// TMEM (all 512 columns): a ring of ASLOTS split A tiles (SLOT_COLS columns each:
 // hi, then lo) in the top columns, below it a ring of NBUF accumulators of
 // BNP columns (at least 32): the products of one range go to the next
 // accumulator of the ring while the epilogue drains the previous ones.
 template <int MODE, int BNP, int STAGES>
 struct TcSmem {
-  static constexpr uint32_t A_BYTES = BM * stage_k<MODE>() * 4;         // FP32 tile as loaded
-  static constexpr uint32_t B_BYTES = BNP * 64;
+  static constexpr uint32_t A_BYTES = BM * stage_k<MODE>() * 4;         // FP32 tile as loaded (128-byte rows)
+  static constexpr uint32_t BROW = MODE == MODE_TF32 ? 128 : 64;        // bytes per split B row
+  static constexpr uint32_t B_BYTES = BNP * BROW;
+  static constexpr uint32_t SLOT_COLS = MODE == MODE_TF32 ? 64 : 32;    // TMEM columns of a split A tile
   static constexpr uint32_t STAGE = A_BYTES + 2 * B_BYTES;
   static constexpr int EC = BNP >= 32 ? BNP / 2 : BNP;                // real columns per epilogue warp
   static constexpr uint32_t BARS = 512;                                // barriers and flags
@@ -274,7 +280,7 @@ struct TcSmem {
   static constexpr uint32_t ACC_COLS = BNP < 32 ? 32 : BNP;
   static constexpr uint32_t TMEM_COLS = 512;
   static constexpr int ASLOTS = 4;
-  static constexpr uint32_t A_COL0 = TMEM_COLS - ASLOTS * 32;
+  static constexpr uint32_t A_COL0 = TMEM_COLS - ASLOTS * SLOT_COLS;
   static constexpr int NBUF = A_COL0 / ACC_COLS;
   static_assert(BNP <= 128, "an epilogue thread holds half a row of the tile in registers");
   static_assert(3 * STAGES + 2 * NBUF + ASLOTS + 1 <= 62, "barriers and flags fit in BARS");
@@ -382,9 +388,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = MODE == MODE_TF32 ? idesc_tf32(BNP) : idesc_bf16(BNP);
-      // K per instruction: 8 TF32 or 16 BF16 values, 32 bytes either way;
-      // two instructions per 64-byte row
-      constexpr int kSteps = 2;
+      // K per instruction: 8 TF32 or 16 BF16 values (32 bytes of a B row,
+      // 8 TMEM columns of A)
+      constexpr int kSteps = stage_k<MODE>() / (MODE == MODE_TF32 ? 8 : 16);
       constexpr int kFoldKb = kFoldK / stage_k<MODE>();  // k-blocks per accumulation range
       int64_t g = 0, rg = 0;  // k-blocks and accumulation ranges issued
       bool ok = true;
@@ -409,12 +415,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_fence_after();
             const int slot = (int)(g % L::ASLOTS);
-            const uint32_t ah = tmem + L::A_COL0 + (uint32_t)(slot * 32), al = ah + 16;
+            const uint32_t ah = tmem + L::A_COL0 + (uint32_t)(slot * L::SLOT_COLS), al = ah + L::SLOT_COLS / 2;
             const uint32_t bh = smem_u32(B_hi(s)), bl = smem_u32(B_lo(s));
 #pragma unroll
             for (int kk = 0; kk < kSteps; kk++) {
               // 8 TMEM columns and 32 bytes of each B row per instruction
-              const uint64_t dbh = sw64_desc(bh + kk * 32), dbl = sw64_desc(bl + kk * 32);
+              const uint64_t dbh = L::BROW == 128 ? sw128_desc(bh + kk * 32) : sw64_desc(bh + kk * 32);
+              const uint64_t dbl = L::BROW == 128 ? sw128_desc(bl + kk * 32) : sw64_desc(bl + kk * 32);
               const uint32_t acc = ((kb - r0) | kk) != 0;
               if (MODE == MODE_TF32) {
                 umma_tf32_ts(d_acc, ah + kk * 8, dbh, idesc, acc);
@@ -456,33 +463,40 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        uint32_t hi[16], lo[16];
+        // 32 floats: 16-byte chunk c of the row at chunk c ^ (row & 7)
+        const uint4 *src = reinterpret_cast<const uint4 *>(A_raw(s) + row * 128);
+        const uint32_t ts = tq + (uint32_t)(slot * L::SLOT_COLS);
         if (MODE == MODE_TF32) {
-          // 16 floats: 16-byte chunk c of the row at chunk c ^ ((row >> 1) & 3)
-          const uint4 *src = reinterpret_cast<const uint4 *>(A_raw(s) + row * 64);
+          // hi in columns 0..31 of the slot, lo in 32..63
 #pragma unroll
-          for (int c = 0; c < 4; c++) {
-            const uint4 v = src[c ^ ((row >> 1) & 3)];
-            const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+          for (int h = 0; h < 2; h++) {
+            uint32_t hi[16], lo[16];
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
-              hi[4 * c + j] = split_hi(x[j]);
-              lo[4 * c + j] = __float_as_uint(__uint_as_float(x[j]) - __uint_as_float(hi[4 * c + j]));
+            for (int c = 0; c < 4; c++) {
+              const uint4 v = src[(4 * h + c) ^ (row & 7)];
+              const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+              for (int j = 0; j < 4; j++) {
+                hi[4 * c + j] = split_hi(x[j]);
+                lo[4 * c + j] = __float_as_uint(__uint_as_float(x[j]) - __uint_as_float(hi[4 * c + j]));
+              }
             }
+            tmem_st16(ts + (uint32_t)(16 * h), hi);
+            tmem_st16(ts + (uint32_t)(32 + 16 * h), lo);
           }
         } else {
-          // 32 floats: chunk c of the row at chunk c ^ (row & 7); BF16 pairs
-          // packed with the lower k in the low half
-          const uint4 *src = reinterpret_cast<const uint4 *>(A_raw(s) + row * 128);
+          // BF16 pairs packed with the lower k in the low half: hi in columns
+          // 0..15, lo in 16..31
+          uint32_t hi[16], lo[16];
 #pragma unroll
           for (int c = 0; c < 8; c++) {
             const uint4 v = src[c ^ (row & 7)];
             split_bf16x2(__uint_as_float(v.x), __uint_as_float(v.y), hi[2 * c], lo[2 * c]);
             split_bf16x2(__uint_as_float(v.z), __uint_as_float(v.w), hi[2 * c + 1], lo[2 * c + 1]);
           }
+          tmem_st16(ts, hi);
+          tmem_st16(ts + 16, lo);
         }
-        tmem_st16(tq + (uint32_t)(slot * 32), hi);
-        tmem_st16(tq + (uint32_t)(slot * 32 + 16), lo);
         tmem_st_wait();
         tc_fence_before();
         mbar_arrive(&conv[s]);
@@ -732,6 +746,8 @@ cudaError_t run_tc(const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensor
                    const TcArgs &args, int64_t n_tiles, cudaStream_t s) {
   using L = TcSmem<MODE, BNP, STAGES>;
   static_assert(L::TOTAL <= 227 * 1024, "shared memory budget");
+  // one CTA per SM: each allocates all of TMEM
+  static_assert(L::TOTAL > 114 * 1024, "two CTAs would share an SM");
   auto kernel = tc_split3_kernel<MODE, BNP, STAGES>;
   static int resident = 0;
   if (!resident) {
@@ -749,13 +765,14 @@ cudaError_t run_tc(const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensor
 template <int MODE>
 cudaError_t dispatch(int bnp, const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensorMap &tbl,
                      const CUtensorMap &tc, const TcArgs &args, int64_t n_tiles, cudaStream_t s) {
-  // stages: as many as fit beside the epilogue staging (at most 8)
+  // stages: at most what fits beside the epilogue staging (and at most 8);
+  // for the 128-column tiles, the counts measured fastest
   constexpr bool T = MODE == MODE_TF32;
   switch (bnp) {
     case 16: return run_tc<MODE, 16, 8>(ta, tbh, tbl, tc, args, n_tiles, s);
-    case 32: return run_tc<MODE, 32, 8>(ta, tbh, tbl, tc, args, n_tiles, s);
-    case 64: return run_tc<MODE, 64, T ? 8 : 7>(ta, tbh, tbl, tc, args, n_tiles, s);
-    default: return run_tc<MODE, 128, T ? 7 : 5>(ta, tbh, tbl, tc, args, n_tiles, s);
+    case 32: return run_tc<MODE, 32, T ? 7 : 8>(ta, tbh, tbl, tc, args, n_tiles, s);
+    case 64: return run_tc<MODE, 64, T ? 5 : 7>(ta, tbh, tbl, tc, args, n_tiles, s);
+    default: return run_tc<MODE, 128, T ? 3 : 4>(ta, tbh, tbl, tc, args, n_tiles, s);
   }
 }
 
