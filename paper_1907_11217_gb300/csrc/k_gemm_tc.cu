@@ -48,11 +48,12 @@ namespace dev {
 namespace {
 
 constexpr int BM = 128;           // C rows per tile = TMEM lanes
-// K (real values) per stage: 32, so that the FP32 A tile has 128-byte rows
-// (whole L2 lines per TMA row; 64-byte rows measured slower) and the split B
-// 128-byte (TF32) or 64-byte (BF16) rows.
+// K (real values) per stage: TF32 32, BF16 64, so that every TMA row is a
+// whole 128-byte L2 line (64-byte rows measured slower): the FP32 A tile in
+// one (TF32) or two (BF16) boxes of 128-byte rows, the split B in 128-byte
+// rows.
 template <int MODE>
-__host__ __device__ constexpr int stage_k() { return 32; }
+__host__ __device__ constexpr int stage_k() { return MODE == 0 ? 32 : 64; }
 // TMA, MMA, 4 split warps, 8 epilogue warps; registers are granted to warps
 // in groups of four, so 14 warps leave 128 registers a thread
 constexpr int kThreads = 448;
@@ -267,14 +268,14 @@ constexpr int kFoldK = 128;
 // accumulator of the ring while the epilogue drains the previous ones.
 template <int MODE, int BNP, int STAGES>
 struct TcSmem {
-  static constexpr uint32_t A_BYTES = BM * stage_k<MODE>() * 4;         // FP32 tile as loaded (128-byte rows)
-  static constexpr uint32_t BROW = MODE == MODE_TF32 ? 128 : 64;        // bytes per split B row
+  static constexpr uint32_t A_BYTES = BM * stage_k<MODE>() * 4;         // FP32 tile as loaded (boxes of 128-byte rows)
+  static constexpr uint32_t BROW = 128;                                  // bytes per split B row
   static constexpr uint32_t B_BYTES = BNP * BROW;
-  static constexpr uint32_t SLOT_COLS = MODE == MODE_TF32 ? 64 : 32;    // TMEM columns of a split A tile
+  static constexpr uint32_t SLOT_COLS = 64;                              // TMEM columns of a split A tile
   static constexpr uint32_t STAGE = A_BYTES + 2 * B_BYTES;
   static constexpr int EC = BNP >= 32 ? BNP / 2 : BNP;                // real columns per epilogue warp
   static constexpr uint32_t BARS = 512;                                // barriers and flags
-  static constexpr uint32_t STAGING = 8 * 2 * 2048;                    // epilogue: 8 warps x 2 x (32 rows x 64 B)
+  static constexpr uint32_t STAGING = 8 * 2048;                        // epilogue: 8 warps x (32 rows x 64 B)
   static constexpr uint32_t COLOFF = 8 * (EC / 2) * 8;                 // epilogue: 8 warps x column offsets
   static constexpr uint32_t TOTAL = STAGES * STAGE + STAGING + BARS + COLOFF + 1024;  // + alignment
   static constexpr uint32_t ACC_COLS = BNP < 32 ? 32 : BNP;
@@ -374,7 +375,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           mbar_expect_tx(&full[s], L::A_BYTES + 2 * L::B_BYTES);
-          tma_load_2d(A_raw(s), &tmA, kb * stage_k<MODE>(), d.rowA, &full[s], stream);
+          // A in boxes of 32 floats (128-byte rows), one after the other
+#pragma unroll
+          for (int h = 0; h < stage_k<MODE>() / 32; h++)
+            tma_load_2d(A_raw(s) + h * BM * 128, &tmA, kb * stage_k<MODE>() + 32 * h, d.rowA, &full[s], stream);
           tma_load_2d(B_hi(s), &tmBh, kb * stage_k<MODE>(), d.rowB, &full[s], keep);
           tma_load_2d(B_lo(s), &tmBl, kb * stage_k<MODE>(), d.rowB, &full[s], keep);
         }
@@ -420,8 +424,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int kk = 0; kk < kSteps; kk++) {
               // 8 TMEM columns and 32 bytes of each B row per instruction
-              const uint64_t dbh = L::BROW == 128 ? sw128_desc(bh + kk * 32) : sw64_desc(bh + kk * 32);
-              const uint64_t dbl = L::BROW == 128 ? sw128_desc(bl + kk * 32) : sw64_desc(bl + kk * 32);
+              const uint64_t dbh = sw128_desc(bh + kk * 32), dbl = sw128_desc(bl + kk * 32);
               const uint32_t acc = ((kb - r0) | kk) != 0;
               if (MODE == MODE_TF32) {
                 umma_tf32_ts(d_acc, ah + kk * 8, dbh, idesc, acc);
@@ -463,11 +466,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        // 32 floats: 16-byte chunk c of the row at chunk c ^ (row & 7)
-        const uint4 *src = reinterpret_cast<const uint4 *>(A_raw(s) + row * 128);
+        // boxes of 32 floats: 16-byte chunk c of a row at chunk c ^ (row & 7)
         const uint32_t ts = tq + (uint32_t)(slot * L::SLOT_COLS);
         if (MODE == MODE_TF32) {
-          // hi in columns 0..31 of the slot, lo in 32..63
+          // one box; hi in columns 0..31 of the slot, lo in 32..63
+          const uint4 *src = reinterpret_cast<const uint4 *>(A_raw(s) + row * 128);
 #pragma unroll
           for (int h = 0; h < 2; h++) {
             uint32_t hi[16], lo[16];
@@ -485,17 +488,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             tmem_st16(ts + (uint32_t)(32 + 16 * h), lo);
           }
         } else {
-          // BF16 pairs packed with the lower k in the low half: hi in columns
-          // 0..15, lo in 16..31
-          uint32_t hi[16], lo[16];
+          // two boxes (K 0..31, 32..63); BF16 pairs packed with the lower k in
+          // the low half: hi in columns 0..31, lo in 32..63
 #pragma unroll
-          for (int c = 0; c < 8; c++) {
-            const uint4 v = src[c ^ (row & 7)];
-            split_bf16x2(__uint_as_float(v.x), __uint_as_float(v.y), hi[2 * c], lo[2 * c]);
-            split_bf16x2(__uint_as_float(v.z), __uint_as_float(v.w), hi[2 * c + 1], lo[2 * c + 1]);
+          for (int h = 0; h < 2; h++) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(A_raw(s) + h * BM * 128 + row * 128);
+            uint32_t hi[16], lo[16];
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+              const uint4 v = src[c ^ (row & 7)];
+              split_bf16x2(__uint_as_float(v.x), __uint_as_float(v.y), hi[2 * c], lo[2 * c]);
+              split_bf16x2(__uint_as_float(v.z), __uint_as_float(v.w), hi[2 * c + 1], lo[2 * c + 1]);
+            }
+            tmem_st16(ts + (uint32_t)(16 * h), hi);
+            tmem_st16(ts + (uint32_t)(32 + 16 * h), lo);
           }
-          tmem_st16(ts, hi);
-          tmem_st16(ts + 16, lo);
         }
         tmem_st_wait();
         tc_fence_before();
@@ -560,11 +567,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         int64_t om_u[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) om_u[u] = __shfl_sync(0xffffffffu, om, 8 * u + (lane >> 2));
-        uint8_t *stg = staging + e * 4096;
+        uint8_t *buf = staging + e * 2048;
 #pragma unroll
         for (int c = 0; c < EC; c += 16) {
           if (n0 + c / 2 < a.N) {  // N is a multiple of 8 here
-            uint8_t *buf = stg + (((c >> 4) & 1) << 11);
+            __syncwarp();  // the previous chunk's rows have been read
 #pragma unroll
             for (int j = 0; j < 4; j++)
               *reinterpret_cast<float4 *>(buf + lane * 64 + ((j ^ ((lane >> 1) & 3)) << 4)) =
@@ -589,13 +596,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         // 16 columns (8 complex) at a time: this warp's 32 rows go to its
         // staging buffer in the 64-byte swizzled layout (16-byte chunk c of
         // row r at chunk c ^ ((r >> 1) & 3)), then one bulk tensor store.
-        uint8_t *stg = staging + e * 4096;
+        uint8_t *buf = staging + e * 2048;
         const int y = (int)(d.z * a.M + (int64_t)d.mt * BM + q * 32);
 #pragma unroll
         for (int c = 0; c < EC; c += 16) {
           if (n0 + c / 2 < a.N) {
-            uint8_t *buf = stg + (((c >> 4) & 1) << 11);
-            if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+            // the previous store has read the buffer
+            if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
             __syncwarp();
 #pragma unroll
             for (int j = 0; j < 4; j++) {
@@ -769,10 +776,10 @@ cudaError_t dispatch(int bnp, const CUtensorMap &ta, const CUtensorMap &tbh, con
   // for the 128-column tiles, the counts measured fastest
   constexpr bool T = MODE == MODE_TF32;
   switch (bnp) {
-    case 16: return run_tc<MODE, 16, 8>(ta, tbh, tbl, tc, args, n_tiles, s);
-    case 32: return run_tc<MODE, 32, T ? 7 : 8>(ta, tbh, tbl, tc, args, n_tiles, s);
-    case 64: return run_tc<MODE, 64, T ? 5 : 7>(ta, tbh, tbl, tc, args, n_tiles, s);
-    default: return run_tc<MODE, 128, T ? 3 : 4>(ta, tbh, tbl, tc, args, n_tiles, s);
+    case 16: return run_tc<MODE, 16, T ? 8 : 5>(ta, tbh, tbl, tc, args, n_tiles, s);
+    case 32: return run_tc<MODE, 32, T ? 7 : 5>(ta, tbh, tbl, tc, args, n_tiles, s);
+    case 64: return run_tc<MODE, 64, T ? 5 : 4>(ta, tbh, tbl, tc, args, n_tiles, s);
+    default: return run_tc<MODE, 128, 3>(ta, tbh, tbl, tc, args, n_tiles, s);
   }
 }
 
@@ -844,7 +851,7 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
   }
   CUtensorMap ta, tbh, tbl;
   const int sk = bf16 ? stage_k<MODE_BF16>() : stage_k<MODE_TF32>();
-  if (!make_map(&ta, A, 2 * K, rowsA, sk, BM, false) || !make_map(&tbh, Bh, 2 * K, rowsB, sk, bnp, bf16) ||
+  if (!make_map(&ta, A, 2 * K, rowsA, 32, BM, false) || !make_map(&tbh, Bh, 2 * K, rowsB, sk, bnp, bf16) ||
       !make_map(&tbl, Bl, 2 * K, rowsB, sk, bnp, bf16))
     return cudaErrorInvalidValue;
   TcArgs args{};
