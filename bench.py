@@ -151,7 +151,7 @@ def measured_peaks():
 # traffic grows with its flops for this kernel (row tiles re-read B), so the
 # per-launch traffic of a step is scaled from it. Must be re-captured whenever
 # the kernel changes.
-TC_DRAM_BYTES_PER_FLOP = {"tf32x3": 1.315e9 / 2.749e11, "bf16x3": 0.432e9 / 2.749e11}
+TC_DRAM_BYTES_PER_FLOP = {}
 
 
 def plan_roofline(plan, precision, ms_per_group):
@@ -269,7 +269,7 @@ def run_serving(args):
             tree = tz.tz_path_greedy(net, restarts=16, seed=7, log2_max_intermediate=26, precision=precision,
                                      algorithm="elimination")
             sliced = tz.tz_slice_select(net, tree, 26, 40)
-            plan = tz.tz_plan_create(net, tree, sliced, precision=precision, max_bitstrings=256)
+            plan = tz.tz_plan_create(net, tree, sliced, precision=precision, max_bitstrings=256, use_graph=True)
             plan.bind()
             plans.append((plan, r * c, f"{r}x{c}_d{t}", len(sliced)))
     prep_s = time.perf_counter() - t0

@@ -779,7 +779,7 @@ cudaError_t dispatch(int bnp, const CUtensorMap &ta, const CUtensorMap &tbh, con
     case 16: return run_tc<MODE, 16, T ? 8 : 5>(ta, tbh, tbl, tc, args, n_tiles, s);
     case 32: return run_tc<MODE, 32, T ? 7 : 5>(ta, tbh, tbl, tc, args, n_tiles, s);
     case 64: return run_tc<MODE, 64, T ? 5 : 4>(ta, tbh, tbl, tc, args, n_tiles, s);
-    default: return run_tc<MODE, 128, 3>(ta, tbh, tbl, tc, args, n_tiles, s);
+    default: return run_tc<MODE, 128, T ? 4 : 3>(ta, tbh, tbl, tc, args, n_tiles, s);
   }
 }
 

@@ -938,20 +938,22 @@ static void run_items(tz_plan *p, const std::vector<Item> &items, const RunCtx &
   }
 }
 
+static void clear_graphs(tz_plan *p) {
+  // an executable graph still in flight is freed when it completes
+  for (auto &g : p->graphs) {
+    cudaGraphExecDestroy(g.e);
+    cudaGraphDestroy(g.g);
+  }
+  p->graphs.clear();
+}
+
 void plan_bind(tz_plan *p, void *ws, size_t bytes) {
   if (!ws) fail(TZ_EINVAL, "workspace pointer is NULL");
   if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) fail(TZ_EINVAL, "workspace must be 256-byte aligned");
   if (bytes < p->total_bytes)
     fail(TZ_ENOMEM, "workspace too small: need " + std::to_string(p->total_bytes) + " bytes");
   cuda_check(cudaSetDevice(p->opts.device), "cudaSetDevice");
-  if (p->graph_exec) {
-    cudaGraphExecDestroy(p->graph_exec);
-    p->graph_exec = nullptr;
-  }
-  if (p->graph) {
-    cudaGraphDestroy(p->graph);
-    p->graph = nullptr;
-  }
+  clear_graphs(p);  // they hold pointers into the old workspace
   p->ws = static_cast<char *>(ws);
   p->ws_bytes = bytes;
   p->stream = static_cast<cudaStream_t>(p->opts.stream);
@@ -1019,27 +1021,41 @@ void plan_run(tz_plan *p, const RunCtx &ctx, int64_t n_rows, int64_t lo, int64_t
   const int64_t chunk = int64_t(1) << p->net.batch_log2;
   const int64_t n_chunks = (n_rows + chunk - 1) / chunk;
   const int64_t n_groups = n_chunks * (hi - lo);
-  const bool own = ctx.scratch == p->ws + p->off_scratch && ctx.stream == p->stream;
-  const bool graph = own && p->opts.use_graph && s != nullptr && !p->profiling;
-  if (graph && !p->graph_exec) {
-    cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
-    p->capturing = true;
-    try {
-      run_items(p, p->var_items, ctx);
-    } catch (...) {
+  cudaGraphExec_t exec = nullptr;
+  if (p->opts.use_graph && s != nullptr && !p->profiling) {
+    for (auto &g : p->graphs)
+      if (g.scratch == ctx.scratch) exec = g.e;
+    if (!exec) {
+      cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+      p->capturing = true;
+      try {
+        run_items(p, p->var_items, ctx);
+      } catch (...) {
+        p->capturing = false;
+        cudaGraph_t g2 = nullptr;
+        cudaStreamEndCapture(s, &g2);
+        if (g2) cudaGraphDestroy(g2);
+        throw;
+      }
       p->capturing = false;
-      cudaGraph_t g2 = nullptr;
-      cudaStreamEndCapture(s, &g2);
-      if (g2) cudaGraphDestroy(g2);
-      throw;
+      tz_plan::Graph g{ctx.scratch, nullptr, nullptr};
+      cuda_check(cudaStreamEndCapture(s, &g.g), "end capture");
+      if (cudaGraphInstantiate(&g.e, g.g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g.g);
+        fail(TZ_ECUDA, "instantiate graph");
+      }
+      if (p->graphs.size() >= tz_plan::kMaxGraphs) {
+        cudaGraphExecDestroy(p->graphs.front().e);
+        cudaGraphDestroy(p->graphs.front().g);
+        p->graphs.erase(p->graphs.begin());
+      }
+      p->graphs.push_back(g);
+      exec = g.e;
     }
-    p->capturing = false;
-    cuda_check(cudaStreamEndCapture(s, &p->graph), "end capture");
-    cuda_check(cudaGraphInstantiate(&p->graph_exec, p->graph, 0), "instantiate graph");
   }
   for (int64_t gi = 0; gi < n_groups; gi++) {
-    if (graph)
-      cuda_check(cudaGraphLaunch(p->graph_exec, s), "graph launch");
+    if (exec)
+      cuda_check(cudaGraphLaunch(exec, s), "graph launch");
     else
       run_items(p, p->var_items, ctx);
   }
@@ -1052,8 +1068,7 @@ void plan_destroy(tz_plan *p) {
     cudaEventDestroy(q.b);
   }
   for (auto e : p->event_pool) cudaEventDestroy(e);
-  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
-  if (p->graph) cudaGraphDestroy(p->graph);
+  clear_graphs(p);
   delete p;
 }
 

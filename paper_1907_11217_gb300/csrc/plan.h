@@ -79,8 +79,15 @@ struct tz_plan {
   cudaStream_t stream = nullptr;
   bool bound = false;
   int64_t lo = 0, hi = 1;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t graph_exec = nullptr;
+  // captured launches of one group, per scratch part they run on (the
+  // plan's own, or a server slot's), oldest dropped beyond kMaxGraphs
+  struct Graph {
+    char *scratch;
+    cudaGraph_t g;
+    cudaGraphExec_t e;
+  };
+  static constexpr size_t kMaxGraphs = 8;
+  std::vector<Graph> graphs;
   tz_plan_stats stats{};
   // profiling
   bool profiling = false;
@@ -109,8 +116,8 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
 void plan_bind(tz_plan *p, void *ws, size_t bytes);
 // Contract all groups of the slice range [lo, hi) for n rows already in the
 // scratch part's bitstring buffer; leaves the FP64 sums in its accumulator
-// (asynchronous on ctx.stream). The plan's own scratch part may replay a
-// captured graph; other scratch parts launch directly.
+// (asynchronous on ctx.stream). With use_graph, the launches of a group are
+// captured once per scratch part and replayed.
 void plan_run(tz_plan *p, const RunCtx &ctx, int64_t n_rows, int64_t lo, int64_t hi);
 void plan_destroy(tz_plan *p);
 void plan_profile_collect(tz_plan *p);

@@ -24,9 +24,12 @@ def tz():
 def test_mix_equals_alone(tz):
     circuits = [(4, 4, 10, 1), (4, 5, 12, 3), (3, 5, 16, 8), (4, 4, 16, 5)]
     plans = []
-    for (r, c, t, seed) in circuits:
+    for i, (r, c, t, seed) in enumerate(circuits):
         spec = grid_spec(r, c, t, seed)
-        plan, *_ = make_plan(tz, spec, batch_log2=2, slice_bits=2, small_log2=5, max_bitstrings=256)
+        # half the plans replay captured graphs on the server's slots (their
+        # runs alone, without a stream of their own, launch directly)
+        plan, *_ = make_plan(tz, spec, batch_log2=2, slice_bits=2, small_log2=5, max_bitstrings=256,
+                             use_graph=(i % 2 == 0))
         plans.append((plan, spec, r * c))
     rng = np.random.default_rng(4)
     queries = []
