@@ -151,7 +151,7 @@ def measured_peaks():
 # traffic grows with its flops for this kernel (row tiles re-read B), so the
 # per-launch traffic of a step is scaled from it. Must be re-captured whenever
 # the kernel changes.
-TC_DRAM_BYTES_PER_FLOP = {}
+TC_DRAM_BYTES_PER_FLOP = {"tf32x3": 1.474e9 / 2.749e11, "bf16x3": 0.4164e9 / 2.749e11}
 
 
 def plan_roofline(plan, precision, ms_per_group):
