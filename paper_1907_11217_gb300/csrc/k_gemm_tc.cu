@@ -15,9 +15,9 @@
 // dropped lo*lo term is below 2^-22 |a||b|.
 //
 // Pipeline per CTA (tiles of 128 rows of C by up to 64 complex columns):
-//   warp 0     : TMA loads of the A tile (TF32: 128 rows x 16 floats, 64B
-//                swizzle; BF16: 128 rows x 32 floats, 128B swizzle) and of
-//                the prepared hi/lo B tiles, into a ring of stages;
+//   warp 0     : TMA loads of the FP32 A tile (128 rows in boxes of 32 floats,
+//                128B swizzle: one box TF32, two BF16) and of the prepared
+//                hi/lo B tiles (128-byte rows), into a ring of stages;
 //   warp 1     : TMEM allocation; one thread issues tcgen05.mma (A from
 //                TMEM, B from shared memory) and commits stage, A-slot and
 //                accumulator releases to mbarriers;
@@ -217,13 +217,6 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
-// K-major operand in the 64-byte swizzled layout (rows of 64 bytes, 8-row
-// atoms of 512 bytes): 16-byte chunk c of row r sits at chunk c ^ ((r>>1)&3).
-__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
-}
-
 // FP32 accumulator, BF16 A and B, both K-major, N = n_cols, M = 128.
 __host__ __device__ constexpr uint32_t idesc_bf16(int n_cols) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n_cols >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
@@ -260,8 +253,9 @@ __device__ __forceinline__ int64_t scatter_bits(int64_t v, int n, const int8_t *
 // (round to nearest), which bounds that bias at about 6e-9 kFoldK per product.
 constexpr int kFoldK = 128;
 
-// Per stage (shared memory): the FP32 A tile as loaded (128 rows x 64 B TF32 /
-// 128 B BF16) and the prepared B hi and lo tiles (BNP rows x 64 B).
+// Per stage (shared memory): the FP32 A tile as loaded (128 rows in boxes of
+// 128-byte rows: one TF32, two BF16) and the prepared B hi and lo tiles (BNP
+// rows x 128 B).
 // TMEM (all 512 columns): a ring of ASLOTS split A tiles (SLOT_COLS columns each:
 // hi, then lo) in the top columns, below it a ring of NBUF accumulators of
 // BNP columns (at least 32): the products of one range go to the next
