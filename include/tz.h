@@ -174,8 +174,10 @@ typedef struct {
   int device;            /* CUDA device ordinal                                     */
   void *stream;          /* cudaStream_t the plan launches on (NULL = default)     */
   int small_log2;        /* steps with output and work below this use the direct SIMT kernel (0 = default) */
-  int use_graph;         /* 1: replay the per-group launch sequence as a CUDA graph
-                            (needs a non-NULL stream)                              */
+  int use_graph;         /* 1: replay the per-group launch sequence as a CUDA graph,
+                            captured once per scratch part it runs on (the plan's
+                            own, or a server slot's; up to 8 kept) and replayed on
+                            any non-NULL stream                                    */
   int64_t max_bitstrings;/* bitstrings per call the workspace is sized for (0 = 4096) */
 } tz_plan_opts;
 
