@@ -34,6 +34,7 @@ WORKLOADS = {
     # name: (lattice kind, rows, cols, n_qubits, depth t, circuit seed, log2 target, bitstring seed)
     "bristlecone70_d32": ("bristlecone", 0, 0, 70, 32, 3, 30, 103),
     "grid7x7_d32": ("grid", 7, 7, 49, 32, 2, 24, 102),
+    "grid7x7_d40": ("grid", 7, 7, 49, 40, 5, 24, 105),
     "grid4x4_d10": ("grid", 4, 4, 16, 10, 1, 0, 101),
 }
 PAPER_S_PER_AMP = {"bristlecone70_d32": 0.43}  # Table 2 (1449 x 88 vCPU), context only

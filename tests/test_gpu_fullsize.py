@@ -220,3 +220,28 @@ def test_bristlecone72_reduced_depth_vs_oracle(tz, prec):
     err = rel_err(got, ref, 72)
     print(f"bristlecone72 d12 {prec}: max rel err {err:.2e}")
     assert err <= (TOL if prec == "c64" else 3e-5)
+
+
+def test_grid7x7_depth40_precision_sweep(tz):
+    """7x7 depth 1+40+1 with 2^14 slices (the deepest grid workload): the
+    partial amplitude of slices [0, 32) for 4 bitstrings in each FP32-class
+    mode against complex128 on the same tree and slicing; errors printed."""
+    import torch
+    spec = grid_spec(7, 7, 40, 5)
+    bits = ti.random_bitstrings(49, 4, 105)
+    net = tz.tz_network_from_circuit(tz.tz_circuit_from_spec(spec), 0)
+    tree = tz.tz_path_greedy(net, restarts=32, seed=7, log2_max_intermediate=24, algorithm="elimination")
+    sl = tz.tz_slice_select(net, tree, 24, 20)
+    assert len(sl) == 14
+    out = {}
+    for prec in ("c128", "c64", "tf32x3", "bf16x3"):
+        plan = tz.tz_plan_create(net, tree, sl, precision=prec, stream=torch.cuda.Stream(), use_graph=True,
+                                 max_bitstrings=4)
+        st = plan.stats()
+        assert st["flops_per_group"] * 32 < MAX_FLOPS_PER_AMPLITUDE
+        plan.bind()
+        plan.set_slice_range(0, 32)
+        out[prec] = tz.tz_contract_amplitudes(plan, bits)
+    errs = {m: rel_err(out[m], out["c128"], 49) for m in ("c64", "tf32x3", "bf16x3")}
+    print("grid7x7 d40 (32 of 2^14 slices) errors vs complex128:", {m: f"{e:.2e}" for m, e in errs.items()})
+    assert errs["c64"] <= 1e-5 and errs["tf32x3"] <= 3e-5 and errs["bf16x3"] <= 1e-4
