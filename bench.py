@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bristlecone70_d32", choices=sorted(WORKLOADS) + ["serving_mix"])
     ap.add_argument("--queries", type=int, default=96, help="serving_mix: queries in the Poisson stream")
-    ap.add_argument("--precision", default="auto", choices=["auto", "c64", "tf32x3", "bf16x3", "c128"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "c64", "tf32x3", "bf16x3", "fp16x3", "c128"])
     ap.add_argument("--batch-log2", type=int, default=0)
     ap.add_argument("--slices", type=int, default=0, help="slices per step (0: auto)")
     ap.add_argument("--log2-max", type=int, default=0, help="slicing target (0: workload default)")
@@ -162,7 +162,7 @@ def plan_roofline(plan, precision, ms_per_group):
     group (one slice, one bitstring batch)."""
     hbm, bf16, _, sm_mhz, src = measured_peaks()
     simt = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    tc = {"tf32x3": bf16 * 1.1 / 2.25, "bf16x3": bf16}.get(precision)
+    tc = {"tf32x3": bf16 * 1.1 / 2.25, "bf16x3": bf16, "fp16x3": bf16}.get(precision)
     fp64 = simt / 64   # GB300 FP64 CUDA-core rate, 1/64 of FP32
     d = json.loads(plan.describe())
     size = [1 << len(t["lay"]) for t in d["tensors"]]
@@ -202,7 +202,7 @@ def roofline(prof, precision):
     out = {"kernel": dom, "launches": d["launches"], "share_of_step": d["ms"] / total_ms if total_ms else None,
            "traffic": None}
     if dom == "gemm_tc":
-        ratio = {"tf32x3": 1.1 / 2.25, "bf16x3": 1.0}[precision]   # nominal dense TF32 : BF16
+        ratio = {"tf32x3": 1.1 / 2.25, "bf16x3": 1.0, "fp16x3": 1.0}[precision]   # nominal dense : BF16
         peak = bf16 * ratio
         out.update(bound="tensor", unit="TFLOP/s", achieved=d["flops"] / sec / 1e12, peak=peak,
                    peak_source=f"{src} bf16 x nominal {precision[:4]}/bf16 ratio",
@@ -486,7 +486,7 @@ def main():
     if world == 1 and not args.no_compare:
         compare = {}
         plan.close()  # free its workspace before the other plans bind theirs
-        for other in ("c64", "bf16x3", "tf32x3"):
+        for other in ("c64", "bf16x3", "fp16x3", "tf32x3"):
             if other == precision:
                 continue
             p2, _, _ = build_plan(tz, spec, args, other, stream, device, log2_max)

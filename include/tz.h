@@ -168,9 +168,12 @@ int tz_slice_select(const tz_network *net, const tz_tree *tree, int log2_max_int
 #define TZ_BF16X3       2   /* FP32 operands split hi+lo BF16, 3 tcgen05 products  */
 #define TZ_C128_SIMT    3   /* complex128, FP64 FMA on CUDA cores (reference-grade,
                                every tensor in FP64; slow on GB300's FP64 units)    */
+#define TZ_FP16X3       4   /* FP32 operands scaled by a power of two per tensor,
+                               split hi+lo FP16, 3 tcgen05 products; the scale is
+                               undone exactly in the product's epilogue            */
 
 typedef struct {
-  int precision;         /* TZ_C64_SIMT, TZ_TF32X3, TZ_BF16X3 or TZ_C128_SIMT      */
+  int precision;         /* TZ_C64_SIMT, TZ_TF32X3, TZ_BF16X3, TZ_FP16X3 or TZ_C128_SIMT */
   int device;            /* CUDA device ordinal                                     */
   void *stream;          /* cudaStream_t the plan launches on (NULL = default)     */
   int small_log2;        /* steps with output and work below this use the direct SIMT kernel (0 = default) */
@@ -295,22 +298,23 @@ int tz_op_permute(const void *in, void *out, int rank, const int32_t *perm, void
  * contraction of Sec. 1's network once operands are laid out):
  * A[z] is m x k row-major (k contiguous), B[z] is n x k row-major,
  * C[z] is m x n row-major; z-th matrices at element offsets z*sa, z*sb, z*sc.
- * precision: TZ_C64_SIMT, TZ_TF32X3, TZ_BF16X3, or TZ_C128_SIMT (then A,
- * B and C are complex128 arrays). The split-precision
+ * precision: TZ_C64_SIMT, TZ_TF32X3, TZ_BF16X3, TZ_FP16X3, or TZ_C128_SIMT
+ * (then A, B and C are complex128 arrays). The split-precision
  * modes need device scratch of tz_op_cgemm_scratch_bytes() bytes (256-byte
- * aligned): the hi/lo copies of B in the real view, and the partial products
+ * aligned): the hi/lo copies of B in the real view, the partial products
  * when a long K is split across CTAs (summed in a fixed order, so results do
- * not depend on scheduling); they accumulate in FP32 over ranges of 128 real
- * K values, added in FP32 with round to nearest. TZ_EUNSUPPORTED for shapes
- * they do not handle (m not a multiple of 128; k odd for TF32, not a multiple
- * of 4 for BF16). */
+ * not depend on scheduling), and for TZ_FP16X3 the partial maxima of |A| and
+ * |B| that set each operand's power-of-two scale; they accumulate in FP32
+ * over ranges of 128 real K values, added in FP32 with round to nearest.
+ * TZ_EUNSUPPORTED for shapes they do not handle (m not a multiple of 128; k
+ * odd for TF32, not a multiple of 4 for BF16 and FP16). */
 int tz_op_cgemm(int precision, int64_t batch, int64_t m, int64_t n, int64_t k,
                 const void *A, int64_t sa, const void *B, int64_t sb, void *C, int64_t sc,
                 void *scratch, size_t scratch_bytes, void *stream);
 int tz_op_cgemm_scratch_bytes(int precision, int64_t batch, int64_t m, int64_t n, int64_t k, size_t *bytes);
 
 /* Allocation-free variant of tz_op_cgemm for the split-precision modes
- * (TZ_TF32X3, TZ_BF16X3). The paper has no counterpart: this entry point
+ * (TZ_TF32X3, TZ_BF16X3, TZ_FP16X3). The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc (they hand all device memory
  * to another allocator, or must not pay for or fail in an allocation in a
  * latency-critical loop). The same arguments as tz_op_cgemm, without the

@@ -18,7 +18,7 @@ import ctypes
 
 import numpy as np
 
-from ._lib import (PROFILE_KINDS, tz_plan_profile, tz_server_opts, PRECISIONS, TZ_BF16X3, TZ_C64_SIMT, TZ_LATTICE_BRISTLECONE, TZ_LATTICE_GRID, TZ_TF32X3, TzError,
+from ._lib import (PROFILE_KINDS, tz_plan_profile, tz_server_opts, PRECISIONS, TZ_BF16X3, TZ_C64_SIMT, TZ_FP16X3, TZ_LATTICE_BRISTLECONE, TZ_LATTICE_GRID, TZ_TF32X3, TzError,
                    check, lib, tz_lattice, tz_network_opts, tz_path_opts, tz_plan_opts, tz_plan_stats)
 
 __all__ = [
@@ -26,7 +26,7 @@ __all__ = [
     "tz_circuit_generate_grid", "tz_circuit_generate_bristlecone", "tz_network_from_circuit", "tz_path_greedy",
     "tz_tree_from_pairs", "tz_slice_select", "tz_plan_create", "tz_contract_amplitudes",
     "tz_contract_amplitudes_device", "tz_op_permute", "tz_op_cgemm", "tz_op_accumulate", "PRECISIONS",
-    "TZ_C64_SIMT", "TZ_TF32X3", "TZ_BF16X3",
+    "TZ_C64_SIMT", "TZ_TF32X3", "TZ_BF16X3", "TZ_FP16X3",
 ]
 
 

@@ -11,8 +11,9 @@ LIB_PATH = os.path.join(_HERE, "libtz.so")
 
 TZ_OK, TZ_EINVAL, TZ_ENOMEM, TZ_EHBM_ADMIT, TZ_ECUDA, TZ_ETIMEOUT, TZ_EUNSUPPORTED, TZ_EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
 TZ_LATTICE_GRID, TZ_LATTICE_BRISTLECONE = 0, 1
-TZ_C64_SIMT, TZ_TF32X3, TZ_BF16X3, TZ_C128_SIMT = 0, 1, 2, 3
-PRECISIONS = {"c64": TZ_C64_SIMT, "tf32x3": TZ_TF32X3, "bf16x3": TZ_BF16X3, "c128": TZ_C128_SIMT}
+TZ_C64_SIMT, TZ_TF32X3, TZ_BF16X3, TZ_C128_SIMT, TZ_FP16X3 = 0, 1, 2, 3, 4
+PRECISIONS = {"c64": TZ_C64_SIMT, "tf32x3": TZ_TF32X3, "bf16x3": TZ_BF16X3, "c128": TZ_C128_SIMT,
+              "fp16x3": TZ_FP16X3}
 
 _ERR_NAMES = {TZ_EINVAL: "TZ_EINVAL", TZ_ENOMEM: "TZ_ENOMEM", TZ_EHBM_ADMIT: "TZ_EHBM_ADMIT", TZ_ECUDA: "TZ_ECUDA",
               TZ_ETIMEOUT: "TZ_ETIMEOUT", TZ_EUNSUPPORTED: "TZ_EUNSUPPORTED", TZ_EBUSY: "TZ_EBUSY"}

@@ -407,7 +407,7 @@ int tz_op_cgemm_scratch_bytes(int precision, int64_t batch, int64_t m, int64_t n
   REQUIRE(bytes, "NULL argument");
   REQUIRE(batch >= 1 && m >= 1 && n >= 1 && k >= 1, "sizes must be >= 1");
   *bytes = 0;
-  if (precision == TZ_TF32X3 || precision == TZ_BF16X3) {
+  if (precision == TZ_TF32X3 || precision == TZ_BF16X3 || precision == TZ_FP16X3) {
     if (!tz::dev::cgemm_tc_supported(precision, m, n, k))
       tz::fail(TZ_EUNSUPPORTED, "shape not supported by the tensor-core product");
     *bytes = tz::dev::cgemm_tc_scratch_bytes(precision, batch, m, n, k);
@@ -431,7 +431,7 @@ int tz_op_cgemm(int precision, int64_t batch, int64_t m, int64_t n, int64_t k, c
     tz::cuda_check(tz::dev::launch_cgemm_simt((const float2 *)A, (const float2 *)B, (float2 *)C, batch, m, n, k, sa,
                                               sb, sc, nullptr, s),
                    "simt gemm");
-  } else if (precision == TZ_TF32X3 || precision == TZ_BF16X3) {
+  } else if (precision == TZ_TF32X3 || precision == TZ_BF16X3 || precision == TZ_FP16X3) {
     if (!tz::dev::cgemm_tc_supported(precision, m, n, k))
       tz::fail(TZ_EUNSUPPORTED, "shape not supported by the tensor-core product");
     size_t need = tz::dev::cgemm_tc_scratch_bytes(precision, batch, m, n, k);

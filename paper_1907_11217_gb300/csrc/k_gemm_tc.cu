@@ -1,7 +1,9 @@
 // Split-precision complex products on the tcgen05 tensor cores (sm_103a).
-// Two modes share the pipeline: TF32x3 (operands split into TF32 hi + lo,
-// kind::tf32) and BF16x3 (operands split into BF16 hi + lo, kind::f16 with
-// BF16 inputs). Both accumulate in FP32 in TMEM.
+// Three modes share the pipeline: TF32x3 (operands split into TF32 hi + lo,
+// kind::tf32), BF16x3 (operands split into BF16 hi + lo, kind::f16 with BF16
+// inputs) and FP16x3 (operands scaled by a power of two per tensor, then split
+// into FP16 hi + lo, kind::f16 with FP16 inputs). All accumulate in FP32 in
+// TMEM.
 //
 // C[z] = A[z] B[z]^T in complex64, computed as one real product on the
 // interleaved (re, im) view: A is read as an m x 2k FP32 matrix and C is
@@ -34,6 +36,7 @@
 // drains its copies in flight, frees TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -203,6 +206,39 @@ __device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t &hi, u
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(x1 - h1), "f"(x0 - h0));
 }
 
+// FP16 counterpart of split_bf16x2 (x0, x1 already scaled into FP16 range):
+// hi = f16(x) and lo = f16(x - hi), both rounded to nearest even; x - hi is
+// exact in FP32.
+__device__ __forceinline__ void split_f16x2(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(x1), "f"(x0));
+  float h0, h1;
+  asm("{\n .reg .b16 l, h;\n mov.b32 {l, h}, %2;\n cvt.f32.f16 %0, l;\n cvt.f32.f16 %1, h;\n}\n"
+      : "=f"(h0), "=f"(h1)
+      : "r"(hi));
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(x1 - h1), "f"(x0 - h0));
+}
+__device__ __forceinline__ void split_f16(float x, uint16_t &hi, uint16_t &lo) {
+  const __half h = __float2half_rn(x);
+  const __half l = __float2half_rn(x - __half2float(h));
+  hi = __half_as_ushort(h);
+  lo = __half_as_ushort(l);
+}
+
+// Per-tensor scaling of the FP16 mode (the paper's amplitudes sit near
+// 2^(-n/2), far below FP16's normal range). The exponent s puts the largest
+// magnitude of an operand in [2^14, 2^15): every scaled value stays below
+// 65504 with its rounding, and FP16's subnormal spacing 2^-24 is 2^-38 of that
+// maximum, so x = hi + lo keeps about 22 bits relative to the tensor's
+// largest value. Scaling by 2^s is exact. maxbits is the FP32 bit pattern of
+// the largest |x|; zero, subnormal and non-finite maxima are clamped so that
+// 2^s and 2^-s stay normal FP32 numbers.
+__device__ __forceinline__ int f16_scale_exp(uint32_t maxbits) {
+  if (maxbits == 0 || maxbits >= 0x7f800000u) return 0;
+  const int e = (int)(maxbits >> 23) - 127;  // max|x| in [2^e, 2^(e+1))
+  return min(max(14 - e, -110), 110);
+}
+__device__ __forceinline__ float pow2i(int s) { return __int_as_float((s + 127) << 23); }  // s in [-126, 127]
+
 // Round-to-nearest-even BF16 split: hi = bf16(x), lo = bf16(x - hi).
 __device__ __forceinline__ void split_bf16(float x, uint16_t &hi, uint16_t &lo) {
   const __nv_bfloat16 h = __float2bfloat16_rn(x);
@@ -221,8 +257,16 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t idesc_bf16(int n_cols) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n_cols >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
+// FP32 accumulator, FP16 A and B (format 0), both K-major, N = n_cols, M = 128.
+__host__ __device__ constexpr uint32_t idesc_f16(int n_cols) {
+  return (1u << 4) | ((uint32_t)(n_cols >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
-enum TcMode { MODE_TF32 = 0, MODE_BF16 = 1 };
+enum TcMode { MODE_TF32 = 0, MODE_BF16 = 1, MODE_F16 = 2 };
+
+// FP16 mode: the largest |x| of A and of B, as per-block partial maxima
+// (FP32 bit patterns of |x|): A's at [0, pa), B's at [kMaxPartials, + pb).
+constexpr int kMaxPartials = 304;  // two blocks per SM of GB300
 
 struct TcArgs {
   float2 *C;
@@ -236,6 +280,8 @@ struct TcArgs {
   int tma_store;       // 1: row-major C written by bulk tensor stores (tmC)
   int ksplit, kb_per;  // K split into ksplit ranges of kb_per k-blocks; with
   int64_t split_stride;  // ksplit > 1, range s writes row-major partials at C + s * split_stride
+  const uint32_t *amax;  // FP16 mode: partial maxima of A and B (kMaxPartials apart)
+  int pa, pb;            // their counts
   CScatter sc;
 };
 
@@ -278,7 +324,8 @@ struct TcSmem {
   static constexpr uint32_t A_COL0 = TMEM_COLS - ASLOTS * SLOT_COLS;
   static constexpr int NBUF = A_COL0 / ACC_COLS;
   static_assert(BNP <= 128, "an epilogue thread holds half a row of the tile in registers");
-  static_assert(3 * STAGES + 2 * NBUF + ASLOTS + 1 <= 62, "barriers and flags fit in BARS");
+  // barriers, then the TMEM address, the abort flag and two scale exponents
+  static_assert((3 * STAGES + 2 * NBUF + ASLOTS + 1) * 8 + 16 <= BARS, "barriers and flags fit in BARS");
 };
 
 // Persistent: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
@@ -301,6 +348,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t *aempty = drain + 1;         // [ASLOTS] TMEM A slot read by its products
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(aempty + L::ASLOTS);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  int *scale_exp = reinterpret_cast<int *>(tmem_slot + 2);  // FP16 mode: exponents of A and B
   int64_t *coloff_all = reinterpret_cast<int64_t *>(smem + STAGES * L::STAGE + L::STAGING + L::BARS);
   uint8_t *staging = smem + STAGES * L::STAGE;  // 1024-aligned
   auto A_raw = [&](int s) { return smem + s * L::STAGE; };
@@ -349,6 +397,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                  "r"((uint32_t)L::TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  if (MODE == MODE_F16 && warp == 2) {
+    // reduce the partial maxima written by absmax_kernel earlier on the stream
+    uint32_t ma = 0, mb = 0;
+    for (int j = lane; j < a.pa; j += 32) ma = max(ma, a.amax[j]);
+    for (int j = lane; j < a.pb; j += 32) mb = max(mb, a.amax[kMaxPartials + j]);
+    ma = __reduce_max_sync(0xffffffffu, ma);
+    mb = __reduce_max_sync(0xffffffffu, mb);
+    if (lane == 0) {
+      scale_exp[0] = f16_scale_exp(ma);
+      scale_exp[1] = f16_scale_exp(mb);
+    }
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -385,7 +445,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = MODE == MODE_TF32 ? idesc_tf32(BNP) : idesc_bf16(BNP);
+      constexpr uint32_t idesc =
+          MODE == MODE_TF32 ? idesc_tf32(BNP) : (MODE == MODE_BF16 ? idesc_bf16(BNP) : idesc_f16(BNP));
       // K per instruction: 8 TF32 or 16 BF16 values (32 bytes of a B row,
       // 8 TMEM columns of A)
       constexpr int kSteps = stage_k<MODE>() / (MODE == MODE_TF32 ? 8 : 16);
@@ -446,6 +507,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;
     const int row = q * 32 + lane;
     const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16) + L::A_COL0;
+    const float sa = MODE == MODE_F16 ? pow2i(scale_exp[0]) : 1.f;
     int64_t g = 0;
     bool ok = true;
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
@@ -482,8 +544,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             tmem_st16(ts + (uint32_t)(32 + 16 * h), lo);
           }
         } else {
-          // two boxes (K 0..31, 32..63); BF16 pairs packed with the lower k in
-          // the low half: hi in columns 0..31, lo in 32..63
+          // two boxes (K 0..31, 32..63); BF16 or FP16 pairs packed with the
+          // lower k in the low half: hi in columns 0..31, lo in 32..63
 #pragma unroll
           for (int h = 0; h < 2; h++) {
             const uint4 *src = reinterpret_cast<const uint4 *>(A_raw(s) + h * BM * 128 + row * 128);
@@ -491,8 +553,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int c = 0; c < 8; c++) {
               const uint4 v = src[c ^ (row & 7)];
-              split_bf16x2(__uint_as_float(v.x), __uint_as_float(v.y), hi[2 * c], lo[2 * c]);
-              split_bf16x2(__uint_as_float(v.z), __uint_as_float(v.w), hi[2 * c + 1], lo[2 * c + 1]);
+              if (MODE == MODE_BF16) {
+                split_bf16x2(__uint_as_float(v.x), __uint_as_float(v.y), hi[2 * c], lo[2 * c]);
+                split_bf16x2(__uint_as_float(v.z), __uint_as_float(v.w), hi[2 * c + 1], lo[2 * c + 1]);
+              } else {
+                split_f16x2(__uint_as_float(v.x) * sa, __uint_as_float(v.y) * sa, hi[2 * c], lo[2 * c]);
+                split_f16x2(__uint_as_float(v.z) * sa, __uint_as_float(v.w) * sa, hi[2 * c + 1], lo[2 * c + 1]);
+              }
             }
             tmem_st16(ts + (uint32_t)(16 * h), hi);
             tmem_st16(ts + (uint32_t)(32 + 16 * h), lo);
@@ -516,6 +583,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int c0 = (e >> 2) * EC;  // first column (real) of this warp
     const bool active = c0 < BNP;
     int64_t *coloff = coloff_all + e * (EC / 2);  // this warp's copy
+    // FP16 mode: the accumulators hold 2^(sa + sb) C; undo it exactly (one
+    // factor when 2^-(sa + sb) is a normal FP32 number, else two)
+    const int us = MODE == MODE_F16 ? -(scale_exp[0] + scale_exp[1]) : 0;
+    const bool one_factor = us >= -126 && us <= 127;
+    const float u0 = one_factor ? pow2i(us) : pow2i(-scale_exp[0]);
+    const float u1 = one_factor ? 1.f : pow2i(-scale_exp[1]);
     int64_t rg = 0;
     bool ok = true;
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
@@ -552,6 +625,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok) break;
       if (!active) continue;
+      if (MODE == MODE_F16) {
+#pragma unroll
+        for (int j = 0; j < EC; j++) acc[j] = acc[j] * u0 * u1;
+      }
       if (a.scatter == 2) {
         // a warp's 32 rows x 8 complex go through its staging buffer (16-byte
         // chunk j of row r at chunk j ^ ((r >> 1) & 3), so both sides are
@@ -643,11 +720,57 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// FP16 mode: per-block maxima of |x| over A (blocks [0, pa)) and over B
+// (blocks [pa, pa + pb)), as FP32 bit patterns (ordered like the magnitudes);
+// a fixed grid, so the consumers reduce a known number of partials.
+__global__ void __launch_bounds__(512) absmax_kernel(const float4 *__restrict__ A, int64_t nA4,
+                                                     const float2 *__restrict__ B, int64_t nB2, int pa, int pb,
+                                                     uint32_t *__restrict__ out) {
+  uint32_t m = 0;
+  const bool onA = (int)blockIdx.x < pa;
+  const int blk = onA ? (int)blockIdx.x : (int)blockIdx.x - pa;
+  const int64_t stride = (int64_t)(onA ? pa : pb) * blockDim.x;
+  if (onA) {
+    for (int64_t i = blk * (int64_t)blockDim.x + threadIdx.x; i < nA4; i += stride) {
+      const float4 v = A[i];
+      m = max(m, max(max(__float_as_uint(v.x) & 0x7fffffffu, __float_as_uint(v.y) & 0x7fffffffu),
+                     max(__float_as_uint(v.z) & 0x7fffffffu, __float_as_uint(v.w) & 0x7fffffffu)));
+    }
+  } else {
+    for (int64_t i = blk * (int64_t)blockDim.x + threadIdx.x; i < nB2; i += stride) {
+      const float2 v = B[i];
+      m = max(m, max(__float_as_uint(v.x) & 0x7fffffffu, __float_as_uint(v.y) & 0x7fffffffu));
+    }
+  }
+  __shared__ uint32_t wm[16];
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint32_t v = threadIdx.x < blockDim.x / 32 ? wm[threadIdx.x] : 0u;
+    v = __reduce_max_sync(0xffffffffu, v);
+    if (threadIdx.x == 0) out[(onA ? 0 : kMaxPartials) + blk] = v;
+  }
+}
+
 // B (batch x n x k complex) -> prepared real rows, hi and lo parts:
 // row 2j = (Re b, -Im b) per k, row 2j+1 = (Im b, Re b); rows >= 2n are zero.
+// FP16 mode: scaled by 2^sb first, sb from the pb partial maxima of B.
 template <int MODE>
 __global__ void prep_b_kernel(const float2 *__restrict__ B, void *__restrict__ Bh_, void *__restrict__ Bl_,
-                              int64_t batch, int64_t N, int64_t K, int64_t sB, int NT) {
+                              int64_t batch, int64_t N, int64_t K, int64_t sB, int NT, const uint32_t *bmax, int pb) {
+  float sb = 1.f;
+  if (MODE == MODE_F16) {
+    __shared__ int s_exp;
+    if (threadIdx.x < 32) {
+      uint32_t m = 0;
+      for (int j = threadIdx.x; j < pb; j += 32) m = max(m, bmax[j]);
+      m = __reduce_max_sync(0xffffffffu, m);
+      if (threadIdx.x == 0) s_exp = f16_scale_exp(m);
+    }
+    __syncthreads();
+    sb = pow2i(s_exp);
+  }
   const int64_t total = batch * NT * K;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = i % K;
@@ -673,10 +796,14 @@ __global__ void prep_b_kernel(const float2 *__restrict__ B, void *__restrict__ B
       Bh[o + 1] = split_hi(u1);
       Bl[o] = split_lo(u0);
       Bl[o + 1] = split_lo(u1);
-    } else {
+    } else if (MODE == MODE_BF16) {
       uint16_t *Bh = static_cast<uint16_t *>(Bh_), *Bl = static_cast<uint16_t *>(Bl_);
       split_bf16(x0, Bh[o], Bl[o]);
       split_bf16(x1, Bh[o + 1], Bl[o + 1]);
+    } else {
+      uint16_t *Bh = static_cast<uint16_t *>(Bh_), *Bl = static_cast<uint16_t *>(Bl_);
+      split_f16(x0 * sb, Bh[o], Bl[o]);
+      split_f16(x1 * sb, Bh[o + 1], Bl[o + 1]);
     }
   }
 }
@@ -715,15 +842,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // 2D tensor map: rows x cols (cols contiguous), box = box_cols x box_rows,
 // zero fill outside; box rows of 128 bytes (128-byte swizzle) or 64 bytes
 // (64-byte swizzle).
-bool make_map(CUtensorMap *tm, const void *base, int64_t cols, int64_t rows, int box_cols, int box_rows, bool bf16) {
+bool make_map(CUtensorMap *tm, const void *base, int64_t cols, int64_t rows, int box_cols, int box_rows,
+              CUtensorMapDataType dt) {
   auto fn = encode_fn();
   if (!fn) return false;
-  const int esz = bf16 ? 2 : 4;
+  const int esz = dt == CU_TENSOR_MAP_DATA_TYPE_FLOAT32 ? 4 : 2;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(cols * esz)};
   cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+  CUresult r = fn(tm, dt, 2,
                   const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                   box_cols * esz == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -779,10 +907,14 @@ cudaError_t dispatch(int bnp, const CUtensorMap &ta, const CUtensorMap &tbh, con
 
 }  // namespace
 
+static bool is_tc(int precision) {
+  return precision == TZ_TF32X3 || precision == TZ_BF16X3 || precision == TZ_FP16X3;
+}
+
 bool cgemm_tc_supported(int precision, int64_t M, int64_t N, int64_t K) {
-  if (precision != TZ_TF32X3 && precision != TZ_BF16X3) return false;
+  if (!is_tc(precision)) return false;
   // M: whole 128-row tiles; K: rows of the operands a multiple of 16 bytes
-  // for TMA (2 complex in FP32, 4 complex in BF16)
+  // for TMA (2 complex in FP32, 4 complex in BF16 or FP16)
   const int64_t kmin = precision == TZ_TF32X3 ? 2 : 4;
   if (M < BM || (M % BM) != 0 || K < kmin || (K % kmin) != 0 || N < 1) return false;
   return true;
@@ -796,7 +928,7 @@ bool cgemm_tc_supported(int precision, int64_t M, int64_t N, int64_t K) {
 static int split_k(int precision, int64_t batch, int64_t M, int64_t N, int64_t K) {
   const int bnp = tile_cols(N);
   const int64_t tiles = batch * (M / BM) * ((2 * N + bnp - 1) / bnp);
-  const int sk = precision == TZ_BF16X3 ? stage_k<MODE_BF16>() : stage_k<MODE_TF32>();
+  const int sk = precision == TZ_TF32X3 ? stage_k<MODE_TF32>() : stage_k<MODE_BF16>();
   const int64_t kblocks = (2 * K + sk - 1) / sk;
   int64_t s = std::min<int64_t>({16, 152 / std::max<int64_t>(tiles, 1), kblocks / 32});
   while (s > 1 && s * batch * M * N * 8 > (int64_t(64) << 20)) s--;
@@ -804,17 +936,21 @@ static int split_k(int precision, int64_t batch, int64_t M, int64_t N, int64_t K
 }
 
 int cgemm_tc_launches(int precision, int64_t batch, int64_t M, int64_t N, int64_t K, bool scatter) {
-  return 2 + (!scatter && split_k(precision, batch, M, N, K) > 1 ? 1 : 0);
+  return 2 + (precision == TZ_FP16X3 ? 1 : 0) + (!scatter && split_k(precision, batch, M, N, K) > 1 ? 1 : 0);
 }
 
+// Scratch: prepared B hi | prepared B lo | split-K partials (when split) |
+// FP16 mode: the partial maxima (2 x kMaxPartials words).
 size_t cgemm_tc_scratch_bytes(int precision, int64_t batch, int64_t M, int64_t N, int64_t K) {
-  if (precision != TZ_TF32X3 && precision != TZ_BF16X3) return 0;
+  if (!is_tc(precision)) return 0;
   const int bnp = tile_cols(N);
   const int64_t nt = (2 * N + bnp - 1) / bnp;
   const int esz = precision == TZ_TF32X3 ? 4 : 2;
   const size_t half = ((size_t)(batch * nt * bnp * 2 * K * esz) + 255) & ~size_t(255);
   const int ks = split_k(precision, batch, M, N, K);
-  return 2 * half + (ks > 1 ? (size_t)(ks * batch * M * N * 8) : 0) + 256;
+  const size_t part = ks > 1 ? (size_t)(ks * batch * M * N * 8) : 0;
+  const size_t amax = precision == TZ_FP16X3 ? 2 * kMaxPartials * sizeof(uint32_t) : 0;
+  return 2 * half + ((part + 255) & ~size_t(255)) + amax + 256;
 }
 
 cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M,
@@ -829,26 +965,52 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
   if (rowsA >= (int64_t(1) << 31) || rowsB >= (int64_t(1) << 31) || 2 * K >= (int64_t(1) << 31))
     return cudaErrorNotSupported;
   if (scratch_bytes < cgemm_tc_scratch_bytes(precision, batch, M, N, K) || !scratch) return cudaErrorInvalidValue;
-  const bool bf16 = precision == TZ_BF16X3;
-  const size_t half = (size_t)(batch * NT * 2 * K) * (bf16 ? 2 : 4);
+  const bool tf32 = precision == TZ_TF32X3, f16 = precision == TZ_FP16X3;
+  const size_t half = (size_t)(batch * NT * 2 * K) * (tf32 ? 4 : 2);
   char *Bh = static_cast<char *>(scratch);
   char *Bl = Bh + ((half + 255) & ~size_t(255));
-  {
-    const int64_t total = batch * NT * K;
-    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
-    if (bf16)
-      prep_b_kernel<MODE_BF16><<<blocks, 256, 0, s>>>(B, Bh, Bl, batch, N, K, sB, NT);
-    else
-      prep_b_kernel<MODE_TF32><<<blocks, 256, 0, s>>>(B, Bh, Bl, batch, N, K, sB, NT);
+  // after the prepared B: room for split-K partials (sized by the shape, as
+  // in cgemm_tc_scratch_bytes), then the FP16 partial maxima
+  const int ks_shape = split_k(precision, batch, M, N, K);
+  const int ks = sc ? 1 : ks_shape;
+  char *after_b = Bl + ((half + 255) & ~size_t(255));
+  float2 *P = ks > 1 ? reinterpret_cast<float2 *>(after_b) : nullptr;
+  const size_t part_all = ks_shape > 1 ? (size_t)(ks_shape * batch * M * N * 8) : 0;
+  uint32_t *amax = reinterpret_cast<uint32_t *>(after_b + ((part_all + 255) & ~size_t(255)));
+  CUtensorMap ta, tbh, tbl;
+  const int sk = tf32 ? stage_k<MODE_TF32>() : stage_k<MODE_BF16>();
+  const CUtensorMapDataType bdt =
+      tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : (f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+  if (!make_map(&ta, A, 2 * K, rowsA, 32, BM, CU_TENSOR_MAP_DATA_TYPE_FLOAT32) ||
+      !make_map(&tbh, Bh, 2 * K, rowsB, sk, bnp, bdt) || !make_map(&tbl, Bl, 2 * K, rowsB, sk, bnp, bdt))
+    return cudaErrorInvalidValue;
+  int pa = 0, pb = 0;
+  if (f16) {
+    // A is 16-byte aligned (checked by its tensor map) and its rows hold a
+    // multiple of 8 floats; B is read as float2
+    const int64_t nA4 = batch * M * 2 * K / 4, nB2 = batch * N * K;
+    pa = (int)std::min<int64_t>(kMaxPartials, std::max<int64_t>(1, nA4 / (512 * 8)));
+    pb = (int)std::min<int64_t>(kMaxPartials, std::max<int64_t>(1, nB2 / (512 * 8)));
+    absmax_kernel<<<pa + pb, 512, 0, s>>>(reinterpret_cast<const float4 *>(A), nA4, B, nB2, pa, pb, amax);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  CUtensorMap ta, tbh, tbl;
-  const int sk = bf16 ? stage_k<MODE_BF16>() : stage_k<MODE_TF32>();
-  if (!make_map(&ta, A, 2 * K, rowsA, 32, BM, false) || !make_map(&tbh, Bh, 2 * K, rowsB, sk, bnp, bf16) ||
-      !make_map(&tbl, Bl, 2 * K, rowsB, sk, bnp, bf16))
-    return cudaErrorInvalidValue;
+  {
+    const int64_t total = batch * NT * K;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
+    if (tf32)
+      prep_b_kernel<MODE_TF32><<<blocks, 256, 0, s>>>(B, Bh, Bl, batch, N, K, sB, NT, nullptr, 0);
+    else if (f16)
+      prep_b_kernel<MODE_F16><<<blocks, 256, 0, s>>>(B, Bh, Bl, batch, N, K, sB, NT, amax + kMaxPartials, pb);
+    else
+      prep_b_kernel<MODE_BF16><<<blocks, 256, 0, s>>>(B, Bh, Bl, batch, N, K, sB, NT, nullptr, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   TcArgs args{};
+  args.amax = amax;
+  args.pa = pa;
+  args.pb = pb;
   args.C = C;
   args.batch = batch;
   args.M = M;
@@ -858,12 +1020,9 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
   args.n_tiles_m = (int)(M / BM);
   args.n_tiles_n = n_tiles_n;
   args.kblocks = (int)((2 * K + sk - 1) / sk);
-  const int ks = sc ? 1 : split_k(precision, batch, M, N, K);
   args.ksplit = ks;
   args.kb_per = (args.kblocks + ks - 1) / ks;
   args.split_stride = batch * M * N;
-  float2 *P = nullptr;  // split-K partials, after the prepared B
-  if (ks > 1) P = reinterpret_cast<float2 *>(Bl + ((half + 255) & ~size_t(255)));
   args.NT = NT;
   args.scatter = sc ? 1 : 0;
   if (sc) {
@@ -894,8 +1053,9 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
       args.tma_store = 1;
   }
-  cudaError_t e = bf16 ? dispatch<MODE_BF16>(bnp, ta, tbh, tbl, tcm, args, n_tiles, s)
-                       : dispatch<MODE_TF32>(bnp, ta, tbh, tbl, tcm, args, n_tiles, s);
+  cudaError_t e = tf32  ? dispatch<MODE_TF32>(bnp, ta, tbh, tbl, tcm, args, n_tiles, s)
+                  : f16 ? dispatch<MODE_F16>(bnp, ta, tbh, tbl, tcm, args, n_tiles, s)
+                        : dispatch<MODE_BF16>(bnp, ta, tbh, tbl, tcm, args, n_tiles, s);
   if (e != cudaSuccess || ks == 1) return e;
   const int64_t total = batch * M * N;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);

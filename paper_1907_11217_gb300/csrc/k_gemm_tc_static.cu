@@ -54,8 +54,8 @@ extern "C" int tz_op_cgemm_static(int precision, int64_t batch, int64_t m, int64
   try {
     if (!A || !B || !C) tz::fail(TZ_EINVAL, "NULL argument");
     if (batch < 1 || m < 1 || n < 1 || k < 1) tz::fail(TZ_EINVAL, "sizes must be >= 1");
-    if (precision != TZ_TF32X3 && precision != TZ_BF16X3)
-      tz::fail(TZ_EINVAL, "tz_op_cgemm_static serves the split-precision modes (TZ_TF32X3, TZ_BF16X3)");
+    if (precision != TZ_TF32X3 && precision != TZ_BF16X3 && precision != TZ_FP16X3)
+      tz::fail(TZ_EINVAL, "tz_op_cgemm_static serves the split-precision modes (TZ_TF32X3, TZ_BF16X3, TZ_FP16X3)");
     if (!tz::dev::cgemm_tc_supported(precision, m, n, k))
       tz::fail(TZ_EUNSUPPORTED, "shape not supported by the tensor-core product");
     const size_t need = tz::dev::cgemm_tc_scratch_bytes(precision, batch, m, n, k);

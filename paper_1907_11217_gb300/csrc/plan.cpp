@@ -92,7 +92,7 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
     slice_bit[e] = (int)j;
   }
   if (sliced.size() > 40) fail(TZ_EUNSUPPORTED, "more than 40 sliced indices");
-  if (o.precision < TZ_C64_SIMT || o.precision > TZ_C128_SIMT) fail(TZ_EINVAL, "unknown precision");
+  if (o.precision < TZ_C64_SIMT || o.precision > TZ_FP16X3) fail(TZ_EINVAL, "unknown precision");
 
   auto p = std::make_unique<tz_plan>();
   p->net = net;
@@ -183,7 +183,7 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
     ps.K = int64_t(1) << st.contr.size();
     ps.batch = int64_t(1) << st.batch.size();
     // skinny products are memory-bound: the streaming SIMT kernel serves them
-    ps.tc = (o.precision == TZ_TF32X3 || o.precision == TZ_BF16X3) &&
+    ps.tc = (o.precision == TZ_TF32X3 || o.precision == TZ_BF16X3 || o.precision == TZ_FP16X3) &&
             dev::cgemm_tc_supported(o.precision, ps.M, ps.N, ps.K) &&
             !(ps.N <= 4 && ps.K <= 16);
     ps.skinny = !ps.tc && ps.N <= 4 && ps.K <= 16 && ps.M >= 256;

@@ -15,7 +15,7 @@ import numpy as np
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--op", choices=["cgemm", "permute"], default="cgemm")
-    ap.add_argument("--precision", default="tf32x3", choices=["c64", "tf32x3", "bf16x3", "c128"])
+    ap.add_argument("--precision", default="tf32x3", choices=["c64", "tf32x3", "bf16x3", "fp16x3", "c128"])
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--m", type=int, default=4096)
     ap.add_argument("--n", type=int, default=256)
@@ -40,7 +40,7 @@ def main():
         B = torch.randn(a.batch * a.n * a.k * 2, device=dev, dtype=dt)
         C = torch.empty(a.batch * a.m * a.n * 2, device=dev, dtype=dt)
         scratch = None
-        if a.precision in ("tf32x3", "bf16x3"):
+        if a.precision in ("tf32x3", "bf16x3", "fp16x3"):
             nb = tz.tz_op_cgemm_scratch_bytes(a.precision, a.batch, a.m, a.n, a.k)
             scratch = torch.empty(nb // 4 + 64, device=dev, dtype=torch.float32)
         run = lambda: tz.tz_op_cgemm(a.precision, a.batch, a.m, a.n, a.k, A, a.m * a.k, B, a.n * a.k, C, a.m * a.n,

@@ -9,9 +9,10 @@ tree, 2^30 cap, captured graph on a stream):
 * slicing is exact: the partial amplitudes of the slices add up to the full
   amplitude (Sec. 1: subtask results add up to the amplitude);
 * the amplitude does not depend on the contraction tree or the slicing;
-* the FP32-class modes (complex64, split TF32, split BF16) agree with the
-  complex128 mode run on the same tree; their errors against it are printed
-  and held to 1e-5 (complex64, split TF32) and 3e-5 (split BF16) (the
+* the FP32-class modes (complex64, split TF32, split BF16, scaled split
+  FP16) agree with the complex128 mode run on the same tree; their errors
+  against it are printed and held to 1e-5 (complex64, split TF32, split FP16)
+  and 3e-5 (split BF16) (the
   complex128 mode itself is pinned to the FP64 oracle to 1e-12 wherever the
   oracle reaches);
 * Porter-Thomas (Sec. 2): E[2^n |a|^2] = 1 over random bitstrings.
@@ -92,10 +93,13 @@ def test_bristlecone70_depth32_properties(tz):
     a64 = tz.tz_contract_amplitudes(p64, bits)
     pbf, *_ = build(tz, spec, "bf16x3", 30)
     abf = tz.tz_contract_amplitudes(pbf, bits)
-    errs = {m: rel_err(x[:1], a128, 70) for m, x in (("tf32x3", a), ("c64", a64), ("bf16x3", abf))}
+    pfp, *_ = build(tz, spec, "fp16x3", 30)
+    afp = tz.tz_contract_amplitudes(pfp, bits)
+    errs = {m: rel_err(x[:1], a128, 70) for m, x in (("tf32x3", a), ("c64", a64), ("bf16x3", abf),
+                                                      ("fp16x3", afp))}
     print("bristlecone70 d32 errors vs complex128:", {m: f"{e:.2e}" for m, e in errs.items()})
     # measured on GB300: c64 3.3e-6, tf32x3 7.6e-6, bf16x3 9.0e-6
-    assert errs["c64"] <= 1e-5 and errs["tf32x3"] <= 1e-5 and errs["bf16x3"] <= 3e-5
+    assert errs["c64"] <= 1e-5 and errs["tf32x3"] <= 1e-5 and errs["bf16x3"] <= 3e-5 and errs["fp16x3"] <= 1e-5
     # another tree (other seed) with a different cap, hence other slices
     p2, _, tree2, sl2 = build(tz, spec, "c64", 29, seed=11, restarts=32)
     assert not np.array_equal(tree.pairs(), tree2.pairs())
@@ -118,7 +122,7 @@ def test_bristlecone70_depth32_porter_thomas_mean(tz):
     assert abs(npk.mean() - 1.0) < 0.75
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "c64", "bf16x3", "c128"])
+@pytest.mark.parametrize("prec", ["tf32x3", "c64", "bf16x3", "fp16x3", "c128"])
 def test_bristlecone70_reduced_depth_vs_oracle(tz, prec):
     """All 70 qubits, depth 1+12+1, sliced (k >= 3), against the oracle."""
     spec = bris_spec(12, 3)
@@ -183,16 +187,16 @@ def test_grid7x7_depth32_errors_vs_complex128(tz):
     tree = tz.tz_path_greedy(net, restarts=32, seed=7, log2_max_intermediate=22, algorithm="elimination")
     sl = tz.tz_slice_select(net, tree, 1, 10)
     out = {}
-    for prec in ("c128", "c64", "tf32x3", "bf16x3"):
+    for prec in ("c128", "c64", "tf32x3", "bf16x3", "fp16x3"):
         plan = tz.tz_plan_create(net, tree, sl, precision=prec, stream=torch.cuda.Stream(), use_graph=True,
                                  max_bitstrings=4)
         plan.bind()
         plan.set_slice_range(0, 32)
         out[prec] = tz.tz_contract_amplitudes(plan, bits)
-    errs = {m: rel_err(out[m], out["c128"], 49) for m in ("c64", "tf32x3", "bf16x3")}
+    errs = {m: rel_err(out[m], out["c128"], 49) for m in ("c64", "tf32x3", "bf16x3", "fp16x3")}
     print("grid7x7 d32 (32 slices) errors vs complex128:", {m: f"{e:.2e}" for m, e in errs.items()})
     # measured on GB300: c64 6.8e-7, tf32x3 2.2e-6, bf16x3 6.3e-6
-    assert errs["c64"] <= 1e-5 and errs["tf32x3"] <= 1e-5 and errs["bf16x3"] <= 3e-5
+    assert errs["c64"] <= 1e-5 and errs["tf32x3"] <= 1e-5 and errs["bf16x3"] <= 3e-5 and errs["fp16x3"] <= 1e-5
 
 
 def test_grid7x7_reduced_depth_batch64_vs_oracle(tz):
@@ -235,7 +239,7 @@ def test_grid7x7_depth40_precision_sweep(tz):
     sl = tz.tz_slice_select(net, tree, 24, 20)
     assert 12 <= len(sl) <= 16   # 14 with this tree
     out = {}
-    for prec in ("c128", "c64", "tf32x3", "bf16x3"):
+    for prec in ("c128", "c64", "tf32x3", "bf16x3", "fp16x3"):
         plan = tz.tz_plan_create(net, tree, sl, precision=prec, stream=torch.cuda.Stream(), use_graph=True,
                                  max_bitstrings=4)
         st = plan.stats()
@@ -243,6 +247,7 @@ def test_grid7x7_depth40_precision_sweep(tz):
         plan.bind()
         plan.set_slice_range(0, 32)
         out[prec] = tz.tz_contract_amplitudes(plan, bits)
-    errs = {m: rel_err(out[m], out["c128"], 49) for m in ("c64", "tf32x3", "bf16x3")}
+    errs = {m: rel_err(out[m], out["c128"], 49) for m in ("c64", "tf32x3", "bf16x3", "fp16x3")}
     print("grid7x7 d40 (32 of 2^14 slices) errors vs complex128:", {m: f"{e:.2e}" for m, e in errs.items()})
-    assert errs["c64"] <= 1e-5 and errs["tf32x3"] <= 3e-5 and errs["bf16x3"] <= 1e-4
+    # measured on GB300: c64 1.5e-7, tf32x3 4.9e-7, bf16x3 6.5e-7
+    assert errs["c64"] <= 1e-5 and errs["tf32x3"] <= 3e-5 and errs["bf16x3"] <= 1e-4 and errs["fp16x3"] <= 3e-5

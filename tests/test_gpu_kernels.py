@@ -105,7 +105,63 @@ def test_cgemm_bf16x3(env, batch, m, n, k):
     assert np.max(err / bound) < 2.0 ** -10   # far better than one BF16 product
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def _fp16x3(tz, torch, A, B):
+    batch, m, k = A.shape
+    n = B.shape[1]
+    dA = torch.from_numpy(A.astype(np.complex64).view(np.float32).copy()).cuda()
+    dB = torch.from_numpy(B.astype(np.complex64).view(np.float32).copy()).cuda()
+    dC = torch.zeros(batch * m * n * 2, dtype=torch.float32, device="cuda")
+    nbytes = tz.tz_op_cgemm_scratch_bytes("fp16x3", batch, m, n, k)
+    scratch = torch.empty(nbytes // 4 + 64, dtype=torch.float32, device="cuda")
+    tz.tz_op_cgemm("fp16x3", batch, m, n, k, dA, m * k, dB, n * k, dC, m * n, scratch=scratch)
+    torch.cuda.synchronize()
+    return dC.cpu().numpy().view(np.complex64).reshape(batch, m, n)
+
+
+@pytest.mark.parametrize("batch,m,n,k,ea,eb", [(1, 128, 8, 16, 0, 0), (2, 256, 64, 32, -40, -35),
+                                               (1, 1024, 128, 64, 30, -20), (3, 128, 4, 4, -60, 10),
+                                               (1, 512, 256, 128, -20, -20), (4, 384, 24, 12, 5, 5),
+                                               (1, 8192, 16, 256, -35, 0), (37, 256, 40, 8, 0, -50),
+                                               (2, 256, 24, 100, -10, 12)])
+def test_cgemm_fp16x3(env, batch, m, n, k, ea, eb):
+    """Split-FP16 product with per-tensor power-of-two scaling (the paper's
+    amplitudes, near 2^(-n/2), lie below FP16's normal range): operands
+    multiplied by 2^ea and 2^eb, far outside FP16's range for most cases, must
+    come back with 11+11 significand bits, i.e. split-TF32 accuracy."""
+    tz, torch = env
+    rng = np.random.default_rng(m + 5 * n + 11 * k + ea)
+    A = (rng.standard_normal((batch, m, k)) + 1j * rng.standard_normal((batch, m, k))) * 2.0 ** ea
+    B = (rng.standard_normal((batch, n, k)) + 1j * rng.standard_normal((batch, n, k))) * 2.0 ** eb
+    A, B = A.astype(np.complex64), B.astype(np.complex64)
+    C = _fp16x3(tz, torch, A, B)
+    ref = linalg.cgemm(A, B)
+    bound = linalg.cgemm(np.abs(A).astype(np.complex128), np.abs(B).astype(np.complex128)).real
+    err = np.abs(C - ref)
+    assert np.all(err <= (2.0 ** -18 + 4 * (k + 2) * 2.0 ** -24) * bound), float(np.max(err / bound))
+    assert np.max(err / bound) < 2.0 ** -16   # one FP16 product would leave ~2^-11
+
+
+def test_cgemm_fp16x3_zero_and_wide_range(env):
+    """A zero operand gives an exact zero product; an operand whose entries
+    span 2^-30..2^0 keeps its small entries to the error of its largest."""
+    tz, torch = env
+    rng = np.random.default_rng(7)
+    batch, m, n, k = 2, 256, 16, 64
+    A = (rng.standard_normal((batch, m, k)) + 1j * rng.standard_normal((batch, m, k))).astype(np.complex64)
+    B0 = np.zeros((batch, n, k), np.complex64)
+    assert not np.any(_fp16x3(tz, torch, A, B0))
+    B = (rng.standard_normal((batch, n, k)) + 1j * rng.standard_normal((batch, n, k)))
+    B *= 2.0 ** -rng.integers(0, 31, size=(batch, n, k))
+    B = B.astype(np.complex64)
+    C = _fp16x3(tz, torch, A, B)
+    ref = linalg.cgemm(A, B)
+    bound = linalg.cgemm(np.abs(A).astype(np.complex128), np.abs(B).astype(np.complex128)).real
+    scale = np.max(np.abs(A)) * np.max(np.abs(B)) * k
+    err = np.abs(C - ref)
+    assert np.all(err <= (2.0 ** -18 + 4 * (k + 2) * 2.0 ** -24) * bound + 2.0 ** -36 * scale)
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "fp16x3"])
 def test_cgemm_tc_many_tiles_scatter_free(env, prec):
     """More tiles than SMs, so each persistent CTA walks several tiles and
     both accumulator buffers are reused."""
@@ -122,11 +178,11 @@ def test_cgemm_tc_many_tiles_scatter_free(env, prec):
     C = dC.cpu().numpy().view(np.complex64).reshape(batch, m, n)
     ref = linalg.cgemm(A, B)
     bound = linalg.cgemm(np.abs(A).astype(np.complex128), np.abs(B).astype(np.complex128)).real
-    tol = 2.0 ** -18 if prec == "tf32x3" else 2.0 ** -14
+    tol = 2.0 ** -14 if prec == "bf16x3" else 2.0 ** -18
     assert np.all(np.abs(C - ref) <= (tol + 4 * (k + 2) * 2.0 ** -24) * bound)
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "fp16x3"])
 @pytest.mark.parametrize("batch,m,n,k", [(2, 128, 16, 4096), (64, 128, 32, 2048), (1, 256, 8, 1024)])
 def test_cgemm_tc_split_k(env, prec, batch, m, n, k):
     """Few output tiles and a long K: the product splits K across CTAs (2 to
@@ -148,12 +204,12 @@ def test_cgemm_tc_split_k(env, prec, batch, m, n, k):
     C = outs[0]
     ref = linalg.cgemm(A, B)
     bound = linalg.cgemm(np.abs(A).astype(np.complex128), np.abs(B).astype(np.complex128)).real
-    tol = 2.0 ** -18 if prec == "tf32x3" else 2.0 ** -14
+    tol = 2.0 ** -14 if prec == "bf16x3" else 2.0 ** -18
     err = np.abs(C - ref)
     assert np.all(err <= (tol + 4 * (k + 2) * 2.0 ** -24) * bound), float(np.max(err / bound))
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "fp16x3"])
 def test_cgemm_tc_accumulation_bias(env, prec):
     """The tensor cores' FP32 accumulation rounds toward zero, so a product
     summed over K real values in one accumulator comes out smaller by about

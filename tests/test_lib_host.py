@@ -121,12 +121,35 @@ def test_plan_stats_and_workspace_sizes(tz):
     c = tz.tz_circuit_generate_grid(4, 4, 10, 1)
     net = tz.tz_network_from_circuit(c, 2)
     tree = tz.tz_path_greedy(net)
-    for prec in ("c64", "tf32x3", "bf16x3"):
+    for prec in ("c64", "tf32x3", "bf16x3", "fp16x3"):
         p = tz.tz_plan_create(net, tree, [], precision=prec, max_bitstrings=64)
         st = p.stats()
         assert st["workspace_bytes"] > 0 and st["n_steps"] == net.n_tensors - 1
         assert st["flops_per_group"] > 0
         assert '"steps"' in p.describe()
+
+
+def test_fp16x3_scratch_and_launch_counts(tz):
+    """The scaled split-FP16 product needs the split-BF16 product's scratch
+    plus room for the partial maxima of |A| and |B| (2 x 304 words), and one
+    more launch per tensor-core step (the maxima pass)."""
+    import json
+    for shape in [(1, 128, 8, 16), (4, 1024, 64, 256), (2, 128, 16, 4096)]:
+        bf = tz.tz_op_cgemm_scratch_bytes("bf16x3", *shape)
+        fp = tz.tz_op_cgemm_scratch_bytes("fp16x3", *shape)
+        assert fp >= bf + 2 * 304 * 4
+    with pytest.raises(tz.TzError):
+        tz.tz_op_cgemm_scratch_bytes("fp16x3", 1, 128, 8, 6)   # K not a multiple of 4
+    c = tz.tz_circuit_generate_grid(5, 6, 20, 7)
+    net = tz.tz_network_from_circuit(c, 6)
+    tree = tz.tz_path_greedy(net, restarts=4, seed=3, precision="bf16x3")
+    st = {}
+    for prec in ("bf16x3", "fp16x3"):
+        p = tz.tz_plan_create(net, tree, [], precision=prec, small_log2=8, max_bitstrings=64)
+        n_tc = sum(1 for x in json.loads(p.describe())["steps"] if x.get("tc"))
+        st[prec] = (p.stats()["n_launches_per_group"], n_tc)
+    assert st["fp16x3"][1] == st["bf16x3"][1] > 0
+    assert st["fp16x3"][0] == st["bf16x3"][0] + st["fp16x3"][1]
 
 
 def test_bind_rejects_bad_workspace(tz):

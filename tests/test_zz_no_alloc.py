@@ -18,7 +18,7 @@ def _c64(torch, rng, shape):
     return torch.from_numpy(x.view(np.float32).copy()).cuda()
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "fp16x3"])
 def test_static_scratch_matches_caller_scratch(prec):
     import torch
     import paper_1907_11217_gb300 as tz
