@@ -1,9 +1,10 @@
 // Split-precision complex products on the tcgen05 tensor cores (sm_103a).
 // Three modes share the pipeline: TF32x3 (operands split into TF32 hi + lo,
 // kind::tf32), BF16x3 (operands split into BF16 hi + lo, kind::f16 with BF16
-// inputs) and FP16x3 (operands scaled by a power of two per tensor, then split
-// into FP16 hi + lo, kind::f16 with FP16 inputs). All accumulate in FP32 in
-// TMEM.
+// inputs) and FP16x3 (operands scaled by powers of two into FP16's range, then
+// split into FP16 hi + lo, kind::f16 with FP16 inputs: B by one exponent per
+// tensor, A by one per row and k-block, chosen on chip). All accumulate in
+// FP32 in TMEM.
 //
 // C[z] = A[z] B[z]^T in complex64, computed as one real product on the
 // interleaved (re, im) view: A is read as an m x 2k FP32 matrix and C is
@@ -175,6 +176,12 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
       "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
       : "memory");
 }
+// 8 columns (same layout as tmem_st16)
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // 16 columns of this warp's 32 TMEM lanes; the wait is in the same asm
@@ -208,7 +215,8 @@ __device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t &hi, u
 
 // FP16 counterpart of split_bf16x2 (x0, x1 already scaled into FP16 range):
 // hi = f16(x) and lo = f16(x - hi), both rounded to nearest even; x - hi is
-// exact in FP32.
+// exact in FP32. (Computing hi by Veltkamp's splitting in FP32 arithmetic
+// instead of converting it back from FP16 measured slower.)
 __device__ __forceinline__ void split_f16x2(float x0, float x1, uint32_t &hi, uint32_t &lo) {
   asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(x1), "f"(x0));
   float h0, h1;
@@ -264,8 +272,8 @@ __host__ __device__ constexpr uint32_t idesc_f16(int n_cols) {
 
 enum TcMode { MODE_TF32 = 0, MODE_BF16 = 1, MODE_F16 = 2 };
 
-// FP16 mode: the largest |x| of A and of B, as per-block partial maxima
-// (FP32 bit patterns of |x|): A's at [0, pa), B's at [kMaxPartials, + pb).
+// FP16 mode: the largest |x| of B, as per-block partial maxima (FP32 bit
+// patterns of |x|), at most kMaxPartials of them.
 constexpr int kMaxPartials = 304;  // two blocks per SM of GB300
 
 struct TcArgs {
@@ -280,8 +288,8 @@ struct TcArgs {
   int tma_store;       // 1: row-major C written by bulk tensor stores (tmC)
   int ksplit, kb_per;  // K split into ksplit ranges of kb_per k-blocks; with
   int64_t split_stride;  // ksplit > 1, range s writes row-major partials at C + s * split_stride
-  const uint32_t *amax;  // FP16 mode: partial maxima of A and B (kMaxPartials apart)
-  int pa, pb;            // their counts
+  const uint32_t *bmax;  // FP16 mode: pb partial maxima of |B|
+  int pb;
   CScatter sc;
 };
 
@@ -298,6 +306,10 @@ __device__ __forceinline__ int64_t scatter_bits(int64_t v, int n, const int8_t *
 // whatever the total K. The epilogue warps add the ranges in FP32 registers
 // (round to nearest), which bounds that bias at about 6e-9 kFoldK per product.
 constexpr int kFoldK = 128;
+// FP16 mode: one accumulation range per k-block (64 real K), because each
+// k-block of a row of A carries its own scale exponent.
+template <int MODE>
+__host__ __device__ constexpr int fold_k() { return MODE == MODE_F16 ? 64 : kFoldK; }
 
 // Per stage (shared memory): the FP32 A tile as loaded (128 rows in boxes of
 // 128-byte rows: one TF32, two BF16) and the prepared B hi and lo tiles (BNP
@@ -306,6 +318,9 @@ constexpr int kFoldK = 128;
 // hi, then lo) in the top columns, below it a ring of NBUF accumulators of
 // BNP columns (at least 32): the products of one range go to the next
 // accumulator of the ring while the epilogue drains the previous ones.
+// FP16 mode: a ring of XR x 128 scale exponents of A (one per row and
+// k-block), written by the split warps and read by the epilogue, each ring
+// entry with its own barrier.
 template <int MODE, int BNP, int STAGES>
 struct TcSmem {
   static constexpr uint32_t A_BYTES = BM * stage_k<MODE>() * 4;         // FP32 tile as loaded (boxes of 128-byte rows)
@@ -317,7 +332,10 @@ struct TcSmem {
   static constexpr uint32_t BARS = 512;                                // barriers and flags
   static constexpr uint32_t STAGING = 8 * 2048;                        // epilogue: 8 warps x (32 rows x 64 B)
   static constexpr uint32_t COLOFF = 8 * (EC / 2) * 8;                 // epilogue: 8 warps x column offsets
-  static constexpr uint32_t TOTAL = STAGES * STAGE + STAGING + BARS + COLOFF + 1024;  // + alignment
+  static constexpr int XR = MODE == MODE_F16 ? 16 : 0;                 // FP16: ring of A exponents
+  static constexpr uint32_t XEXP = XR * BM;                            // one int8 per row and entry
+  static constexpr int XRI = XR > 0 ? XR : 1;                          // ring size for indexing
+  static constexpr uint32_t TOTAL = STAGES * STAGE + STAGING + BARS + COLOFF + XEXP + 1024;  // + alignment
   static constexpr uint32_t ACC_COLS = BNP < 32 ? 32 : BNP;
   static constexpr uint32_t TMEM_COLS = 512;
   static constexpr int ASLOTS = 4;
@@ -325,7 +343,12 @@ struct TcSmem {
   static constexpr int NBUF = A_COL0 / ACC_COLS;
   static_assert(BNP <= 128, "an epilogue thread holds half a row of the tile in registers");
   // barriers, then the TMEM address, the abort flag and two scale exponents
-  static_assert((3 * STAGES + 2 * NBUF + ASLOTS + 1) * 8 + 16 <= BARS, "barriers and flags fit in BARS");
+  static_assert((3 * STAGES + 2 * NBUF + ASLOTS + 1 + XR) * 8 + 16 <= BARS, "barriers and flags fit in BARS");
+  // the split warps run at most ASLOTS k-blocks ahead of the products, which
+  // run at most NBUF ranges ahead of the epilogue: a split warp never reaches
+  // an exponent entry, or its barrier's next phase, that the epilogue has yet
+  // to read
+  static_assert(XR == 0 || XR >= ASLOTS + NBUF + 1, "exponent ring deep enough");
 };
 
 // Persistent: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
@@ -346,10 +369,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t *tempty = tfull + L::NBUF;   // [NBUF] accumulator drained by the epilogue
   uint64_t *drain = tempty + L::NBUF;   // all products retired
   uint64_t *aempty = drain + 1;         // [ASLOTS] TMEM A slot read by its products
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(aempty + L::ASLOTS);
+  uint64_t *xfull = aempty + L::ASLOTS;  // [XR] FP16: exponent ring entry written
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(xfull + L::XR);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-  int *scale_exp = reinterpret_cast<int *>(tmem_slot + 2);  // FP16 mode: exponents of A and B
+  int *scale_exp = reinterpret_cast<int *>(tmem_slot + 2);  // FP16 mode: [1] = exponent of B
   int64_t *coloff_all = reinterpret_cast<int64_t *>(smem + STAGES * L::STAGE + L::STAGING + L::BARS);
+  int8_t *aexp = reinterpret_cast<int8_t *>(smem + STAGES * L::STAGE + L::STAGING + L::BARS + L::COLOFF);
   uint8_t *staging = smem + STAGES * L::STAGE;  // 1024-aligned
   auto A_raw = [&](int s) { return smem + s * L::STAGE; };
   auto B_hi = [&](int s) { return smem + s * L::STAGE + L::A_BYTES; };
@@ -389,6 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     mbar_init(drain, 1);
     for (int b = 0; b < L::ASLOTS; b++) mbar_init(&aempty[b], 1);
+    for (int b = 0; b < L::XR; b++) mbar_init(&xfull[b], 128);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -398,16 +424,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (MODE == MODE_F16 && warp == 2) {
-    // reduce the partial maxima written by absmax_kernel earlier on the stream
-    uint32_t ma = 0, mb = 0;
-    for (int j = lane; j < a.pa; j += 32) ma = max(ma, a.amax[j]);
-    for (int j = lane; j < a.pb; j += 32) mb = max(mb, a.amax[kMaxPartials + j]);
-    ma = __reduce_max_sync(0xffffffffu, ma);
+    // B's exponent: reduce the partial maxima written by absmax_kernel
+    // earlier on the stream
+    uint32_t mb = 0;
+    for (int j = lane; j < a.pb; j += 32) mb = max(mb, a.bmax[j]);
     mb = __reduce_max_sync(0xffffffffu, mb);
-    if (lane == 0) {
-      scale_exp[0] = f16_scale_exp(ma);
-      scale_exp[1] = f16_scale_exp(mb);
-    }
+    if (lane == 0) scale_exp[1] = f16_scale_exp(mb);
   }
   tc_fence_before();
   __syncthreads();
@@ -450,7 +472,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // K per instruction: 8 TF32 or 16 BF16 values (32 bytes of a B row,
       // 8 TMEM columns of A)
       constexpr int kSteps = stage_k<MODE>() / (MODE == MODE_TF32 ? 8 : 16);
-      constexpr int kFoldKb = kFoldK / stage_k<MODE>();  // k-blocks per accumulation range
+      constexpr int kFoldKb = fold_k<MODE>() / stage_k<MODE>();  // k-blocks per accumulation range
       int64_t g = 0, rg = 0;  // k-blocks and accumulation ranges issued
       bool ok = true;
       for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
@@ -507,7 +529,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;
     const int row = q * 32 + lane;
     const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16) + L::A_COL0;
-    const float sa = MODE == MODE_F16 ? pow2i(scale_exp[0]) : 1.f;
     int64_t g = 0;
     bool ok = true;
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
@@ -543,9 +564,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             tmem_st16(ts + (uint32_t)(16 * h), hi);
             tmem_st16(ts + (uint32_t)(32 + 16 * h), lo);
           }
-        } else {
-          // two boxes (K 0..31, 32..63); BF16 or FP16 pairs packed with the
-          // lower k in the low half: hi in columns 0..31, lo in 32..63
+        } else if (MODE == MODE_BF16) {
+          // two boxes (K 0..31, 32..63); BF16 pairs packed with the lower k
+          // in the low half: hi in columns 0..31, lo in 32..63
 #pragma unroll
           for (int h = 0; h < 2; h++) {
             const uint4 *src = reinterpret_cast<const uint4 *>(A_raw(s) + h * BM * 128 + row * 128);
@@ -553,21 +574,48 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int c = 0; c < 8; c++) {
               const uint4 v = src[c ^ (row & 7)];
-              if (MODE == MODE_BF16) {
-                split_bf16x2(__uint_as_float(v.x), __uint_as_float(v.y), hi[2 * c], lo[2 * c]);
-                split_bf16x2(__uint_as_float(v.z), __uint_as_float(v.w), hi[2 * c + 1], lo[2 * c + 1]);
-              } else {
-                split_f16x2(__uint_as_float(v.x) * sa, __uint_as_float(v.y) * sa, hi[2 * c], lo[2 * c]);
-                split_f16x2(__uint_as_float(v.z) * sa, __uint_as_float(v.w) * sa, hi[2 * c + 1], lo[2 * c + 1]);
-              }
+              split_bf16x2(__uint_as_float(v.x), __uint_as_float(v.y), hi[2 * c], lo[2 * c]);
+              split_bf16x2(__uint_as_float(v.z), __uint_as_float(v.w), hi[2 * c + 1], lo[2 * c + 1]);
             }
             tmem_st16(ts + (uint32_t)(16 * h), hi);
             tmem_st16(ts + (uint32_t)(32 + 16 * h), lo);
           }
+        } else {
+          // FP16: the row's 64 values of this k-block set its exponent (the
+          // largest magnitude scaled into [2^14, 2^15)); then as for BF16,
+          // with FP16 pairs
+          uint4 v[16];
+#pragma unroll
+          for (int c = 0; c < 16; c++)
+            v[c] = reinterpret_cast<const uint4 *>(A_raw(s) + (c >> 3) * BM * 128 + row * 128)[(c & 7) ^ (row & 7)];
+          // (FP32 max of magnitudes, one instruction a value; a NaN is
+          // skipped here and still propagates through the products)
+          float m = 0.f;
+#pragma unroll
+          for (int c = 0; c < 16; c++)
+            m = fmaxf(fmaxf(m, fmaxf(fabsf(__uint_as_float(v[c].x)), fabsf(__uint_as_float(v[c].y)))),
+                      fmaxf(fabsf(__uint_as_float(v[c].z)), fabsf(__uint_as_float(v[c].w))));
+          const int se = f16_scale_exp(__float_as_uint(m));
+          const float sa = pow2i(se);
+          // 8 columns at a time, so the raw values die as they are split
+#pragma unroll
+          for (int h = 0; h < 4; h++) {
+            uint32_t hi[8], lo[8];
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+              const uint4 w = v[4 * h + c];
+              split_f16x2(__uint_as_float(w.x) * sa, __uint_as_float(w.y) * sa, hi[2 * c], lo[2 * c]);
+              split_f16x2(__uint_as_float(w.z) * sa, __uint_as_float(w.w) * sa, hi[2 * c + 1], lo[2 * c + 1]);
+            }
+            tmem_st8(ts + (uint32_t)(8 * h), hi);
+            tmem_st8(ts + (uint32_t)(32 + 8 * h), lo);
+          }
+          aexp[(int)(g % L::XRI) * BM + row] = (int8_t)se;
         }
         tmem_st_wait();
         tc_fence_before();
         mbar_arrive(&conv[s]);
+        if (MODE == MODE_F16) mbar_arrive(&xfull[g % L::XRI]);  // releases the exponent written above
       }
     }
   } else {
@@ -575,7 +623,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // warps 6..9 take the first EC columns of the tile, warps 10..13 the
     // rest (none when the tile is narrower than 32 columns); each thread
     // sums its part of a row over the accumulation ranges in registers
-    constexpr int kFoldKb = kFoldK / stage_k<MODE>();
+    constexpr int kFoldKb = fold_k<MODE>() / stage_k<MODE>();
     constexpr int EC = L::EC;
     const int e = warp - 6;
     const int q = warp & 3;
@@ -583,12 +631,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int c0 = (e >> 2) * EC;  // first column (real) of this warp
     const bool active = c0 < BNP;
     int64_t *coloff = coloff_all + e * (EC / 2);  // this warp's copy
-    // FP16 mode: the accumulators hold 2^(sa + sb) C; undo it exactly (one
-    // factor when 2^-(sa + sb) is a normal FP32 number, else two)
-    const int us = MODE == MODE_F16 ? -(scale_exp[0] + scale_exp[1]) : 0;
-    const bool one_factor = us >= -126 && us <= 127;
-    const float u0 = one_factor ? pow2i(us) : pow2i(-scale_exp[0]);
-    const float u1 = one_factor ? 1.f : pow2i(-scale_exp[1]);
+    // FP16 mode: the range of k-block g holds 2^(sa(row, g) + sb) times its
+    // part of C; each range is added times 2^-sa(row, g) and the sum times
+    // 2^-sb at the end (both exact: the exponents are clamped to +-110)
+    const float ub = MODE == MODE_F16 ? pow2i(-scale_exp[1]) : 1.f;
     int64_t rg = 0;
     bool ok = true;
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
@@ -612,12 +658,27 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         const uint32_t taddr = tmem + (uint32_t)(buf * L::ACC_COLS + c0) + ((uint32_t)(q * 32) << 16);
         if (active) {
+          float ua = 1.f;
+          if (MODE == MODE_F16) {
+            // the split warps released this entry before the products of the
+            // range were issued, so the wait does not block in practice
+            if (!mbar_wait(&xfull[rg % L::XRI], (uint32_t)((rg / L::XRI) & 1), abort_flag)) {
+              ok = false;
+              break;
+            }
+            ua = pow2i(-(int)aexp[(int)(rg % L::XRI) * BM + row]);
+          }
 #pragma unroll
           for (int c = 0; c < EC; c += 16) {
             uint32_t r[16];
             tmem_ld16(taddr + (uint32_t)c, r);
 #pragma unroll
-            for (int j = 0; j < 16; j++) acc[c + j] += __uint_as_float(r[j]);
+            for (int j = 0; j < 16; j++) {
+              if (MODE == MODE_F16)
+                acc[c + j] = fmaf(__uint_as_float(r[j]), ua, acc[c + j]);
+              else
+                acc[c + j] += __uint_as_float(r[j]);
+            }
           }
         }
         tc_fence_before();
@@ -627,7 +688,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!active) continue;
       if (MODE == MODE_F16) {
 #pragma unroll
-        for (int j = 0; j < EC; j++) acc[j] = acc[j] * u0 * u1;
+        for (int j = 0; j < EC; j++) acc[j] *= ub;
       }
       if (a.scatter == 2) {
         // a warp's 32 rows x 8 complex go through its staging buffer (16-byte
@@ -720,27 +781,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// FP16 mode: per-block maxima of |x| over A (blocks [0, pa)) and over B
-// (blocks [pa, pa + pb)), as FP32 bit patterns (ordered like the magnitudes);
-// a fixed grid, so the consumers reduce a known number of partials.
-__global__ void __launch_bounds__(512) absmax_kernel(const float4 *__restrict__ A, int64_t nA4,
-                                                     const float2 *__restrict__ B, int64_t nB2, int pa, int pb,
+// FP16 mode: per-block maxima of |x| over B (n2 float2 values), as FP32 bit
+// patterns (ordered like the magnitudes); a fixed grid, so the consumers
+// reduce a known number of partials. (A needs no such pass: its exponents
+// are chosen per row and k-block on chip.)
+__global__ void __launch_bounds__(512) absmax_kernel(const float2 *__restrict__ B, int64_t n2,
                                                      uint32_t *__restrict__ out) {
   uint32_t m = 0;
-  const bool onA = (int)blockIdx.x < pa;
-  const int blk = onA ? (int)blockIdx.x : (int)blockIdx.x - pa;
-  const int64_t stride = (int64_t)(onA ? pa : pb) * blockDim.x;
-  if (onA) {
-    for (int64_t i = blk * (int64_t)blockDim.x + threadIdx.x; i < nA4; i += stride) {
-      const float4 v = A[i];
-      m = max(m, max(max(__float_as_uint(v.x) & 0x7fffffffu, __float_as_uint(v.y) & 0x7fffffffu),
-                     max(__float_as_uint(v.z) & 0x7fffffffu, __float_as_uint(v.w) & 0x7fffffffu)));
-    }
-  } else {
-    for (int64_t i = blk * (int64_t)blockDim.x + threadIdx.x; i < nB2; i += stride) {
-      const float2 v = B[i];
-      m = max(m, max(__float_as_uint(v.x) & 0x7fffffffu, __float_as_uint(v.y) & 0x7fffffffu));
-    }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = B[i];
+    m = max(m, max(__float_as_uint(v.x) & 0x7fffffffu, __float_as_uint(v.y) & 0x7fffffffu));
   }
   __shared__ uint32_t wm[16];
   m = __reduce_max_sync(0xffffffffu, m);
@@ -749,7 +799,7 @@ __global__ void __launch_bounds__(512) absmax_kernel(const float4 *__restrict__ 
   if (threadIdx.x < 32) {
     uint32_t v = threadIdx.x < blockDim.x / 32 ? wm[threadIdx.x] : 0u;
     v = __reduce_max_sync(0xffffffffu, v);
-    if (threadIdx.x == 0) out[(onA ? 0 : kMaxPartials) + blk] = v;
+    if (threadIdx.x == 0) out[blockIdx.x] = v;
   }
 }
 
@@ -940,7 +990,7 @@ int cgemm_tc_launches(int precision, int64_t batch, int64_t M, int64_t N, int64_
 }
 
 // Scratch: prepared B hi | prepared B lo | split-K partials (when split) |
-// FP16 mode: the partial maxima (2 x kMaxPartials words).
+// FP16 mode: the partial maxima of |B| (kMaxPartials words).
 size_t cgemm_tc_scratch_bytes(int precision, int64_t batch, int64_t M, int64_t N, int64_t K) {
   if (!is_tc(precision)) return 0;
   const int bnp = tile_cols(N);
@@ -949,8 +999,8 @@ size_t cgemm_tc_scratch_bytes(int precision, int64_t batch, int64_t M, int64_t N
   const size_t half = ((size_t)(batch * nt * bnp * 2 * K * esz) + 255) & ~size_t(255);
   const int ks = split_k(precision, batch, M, N, K);
   const size_t part = ks > 1 ? (size_t)(ks * batch * M * N * 8) : 0;
-  const size_t amax = precision == TZ_FP16X3 ? 2 * kMaxPartials * sizeof(uint32_t) : 0;
-  return 2 * half + ((part + 255) & ~size_t(255)) + amax + 256;
+  const size_t bmax = precision == TZ_FP16X3 ? kMaxPartials * sizeof(uint32_t) : 0;
+  return 2 * half + ((part + 255) & ~size_t(255)) + bmax + 256;
 }
 
 cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M,
@@ -976,7 +1026,7 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
   char *after_b = Bl + ((half + 255) & ~size_t(255));
   float2 *P = ks > 1 ? reinterpret_cast<float2 *>(after_b) : nullptr;
   const size_t part_all = ks_shape > 1 ? (size_t)(ks_shape * batch * M * N * 8) : 0;
-  uint32_t *amax = reinterpret_cast<uint32_t *>(after_b + ((part_all + 255) & ~size_t(255)));
+  uint32_t *bmax = reinterpret_cast<uint32_t *>(after_b + ((part_all + 255) & ~size_t(255)));
   CUtensorMap ta, tbh, tbl;
   const int sk = tf32 ? stage_k<MODE_TF32>() : stage_k<MODE_BF16>();
   const CUtensorMapDataType bdt =
@@ -984,14 +1034,11 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
   if (!make_map(&ta, A, 2 * K, rowsA, 32, BM, CU_TENSOR_MAP_DATA_TYPE_FLOAT32) ||
       !make_map(&tbh, Bh, 2 * K, rowsB, sk, bnp, bdt) || !make_map(&tbl, Bl, 2 * K, rowsB, sk, bnp, bdt))
     return cudaErrorInvalidValue;
-  int pa = 0, pb = 0;
+  int pb = 0;
   if (f16) {
-    // A is 16-byte aligned (checked by its tensor map) and its rows hold a
-    // multiple of 8 floats; B is read as float2
-    const int64_t nA4 = batch * M * 2 * K / 4, nB2 = batch * N * K;
-    pa = (int)std::min<int64_t>(kMaxPartials, std::max<int64_t>(1, nA4 / (512 * 8)));
+    const int64_t nB2 = batch * N * K;
     pb = (int)std::min<int64_t>(kMaxPartials, std::max<int64_t>(1, nB2 / (512 * 8)));
-    absmax_kernel<<<pa + pb, 512, 0, s>>>(reinterpret_cast<const float4 *>(A), nA4, B, nB2, pa, pb, amax);
+    absmax_kernel<<<pb, 512, 0, s>>>(B, nB2, bmax);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1001,15 +1048,14 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
     if (tf32)
       prep_b_kernel<MODE_TF32><<<blocks, 256, 0, s>>>(B, Bh, Bl, batch, N, K, sB, NT, nullptr, 0);
     else if (f16)
-      prep_b_kernel<MODE_F16><<<blocks, 256, 0, s>>>(B, Bh, Bl, batch, N, K, sB, NT, amax + kMaxPartials, pb);
+      prep_b_kernel<MODE_F16><<<blocks, 256, 0, s>>>(B, Bh, Bl, batch, N, K, sB, NT, bmax, pb);
     else
       prep_b_kernel<MODE_BF16><<<blocks, 256, 0, s>>>(B, Bh, Bl, batch, N, K, sB, NT, nullptr, 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   TcArgs args{};
-  args.amax = amax;
-  args.pa = pa;
+  args.bmax = bmax;
   args.pb = pb;
   args.C = C;
   args.batch = batch;
