@@ -69,12 +69,21 @@ def make_circuit_spec(w):
     return ti.circuit_to_spec(lat.n_qubits, ti.generate_circuit(lat, t, seed)), lat.n_qubits
 
 
+_TREES = {}
+
+
 def build_plan(tz, spec, args, precision, stream, device, log2_max):
     circ = tz.tz_circuit_from_spec(spec)
     net = tz.tz_network_from_circuit(circ, args.batch_log2)
     t0 = time.perf_counter()
-    tree = tz.tz_path_greedy(net, restarts=args.restarts, seed=args.tree_seed, log2_max_intermediate=log2_max,
-                             precision=precision, algorithm=args.algorithm)
+    # the time model that scores trees tells the CUDA-core modes from the
+    # tensor-core ones only, so the three tensor-core modes share one search
+    key = (spec, precision if precision in ("c64", "c128") else "tensor-core", log2_max)
+    if key not in _TREES:
+        _TREES[key] = tz.tz_path_greedy(net, restarts=args.restarts, seed=args.tree_seed,
+                                        log2_max_intermediate=log2_max, precision=precision,
+                                        algorithm=args.algorithm).pairs()
+    tree = tz.tz_tree_from_pairs(net, _TREES[key])
     sliced = tz.tz_slice_select(net, tree, log2_max, 40) if log2_max > 0 else []
     plan = tz.tz_plan_create(net, tree, sliced, precision=precision, device=device, stream=stream, use_graph=True,
                              max_bitstrings=1 << max(args.batch_log2, 0))
@@ -152,7 +161,7 @@ def measured_peaks():
 # traffic grows with its flops for this kernel (row tiles re-read B), so the
 # per-launch traffic of a step is scaled from it. Must be re-captured whenever
 # the kernel changes.
-TC_DRAM_BYTES_PER_FLOP = {"tf32x3": 1.474e9 / 2.749e11, "bf16x3": 0.4164e9 / 2.749e11}
+TC_DRAM_BYTES_PER_FLOP = {"tf32x3": 1.474e9 / 2.749e11, "bf16x3": 0.4164e9 / 2.749e11, "fp16x3": 0.4627e9 / 2.749e11}
 
 
 def plan_roofline(plan, precision, ms_per_group):

@@ -130,7 +130,10 @@ void tz_network_destroy(tz_network *net);
  *                       (merge every holder of the index, then sum it out);
  * TZ_PATH_AUTO alternates them. Each restart is scored by the estimated
  * GB300 time of the plan after slicing to log2_max_intermediate, and the
- * best tree is kept.
+ * best tree is kept (the earliest restart among equal scores). Restarts run
+ * on host threads: one per hardware thread (at most 64), or the number in
+ * the environment variable TZ_PATH_THREADS; the tree returned does not depend
+ * on the thread count.
  * Trees are lists of SSA pairs: leaves are ids 0..T-1, the i-th pair
  * creates id T+i. A complete tree has T-1 pairs.
  */

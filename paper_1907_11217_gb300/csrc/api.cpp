@@ -1,8 +1,14 @@
 // C ABI entry points (include/tz.h): argument checks, error codes, handles.
+#include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <exception>
 #include <memory>
+#include <mutex>
 #include <new>
+#include <thread>
 
 #include "plan.h"
 
@@ -152,27 +158,40 @@ int tz_path_greedy(const tz_network *net, const tz_path_opts *opts, tz_tree **ou
   if (opts) o = *opts;
   if (o.restarts < 1) o.restarts = 1;
   tz::CostModel cm = cost_model(o.precision);
-  uint64_t rng = o.seed ^ 0x5DEECE66DULL;
-  tz::Pairs best;
-  double best_score = 0;
-  int best_bits = 0;
   REQUIRE(o.algorithm >= TZ_PATH_AUTO && o.algorithm <= TZ_PATH_ELIMINATION, "unknown path algorithm");
+  // Every trial's parameters are drawn first, in trial order, from one
+  // stream; the trials then run on host threads, and the earliest trial with
+  // the lowest score wins. The result does not depend on the thread count.
+  struct Trial {
+    int algo;
+    double alpha, temp;
+    uint64_t seed;
+    tz::Pairs pairs;
+    double score;
+  };
+  std::vector<Trial> trials(o.restarts);
+  uint64_t rng = o.seed ^ 0x5DEECE66DULL;
   for (int trial = 0; trial < o.restarts; trial++) {
-    int algo = o.algorithm;
+    Trial &tr = trials[trial];
+    tr.algo = o.algorithm;
     int nth = trial;  // trial number within its algorithm
-    if (algo == TZ_PATH_AUTO) {
-      algo = (trial % 2 == 0) ? TZ_PATH_ELIMINATION : TZ_PATH_GREEDY;
+    if (tr.algo == TZ_PATH_AUTO) {
+      tr.algo = (trial % 2 == 0) ? TZ_PATH_ELIMINATION : TZ_PATH_GREEDY;
       nth = trial / 2;
     }
-    double alpha = 1.0, temp = 0.0;
+    tr.alpha = 1.0;
+    tr.temp = 0.0;
     const double u1 = (tz::splitmix64_next(rng) >> 11) * (1.0 / 9007199254740992.0);
     const double u2 = (tz::splitmix64_next(rng) >> 11) * (1.0 / 9007199254740992.0);
     if (nth > 0) {
-      alpha = 0.5 + 1.0 * u1;
-      temp = 0.05 + 1.0 * u2;
+      tr.alpha = 0.5 + 1.0 * u1;
+      tr.temp = 0.05 + 1.0 * u2;
     }
-    tz::Pairs pr = algo == TZ_PATH_GREEDY ? tz::greedy_tree(net->n, alpha, temp, tz::splitmix64_next(rng))
-                                          : tz::elimination_tree(net->n, temp, tz::splitmix64_next(rng));
+    tr.seed = tz::splitmix64_next(rng);
+  }
+  auto run_trial = [&](Trial &tr) {
+    tz::Pairs pr = tr.algo == TZ_PATH_GREEDY ? tz::greedy_tree(net->n, tr.alpha, tr.temp, tr.seed)
+                                             : tz::elimination_tree(net->n, tr.temp, tr.seed);
     if (o.log2_max_intermediate > 0) {
       // local three-way rotations under the slicing this tree would get
       std::vector<int> sl = tz::select_slices(net->n, pr, o.log2_max_intermediate, 40, cm);
@@ -181,16 +200,42 @@ int tz_path_greedy(const tz_network *net, const tz_path_opts *opts, tz_tree **ou
       pr = tz::rotate_tree(net->n, pr, flag, cm, 16);
     }
     int mb = 0;
-    double sc = tree_score(net->n, pr, o.log2_max_intermediate, cm, &mb);
-    if (trial == 0 || sc < best_score) {
-      best = pr;
-      best_score = sc;
-      best_bits = mb;
-    }
+    tr.score = tree_score(net->n, pr, o.log2_max_intermediate, cm, &mb);
+    tr.pairs = std::move(pr);
+  };
+  // host threads: TZ_PATH_THREADS if set (>= 1), else one per hardware thread (at most 64)
+  unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  if (const char *env = std::getenv("TZ_PATH_THREADS")) {
+    const long v = std::strtol(env, nullptr, 10);
+    if (v >= 1) hw = (unsigned)std::min<long>(v, 1024);
   }
-  (void)best_bits;
+  const int n_threads = (int)std::min<unsigned>({(unsigned)o.restarts, hw, 64u});
+  if (n_threads <= 1) {
+    for (Trial &tr : trials) run_trial(tr);
+  } else {
+    std::atomic<int> next{0};
+    std::exception_ptr err;
+    std::mutex err_mu;
+    std::vector<std::thread> pool;
+    for (int w = 0; w < n_threads; w++)
+      pool.emplace_back([&] {
+        for (int i; (i = next.fetch_add(1)) < o.restarts;) {
+          try {
+            run_trial(trials[i]);
+          } catch (...) {
+            std::lock_guard<std::mutex> lk(err_mu);
+            if (!err) err = std::current_exception();
+          }
+        }
+      });
+    for (auto &th : pool) th.join();
+    if (err) std::rethrow_exception(err);
+  }
+  int best = 0;
+  for (int i = 1; i < o.restarts; i++)
+    if (trials[i].score < trials[best].score) best = i;
   auto t = std::make_unique<tz_tree>();
-  t->pairs = best;
+  t->pairs = std::move(trials[best].pairs);
   *out = t.release();
   TZ_CATCH
 }

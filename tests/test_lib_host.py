@@ -183,3 +183,19 @@ def test_degree_one_qubits_cost_like_70(tz, depth, seed):
                                  precision="bf16x3")
         flops[n] = tz.tz_plan_create(net, tree, [], precision="bf16x3").stats()["flops_per_group"]
     assert abs(math.log2(flops[72]) - math.log2(flops[70])) <= 1.0, flops
+
+
+def test_path_search_independent_of_thread_count(tz, monkeypatch):
+    """Restarts run on host threads; the tree returned, and so every plan
+    built on it, must not depend on how many (TZ_PATH_THREADS)."""
+    c = tz.tz_circuit_generate_grid(5, 5, 16, 3)
+    net = tz.tz_network_from_circuit(c, 0)
+    trees = []
+    for th in ("1", "3", "8"):
+        monkeypatch.setenv("TZ_PATH_THREADS", th)
+        for alg in ("auto", "elimination"):
+            t = tz.tz_path_greedy(net, restarts=24, seed=5, log2_max_intermediate=12, algorithm=alg)
+            trees.append((th, alg, t.pairs().tobytes()))
+    for alg in ("auto", "elimination"):
+        got = {th: p for th, a, p in trees if a == alg}
+        assert got["1"] == got["3"] == got["8"]
