@@ -52,7 +52,10 @@ def parse():
     ap.add_argument("--batch-log2", type=int, default=0)
     ap.add_argument("--slices", type=int, default=0, help="slices per step (0: auto)")
     ap.add_argument("--log2-max", type=int, default=0, help="slicing target (0: workload default)")
-    ap.add_argument("--restarts", type=int, default=256)
+    ap.add_argument("--restarts", type=int, default=16384,
+                    help="tree search restarts (untimed preprocessing, run on all host threads)")
+    ap.add_argument("--tree-file", default="",
+                    help="load the tensor-core modes' tree from this .npy if it exists, else save it there")
     ap.add_argument("--algorithm", default="elimination", choices=["auto", "greedy", "elimination"])
     ap.add_argument("--tree-seed", type=int, default=7)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -78,11 +81,17 @@ def build_plan(tz, spec, args, precision, stream, device, log2_max):
     t0 = time.perf_counter()
     # the time model that scores trees tells the CUDA-core modes from the
     # tensor-core ones only, so the three tensor-core modes share one search
-    key = (spec, precision if precision in ("c64", "c128") else "tensor-core", log2_max)
+    tc_mode = precision not in ("c64", "c128")
+    key = (spec, precision if not tc_mode else "tensor-core", log2_max)
+    cache = args.tree_file if tc_mode else ""
+    if key not in _TREES and cache and os.path.exists(cache):
+        _TREES[key] = np.load(cache)
     if key not in _TREES:
         _TREES[key] = tz.tz_path_greedy(net, restarts=args.restarts, seed=args.tree_seed,
                                         log2_max_intermediate=log2_max, precision=precision,
                                         algorithm=args.algorithm).pairs()
+        if cache:
+            np.save(cache, _TREES[key])
     tree = tz.tz_tree_from_pairs(net, _TREES[key])
     sliced = tz.tz_slice_select(net, tree, log2_max, 40) if log2_max > 0 else []
     plan = tz.tz_plan_create(net, tree, sliced, precision=precision, device=device, stream=stream, use_graph=True,
