@@ -111,6 +111,36 @@ def test_bristlecone70_depth32_properties(tz):
     assert np.all(npk > 1e-6) and np.all(npk < 40)
 
 
+def test_bristlecone70_depth32_bench_tree(tz):
+    """The exact tree bench.py times (16384 restarts, seed 7, 2^30 cap,
+    elimination, split-BF16 time model): every FP32-class mode against the
+    complex128 mode on that tree and slicing, and the tree's cost."""
+    spec = bris_spec(32, 3)
+    bits = ti.random_bitstrings(70, 1, 103)
+    # the tree search scores with the tensor-core time model, as bench.py does
+    plan, net, tree, sl = build(tz, spec, "bf16x3", 30, restarts=16384)
+    out, stats = {}, {}
+    for prec in ("bf16x3", "c128", "fp16x3", "tf32x3", "c64"):
+        if prec != "bf16x3":
+            plan = _plan_on(tz, net, tree, sl, prec)
+        stats[prec] = plan.stats()
+        out[prec] = tz.tz_contract_amplitudes(plan, bits)
+        plan.close()
+    # the tree bench.py times: about 2.7e12 useful flops, no slicing
+    assert stats["bf16x3"]["flops_per_group"] * 2.0 ** stats["bf16x3"]["k"] < 4e12
+    errs = {m: rel_err(out[m], out["c128"], 70) for m in ("bf16x3", "fp16x3", "tf32x3", "c64")}
+    print("bristlecone70 d32 bench tree, errors vs complex128:", {m: f"{e:.2e}" for m, e in errs.items()})
+    assert errs["c64"] <= 1e-5 and errs["tf32x3"] <= 1e-5 and errs["fp16x3"] <= 1e-5 and errs["bf16x3"] <= 3e-5
+
+
+def _plan_on(tz, net, tree, sliced, precision):
+    import torch
+    plan = tz.tz_plan_create(net, tree, sliced, precision=precision, stream=torch.cuda.Stream(), use_graph=True,
+                             max_bitstrings=64)
+    plan.bind()
+    return plan
+
+
 def test_bristlecone70_depth32_porter_thomas_mean(tz):
     """Sec. 2: N p follows exp(-x); the mean over 32 random bitstrings is
     1 +- 0.18 (one standard deviation)."""
