@@ -283,8 +283,8 @@ struct TcArgs {
   int64_t sC;          // complex elements between batches of C
   int n_tiles_m, n_tiles_n, kblocks;
   int NT;              // rows of the prepared B per batch
-  int scatter;         // 1: write C through sc; 2: likewise, the three lowest
-                       // bits of C being n bits 0..2 (stores staged per warp)
+  int scatter;         // 1: write C through sc; 2: likewise, the lowest bit of
+                       // C being n bit 0 (stores of column pairs, staged per warp)
   int tma_store;       // 1: row-major C written by bulk tensor stores (tmC)
   int ksplit, kb_per;  // K split into ksplit ranges of kb_per k-blocks; with
   int64_t split_stride;  // ksplit > 1, range s writes row-major partials at C + s * split_stride
@@ -694,7 +694,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         // a warp's 32 rows x 8 complex go through its staging buffer (16-byte
         // chunk j of row r at chunk j ^ ((r >> 1) & 3), so both sides are
         // free of bank conflicts); then each store instruction writes 8 rows
-        // x 64 contiguous bytes (lane: row 8 u + lane / 4, pair lane % 4)
+        // x 4 column pairs (lane: row 8 u + lane / 4, pair lane % 4). A pair
+        // is 16 contiguous bytes because n bit 0 is the lowest bit of C; when
+        // n bits 1 and 2 follow it, a row's 4 pairs are 64 contiguous bytes.
         const int64_t om = scatter_bits(d.z, a.sc.nb, a.sc.pb) + scatter_bits((int64_t)d.mt * BM + row, a.sc.nm, a.sc.pm);
         int64_t om_u[4];
 #pragma unroll
@@ -709,7 +711,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               *reinterpret_cast<float4 *>(buf + lane * 64 + ((j ^ ((lane >> 1) & 3)) << 4)) =
                   make_float4(acc[c + 4 * j], acc[c + 4 * j + 1], acc[c + 4 * j + 2], acc[c + 4 * j + 3]);
             __syncwarp();
-            const int64_t col = coloff[c / 2] + 2 * (lane & 3);
+            const int64_t col = coloff[c / 2 + 2 * (lane & 3)];
 #pragma unroll
             for (int u = 0; u < 4; u++) {
               const int rr = 8 * u + (lane >> 2);
@@ -854,6 +856,75 @@ __global__ void prep_b_kernel(const float2 *__restrict__ B, void *__restrict__ B
       uint16_t *Bh = static_cast<uint16_t *>(Bh_), *Bl = static_cast<uint16_t *>(Bl_);
       split_f16(x0 * sb, Bh[o], Bl[o]);
       split_f16(x1 * sb, Bh[o + 1], Bl[o + 1]);
+    }
+  }
+}
+
+// The same preparation, vectorised (B 16-byte aligned, K even): a thread
+// takes one column j of B and two consecutive k, reads them with one 16-byte
+// load and writes both prepared rows, 2j and 2j + 1, with 8-byte (BF16, FP16)
+// or 16-byte (TF32) stores of hi and of lo.
+template <int MODE>
+__global__ void prep_b_vec_kernel(const float4 *__restrict__ B, void *__restrict__ Bh_, void *__restrict__ Bl_,
+                                  int64_t batch, int64_t N, int64_t K, int64_t sB, int NT, const uint32_t *bmax,
+                                  int pb) {
+  float sb = 1.f;
+  if (MODE == MODE_F16) {
+    __shared__ int s_exp;
+    if (threadIdx.x < 32) {
+      uint32_t m = 0;
+      for (int j = threadIdx.x; j < pb; j += 32) m = max(m, bmax[j]);
+      m = __reduce_max_sync(0xffffffffu, m);
+      if (threadIdx.x == 0) s_exp = f16_scale_exp(m);
+    }
+    __syncthreads();
+    sb = pow2i(s_exp);
+  }
+  const int64_t K2 = K / 2, J = NT / 2;
+  const int64_t total = batch * J * K2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t kp = i % K2;
+    const int64_t j = (i / K2) % J;
+    const int64_t z = i / (K2 * J);
+    float4 b = make_float4(0.f, 0.f, 0.f, 0.f);  // (Re, Im) at k = 2 kp and 2 kp + 1
+    if (j < N) b = B[(z * sB + j * K) / 2 + kp];
+    const float r0[4] = {b.x, -b.y, b.z, -b.w};  // row 2j
+    const float r1[4] = {b.y, b.x, b.w, b.z};    // row 2j + 1
+    const int64_t o0 = (z * NT + 2 * j) * 2 * K + 4 * kp, o1 = o0 + 2 * K;
+    if (MODE == MODE_TF32) {
+      uint32_t *Bh = static_cast<uint32_t *>(Bh_), *Bl = static_cast<uint32_t *>(Bl_);
+      uint32_t h0[4], l0[4], h1[4], l1[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        h0[q] = split_hi(__float_as_uint(r0[q]));
+        l0[q] = split_lo(__float_as_uint(r0[q]));
+        h1[q] = split_hi(__float_as_uint(r1[q]));
+        l1[q] = split_lo(__float_as_uint(r1[q]));
+      }
+      *reinterpret_cast<uint4 *>(Bh + o0) = make_uint4(h0[0], h0[1], h0[2], h0[3]);
+      *reinterpret_cast<uint4 *>(Bl + o0) = make_uint4(l0[0], l0[1], l0[2], l0[3]);
+      *reinterpret_cast<uint4 *>(Bh + o1) = make_uint4(h1[0], h1[1], h1[2], h1[3]);
+      *reinterpret_cast<uint4 *>(Bl + o1) = make_uint4(l1[0], l1[1], l1[2], l1[3]);
+    } else {
+      uint16_t *Bh = static_cast<uint16_t *>(Bh_), *Bl = static_cast<uint16_t *>(Bl_);
+      uint16_t h[8], l[8];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        if (MODE == MODE_BF16) {
+          split_bf16(r0[q], h[q], l[q]);
+          split_bf16(r1[q], h[4 + q], l[4 + q]);
+        } else {
+          split_f16(r0[q] * sb, h[q], l[q]);
+          split_f16(r1[q] * sb, h[4 + q], l[4 + q]);
+        }
+      }
+      auto pack = [](const uint16_t *v) {
+        return make_uint2((uint32_t)v[0] | ((uint32_t)v[1] << 16), (uint32_t)v[2] | ((uint32_t)v[3] << 16));
+      };
+      *reinterpret_cast<uint2 *>(Bh + o0) = pack(h);
+      *reinterpret_cast<uint2 *>(Bl + o0) = pack(l);
+      *reinterpret_cast<uint2 *>(Bh + o1) = pack(h + 4);
+      *reinterpret_cast<uint2 *>(Bl + o1) = pack(l + 4);
     }
   }
 }
@@ -1042,7 +1113,18 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  {
+  if ((reinterpret_cast<uintptr_t>(B) & 15) == 0 && (K % 2) == 0) {
+    // NT is even (whole tiles of at least 16 rows)
+    const int64_t total = batch * (NT / 2) * (K / 2);
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
+    const float4 *B4 = reinterpret_cast<const float4 *>(B);
+    if (tf32)
+      prep_b_vec_kernel<MODE_TF32><<<blocks, 256, 0, s>>>(B4, Bh, Bl, batch, N, K, sB, NT, nullptr, 0);
+    else if (f16)
+      prep_b_vec_kernel<MODE_F16><<<blocks, 256, 0, s>>>(B4, Bh, Bl, batch, N, K, sB, NT, bmax, pb);
+    else
+      prep_b_vec_kernel<MODE_BF16><<<blocks, 256, 0, s>>>(B4, Bh, Bl, batch, N, K, sB, NT, nullptr, 0);
+  } else {
     const int64_t total = batch * NT * K;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
     if (tf32)
@@ -1051,6 +1133,8 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
       prep_b_kernel<MODE_F16><<<blocks, 256, 0, s>>>(B, Bh, Bl, batch, N, K, sB, NT, bmax, pb);
     else
       prep_b_kernel<MODE_BF16><<<blocks, 256, 0, s>>>(B, Bh, Bl, batch, N, K, sB, NT, nullptr, 0);
+  }
+  {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1073,10 +1157,9 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
   args.scatter = sc ? 1 : 0;
   if (sc) {
     args.sc = *sc;
-    // n bits 0..2 lowest in C, C 16-byte aligned: whole 64-byte runs per row
-    if (sc->nn >= 3 && sc->pn[0] == 0 && sc->pn[1] == 1 && sc->pn[2] == 2 &&
-        (reinterpret_cast<uintptr_t>(C) & 15) == 0)
-      args.scatter = 2;
+    // n bit 0 lowest in C (N a multiple of 8), C 16-byte aligned: stores of
+    // 16-byte column pairs, instead of single columns at 32 different rows
+    if (sc->nn >= 3 && sc->pn[0] == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0) args.scatter = 2;
   }
   const int64_t n_tiles = batch * args.n_tiles_m * (int64_t)n_tiles_n * ks;
   // row-major C with 16-byte aligned rows: bulk tensor stores of 32-row x
