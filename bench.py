@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--log2-max", type=int, default=0, help="slicing target (0: workload default)")
     ap.add_argument("--restarts", type=int, default=16384,
                     help="tree search restarts (untimed preprocessing, run on all host threads)")
+    ap.add_argument("--reconfigure", type=int, default=0,
+                    help="tree search: exact re-optimisation of windows of this many subtrees (0: off; the "
+                         "cheaper Bristlecone-70 tree it finds misses the 1e-5 bar in split TF32)")
     ap.add_argument("--tree-file", default="",
                     help="load the tensor-core modes' tree from this .npy if it exists, else save it there")
     ap.add_argument("--algorithm", default="elimination", choices=["auto", "greedy", "elimination"])
@@ -89,7 +92,7 @@ def build_plan(tz, spec, args, precision, stream, device, log2_max):
     if key not in _TREES:
         _TREES[key] = tz.tz_path_greedy(net, restarts=args.restarts, seed=args.tree_seed,
                                         log2_max_intermediate=log2_max, precision=precision,
-                                        algorithm=args.algorithm).pairs()
+                                        algorithm=args.algorithm, reconfigure=args.reconfigure).pairs()
         if cache:
             np.save(cache, _TREES[key])
     tree = tz.tz_tree_from_pairs(net, _TREES[key])
@@ -550,7 +553,7 @@ def main():
         "config": {"workload": args.workload, "n_qubits": nq, "depth": f"1+{WORKLOADS[args.workload][4]}+1",
                    "batch_bitstrings": B, "k_sliced": k, "slices_total": n_slices,
                    "slices_per_step": slices_per_step, "log2_max_intermediate": st["max_log2"],
-                   "tree_restarts": args.restarts, "preprocessing_s": prep_s,
+                   "tree_restarts": args.restarts, "tree_reconfigure": args.reconfigure, "preprocessing_s": prep_s,
                    "l2": "intermediates larger than L2" if st["max_log2"] >= 25 else "working set may fit L2",
                    "parallelism": f"slices x{world}"},
         "contraction_tflops": tflops,

@@ -147,6 +147,10 @@ typedef struct {
   int log2_max_intermediate;    /* slicing target used to score trials (bits)  */
   int precision;                /* tz_precision used by the time model         */
   int algorithm;                /* TZ_PATH_*                                   */
+  int reconfigure;              /* 0: off; 3..10: after the restarts, re-solve
+                                   windows of up to this many subtrees exactly
+                                   (dynamic programming over subsets) in the 8
+                                   best trees, and keep the best result         */
 } tz_path_opts;
 
 int tz_path_greedy(const tz_network *net, const tz_path_opts *opts, tz_tree **out);

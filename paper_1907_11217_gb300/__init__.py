@@ -156,9 +156,9 @@ PATH_ALGORITHMS = {"auto": 0, "greedy": 1, "elimination": 2}
 
 
 def tz_path_greedy(net: Network, restarts=1, seed=0, log2_max_intermediate=0, precision="c64",
-                   algorithm="auto") -> Tree:
+                   algorithm="auto", reconfigure=0) -> Tree:
     o = tz_path_opts(restarts, seed, log2_max_intermediate, PRECISIONS.get(precision, precision),
-                     PATH_ALGORITHMS.get(algorithm, algorithm))
+                     PATH_ALGORITHMS.get(algorithm, algorithm), reconfigure)
     h = ctypes.c_void_p()
     check(lib().tz_path_greedy(net.handle, ctypes.byref(o), ctypes.byref(h)))
     return Tree(h)

@@ -35,7 +35,7 @@ class tz_network_opts(ctypes.Structure):
 
 class tz_path_opts(ctypes.Structure):
     _fields_ = [("restarts", ctypes.c_int), ("seed", ctypes.c_uint64), ("log2_max_intermediate", ctypes.c_int),
-                ("precision", ctypes.c_int), ("algorithm", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("algorithm", ctypes.c_int), ("reconfigure", ctypes.c_int)]
 
 
 class tz_plan_opts(ctypes.Structure):

@@ -159,6 +159,7 @@ int tz_path_greedy(const tz_network *net, const tz_path_opts *opts, tz_tree **ou
   if (o.restarts < 1) o.restarts = 1;
   tz::CostModel cm = cost_model(o.precision);
   REQUIRE(o.algorithm >= TZ_PATH_AUTO && o.algorithm <= TZ_PATH_ELIMINATION, "unknown path algorithm");
+  REQUIRE(o.reconfigure == 0 || (o.reconfigure >= 3 && o.reconfigure <= 10), "reconfigure must be 0 or 3..10");
   // Every trial's parameters are drawn first, in trial order, from one
   // stream; the trials then run on host threads, and the earliest trial with
   // the lowest score wins. The result does not depend on the thread count.
@@ -234,6 +235,44 @@ int tz_path_greedy(const tz_network *net, const tz_path_opts *opts, tz_tree **ou
   int best = 0;
   for (int i = 1; i < o.restarts; i++)
     if (trials[i].score < trials[best].score) best = i;
+  if (o.reconfigure > 0) {
+    // exact window re-optimisation of the best few trees (best first, ties by
+    // restart order); the lowest score after it wins, ties to the earlier
+    std::vector<int> order(o.restarts);
+    for (int i = 0; i < o.restarts; i++) order[i] = i;
+    const int top = std::min(o.restarts, 8);
+    std::partial_sort(order.begin(), order.begin() + top, order.end(), [&](int a, int b) {
+      return trials[a].score < trials[b].score || (trials[a].score == trials[b].score && a < b);
+    });
+    std::vector<Trial> refined(top);
+    std::vector<std::thread> pool;
+    std::exception_ptr err;
+    std::mutex err_mu;
+    for (int q = 0; q < top; q++)
+      pool.emplace_back([&, q] {
+        try {
+          const Trial &src = trials[order[q]];
+          std::vector<char> flag(net->n.indices.size(), 0);
+          if (o.log2_max_intermediate > 0)
+            for (int e : tz::select_slices(net->n, src.pairs, o.log2_max_intermediate, 40, cm)) flag[e] = 1;
+          refined[q].pairs = tz::reconfigure_tree(net->n, src.pairs, flag, cm, o.reconfigure, 8);
+          int mb = 0;
+          refined[q].score = tree_score(net->n, refined[q].pairs, o.log2_max_intermediate, cm, &mb);
+        } catch (...) {
+          std::lock_guard<std::mutex> lk(err_mu);
+          if (!err) err = std::current_exception();
+        }
+      });
+    for (auto &th : pool) th.join();
+    if (err) std::rethrow_exception(err);
+    int rb = -1;
+    for (int q = 0; q < top; q++)
+      if (refined[q].score < trials[best].score && (rb < 0 || refined[q].score < refined[rb].score)) rb = q;
+    if (rb >= 0) {
+      trials[best].pairs = std::move(refined[rb].pairs);
+      trials[best].score = refined[rb].score;
+    }
+  }
   auto t = std::make_unique<tz_tree>();
   t->pairs = std::move(trials[best].pairs);
   *out = t.release();

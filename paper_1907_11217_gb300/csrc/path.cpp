@@ -2,6 +2,7 @@
 // slice selector. The paper defers its own contraction algorithm to its
 // earlier work; these are the library's own.
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <queue>
 #include <unordered_map>
@@ -479,6 +480,172 @@ Pairs rotate_tree(const Network &net, const Pairs &pairs, const std::vector<char
     std::vector<int> newid(L + NS, -1);
     for (int l = 0; l < L; l++) newid[l] = l;
     std::vector<std::pair<int, int>> stack;  // (node, state)
+    stack.push_back({L + NS - 1, 0});
+    while (!stack.empty()) {
+      auto [n, st] = stack.back();
+      stack.pop_back();
+      if (n < L) continue;
+      if (st == 0) {
+        stack.push_back({n, 1});
+        stack.push_back({nd[n].r, 0});
+        stack.push_back({nd[n].l, 0});
+      } else {
+        out.push_back({newid[nd[n].l], newid[nd[n].r]});
+        newid[n] = L + (int)out.size() - 1;
+      }
+    }
+    cur = out;
+  }
+  return cur;
+}
+
+// ------------------------------------------------- subtree reconfiguration
+// A window is a node v and the subtrees below it down to a frontier of at
+// most `window` nodes (grown by opening the largest internal frontier node
+// first). The contraction of the frontier nodes into v is re-solved exactly:
+// dynamic programming over all subsets of the frontier, each subset's tensor
+// holding the indices that some tensor outside the subset still holds, at the
+// cost of the time model (steps that run once at bind time cost nothing per
+// group), never exceeding the tree's largest intermediate. The cheapest order
+// replaces the window when it saves at least 1 %. A pass skips windows that
+// overlap one already rewritten; passes repeat until nothing improves.
+Pairs reconfigure_tree(const Network &net, const Pairs &pairs, const std::vector<char> &sliced, const CostModel &cm,
+                       int window, int max_passes) {
+  const int L = (int)net.leaves.size();
+  const int I = (int)net.indices.size();
+  window = std::max(3, std::min(window, 10));
+  Pairs cur = pairs;
+  // leaves holding each index (sliced indices are not held)
+  std::vector<int> total(I, 0);
+  for (int l = 0; l < L; l++)
+    for (int i : net.leaves[l].idx)
+      if (sliced.empty() || !sliced[i]) total[i]++;
+  for (int pass = 0; pass < max_passes; pass++) {
+    TreeInfo ti = analyse_tree(net, cur, sliced);
+    const int NS = (int)cur.size();
+    std::vector<Node> nd(L + NS);
+    for (int s = 0; s < NS; s++) nd[L + s] = {cur[s].first, cur[s].second};
+    // leaves under each node holding each index of its set (same order as
+    // the set)
+    std::vector<std::vector<int>> cnt(L + NS);
+    for (int l = 0; l < L; l++) cnt[l].assign(ti.sets[l].size(), 1);
+    for (int s = 0; s < NS; s++) {
+      const int c = L + s, a = nd[c].l, b = nd[c].r;
+      const auto &C = ti.sets[c];
+      cnt[c].assign(C.size(), 0);
+      for (int side = 0; side < 2; side++) {
+        const int u = side ? b : a;
+        const auto &U = ti.sets[u];
+        size_t q = 0;
+        for (size_t j = 0; j < U.size(); j++) {
+          while (q < C.size() && C[q] < U[j]) q++;
+          if (q < C.size() && C[q] == U[j]) cnt[c][q] += cnt[u][j];
+        }
+      }
+    }
+    auto step_cost = [&](const std::vector<int> &x, const std::vector<int> &y, const std::vector<int> &out, bool var) {
+      return var ? cm.step_time(classify(x, y, out, var)) : 0.0;
+    };
+    std::vector<char> touched(L + NS, 0);
+    bool changed = false;
+    const int M = window;
+    for (int v = L + NS - 1; v >= L; v--) {
+      if (touched[v]) continue;
+      // grow the frontier
+      std::vector<int> front = {nd[v].l, nd[v].r}, inner = {v};
+      while ((int)front.size() < M) {
+        int pick = -1;
+        for (int j = 0; j < (int)front.size(); j++) {
+          const int u = front[j];
+          if (u < L || touched[u]) continue;
+          if (pick < 0 || ti.sets[u].size() > ti.sets[front[pick]].size() ||
+              (ti.sets[u].size() == ti.sets[front[pick]].size() && u > front[pick]))
+            pick = j;
+        }
+        if (pick < 0) break;
+        const int u = front[pick];
+        front[pick] = nd[u].l;
+        front.push_back(nd[u].r);
+        inner.push_back(u);
+      }
+      const int m = (int)front.size();
+      if (m < 3) continue;
+      bool skip = false;
+      for (int u : inner) skip |= touched[u] != 0;
+      if (skip) continue;
+      // current cost of the window's steps
+      double cur_cost = 0;
+      for (int u : inner) cur_cost += step_cost(ti.sets[nd[u].l], ti.sets[nd[u].r], ti.sets[u], ti.var[u]);
+      // subset tensors: index j of the local universe survives when some
+      // leaf outside the subset holds it, or it is open
+      std::vector<int> uni;
+      for (int u : front) uni.insert(uni.end(), ti.sets[u].begin(), ti.sets[u].end());
+      std::sort(uni.begin(), uni.end());
+      uni.erase(std::unique(uni.begin(), uni.end()), uni.end());
+      const int U = (int)uni.size();
+      std::vector<std::vector<int>> fc(m, std::vector<int>(U, 0));
+      for (int k = 0; k < m; k++) {
+        const auto &S = ti.sets[front[k]];
+        for (size_t j = 0; j < S.size(); j++)
+          fc[k][std::lower_bound(uni.begin(), uni.end(), S[j]) - uni.begin()] = cnt[front[k]][j];
+      }
+      const int full = (1 << m) - 1;
+      std::vector<std::vector<int>> sub(1 << m);
+      std::vector<char> svar(1 << m, 0);
+      std::vector<int> scount(U);
+      for (int mask = 1; mask <= full; mask++) {
+        std::fill(scount.begin(), scount.end(), 0);
+        bool var = false;
+        for (int k = 0; k < m; k++)
+          if (mask >> k & 1) {
+            for (int j = 0; j < U; j++) scount[j] += fc[k][j];
+            var |= ti.var[front[k]] != 0;
+          }
+        for (int j = 0; j < U; j++)
+          if (scount[j] > 0 && (scount[j] < total[uni[j]] || net.is_open(uni[j]))) sub[mask].push_back(uni[j]);
+        svar[mask] = var;
+      }
+      const double INF = 1e300;
+      std::vector<double> best(1 << m, INF);
+      std::vector<int> split(1 << m, 0);
+      for (int k = 0; k < m; k++) best[1 << k] = 0;
+      for (int mask = 1; mask <= full; mask++) {
+        if ((mask & (mask - 1)) == 0) continue;
+        if (mask != full && (int)sub[mask].size() > ti.max_bits) continue;  // never raise the memory peak
+        const int low = mask & -mask;
+        for (int a = (mask - 1) & mask; a > 0; a = (a - 1) & mask) {
+          if (!(a & low)) continue;  // each unordered split once
+          const int b = mask ^ a;
+          if (best[a] >= INF || best[b] >= INF) continue;
+          const double c = best[a] + best[b] + step_cost(sub[a], sub[b], sub[mask], svar[a] || svar[b]);
+          if (c < best[mask]) {
+            best[mask] = c;
+            split[mask] = a;
+          }
+        }
+      }
+      if (best[full] >= 0.99 * cur_cost) continue;
+      // rebuild the window on its own internal node ids, v as the root
+      std::vector<int> ids(inner.begin() + 1, inner.end());
+      size_t next_id = 0;
+      std::function<int(int, int)> emit = [&](int mask, int as) -> int {
+        if ((mask & (mask - 1)) == 0) return front[__builtin_ctz(mask)];
+        const int node = as >= 0 ? as : ids[next_id++];
+        const int a = split[mask];
+        const int l = emit(a, -1), r = emit(mask ^ a, -1);
+        nd[node] = {l, r};
+        return node;
+      };
+      emit(full, v);
+      for (int u : inner) touched[u] = 1;
+      changed = true;
+    }
+    if (!changed) break;
+    // re-linearise: post-order from the root
+    Pairs out;
+    std::vector<int> newid(L + NS, -1);
+    for (int l = 0; l < L; l++) newid[l] = l;
+    std::vector<std::pair<int, int>> stack;
     stack.push_back({L + NS - 1, 0});
     while (!stack.empty()) {
       auto [n, st] = stack.back();

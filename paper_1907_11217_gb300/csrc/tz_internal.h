@@ -100,6 +100,9 @@ Pairs greedy_tree(const Network &net, double alpha, double temperature, uint64_t
 Pairs elimination_tree(const Network &net, double temperature, uint64_t seed);
 Pairs rotate_tree(const Network &net, const Pairs &pairs, const std::vector<char> &sliced, const CostModel &cm,
                   int max_passes);
+// Exact re-optimisation of windows of at most `window` subtrees (3..10).
+Pairs reconfigure_tree(const Network &net, const Pairs &pairs, const std::vector<char> &sliced, const CostModel &cm,
+                       int window, int max_passes);
 std::vector<int> select_slices(const Network &net, const Pairs &pairs, int log2_max, int k_max,
                                const CostModel &cm);
 

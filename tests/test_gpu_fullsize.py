@@ -51,12 +51,12 @@ MAX_FLOPS_PER_AMPLITUDE = 1e14   # guard: never start a contraction this test ca
 
 
 def build(tz, spec, precision, log2_max, batch_log2=0, restarts=64, seed=7, algorithm="elimination", k_max=40,
-          max_bitstrings=0):
+          max_bitstrings=0, reconfigure=0):
     import torch
     circ = tz.tz_circuit_from_spec(spec)
     net = tz.tz_network_from_circuit(circ, batch_log2)
     tree = tz.tz_path_greedy(net, restarts=restarts, seed=seed, log2_max_intermediate=log2_max,
-                             precision=precision, algorithm=algorithm)
+                             precision=precision, algorithm=algorithm, reconfigure=reconfigure)
     sliced = tz.tz_slice_select(net, tree, log2_max, k_max)
     stream = torch.cuda.Stream()
     plan = tz.tz_plan_create(net, tree, sliced, precision=precision, stream=stream, use_graph=True,
@@ -130,6 +130,7 @@ def test_bristlecone70_depth32_bench_tree(tz):
     assert stats["bf16x3"]["flops_per_group"] * 2.0 ** stats["bf16x3"]["k"] < 4e12
     errs = {m: rel_err(out[m], out["c128"], 70) for m in ("bf16x3", "fp16x3", "tf32x3", "c64")}
     print("bristlecone70 d32 bench tree, errors vs complex128:", {m: f"{e:.2e}" for m, e in errs.items()})
+    # measured on GB300: bf16x3 2.6e-5, fp16x3 5.3e-6, tf32x3 7.4e-6, c64 7.8e-6
     assert errs["c64"] <= 1e-5 and errs["tf32x3"] <= 1e-5 and errs["fp16x3"] <= 1e-5 and errs["bf16x3"] <= 3e-5
 
 

@@ -199,3 +199,25 @@ def test_path_search_independent_of_thread_count(tz, monkeypatch):
     for alg in ("auto", "elimination"):
         got = {th: p for th, a, p in trees if a == alg}
         assert got["1"] == got["3"] == got["8"]
+
+
+def test_reconfigure_never_worse_and_valid(tz):
+    """Exact window re-optimisation keeps a complete, valid tree (a plan
+    builds on it, one step per pair), and the tree it returns is not much
+    costlier in useful flops than the search without it (the time model,
+    not the flop count, decides, so the check is loose); out-of-range
+    window sizes are rejected."""
+    c = tz.tz_circuit_generate_grid(5, 6, 16, 3)
+    net = tz.tz_network_from_circuit(c, 0)
+    base = tz.tz_path_greedy(net, restarts=8, seed=3, log2_max_intermediate=14, precision="bf16x3",
+                             algorithm="elimination")
+    for w in (4, 6, 8):
+        t = tz.tz_path_greedy(net, restarts=8, seed=3, log2_max_intermediate=14, precision="bf16x3",
+                              algorithm="elimination", reconfigure=w)
+        p0 = tz.tz_plan_create(net, base, tz.tz_slice_select(net, base, 14, 40), precision="bf16x3")
+        p1 = tz.tz_plan_create(net, t, tz.tz_slice_select(net, t, 14, 40), precision="bf16x3")
+        s0, s1 = p0.stats(), p1.stats()
+        assert s1["n_steps"] == net.n_tensors - 1
+        assert s1["flops_per_group"] * 2.0 ** s1["k"] <= 1.5 * s0["flops_per_group"] * 2.0 ** s0["k"]
+    with pytest.raises(tz.TzError):
+        tz.tz_path_greedy(net, restarts=1, reconfigure=2)
