@@ -168,12 +168,12 @@ def measured_peaks():
 
 
 # DRAM bytes (read + write) per useful flop of the tensor-core product, from
-# one ncu capture of the dominant Bristlecone-70 shape (M 16384, N 1024,
-# K 2048, batch 1; profiles/tc_split3_*_m16384_n1024_k2048.md). A launch's
-# traffic grows with its flops for this kernel (row tiles re-read B), so the
-# per-launch traffic of a step is scaled from it. Must be re-captured whenever
-# the kernel changes.
-TC_DRAM_BYTES_PER_FLOP = {"tf32x3": 1.474e9 / 2.749e11, "bf16x3": 0.4164e9 / 2.749e11, "fp16x3": 0.4627e9 / 2.749e11}
+# one ncu capture of a shape (M 16384, N 1024, K 2048, batch 1;
+# profiles/tc_split3_*_m16384_n1024_k2048.md) per mode, scaled to a launch by
+# its flops (row tiles re-read B, so traffic grows with flops). Only modes
+# whose kernel is unchanged since their capture are listed: the product's
+# epilogue has changed since all three captures, so none is (traffic: null).
+TC_DRAM_BYTES_PER_FLOP = {}
 
 
 def plan_roofline(plan, precision, ms_per_group):
@@ -232,6 +232,9 @@ def roofline(prof, precision):
             out["traffic"] = TC_DRAM_BYTES_PER_FLOP[precision] * d["flops"] / d["launches"]
             out["traffic_note"] = ("bytes per launch, scaled by flops from an ncu capture of the dominant shape "
                                    "at batch 1")
+        else:
+            out["traffic_note"] = ("null: the product kernel changed after its last ncu capture (DRAM 0.99x to "
+                                   "1.1x the algorithmic bytes then; profiles/tc_split3_*)")
     elif dom == "gemm_simt":
         out.update(bound="alu", unit="TFLOP/s", achieved=d["flops"] / sec / 1e12, peak=fp32_alu_tflops,
                    peak_source="152 SMs x 128 FP32 lanes x 2 flops x max SM clock")
