@@ -36,8 +36,11 @@ WORKLOADS = {
     "grid7x7_d32": ("grid", 7, 7, 49, 32, 2, 24, 102),
     "grid7x7_d40": ("grid", 7, 7, 49, 40, 5, 24, 105),
     "grid4x4_d10": ("grid", 4, 4, 16, 10, 1, 0, 101),
+    "bristlecone70_d36": ("bristlecone", 0, 0, 70, 36, 3, 30, 103),
+    "bristlecone70_d40": ("bristlecone", 0, 0, 70, 40, 3, 30, 103),
 }
-PAPER_S_PER_AMP = {"bristlecone70_d32": 0.43}  # Table 2 (1449 x 88 vCPU), context only
+# Table 2 (1449 x 88 vCPU), context only
+PAPER_S_PER_AMP = {"bristlecone70_d32": 0.43, "bristlecone70_d36": 5.6, "bristlecone70_d40": 580.7}
 
 
 def parse():

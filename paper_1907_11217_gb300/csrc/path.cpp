@@ -107,10 +107,13 @@ TreeInfo analyse_tree(const Network &net, const Pairs &pairs, const std::vector<
 double CostModel::step_time(const StepInfo &s) const {
   const int all = s.bitsAll();
   const double macs = std::ldexp(1.0, all);
-  const double bytes = 8.0 * (std::ldexp(1.0, s.bitsA()) + std::ldexp(1.0, s.bitsB()) + std::ldexp(1.0, s.bitsC()));
-  if (all <= small_log2) return small_step_s + bytes / hbm_bps + 8.0 * macs / simt_flops * 0.5;
-  double rate = simt_flops;
-  if (precision != TZ_C64_SIMT) {
+  const bool c128 = precision == TZ_C128_SIMT;
+  const double esz = c128 ? 16.0 : 8.0;
+  const double bytes = esz * (std::ldexp(1.0, s.bitsA()) + std::ldexp(1.0, s.bitsB()) + std::ldexp(1.0, s.bitsC()));
+  const double simt = c128 ? simt_fp64_flops : simt_flops;
+  if (all <= small_log2) return small_step_s + bytes / hbm_bps + 8.0 * macs / simt * 0.5;
+  double rate = simt;
+  if (precision == TZ_TF32X3 || precision == TZ_BF16X3 || precision == TZ_FP16X3) {
     // the tensor-core path needs a real contraction (k >= 2 complex, m >= 64)
     int mk = (int)std::max(s.freeA.size(), s.freeB.size());
     if (s.contr.size() >= 1 && mk >= 6) rate = tc_useful_flops;

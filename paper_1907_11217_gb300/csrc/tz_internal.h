@@ -89,6 +89,7 @@ struct CostModel {
   int precision = TZ_C64_SIMT;
   double hbm_bps = 6.8e12;
   double simt_flops = 60e12;        // complex64 useful flop rate on CUDA cores
+  double simt_fp64_flops = 1.0e12;  // complex128 useful flop rate (GB300's FP64 units)
   double tc_useful_flops = 300e12;  // useful flop rate of the split tensor-core product
   double small_step_s = 2.0e-6;     // fixed cost of a small step
   int small_log2 = 22;
