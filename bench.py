@@ -413,6 +413,12 @@ def main():
     if dist:
         import torch.distributed as td
         td.init_process_group("nccl")
+        # every rank searches the same tree (the search is deterministic and
+        # independent of its thread count): share the host's cores among the
+        # ranks of this node instead of oversubscribing them
+        if "TZ_PATH_THREADS" not in os.environ:
+            per_node = int(os.environ.get("LOCAL_WORLD_SIZE", str(world)))
+            os.environ["TZ_PATH_THREADS"] = str(max(1, (os.cpu_count() or 1) // max(1, per_node)))
     torch.cuda.set_device(local)
     device = local
 
