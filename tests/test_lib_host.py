@@ -193,11 +193,11 @@ def test_path_search_independent_of_thread_count(tz, monkeypatch):
     trees = []
     for th in ("1", "3", "8"):
         monkeypatch.setenv("TZ_PATH_THREADS", th)
-        for alg in ("auto", "elimination"):
-            t = tz.tz_path_greedy(net, restarts=24, seed=5, log2_max_intermediate=12, algorithm=alg)
-            trees.append((th, alg, t.pairs().tobytes()))
-    for alg in ("auto", "elimination"):
-        got = {th: p for th, a, p in trees if a == alg}
+        for alg, rc in (("auto", 0), ("elimination", 0), ("elimination", 6)):
+            t = tz.tz_path_greedy(net, restarts=24, seed=5, log2_max_intermediate=12, algorithm=alg, reconfigure=rc)
+            trees.append((th, (alg, rc), t.pairs().tobytes()))
+    for key in (("auto", 0), ("elimination", 0), ("elimination", 6)):
+        got = {th: p for th, k, p in trees if k == key}
         assert got["1"] == got["3"] == got["8"]
 
 
