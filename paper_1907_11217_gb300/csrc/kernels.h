@@ -126,11 +126,13 @@ bool cgemm_tc_supported(int precision, int64_t M, int64_t N, int64_t K);
 // Read and clear the flag a tensor-core kernel raises when a bounded wait
 // times out (synchronous; 1 = a wait gave up).
 int tc_take_error();
-// Device scratch of one tensor-core product: the prepared hi/lo copies of B
-// and, for products that split K across CTAs, the partial results.
+// Device scratch of one tensor-core product: the prepared hi/lo copies of B,
+// for products that split K across CTAs the partial results, and in the FP16
+// mode the partial maxima of |B|.
 size_t cgemm_tc_scratch_bytes(int precision, int64_t batch, int64_t M, int64_t N, int64_t K);
-// Kernel launches of one tensor-core product (B preparation, the product, and
-// the sum of split-K partials when K is split; scatter outputs never split).
+// Kernel launches of one tensor-core product (FP16 mode: the maxima of |B|;
+// B preparation, the product, and the sum of split-K partials when K is
+// split; scatter outputs never split).
 int cgemm_tc_launches(int precision, int64_t batch, int64_t M, int64_t N, int64_t K, bool scatter);
 cudaError_t launch_accumulate(const AccumArgs &a, cudaStream_t s);
 cudaError_t launch_accumulate_plain(const float2 *part, double2 *acc, int64_t n, double sre, double sim,
