@@ -235,7 +235,9 @@ int tz_plan_describe(const tz_plan *plan, char *buf, size_t cap, size_t *len);
 
 /* Amplitudes of n bitstrings (host pointers): copies the bitstrings in,
  * contracts every group of the slice range, sums partial amplitudes in
- * FP64, copies 2n doubles out, and synchronises the plan's stream. */
+ * FP64, copies 2n doubles out, and synchronises the plan's stream.
+ * n = 0 does nothing and returns TZ_OK (the pointers are not read); n above
+ * the plan's max_bitstrings, or negative, returns TZ_EINVAL. */
 int tz_contract_amplitudes(tz_plan *plan, const uint8_t *bitstrings, int64_t n, double *out);
 /* Same with device pointers; asynchronous on the plan's stream (no host
  * synchronisation). d_bitstrings: n x n_qubits uint8; d_out: 2n doubles. */

@@ -372,15 +372,17 @@ int tz_plan_sliced_segments(const tz_plan *plan, int32_t *qubit_segment, int cap
 }
 
 static void check_rows(const tz_plan *plan, int64_t n) {
-  REQUIRE(n >= 1, "need at least one bitstring");
+  REQUIRE(n >= 0, "bitstring count must be >= 0");
   if (n > plan->max_rows)
     tz::fail(TZ_EINVAL, "at most " + std::to_string(plan->max_rows) + " bitstrings per call");
 }
 
 int tz_contract_amplitudes(tz_plan *plan, const uint8_t *bitstrings, int64_t n, double *out) {
   TZ_TRY
-  REQUIRE(plan && bitstrings && out, "NULL argument");
+  REQUIRE(plan, "NULL argument");
   check_rows(plan, n);
+  if (n == 0) return TZ_OK;  // nothing to contract, nothing written
+  REQUIRE(bitstrings && out, "NULL argument");
   REQUIRE(plan->bound, "plan has no workspace bound");
   const int nq = plan->net.n_qubits;
   for (int64_t i = 0; i < n * nq; i++)
@@ -401,8 +403,10 @@ int tz_contract_amplitudes(tz_plan *plan, const uint8_t *bitstrings, int64_t n, 
 
 int tz_contract_amplitudes_device(tz_plan *plan, const uint8_t *d_bitstrings, int64_t n, double *d_out) {
   TZ_TRY
-  REQUIRE(plan && d_bitstrings && d_out, "NULL argument");
+  REQUIRE(plan, "NULL argument");
   check_rows(plan, n);
+  if (n == 0) return TZ_OK;  // nothing to contract, nothing written
+  REQUIRE(d_bitstrings && d_out, "NULL argument");
   REQUIRE(plan->bound, "plan has no workspace bound");
   tz::cuda_check(cudaSetDevice(plan->opts.device), "cudaSetDevice");
   const tz::RunCtx ctx = tz::default_ctx(plan);

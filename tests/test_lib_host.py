@@ -221,3 +221,18 @@ def test_reconfigure_never_worse_and_valid(tz):
         assert s1["flops_per_group"] * 2.0 ** s1["k"] <= 1.5 * s0["flops_per_group"] * 2.0 ** s0["k"]
     with pytest.raises(tz.TzError):
         tz.tz_path_greedy(net, restarts=1, reconfigure=2)
+
+
+def test_contract_empty_and_oversized_batches(tz):
+    """Zero bitstrings is a valid, empty request (nothing is read or
+    written, no device work); more than the plan's max_bitstrings is
+    rejected before any device work."""
+    c = tz.tz_circuit_generate_grid(4, 4, 10, 1)
+    net = tz.tz_network_from_circuit(c, 0)
+    tree = tz.tz_path_greedy(net, restarts=2, seed=1)
+    plan = tz.tz_plan_create(net, tree, [], precision="c64", max_bitstrings=4)   # not bound
+    out = tz.tz_contract_amplitudes(plan, np.zeros((0, 16), dtype=np.uint8))
+    assert out.shape == (0,) and out.dtype == np.complex128
+    with pytest.raises(tz.TzError) as e:
+        tz.tz_contract_amplitudes(plan, np.zeros((5, 16), dtype=np.uint8))
+    assert e.value.code == -1
