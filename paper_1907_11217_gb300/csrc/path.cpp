@@ -3,6 +3,7 @@
 // earlier work; these are the library's own.
 #include <algorithm>
 #include <functional>
+#include <limits>
 #include <cmath>
 #include <queue>
 #include <unordered_map>
@@ -104,21 +105,27 @@ TreeInfo analyse_tree(const Network &net, const Pairs &pairs, const std::vector<
   return ti;
 }
 
-double CostModel::step_time(const StepInfo &s) const {
-  const int all = s.bitsAll();
+// The estimate depends only on the sizes of the four index classes.
+double CostModel::step_time_sizes(int nb, int nc, int na, int nf) const {
+  const int all = nb + nc + na + nf;
   const double macs = std::ldexp(1.0, all);
   const bool c128 = precision == TZ_C128_SIMT;
   const double esz = c128 ? 16.0 : 8.0;
-  const double bytes = esz * (std::ldexp(1.0, s.bitsA()) + std::ldexp(1.0, s.bitsB()) + std::ldexp(1.0, s.bitsC()));
+  const double bytes =
+      esz * (std::ldexp(1.0, nb + nc + na) + std::ldexp(1.0, nb + nc + nf) + std::ldexp(1.0, nb + na + nf));
   const double simt = c128 ? simt_fp64_flops : simt_flops;
   if (all <= small_log2) return small_step_s + bytes / hbm_bps + 8.0 * macs / simt * 0.5;
   double rate = simt;
   if (precision == TZ_TF32X3 || precision == TZ_BF16X3 || precision == TZ_FP16X3) {
     // the tensor-core path needs a real contraction (k >= 2 complex, m >= 64)
-    int mk = (int)std::max(s.freeA.size(), s.freeB.size());
-    if (s.contr.size() >= 1 && mk >= 6) rate = tc_useful_flops;
+    const int mk = std::max(na, nf);
+    if (nc >= 1 && mk >= 6) rate = tc_useful_flops;
   }
   return 3.0e-6 + std::max(8.0 * macs / rate, bytes / hbm_bps);
+}
+
+double CostModel::step_time(const StepInfo &s) const {
+  return step_time_sizes((int)s.batch.size(), (int)s.contr.size(), (int)s.freeA.size(), (int)s.freeB.size());
 }
 
 double group_time(const TreeInfo &ti, const CostModel &cm) {
@@ -391,14 +398,50 @@ namespace {
 struct Node {
   int l = -1, r = -1;
 };
-std::vector<int> keep_of(const std::vector<int> &x, const std::vector<int> &y, const std::vector<int> &z,
-                         const std::vector<int> &out, const Network &net) {
-  std::vector<int> u = set_union(x, y), k;
-  for (int i : u)
-    if (net.is_open(i) || std::binary_search(z.begin(), z.end(), i) || std::binary_search(out.begin(), out.end(), i))
-      k.push_back(i);
-  return k;
+// Estimated cost of ((X Y) Z) -> O (steps that run once at bind time cost
+// nothing), and in *wbits the size of W = (X Y). W keeps the indices of X and
+// Y that are open or also held by Z or O. The step classes (those classify()
+// gives) come from one merge over the sorted sets, without allocation.
+double two_step_cost(const std::vector<int> &X, const std::vector<int> &Y, const std::vector<int> &Z,
+                     const std::vector<int> &O, bool vxy, bool vz, const Network &net, const CostModel &cm,
+                     int *wbits) {
+  constexpr int kEnd = std::numeric_limits<int>::max();
+  size_t ix = 0, iy = 0, iz = 0, io = 0;
+  int b1 = 0, c1 = 0, a1 = 0, f1 = 0, b2 = 0, c2 = 0, a2 = 0, f2 = 0, w = 0;
+  for (;;) {
+    const int hx = ix < X.size() ? X[ix] : kEnd, hy = iy < Y.size() ? Y[iy] : kEnd, hz = iz < Z.size() ? Z[iz] : kEnd;
+    const int i = std::min(hx, std::min(hy, hz));
+    if (i == kEnd) break;
+    const bool inX = hx == i, inY = hy == i, inZ = hz == i;
+    ix += inX;
+    iy += inY;
+    iz += inZ;
+    while (io < O.size() && O[io] < i) io++;
+    const bool inO = io < O.size() && O[io] == i;
+    bool inW = false;
+    if (inX || inY) {
+      inW = net.is_open(i) || inZ || inO;
+      if (inX && inY)
+        (inW ? b1 : c1)++;
+      else if (inX)
+        a1++;
+      else
+        f1++;
+    }
+    if (inW) {
+      w++;
+      if (inZ)
+        (inO ? b2 : c2)++;
+      else
+        a2++;
+    } else if (inZ) {
+      f2++;
+    }
+  }
+  *wbits = w;
+  return (vxy ? cm.step_time_sizes(b1, c1, a1, f1) : 0.0) + ((vxy || vz) ? cm.step_time_sizes(b2, c2, a2, f2) : 0.0);
 }
+
 StepInfo classify(const std::vector<int> &x, const std::vector<int> &y, const std::vector<int> &c, bool var) {
   StepInfo st;
   for (int i : x) {
@@ -424,7 +467,6 @@ Pairs rotate_tree(const Network &net, const Pairs &pairs, const std::vector<char
     const int NS = (int)cur.size();
     std::vector<Node> nd(L + NS);
     for (int s = 0; s < NS; s++) nd[L + s] = {cur[s].first, cur[s].second};
-    auto cost = [&](const StepInfo &st) { return st.var ? cm.step_time(st) : 0.0; };
     std::vector<char> touched(L + NS, 0);
     bool changed = false;
     for (int q = L; q < L + NS; q++) {
@@ -434,39 +476,28 @@ Pairs rotate_tree(const Network &net, const Pairs &pairs, const std::vector<char
         const int y2 = side == 0 ? nd[q].r : nd[q].l;
         if (p < L || touched[p]) continue;
         const int s0 = nd[p].l, y1 = nd[p].r;
-        const auto &S = ti.sets[s0], &Y1 = ti.sets[y1], &Y2 = ti.sets[y2], &Out = ti.sets[q];
-        const bool vS = ti.var[s0], v1 = ti.var[y1], v2 = ti.var[y2];
-        // the three ways: first pair, then the third tensor
+        const auto &Out = ti.sets[q];
+        // the three ways: first pair, then the third tensor (k = 0 is the
+        // current arrangement)
         const int first[3][2] = {{s0, y1}, {s0, y2}, {y1, y2}};
         const int third[3] = {y2, y1, s0};
-        double best = 0;
+        double best = 0, c0 = 0;
         int best_k = 0;
         for (int k = 0; k < 3; k++) {
           const auto &X = ti.sets[first[k][0]], &Y = ti.sets[first[k][1]], &Z = ti.sets[third[k]];
           const bool vxy = ti.var[first[k][0]] || ti.var[first[k][1]];
-          std::vector<int> w = keep_of(X, Y, Z, Out, net);
-          if (k > 0 && (int)w.size() > ti.max_bits) continue;  // never raise the memory peak
-          double c = cost(classify(X, Y, w, vxy)) + cost(classify(w, Z, Out, vxy || ti.var[third[k]]));
+          int wbits = 0;
+          const double c = two_step_cost(X, Y, Z, Out, vxy, ti.var[third[k]] != 0, net, cm, &wbits);
+          if (k == 0) c0 = c;
+          if (k > 0 && wbits > ti.max_bits) continue;  // never raise the memory peak
           if (k == 0 || c < best) {
             best = c;
             best_k = k;
           }
         }
-        (void)S;
-        (void)Y1;
-        (void)Y2;
-        (void)vS;
-        (void)v1;
-        (void)v2;
         if (best_k == 0) continue;
         // keep it only if clearly cheaper than the current arrangement
-        {
-          const auto &X = ti.sets[s0], &Y = ti.sets[y1], &Z = ti.sets[y2];
-          std::vector<int> w = keep_of(X, Y, Z, Out, net);
-          double c0 = cost(classify(X, Y, w, ti.var[s0] || ti.var[y1])) +
-                      cost(classify(w, Z, Out, ti.var[s0] || ti.var[y1] || ti.var[y2]));
-          if (best >= 0.98 * c0) continue;
-        }
+        if (best >= 0.98 * c0) continue;
         nd[p] = {first[best_k][0], first[best_k][1]};
         if (side == 0)
           nd[q] = {p, third[best_k]};
@@ -687,25 +718,29 @@ std::vector<int> select_slices(const Network &net, const Pairs &pairs, int log2_
     int best = -1;
     int best_max = 1 << 30;
     double best_cost = 0;
+    // each step's estimate without slicing, reused for the steps a
+    // candidate does not touch (summed in the same order as before)
+    std::vector<double> base(ti.steps.size());
+    for (size_t q = 0; q < ti.steps.size(); q++) base[q] = cm.step_time(ti.steps[q]);
+    auto has = [](const std::vector<int> &v, int e) { return std::binary_search(v.begin(), v.end(), e); };
     for (int e : cands) {
       int mx = 0;
       for (const auto &s : ti.sets) {
-        int b = (int)s.size() - (std::binary_search(s.begin(), s.end(), e) ? 1 : 0);
+        int b = (int)s.size() - (has(s, e) ? 1 : 0);
         mx = std::max(mx, b);
       }
       double cost = 0;
-      for (const StepInfo &st : ti.steps) {
-        if (!st.var && !std::binary_search(ti.sets[st.c].begin(), ti.sets[st.c].end(), e)) {
-          bool inA = std::binary_search(ti.sets[st.a].begin(), ti.sets[st.a].end(), e);
-          bool inB = std::binary_search(ti.sets[st.b].begin(), ti.sets[st.b].end(), e);
-          if (!inA && !inB) continue;  // stays a bind-time step
+      for (size_t q = 0; q < ti.steps.size(); q++) {
+        const StepInfo &st = ti.steps[q];
+        // the class of e in this step, if any (the classes are disjoint)
+        const int where = has(st.batch, e) ? 0 : has(st.contr, e) ? 1 : has(st.freeA, e) ? 2 : has(st.freeB, e) ? 3 : -1;
+        if (!st.var && where < 0) continue;  // stays a bind-time step
+        if (where < 0) {
+          cost += base[q];
+          continue;
         }
-        StepInfo s2 = st;
-        for (auto *v : {&s2.batch, &s2.contr, &s2.freeA, &s2.freeB}) {
-          auto it = std::find(v->begin(), v->end(), e);
-          if (it != v->end()) v->erase(it);
-        }
-        cost += cm.step_time(s2);
+        cost += cm.step_time_sizes((int)st.batch.size() - (where == 0), (int)st.contr.size() - (where == 1),
+                                   (int)st.freeA.size() - (where == 2), (int)st.freeB.size() - (where == 3));
       }
       cost *= 2.0;  // twice as many slices
       if (best < 0 || mx < best_max || (mx == best_max && cost < best_cost)) {

@@ -94,6 +94,7 @@ struct CostModel {
   double small_step_s = 2.0e-6;     // fixed cost of a small step
   int small_log2 = 22;
   double step_time(const StepInfo &s) const;
+  double step_time_sizes(int n_batch, int n_contr, int n_freeA, int n_freeB) const;
 };
 double group_time(const TreeInfo &ti, const CostModel &cm);
 
