@@ -719,26 +719,46 @@ std::vector<int> select_slices(const Network &net, const Pairs &pairs, int log2_
     int best_max = 1 << 30;
     double best_cost = 0;
     // each step's estimate without slicing, reused for the steps a
-    // candidate does not touch (summed in the same order as before)
-    std::vector<double> base(ti.steps.size());
-    for (size_t q = 0; q < ti.steps.size(); q++) base[q] = cm.step_time(ti.steps[q]);
-    auto has = [](const std::vector<int> &v, int e) { return std::binary_search(v.begin(), v.end(), e); };
-    for (int e : cands) {
-      int mx = 0;
-      for (const auto &s : ti.sets) {
-        int b = (int)s.size() - (has(s, e) ? 1 : 0);
-        mx = std::max(mx, b);
+    // candidate does not touch (summed in step order)
+    const int NQ = (int)ti.steps.size();
+    std::vector<double> base(NQ);
+    for (int q = 0; q < NQ; q++) base[q] = cm.step_time(ti.steps[q]);
+    // per candidate: the largest tensors holding it, and the steps holding
+    // it with its class there (0 batch, 1 summed, 2 A only, 3 B only; the
+    // classes of a step are disjoint)
+    std::vector<char> is_cand(net.indices.size(), 0);
+    for (int e : cands) is_cand[e] = 1;
+    int n_top = 0;
+    std::vector<int> top_holders(net.indices.size(), 0);
+    for (const auto &st_set : ti.sets)
+      if ((int)st_set.size() == ti.max_bits) {
+        n_top++;
+        for (int i : st_set) top_holders[i]++;
       }
+    std::vector<std::vector<std::pair<int, int>>> held(net.indices.size());
+    for (int q = 0; q < NQ; q++) {
+      const StepInfo &st = ti.steps[q];
+      const std::vector<int> *cls[4] = {&st.batch, &st.contr, &st.freeA, &st.freeB};
+      for (int c = 0; c < 4; c++)
+        for (int i : *cls[c])
+          if (is_cand[i]) held[i].push_back({q, c});
+    }
+    for (int e : cands) {
+      // slicing e shrinks every tensor holding it by one bit: the peak stays
+      // unless every largest tensor holds e
+      const int mx = top_holders[e] < n_top ? ti.max_bits : ti.max_bits - 1;
       double cost = 0;
-      for (size_t q = 0; q < ti.steps.size(); q++) {
+      const auto &lst = held[e];
+      size_t p = 0;
+      for (int q = 0; q < NQ; q++) {
         const StepInfo &st = ti.steps[q];
-        // the class of e in this step, if any (the classes are disjoint)
-        const int where = has(st.batch, e) ? 0 : has(st.contr, e) ? 1 : has(st.freeA, e) ? 2 : has(st.freeB, e) ? 3 : -1;
-        if (!st.var && where < 0) continue;  // stays a bind-time step
-        if (where < 0) {
+        const bool has_e = p < lst.size() && lst[p].first == q;
+        if (!st.var && !has_e) continue;  // stays a bind-time step
+        if (!has_e) {
           cost += base[q];
           continue;
         }
+        const int where = lst[p++].second;
         cost += cm.step_time_sizes((int)st.batch.size() - (where == 0), (int)st.contr.size() - (where == 1),
                                    (int)st.freeA.size() - (where == 2), (int)st.freeB.size() - (where == 3));
       }
