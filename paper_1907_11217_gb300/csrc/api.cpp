@@ -167,8 +167,6 @@ int tz_path_greedy(const tz_network *net, const tz_path_opts *opts, tz_tree **ou
     int algo;
     double alpha, temp;
     uint64_t seed;
-    tz::Pairs pairs;
-    double score;
   };
   std::vector<Trial> trials(o.restarts);
   uint64_t rng = o.seed ^ 0x5DEECE66DULL;
@@ -190,7 +188,19 @@ int tz_path_greedy(const tz_network *net, const tz_path_opts *opts, tz_tree **ou
     }
     tr.seed = tz::splitmix64_next(rng);
   }
-  auto run_trial = [&](Trial &tr) {
+  // Only the best trees are kept: each thread keeps its `keep` best, ordered
+  // by (score, trial), and the lists are merged at the end.
+  struct Kept {
+    double score;
+    int trial;
+    tz::Pairs pairs;
+  };
+  auto before = [](const Kept &a, const Kept &b) {
+    return a.score < b.score || (a.score == b.score && a.trial < b.trial);
+  };
+  const int keep = o.reconfigure > 0 ? 8 : 1;
+  auto run_trial = [&](int i, std::vector<Kept> &mine) {
+    const Trial &tr = trials[i];
     tz::Pairs pr = tr.algo == TZ_PATH_GREEDY ? tz::greedy_tree(net->n, tr.alpha, tr.temp, tr.seed)
                                              : tz::elimination_tree(net->n, tr.temp, tr.seed);
     if (o.log2_max_intermediate > 0) {
@@ -201,8 +211,10 @@ int tz_path_greedy(const tz_network *net, const tz_path_opts *opts, tz_tree **ou
       pr = tz::rotate_tree(net->n, pr, flag, cm, 16);
     }
     int mb = 0;
-    tr.score = tree_score(net->n, pr, o.log2_max_intermediate, cm, &mb);
-    tr.pairs = std::move(pr);
+    Kept k{tree_score(net->n, pr, o.log2_max_intermediate, cm, &mb), i, std::move(pr)};
+    if ((int)mine.size() == keep && !before(k, mine.back())) return;
+    mine.insert(std::upper_bound(mine.begin(), mine.end(), k, before), std::move(k));
+    if ((int)mine.size() > keep) mine.pop_back();
   };
   // host threads: TZ_PATH_THREADS if set (>= 1), else one per hardware thread (at most 64)
   unsigned hw = std::max(1u, std::thread::hardware_concurrency());
@@ -211,18 +223,19 @@ int tz_path_greedy(const tz_network *net, const tz_path_opts *opts, tz_tree **ou
     if (v >= 1) hw = (unsigned)std::min<long>(v, 1024);
   }
   const int n_threads = (int)std::min<unsigned>({(unsigned)o.restarts, hw, 64u});
+  std::vector<std::vector<Kept>> kept(std::max(1, n_threads));
   if (n_threads <= 1) {
-    for (Trial &tr : trials) run_trial(tr);
+    for (int i = 0; i < o.restarts; i++) run_trial(i, kept[0]);
   } else {
     std::atomic<int> next{0};
     std::exception_ptr err;
     std::mutex err_mu;
     std::vector<std::thread> pool;
     for (int w = 0; w < n_threads; w++)
-      pool.emplace_back([&] {
+      pool.emplace_back([&, w] {
         for (int i; (i = next.fetch_add(1)) < o.restarts;) {
           try {
-            run_trial(trials[i]);
+            run_trial(i, kept[w]);
           } catch (...) {
             std::lock_guard<std::mutex> lk(err_mu);
             if (!err) err = std::current_exception();
@@ -232,26 +245,24 @@ int tz_path_greedy(const tz_network *net, const tz_path_opts *opts, tz_tree **ou
     for (auto &th : pool) th.join();
     if (err) std::rethrow_exception(err);
   }
-  int best = 0;
-  for (int i = 1; i < o.restarts; i++)
-    if (trials[i].score < trials[best].score) best = i;
+  std::vector<Kept> top;
+  for (auto &mine : kept)
+    for (auto &k : mine) top.push_back(std::move(k));
+  std::sort(top.begin(), top.end(), before);
+  if ((int)top.size() > keep) top.resize(keep);
+  Kept &best = top[0];
   if (o.reconfigure > 0) {
     // exact window re-optimisation of the best few trees (best first, ties by
     // restart order); the lowest score after it wins, ties to the earlier
-    std::vector<int> order(o.restarts);
-    for (int i = 0; i < o.restarts; i++) order[i] = i;
-    const int top = std::min(o.restarts, 8);
-    std::partial_sort(order.begin(), order.begin() + top, order.end(), [&](int a, int b) {
-      return trials[a].score < trials[b].score || (trials[a].score == trials[b].score && a < b);
-    });
-    std::vector<Trial> refined(top);
+    const int n_top = (int)top.size();
+    std::vector<Kept> refined(n_top);
     std::vector<std::thread> pool;
     std::exception_ptr err;
     std::mutex err_mu;
-    for (int q = 0; q < top; q++)
+    for (int q = 0; q < n_top; q++)
       pool.emplace_back([&, q] {
         try {
-          const Trial &src = trials[order[q]];
+          const Kept &src = top[q];
           std::vector<char> flag(net->n.indices.size(), 0);
           if (o.log2_max_intermediate > 0)
             for (int e : tz::select_slices(net->n, src.pairs, o.log2_max_intermediate, 40, cm)) flag[e] = 1;
@@ -266,15 +277,15 @@ int tz_path_greedy(const tz_network *net, const tz_path_opts *opts, tz_tree **ou
     for (auto &th : pool) th.join();
     if (err) std::rethrow_exception(err);
     int rb = -1;
-    for (int q = 0; q < top; q++)
-      if (refined[q].score < trials[best].score && (rb < 0 || refined[q].score < refined[rb].score)) rb = q;
+    for (int q = 0; q < n_top; q++)
+      if (refined[q].score < best.score && (rb < 0 || refined[q].score < refined[rb].score)) rb = q;
     if (rb >= 0) {
-      trials[best].pairs = std::move(refined[rb].pairs);
-      trials[best].score = refined[rb].score;
+      best.pairs = std::move(refined[rb].pairs);
+      best.score = refined[rb].score;
     }
   }
   auto t = std::make_unique<tz_tree>();
-  t->pairs = std::move(trials[best].pairs);
+  t->pairs = std::move(best.pairs);
   *out = t.release();
   TZ_CATCH
 }
