@@ -249,32 +249,44 @@ def roofline(prof, precision):
     return out
 
 
-def cpu_oracle_sample(spec, segs, bits, budget_s, k):
-    """Time the FP64 oracle contractor on a bounded sample of the workload:
-    sub-slices of slice 0 until the budget is spent; extrapolate to all
-    2^k slices of one amplitude."""
-    from oracle import tn
-    import itertools
+# Largest factor (log2 entries) the path-sum oracle may create when timed
+ORACLE_MAX_LOG2 = 25
+
+
+def oracle_segments(tz, spec, pairs, batch_log2=0, cap=18):
+    """Sliced segments for the CPU baseline: the GPU tree, sliced further to
+    a 2^cap intermediate cap, so that one slice is a bounded unit of oracle
+    work (the sum over all slices is the amplitude, Sec. 1)."""
+    net = tz.tz_network_from_circuit(tz.tz_circuit_from_spec(spec), batch_log2)
+    tree = tz.tz_tree_from_pairs(net, pairs)
+    sl = tz.tz_slice_select(net, tree, cap, 40)
+    return [net.index_info(e) for e in sl]
+
+
+def cpu_oracle_sample(spec, segs, bits, budget_s):
+    """Time the FP64 path-sum oracle, as it stands, on a bounded sample of
+    the workload: the partial amplitudes of slices 0, 1, 2, ... of the given
+    slicing until the budget is spent; extrapolate to all 2^k slices of one
+    amplitude. Cores: the BLAS threads numpy's einsum runs on."""
+    from oracle import pathsum
     t0 = time.perf_counter()
-    c = tn.Contractor(spec, sliced=segs, max_log2=22)
+    c = pathsum.SegmentContractor(spec, sliced=segs, max_log2=ORACLE_MAX_LOG2)
     setup = time.perf_counter() - t0
-    n_sub = 1 << len(c.extra)
+    k = len(segs)
     done = 0
     t1 = time.perf_counter()
-    base = [0] * len(segs)
-    for extra in itertools.product((0, 1), repeat=len(c.extra)):
-        leaves = c.net.leaf_values(bits, c._fixed_map(base + list(extra)))
-        tn.contract_path(leaves, c.pairs)
+    while done < (1 << k):
+        c.partial(bits, done)
         done += 1
         if time.perf_counter() - t1 > budget_s:
             break
     el = time.perf_counter() - t1
-    per_sub = el / done
-    s_per_amp = per_sub * n_sub * (1 << k)
+    s_per_amp = el / done * (1 << k)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": s_per_amp, "unit": "s/amplitude", "cores": cores, "kind": "oracle",
-            "sample": f"{done} of {n_sub} oracle sub-slices of slice 0 (oracle largest intermediate 2^{c.max_log2}), "
-                      f"{el:.1f} s, extrapolated x{n_sub}/{done} sub-slices x 2^{k} slices; oracle setup {setup:.1f} s"}
+            "sample": f"{done} of 2^{k} slice partials of one amplitude by the FP64 path-sum oracle (its own "
+                      f"elimination order, largest factor 2^{c.width - 1}, {len(c.extra)} extra segments of its own), "
+                      f"{el:.1f} s, extrapolated x 2^{k}/{done}; oracle setup {setup:.1f} s"}
 
 
 def run_serving(args):
@@ -361,6 +373,11 @@ def run_serving(args):
     srv.close()
 
 
+def metric_name(workload):
+    """The metric string both arms print (the driver compares them)."""
+    return f"sec/amplitude ({workload})"
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle on the host cores, same metric."""
     rank = int(os.environ.get("RANK", "0"))
@@ -372,22 +389,23 @@ def run_reference(args):
     log2_max = args.log2_max or WORKLOADS[args.workload][6]
     circ = tz.tz_circuit_from_spec(spec)
     net = tz.tz_network_from_circuit(circ, 0)
+    # the same tree as the GPU arm's tensor-core modes (host preprocessing,
+    # untimed), sliced further into oracle-sized slices
     tree = tz.tz_path_greedy(net, restarts=args.restarts, seed=args.tree_seed, log2_max_intermediate=log2_max,
-                             algorithm=args.algorithm)
-    sliced = tz.tz_slice_select(net, tree, log2_max, 40) if log2_max > 0 else []
-    segs = [net.index_info(e) for e in sliced]
+                             precision="bf16x3", algorithm=args.algorithm)
+    segs = oracle_segments(tz, spec, tree.pairs())
     bits = ti.random_bitstrings(nq, 1, WORKLOADS[args.workload][7])[0]
     per = max(2.0, args.cpu_seconds / max(1, args.steps + args.warmup))
     vals = []
     for i in range(args.warmup + args.steps):
-        r = cpu_oracle_sample(spec, segs, bits, per, len(sliced))
+        r = cpu_oracle_sample(spec, segs, bits, per)
         if i >= args.warmup:
             vals.append(r)
     v = statistics.median(x["value"] for x in vals)
-    line = {"impl": "reference", "metric": f"sec/amplitude ({args.workload})", "value": v, "unit": "s/amplitude",
+    line = {"impl": "reference", "metric": metric_name(args.workload), "value": v, "unit": "s/amplitude",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "k": len(sliced)},
+            "config": {"workload": args.workload, "oracle_slices_log2": len(segs)},
             "cpu_baseline": {"kind": "oracle", "cores": vals[-1]["cores"], "sample": vals[-1]["sample"], "value": v,
                              "unit": "s/amplitude"},
             "e2e": {"value": v, "unit": "s/amplitude", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -431,6 +449,7 @@ def main():
     plan, sliced, prep_s = build_plan(tz, spec, args, precision, stream, device, log2_max)
     st = plan.stats()
     plan.bind()
+    plan_bind_ms = plan.stats()["bind_ms"]
     k = len(sliced)
     n_slices = 1 << k
     B = 1 << args.batch_log2
@@ -438,6 +457,10 @@ def main():
     d_bits = torch.from_numpy(bits).to(f"cuda:{device}")
     d_out = torch.zeros(2 * B, dtype=torch.float64, device=f"cuda:{device}")
 
+    # ranks split the slices of one amplitude; with fewer slices than ranks
+    # (the default tree has none) they are replicas instead: each contracts
+    # whole amplitudes of its own bitstrings, and nothing is reduced
+    replicas = dist and n_slices < world
     # slices per step: ~3 s of estimated work (a fixed 2^12 when that is smaller), at least 1
     S = args.slices
     if S <= 0:
@@ -447,19 +470,21 @@ def main():
         tz.tz_contract_amplitudes_device(plan, d_bits, d_out)
         stream.synchronize()
         one = time.perf_counter() - t0
-        S = int(max(1, min(4096, n_slices // world, 3.0 / max(one, 1e-6))))
-    S = min(S, max(1, n_slices // world))
+        S = int(max(1, min(4096, n_slices // (1 if replicas else world), 3.0 / max(one, 1e-6))))
+    S = min(S, max(1, n_slices // (1 if replicas else world)))
 
     from paper_1907_11217_gb300 import shard
 
     def slice_range(step):
+        if replicas:
+            return shard.step_window(n_slices, 1, 0, S, step)
         return shard.step_window(n_slices, world, rank, S, step)
 
     def one_step(step, reduce=True):
         lo, hi = slice_range(step)
         plan.set_slice_range(lo, hi)
         tz.tz_contract_amplitudes_device(plan, d_bits, d_out)
-        if dist and reduce:
+        if dist and reduce and not replicas:
             with torch.cuda.stream(stream):
                 shard.reduce_partials(d_out)
 
@@ -484,6 +509,8 @@ def main():
         t = torch.tensor([ms], device=f"cuda:{device}")
         td.all_reduce(t, op=td.ReduceOp.MAX)
         ms = float(t.item())
+    # slices of one amplitude per step, all ranks together; replicas each
+    # contract their own amplitudes
     slices_per_step = S * world
     s_per_amp = ms / 1e3 * n_slices / slices_per_step / B
     flops_step = st["flops_per_group"] * slices_per_step
@@ -554,10 +581,12 @@ def main():
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(spec, segs, bits[0], args.cpu_seconds, k)
+        tc_key = (spec, "tensor-core" if precision not in ("c64", "c128") else precision, log2_max)
+        cpu = cpu_oracle_sample(spec, oracle_segments(tz, spec, _TREES[tc_key], args.batch_log2), bits[0],
+                                args.cpu_seconds)
     paper = PAPER_S_PER_AMP.get(args.workload)
     line = {
-        "metric": f"sec/amplitude ({args.workload}, extrapolated from timed slices)",
+        "metric": metric_name(args.workload),
         "value": s_per_amp, "unit": "s/amplitude", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": (s_per_amp / paper) if paper else None,
@@ -567,12 +596,15 @@ def main():
                    "slices_per_step": slices_per_step, "log2_max_intermediate": st["max_log2"],
                    "tree_restarts": args.restarts, "tree_reconfigure": args.reconfigure, "preprocessing_s": prep_s,
                    "l2": "intermediates larger than L2" if st["max_log2"] >= 25 else "working set may fit L2",
-                   "parallelism": f"slices x{world}"},
+                   "parallelism": f"replicas x{world}" if replicas else f"slices x{world}",
+                   "extrapolation": f"step time x 2^{k} / {slices_per_step} slices per step / {B} bitstrings"},
         "contraction_tflops": tflops,
         "plan": {"flops_per_slice": st["flops_per_group"], "bytes_per_slice": st["bytes_per_group"],
                  "permute_bytes_per_slice": st["permute_bytes_per_group"], "steps": st["n_steps"],
                  "gemm_steps": st["n_gemm_steps"], "launches_per_slice": st["n_launches_per_group"],
-                 "workspace_gb": st["workspace_bytes"] / 1e9},
+                 "workspace_gb": st["workspace_bytes"] / 1e9,
+                 "const_steps": st["n_const_steps"], "const_flops": st["const_flops"],
+                 "bind_ms": plan_bind_ms},
         "e2e": {"value": e2e_s, "unit": "s/amplitude", "h2d_bytes_per_step": int(bits.nbytes),
                 "d2h_bytes_per_step": 16 * B},
         "roofline": rl,

@@ -207,6 +207,9 @@ typedef struct {
   size_t workspace_bytes;        /* device workspace the plan needs                  */
   size_t const_bytes;            /* part of it holding bind-time constants           */
   size_t scratch_bytes;          /* per-query scratch part (server admission unit)   */
+  double const_flops;            /* useful flops of the bind-time (constant) steps,
+                                    computed once per bind, not per group            */
+  double bind_ms;                /* wall time of the last tz_plan_bind_workspace     */
 } tz_plan_stats;
 
 /* Build a plan: classify steps, choose layouts, permutes and kernels, lay
@@ -240,8 +243,17 @@ int tz_plan_describe(const tz_plan *plan, char *buf, size_t cap, size_t *len);
  * the plan's max_bitstrings, or negative, returns TZ_EINVAL. */
 int tz_contract_amplitudes(tz_plan *plan, const uint8_t *bitstrings, int64_t n, double *out);
 /* Same with device pointers; asynchronous on the plan's stream (no host
- * synchronisation). d_bitstrings: n x n_qubits uint8; d_out: 2n doubles. */
+ * synchronisation). d_bitstrings: n x n_qubits uint8; d_out: 2n doubles.
+ * If a tensor-core product of the call times out in one of its bounded
+ * waits, the amplitudes it could have affected are written as NaN, and
+ * tz_plan_status reports TZ_ETIMEOUT. (tz_contract_amplitudes returns
+ * TZ_ETIMEOUT itself.) */
 int tz_contract_amplitudes_device(tz_plan *plan, const uint8_t *d_bitstrings, int64_t n, double *d_out);
+/* Synchronise the plan's stream and report how its last call (on the plan's
+ * own workspace) ended: TZ_ETIMEOUT if a tensor-core product timed out in a
+ * bounded wait (its amplitudes are then NaN), else TZ_OK. Each call starts
+ * with a clear status. */
+int tz_plan_status(tz_plan *plan);
 void tz_plan_destroy(tz_plan *plan);
 
 /* Per-kernel timing of a plan's launches (CUDA events around every launch on
@@ -321,6 +333,13 @@ int tz_op_cgemm(int precision, int64_t batch, int64_t m, int64_t n, int64_t k,
                 const void *A, int64_t sa, const void *B, int64_t sb, void *C, int64_t sc,
                 void *scratch, size_t scratch_bytes, void *stream);
 int tz_op_cgemm_scratch_bytes(int precision, int64_t batch, int64_t m, int64_t n, int64_t k, size_t *bytes);
+/* The split-precision products wait on on-chip barriers with a time limit
+ * (2 s by default); when a wait runs out, the product stops, leaves C
+ * invalid and sets an error word kept in the first 256 bytes of its scratch
+ * (cleared on the stream when each tz_op_cgemm call starts). This call
+ * synchronises `stream` and returns TZ_ETIMEOUT if the last product on
+ * `scratch` set it, else TZ_OK (always TZ_OK for the CUDA-core modes). */
+int tz_op_cgemm_status(int precision, const void *scratch, void *stream);
 
 /* Allocation-free variant of tz_op_cgemm for the split-precision modes
  * (TZ_TF32X3, TZ_BF16X3, TZ_FP16X3). The paper has no counterpart: this entry point
@@ -332,13 +351,31 @@ int tz_op_cgemm_scratch_bytes(int precision, int64_t batch, int64_t m, int64_t n
  * holds until the process exits. Products needing more scratch than that
  * (tz_op_cgemm_scratch_bytes) return TZ_EINVAL. The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture. All calls
+ * device current and keeps it; make that first call before any stream
+ * capture, and do not reset the device (cudaDeviceReset) after it. All calls
  * share the array: calls that overlap on the GPU race on it and must be
- * serialised by the caller. The array keeps the last call's contents;
- * every call rewrites all of it that it reads. Allocates no device memory. */
+ * serialised by the caller. The array keeps the last call's contents; each
+ * call clears its error word (the array's first 256 bytes) on the stream and
+ * writes every other byte it reads before reading it. Allocates no device
+ * memory. */
 int tz_op_cgemm_static(int precision, int64_t batch, int64_t m, int64_t n, int64_t k,
                        const void *A, int64_t sa, const void *B, int64_t sb, void *C, int64_t sc,
                        void *stream);
+/* Status of the last tz_op_cgemm_static call on the current device, as
+ * tz_op_cgemm_status: synchronises `stream`; TZ_ETIMEOUT if the product
+ * timed out in a bounded wait. */
+int tz_op_cgemm_static_status(void *stream);
+
+/* Test hooks (current device; they change no result of a product that
+ * completes). tz_debug_set_wait_limit: the time limit of the tensor-core
+ * products' bounded waits, in ns (0 restores the default 2 s); waits that let
+ * copies in flight land before a stopped product exits always keep 2 s.
+ * tz_debug_stall_tensor_core(1): every tensor-core product launched while it
+ * is on first waits on a barrier that nothing arrives at, so the wait runs
+ * out after the limit and the product reports TZ_ETIMEOUT; (0) turns it off.
+ * Graph replays captured earlier pick both up (they are read on the device). */
+int tz_debug_set_wait_limit(int64_t ns);
+int tz_debug_stall_tensor_core(int on);
 
 /* FP64 accumulation of partial amplitudes: acc[j] += scale * part[j] for
  * j < n, with part complex64 and acc, scale complex128 (re, im). */

@@ -26,6 +26,8 @@ __all__ = [
     "tz_circuit_generate_grid", "tz_circuit_generate_bristlecone", "tz_network_from_circuit", "tz_path_greedy",
     "tz_tree_from_pairs", "tz_slice_select", "tz_plan_create", "tz_contract_amplitudes",
     "tz_contract_amplitudes_device", "tz_op_permute", "tz_op_cgemm", "tz_op_accumulate", "PRECISIONS",
+    "tz_plan_status", "tz_op_cgemm_status", "tz_op_cgemm_static_status", "tz_debug_set_wait_limit",
+    "tz_debug_stall_tensor_core",
     "TZ_C64_SIMT", "TZ_TF32X3", "TZ_BF16X3", "TZ_FP16X3",
 ]
 
@@ -293,6 +295,36 @@ def tz_op_cgemm(precision, batch, m, n, k, A, sa, B, sb, C, sc, scratch=None, st
     sbytes = 0 if scratch is None else scratch.numel() * scratch.element_size()
     sptr = ctypes.c_void_p(0) if scratch is None else _ptr(scratch)
     check(lib().tz_op_cgemm(p, batch, m, n, k, _ptr(A), sa, _ptr(B), sb, _ptr(C), sc, sptr, sbytes, _stream(stream)))
+
+
+def tz_op_cgemm_status(precision, scratch=None, stream=None):
+    """Synchronise `stream`; raise TzError (TZ_ETIMEOUT) if the last
+    tz_op_cgemm on `scratch` timed out in a bounded wait."""
+    p = PRECISIONS.get(precision, precision)
+    sptr = ctypes.c_void_p(0) if scratch is None else _ptr(scratch)
+    check(lib().tz_op_cgemm_status(p, sptr, _stream(stream)))
+
+
+def tz_op_cgemm_static_status(stream=None):
+    check(lib().tz_op_cgemm_static_status(_stream(stream)))
+
+
+def tz_plan_status(plan: "Plan"):
+    """Synchronise the plan's stream; raise TzError (TZ_ETIMEOUT) if a
+    tensor-core product of the plan's last call timed out."""
+    check(lib().tz_plan_status(plan.handle))
+
+
+def tz_debug_set_wait_limit(ns: int):
+    """Test hook: limit of the products' bounded waits on the current device
+    (0 restores the default, 2 s)."""
+    check(lib().tz_debug_set_wait_limit(int(ns)))
+
+
+def tz_debug_stall_tensor_core(on: bool):
+    """Test hook: while on, every tensor-core product on the current device
+    first waits on a barrier nothing arrives at, so its bounded wait runs out."""
+    check(lib().tz_debug_stall_tensor_core(1 if on else 0))
 
 
 def tz_op_accumulate(d_part, d_acc, n, scale=1.0 + 0j, stream=None):

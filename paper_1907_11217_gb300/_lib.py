@@ -49,7 +49,8 @@ class tz_plan_stats(ctypes.Structure):
                 ("batch_log2", ctypes.c_int), ("max_log2", ctypes.c_int), ("flops_per_group", ctypes.c_double),
                 ("gemm_flops_per_group", ctypes.c_double), ("bytes_per_group", ctypes.c_double),
                 ("permute_bytes_per_group", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t),
-                ("const_bytes", ctypes.c_size_t), ("scratch_bytes", ctypes.c_size_t)]
+                ("const_bytes", ctypes.c_size_t), ("scratch_bytes", ctypes.c_size_t), ("const_flops", ctypes.c_double),
+                ("bind_ms", ctypes.c_double)]
 
 
 PROFILE_KINDS = ("leaves", "direct", "permute", "gemm_simt", "gemm_tc", "accumulate", "gemm_skinny", "gemm_dot")
@@ -115,6 +116,11 @@ SIGNATURES = {
     "tz_op_cgemm_scratch_bytes": (c_int, [c_int, c_int64, c_int64, c_int64, c_int64, ctypes.POINTER(c_size_t)]),
     "tz_op_accumulate": (c_int, [P, F64P, c_int64, c_double, c_double, P]),
     "tz_op_cgemm_static": (c_int, [c_int, c_int64, c_int64, c_int64, c_int64, P, c_int64, P, c_int64, P, c_int64, P]),
+    "tz_plan_status": (c_int, [P]),
+    "tz_op_cgemm_status": (c_int, [c_int, P, P]),
+    "tz_op_cgemm_static_status": (c_int, [P]),
+    "tz_debug_set_wait_limit": (c_int, [c_int64]),
+    "tz_debug_stall_tensor_core": (c_int, [c_int]),
 }
 
 _lib = None

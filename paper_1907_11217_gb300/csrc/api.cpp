@@ -25,6 +25,10 @@ struct tz_tree {
 namespace {
 thread_local std::string g_err;
 void set_error(const std::string &m) { g_err = m; }
+bool is_tc_precision(int p) { return p == TZ_TF32X3 || p == TZ_BF16X3 || p == TZ_FP16X3; }
+// tz_op_cgemm scratch of the split-precision modes: the error word of the
+// call in the first 256 bytes, then the product's own scratch
+constexpr size_t kOpErrBytes = 256;
 }  // namespace
 
 // shared with the other translation units that export C entry points
@@ -407,8 +411,20 @@ int tz_contract_amplitudes(tz_plan *plan, const uint8_t *bitstrings, int64_t n, 
   tz::cuda_check(cudaMemcpyAsync(out, ctx.scratch + plan->s_acc, (size_t)n * 16, cudaMemcpyDeviceToHost, s),
                  "copy amplitudes out");
   tz::cuda_check(cudaStreamSynchronize(s), "contract");
-  if (plan->opts.precision != TZ_C64_SIMT && tz::dev::tc_take_error() == 1)
-    tz::fail(TZ_ETIMEOUT, "a tensor-core kernel wait timed out; results are invalid");
+  if (is_tc_precision(plan->opts.precision) && tz::read_tc_error(plan, ctx))
+    tz::fail(TZ_ETIMEOUT, "a tensor-core product timed out in a bounded wait; the amplitudes are invalid (NaN)");
+  TZ_CATCH
+}
+
+int tz_plan_status(tz_plan *plan) {
+  TZ_TRY
+  REQUIRE(plan, "NULL plan");
+  REQUIRE(plan->bound, "plan has no workspace bound");
+  tz::cuda_check(cudaSetDevice(plan->opts.device), "cudaSetDevice");
+  const tz::RunCtx ctx = tz::default_ctx(plan);
+  tz::cuda_check(cudaStreamSynchronize(ctx.stream), "synchronise the plan's stream");
+  if (is_tc_precision(plan->opts.precision) && tz::read_tc_error(plan, ctx))
+    tz::fail(TZ_ETIMEOUT, "a tensor-core product of the last call timed out in a bounded wait; its amplitudes are NaN");
   TZ_CATCH
 }
 
@@ -509,7 +525,7 @@ int tz_op_cgemm_scratch_bytes(int precision, int64_t batch, int64_t m, int64_t n
   if (precision == TZ_TF32X3 || precision == TZ_BF16X3 || precision == TZ_FP16X3) {
     if (!tz::dev::cgemm_tc_supported(precision, m, n, k))
       tz::fail(TZ_EUNSUPPORTED, "shape not supported by the tensor-core product");
-    *bytes = tz::dev::cgemm_tc_scratch_bytes(precision, batch, m, n, k);
+    *bytes = kOpErrBytes + tz::dev::cgemm_tc_scratch_bytes(precision, batch, m, n, k);
   } else if (precision != TZ_C64_SIMT && precision != TZ_C128_SIMT) {
     tz::fail(TZ_EINVAL, "unknown precision");
   }
@@ -533,14 +549,42 @@ int tz_op_cgemm(int precision, int64_t batch, int64_t m, int64_t n, int64_t k, c
   } else if (precision == TZ_TF32X3 || precision == TZ_BF16X3 || precision == TZ_FP16X3) {
     if (!tz::dev::cgemm_tc_supported(precision, m, n, k))
       tz::fail(TZ_EUNSUPPORTED, "shape not supported by the tensor-core product");
-    size_t need = tz::dev::cgemm_tc_scratch_bytes(precision, batch, m, n, k);
-    REQUIRE(scratch_bytes >= need && (need == 0 || scratch), "scratch too small");
+    const size_t need = kOpErrBytes + tz::dev::cgemm_tc_scratch_bytes(precision, batch, m, n, k);
+    REQUIRE(scratch && scratch_bytes >= need, "scratch too small (tz_op_cgemm_scratch_bytes)");
+    REQUIRE((reinterpret_cast<uintptr_t>(scratch) & 255) == 0, "scratch must be 256-byte aligned");
+    int *err = static_cast<int *>(scratch);
+    tz::cuda_check(cudaMemsetAsync(err, 0, sizeof(int), s), "clear error word");
     tz::cuda_check(tz::dev::launch_cgemm_tc(precision, (const float2 *)A, (const float2 *)B, (float2 *)C, batch, m, n,
-                                            k, sa, sb, sc, nullptr, scratch, scratch_bytes, s),
+                                            k, sa, sb, sc, nullptr, static_cast<char *>(scratch) + kOpErrBytes,
+                                            scratch_bytes - kOpErrBytes, err, s),
                    "tensor-core gemm");
   } else {
     tz::fail(TZ_EINVAL, "unknown precision");
   }
+  TZ_CATCH
+}
+
+int tz_op_cgemm_status(int precision, const void *scratch, void *stream) {
+  TZ_TRY
+  tz::cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "synchronise the stream");
+  if (!is_tc_precision(precision)) return TZ_OK;
+  REQUIRE(scratch, "NULL scratch");
+  int v = 0;
+  tz::cuda_check(cudaMemcpy(&v, scratch, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
+  if (v) tz::fail(TZ_ETIMEOUT, "the tensor-core product timed out in a bounded wait; its result is invalid");
+  TZ_CATCH
+}
+
+int tz_debug_set_wait_limit(int64_t ns) {
+  TZ_TRY
+  REQUIRE(ns >= 0, "wait limit must be >= 0");
+  tz::cuda_check(tz::dev::tc_set_wait_limit((unsigned long long)ns), "set wait limit");
+  TZ_CATCH
+}
+
+int tz_debug_stall_tensor_core(int on) {
+  TZ_TRY
+  tz::cuda_check(tz::dev::tc_set_stall(on), "set stall switch");
   TZ_CATCH
 }
 

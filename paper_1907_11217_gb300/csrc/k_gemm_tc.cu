@@ -33,8 +33,9 @@
 //                FP32 registers (per thread one row of the tile, half of its
 //                columns: two warps per TMEM lane quarter) before the row
 //                goes to global memory.
-// Every wait is bounded in time; on timeout the kernel raises an error flag,
-// drains its copies in flight, frees TMEM and returns.
+// Every wait is bounded in time; on timeout the kernel sets the caller's
+// error word (TcArgs::err), drains its copies in flight, frees TMEM and
+// returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -61,9 +62,17 @@ __host__ __device__ constexpr int stage_k() { return MODE == 0 ? 32 : 64; }
 // TMA, MMA, 4 split warps, 8 epilogue warps; registers are granted to warps
 // in groups of four, so 14 warps leave 128 registers a thread
 constexpr int kThreads = 448;
-constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait (default)
+// Waits that let copies and products in flight finish before the CTA exits
+// (after an abort) always use this limit, never the adjustable one.
+constexpr unsigned long long kDrainNs = 2000000000ull;
 
-__device__ int g_tc_error;
+// Per device: the limit of the ordinary bounded waits (tz_debug_set_wait_limit)
+// and the test switch that makes every product's MMA issuer first wait on a
+// barrier nothing arrives at (tz_debug_stall_tensor_core), so that the wait
+// runs out and the product reports a timeout.
+__device__ unsigned long long g_wait_ns = kWaitNs;
+__device__ int g_stall;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -91,12 +100,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for the phase with the given parity; false on timeout or when another
-// role has aborted (then the caller stops its work).
+// Wait for the phase with the given parity; false on timeout (after limit_ns,
+// which also raises the CTA's abort flag) or, with honour_abort, when another
+// role has aborted (then the caller stops its work). Drains pass
+// honour_abort = false and the fixed kDrainNs.
 // The clock is read only every 256 unsuccessful polls (a wait that succeeds
 // at once costs one try_wait): the time limit counts from the first of them.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                          bool honour_abort = true) {
+                                          unsigned long long limit_ns, bool honour_abort = true) {
   unsigned long long t0 = 0;
   for (uint32_t i = 0;; i++) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -105,8 +116,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
       const unsigned long long now = globaltimer();
       if (t0 == 0) {
         t0 = now;
-      } else if (now - t0 > kWaitNs) {
-        atomicExch(&g_tc_error, 1);
+      } else if (now - t0 > limit_ns) {
         *abort_flag = 1;
         return false;
       }
@@ -290,6 +300,7 @@ struct TcArgs {
   int64_t split_stride;  // ksplit > 1, range s writes row-major partials at C + s * split_stride
   const uint32_t *bmax;  // FP16 mode: pb partial maxima of |B|
   int pb;
+  int *err;              // set to 1 when a bounded wait ran out (never cleared here)
   CScatter sc;
 };
 
@@ -343,7 +354,7 @@ struct TcSmem {
   static constexpr int NBUF = A_COL0 / ACC_COLS;
   static_assert(BNP <= 128, "an epilogue thread holds half a row of the tile in registers");
   // barriers, then the TMEM address, the abort flag and two scale exponents
-  static_assert((3 * STAGES + 2 * NBUF + ASLOTS + 1 + XR) * 8 + 16 <= BARS, "barriers and flags fit in BARS");
+  static_assert((3 * STAGES + 2 * NBUF + ASLOTS + 2 + XR) * 8 + 16 <= BARS, "barriers and flags fit in BARS");
   // the split warps run at most ASLOTS k-blocks ahead of the products, which
   // run at most NBUF ranges ahead of the epilogue: a split warp never reaches
   // an exponent entry, or its barrier's next phase, that the epilogue has yet
@@ -370,7 +381,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t *drain = tempty + L::NBUF;   // all products retired
   uint64_t *aempty = drain + 1;         // [ASLOTS] TMEM A slot read by its products
   uint64_t *xfull = aempty + L::ASLOTS;  // [XR] FP16: exponent ring entry written
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(xfull + L::XR);
+  uint64_t *stall = xfull + L::XR;       // test stall: nothing ever arrives here
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(stall + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   int *scale_exp = reinterpret_cast<int *>(tmem_slot + 2);  // FP16 mode: [1] = exponent of B
   int64_t *coloff_all = reinterpret_cast<int64_t *>(smem + STAGES * L::STAGE + L::STAGING + L::BARS);
@@ -415,6 +427,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(drain, 1);
     for (int b = 0; b < L::ASLOTS; b++) mbar_init(&aempty[b], 1);
     for (int b = 0; b < L::XR; b++) mbar_init(&xfull[b], 128);
+    mbar_init(stall, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -435,6 +448,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const unsigned long long wait_ns = g_wait_ns;
+  auto wait = [&](uint64_t *bar, uint32_t parity) { return mbar_wait(bar, parity, abort_flag, wait_ns); };
 
   if (warp == 0) {
     if (lane == 0) {
@@ -446,7 +461,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int kb = d.kb0; kb < d.kb1; kb++, g++) {
           const int s = (int)(g % STAGES);
           const int64_t round = g / STAGES;
-          if (round > 0 && !mbar_wait(&empty[s], (uint32_t)((round - 1) & 1), abort_flag)) {
+          if (round > 0 && !wait(&empty[s], (uint32_t)((round - 1) & 1))) {
             ok = false;
             break;
           }
@@ -462,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (*abort_flag) {
         // drain: let the copies already issued land before the CTA exits
         for (int64_t q = g > STAGES ? g - STAGES : 0; q < g; q++)
-          mbar_wait(&full[q % STAGES], (uint32_t)((q / STAGES) & 1), abort_flag, false);
+          mbar_wait(&full[q % STAGES], (uint32_t)((q / STAGES) & 1), abort_flag, kDrainNs, false);
       }
     }
   } else if (warp == 1) {
@@ -474,14 +489,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       constexpr int kSteps = stage_k<MODE>() / (MODE == MODE_TF32 ? 8 : 16);
       constexpr int kFoldKb = fold_k<MODE>() / stage_k<MODE>();  // k-blocks per accumulation range
       int64_t g = 0, rg = 0;  // k-blocks and accumulation ranges issued
-      bool ok = true;
+      // test stall: a bounded wait on a barrier nothing arrives at
+      bool ok = !g_stall || wait(stall, 0);
       for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         const Tile d = decode(t);
         const int nkb = d.kb1 - d.kb0;
         for (int r0 = 0; r0 < nkb; r0 += kFoldKb, rg++) {
           const int buf = (int)(rg % L::NBUF);
           const int64_t use = rg / L::NBUF;
-          if (use > 0 && !mbar_wait(&tempty[buf], (uint32_t)((use - 1) & 1), abort_flag)) {
+          if (use > 0 && !wait(&tempty[buf], (uint32_t)((use - 1) & 1))) {
             ok = false;
             break;
           }
@@ -490,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int r1 = min(nkb, r0 + kFoldKb);
           for (int kb = r0; kb < r1; kb++, g++) {
             const int s = (int)(g % STAGES);
-            if (!mbar_wait(&conv[s], (uint32_t)((g / STAGES) & 1), abort_flag)) {
+            if (!wait(&conv[s], (uint32_t)((g / STAGES) & 1))) {
               ok = false;
               break;
             }
@@ -522,7 +538,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // every product issued by this thread has retired once this fires
       umma_commit(drain);
-      mbar_wait(drain, 0, abort_flag, false);
+      mbar_wait(drain, 0, abort_flag, kDrainNs, false);
     }
   } else if (warp < 6) {
     // split warps: warp w takes TMEM lane quarter w % 4, one row of A a thread
@@ -537,8 +553,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int s = (int)(g % STAGES);
         const int slot = (int)(g % L::ASLOTS);
         const int64_t use = g / L::ASLOTS;
-        if ((use > 0 && !mbar_wait(&aempty[slot], (uint32_t)((use - 1) & 1), abort_flag)) ||
-            !mbar_wait(&full[s], (uint32_t)((g / STAGES) & 1), abort_flag)) {
+        if ((use > 0 && !wait(&aempty[slot], (uint32_t)((use - 1) & 1))) ||
+            !wait(&full[s], (uint32_t)((g / STAGES) & 1))) {
           ok = false;
           break;
         }
@@ -651,7 +667,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int nkb = d.kb1 - d.kb0;
       for (int r0 = 0; r0 < nkb; r0 += kFoldKb, rg++) {
         const int buf = (int)(rg % L::NBUF);
-        if (!mbar_wait(&tfull[buf], (uint32_t)((rg / L::NBUF) & 1), abort_flag)) {
+        if (!wait(&tfull[buf], (uint32_t)((rg / L::NBUF) & 1))) {
           ok = false;
           break;
         }
@@ -662,7 +678,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (MODE == MODE_F16) {
             // the split warps released this entry before the products of the
             // range were issued, so the wait does not block in practice
-            if (!mbar_wait(&xfull[rg % L::XRI], (uint32_t)((rg / L::XRI) & 1), abort_flag)) {
+            if (!wait(&xfull[rg % L::XRI], (uint32_t)((rg / L::XRI) & 1))) {
               ok = false;
               break;
             }
@@ -777,6 +793,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp >= 6 && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   tc_fence_before();
   __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag && a.err) atomicExch(a.err, 1);
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)L::TMEM_COLS));
@@ -980,6 +997,8 @@ bool make_map(CUtensorMap *tm, const void *base, int64_t cols, int64_t rows, int
   return r == CUDA_SUCCESS;
 }
 
+constexpr int kMaxDevices = 64;
+
 int tile_cols(int64_t N) {  // real columns per tile (power of two, 16..128)
   int64_t c = 2 * N;
   if (c < 16) c = 16;
@@ -999,16 +1018,27 @@ cudaError_t run_tc(const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensor
   // one CTA per SM: each allocates all of TMEM
   static_assert(L::TOTAL > 114 * 1024, "two CTAs would share an SM");
   auto kernel = tc_split3_kernel<MODE, BNP, STAGES>;
-  static int resident = 0;
-  if (!resident) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::TOTAL);
-    if (e != cudaSuccess) return e;
-    int dev = 0, n_sm = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 148;
-    resident = n_sm;
+  // the shared-memory attribute is set, and the SM count read, once per
+  // device (server threads may launch concurrently)
+  static std::mutex mu;
+  static int resident[kMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  int n_ctas = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!resident[dev]) {
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::TOTAL);
+      if (e != cudaSuccess) return e;
+      int n_sm = 0;
+      if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 148;
+      resident[dev] = n_sm;
+    }
+    n_ctas = resident[dev];
   }
-  kernel<<<(unsigned)std::min<int64_t>(n_tiles, resident), kThreads, L::TOTAL, s>>>(ta, tbh, tbl, tc, args);
+  kernel<<<(unsigned)std::min<int64_t>(n_tiles, n_ctas), kThreads, L::TOTAL, s>>>(ta, tbh, tbl, tc, args);
   return cudaGetLastError();
 }
 
@@ -1076,7 +1106,7 @@ size_t cgemm_tc_scratch_bytes(int precision, int64_t batch, int64_t M, int64_t N
 
 cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M,
                             int64_t N, int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc,
-                            void *scratch, size_t scratch_bytes, cudaStream_t s) {
+                            void *scratch, size_t scratch_bytes, int *err, cudaStream_t s) {
   if (!cgemm_tc_supported(precision, M, N, K)) return cudaErrorNotSupported;
   if (sA != M * K || sB != N * K) return cudaErrorNotSupported;  // contiguous batches only
   const int bnp = tile_cols(N);
@@ -1139,6 +1169,7 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
     if (e != cudaSuccess) return e;
   }
   TcArgs args{};
+  args.err = err;
   args.bmax = bmax;
   args.pb = pb;
   args.C = C;
@@ -1192,11 +1223,14 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
   return cudaGetLastError();
 }
 
-int tc_take_error() {
-  int v = 0, zero = 0;
-  if (cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int)) != cudaSuccess) return -1;
-  if (v) cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int));
-  return v;
+cudaError_t tc_set_wait_limit(unsigned long long ns) {
+  const unsigned long long v = ns ? ns : kWaitNs;
+  return cudaMemcpyToSymbol(g_wait_ns, &v, sizeof(v));
+}
+
+cudaError_t tc_set_stall(int on) {
+  const int v = on ? 1 : 0;
+  return cudaMemcpyToSymbol(g_stall, &v, sizeof(v));
 }
 
 }  // namespace dev

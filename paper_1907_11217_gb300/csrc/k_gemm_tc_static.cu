@@ -9,12 +9,16 @@
 // caller passes only its inputs and outputs.
 //
 // Costs and limits: every GPU that loads the library holds the array
-// (kStaticScratchBytes) until the process exits; products whose prepared B
-// needs more are rejected with TZ_EINVAL. All calls share the one array, so
-// calls that overlap on the GPU (different streams, or different host
-// threads) race on it; serialise them. The array keeps whatever the last
-// call wrote; nothing in it has to start at zero, because each call rewrites
-// every element it reads before reading it.
+// (kStaticScratchBytes) until the process exits; products whose scratch
+// needs more than the array holds (beside the call's error word) are
+// rejected with TZ_EINVAL. All calls share the one array, so calls that
+// overlap on the GPU (different streams, or different host threads) race on
+// it; serialise them. The array keeps whatever the last call wrote; the one
+// word that must start at zero, the call's error word, is cleared on the
+// stream at the start of every call, and every other element a call reads
+// it has written first. The array's device address is looked up once per
+// device and kept: resetting a device (cudaDeviceReset) after the first
+// call on it is not supported.
 #include <mutex>
 #include <string>
 
@@ -23,6 +27,7 @@
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB per device
+constexpr size_t kErrBytes = 256;                          // head: the call's error word
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
@@ -59,17 +64,39 @@ extern "C" int tz_op_cgemm_static(int precision, int64_t batch, int64_t m, int64
     if (!tz::dev::cgemm_tc_supported(precision, m, n, k))
       tz::fail(TZ_EUNSUPPORTED, "shape not supported by the tensor-core product");
     const size_t need = tz::dev::cgemm_tc_scratch_bytes(precision, batch, m, n, k);
-    if (need > kStaticScratchBytes)
+    if (need > kStaticScratchBytes - kErrBytes)
       tz::fail(TZ_EINVAL, "product needs " + std::to_string(need) + " bytes of scratch; the static scratch holds " +
-                              std::to_string(kStaticScratchBytes) + " (use tz_op_cgemm with caller scratch)");
+                              std::to_string(kStaticScratchBytes - kErrBytes) +
+                              " (use tz_op_cgemm with caller scratch)");
     int device = 0;
     tz::cuda_check(cudaGetDevice(&device), "cudaGetDevice");
     if (device < 0 || device >= kMaxDevices) tz::fail(TZ_EUNSUPPORTED, "device ordinal above 63");
-    void *scratch = scratch_address(device);
+    char *scratch = static_cast<char *>(scratch_address(device));
+    int *err = reinterpret_cast<int *>(scratch);
+    tz::cuda_check(cudaMemsetAsync(err, 0, sizeof(int), (cudaStream_t)stream), "clear error word");
     tz::cuda_check(tz::dev::launch_cgemm_tc(precision, (const float2 *)A, (const float2 *)B, (float2 *)C, batch, m, n,
-                                            k, sa, sb, sc, nullptr, scratch, kStaticScratchBytes,
-                                            (cudaStream_t)stream),
+                                            k, sa, sb, sc, nullptr, scratch + kErrBytes, kStaticScratchBytes - kErrBytes,
+                                            err, (cudaStream_t)stream),
                    "tensor-core gemm (static scratch)");
+  } catch (const tz::Error &e) {
+    tz_set_error_message(e.what());
+    return e.code;
+  } catch (const std::exception &e) {
+    tz_set_error_message(e.what());
+    return TZ_EINVAL;
+  }
+  return TZ_OK;
+}
+
+extern "C" int tz_op_cgemm_static_status(void *stream) {
+  try {
+    tz::cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "synchronise the stream");
+    int device = 0;
+    tz::cuda_check(cudaGetDevice(&device), "cudaGetDevice");
+    if (device < 0 || device >= kMaxDevices) tz::fail(TZ_EUNSUPPORTED, "device ordinal above 63");
+    int v = 0;
+    tz::cuda_check(cudaMemcpy(&v, scratch_address(device), sizeof(int), cudaMemcpyDeviceToHost), "read error word");
+    if (v) tz::fail(TZ_ETIMEOUT, "the last tensor-core product on the static scratch timed out in a bounded wait");
   } catch (const tz::Error &e) {
     tz_set_error_message(e.what());
     return e.code;

@@ -20,7 +20,10 @@ struct GroupState {
   int64_t lo, hi;        // slice range
   int64_t n_rows;        // bitstrings in the call
   int64_t groups_done;
-  int64_t pad[2];
+  int tc_error;          // set by a tensor-core product whose bounded wait ran
+                         // out; cleared when a call starts
+  int pad0;
+  int64_t pad[1];
 };
 
 // Device tables address tensors by region-relative byte offsets so that one
@@ -119,13 +122,17 @@ cudaError_t launch_cgemm_skinny_gather(const float2 *X, const float2 *Y, float2 
                                        int64_t N, int64_t K, const GatherMap &g, const CScatter *sc, cudaStream_t s);
 // Split-precision tensor-core product; returns cudaErrorNotSupported when the
 // shape is outside what the kernel handles (the planner checks first).
+// *err (device memory) is set to 1 when one of the product's bounded waits
+// runs out (its result is then invalid); the caller clears it.
 cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M,
                             int64_t N, int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc,
-                            void *scratch, size_t scratch_bytes, cudaStream_t s);
+                            void *scratch, size_t scratch_bytes, int *err, cudaStream_t s);
 bool cgemm_tc_supported(int precision, int64_t M, int64_t N, int64_t K);
-// Read and clear the flag a tensor-core kernel raises when a bounded wait
-// times out (synchronous; 1 = a wait gave up).
-int tc_take_error();
+// Test and debug hooks for the current device: the limit of the products'
+// bounded waits in ns (0 restores the default 2 s), and a switch that makes
+// every product first wait on a barrier that nothing arrives at.
+cudaError_t tc_set_wait_limit(unsigned long long ns);
+cudaError_t tc_set_stall(int on);
 // Device scratch of one tensor-core product: the prepared hi/lo copies of B,
 // for products that split K across CTAs the partial results, and in the FP16
 // mode the partial maxima of |B|.

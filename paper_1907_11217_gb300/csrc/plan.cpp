@@ -1,6 +1,7 @@
 // Plans: from (network, tree, sliced indices) to a launch schedule over one
 // device workspace. A group is one slice (Sec. 1: one subtask) for one chunk
 // of 2^batch_log2 bitstrings; every group runs the same launches.
+#include <chrono>
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -633,11 +634,12 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
   stt.max_log2 = ti.max_bits;
   for (int s = 0; s < NS; s++) {
     const StepInfo &st = ti.steps[s];
+    double fl = 8.0 * std::ldexp(1.0, st.bitsAll());
     if (!st.var) {
       stt.n_const_steps++;
+      stt.const_flops += fl;
       continue;
     }
-    double fl = 8.0 * std::ldexp(1.0, st.bitsAll());
     stt.flops_per_group += fl;
     stt.bytes_per_group +=
         (double)esz * (std::ldexp(1.0, st.bitsA()) + std::ldexp(1.0, st.bitsB()) + std::ldexp(1.0, st.bitsC()));
@@ -902,7 +904,8 @@ static void run_items(tz_plan *p, const std::vector<Item> &items, const RunCtx &
         } else if (ps.tc) {
           void *scr = abase + ps.tc_scratch_off;
           cuda_check(dev::launch_cgemm_tc(p->opts.precision, X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.M * ps.K,
-                                          ps.N * ps.K, ps.M * ps.N, sc, scr, (size_t)ps.tc_scratch, s),
+                                          ps.N * ps.K, ps.M * ps.N, sc, scr, (size_t)ps.tc_scratch, &gs->tc_error,
+                                          s),
                      "tensor-core gemm");
         } else {
           cuda_check(dev::launch_cgemm_simt(X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.M * ps.K, ps.N * ps.K,
@@ -948,6 +951,7 @@ static void clear_graphs(tz_plan *p) {
 }
 
 void plan_bind(tz_plan *p, void *ws, size_t bytes) {
+  const auto t_bind = std::chrono::steady_clock::now();
   if (!ws) fail(TZ_EINVAL, "workspace pointer is NULL");
   if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) fail(TZ_EINVAL, "workspace must be 256-byte aligned");
   if (bytes < p->total_bytes)
@@ -1006,9 +1010,21 @@ void plan_bind(tz_plan *p, void *ws, size_t bytes) {
                  "upload constants");
     cuda_check(cudaStreamSynchronize(s), "sync");  // host buffer is reused
   }
+  auto *gs = reinterpret_cast<dev::GroupState *>(default_ctx(p).scratch + p->s_gs);
+  cuda_check(cudaMemsetAsync(&gs->tc_error, 0, sizeof(int), s), "clear error word");
   run_items(p, p->const_items, default_ctx(p));
   cuda_check(cudaStreamSynchronize(s), "bind-time steps");
+  if (read_tc_error(p, default_ctx(p)))
+    fail(TZ_ETIMEOUT, "a tensor-core product of the bind-time steps timed out in a bounded wait");
+  p->stats.bind_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_bind).count();
   p->bound = true;
+}
+
+int read_tc_error(const tz_plan *p, const RunCtx &ctx) {
+  int v = 0;
+  const auto *gs = reinterpret_cast<const dev::GroupState *>(ctx.scratch + p->s_gs);
+  cuda_check(cudaMemcpy(&v, &gs->tc_error, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
+  return v;
 }
 
 void plan_run(tz_plan *p, const RunCtx &ctx, int64_t n_rows, int64_t lo, int64_t hi) {

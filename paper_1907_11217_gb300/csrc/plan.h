@@ -119,6 +119,10 @@ void plan_bind(tz_plan *p, void *ws, size_t bytes);
 // (asynchronous on ctx.stream). With use_graph, the launches of a group are
 // captured once per scratch part and replayed.
 void plan_run(tz_plan *p, const RunCtx &ctx, int64_t n_rows, int64_t lo, int64_t hi);
+// The error word of a scratch part: 1 when a tensor-core product of the last
+// call on it (or of the bind-time steps) timed out in a bounded wait.
+// Synchronous (reads device memory); call after the stream has finished.
+int read_tc_error(const tz_plan *p, const RunCtx &ctx);
 void plan_destroy(tz_plan *p);
 void plan_profile_collect(tz_plan *p);
 void item_cost_public(const tz_plan *p, int var_item, int *kind, double *flops, double *bytes);

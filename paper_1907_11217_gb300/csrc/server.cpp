@@ -109,7 +109,8 @@ struct tz_server {
     Slot &sl = slots[s];
     tz_plan *p = q.plan;
     const int nq = p->net.n_qubits;
-    ensure_pinned(sl, (size_t)q.n * nq, (size_t)q.n * 16);
+    // pinned out: the amplitudes, then the scratch part's error word
+    ensure_pinned(sl, (size_t)q.n * nq, (size_t)q.n * 16 + 16);
     std::memcpy(sl.pin_in, q.bits.data(), (size_t)q.n * nq);
     char *scratch = static_cast<char *>(opts.arena) + q.arena_off;
     tz::RunCtx ctx{scratch, sl.stream};
@@ -120,6 +121,10 @@ struct tz_server {
     tz::cuda_check(cudaMemcpyAsync(sl.pin_out, scratch + p->s_acc, (size_t)q.n * 16, cudaMemcpyDeviceToHost,
                                    sl.stream),
                    "query amplitudes out");
+    const auto *gs = reinterpret_cast<const tz::dev::GroupState *>(scratch + p->s_gs);
+    tz::cuda_check(cudaMemcpyAsync(sl.pin_out + 2 * q.n, &gs->tc_error, sizeof(int), cudaMemcpyDeviceToHost,
+                                   sl.stream),
+                   "query error word out");
     tz::cuda_check(cudaEventRecord(sl.done, sl.stream), "query event");
     sl.ticket = q.ticket;
     q.slot = s;
@@ -133,7 +138,13 @@ struct tz_server {
       cudaError_t e = cudaEventQuery(sl.done);
       if (e == cudaErrorNotReady) continue;
       Query &q = queries[sl.ticket];
-      if (e == cudaSuccess) {
+      int tc_error = 0;
+      if (e == cudaSuccess) std::memcpy(&tc_error, sl.pin_out + 2 * q.n, sizeof(int));
+      if (e == cudaSuccess && tc_error) {
+        q.state = Q_FAILED;
+        q.err = TZ_ETIMEOUT;
+        q.msg = "a tensor-core product of this query timed out in a bounded wait";
+      } else if (e == cudaSuccess) {
         q.out.assign(sl.pin_out, sl.pin_out + 2 * q.n);
         q.state = Q_DONE;
       } else {

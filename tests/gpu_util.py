@@ -37,3 +37,10 @@ def make_plan(tz, spec, batch_log2=0, log2_max=0, precision="c64", small_log2=0,
 
 def grid_spec(rows, cols, t, seed):
     return ti.circuit_to_spec(rows * cols, ti.generate_circuit(ti.grid(rows, cols), t, seed))
+
+
+def rel_err_partial(got, ref, n_qubits, k):
+    """rel_err for the partial amplitude of one of 2^k slices: the partials
+    of random circuits sit near 2^(-(n+k)/2) (2^k terms of random phase add
+    up to an amplitude of 2^(-n/2)), which is the floor here."""
+    return rel_err(got, ref, n_qubits + k)

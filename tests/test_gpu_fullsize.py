@@ -1,10 +1,12 @@
 """Full-size checks on the benchmark workloads.
 
-The FP64 oracle cannot contract a slice of a depth 1+32+1 circuit on 49 or 70
-qubits in test time (its own contraction orders would need 2^13 - 2^24
-sub-slices), so at full depth the path is checked by properties that hold at
-any size, in the launch configuration bench.py times (bucket-elimination
-tree, 2^30 cap, captured graph on a stream):
+At full depth (1+32+1) the FP64 path-sum oracle reaches single slices: the
+GPU's partial amplitudes of sampled slices are compared with it, element by
+element, on config 2 (7x7, 2^10 slices) and on the tree bench.py times for
+Bristlecone-70, sliced further so that one slice fits the oracle. Beyond
+sampled slices, the path is checked by properties that hold at any size, in
+the launch configuration bench.py times (bucket-elimination tree, 2^30 cap,
+captured graph on a stream):
 
 * slicing is exact: the partial amplitudes of the slices add up to the full
   amplitude (Sec. 1: subtask results add up to the amplitude);
@@ -25,8 +27,8 @@ import numpy as np
 import pytest
 
 import tz_inputs as ti
-from oracle import tn
-from tests.gpu_util import rel_err
+from oracle import pathsum, tn
+from tests.gpu_util import rel_err, rel_err_partial
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -285,3 +287,81 @@ def test_grid7x7_depth40_precision_sweep(tz):
     print("grid7x7 d40 (32 of 2^14 slices) errors vs complex128:", {m: f"{e:.2e}" for m, e in errs.items()})
     # measured on GB300: c64 1.5e-7, tf32x3 4.9e-7, bf16x3 6.5e-7
     assert errs["c64"] <= 1e-5 and errs["tf32x3"] <= 3e-5 and errs["bf16x3"] <= 1e-4 and errs["fp16x3"] <= 3e-5
+
+
+# -------------------------------------------------------------------------
+# Full depth against the FP64 oracle, per sampled slice (Sec. 1: each
+# subtask's partial amplitude is a fixed piece of the amplitude, so the
+# GPU's and the oracle's partial of the same slice must agree)
+
+PARTIAL_TOL = {"c64": 1e-5, "tf32x3": 1e-5, "fp16x3": 1e-5, "bf16x3": 3e-5, "c128": 1e-12}
+
+
+def _partials(tz, net, tree, sliced, prec, bits, slices):
+    import torch
+    plan = tz.tz_plan_create(net, tree, sliced, precision=prec, stream=torch.cuda.Stream(), use_graph=True,
+                             max_bitstrings=len(bits))
+    plan.bind()
+    out = {}
+    for s in slices:
+        plan.set_slice_range(s, s + 1)
+        out[s] = tz.tz_contract_amplitudes(plan, bits)
+    segs = plan.sliced_segments()
+    plan.close()
+    return out, segs
+
+
+def test_grid7x7_depth32_config2_slices_vs_oracle(tz):
+    """Config 2: 7x7, depth 1+32+1, a tree with 2^10 slices; the partial
+    amplitudes of slices 0 and 777 for two of the config's bitstrings in
+    every mode against the path-sum oracle with the plan's sliced segments."""
+    spec = grid_spec(7, 7, 32, 2)
+    bits = ti.random_bitstrings(49, 64, 102)[:2]
+    net = tz.tz_network_from_circuit(tz.tz_circuit_from_spec(spec), 0)
+    tree = tz.tz_path_greedy(net, restarts=32, seed=7, log2_max_intermediate=22, precision="tf32x3",
+                             algorithm="elimination")
+    sl = tz.tz_slice_select(net, tree, 1, 10)
+    assert len(sl) == 10
+    slices = (0, 777)
+    got, segs = {}, None
+    for prec in ("c64", "tf32x3", "fp16x3", "bf16x3", "c128"):
+        got[prec], segs = _partials(tz, net, tree, sl, prec, bits, slices)
+    oracle = pathsum.SegmentContractor(spec, sliced=segs, max_log2=25)
+    ref = {s: np.array([oracle.partial(x, s) for x in bits]) for s in slices}
+    errs = {m: max(rel_err_partial(got[m][s], ref[s], 49, 10) for s in slices) for m in got}
+    print("grid7x7 d32 config 2, slices 0 and 777 vs oracle:", {m: f"{e:.2e}" for m, e in errs.items()})
+    for m, e in errs.items():
+        assert e <= PARTIAL_TOL[m], (m, e)
+
+
+@pytest.fixture(scope="module")
+def bench_tree(tz):
+    """The Bristlecone-70 depth 1+32+1 tree bench.py times (16384 restarts,
+    seed 7, 2^30 cap, elimination, split-BF16 time model)."""
+    spec = bris_spec(32, 3)
+    net = tz.tz_network_from_circuit(tz.tz_circuit_from_spec(spec), 0)
+    tree = tz.tz_path_greedy(net, restarts=16384, seed=7, log2_max_intermediate=30, precision="bf16x3",
+                             algorithm="elimination")
+    return spec, net, tree
+
+
+@pytest.mark.parametrize("cap,slices", [(20, (5,)), (18, (0, 1 << 20, 987654))])
+def test_bristlecone70_depth32_bench_tree_slices_vs_oracle(tz, bench_tree, cap, slices):
+    """The bench's Bristlecone-70 tree, sliced to a 2^cap cap (k = 12 and
+    k = 21) so that one slice is within the oracle's reach: partial amplitudes
+    of sampled slices in every mode against the path-sum oracle."""
+    spec, net, tree = bench_tree
+    bits = ti.random_bitstrings(70, 1, 103)
+    sl = tz.tz_slice_select(net, tree, cap, 40)
+    k = len(sl)
+    assert k >= 10
+    got, segs = {}, None
+    for prec in ("c64", "tf32x3", "fp16x3", "bf16x3", "c128"):
+        got[prec], segs = _partials(tz, net, tree, sl, prec, bits, slices)
+    oracle = pathsum.SegmentContractor(spec, sliced=segs, max_log2=25)
+    ref = {s: np.array([oracle.partial(bits[0], s)]) for s in slices}
+    errs = {m: max(rel_err_partial(got[m][s], ref[s], 70, k) for s in slices) for m in got}
+    print(f"bristlecone70 d32 bench tree, cap 2^{cap} (k={k}), slices {slices} vs oracle:",
+          {m: f"{e:.2e}" for m, e in errs.items()})
+    for m, e in errs.items():
+        assert e <= PARTIAL_TOL[m], (m, e)
