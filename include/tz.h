@@ -377,6 +377,15 @@ int tz_op_cgemm_static_status(void *stream);
 int tz_debug_set_wait_limit(int64_t ns);
 int tz_debug_stall_tensor_core(int on);
 
+/* Process-wide default of how the split BF16 / FP16 products run where the
+ * shape allows pairs (128-column tiles, m a multiple of 256): 1 on pairs of
+ * CTAs on two SMs (cta_group::2, each CTA loading half of the B tile), 0 on
+ * single CTAs, -1 back to the initial default (pairs, unless the environment
+ * variable TZ_TC_PAIRS is 0). Plans autotuned at bind time keep their own
+ * per-step choice. Results are the same either way up to the order of FP32
+ * additions inside a k-block. */
+int tz_tune_tc_pairs(int mode);
+
 /* FP64 accumulation of partial amplitudes: acc[j] += scale * part[j] for
  * j < n, with part complex64 and acc, scale complex128 (re, im). */
 int tz_op_accumulate(const void *part, double *acc, int64_t n, double scale_re, double scale_im, void *stream);

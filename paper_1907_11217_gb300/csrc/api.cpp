@@ -582,6 +582,12 @@ int tz_debug_set_wait_limit(int64_t ns) {
   TZ_CATCH
 }
 
+int tz_tune_tc_pairs(int mode) {
+  TZ_TRY
+  tz::dev::tc_set_pairs(mode);
+  TZ_CATCH
+}
+
 int tz_debug_stall_tensor_core(int on) {
   TZ_TRY
   tz::cuda_check(tz::dev::tc_set_stall(on), "set stall switch");

@@ -42,6 +42,8 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -124,6 +126,70 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
   }
 }
 
+// Wait variant for barriers that CTAs of a cluster arrive on (acquire at
+// cluster scope, so the peer's released writes are visible).
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, "
+      "p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+template <bool CLUSTER>
+__device__ __forceinline__ bool mbar_wait_t(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                            unsigned long long limit_ns, bool honour_abort = true) {
+  if (!CLUSTER) return mbar_wait(bar, parity, abort_flag, limit_ns, honour_abort);
+  unsigned long long t0 = 0;
+  for (uint32_t i = 0;; i++) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    if (honour_abort && *abort_flag) return false;
+    if ((i & 255) == 255) {
+      const unsigned long long now = globaltimer();
+      if (t0 == 0) {
+        t0 = now;
+      } else if (now - t0 > limit_ns) {
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+
+// Thread-block clusters of two CTAs (a pair shares one 256-row tile).
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t n_clusters_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of the same shared-memory location in CTA `rank`
+__device__ __forceinline__ uint32_t cluster_addr(const void *p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t caddr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+}
+__device__ __forceinline__ void st_remote_u32(uint32_t caddr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(caddr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // L2 policies for the TMA loads: B tiles are read by every row tile, so they
 // are kept (evict last); A tiles are read by the few CTAs of one row tile at
 // about the same time, then not again (evict first).
@@ -172,6 +238,22 @@ __device__ __forceinline__ void umma_f16_ts(uint32_t tmem_d, uint32_t tmem_a, ui
 }
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// Pair products (cta_group::2, issued by the pair's first CTA): M = 256 rows,
+// rows 0..127 of A and of the accumulator in the first CTA's tensor memory,
+// rows 128..255 in the second's (same addresses); the first BNP/2 rows of B
+// in the first CTA's shared memory, the rest in the second's (same offset).
+__device__ __forceinline__ void umma_f16_ts_pair(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc,
+                                                 uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::
+          "r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(idesc), "r"(accum));
+}
+// Commit of the pair's products to a barrier in either CTA of the pair.
+__device__ __forceinline__ void umma_commit_pair(uint32_t caddr) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(caddr)
                : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -271,13 +353,14 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
-// FP32 accumulator, BF16 A and B, both K-major, N = n_cols, M = 128.
-__host__ __device__ constexpr uint32_t idesc_bf16(int n_cols) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n_cols >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// FP32 accumulator, BF16 A and B, both K-major, N = n_cols, M = m (128, or
+// 256 for a pair).
+__host__ __device__ constexpr uint32_t idesc_bf16(int n_cols, int m = BM) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n_cols >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
-// FP32 accumulator, FP16 A and B (format 0), both K-major, N = n_cols, M = 128.
-__host__ __device__ constexpr uint32_t idesc_f16(int n_cols) {
-  return (1u << 4) | ((uint32_t)(n_cols >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// FP32 accumulator, FP16 A and B (format 0), both K-major, N = n_cols, M = m.
+__host__ __device__ constexpr uint32_t idesc_f16(int n_cols, int m = BM) {
+  return (1u << 4) | ((uint32_t)(n_cols >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 enum TcMode { MODE_TF32 = 0, MODE_BF16 = 1, MODE_F16 = 2 };
@@ -332,11 +415,11 @@ __host__ __device__ constexpr int fold_k() { return MODE == MODE_F16 ? 64 : kFol
 // FP16 mode: a ring of XR x 128 scale exponents of A (one per row and
 // k-block), written by the split warps and read by the epilogue, each ring
 // entry with its own barrier.
-template <int MODE, int BNP, int STAGES>
+template <int MODE, int BNP, int STAGES, int CG = 1>
 struct TcSmem {
   static constexpr uint32_t A_BYTES = BM * stage_k<MODE>() * 4;         // FP32 tile as loaded (boxes of 128-byte rows)
   static constexpr uint32_t BROW = 128;                                  // bytes per split B row
-  static constexpr uint32_t B_BYTES = BNP * BROW;
+  static constexpr uint32_t B_BYTES = (BNP / CG) * BROW;                 // a pair: this CTA's half of the rows
   static constexpr uint32_t SLOT_COLS = 64;                              // TMEM columns of a split A tile
   static constexpr uint32_t STAGE = A_BYTES + 2 * B_BYTES;
   static constexpr int EC = BNP >= 32 ? BNP / 2 : BNP;                // real columns per epilogue warp
@@ -366,11 +449,18 @@ struct TcSmem {
 // (batch-major, then row tile, then column tile, so CTAs working at the same
 // time share A tiles in L2). The stage ring and the accumulator ring run on
 // across tiles.
-template <int MODE, int BNP, int STAGES>
+// CG = 2: clusters of two CTAs on two SMs work as a pair on tiles of 256
+// rows (cta_group::2 products issued by the first CTA): each CTA loads its
+// own 128 rows of A and half of the B tile, so each SM takes in half the B
+// bytes per product of the 1-CTA form. The split and epilogue warps of each
+// CTA serve its own rows; the pair signals across the cluster (remote
+// barrier arrivals, commits to both CTAs' barriers).
+template <int MODE, int BNP, int STAGES, int CG>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_split3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
                      const __grid_constant__ CUtensorMap tmBl, const __grid_constant__ CUtensorMap tmC, TcArgs a) {
-  using L = TcSmem<MODE, BNP, STAGES>;
+  using L = TcSmem<MODE, BNP, STAGES, CG>;
+  static_assert(CG == 1 || (MODE != MODE_TF32 && BNP == 128), "pairs: split BF16 / FP16, 128-column tiles");
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * L::STAGE + L::STAGING);
@@ -395,9 +485,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t per_batch = (int64_t)a.n_tiles_m * a.n_tiles_n;
   const int64_t n_tiles = per_batch * a.batch * a.ksplit;
+  // tile walkers: CTAs, or pairs of CTAs (clusters)
+  const uint32_t rank = CG == 2 ? cluster_rank() : 0u;
+  const int64_t walker = CG == 2 ? (int64_t)cluster_id_x() : (int64_t)blockIdx.x;
+  const int64_t n_walkers = CG == 2 ? (int64_t)n_clusters_x() : (int64_t)gridDim.x;
   struct Tile {
     int64_t z;
     int mt, nt, rowA, rowB, ks, kb0, kb1;
+    int64_t row0;  // first row of this CTA's part of the tile within its batch
   };
   auto decode = [&](int64_t t) {
     Tile d;
@@ -409,20 +504,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t rem = t - d.z * per_batch;
     d.mt = (int)(rem / a.n_tiles_n);
     d.nt = (int)(rem % a.n_tiles_n);
-    d.rowA = (int)(d.z * a.M + (int64_t)d.mt * BM);
-    d.rowB = (int)(d.z * a.NT + (int64_t)d.nt * BNP);
+    d.row0 = (int64_t)d.mt * (BM * CG) + (int64_t)rank * BM;
+    d.rowA = (int)(d.z * a.M + d.row0);
+    d.rowB = (int)(d.z * a.NT + (int64_t)d.nt * BNP + (int64_t)rank * (BNP / CG));
     return d;
   };
 
   if (threadIdx.x == 0) {
+    // pairs: conv and tempty are counted per warp (one elected arrival of
+    // each split or epilogue warp of both CTAs) on the first CTA's barriers
     for (int s = 0; s < STAGES; s++) {
       mbar_init(&full[s], 1);
-      mbar_init(&conv[s], 128);
+      mbar_init(&conv[s], CG == 2 ? 8 : 128);
       mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < L::NBUF; b++) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 256);
+      mbar_init(&tempty[b], CG == 2 ? 16 : 256);
     }
     mbar_init(drain, 1);
     for (int b = 0; b < L::ASLOTS; b++) mbar_init(&aempty[b], 1);
@@ -432,9 +530,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"((uint32_t)L::TMEM_COLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    // a pair allocates collectively: one warp of each CTA, the same columns
+    if constexpr (CG == 2) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"((uint32_t)L::TMEM_COLS));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"((uint32_t)L::TMEM_COLS));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
   }
   if (MODE == MODE_F16 && warp == 2) {
     // B's exponent: reduce the partial maxima written by absmax_kernel
@@ -446,17 +551,24 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
+  // a pair: the peer's barriers are initialised before anyone arrives on them
+  if constexpr (CG == 2) cluster_sync_all();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const unsigned long long wait_ns = g_wait_ns;
-  auto wait = [&](uint64_t *bar, uint32_t parity) { return mbar_wait(bar, parity, abort_flag, wait_ns); };
+  // a wait that gives up (timeout, or an abort) also stops the peer CTA
+  auto wait = [&](uint64_t *bar, uint32_t parity) {
+    const bool ok = mbar_wait_t<CG == 2>(bar, parity, abort_flag, wait_ns);
+    if (CG == 2 && !ok) st_remote_u32(cluster_addr((const void *)abort_flag, rank ^ 1u), 1u);
+    return ok;
+  };
 
   if (warp == 0) {
     if (lane == 0) {
       const uint64_t keep = l2_evict_last(), stream = l2_evict_first();
       int64_t g = 0;  // k-blocks issued by this CTA
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+      for (int64_t t = walker; t < n_tiles && ok; t += n_walkers) {
         const Tile d = decode(t);
         for (int kb = d.kb0; kb < d.kb1; kb++, g++) {
           const int s = (int)(g % STAGES);
@@ -477,13 +589,28 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (*abort_flag) {
         // drain: let the copies already issued land before the CTA exits
         for (int64_t q = g > STAGES ? g - STAGES : 0; q < g; q++)
-          mbar_wait(&full[q % STAGES], (uint32_t)((q / STAGES) & 1), abort_flag, kDrainNs, false);
+          mbar_wait_t<CG == 2>(&full[q % STAGES], (uint32_t)((q / STAGES) & 1), abort_flag, kDrainNs, false);
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      constexpr uint32_t idesc =
-          MODE == MODE_TF32 ? idesc_tf32(BNP) : (MODE == MODE_BF16 ? idesc_bf16(BNP) : idesc_f16(BNP));
+    if (lane == 0 && CG == 2 && rank != 0) {
+      // the pair's second CTA issues no products: it waits until the first
+      // CTA's products (which use its tensor and shared memory) have retired
+      mbar_wait_t<true>(drain, 0, abort_flag, kDrainNs, false);
+    } else if (lane == 0) {
+      constexpr uint32_t idesc = MODE == MODE_TF32   ? idesc_tf32(BNP)
+                                 : MODE == MODE_BF16 ? idesc_bf16(BNP, BM * CG)
+                                                     : idesc_f16(BNP, BM * CG);
+      // commit to a barrier of this CTA and, for a pair, the same barrier of
+      // the peer
+      auto commit = [&](uint64_t *bar) {
+        if constexpr (CG == 2) {
+          umma_commit_pair(cluster_addr(bar, 0));
+          umma_commit_pair(cluster_addr(bar, 1));
+        } else {
+          umma_commit(bar);
+        }
+      };
       // K per instruction: 8 TF32 or 16 BF16 values (32 bytes of a B row,
       // 8 TMEM columns of A)
       constexpr int kSteps = stage_k<MODE>() / (MODE == MODE_TF32 ? 8 : 16);
@@ -491,7 +618,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int64_t g = 0, rg = 0;  // k-blocks and accumulation ranges issued
       // test stall: a bounded wait on a barrier nothing arrives at
       bool ok = !g_stall || wait(stall, 0);
-      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+      for (int64_t t = walker; t < n_tiles && ok; t += n_walkers) {
         const Tile d = decode(t);
         const int nkb = d.kb1 - d.kb0;
         for (int r0 = 0; r0 < nkb; r0 += kFoldKb, rg++) {
@@ -523,22 +650,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                 umma_tf32_ts(d_acc, ah + kk * 8, dbh, idesc, acc);
                 umma_tf32_ts(d_acc, ah + kk * 8, dbl, idesc, 1);
                 umma_tf32_ts(d_acc, al + kk * 8, dbh, idesc, 1);
+              } else if (CG == 2) {
+                umma_f16_ts_pair(d_acc, ah + kk * 8, dbh, idesc, acc);
+                umma_f16_ts_pair(d_acc, ah + kk * 8, dbl, idesc, 1);
+                umma_f16_ts_pair(d_acc, al + kk * 8, dbh, idesc, 1);
               } else {
                 umma_f16_ts(d_acc, ah + kk * 8, dbh, idesc, acc);
                 umma_f16_ts(d_acc, ah + kk * 8, dbl, idesc, 1);
                 umma_f16_ts(d_acc, al + kk * 8, dbh, idesc, 1);
               }
             }
-            umma_commit(&empty[s]);
-            umma_commit(&aempty[slot]);
+            commit(&empty[s]);
+            commit(&aempty[slot]);
           }
           if (!ok) break;
-          umma_commit(&tfull[buf]);
+          commit(&tfull[buf]);
         }
       }
       // every product issued by this thread has retired once this fires
-      umma_commit(drain);
-      mbar_wait(drain, 0, abort_flag, kDrainNs, false);
+      // (for a pair, in both CTAs)
+      commit(drain);
+      mbar_wait_t<CG == 2>(drain, 0, abort_flag, kDrainNs, false);
     }
   } else if (warp < 6) {
     // split warps: warp w takes TMEM lane quarter w % 4, one row of A a thread
@@ -547,7 +679,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16) + L::A_COL0;
     int64_t g = 0;
     bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    for (int64_t tile = walker; tile < n_tiles && ok; tile += n_walkers) {
       const Tile d = decode(tile);
       for (int kb = 0; kb < d.kb1 - d.kb0; kb++, g++) {
         const int s = (int)(g % STAGES);
@@ -630,7 +762,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tmem_st_wait();
         tc_fence_before();
-        mbar_arrive(&conv[s]);
+        if constexpr (CG == 2) {
+          // one arrival per warp on the first CTA's barrier: this CTA's
+          // stage (its A rows and B half) has landed and its A is split
+          __syncwarp();
+          if (lane == 0) mbar_arrive_remote(cluster_addr(&conv[s], 0));
+        } else {
+          mbar_arrive(&conv[s]);
+        }
         if (MODE == MODE_F16) mbar_arrive(&xfull[g % L::XRI]);  // releases the exponent written above
       }
     }
@@ -653,7 +792,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const float ub = MODE == MODE_F16 ? pow2i(-scale_exp[1]) : 1.f;
     int64_t rg = 0;
     bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    for (int64_t tile = walker; tile < n_tiles && ok; tile += n_walkers) {
       const Tile d = decode(tile);
       const int64_t n0 = (int64_t)d.nt * (BNP / 2) + c0 / 2;  // first complex column of this warp
       if (a.scatter && active) {
@@ -698,7 +837,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         tc_fence_before();
-        mbar_arrive(&tempty[buf]);
+        if constexpr (CG == 2) {
+          __syncwarp();
+          if (lane == 0) mbar_arrive_remote(cluster_addr(&tempty[buf], 0));
+        } else {
+          mbar_arrive(&tempty[buf]);
+        }
       }
       if (!ok) break;
       if (!active) continue;
@@ -713,7 +857,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // x 4 column pairs (lane: row 8 u + lane / 4, pair lane % 4). A pair
         // is 16 contiguous bytes because n bit 0 is the lowest bit of C; when
         // n bits 1 and 2 follow it, a row's 4 pairs are 64 contiguous bytes.
-        const int64_t om = scatter_bits(d.z, a.sc.nb, a.sc.pb) + scatter_bits((int64_t)d.mt * BM + row, a.sc.nm, a.sc.pm);
+        const int64_t om = scatter_bits(d.z, a.sc.nb, a.sc.pb) + scatter_bits(d.row0 + row, a.sc.nm, a.sc.pm);
         int64_t om_u[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) om_u[u] = __shfl_sync(0xffffffffu, om, 8 * u + (lane >> 2));
@@ -738,7 +882,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       } else if (a.scatter) {
-        const int64_t om = scatter_bits(d.z, a.sc.nb, a.sc.pb) + scatter_bits((int64_t)d.mt * BM + row, a.sc.nm, a.sc.pm);
+        const int64_t om = scatter_bits(d.z, a.sc.nb, a.sc.pb) + scatter_bits(d.row0 + row, a.sc.nm, a.sc.pm);
 #pragma unroll
         for (int j = 0; j < EC / 2; j++)
           if (n0 + j < a.N) a.C[om + coloff[j]] = make_float2(acc[2 * j], acc[2 * j + 1]);
@@ -747,7 +891,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // staging buffer in the 64-byte swizzled layout (16-byte chunk c of
         // row r at chunk c ^ ((r >> 1) & 3)), then one bulk tensor store.
         uint8_t *buf = staging + e * 2048;
-        const int y = (int)(d.z * a.M + (int64_t)d.mt * BM + q * 32);
+        const int y = (int)(d.z * a.M + d.row0 + q * 32);
 #pragma unroll
         for (int c = 0; c < EC; c += 16) {
           if (n0 + c / 2 < a.N) {
@@ -772,7 +916,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       } else {
-        float2 *crow = a.C + d.ks * a.split_stride + d.z * a.sC + ((int64_t)d.mt * BM + row) * a.N;
+        float2 *crow = a.C + d.ks * a.split_stride + d.z * a.sC + (d.row0 + row) * a.N;
 #pragma unroll
         for (int c = 0; c < EC; c += 16) {
           const int64_t nb = n0 + c / 2;
@@ -794,9 +938,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x == 0 && *abort_flag && a.err) atomicExch(a.err, 1);
+  // a pair: neither CTA leaves (or frees tensor memory) while the other may
+  // still arrive on its barriers
+  if constexpr (CG == 2) cluster_sync_all();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)L::TMEM_COLS));
+    if constexpr (CG == 2)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)L::TMEM_COLS));
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)L::TMEM_COLS));
   }
 }
 
@@ -999,6 +1149,19 @@ bool make_map(CUtensorMap *tm, const void *base, int64_t cols, int64_t rows, int
 
 constexpr int kMaxDevices = 64;
 
+// Pairs of CTAs for the products that allow them: the process-wide default
+// (tc_set_pairs; initially on unless the environment variable TZ_TC_PAIRS is
+// 0), which a launch's own choice (autotuned) overrides.
+std::atomic<int> g_pairs{-1};
+bool tc_pairs_default() {
+  int v = g_pairs.load(std::memory_order_relaxed);
+  if (v < 0) {
+    const char *e = std::getenv("TZ_TC_PAIRS");
+    v = (e && e[0] == '0') ? 0 : 1;
+  }
+  return v != 0;
+}
+
 int tile_cols(int64_t N) {  // real columns per tile (power of two, 16..128)
   int64_t c = 2 * N;
   if (c < 16) c = 16;
@@ -1008,51 +1171,75 @@ int tile_cols(int64_t N) {  // real columns per tile (power of two, 16..128)
   return (int)p;
 }
 
-// Launches the persistent kernel on at most one CTA per tile, as many as are
-// resident at once (one per SM).
-template <int MODE, int BNP, int STAGES>
+// Launches the persistent kernel on at most one CTA per tile (CG = 2: one
+// pair per tile), as many as are resident at once (one CTA per SM).
+template <int MODE, int BNP, int STAGES, int CG>
 cudaError_t run_tc(const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensorMap &tbl, const CUtensorMap &tc,
                    const TcArgs &args, int64_t n_tiles, cudaStream_t s) {
-  using L = TcSmem<MODE, BNP, STAGES>;
+  using L = TcSmem<MODE, BNP, STAGES, CG>;
   static_assert(L::TOTAL <= 227 * 1024, "shared memory budget");
   // one CTA per SM: each allocates all of TMEM
   static_assert(L::TOTAL > 114 * 1024, "two CTAs would share an SM");
-  auto kernel = tc_split3_kernel<MODE, BNP, STAGES>;
-  // the shared-memory attribute is set, and the SM count read, once per
-  // device (server threads may launch concurrently)
+  auto kernel = tc_split3_kernel<MODE, BNP, STAGES, CG>;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = L::TOTAL;
+  cfg.stream = s;
+  if (CG == 2) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  // the shared-memory attribute is set, and the number of resident CTAs (or
+  // pairs) read, once per device (server threads may launch concurrently)
   static std::mutex mu;
   static int resident[kMaxDevices] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  int n_ctas = 0;
+  int walkers = 0;
   {
     std::lock_guard<std::mutex> lk(mu);
     if (!resident[dev]) {
       e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::TOTAL);
       if (e != cudaSuccess) return e;
-      int n_sm = 0;
-      if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 148;
-      resident[dev] = n_sm;
+      int n = 0;
+      if (CG == 2) {
+        cfg.gridDim = dim3(2);
+        if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess || n <= 0) n = 0;
+      } else if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+        n = 148;
+      }
+      if (n <= 0) return cudaErrorLaunchOutOfResources;
+      resident[dev] = n;
     }
-    n_ctas = resident[dev];
+    walkers = resident[dev];
   }
-  kernel<<<(unsigned)std::min<int64_t>(n_tiles, n_ctas), kThreads, L::TOTAL, s>>>(ta, tbh, tbl, tc, args);
+  cfg.gridDim = dim3((unsigned)(CG * std::min<int64_t>(n_tiles, walkers)));
+  e = cudaLaunchKernelEx(&cfg, kernel, ta, tbh, tbl, tc, args);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 template <int MODE>
-cudaError_t dispatch(int bnp, const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensorMap &tbl,
+cudaError_t dispatch(int bnp, int cg, const CUtensorMap &ta, const CUtensorMap &tbh, const CUtensorMap &tbl,
                      const CUtensorMap &tc, const TcArgs &args, int64_t n_tiles, cudaStream_t s) {
   // stages: at most what fits beside the epilogue staging (and at most 8);
   // for the 128-column tiles, the counts measured fastest
   constexpr bool T = MODE == MODE_TF32;
+  if constexpr (!T) {
+    if (cg == 2) return run_tc<MODE, 128, 4, 2>(ta, tbh, tbl, tc, args, n_tiles, s);
+  }
   switch (bnp) {
-    case 16: return run_tc<MODE, 16, T ? 8 : 5>(ta, tbh, tbl, tc, args, n_tiles, s);
-    case 32: return run_tc<MODE, 32, T ? 7 : 5>(ta, tbh, tbl, tc, args, n_tiles, s);
-    case 64: return run_tc<MODE, 64, T ? 5 : 4>(ta, tbh, tbl, tc, args, n_tiles, s);
-    default: return run_tc<MODE, 128, T ? 4 : 3>(ta, tbh, tbl, tc, args, n_tiles, s);
+    case 16: return run_tc<MODE, 16, T ? 8 : 5, 1>(ta, tbh, tbl, tc, args, n_tiles, s);
+    case 32: return run_tc<MODE, 32, T ? 7 : 5, 1>(ta, tbh, tbl, tc, args, n_tiles, s);
+    case 64: return run_tc<MODE, 64, T ? 5 : 4, 1>(ta, tbh, tbl, tc, args, n_tiles, s);
+    default: return run_tc<MODE, 128, T ? 4 : 3, 1>(ta, tbh, tbl, tc, args, n_tiles, s);
   }
 }
 
@@ -1104,9 +1291,15 @@ size_t cgemm_tc_scratch_bytes(int precision, int64_t batch, int64_t M, int64_t N
   return 2 * half + ((part + 255) & ~size_t(255)) + bmax + 256;
 }
 
+bool tc_pair_supported(int precision, int64_t M, int64_t N) {
+  return (precision == TZ_BF16X3 || precision == TZ_FP16X3) && tile_cols(N) == 128 && (M % (2 * BM)) == 0;
+}
+
+void tc_set_pairs(int mode) { g_pairs.store(mode < 0 ? -1 : (mode ? 1 : 0), std::memory_order_relaxed); }
+
 cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M,
                             int64_t N, int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc,
-                            void *scratch, size_t scratch_bytes, int *err, cudaStream_t s) {
+                            void *scratch, size_t scratch_bytes, int *err, cudaStream_t s, int pair) {
   if (!cgemm_tc_supported(precision, M, N, K)) return cudaErrorNotSupported;
   if (sA != M * K || sB != N * K) return cudaErrorNotSupported;  // contiguous batches only
   const int bnp = tile_cols(N);
@@ -1128,12 +1321,16 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
   float2 *P = ks > 1 ? reinterpret_cast<float2 *>(after_b) : nullptr;
   const size_t part_all = ks_shape > 1 ? (size_t)(ks_shape * batch * M * N * 8) : 0;
   uint32_t *bmax = reinterpret_cast<uint32_t *>(after_b + ((part_all + 255) & ~size_t(255)));
+  // pairs of CTAs (cta_group::2) take the split BF16 / FP16 products with
+  // 128-column tiles and whole 256-row tiles: each CTA loads half of B
+  const bool want_pair = pair < 0 ? tc_pairs_default() : pair != 0;
+  const int cg = want_pair && tc_pair_supported(precision, M, N) ? 2 : 1;
   CUtensorMap ta, tbh, tbl;
   const int sk = tf32 ? stage_k<MODE_TF32>() : stage_k<MODE_BF16>();
   const CUtensorMapDataType bdt =
       tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : (f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
   if (!make_map(&ta, A, 2 * K, rowsA, 32, BM, CU_TENSOR_MAP_DATA_TYPE_FLOAT32) ||
-      !make_map(&tbh, Bh, 2 * K, rowsB, sk, bnp, bdt) || !make_map(&tbl, Bl, 2 * K, rowsB, sk, bnp, bdt))
+      !make_map(&tbh, Bh, 2 * K, rowsB, sk, bnp / cg, bdt) || !make_map(&tbl, Bl, 2 * K, rowsB, sk, bnp / cg, bdt))
     return cudaErrorInvalidValue;
   int pb = 0;
   if (f16) {
@@ -1178,7 +1375,7 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
   args.N = N;
   args.K = K;
   args.sC = sC;
-  args.n_tiles_m = (int)(M / BM);
+  args.n_tiles_m = (int)(M / (BM * cg));
   args.n_tiles_n = n_tiles_n;
   args.kblocks = (int)((2 * K + sk - 1) / sk);
   args.ksplit = ks;
@@ -1213,9 +1410,9 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
       args.tma_store = 1;
   }
-  cudaError_t e = tf32  ? dispatch<MODE_TF32>(bnp, ta, tbh, tbl, tcm, args, n_tiles, s)
-                  : f16 ? dispatch<MODE_F16>(bnp, ta, tbh, tbl, tcm, args, n_tiles, s)
-                        : dispatch<MODE_BF16>(bnp, ta, tbh, tbl, tcm, args, n_tiles, s);
+  cudaError_t e = tf32  ? dispatch<MODE_TF32>(bnp, cg, ta, tbh, tbl, tcm, args, n_tiles, s)
+                  : f16 ? dispatch<MODE_F16>(bnp, cg, ta, tbh, tbl, tcm, args, n_tiles, s)
+                        : dispatch<MODE_BF16>(bnp, cg, ta, tbh, tbl, tcm, args, n_tiles, s);
   if (e != cudaSuccess || ks == 1) return e;
   const int64_t total = batch * M * N;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);

@@ -124,10 +124,17 @@ cudaError_t launch_cgemm_skinny_gather(const float2 *X, const float2 *Y, float2 
 // shape is outside what the kernel handles (the planner checks first).
 // *err (device memory) is set to 1 when one of the product's bounded waits
 // runs out (its result is then invalid); the caller clears it.
+// pair: 1 runs the product on pairs of CTAs (cta_group::2) where the shape
+// allows it (tc_pair_supported), 0 on single CTAs, -1 the process default.
 cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M,
                             int64_t N, int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc,
-                            void *scratch, size_t scratch_bytes, int *err, cudaStream_t s);
+                            void *scratch, size_t scratch_bytes, int *err, cudaStream_t s, int pair = -1);
 bool cgemm_tc_supported(int precision, int64_t M, int64_t N, int64_t K);
+// Split BF16 / FP16 products with 128-column tiles and whole 256-row tiles.
+bool tc_pair_supported(int precision, int64_t M, int64_t N);
+// Process default for pair = -1: 1 on, 0 off, -1 back to the initial default
+// (on unless the environment variable TZ_TC_PAIRS is 0).
+void tc_set_pairs(int mode);
 // Test and debug hooks for the current device: the limit of the products'
 // bounded waits in ns (0 restores the default 2 s), and a switch that makes
 // every product first wait on a barrier that nothing arrives at.

@@ -23,9 +23,12 @@ def main():
     ap.add_argument("--rank", type=int, default=26)
     ap.add_argument("--iters", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--pairs", type=int, default=-1, choices=[-1, 0, 1],
+                    help="split BF16/FP16 products: 1 pairs of CTAs, 0 single CTAs, -1 default")
     a = ap.parse_args()
     import torch
     import paper_1907_11217_gb300 as tz
+    tz.tz_tune_tc_pairs(a.pairs)
     dev = "cuda"
     if a.op == "permute":
         x = torch.randn(2 << a.rank, device=dev)
@@ -58,7 +61,7 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / a.iters
-    print(json.dumps({"op": a.op, "precision": a.precision, **shape, "ms": ms,
+    print(json.dumps({"op": a.op, "precision": a.precision, **shape, "pairs": a.pairs, "ms": ms,
                       "useful_tflops": flops / ms / 1e9, "algorithmic_gbs": nbytes / ms / 1e6}))
 
 

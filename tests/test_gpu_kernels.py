@@ -275,3 +275,41 @@ def test_accumulate_fp64(env):
     got = dacc.cpu().numpy().view(np.complex128)
     ref = linalg.accumulate(acc0, part, s)
     assert np.max(np.abs(got - ref)) <= 1e-15 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
+@pytest.mark.parametrize("batch,m,n,k", [(2, 256, 64, 32), (1, 1024, 128, 64), (3, 512, 100, 72),
+                                         (1, 256, 64, 8192), (2, 4096, 256, 512)])
+def test_cgemm_pairs_match_single_cta(env, prec, batch, m, n, k):
+    """Products on pairs of CTAs (cta_group::2: M = 256 per pair, each CTA
+    loading half of the B tile) against the same products on single CTAs and
+    against the complex128 definition: ragged column tiles (n = 100), a
+    ragged last k-block (k = 72), split K (k = 8192 over two tiles)."""
+    tz, torch = env
+    rng = np.random.default_rng(m + 13 * n + 17 * k)
+    A, dA = c64(torch, rng, (batch, m, k))
+    B, dB = c64(torch, rng, (batch, n, k))
+    nbytes = tz.tz_op_cgemm_scratch_bytes(prec, batch, m, n, k)
+    scratch = torch.empty(nbytes // 4 + 64, dtype=torch.float32, device="cuda")
+    out = {}
+    try:
+        for mode in (0, 1):
+            tz.tz_tune_tc_pairs(mode)
+            dC = torch.full((batch * m * n * 2,), float("nan"), dtype=torch.float32, device="cuda")
+            tz.tz_op_cgemm(prec, batch, m, n, k, dA, m * k, dB, n * k, dC, m * n, scratch=scratch)
+            tz.tz_op_cgemm_status(prec, scratch)
+            out[mode] = dC.cpu().numpy().view(np.complex64).reshape(batch, m, n)
+    finally:
+        tz.tz_tune_tc_pairs(-1)
+    ref = linalg.cgemm(A, B)
+    bound = linalg.cgemm(np.abs(A).astype(np.complex128), np.abs(B).astype(np.complex128)).real
+    for mode, C in out.items():
+        assert np.all(np.isfinite(C)), mode
+        err = np.abs(C - ref)
+        assert np.all(err <= (2.0 ** -14 + 4 * (k + 2) * 2.0 ** -24) * bound + 1e-30), (mode, float(np.max(err / bound)))
+    # the same splits and the same accumulation ranges: the two forms agree to
+    # the FP32 rounding of the accumulation
+    diff = np.abs(out[1] - out[0])
+    print(f"{prec} {batch}x{m}x{n}x{k}: pairs vs single CTA max |diff|/bound {np.max(diff / bound):.2e}, "
+          f"bit-identical {np.array_equal(out[1], out[0])}")
+    assert np.all(diff <= 4 * (k + 2) * 2.0 ** -24 * bound + 1e-30)
