@@ -126,36 +126,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
   }
 }
 
-// Wait variant for barriers that CTAs of a cluster arrive on (acquire at
-// cluster scope, so the peer's released writes are visible).
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, "
-      "p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
+// Waits on barriers that the peer CTA of a pair also arrives on use the
+// same (default-scope) wait: what a pair hands across is tensor memory and
+// products, ordered by tcgen05 fences around the barrier.
 template <bool CLUSTER>
 __device__ __forceinline__ bool mbar_wait_t(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
                                             unsigned long long limit_ns, bool honour_abort = true) {
-  if (!CLUSTER) return mbar_wait(bar, parity, abort_flag, limit_ns, honour_abort);
-  unsigned long long t0 = 0;
-  for (uint32_t i = 0;; i++) {
-    if (mbar_try_wait_cluster(bar, parity)) return true;
-    if (honour_abort && *abort_flag) return false;
-    if ((i & 255) == 255) {
-      const unsigned long long now = globaltimer();
-      if (t0 == 0) {
-        t0 = now;
-      } else if (now - t0 > limit_ns) {
-        *abort_flag = 1;
-        return false;
-      }
-    }
-  }
+  return mbar_wait(bar, parity, abort_flag, limit_ns, honour_abort);
 }
 
 // Thread-block clusters of two CTAs (a pair shares one 256-row tile).
@@ -180,8 +157,13 @@ __device__ __forceinline__ uint32_t cluster_addr(const void *p, uint32_t rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
   return r;
 }
+// Arrival on a barrier of either CTA of the pair, with the default
+// (CTA-scope) release: the tensor-memory writes and reads it publishes are
+// ordered by tcgen05 fences, and a cluster-scope release would also wait for
+// the thread's global stores to be acknowledged (a memory barrier per
+// arrival, measured as the dominant stall of the epilogue warps).
 __device__ __forceinline__ void mbar_arrive_remote(uint32_t caddr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
 }
 __device__ __forceinline__ void st_remote_u32(uint32_t caddr, uint32_t v) {
   asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(caddr), "r"(v) : "memory");

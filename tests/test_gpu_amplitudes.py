@@ -176,3 +176,25 @@ def test_tensor_core_scatter_epilogue_n_low(tz, prec):
     err = rel_err(got, ref, 49)
     print(f"grid7x7 d16 batch64 {prec}: max rel err {err:.3e}")
     assert err <= (1e-3 if prec == "bf16x3" else TOL_C64)
+
+
+def test_slice_farm_ledger_resume_on_gpu(tz, tmp_path):
+    """The checkpointed slice farm on the GPU path: a run that stops after
+    two ranges, then a resumed run, give the amplitudes of one whole run."""
+    from paper_1907_11217_gb300 import ledger
+    spec = grid_spec(4, 5, 12, 3)
+    bits = ti.random_bitstrings(20, 3, 8)
+    plan, net, tree, sl = make_plan(tz, spec, slice_bits=4, small_log2=5, k_max=6)
+    n_slices = 1 << len(sl)
+    assert n_slices >= 16
+    key = ledger.job_key(spec=spec, tree=np.asarray(tree.pairs()), segs=[list(s) for s in plan.sliced_segments()],
+                         bits=bits, precision="c64", chunk=3)
+    f = ledger.plan_range_contractor(tz, plan, bits)
+    d = str(tmp_path)
+    assert ledger.run_ranges(f, d, key, n_slices, 3, 0, 1, stop_after=2) == 2
+    assert ledger.total(d, key, n_slices, 3) is None
+    ledger.run_ranges(f, d, key, n_slices, 3, 0, 1)
+    got = ledger.total(d, key, n_slices, 3)
+    plan.set_slice_range(0, n_slices)
+    assert rel_err(got, tz.tz_contract_amplitudes(plan, bits), 20) <= 1e-6
+    assert rel_err(got, sv.amplitudes(spec, bits), 20) <= TOL_C64

@@ -365,3 +365,36 @@ def test_bristlecone70_depth32_bench_tree_slices_vs_oracle(tz, bench_tree, cap, 
           {m: f"{e:.2e}" for m, e in errs.items()})
     for m, e in errs.items():
         assert e <= PARTIAL_TOL[m], (m, e)
+
+
+def test_bristlecone70_depth28_porter_thomas(tz):
+    """Sec. 2 (the Porter-Thomas check of its 200,000-amplitude run, on a
+    smaller sample): for 4096 uniform random bitstrings of a Bristlecone-70
+    depth 1+28+1 circuit, x = 2^70 |a|^2 follows e^-x: mean 1 within three
+    standard errors (3/sqrt(M)), second moment 2 within three standard errors
+    (sqrt(20/M) each), P(x > 1) = 1/e, and the Kolmogorov-Smirnov distance to
+    1 - e^-x below its 1 % critical value 1.63/sqrt(M)."""
+    import math
+    import torch
+    spec = bris_spec(28, 3)
+    m = 4096
+    bits = ti.random_bitstrings(70, m, 28_200)
+    net = tz.tz_network_from_circuit(tz.tz_circuit_from_spec(spec), 0)
+    tree = tz.tz_path_greedy(net, restarts=1024, seed=7, log2_max_intermediate=30, precision="fp16x3",
+                             algorithm="elimination")
+    sl = tz.tz_slice_select(net, tree, 30, 40)
+    plan = tz.tz_plan_create(net, tree, sl, precision="fp16x3", stream=torch.cuda.Stream(), use_graph=True,
+                             max_bitstrings=m)
+    st = plan.stats()
+    assert st["flops_per_group"] * 2.0 ** st["k"] * m < 2e15
+    plan.bind()
+    x = np.abs(tz.tz_contract_amplitudes(plan, bits)) ** 2 * 2.0 ** 70
+    xs = np.sort(x)
+    cdf = 1.0 - np.exp(-xs)
+    ks = max(np.max(np.arange(1, m + 1) / m - cdf), np.max(cdf - np.arange(m) / m))
+    print(f"bristlecone70 d28 Porter-Thomas, {m} amplitudes: mean {x.mean():.4f}, second moment "
+          f"{(x ** 2).mean():.4f}, P(x>1) {(x > 1).mean():.4f}, KS {ks:.4f}")
+    assert abs(x.mean() - 1.0) < 3.0 / math.sqrt(m)
+    assert abs((x ** 2).mean() - 2.0) < 3.0 * math.sqrt(20.0 / m)
+    assert abs((x > 1).mean() - math.exp(-1.0)) < 3.0 * math.sqrt(math.exp(-1) * (1 - math.exp(-1)) / m)
+    assert ks < 1.63 / math.sqrt(m)

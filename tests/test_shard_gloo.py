@@ -79,3 +79,95 @@ def test_two_gloo_ranks_sum_to_full_amplitude():
         assert p.exitcode == 0
     ref = sv.amplitudes(spec, bits)
     assert np.max(np.abs(got - ref)) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# Checkpointed slice farm (ledger.py): a rank that leaves between ranges
+# loses nothing it recorded, and a second run redoes only the rest.
+
+from paper_1907_11217_gb300 import ledger  # noqa: E402
+
+
+def _farm_worker(rank, world, port, spec, segs, bits, directory, key, chunk, stop_rank, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from oracle import tn
+    c = tn.Contractor(spec, sliced=segs)
+    calls = []
+
+    def contract_range(lo, hi):
+        calls.append((lo, hi))
+        return np.sum([[c.partial(x, s) for x in bits] for s in range(lo, hi)], axis=0)
+
+    n_slices = 1 << len(segs)
+    stop = 1 if rank == stop_rank else None
+    ledger.run_ranges(contract_range, directory, key, n_slices, chunk, rank, world, sync=dist.barrier,
+                      stop_after=stop)
+    # the others learn on the host that the job is incomplete; nothing is
+    # left in flight when a rank leaves
+    dist.barrier()
+    q.put((rank, calls, None if rank else ledger.total(directory, key, n_slices, chunk)))
+    dist.destroy_process_group()
+
+
+def _farm_run(spec, segs, bits, directory, key, chunk, stop_rank):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_farm_worker, args=(r, 2, port, spec, segs, bits, directory, key, chunk,
+                                                    stop_rank, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = {}
+    for _ in procs:
+        rank, calls, tot = q.get(timeout=180)
+        out[rank] = (calls, tot)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    return out
+
+
+def test_slice_farm_resumes_from_ledgers(tmp_path):
+    import tz_inputs as ti
+    from oracle import statevector as sv
+    spec = ti.circuit_to_spec(12, ti.generate_circuit(ti.grid(3, 4), 12, 3))
+    segs = [(1, 2), (5, 3), (7, 2), (10, 1)]
+    bits = ti.random_bitstrings(12, 3, 9)
+    chunk = 2   # 16 slices in 8 ranges, 4 per rank
+    key = ledger.job_key(spec=spec, segs=[list(s) for s in segs], bits=bits, chunk=chunk, precision="oracle")
+    d = str(tmp_path / "farm")
+    # run 1: rank 1 leaves after its first range
+    out1 = _farm_run(spec, segs, bits, d, key, chunk, stop_rank=1)
+    assert len(out1[0][0]) == 4 and len(out1[1][0]) == 1
+    assert out1[0][1] is None          # incomplete: three ranges missing
+    # run 2: only the three missing ranges are contracted, split over both ranks
+    out2 = _farm_run(spec, segs, bits, d, key, chunk, stop_rank=-1)
+    redone = sorted(out2[0][0] + out2[1][0])
+    assert len(redone) == 3 and not set(redone) & set(out1[0][0] + out1[1][0])
+    got = out2[0][1]
+    ref = sv.amplitudes(spec, bits)
+    assert np.max(np.abs(got - ref)) < 1e-14
+    # the sum is in range order: the same bits as one run without a stop
+    full = tmp_path / "one_run"
+    out3 = _farm_run(spec, segs, bits, str(full), key, chunk, stop_rank=-1)
+    assert np.array_equal(out3[0][1], got)
+
+
+def test_ledger_refuses_another_job(tmp_path):
+    d = str(tmp_path)
+    k1 = ledger.job_key(spec="a", chunk=2)
+    k2 = ledger.job_key(spec="b", chunk=2)
+    assert k1 != k2
+    led = ledger.SliceLedger(d, k1, 0)
+    led.record(0, 2, np.array([1.0 + 2.0j]))
+    assert ledger.pending(d, k1, 8, 2, 0, 1) == [(2, 4), (4, 6), (6, 8)]
+    with pytest.raises(ValueError):
+        ledger.recorded(d, k2)
+    with pytest.raises(ValueError):
+        ledger.SliceLedger(d, k2, 0)
+    assert ledger.total(d, k1, 8, 2) is None
+    for lo in (2, 4, 6):
+        led.record(lo, lo + 2, np.array([1.0]))
+    assert ledger.total(d, k1, 8, 2)[0] == 4.0 + 2.0j
