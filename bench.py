@@ -72,6 +72,9 @@ def parse():
     ap.add_argument("--tree-file", default="",
                     help="load the tensor-core modes' tree from this .npy if it exists, else save it there")
     ap.add_argument("--algorithm", default="elimination", choices=["auto", "greedy", "elimination"])
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1: time each tensor-core step's launch choices when the plan is bound (untimed "
+                         "preprocessing) and keep the fastest; 0: built-in defaults")
     ap.add_argument("--tree-seed", type=int, default=7)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
@@ -110,7 +113,7 @@ def build_plan(tz, spec, args, precision, stream, device, log2_max, max_rows=0):
     tree = tz.tz_tree_from_pairs(net, _TREES[key])
     sliced = tz.tz_slice_select(net, tree, log2_max, 40) if log2_max > 0 else []
     plan = tz.tz_plan_create(net, tree, sliced, precision=precision, device=device, stream=stream, use_graph=True,
-                             max_bitstrings=max_rows or 1 << max(args.batch_log2, 0))
+                             max_bitstrings=max_rows or 1 << max(args.batch_log2, 0), autotune=bool(args.autotune))
     prep_s = time.perf_counter() - t0
     return plan, sliced, prep_s
 
@@ -542,6 +545,8 @@ def main():
     st = plan.stats()
     plan.bind()
     plan_bind_ms = plan.stats()["bind_ms"]
+    n_tuned = plan.stats()["n_tuned_steps"]
+    st = plan.stats()   # the launch count follows the autotuned choices
     k = len(sliced)
     n_slices = 1 << k
     B = 1 << args.batch_log2
@@ -696,7 +701,7 @@ def main():
                  "gemm_steps": st["n_gemm_steps"], "launches_per_slice": st["n_launches_per_group"],
                  "workspace_gb": st["workspace_bytes"] / 1e9,
                  "const_steps": st["n_const_steps"], "const_flops": st["const_flops"],
-                 "bind_ms": plan_bind_ms},
+                 "bind_ms": plan_bind_ms, "autotuned_steps": n_tuned},
         "e2e": {"value": e2e_s, "unit": "s/amplitude", "h2d_bytes_per_step": int(bits.nbytes),
                 "d2h_bytes_per_step": 16 * B},
         "roofline": rl,

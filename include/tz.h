@@ -189,6 +189,11 @@ typedef struct {
                             own, or a server slot's; up to 8 kept) and replayed on
                             any non-NULL stream                                    */
   int64_t max_bitstrings;/* bitstrings per call the workspace is sized for (0 = 4096) */
+  int autotune;          /* 1: when the workspace is bound, time each tensor-core step's
+                            launch choices (pairs of CTAs or single CTAs, K split or
+                            not) on the plan's own buffers and keep the fastest; choices
+                            are cached per device, precision, shape and output kind.
+                            0: the built-in defaults                                  */
 } tz_plan_opts;
 
 typedef struct {
@@ -210,6 +215,8 @@ typedef struct {
   double const_flops;            /* useful flops of the bind-time (constant) steps,
                                     computed once per bind, not per group            */
   double bind_ms;                /* wall time of the last tz_plan_bind_workspace     */
+  int n_tuned_steps;             /* tensor-core steps with an autotuned launch choice */
+  int pad0;
 } tz_plan_stats;
 
 /* Build a plan: classify steps, choose layouts, permutes and kernels, lay
@@ -380,10 +387,10 @@ int tz_debug_stall_tensor_core(int on);
 /* Process-wide default of how the split BF16 / FP16 products run where the
  * shape allows pairs (128-column tiles, m a multiple of 256): 1 on pairs of
  * CTAs on two SMs (cta_group::2, each CTA loading half of the B tile), 0 on
- * single CTAs, -1 back to the initial default (pairs, unless the environment
- * variable TZ_TC_PAIRS is 0). Plans autotuned at bind time keep their own
- * per-step choice. Results are the same either way up to the order of FP32
- * additions inside a k-block. */
+ * single CTAs, -1 back to the initial default (single CTAs, unless the
+ * environment variable TZ_TC_PAIRS is 1). Plans autotuned at bind time keep
+ * their own per-step choice. The two forms give the same results (the same
+ * splits, products and accumulation ranges). */
 int tz_tune_tc_pairs(int mode);
 
 /* FP64 accumulation of partial amplitudes: acc[j] += scale * part[j] for

@@ -40,7 +40,8 @@ class tz_path_opts(ctypes.Structure):
 
 class tz_plan_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("device", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("small_log2", ctypes.c_int), ("use_graph", ctypes.c_int), ("max_bitstrings", ctypes.c_int64)]
+                ("small_log2", ctypes.c_int), ("use_graph", ctypes.c_int), ("max_bitstrings", ctypes.c_int64),
+                ("autotune", ctypes.c_int)]
 
 
 class tz_plan_stats(ctypes.Structure):
@@ -50,7 +51,7 @@ class tz_plan_stats(ctypes.Structure):
                 ("gemm_flops_per_group", ctypes.c_double), ("bytes_per_group", ctypes.c_double),
                 ("permute_bytes_per_group", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t),
                 ("const_bytes", ctypes.c_size_t), ("scratch_bytes", ctypes.c_size_t), ("const_flops", ctypes.c_double),
-                ("bind_ms", ctypes.c_double)]
+                ("bind_ms", ctypes.c_double), ("n_tuned_steps", ctypes.c_int), ("pad0", ctypes.c_int)]
 
 
 PROFILE_KINDS = ("leaves", "direct", "permute", "gemm_simt", "gemm_tc", "accumulate", "gemm_skinny", "gemm_dot")

@@ -1132,14 +1132,15 @@ bool make_map(CUtensorMap *tm, const void *base, int64_t cols, int64_t rows, int
 constexpr int kMaxDevices = 64;
 
 // Pairs of CTAs for the products that allow them: the process-wide default
-// (tc_set_pairs; initially on unless the environment variable TZ_TC_PAIRS is
-// 0), which a launch's own choice (autotuned) overrides.
+// (tc_set_pairs; initially off unless the environment variable TZ_TC_PAIRS is
+// 1: on the measured shapes pairs are no faster yet), which a launch's own
+// choice (autotuned) overrides.
 std::atomic<int> g_pairs{-1};
 bool tc_pairs_default() {
   int v = g_pairs.load(std::memory_order_relaxed);
   if (v < 0) {
     const char *e = std::getenv("TZ_TC_PAIRS");
-    v = (e && e[0] == '0') ? 0 : 1;
+    v = (e && e[0] == '1') ? 1 : 0;
   }
   return v != 0;
 }
@@ -1255,8 +1256,13 @@ static int split_k(int precision, int64_t batch, int64_t M, int64_t N, int64_t K
   return s < 2 ? 1 : (int)s;
 }
 
-int cgemm_tc_launches(int precision, int64_t batch, int64_t M, int64_t N, int64_t K, bool scatter) {
-  return 2 + (precision == TZ_FP16X3 ? 1 : 0) + (!scatter && split_k(precision, batch, M, N, K) > 1 ? 1 : 0);
+int cgemm_tc_launches(int precision, int64_t batch, int64_t M, int64_t N, int64_t K, bool scatter, int ksplit) {
+  return 2 + (precision == TZ_FP16X3 ? 1 : 0) +
+         (!scatter && ksplit != 1 && split_k(precision, batch, M, N, K) > 1 ? 1 : 0);
+}
+
+int cgemm_tc_split(int precision, int64_t batch, int64_t M, int64_t N, int64_t K) {
+  return split_k(precision, batch, M, N, K);
 }
 
 // Scratch: prepared B hi | prepared B lo | split-K partials (when split) |
@@ -1281,7 +1287,8 @@ void tc_set_pairs(int mode) { g_pairs.store(mode < 0 ? -1 : (mode ? 1 : 0), std:
 
 cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M,
                             int64_t N, int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc,
-                            void *scratch, size_t scratch_bytes, int *err, cudaStream_t s, int pair) {
+                            void *scratch, size_t scratch_bytes, int *err, cudaStream_t s, int pair,
+                            int ksplit) {
   if (!cgemm_tc_supported(precision, M, N, K)) return cudaErrorNotSupported;
   if (sA != M * K || sB != N * K) return cudaErrorNotSupported;  // contiguous batches only
   const int bnp = tile_cols(N);
@@ -1298,7 +1305,7 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
   // after the prepared B: room for split-K partials (sized by the shape, as
   // in cgemm_tc_scratch_bytes), then the FP16 partial maxima
   const int ks_shape = split_k(precision, batch, M, N, K);
-  const int ks = sc ? 1 : ks_shape;
+  const int ks = (sc || ksplit == 1) ? 1 : ks_shape;
   char *after_b = Bl + ((half + 255) & ~size_t(255));
   float2 *P = ks > 1 ? reinterpret_cast<float2 *>(after_b) : nullptr;
   const size_t part_all = ks_shape > 1 ? (size_t)(ks_shape * batch * M * N * 8) : 0;

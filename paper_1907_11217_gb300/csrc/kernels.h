@@ -126,14 +126,18 @@ cudaError_t launch_cgemm_skinny_gather(const float2 *X, const float2 *Y, float2 
 // runs out (its result is then invalid); the caller clears it.
 // pair: 1 runs the product on pairs of CTAs (cta_group::2) where the shape
 // allows it (tc_pair_supported), 0 on single CTAs, -1 the process default.
+// ksplit: 1 never splits K across CTAs; 0 splits as cgemm_tc_split says.
 cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M,
                             int64_t N, int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc,
-                            void *scratch, size_t scratch_bytes, int *err, cudaStream_t s, int pair = -1);
+                            void *scratch, size_t scratch_bytes, int *err, cudaStream_t s, int pair = -1,
+                            int ksplit = 0);
+// K ranges a row-major product of this shape is split into by default (1: none).
+int cgemm_tc_split(int precision, int64_t batch, int64_t M, int64_t N, int64_t K);
 bool cgemm_tc_supported(int precision, int64_t M, int64_t N, int64_t K);
 // Split BF16 / FP16 products with 128-column tiles and whole 256-row tiles.
 bool tc_pair_supported(int precision, int64_t M, int64_t N);
 // Process default for pair = -1: 1 on, 0 off, -1 back to the initial default
-// (on unless the environment variable TZ_TC_PAIRS is 0).
+// (off unless the environment variable TZ_TC_PAIRS is 1).
 void tc_set_pairs(int mode);
 // Test and debug hooks for the current device: the limit of the products'
 // bounded waits in ns (0 restores the default 2 s), and a switch that makes
@@ -147,7 +151,7 @@ size_t cgemm_tc_scratch_bytes(int precision, int64_t batch, int64_t M, int64_t N
 // Kernel launches of one tensor-core product (FP16 mode: the maxima of |B|;
 // B preparation, the product, and the sum of split-K partials when K is
 // split; scatter outputs never split).
-int cgemm_tc_launches(int precision, int64_t batch, int64_t M, int64_t N, int64_t K, bool scatter);
+int cgemm_tc_launches(int precision, int64_t batch, int64_t M, int64_t N, int64_t K, bool scatter, int ksplit = 0);
 cudaError_t launch_accumulate(const AccumArgs &a, cudaStream_t s);
 cudaError_t launch_accumulate_plain(const float2 *part, double2 *acc, int64_t n, double sre, double sim,
                                     cudaStream_t s);

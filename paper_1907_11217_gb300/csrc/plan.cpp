@@ -6,6 +6,8 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <tuple>
+#include <mutex>
 #include <memory>
 #include <sstream>
 
@@ -690,7 +692,8 @@ std::string plan_describe(const tz_plan *p) {
       << ",\"gemm\":" << x.gemm << ",\"tc\":" << x.tc << ",\"opX\":" << x.opX << ",\"opY\":" << x.opY
       << ",\"M\":" << x.M << ",\"N\":" << x.N << ",\"K\":" << x.K << ",\"batch\":" << x.batch
       << ",\"level\":" << x.level << ",\"dstep\":" << x.dstep << ",\"permX\":" << x.permX << ",\"permY\":" << x.permY
-      << ",\"row_major\":" << x.row_major << ",\"c_nat\":" << x.c_nat << ",\"skinny\":" << x.skinny;
+      << ",\"row_major\":" << x.row_major << ",\"c_nat\":" << x.c_nat << ",\"skinny\":" << x.skinny
+      << ",\"tc_pair\":" << x.tc_pair << ",\"tc_ksplit\":" << x.tc_ksplit;
     auto arr = [&](const char *name, const int8_t *v, int n) {
       o << ",\"" << name << "\":[";
       for (int j = 0; j < n; j++) o << (j ? "," : "") << (int)v[j];
@@ -905,7 +908,7 @@ static void run_items(tz_plan *p, const std::vector<Item> &items, const RunCtx &
           void *scr = abase + ps.tc_scratch_off;
           cuda_check(dev::launch_cgemm_tc(p->opts.precision, X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.M * ps.K,
                                           ps.N * ps.K, ps.M * ps.N, sc, scr, (size_t)ps.tc_scratch, &gs->tc_error,
-                                          s),
+                                          s, ps.tc_pair, ps.tc_ksplit),
                      "tensor-core gemm");
         } else {
           cuda_check(dev::launch_cgemm_simt(X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.M * ps.K, ps.N * ps.K,
@@ -939,6 +942,112 @@ static void run_items(tz_plan *p, const std::vector<Item> &items, const RunCtx &
       if (p->pending.size() >= 4096) plan_profile_collect(p);
     }
   }
+}
+
+// ---------------------------------------------------------------- autotuner
+// For every tensor-core step of the group, time the product's launch
+// configurations (pairs of CTAs or single CTAs; K split or not) on the
+// plan's own operand and scratch buffers, and keep the fastest. Choices are
+// cached per (device, precision, product shape, output kind), so plans that
+// share step shapes (other slicings, other bitstrings, server slots) reuse
+// them. The buffers hold whatever the arena holds at bind time: the product
+// writes only its own output buffer, which every group recomputes.
+namespace {
+struct TuneKey {
+  int dev, prec;
+  int64_t batch, M, N, K;
+  int out;  // 0 row-major, 1 scatter
+  bool operator<(const TuneKey &o) const {
+    return std::tie(dev, prec, batch, M, N, K, out) < std::tie(o.dev, o.prec, o.batch, o.M, o.N, o.K, o.out);
+  }
+};
+struct TuneChoice {
+  int pair, ksplit;
+  float ms;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tune_cache;
+}  // namespace
+
+static void autotune_tc_steps(tz_plan *p) {
+  cudaStream_t s = p->stream;
+  const RunCtx ctx = default_ctx(p);
+  auto *gs = reinterpret_cast<dev::GroupState *>(ctx.scratch + p->s_gs);
+  char *abase = ctx.scratch + p->s_arena;
+  int dev = 0;
+  cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  cudaEvent_t e0, e1;
+  cuda_check(cudaEventCreate(&e0), "event");
+  cuda_check(cudaEventCreate(&e1), "event");
+  int tuned = 0;
+  try {
+    for (const Item &it : p->var_items) {
+      if (it.kind != IT_GEMM) continue;
+      PStep &ps = p->S[it.a];
+      if (!ps.tc) continue;
+      const TuneKey key{dev, p->opts.precision, ps.batch, ps.M, ps.N, ps.K, ps.row_major ? 0 : 1};
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto f = g_tune_cache.find(key);
+        if (f != g_tune_cache.end()) {
+          ps.tc_pair = f->second.pair;
+          ps.tc_ksplit = f->second.ksplit;
+          tuned++;
+          continue;
+        }
+      }
+      std::vector<int> pairs = {0};
+      if (dev::tc_pair_supported(p->opts.precision, ps.M, ps.N)) pairs.push_back(1);
+      std::vector<int> splits = {0};
+      if (ps.row_major && dev::cgemm_tc_split(p->opts.precision, ps.batch, ps.M, ps.N, ps.K) > 1) splits.push_back(1);
+      const float2 *X = (const float2 *)tensor_ptr(p, ctx, ps.opX);
+      const float2 *Y = (const float2 *)tensor_ptr(p, ctx, ps.opY);
+      float2 *C = (float2 *)tensor_ptr(p, ctx, ps.c_nat >= 0 ? ps.c_nat : ps.c);
+      const dev::CScatter *sc = ps.row_major ? nullptr : &ps.scatter;
+      void *scr = abase + ps.tc_scratch_off;
+      TuneChoice best{-1, 0, 1e30f};
+      for (int pr : pairs)
+        for (int ks : splits) {
+          auto launch = [&] {
+            cuda_check(dev::launch_cgemm_tc(p->opts.precision, X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.M * ps.K,
+                                            ps.N * ps.K, ps.M * ps.N, sc, scr, (size_t)ps.tc_scratch, &gs->tc_error,
+                                            s, pr, ks),
+                       "autotune launch");
+          };
+          launch();  // warm-up
+          cuda_check(cudaEventRecord(e0, s), "event");
+          for (int r = 0; r < 3; r++) launch();
+          cuda_check(cudaEventRecord(e1, s), "event");
+          cuda_check(cudaEventSynchronize(e1), "event");
+          float ms = 0;
+          cuda_check(cudaEventElapsedTime(&ms, e0, e1), "event");
+          if (ms < best.ms) best = TuneChoice{pr, ks, ms};
+        }
+      ps.tc_pair = best.pair;
+      ps.tc_ksplit = best.ksplit;
+      tuned++;
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune_cache[key] = best;
+    }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->stats.n_tuned_steps = tuned;
+  // the launch count per group follows the choices
+  int n = 0;
+  for (const Item &it : p->var_items) {
+    int c = 1;
+    if (it.kind == IT_GEMM && p->S[it.a].tc) {
+      const PStep &ps = p->S[it.a];
+      c = dev::cgemm_tc_launches(p->opts.precision, ps.batch, ps.M, ps.N, ps.K, !ps.row_major, ps.tc_ksplit);
+    }
+    n += c;
+  }
+  p->stats.n_launches_per_group = n;
 }
 
 static void clear_graphs(tz_plan *p) {
@@ -1014,6 +1123,7 @@ void plan_bind(tz_plan *p, void *ws, size_t bytes) {
   cuda_check(cudaMemsetAsync(&gs->tc_error, 0, sizeof(int), s), "clear error word");
   run_items(p, p->const_items, default_ctx(p));
   cuda_check(cudaStreamSynchronize(s), "bind-time steps");
+  if (p->opts.autotune) autotune_tc_steps(p);
   if (read_tc_error(p, default_ctx(p)))
     fail(TZ_ETIMEOUT, "a tensor-core product of the bind-time steps timed out in a bounded wait");
   p->stats.bind_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_bind).count();

@@ -33,6 +33,8 @@ struct PStep {
   int dstep = -1;             // index into dsteps (direct steps)
   int64_t tc_scratch = 0;     // bytes of tensor-core operand scratch
   int64_t tc_scratch_off = -1;
+  int tc_pair = -1;           // tensor-core launch choice (autotuned at bind): pairs of
+  int tc_ksplit = 0;          // CTAs (1/0, -1 default) and K split (1 none, 0 default)
   dev::CScatter scatter{};    // where the GEMM writes its result
   bool row_major = false;     // scatter is the plain row-major order
   int c_nat = -1;             // tensor the GEMM writes in row-major order when a

@@ -198,3 +198,25 @@ def test_slice_farm_ledger_resume_on_gpu(tz, tmp_path):
     plan.set_slice_range(0, n_slices)
     assert rel_err(got, tz.tz_contract_amplitudes(plan, bits), 20) <= 1e-6
     assert rel_err(got, sv.amplitudes(spec, bits), 20) <= TOL_C64
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
+def test_autotuned_plan_matches_oracle(tz, prec):
+    """A plan bound with autotune: every tensor-core step gets a timed
+    launch choice (pairs of CTAs or single CTAs; K split or not), recorded
+    in the plan description, and the amplitudes still match the oracle."""
+    import json
+    spec = grid_spec(7, 7, 16, 2)
+    bits = ti.random_bitstrings(49, 64, 77)
+    net = tz.tz_network_from_circuit(tz.tz_circuit_from_spec(spec), 6)
+    tree = tz.tz_path_greedy(net, restarts=16, seed=7, algorithm="elimination", precision=prec)
+    plan = tz.tz_plan_create(net, tree, [], precision=prec, max_bitstrings=64, autotune=True)
+    plan.bind()
+    st = plan.stats()
+    steps = [s for s in json.loads(plan.describe())["steps"] if s.get("var") and s.get("gemm") and s.get("tc")]
+    assert steps and st["n_tuned_steps"] == len(steps)
+    assert all(s["tc_pair"] in (0, 1) and s["tc_ksplit"] in (0, 1) for s in steps)
+    print(f"{prec}: tuned {len(steps)} steps, pairs chosen for {sum(s['tc_pair'] for s in steps)}")
+    got = tz.tz_contract_amplitudes(plan, bits)
+    ref = np.array([tn.Contractor(spec, max_log2=24).amplitude(x) for x in bits[:16]])
+    assert rel_err(got[:16], ref, 49) <= (3e-5 if prec == "bf16x3" else TOL_C64)
