@@ -290,7 +290,11 @@ int tz_plan_profile_items(tz_plan *plan, double *out, int cap, int *n);
  * A request loop for amplitude-batch queries over resident plans: plans
  * stay bound to their workspaces, queries are admitted while their device
  * footprint fits the budget and a slot is free, and admitted queries run
- * concurrently on separate streams.
+ * concurrently on separate streams. A query runs in chunks of its slice
+ * range (each slice is an independent subtask, Sec. 1); between chunks a
+ * query yields its slot to queries that wait for one and resumes later with
+ * its partial sums kept, so long queries do not hold slots while short ones
+ * queue.
  */
 typedef struct {
   size_t hbm_budget;     /* bytes of device memory queries may hold at once         */
@@ -299,6 +303,9 @@ typedef struct {
   void *arena;           /* caller-owned device memory of arena_bytes for query buffers */
   size_t arena_bytes;
   int wait_admit;        /* 1: submit queues a query that does not fit yet; 0: TZ_EHBM_ADMIT */
+  double chunk_ms;       /* a query runs in chunks of its slice range of about this many
+                            ms of estimated work (0 = 4 ms); between chunks it yields
+                            its slot to waiting queries and keeps its partial sums   */
 } tz_server_opts;
 
 int tz_server_create(const tz_server_opts *opts, tz_server **out);

@@ -376,15 +376,18 @@ class Server(_Handle):
         return p50.value, p99.value, n.value
 
 
-def tz_server_create(arena_bytes, max_inflight=4, device=0, hbm_budget=0, wait_admit=True, arena=None) -> Server:
+def tz_server_create(arena_bytes, max_inflight=4, device=0, hbm_budget=0, wait_admit=True, arena=None,
+                     chunk_ms=0.0) -> Server:
     """Server with a device arena of arena_bytes (a torch uint8 tensor is
-    allocated when `arena` is None)."""
+    allocated when `arena` is None); queries run in chunks of about chunk_ms
+    of estimated work (0: the default, 4 ms) and yield between chunks."""
     import torch
     if arena is None:
         arena = torch.empty(arena_bytes + 256, dtype=torch.uint8, device=f"cuda:{device}")
     base = arena.data_ptr()
     aligned = (base + 255) & ~255
-    o = tz_server_opts(hbm_budget, max_inflight, device, ctypes.c_void_p(aligned), arena_bytes, int(wait_admit))
+    o = tz_server_opts(hbm_budget, max_inflight, device, ctypes.c_void_p(aligned), arena_bytes, int(wait_admit),
+                       float(chunk_ms))
     h = ctypes.c_void_p()
     check(lib().tz_server_create(ctypes.byref(o), ctypes.byref(h)))
     return Server(h, arena)

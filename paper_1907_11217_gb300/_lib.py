@@ -64,7 +64,8 @@ class tz_plan_profile(ctypes.Structure):
 
 class tz_server_opts(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_inflight", ctypes.c_int), ("device", ctypes.c_int),
-                ("arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t), ("wait_admit", ctypes.c_int)]
+                ("arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t), ("wait_admit", ctypes.c_int),
+                ("chunk_ms", ctypes.c_double)]
 
 
 P = ctypes.c_void_p

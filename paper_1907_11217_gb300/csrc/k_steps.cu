@@ -35,18 +35,19 @@ __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0
 __device__ __forceinline__ float2 table_value(const LeafJob &j, int i, float2 *) { return j.M[i]; }
 __device__ __forceinline__ double2 table_value(const LeafJob &j, int i, double2 *) { return j.Md[i]; }
 
-__global__ void init_state_kernel(GroupState *gs, int64_t lo, int64_t hi, int64_t n_rows) {
+__global__ void init_state_kernel(GroupState *gs, int64_t lo, int64_t hi, int64_t n_rows, int keep_error) {
   gs->slice = lo;
   gs->chunk = 0;
   gs->lo = lo;
   gs->hi = hi;
   gs->n_rows = n_rows;
   gs->groups_done = 0;
-  gs->tc_error = 0;
+  if (!keep_error) gs->tc_error = 0;
 }
 
-cudaError_t launch_init_state(GroupState *gs, int64_t lo, int64_t hi, int64_t n_rows, cudaStream_t s) {
-  init_state_kernel<<<1, 1, 0, s>>>(gs, lo, hi, n_rows);
+cudaError_t launch_init_state(GroupState *gs, int64_t lo, int64_t hi, int64_t n_rows, cudaStream_t s,
+                              int keep_error) {
+  init_state_kernel<<<1, 1, 0, s>>>(gs, lo, hi, n_rows, keep_error);
   return cudaGetLastError();
 }
 

@@ -100,7 +100,9 @@ struct AccumArgs {
   int dbl;                    // root is complex128
 };
 
-cudaError_t launch_init_state(GroupState *gs, int64_t lo, int64_t hi, int64_t n_rows, cudaStream_t s);
+// keep_error: a later part of the same call (the error word is kept)
+cudaError_t launch_init_state(GroupState *gs, int64_t lo, int64_t hi, int64_t n_rows, cudaStream_t s,
+                              int keep_error = 0);
 // dbl: tensors are complex128 (else complex64)
 cudaError_t launch_leaf_build(const LeafJob *jobs, int n_jobs, const GroupState *gs, const uint8_t *bits, int nq,
                               int g, const char *cbase, char *abase, int dbl, cudaStream_t s);

@@ -1137,13 +1137,13 @@ int read_tc_error(const tz_plan *p, const RunCtx &ctx) {
   return v;
 }
 
-void plan_run(tz_plan *p, const RunCtx &ctx, int64_t n_rows, int64_t lo, int64_t hi) {
+void plan_run(tz_plan *p, const RunCtx &ctx, int64_t n_rows, int64_t lo, int64_t hi, bool fresh) {
   if (!p->bound) fail(TZ_EINVAL, "plan has no workspace bound (tz_plan_bind_workspace)");
   cuda_check(cudaSetDevice(p->opts.device), "cudaSetDevice");
   cudaStream_t s = ctx.stream;
   auto *gs = reinterpret_cast<dev::GroupState *>(ctx.scratch + p->s_gs);
-  cuda_check(cudaMemsetAsync(ctx.scratch + p->s_acc, 0, (size_t)n_rows * 16, s), "clear accumulator");
-  cuda_check(dev::launch_init_state(gs, lo, hi, n_rows, s), "init group state");
+  if (fresh) cuda_check(cudaMemsetAsync(ctx.scratch + p->s_acc, 0, (size_t)n_rows * 16, s), "clear accumulator");
+  cuda_check(dev::launch_init_state(gs, lo, hi, n_rows, s, fresh ? 0 : 1), "init group state");
   const int64_t chunk = int64_t(1) << p->net.batch_log2;
   const int64_t n_chunks = (n_rows + chunk - 1) / chunk;
   const int64_t n_groups = n_chunks * (hi - lo);

@@ -119,8 +119,10 @@ void plan_bind(tz_plan *p, void *ws, size_t bytes);
 // Contract all groups of the slice range [lo, hi) for n rows already in the
 // scratch part's bitstring buffer; leaves the FP64 sums in its accumulator
 // (asynchronous on ctx.stream). With use_graph, the launches of a group are
-// captured once per scratch part and replayed.
-void plan_run(tz_plan *p, const RunCtx &ctx, int64_t n_rows, int64_t lo, int64_t hi);
+// captured once per scratch part and replayed. fresh = false continues a
+// call: the accumulator and the error word keep what earlier slice ranges
+// left (a query run in several slice ranges, as the server does).
+void plan_run(tz_plan *p, const RunCtx &ctx, int64_t n_rows, int64_t lo, int64_t hi, bool fresh = true);
 // The error word of a scratch part: 1 when a tensor-core product of the last
 // call on it (or of the bind-time steps) timed out in a bounded wait.
 // Synchronous (reads device memory); call after the stream has finished.

@@ -7,6 +7,14 @@
 // soon as a slot and enough arena are free, and their launches overlap on the
 // device. A worker thread admits queued queries (first fit, in arrival order)
 // and retires finished ones; results wait in pinned host memory until polled.
+//
+// A query runs in chunks of its slice range (about chunk_ms of estimated
+// work each; Sec. 1's subtasks are independent, so any cut is exact). When a
+// chunk ends while queries wait for a slot, the running query yields: it
+// keeps its scratch part (its partial sums and group state) and resumes, on
+// whichever slot frees up next, after the waiting queries have been started.
+// So a query of thousands of slices does not hold a slot while small queries
+// queue behind it.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -23,7 +31,7 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-enum QState { Q_QUEUED = 0, Q_RUNNING = 1, Q_DONE = 2, Q_FAILED = 3 };
+enum QState { Q_QUEUED = 0, Q_RUNNING = 1, Q_DONE = 2, Q_FAILED = 3, Q_PAUSED = 4 };
 
 struct Query {
   uint64_t ticket = 0;
@@ -38,6 +46,9 @@ struct Query {
   int err = TZ_OK;
   std::string msg;
   Clock::time_point t_submit, t_done;
+  int64_t lo = 0, hi = 0;   // the plan's slice range at submission
+  int64_t next = 0;         // first slice not yet launched
+  int64_t chunk = 1;        // slices per chunk
 };
 
 struct Slot {
@@ -47,6 +58,7 @@ struct Slot {
   double *pin_out = nullptr;
   size_t cap_in = 0, cap_out = 0;
   uint64_t ticket = 0;  // query running here, 0 = free
+  bool last = false;    // the work in flight ends the query (its copy-out included)
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -58,6 +70,7 @@ struct tz_server {
   std::vector<Slot> slots;
   std::map<uint64_t, Query> queries;
   std::deque<uint64_t> queue;
+  std::deque<uint64_t> paused;  // started queries waiting for a slot
   std::vector<std::pair<int64_t, int64_t>> used;  // arena intervals (offset, size)
   size_t in_use = 0;
   uint64_t next_ticket = 1;
@@ -104,67 +117,104 @@ struct tz_server {
     }
   }
 
-  // Launch query q on slot s (called with the lock held).
-  void start(Query &q, int s) {
+  // Launch the next chunk of query q on slot s (called with the lock held):
+  // the first chunk also copies the bitstrings in and clears the partial
+  // sums; the last one also copies the amplitudes and the error word out.
+  void launch_chunk(Query &q, int s) {
     Slot &sl = slots[s];
     tz_plan *p = q.plan;
     const int nq = p->net.n_qubits;
-    // pinned out: the amplitudes, then the scratch part's error word
-    ensure_pinned(sl, (size_t)q.n * nq, (size_t)q.n * 16 + 16);
-    std::memcpy(sl.pin_in, q.bits.data(), (size_t)q.n * nq);
     char *scratch = static_cast<char *>(opts.arena) + q.arena_off;
     tz::RunCtx ctx{scratch, sl.stream};
-    tz::cuda_check(cudaMemcpyAsync(scratch + p->s_bits, sl.pin_in, (size_t)q.n * nq, cudaMemcpyHostToDevice,
-                                   sl.stream),
-                   "query bitstrings in");
-    tz::plan_run(p, ctx, q.n, p->lo, p->hi);
-    tz::cuda_check(cudaMemcpyAsync(sl.pin_out, scratch + p->s_acc, (size_t)q.n * 16, cudaMemcpyDeviceToHost,
-                                   sl.stream),
-                   "query amplitudes out");
-    const auto *gs = reinterpret_cast<const tz::dev::GroupState *>(scratch + p->s_gs);
-    tz::cuda_check(cudaMemcpyAsync(sl.pin_out + 2 * q.n, &gs->tc_error, sizeof(int), cudaMemcpyDeviceToHost,
-                                   sl.stream),
-                   "query error word out");
+    const bool first = q.next == q.lo;
+    if (first) {
+      ensure_pinned(sl, (size_t)q.n * nq, (size_t)q.n * 16 + 16);
+      std::memcpy(sl.pin_in, q.bits.data(), (size_t)q.n * nq);
+      tz::cuda_check(cudaMemcpyAsync(scratch + p->s_bits, sl.pin_in, (size_t)q.n * nq, cudaMemcpyHostToDevice,
+                                     sl.stream),
+                     "query bitstrings in");
+    }
+    const int64_t lo = q.next, hi = std::min(q.hi, q.next + q.chunk);
+    tz::plan_run(p, ctx, q.n, lo, hi, first);
+    q.next = hi;
+    sl.last = hi == q.hi;
+    if (sl.last) {
+      // pinned out: the amplitudes, then the scratch part's error word
+      ensure_pinned(sl, (size_t)q.n * nq, (size_t)q.n * 16 + 16);
+      tz::cuda_check(cudaMemcpyAsync(sl.pin_out, scratch + p->s_acc, (size_t)q.n * 16, cudaMemcpyDeviceToHost,
+                                     sl.stream),
+                     "query amplitudes out");
+      const auto *gs = reinterpret_cast<const tz::dev::GroupState *>(scratch + p->s_gs);
+      tz::cuda_check(cudaMemcpyAsync(sl.pin_out + 2 * q.n, &gs->tc_error, sizeof(int), cudaMemcpyDeviceToHost,
+                                     sl.stream),
+                     "query error word out");
+    }
     tz::cuda_check(cudaEventRecord(sl.done, sl.stream), "query event");
     sl.ticket = q.ticket;
     q.slot = s;
     q.state = Q_RUNNING;
   }
 
-  void step() {  // one pass of retire + admit, lock held
+  int free_slot() const {
+    for (size_t s = 0; s < slots.size(); s++)
+      if (!slots[s].ticket) return (int)s;
+    return -1;
+  }
+
+  void fail_query(Query &q, int code, const std::string &m) {
+    q.state = Q_FAILED;
+    q.err = code;
+    q.msg = m;
+    q.t_done = Clock::now();
+    latencies.push_back(std::chrono::duration<double>(q.t_done - q.t_submit).count());
+    if (q.arena_off >= 0) arena_free(q.arena_off);
+    q.arena_off = -1;
+  }
+
+  void step() {  // one pass of retire + continue/yield + admit, lock held
     for (size_t s = 0; s < slots.size(); s++) {
       Slot &sl = slots[s];
       if (!sl.ticket) continue;
       cudaError_t e = cudaEventQuery(sl.done);
       if (e == cudaErrorNotReady) continue;
       Query &q = queries[sl.ticket];
-      int tc_error = 0;
-      if (e == cudaSuccess) std::memcpy(&tc_error, sl.pin_out + 2 * q.n, sizeof(int));
-      if (e == cudaSuccess && tc_error) {
-        q.state = Q_FAILED;
-        q.err = TZ_ETIMEOUT;
-        q.msg = "a tensor-core product of this query timed out in a bounded wait";
-      } else if (e == cudaSuccess) {
-        q.out.assign(sl.pin_out, sl.pin_out + 2 * q.n);
-        q.state = Q_DONE;
-      } else {
-        q.state = Q_FAILED;
-        q.err = TZ_ECUDA;
-        q.msg = cudaGetErrorString(e);
+      sl.ticket = 0;
+      if (e != cudaSuccess) {
+        fail_query(q, TZ_ECUDA, cudaGetErrorString(e));
+        continue;
       }
+      if (!sl.last) {
+        // more slices: yield the slot to a waiting query, else go on here
+        if (!queue.empty()) {
+          q.state = Q_PAUSED;
+          q.slot = -1;
+          paused.push_back(q.ticket);
+        } else {
+          try {
+            launch_chunk(q, (int)s);
+          } catch (const tz::Error &err) {
+            fail_query(q, err.code, err.what());
+          }
+        }
+        continue;
+      }
+      int tc_error = 0;
+      std::memcpy(&tc_error, sl.pin_out + 2 * q.n, sizeof(int));
+      if (tc_error) {
+        fail_query(q, TZ_ETIMEOUT, "a tensor-core product of this query timed out in a bounded wait");
+        continue;
+      }
+      q.out.assign(sl.pin_out, sl.pin_out + 2 * q.n);
+      q.state = Q_DONE;
       q.t_done = Clock::now();
       latencies.push_back(std::chrono::duration<double>(q.t_done - q.t_submit).count());
       arena_free(q.arena_off);
-      sl.ticket = 0;
+      q.arena_off = -1;
     }
+    // new queries first (first fit in arrival order), then paused ones
     for (auto it = queue.begin(); it != queue.end();) {
-      int free_slot = -1;
-      for (size_t s = 0; s < slots.size(); s++)
-        if (!slots[s].ticket) {
-          free_slot = (int)s;
-          break;
-        }
-      if (free_slot < 0) break;
+      const int fs = free_slot();
+      if (fs < 0) break;
       Query &q = queries[*it];
       int64_t off = arena_alloc(q.bytes);
       if (off < 0) {
@@ -173,14 +223,22 @@ struct tz_server {
       }
       q.arena_off = off;
       try {
-        start(q, free_slot);
+        launch_chunk(q, fs);
       } catch (const tz::Error &e) {
-        arena_free(off);
-        q.state = Q_FAILED;
-        q.err = e.code;
-        q.msg = e.what();
+        fail_query(q, e.code, e.what());
       }
       it = queue.erase(it);
+    }
+    while (!paused.empty()) {
+      const int fs = free_slot();
+      if (fs < 0) break;
+      Query &q = queries[paused.front()];
+      paused.pop_front();
+      try {
+        launch_chunk(q, fs);
+      } catch (const tz::Error &e) {
+        fail_query(q, e.code, e.what());
+      }
     }
   }
 
@@ -189,7 +247,7 @@ struct tz_server {
     std::unique_lock<std::mutex> lk(mu);
     while (!stop) {
       step();
-      bool busy = !queue.empty();
+      bool busy = !queue.empty() || !paused.empty();
       for (auto &sl : slots) busy |= sl.ticket != 0;
       cv.wait_for(lk, busy ? std::chrono::microseconds(20) : std::chrono::milliseconds(2));
     }
@@ -260,6 +318,18 @@ int tz_server_submit(tz_server *srv, tz_plan *plan, const uint8_t *bitstrings, i
   q.plan = plan;
   q.bits.assign(bitstrings, bitstrings + n * nq);
   q.n = n;
+  q.lo = q.next = plan->lo;
+  q.hi = plan->hi;
+  // slices per chunk: about chunk_ms of work by the plan's own estimate
+  // (useful flops at a modest rate plus a few microseconds per launch, for
+  // every bitstring group of the query)
+  {
+    const tz_plan_stats &st = plan->stats;
+    const double groups = (double)((n + (int64_t(1) << plan->net.batch_log2) - 1) >> plan->net.batch_log2);
+    const double group_s = st.flops_per_group / 100e12 + st.n_launches_per_group * 4e-6;
+    const double chunk_s = (srv->opts.chunk_ms > 0 ? srv->opts.chunk_ms : 4.0) * 1e-3;
+    q.chunk = std::max<int64_t>(1, (int64_t)(chunk_s / std::max(group_s * groups, 1e-9)));
+  }
   q.bytes = bytes;
   q.t_submit = Clock::now();
   *ticket = q.ticket;

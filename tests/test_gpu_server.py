@@ -84,3 +84,39 @@ def test_admission_budget(tz):
                     out[t] = r
     assert len(out) == len(ts)
     one.close()
+
+
+def test_long_query_yields_its_slot(tz):
+    """One slot, chunks of one slice: a query over 2^k slices submitted
+    first yields the slot between chunks, so short queries submitted after
+    it finish before it; every result equals the query run alone (the
+    chunks' partial sums stay in the query's scratch part)."""
+    big_spec = grid_spec(4, 5, 16, 4)
+    big, *_ = make_plan(tz, big_spec, slice_bits=5, small_log2=5, k_max=6, use_graph=True, max_bitstrings=8)
+    assert big.stats()["k"] >= 5
+    small_spec = grid_spec(4, 4, 10, 1)
+    small, *_ = make_plan(tz, small_spec, max_bitstrings=8)
+    big_bits = ti.random_bitstrings(20, 3, 21)
+    small_bits = [ti.random_bitstrings(16, 2, 30 + i) for i in range(4)]
+    alone_big = tz.tz_contract_amplitudes(big, big_bits)
+    alone_small = [tz.tz_contract_amplitudes(small, b) for b in small_bits]
+    need = max(big.stats()["scratch_bytes"], small.stats()["scratch_bytes"])
+    srv = tz.tz_server_create(arena_bytes=6 * need + 65536, max_inflight=1, chunk_ms=1e-6)
+    t_big = srv.submit(big, big_bits)
+    t_small = [srv.submit(small, b) for b in small_bits]
+    order, res = [], {}
+    t0 = time.time()
+    while len(res) < 5 and time.time() - t0 < 120:
+        for t in [t_big] + t_small:
+            if t not in res:
+                r = srv.poll(t)
+                if r is not None:
+                    res[t] = r
+                    order.append(t)
+    assert len(res) == 5
+    assert order[-1] == t_big, order
+    assert rel_err(res[t_big], alone_big, 20) <= 1e-6
+    assert rel_err(res[t_big], sv.amplitudes(big_spec, big_bits), 20) <= 1e-5
+    for t, a in zip(t_small, alone_small):
+        assert rel_err(res[t], a, 16) <= 1e-6
+    srv.close()
