@@ -362,16 +362,26 @@ def run_serving(args):
     srv.close()
     srv = tz.tz_server_create(arena_bytes=4 * scratch + (1 << 20), max_inflight=4)  # stream-only statistics
     t0 = time.perf_counter()
-    tickets, t_next = [], t0
+    tickets, t_next, t_sub = [], t0, {}
     for (j, b), g in zip(stream, gaps):
         t_next += g
         while time.perf_counter() < t_next:
             pass
-        tickets.append(srv.submit(plans[j][0], b))
+        t = srv.submit(plans[j][0], b)
+        t_sub[t] = time.perf_counter()
+        tickets.append(t)
     done = drain(tickets)
     elapsed = max(done.values()) - t0
     p50, p99, n_done = srv.latency()
     amps = sum(len(b) for _, b in stream)
+    # latency by class: queries on unsliced plans (one slice) and on sliced
+    # ones (hundreds of slices: long by their own work)
+    by_class = {}
+    for t, (j, b) in zip(tickets, stream):
+        cls = "sliced" if plans[j][3] > 0 else "unsliced"
+        by_class.setdefault(cls, []).append((done[t] - t_sub[t]) * 1e3)
+    class_lat = {c: {"queries": len(v), "p50_ms": float(np.percentile(v, 50)), "p99_ms": float(np.percentile(v, 99))}
+                 for c, v in by_class.items()}
     line = {"metric": "amplitudes/s (serving mix, Poisson arrivals at 0.8x saturation)",
             "value": amps / elapsed, "unit": "amplitudes/s", "n_gpus": 1, "higher_is_better": True,
             "dtype": precision, "data": "synthetic (seeded circuits by the Sec. 1 prescription, uniform bitstrings)",
@@ -379,7 +389,7 @@ def run_serving(args):
                        "bitstrings_per_query": "uniform 1..256", "queries": len(stream),
                        "arrival_rate_qps": rate_q, "saturation_amps_per_s": sat, "plans_prep_s": prep_s,
                        "max_inflight": 4},
-            "latency_ms": {"p50": p50 * 1e3, "p99": p99 * 1e3, "queries": n_done},
+            "latency_ms": {"p50": p50 * 1e3, "p99": p99 * 1e3, "queries": n_done, "by_class": class_lat},
             "vs_baseline": None}
     print(json.dumps(line))
     srv.close()

@@ -131,7 +131,8 @@ def test_tensor_core_path_5x6(tz, prec):
         assert prof["gemm_simt"]["launches"] + prof["gemm_skinny"]["launches"] > 0
     else:
         assert prof["gemm_tc"]["launches"] > 0
-        assert err <= (1e-3 if prec == "bf16x3" else TOL_C64)
+        # bf16x3 measured 9.6e-6 on GB300
+        assert err <= (3e-5 if prec == "bf16x3" else TOL_C64)
 
 
 @pytest.mark.parametrize("prec", ["c64", "c128"])
@@ -175,7 +176,7 @@ def test_tensor_core_scatter_epilogue_n_low(tz, prec):
     ref = np.array([oc.amplitude(x) for x in bits])
     err = rel_err(got, ref, 49)
     print(f"grid7x7 d16 batch64 {prec}: max rel err {err:.3e}")
-    assert err <= (1e-3 if prec == "bf16x3" else TOL_C64)
+    assert err <= (3e-5 if prec == "bf16x3" else TOL_C64)   # bf16x3 measured 9.3e-6
 
 
 def test_slice_farm_ledger_resume_on_gpu(tz, tmp_path):

@@ -87,7 +87,7 @@ def test_bristlecone70_depth32_properties(tz):
         parts.append(tz.tz_contract_amplitudes(ps, bits))
     add = rel_err(np.sum(parts, axis=0), a, 70)
     print(f"bristlecone70 d32 slices (k={k}) sum vs unsliced (split TF32): {add:.2e}")
-    assert add <= 3e-5
+    assert add <= 1e-5   # measured 2.3e-6
     # every mode, each on the tree its own time model picks, against
     # complex128 (one bitstring: the FP64 units of GB300 are slow); the
     # tensor-core modes share one tree, and the same-tree comparison is
@@ -174,7 +174,8 @@ def test_bristlecone70_reduced_depth_vs_oracle(tz, prec):
     got = tz.tz_contract_amplitudes(plan, bits)
     err = rel_err(got, ref, 70)
     print(f"bristlecone70 d12 {prec}: max rel err {err:.2e}")
-    assert err <= {"c128": 1e-12, "bf16x3": 1e-3}.get(prec, TOL)
+    # measured on GB300: 2.0e-6 in every FP32-class mode
+    assert err <= {"c128": 1e-12, "bf16x3": 6e-6}.get(prec, TOL)
 
 
 def test_grid7x7_depth32_config2_properties(tz):
@@ -207,7 +208,7 @@ def test_grid7x7_depth32_config2_properties(tz):
         results[prec] = a
     agree = rel_err(results["tf32x3"], results["c64"], 49)
     print(f"grid7x7 d32 split TF32 vs complex64: {agree:.2e}")
-    assert agree <= 2e-5
+    assert agree <= 1e-5   # measured 6.8e-6
     npk = np.abs(results["c64"]) ** 2 * 2.0 ** 49
     assert abs(npk.mean() - 1.0) < 0.5
 
@@ -259,7 +260,7 @@ def test_bristlecone72_reduced_depth_vs_oracle(tz, prec):
     got = tz.tz_contract_amplitudes(plan, bits)
     err = rel_err(got, ref, 72)
     print(f"bristlecone72 d12 {prec}: max rel err {err:.2e}")
-    assert err <= (TOL if prec == "c64" else 3e-5)
+    assert err <= (TOL if prec == "c64" else 6e-6)   # measured 1.8e-6 in both
 
 
 def test_grid7x7_depth40_precision_sweep(tz):
@@ -285,8 +286,8 @@ def test_grid7x7_depth40_precision_sweep(tz):
         out[prec] = tz.tz_contract_amplitudes(plan, bits)
     errs = {m: rel_err(out[m], out["c128"], 49) for m in ("c64", "tf32x3", "bf16x3", "fp16x3")}
     print("grid7x7 d40 (32 of 2^14 slices) errors vs complex128:", {m: f"{e:.2e}" for m, e in errs.items()})
-    # measured on GB300: c64 1.5e-7, tf32x3 4.9e-7, bf16x3 6.5e-7
-    assert errs["c64"] <= 1e-5 and errs["tf32x3"] <= 3e-5 and errs["bf16x3"] <= 1e-4 and errs["fp16x3"] <= 3e-5
+    # measured on GB300: c64 1.5e-7, tf32x3 4.9e-7, bf16x3 6.5e-7, fp16x3 2.3e-7
+    assert errs["c64"] <= 1e-5 and errs["tf32x3"] <= 1e-5 and errs["bf16x3"] <= 3e-6 and errs["fp16x3"] <= 1e-5
 
 
 # -------------------------------------------------------------------------
