@@ -182,13 +182,12 @@ def measured_peaks():
     return 6800.0, 1900.0, 1700.0, 2070.0, "fallback"
 
 
-# DRAM bytes (read + write) per useful flop of the tensor-core product, from
-# one ncu capture of a shape (M 16384, N 1024, K 2048, batch 1;
-# profiles/tc_split3_*_m16384_n1024_k2048.md) per mode, scaled to a launch by
-# its flops (row tiles re-read B, so traffic grows with flops). Only modes
-# whose kernel is unchanged since their capture are listed: the product's
-# epilogue has changed since all three captures, so none is (traffic: null).
-TC_DRAM_BYTES_PER_FLOP = {}
+# DRAM bytes (read + write) per tensor-core product launch, averaged over the
+# 20 product launches of one step, from one ncu capture of the bench command
+# itself (dram__bytes_read.sum + dram__bytes_write.sum, one pass;
+# profiles/launch_list_bristlecone70_d32_fp16x3.md), keyed by (precision,
+# workload). A mode or workload without an up-to-date capture reports null.
+TC_DRAM_BYTES_PER_LAUNCH = {("fp16x3", "bristlecone70_d32"): 1.4938e9}
 
 
 def plan_roofline(plan, precision, ms_per_group):
@@ -226,7 +225,7 @@ def plan_roofline(plan, precision, ms_per_group):
             "peaks": f"{src}: HBM {hbm:.0f} GB/s, tensor {tc or 0:.0f} TF/s, FP32 {simt:.1f} TF/s"}
 
 
-def roofline(prof, precision):
+def roofline(prof, precision, workload):
     """Dominant kernel kind of the profiled pass and its roofline position."""
     hbm, bf16, bf16_s, sm_mhz, src = measured_peaks()
     kinds = {k: v for k, v in prof.items() if v["launches"] > 0}
@@ -243,13 +242,13 @@ def roofline(prof, precision):
         out.update(bound="tensor", unit="TFLOP/s", achieved=d["flops"] / sec / 1e12, peak=peak,
                    peak_source=f"{src} bf16 x nominal {precision[:4]}/bf16 ratio",
                    issued_tflops=3 * d["flops"] / sec / 1e12)
-        if precision in TC_DRAM_BYTES_PER_FLOP:
-            out["traffic"] = TC_DRAM_BYTES_PER_FLOP[precision] * d["flops"] / d["launches"]
-            out["traffic_note"] = ("bytes per launch, scaled by flops from an ncu capture of the dominant shape "
-                                   "at batch 1")
+        if (precision, workload) in TC_DRAM_BYTES_PER_LAUNCH:
+            out["traffic"] = TC_DRAM_BYTES_PER_LAUNCH[(precision, workload)]
+            out["traffic_note"] = ("DRAM bytes per product launch, mean over one step's launches, from an ncu "
+                                   "capture of this command; algorithmic bytes per launch: algorithmic_bytes")
         else:
-            out["traffic_note"] = ("null: the product kernel changed after its last ncu capture (DRAM 0.99x to "
-                                   "1.1x the algorithmic bytes then; profiles/tc_split3_*)")
+            out["traffic_note"] = "null: no ncu capture of this mode and workload with the current kernel"
+        out["algorithmic_bytes"] = d["bytes"] / d["launches"]
     elif dom == "gemm_simt":
         out.update(bound="alu", unit="TFLOP/s", achieved=d["flops"] / sec / 1e12, peak=fp32_alu_tflops,
                    peak_source="152 SMs x 128 FP32 lanes x 2 flops x max SM clock")
@@ -641,7 +640,7 @@ def main():
     one_step(args.warmup + args.steps, reduce=False)
     prof = plan.profile()
     plan.profile_enable(False)
-    rl = roofline(prof, precision)
+    rl = roofline(prof, precision, args.workload)
     rl["plan_roofline"] = plan_roofline(plan, precision, ms / S)
     per_launch = {k: v["launches"] for k, v in prof.items()}
     launches_per_call = 1 + S * st["n_launches_per_group"]

@@ -399,6 +399,11 @@ int tz_debug_stall_tensor_core(int on);
  * their own per-step choice. The two forms give the same results (the same
  * splits, products and accumulation ranges). */
 int tz_tune_tc_pairs(int mode);
+/* Process-wide default of how far ahead (in k-blocks of the product's K loop)
+ * the tensor-core products prefetch their A tiles into L2, so that the tile
+ * loads that follow hit L2; 0 turns it off, -1 restores the initial default
+ * (the environment variable TZ_TC_PREFETCH, else 0). Results do not change. */
+int tz_tune_tc_prefetch(int kblocks);
 
 /* FP64 accumulation of partial amplitudes: acc[j] += scale * part[j] for
  * j < n, with part complex64 and acc, scale complex128 (re, im). */

@@ -124,6 +124,7 @@ SIGNATURES = {
     "tz_debug_set_wait_limit": (c_int, [c_int64]),
     "tz_debug_stall_tensor_core": (c_int, [c_int]),
     "tz_tune_tc_pairs": (c_int, [c_int]),
+    "tz_tune_tc_prefetch": (c_int, [c_int]),
 }
 
 _lib = None

@@ -588,6 +588,12 @@ int tz_tune_tc_pairs(int mode) {
   TZ_CATCH
 }
 
+int tz_tune_tc_prefetch(int kblocks) {
+  TZ_TRY
+  tz::dev::tc_set_prefetch(kblocks);
+  TZ_CATCH
+}
+
 int tz_debug_stall_tensor_core(int on) {
   TZ_TRY
   tz::cuda_check(tz::dev::tc_set_stall(on), "set stall switch");

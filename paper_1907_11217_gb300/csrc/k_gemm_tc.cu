@@ -195,6 +195,13 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, in
       : "memory");
 }
 
+// Hint that a tile will be loaded soon: bring it into L2 (no shared memory,
+// no completion to wait for).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *tm, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global [%0, {%1, %2}];" ::"l"((uint64_t)tm), "r"(x), "r"(y)
+               : "memory");
+}
+
 // Instruction descriptor: FP32 accumulator, TF32 A and B, both K-major,
 // N = n_cols, M = 128.
 __host__ __device__ constexpr uint32_t idesc_tf32(int n_cols) {
@@ -366,6 +373,7 @@ struct TcArgs {
   const uint32_t *bmax;  // FP16 mode: pb partial maxima of |B|
   int pb;
   int *err;              // set to 1 when a bounded wait ran out (never cleared here)
+  int prefetch;          // A tiles prefetched into L2 this many k-blocks ahead of their loads (0: off)
   CScatter sc;
 };
 
@@ -550,9 +558,31 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint64_t keep = l2_evict_last(), stream = l2_evict_first();
       int64_t g = 0;  // k-blocks issued by this CTA
       bool ok = true;
+      // L2 prefetch of A: a second cursor walks the same k-blocks a.prefetch
+      // ahead of the loads, so that a load finds its A tile in L2
+      int64_t pt = walker;
+      int pkb = -1;
+      Tile pd{};
+      bool pf = a.prefetch > 0;
+      auto prefetch_next = [&]() {
+        if (!pf) return;
+        if (pkb < 0 || ++pkb >= pd.kb1) {
+          if (pkb >= 0) pt += n_walkers;
+          if (pt >= n_tiles) {
+            pf = false;
+            return;
+          }
+          pd = decode(pt);
+          pkb = pd.kb0;
+        }
+#pragma unroll
+        for (int h = 0; h < stage_k<MODE>() / 32; h++) tma_prefetch_2d(&tmA, pkb * stage_k<MODE>() + 32 * h, pd.rowA);
+      };
+      for (int i = 0; i < a.prefetch; i++) prefetch_next();
       for (int64_t t = walker; t < n_tiles && ok; t += n_walkers) {
         const Tile d = decode(t);
         for (int kb = d.kb0; kb < d.kb1; kb++, g++) {
+          prefetch_next();
           const int s = (int)(g % STAGES);
           const int64_t round = g / STAGES;
           if (round > 0 && !wait(&empty[s], (uint32_t)((round - 1) & 1))) {
@@ -1285,6 +1315,20 @@ bool tc_pair_supported(int precision, int64_t M, int64_t N) {
 
 void tc_set_pairs(int mode) { g_pairs.store(mode < 0 ? -1 : (mode ? 1 : 0), std::memory_order_relaxed); }
 
+// L2 prefetch distance of the A tiles in k-blocks: the process default
+// (tc_set_prefetch; initially the environment variable TZ_TC_PREFETCH, else
+// 0: measured no faster on the bench tree's products).
+std::atomic<int> g_prefetch{-1};
+int tc_prefetch_default() {
+  int v = g_prefetch.load(std::memory_order_relaxed);
+  if (v < 0) {
+    const char *e = std::getenv("TZ_TC_PREFETCH");
+    v = e ? std::max(0, std::min(64, std::atoi(e))) : 0;
+  }
+  return v;
+}
+void tc_set_prefetch(int kblocks) { g_prefetch.store(kblocks < 0 ? -1 : std::min(64, kblocks), std::memory_order_relaxed); }
+
 cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M,
                             int64_t N, int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc,
                             void *scratch, size_t scratch_bytes, int *err, cudaStream_t s, int pair,
@@ -1356,6 +1400,7 @@ cudaError_t launch_cgemm_tc(int precision, const float2 *A, const float2 *B, flo
   }
   TcArgs args{};
   args.err = err;
+  args.prefetch = tc_prefetch_default();
   args.bmax = bmax;
   args.pb = pb;
   args.C = C;

@@ -141,6 +141,9 @@ bool tc_pair_supported(int precision, int64_t M, int64_t N);
 // Process default for pair = -1: 1 on, 0 off, -1 back to the initial default
 // (off unless the environment variable TZ_TC_PAIRS is 1).
 void tc_set_pairs(int mode);
+// Process default of the L2 prefetch distance of A tiles, in k-blocks (0 off,
+// -1 back to the initial default: the environment variable TZ_TC_PREFETCH, else 0).
+void tc_set_prefetch(int kblocks);
 // Test and debug hooks for the current device: the limit of the products'
 // bounded waits in ns (0 restores the default 2 s), and a switch that makes
 // every product first wait on a barrier that nothing arrives at.

@@ -25,10 +25,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--pairs", type=int, default=-1, choices=[-1, 0, 1],
                     help="split BF16/FP16 products: 1 pairs of CTAs, 0 single CTAs, -1 default")
+    ap.add_argument("--prefetch", type=int, default=-1,
+                    help="L2 prefetch distance of A tiles in k-blocks (0 off, -1 default)")
     a = ap.parse_args()
     import torch
     import paper_1907_11217_gb300 as tz
     tz.tz_tune_tc_pairs(a.pairs)
+    tz.tz_tune_tc_prefetch(a.prefetch)
     dev = "cuda"
     if a.op == "permute":
         x = torch.randn(2 << a.rank, device=dev)
@@ -61,7 +64,7 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / a.iters
-    print(json.dumps({"op": a.op, "precision": a.precision, **shape, "pairs": a.pairs, "ms": ms,
+    print(json.dumps({"op": a.op, "precision": a.precision, **shape, "pairs": a.pairs, "prefetch": a.prefetch, "ms": ms,
                       "useful_tflops": flops / ms / 1e9, "algorithmic_gbs": nbytes / ms / 1e6}))
 
 
