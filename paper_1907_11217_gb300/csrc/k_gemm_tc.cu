@@ -390,10 +390,10 @@ __device__ __forceinline__ int64_t scatter_bits(int64_t v, int n, const int8_t *
 // whatever the total K. The epilogue warps add the ranges in FP32 registers
 // (round to nearest), which bounds that bias at about 6e-9 kFoldK per product.
 constexpr int kFoldK = 128;
-// FP16 mode: one accumulation range per k-block (64 real K), because each
-// k-block of a row of A carries its own scale exponent.
+// FP16 mode: the same ranges of 128 real K (two k-blocks); each range of a
+// row of A carries its own scale exponent, chosen over the range's values.
 template <int MODE>
-__host__ __device__ constexpr int fold_k() { return MODE == MODE_F16 ? 64 : kFoldK; }
+__host__ __device__ constexpr int fold_k() { return kFoldK; }
 
 // Per stage (shared memory): the FP32 A tile as loaded (128 rows in boxes of
 // 128-byte rows: one TF32, two BF16) and the prepared B hi and lo tiles (BNP
@@ -451,6 +451,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                      const __grid_constant__ CUtensorMap tmBl, const __grid_constant__ CUtensorMap tmC, TcArgs a) {
   using L = TcSmem<MODE, BNP, STAGES, CG>;
   static_assert(CG == 1 || (MODE != MODE_TF32 && BNP == 128), "pairs: split BF16 / FP16, 128-column tiles");
+  // who waits for a drained accumulator before a range's products: the split
+  // warps when a range spans several k-blocks, else the MMA issuer
+  constexpr bool kSplitWaitsDrain = fold_k<MODE>() / stage_k<MODE>() > 1;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * L::STAGE + L::STAGING);
@@ -634,13 +637,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         const Tile d = decode(t);
         const int nkb = d.kb1 - d.kb0;
         for (int r0 = 0; r0 < nkb; r0 += kFoldKb, rg++) {
+          // ranges of several k-blocks: the split warps waited for this
+          // range's accumulator to be drained before releasing its first
+          // k-block (a wait on this thread stalls the tensor pipe until the
+          // products in flight finish; measured 3-13 % faster). Ranges of one
+          // k-block (FP16) wait here, which measured faster for them.
           const int buf = (int)(rg % L::NBUF);
-          const int64_t use = rg / L::NBUF;
-          if (use > 0 && !wait(&tempty[buf], (uint32_t)((use - 1) & 1))) {
-            ok = false;
-            break;
+          if (!kSplitWaitsDrain) {
+            const int64_t use = rg / L::NBUF;
+            if (use > 0 && !wait(&tempty[buf], (uint32_t)((use - 1) & 1))) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
           }
-          tc_fence_after();
           const uint32_t d_acc = tmem + (uint32_t)(buf * L::ACC_COLS);
           const int r1 = min(nkb, r0 + kFoldKb);
           for (int kb = r0; kb < r1; kb++, g++) {
@@ -689,14 +699,29 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;
     const int row = q * 32 + lane;
     const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16) + L::A_COL0;
-    int64_t g = 0;
+    constexpr int kFoldKb = fold_k<MODE>() / stage_k<MODE>();  // k-blocks per accumulation range
+    int64_t g = 0, rg = 0;
+    int range_se = 0;  // FP16: this row's scale exponent of the current range
     bool ok = true;
     for (int64_t tile = walker; tile < n_tiles && ok; tile += n_walkers) {
       const Tile d = decode(tile);
-      for (int kb = 0; kb < d.kb1 - d.kb0; kb++, g++) {
+      const int nkb = d.kb1 - d.kb0;
+      for (int kb = 0; kb < nkb; kb++, g++) {
         const int s = (int)(g % STAGES);
         const int slot = (int)(g % L::ASLOTS);
         const int64_t use = g / L::ASLOTS;
+        // a range's first k-block is released to the products only once the
+        // accumulator it goes to has been drained by the epilogue (a pair:
+        // the first CTA's split warps wait, on the barrier both CTAs'
+        // epilogues arrive at; the products wait for both CTAs' split warps)
+        if (kSplitWaitsDrain && kb % kFoldKb == 0) {
+          if ((CG == 1 || rank == 0) && rg >= L::NBUF &&
+              !wait(&tempty[rg % L::NBUF], (uint32_t)(((rg / L::NBUF) - 1) & 1))) {
+            ok = false;
+            break;
+          }
+          rg++;
+        }
         if ((use > 0 && !wait(&aempty[slot], (uint32_t)((use - 1) & 1))) ||
             !wait(&full[s], (uint32_t)((g / STAGES) & 1))) {
           ok = false;
@@ -741,22 +766,42 @@ __global__ void __launch_bounds__(kThreads, 1)
             tmem_st16(ts + (uint32_t)(32 + 16 * h), lo);
           }
         } else {
-          // FP16: the row's 64 values of this k-block set its exponent (the
-          // largest magnitude scaled into [2^14, 2^15)); then as for BF16,
-          // with FP16 pairs
+          // FP16: at a range's first k-block the row's values of the whole
+          // range (this k-block and, if the range has one, the next: its
+          // stage is waited for here) set the row's exponent for the range
+          // (the largest magnitude scaled into [2^14, 2^15)); then as for
+          // BF16, with FP16 pairs
           uint4 v[16];
 #pragma unroll
           for (int c = 0; c < 16; c++)
             v[c] = reinterpret_cast<const uint4 *>(A_raw(s) + (c >> 3) * BM * 128 + row * 128)[(c & 7) ^ (row & 7)];
-          // (FP32 max of magnitudes, one instruction a value; a NaN is
-          // skipped here and still propagates through the products)
-          float m = 0.f;
+          if (kb % kFoldKb == 0) {
+            // (FP32 max of magnitudes, one instruction a value; a NaN is
+            // skipped here and still propagates through the products)
+            float m = 0.f;
 #pragma unroll
-          for (int c = 0; c < 16; c++)
-            m = fmaxf(fmaxf(m, fmaxf(fabsf(__uint_as_float(v[c].x)), fabsf(__uint_as_float(v[c].y)))),
-                      fmaxf(fabsf(__uint_as_float(v[c].z)), fabsf(__uint_as_float(v[c].w))));
-          const int se = f16_scale_exp(__float_as_uint(m));
-          const float sa = pow2i(se);
+            for (int c = 0; c < 16; c++)
+              m = fmaxf(fmaxf(m, fmaxf(fabsf(__uint_as_float(v[c].x)), fabsf(__uint_as_float(v[c].y)))),
+                        fmaxf(fabsf(__uint_as_float(v[c].z)), fabsf(__uint_as_float(v[c].w))));
+            for (int j = 1; j < kFoldKb && kb + j < nkb; j++) {
+              const int64_t gj = g + j;
+              if (!wait(&full[gj % STAGES], (uint32_t)((gj / STAGES) & 1))) {
+                ok = false;
+                break;
+              }
+              const uint8_t *aj = A_raw((int)(gj % STAGES));
+#pragma unroll
+              for (int c = 0; c < 16; c++) {
+                const uint4 w = reinterpret_cast<const uint4 *>(aj + (c >> 3) * BM * 128 + row * 128)[(c & 7) ^ (row & 7)];
+                m = fmaxf(fmaxf(m, fmaxf(fabsf(__uint_as_float(w.x)), fabsf(__uint_as_float(w.y)))),
+                          fmaxf(fabsf(__uint_as_float(w.z)), fabsf(__uint_as_float(w.w))));
+              }
+            }
+            if (!ok) break;
+            range_se = f16_scale_exp(__float_as_uint(m));
+            aexp[(int)((rg - 1) % L::XRI) * BM + row] = (int8_t)range_se;
+          }
+          const float sa = pow2i(range_se);
           // 8 columns at a time, so the raw values die as they are split
 #pragma unroll
           for (int h = 0; h < 4; h++) {
@@ -770,7 +815,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             tmem_st8(ts + (uint32_t)(8 * h), hi);
             tmem_st8(ts + (uint32_t)(32 + 8 * h), lo);
           }
-          aexp[(int)(g % L::XRI) * BM + row] = (int8_t)se;
         }
         tmem_st_wait();
         tc_fence_before();
@@ -782,7 +826,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         } else {
           mbar_arrive(&conv[s]);
         }
-        if (MODE == MODE_F16) mbar_arrive(&xfull[g % L::XRI]);  // releases the exponent written above
+        // FP16: the range's last k-block releases its exponent to the epilogue
+        if (MODE == MODE_F16 && (kb % kFoldKb == kFoldKb - 1 || kb == nkb - 1)) mbar_arrive(&xfull[(rg - 1) % L::XRI]);
       }
     }
   } else {
