@@ -64,6 +64,10 @@ def parse():
     ap.add_argument("--batch-log2", type=int, default=0)
     ap.add_argument("--slices", type=int, default=0, help="slices per step (0: auto)")
     ap.add_argument("--log2-max", type=int, default=0, help="slicing target (0: workload default)")
+    ap.add_argument("--k-slices", type=int, default=0,
+                    help="slice exactly this many indices (config 2: 10), instead of slicing to a size target")
+    ap.add_argument("--bitstrings", type=int, default=0,
+                    help="bitstrings per step (0: 2^batch-log2); groups of 2^batch-log2 are contracted together")
     ap.add_argument("--restarts", type=int, default=16384,
                     help="tree search restarts (untimed preprocessing, run on all host threads)")
     ap.add_argument("--reconfigure", type=int, default=0,
@@ -111,9 +115,13 @@ def build_plan(tz, spec, args, precision, stream, device, log2_max, max_rows=0):
         if cache:
             np.save(cache, _TREES[key])
     tree = tz.tz_tree_from_pairs(net, _TREES[key])
-    sliced = tz.tz_slice_select(net, tree, log2_max, 40) if log2_max > 0 else []
+    if args.k_slices > 0:
+        sliced = tz.tz_slice_select(net, tree, 1, args.k_slices)
+    else:
+        sliced = tz.tz_slice_select(net, tree, log2_max, 40) if log2_max > 0 else []
     plan = tz.tz_plan_create(net, tree, sliced, precision=precision, device=device, stream=stream, use_graph=True,
-                             max_bitstrings=max_rows or 1 << max(args.batch_log2, 0), autotune=bool(args.autotune))
+                             max_bitstrings=max_rows or args.bitstrings or 1 << max(args.batch_log2, 0),
+                             autotune=bool(args.autotune))
     prep_s = time.perf_counter() - t0
     return plan, sliced, prep_s
 
@@ -361,15 +369,19 @@ def run_serving(args):
     srv.close()
     srv = tz.tz_server_create(arena_bytes=4 * scratch + (1 << 20), max_inflight=4)  # stream-only statistics
     t0 = time.perf_counter()
-    tickets, t_next, t_sub = [], t0, {}
+    tickets, t_next, t_sub, done = [], t0, {}, {}
     for (j, b), g in zip(stream, gaps):
         t_next += g
         while time.perf_counter() < t_next:
-            pass
+            # completions are polled while the next arrival is awaited, so
+            # each query's latency ends when it finished, not when polled
+            for t in tickets:
+                if t not in done and srv.poll(t) is not None:
+                    done[t] = time.perf_counter()
         t = srv.submit(plans[j][0], b)
         t_sub[t] = time.perf_counter()
         tickets.append(t)
-    done = drain(tickets)
+    done.update(drain([t for t in tickets if t not in done]))
     elapsed = max(done.values()) - t0
     p50, p99, n_done = srv.latency()
     amps = sum(len(b) for _, b in stream)
@@ -558,7 +570,7 @@ def main():
     st = plan.stats()   # the launch count follows the autotuned choices
     k = len(sliced)
     n_slices = 1 << k
-    B = 1 << args.batch_log2
+    B = args.bitstrings or 1 << args.batch_log2
     bits = ti.random_bitstrings(nq, B, WORKLOADS[args.workload][7] + rank)
     d_bits = torch.from_numpy(bits).to(f"cuda:{device}")
     d_out = torch.zeros(2 * B, dtype=torch.float64, device=f"cuda:{device}")
@@ -619,7 +631,8 @@ def main():
     # contract their own amplitudes
     slices_per_step = S * world
     s_per_amp = ms / 1e3 * n_slices / slices_per_step / B
-    flops_step = st["flops_per_group"] * slices_per_step
+    chunks = -(-B // (1 << args.batch_log2))   # groups of 2^batch_log2 bitstrings per slice
+    flops_step = st["flops_per_group"] * slices_per_step * chunks
     tflops = flops_step / (ms / 1e3) / 1e12
 
     # end to end through the host API: bitstrings in from host memory, FP64
@@ -641,9 +654,9 @@ def main():
     prof = plan.profile()
     plan.profile_enable(False)
     rl = roofline(prof, precision, args.workload)
-    rl["plan_roofline"] = plan_roofline(plan, precision, ms / S)
+    rl["plan_roofline"] = plan_roofline(plan, precision, ms / S / chunks)
     per_launch = {k: v["launches"] for k, v in prof.items()}
-    launches_per_call = 1 + S * st["n_launches_per_group"]
+    launches_per_call = 1 + S * chunks * st["n_launches_per_group"]
 
     # the same workload in the other modes (split precision against complex64),
     # each with its own tree and plan, timed over the same slice windows

@@ -228,6 +228,50 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Few outputs per batch, moderate summed index (m*n small, 64 <= k < 2048,
+// many batches): one warp per output element streams its A row and B row
+// (k-contiguous) with 16-byte loads and sums in FP32 (a shuffle reduction);
+// HBM-bound. The tiled kernels waste their tiles on such shapes (a batch of
+// 8192 1 x 1 products with k = 1024 ran 100x slower there).
+__global__ void __launch_bounds__(256)
+    cgemm_dot_warp_kernel(const float2 *__restrict__ A, const float2 *__restrict__ B, float2 *__restrict__ C,
+                          int64_t batch, int64_t M, int64_t N, int64_t K, int64_t sA, int64_t sB, int64_t sC,
+                          const __grid_constant__ CScatter sc, int scatter) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n_out = batch * M * N;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t o = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); o < n_out; o += warps) {
+    const int64_t z = o / (M * N);
+    const int64_t m = (o / N) % M;
+    const int64_t n = o % N;
+    const float4 *a = reinterpret_cast<const float4 *>(A + z * sA + m * K);
+    const float4 *b = reinterpret_cast<const float4 *>(B + z * sB + n * K);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int64_t k = lane; k < K / 2; k += 32) {
+      const float4 va = a[k], vb = b[k];
+      acc.x = fmaf(va.x, vb.x, acc.x);
+      acc.x = fmaf(-va.y, vb.y, acc.x);
+      acc.y = fmaf(va.x, vb.y, acc.y);
+      acc.y = fmaf(va.y, vb.x, acc.y);
+      acc.x = fmaf(va.z, vb.z, acc.x);
+      acc.x = fmaf(-va.w, vb.w, acc.x);
+      acc.y = fmaf(va.z, vb.w, acc.y);
+      acc.y = fmaf(va.w, vb.z, acc.y);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    if (lane == 0) {
+      const int64_t off = scatter ? scatter_bits(z, sc.nb, sc.pb) + scatter_bits(m, sc.nm, sc.pm) +
+                                        scatter_bits(n, sc.nn, sc.pn)
+                                  : z * sC + m * N + n;
+      C[off] = acc;
+    }
+  }
+}
+
 // Few outputs, long summed index (m*n small, k large): one block per output
 // element streams its A row and B row (both k-contiguous) with 16-byte loads;
 // each thread sums its strided share in FP32, then a tree reduction.
@@ -407,11 +451,21 @@ cudaError_t launch_zgemm_simt(const double2 *A, const double2 *B, double2 *C, in
 cudaError_t launch_cgemm_simt(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N,
                               int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s) {
   if (batch <= 0 || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
-  if (M * N <= 64 && K >= 2048 && (K % 2) == 0) {
+  const bool aligned = (K % 2) == 0 && (sA % 2) == 0 && (sB % 2) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0 &&
+                       (reinterpret_cast<uintptr_t>(B) & 15) == 0;
+  if (M * N <= 64 && K >= 2048 && aligned) {
     CScatter none{};
     const int64_t outs = batch * M * N;
     cgemm_dot_kernel<<<(unsigned)std::min<int64_t>(outs, 152 * 8), 256, 0, s>>>(A, B, C, batch, M, N, K, sA, sB, sC,
                                                                              sc ? *sc : none, sc ? 1 : 0);
+    return cudaGetLastError();
+  }
+  if (M * N <= 64 && K >= 64 && aligned) {
+    CScatter none{};
+    const int64_t outs = batch * M * N;
+    const int64_t blocks = std::min<int64_t>((outs + 7) / 8, 152 * 16);
+    cgemm_dot_warp_kernel<<<(unsigned)blocks, 256, 0, s>>>(A, B, C, batch, M, N, K, sA, sB, sC, sc ? *sc : none,
+                                                           sc ? 1 : 0);
     return cudaGetLastError();
   }
   if (N <= 4 && K <= 16 && M >= 256) {

@@ -823,7 +823,7 @@ static void item_cost(const tz_plan *p, const Item &it, int *kind, double *flops
       break;
     case IT_GEMM: {
       const PStep &ps = p->S[it.a];
-      const bool dot = ps.M * ps.N <= 64 && ps.K >= 2048 && (ps.K % 2) == 0;
+      const bool dot = ps.M * ps.N <= 64 && ps.K >= 64 && (ps.K % 2) == 0;
       *kind = ps.tc ? 4 : ps.skinny ? 6 : dot ? 7 : 3;
       *flops = 8.0 * ps.batch * (double)ps.M * (double)ps.N * (double)ps.K;
       *bytes = (double)p->esz * ps.batch * ((double)ps.M * ps.K + (double)ps.N * ps.K + (double)ps.M * ps.N);

@@ -42,7 +42,7 @@ def test_permute_bit_exact(env, rank):
 @pytest.mark.parametrize("batch,m,n,k", [(1, 1, 1, 1), (1, 7, 3, 5), (3, 64, 64, 8), (2, 130, 17, 33),
                                          (1, 1000, 2, 4), (5, 33, 80, 1), (1, 4096, 16, 64), (16, 256, 256, 256),
                                          (1, 1, 300, 9), (3, 4096, 1, 2), (1, 512, 4, 16), (2, 300, 3, 5),
-                                         (1, 1 << 16, 2, 8)])
+                                         (1, 1 << 16, 2, 8), (8192, 1, 1, 1024), (16, 8, 8, 64), (3, 2, 3, 200)])
 def test_cgemm_simt(env, batch, m, n, k):
     tz, torch = env
     rng = np.random.default_rng(m * 7 + n)
