@@ -45,6 +45,10 @@ WORKLOADS = {
 # faster per product but misses it on the Bristlecone-70 tree; its error is
 # reported beside the others)
 DEFAULT_PRECISION = "fp16x3"
+# Workload shapes beyond the circuit: exact slice count, bitstrings per step
+# and per group (config 2: a tree with 2^10 slices and 64 bitstrings, which
+# run as one batch of 64, the batch hyperedge of the network)
+WORKLOAD_SHAPE = {"grid7x7_d32": {"k_slices": 10, "bitstrings": 64, "batch_log2": 6}}
 # Table 2 (1449 x 88 vCPU), context only
 PAPER_S_PER_AMP = {"bristlecone70_d32": 0.43, "bristlecone70_d36": 5.6, "bristlecone70_d40": 580.7}
 
@@ -527,6 +531,9 @@ def run_reference(args):
 
 def main():
     args = parse()
+    for key, v in WORKLOAD_SHAPE.get(args.workload, {}).items():
+        if not getattr(args, key):
+            setattr(args, key, v)
     if args.impl == "reference":
         run_reference(args)
         return
