@@ -39,6 +39,7 @@ WORKLOADS = {
     "bristlecone70_d36": ("bristlecone", 0, 0, 70, 36, 3, 30, 103),
     "bristlecone70_d40": ("bristlecone", 0, 0, 70, 40, 3, 30, 103),
     "bristlecone70_d28": ("bristlecone", 0, 0, 70, 28, 3, 30, 103),
+    "bristlecone70_d32_open12": ("bristlecone", 0, 0, 70, 32, 3, 30, 103),
 }
 # The default mode: scaled split FP16, the tensor-core mode that meets the
 # 1e-5 bar against the FP64 oracle on every full-size workload (split BF16 is
@@ -48,7 +49,11 @@ DEFAULT_PRECISION = "fp16x3"
 # Workload shapes beyond the circuit: exact slice count, bitstrings per step
 # and per group (config 2: a tree with 2^10 slices and 64 bitstrings, which
 # run as one batch of 64, the batch hyperedge of the network)
-WORKLOAD_SHAPE = {"grid7x7_d32": {"k_slices": 10, "bitstrings": 64, "batch_log2": 6}}
+WORKLOAD_SHAPE = {"grid7x7_d32": {"k_slices": 10, "bitstrings": 64, "batch_log2": 6},
+                  # qubits 0..11 left open: every contraction yields the 4096
+                  # amplitudes of all their output assignments (the rest of
+                  # the bitstring uniform random)
+                  "bristlecone70_d32_open12": {"open_qubits": 12}}
 # Table 2 (1449 x 88 vCPU), context only
 PAPER_S_PER_AMP = {"bristlecone70_d32": 0.43, "bristlecone70_d36": 5.6, "bristlecone70_d40": 580.7}
 
@@ -66,6 +71,8 @@ def parse():
     ap.add_argument("--queries", type=int, default=96, help="serving_mix: queries in the Poisson stream")
     ap.add_argument("--precision", default="auto", choices=["auto", "c64", "tf32x3", "bf16x3", "fp16x3", "c128"])
     ap.add_argument("--batch-log2", type=int, default=0)
+    ap.add_argument("--open-qubits", type=int, default=0,
+                    help="leave output qubits 0..N-1 open: 2^N correlated amplitudes per bitstring and contraction")
     ap.add_argument("--slices", type=int, default=0, help="slices per step (0: auto)")
     ap.add_argument("--log2-max", type=int, default=0, help="slicing target (0: workload default)")
     ap.add_argument("--k-slices", type=int, default=0,
@@ -103,12 +110,12 @@ _TREES = {}
 
 def build_plan(tz, spec, args, precision, stream, device, log2_max, max_rows=0):
     circ = tz.tz_circuit_from_spec(spec)
-    net = tz.tz_network_from_circuit(circ, args.batch_log2)
+    net = tz.tz_network_from_circuit(circ, args.batch_log2, tuple(range(args.open_qubits)))
     t0 = time.perf_counter()
     # the time model that scores trees tells the CUDA-core modes from the
     # tensor-core ones only, so the three tensor-core modes share one search
     tc_mode = precision not in ("c64", "c128")
-    key = (spec, precision if not tc_mode else "tensor-core", log2_max)
+    key = (spec, precision if not tc_mode else "tensor-core", log2_max, args.open_qubits)
     cache = args.tree_file if tc_mode else ""
     if key not in _TREES and cache and os.path.exists(cache):
         _TREES[key] = np.load(cache)
@@ -276,11 +283,12 @@ def roofline(prof, precision, workload):
 ORACLE_MAX_LOG2 = 25
 
 
-def oracle_segments(tz, spec, pairs, batch_log2=0, cap=18):
+def oracle_segments(tz, spec, pairs, batch_log2=0, cap=18, open_qubits=0):
     """Sliced segments for the CPU baseline: the GPU tree, sliced further to
     a 2^cap intermediate cap, so that one slice is a bounded unit of oracle
-    work (the sum over all slices is the amplitude, Sec. 1)."""
-    net = tz.tz_network_from_circuit(tz.tz_circuit_from_spec(spec), batch_log2)
+    work (the sum over all slices is the amplitude, Sec. 1). Open output
+    qubits are never sliced, so the segments also slice the closed circuit."""
+    net = tz.tz_network_from_circuit(tz.tz_circuit_from_spec(spec), batch_log2, tuple(range(open_qubits)))
     tree = tz.tz_tree_from_pairs(net, pairs)
     sl = tz.tz_slice_select(net, tree, cap, 40)
     return [net.index_info(e) for e in sl]
@@ -580,7 +588,8 @@ def main():
     B = args.bitstrings or 1 << args.batch_log2
     bits = ti.random_bitstrings(nq, B, WORKLOADS[args.workload][7] + rank)
     d_bits = torch.from_numpy(bits).to(f"cuda:{device}")
-    d_out = torch.zeros(2 * B, dtype=torch.float64, device=f"cuda:{device}")
+    A = B << args.open_qubits   # amplitudes per contraction of the B bitstrings
+    d_out = torch.zeros(2 * A, dtype=torch.float64, device=f"cuda:{device}")
 
     # ranks split the slices of one amplitude; with fewer slices than ranks
     # (the default tree has none) they are replicas instead: each contracts
@@ -637,7 +646,7 @@ def main():
     # slices of one amplitude per step, all ranks together; replicas each
     # contract their own amplitudes
     slices_per_step = S * world
-    s_per_amp = ms / 1e3 * n_slices / slices_per_step / B
+    s_per_amp = ms / 1e3 * n_slices / slices_per_step / A
     chunks = -(-B // (1 << args.batch_log2))   # groups of 2^batch_log2 bitstrings per slice
     flops_step = st["flops_per_group"] * slices_per_step * chunks
     tflops = flops_step / (ms / 1e3) / 1e12
@@ -653,7 +662,7 @@ def main():
         t0 = time.perf_counter()
         tz.tz_contract_amplitudes(plan_e2e, bits)
         e2e_times.append(time.perf_counter() - t0)
-    e2e_s = statistics.median(e2e_times) * n_slices / slices_per_step / B
+    e2e_s = statistics.median(e2e_times) * n_slices / slices_per_step / A
 
     # per-kernel profile of one more step (events around every launch)
     plan.profile_enable(True)
@@ -696,7 +705,7 @@ def main():
             e1.record(stream)
             torch.cuda.synchronize()
             ms2 = e0.elapsed_time(e1) / 2
-            compare[other] = {"s_per_amplitude": ms2 / 1e3 * n2 / S2 / B,
+            compare[other] = {"s_per_amplitude": ms2 / 1e3 * n2 / S2 / A,
                               "contraction_tflops": st2["flops_per_group"] * S2 / (ms2 / 1e3) / 1e12,
                               "k_sliced": k2}
             p2.close()
@@ -707,9 +716,10 @@ def main():
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        tc_key = (spec, "tensor-core" if precision not in ("c64", "c128") else precision, log2_max)
-        cpu = cpu_oracle_sample(spec, oracle_segments(tz, spec, _TREES[tc_key], args.batch_log2), bits[0],
-                                args.cpu_seconds)
+        tc_key = (spec, "tensor-core" if precision not in ("c64", "c128") else precision, log2_max,
+                  args.open_qubits)
+        cpu = cpu_oracle_sample(spec, oracle_segments(tz, spec, _TREES[tc_key], args.batch_log2,
+                                                      open_qubits=args.open_qubits), bits[0], args.cpu_seconds)
     paper = PAPER_S_PER_AMP.get(args.workload)
     line = {
         "metric": metric_name(args.workload),
@@ -718,12 +728,13 @@ def main():
         "vs_baseline": (s_per_amp / paper) if paper else None,
         "dtype": precision, "data": "synthetic (seeded circuit by the Sec. 1 prescription, uniform random bitstrings)",
         "config": {"workload": args.workload, "n_qubits": nq, "depth": f"1+{WORKLOADS[args.workload][4]}+1",
-                   "batch_bitstrings": B, "k_sliced": k, "slices_total": n_slices,
+                   "batch_bitstrings": B, "open_qubits": args.open_qubits, "amplitudes_per_step": A,
+                   "k_sliced": k, "slices_total": n_slices,
                    "slices_per_step": slices_per_step, "log2_max_intermediate": st["max_log2"],
                    "tree_restarts": args.restarts, "tree_reconfigure": args.reconfigure, "preprocessing_s": prep_s,
                    "l2": "intermediates larger than L2" if st["max_log2"] >= 25 else "working set may fit L2",
                    "parallelism": f"replicas x{world}" if replicas else f"slices x{world}",
-                   "extrapolation": f"step time x 2^{k} / {slices_per_step} slices per step / {B} bitstrings"},
+                   "extrapolation": f"step time x 2^{k} / {slices_per_step} slices per step / {A} amplitudes"},
         "contraction_tflops": tflops,
         "plan": {"flops_per_slice": st["flops_per_group"], "bytes_per_slice": st["bytes_per_group"],
                  "permute_bytes_per_slice": st["permute_bytes_per_group"], "steps": st["n_steps"],
@@ -732,7 +743,7 @@ def main():
                  "const_steps": st["n_const_steps"], "const_flops": st["const_flops"],
                  "bind_ms": plan_bind_ms, "autotuned_steps": n_tuned},
         "e2e": {"value": e2e_s, "unit": "s/amplitude", "h2d_bytes_per_step": int(bits.nbytes),
-                "d2h_bytes_per_step": 16 * B},
+                "d2h_bytes_per_step": 16 * A},
         "roofline": rl,
         "compare": compare,
         "cpu_baseline": cpu,

@@ -105,16 +105,32 @@ void tz_circuit_destroy(tz_circuit *c);
  * its output tensor (exact rewrites). Output tensors carry `batch_log2`
  * extra open indices (the bitstring batch): one call contracts 2^batch_log2
  * bitstrings at once.
+ *
+ * Open output qubits (the multi-amplitude trend of Sec. 2, Table 1: more
+ * amplitudes per contraction, less time each): the listed qubits get no
+ * output tensor; their last wire index stays open to the end of the
+ * contraction, so one contraction yields the 2^n_open amplitudes of every
+ * assignment of those qubits' output bits. Each bitstring then yields
+ * 2^n_open amplitudes: amplitude o (0 <= o < 2^n_open) is that of the
+ * bitstring with the output bit of open_qubits[j] (sorted ascending) set to
+ * bit j of o; the bitstring's own bits on the open qubits are ignored.
+ * TZ_EINVAL: more than 12 open qubits, a qubit out of range or listed twice,
+ * or every qubit open (one must stay closed).
  */
 typedef struct {
-  int batch_log2;   /* 0..8: bitstrings contracted together per group    */
+  int batch_log2;               /* 0..8: bitstrings contracted together per group */
+  int n_open;                   /* 0..12 open output qubits                       */
+  const int32_t *open_qubits;   /* n_open qubit numbers (any order; caller-owned,
+                                   read during the call only)                     */
 } tz_network_opts;
 
 int tz_network_from_circuit(const tz_circuit *c, const tz_network_opts *opts, tz_network **out);
 int tz_network_n_tensors(const tz_network *net);
 int tz_network_n_indices(const tz_network *net);
 /* Index info: *qubit = owning qubit and *segment = segment number for wire
- * indices; *qubit = -1 and *segment = bit number for batch indices. */
+ * indices; *qubit = -1 and *segment = bit number for batch indices;
+ * *qubit = -2 and *segment = j for the index of open output qubit j (bit j of
+ * the open value, the j-th smallest open qubit). */
 int tz_network_index_info(const tz_network *net, int index, int *qubit, int *segment);
 /* Indices of tensor t in storage order (bit p of a linear element offset is
  * the p-th index). cap = capacity of idx; *rank receives the rank. */
@@ -216,7 +232,7 @@ typedef struct {
                                     computed once per bind, not per group            */
   double bind_ms;                /* wall time of the last tz_plan_bind_workspace     */
   int n_tuned_steps;             /* tensor-core steps with an autotuned launch choice */
-  int pad0;
+  int n_open;                    /* open output qubits: 2^n_open amplitudes per bitstring */
 } tz_plan_stats;
 
 /* Build a plan: classify steps, choose layouts, permutes and kernels, lay
@@ -245,12 +261,15 @@ int tz_plan_describe(const tz_plan *plan, char *buf, size_t cap, size_t *len);
 
 /* Amplitudes of n bitstrings (host pointers): copies the bitstrings in,
  * contracts every group of the slice range, sums partial amplitudes in
- * FP64, copies 2n doubles out, and synchronises the plan's stream.
+ * FP64, copies 2n doubles out (2n * 2^n_open with open output qubits: row r
+ * holds the 2^n_open amplitudes of bitstring r, in open-value order), and
+ * synchronises the plan's stream.
  * n = 0 does nothing and returns TZ_OK (the pointers are not read); n above
  * the plan's max_bitstrings, or negative, returns TZ_EINVAL. */
 int tz_contract_amplitudes(tz_plan *plan, const uint8_t *bitstrings, int64_t n, double *out);
 /* Same with device pointers; asynchronous on the plan's stream (no host
- * synchronisation). d_bitstrings: n x n_qubits uint8; d_out: 2n doubles.
+ * synchronisation). d_bitstrings: n x n_qubits uint8; d_out: 2n doubles
+ * (2n * 2^n_open with open output qubits).
  * If a tensor-core product of the call times out in one of its bounded
  * waits, the amplitudes it could have affected are written as NaN, and
  * tz_plan_status reports TZ_ETIMEOUT. (tz_contract_amplitudes returns
@@ -311,7 +330,8 @@ typedef struct {
 int tz_server_create(const tz_server_opts *opts, tz_server **out);
 /* Queue a query (bitstrings copied). *ticket identifies it. */
 int tz_server_submit(tz_server *srv, tz_plan *plan, const uint8_t *bitstrings, int64_t n, uint64_t *ticket);
-/* Non-blocking: *done = 1 and out (2n doubles) filled once the query has
+/* Non-blocking: *done = 1 and out (2n doubles, 2n * 2^n_open with open
+ * output qubits) filled once the query has
  * finished; *done = 0 otherwise. A finished ticket is released after a
  * successful poll. */
 int tz_server_poll(tz_server *srv, uint64_t ticket, double *out, int *done);

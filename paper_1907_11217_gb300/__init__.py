@@ -110,10 +110,11 @@ def tz_circuit_generate_bristlecone(n_qubits, depth, seed) -> Circuit:
 class Network(_Handle):
     _destroy = "tz_network_destroy"
 
-    def __init__(self, h, n_qubits, batch_log2):
+    def __init__(self, h, n_qubits, batch_log2, open_qubits=()):
         super().__init__(h)
         self.n_qubits = n_qubits
         self.batch_log2 = batch_log2
+        self.open_qubits = tuple(sorted(open_qubits))
 
     @property
     def n_tensors(self):
@@ -135,11 +136,16 @@ class Network(_Handle):
         return list(buf[: r.value])
 
 
-def tz_network_from_circuit(circ: Circuit, batch_log2: int = 0) -> Network:
-    o = tz_network_opts(batch_log2)
+def tz_network_from_circuit(circ: Circuit, batch_log2: int = 0, open_qubits=()) -> Network:
+    """open_qubits: output qubits left open; each bitstring then yields the
+    2^len(open_qubits) amplitudes of every assignment of their bits (bit j of
+    the open value is the j-th smallest open qubit)."""
+    arr = np.ascontiguousarray(np.asarray(list(open_qubits), dtype=np.int32))
+    ptr = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if len(arr) else None
+    o = tz_network_opts(batch_log2, len(arr), ptr)
     h = ctypes.c_void_p()
     check(lib().tz_network_from_circuit(circ.handle, ctypes.byref(o), ctypes.byref(h)))
-    return Network(h, circ.n_qubits, batch_log2)
+    return Network(h, circ.n_qubits, batch_log2, arr.tolist())
 
 
 class Tree(_Handle):
@@ -188,6 +194,7 @@ class Plan(_Handle):
         super().__init__(h)
         self.n_qubits = n_qubits
         self.device = device
+        self.n_open = 0
         self._ws = None
 
     def stats(self) -> dict:
@@ -259,21 +266,27 @@ def tz_plan_create(net: Network, tree: Tree, sliced=(), precision="c64", device=
     h = ctypes.c_void_p()
     ptr = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if len(arr) else None
     check(lib().tz_plan_create(net.handle, tree.handle, ptr, len(arr), ctypes.byref(o), ctypes.byref(h)))
-    return Plan(h, net.n_qubits, device)
+    plan = Plan(h, net.n_qubits, device)
+    plan.n_open = plan.stats()["n_open"]
+    return plan
 
 
 def tz_contract_amplitudes(plan: Plan, bitstrings) -> np.ndarray:
-    """Amplitudes of host bitstrings (n x n_qubits of 0/1) as complex128."""
+    """Amplitudes of host bitstrings (n x n_qubits of 0/1) as complex128:
+    shape (n,), or (n, 2^n_open) for a plan with open output qubits."""
     b = np.ascontiguousarray(np.asarray(bitstrings, dtype=np.uint8).reshape(-1, plan.n_qubits))
-    out = np.zeros(2 * len(b), dtype=np.float64)
+    m = plan.n_open
+    out = np.zeros(2 * (len(b) << m), dtype=np.float64)
     check(lib().tz_contract_amplitudes(plan.handle, b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), len(b),
                                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
-    return out.view(np.complex128)
+    amps = out.view(np.complex128)
+    return amps.reshape(len(b), 1 << m) if m else amps
 
 
 def tz_contract_amplitudes_device(plan: Plan, d_bitstrings, d_out):
     """Device form: d_bitstrings (uint8, n x n_qubits) and d_out (float64,
-    2n) are torch CUDA tensors; asynchronous on the plan's stream."""
+    2n, or 2n * 2^n_open with open output qubits) are torch CUDA tensors;
+    asynchronous on the plan's stream."""
     n = d_bitstrings.shape[0]
     check(lib().tz_contract_amplitudes_device(plan.handle, _ptr(d_bitstrings), n, _ptr(d_out)))
 
@@ -361,19 +374,21 @@ class Server(_Handle):
         check(lib().tz_server_submit(self._h, plan.handle, b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), len(b),
                                      ctypes.byref(t)))
         self._rows = getattr(self, "_rows", {})
-        self._rows[t.value] = len(b)
+        self._rows[t.value] = (len(b), plan.n_open)
         return t.value
 
     def poll(self, ticket: int):
-        """complex128 amplitudes once the query is done, else None."""
-        n = self._rows[ticket]
-        out = np.zeros(2 * n, dtype=np.float64)
+        """complex128 amplitudes once the query is done, else None (shape
+        (n,), or (n, 2^n_open) for a plan with open output qubits)."""
+        n, m = self._rows[ticket]
+        out = np.zeros(2 * (n << m), dtype=np.float64)
         done = ctypes.c_int()
         check(lib().tz_server_poll(self._h, ticket, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                    ctypes.byref(done)))
         if done.value:
             del self._rows[ticket]
-            return out.view(np.complex128)
+            amps = out.view(np.complex128)
+            return amps.reshape(n, 1 << m) if m else amps
         return None
 
     def latency(self):

@@ -30,7 +30,7 @@ class tz_lattice(ctypes.Structure):
 
 
 class tz_network_opts(ctypes.Structure):
-    _fields_ = [("batch_log2", ctypes.c_int)]
+    _fields_ = [("batch_log2", ctypes.c_int), ("n_open", ctypes.c_int), ("open_qubits", ctypes.POINTER(ctypes.c_int32))]
 
 
 class tz_path_opts(ctypes.Structure):
@@ -51,7 +51,7 @@ class tz_plan_stats(ctypes.Structure):
                 ("gemm_flops_per_group", ctypes.c_double), ("bytes_per_group", ctypes.c_double),
                 ("permute_bytes_per_group", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t),
                 ("const_bytes", ctypes.c_size_t), ("scratch_bytes", ctypes.c_size_t), ("const_flops", ctypes.c_double),
-                ("bind_ms", ctypes.c_double), ("n_tuned_steps", ctypes.c_int), ("pad0", ctypes.c_int)]
+                ("bind_ms", ctypes.c_double), ("n_tuned_steps", ctypes.c_int), ("n_open", ctypes.c_int)]
 
 
 PROFILE_KINDS = ("leaves", "direct", "permute", "gemm_simt", "gemm_tc", "accumulate", "gemm_skinny", "gemm_dot")

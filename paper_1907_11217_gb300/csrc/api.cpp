@@ -100,7 +100,12 @@ int tz_network_from_circuit(const tz_circuit *c, const tz_network_opts *opts, tz
   REQUIRE(c && out, "NULL argument");
   *out = nullptr;
   auto n = std::make_unique<tz_network>();
-  n->n = tz::build_network(c->c, opts ? opts->batch_log2 : 0);
+  std::vector<int> open_q;
+  if (opts && opts->n_open) {
+    REQUIRE(opts->n_open > 0 && opts->open_qubits, "n_open > 0 needs open_qubits");
+    open_q.assign(opts->open_qubits, opts->open_qubits + opts->n_open);
+  }
+  n->n = tz::build_network(c->c, opts ? opts->batch_log2 : 0, open_q);
   *out = n.release();
   TZ_CATCH
 }
@@ -408,7 +413,8 @@ int tz_contract_amplitudes(tz_plan *plan, const uint8_t *bitstrings, int64_t n, 
   tz::cuda_check(cudaMemcpyAsync(ctx.scratch + plan->s_bits, bitstrings, (size_t)(n * nq), cudaMemcpyHostToDevice, s),
                  "copy bitstrings in");
   tz::plan_run(plan, ctx, n, plan->lo, plan->hi);
-  tz::cuda_check(cudaMemcpyAsync(out, ctx.scratch + plan->s_acc, (size_t)n * 16, cudaMemcpyDeviceToHost, s),
+  tz::cuda_check(cudaMemcpyAsync(out, ctx.scratch + plan->s_acc, (size_t)n * 16 << plan->net.n_open,
+                                 cudaMemcpyDeviceToHost, s),
                  "copy amplitudes out");
   tz::cuda_check(cudaStreamSynchronize(s), "contract");
   if (is_tc_precision(plan->opts.precision) && tz::read_tc_error(plan, ctx))
@@ -442,7 +448,8 @@ int tz_contract_amplitudes_device(tz_plan *plan, const uint8_t *d_bitstrings, in
                                  cudaMemcpyDeviceToDevice, s),
                  "copy bitstrings in");
   tz::plan_run(plan, ctx, n, plan->lo, plan->hi);
-  tz::cuda_check(cudaMemcpyAsync(d_out, ctx.scratch + plan->s_acc, (size_t)n * 16, cudaMemcpyDeviceToDevice, s),
+  tz::cuda_check(cudaMemcpyAsync(d_out, ctx.scratch + plan->s_acc, (size_t)n * 16 << plan->net.n_open,
+                                 cudaMemcpyDeviceToDevice, s),
                  "copy amplitudes out");
   TZ_CATCH
 }

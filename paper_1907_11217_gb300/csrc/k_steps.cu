@@ -176,31 +176,36 @@ cudaError_t launch_direct(const DStep *steps, int n_steps, int64_t total_blocks,
   return cudaGetLastError();
 }
 
-// acc[row] += scale * root[beta] in FP64 for the current chunk; then advance
-// the group state (next slice, wrapping to the next chunk).
+// acc[row][o] += scale * root[beta, o] in FP64 for the current chunk (o the
+// value of the open output qubits; m = 0 without them); then advance the
+// group state (next slice, wrapping to the next chunk).
 template <typename T>
 __global__ void accum_kernel(AccumArgs a) {
   const T *root = static_cast<const T *>(a.root);
   GroupState *gs = a.gs;
   const int64_t chunk = gs->chunk, n_rows = gs->n_rows;
-  const int nb = 1 << a.g;
-  for (int beta = threadIdx.x; beta < nb; beta += blockDim.x) {
+  const int total = 1 << (a.g + a.m);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int beta = e >> a.m, o = e & ((1 << a.m) - 1);
     int64_t off = 0;
     for (int j = 0; j < a.g; j++) off |= int64_t((beta >> j) & 1) << a.beta_pos[j];
+    for (int j = 0; j < a.m; j++) off |= int64_t((o >> j) & 1) << a.open_pos[j];
     const int64_t row = (chunk << a.g) | beta;
     if (row < n_rows) {
       const T v = root[off];
       const double vr = v.x, vi = v.y;
-      double2 r = a.acc[row];
+      const int64_t at = (row << a.m) | o;
+      double2 r = a.acc[at];
       r.x += a.scale_re * vr - a.scale_im * vi;
       r.y += a.scale_re * vi + a.scale_im * vr;
       // a product of this call timed out: its rows are poisoned, so a
       // caller that only reads the amplitudes still sees the failure
       if (gs->tc_error) r = make_double2(__longlong_as_double(0x7ff8000000000000ll),
                                          __longlong_as_double(0x7ff8000000000000ll));
-      a.acc[row] = r;
+      a.acc[at] = r;
     }
   }
+  if (gridDim.x > 1) return;  // the state advances in a launch of its own
   __syncthreads();
   if (threadIdx.x == 0 && a.advance) {
     int64_t sl = gs->slice + 1;
@@ -213,11 +218,31 @@ __global__ void accum_kernel(AccumArgs a) {
   }
 }
 
+__global__ void advance_kernel(GroupState *gs) {
+  int64_t sl = gs->slice + 1;
+  if (sl >= gs->hi) {
+    sl = gs->lo;
+    gs->chunk = gs->chunk + 1;
+  }
+  gs->slice = sl;
+  gs->groups_done++;
+}
+
+// one block up to 4096 root values; beyond, one value per thread over
+// several blocks, and a separate launch advances the state once they are done
+constexpr int kAccumOneBlock = 12;
+
+int accumulate_launches(int g, int m) { return g + m <= kAccumOneBlock ? 1 : 2; }
+
 cudaError_t launch_accumulate(const AccumArgs &a, cudaStream_t s) {
+  if (a.g < 0 || a.m < 0 || a.g > kMaxBatch || a.m > kMaxOpen) return cudaErrorInvalidValue;
+  const int bits = a.g + a.m;
+  const unsigned blocks = bits <= kAccumOneBlock ? 1u : (unsigned)(((1 << bits) + 255) / 256);
   if (a.dbl)
-    accum_kernel<double2><<<1, 256, 0, s>>>(a);
+    accum_kernel<double2><<<blocks, 256, 0, s>>>(a);
   else
-    accum_kernel<float2><<<1, 256, 0, s>>>(a);
+    accum_kernel<float2><<<blocks, 256, 0, s>>>(a);
+  if (blocks > 1 && a.advance) advance_kernel<<<1, 1, 0, s>>>(a.gs);
   return cudaGetLastError();
 }
 

@@ -11,6 +11,7 @@ namespace dev {
 constexpr int kMaxBits = 40;    // largest tensor rank handled (2^40 elements)
 constexpr int kMaxDirect = 32;  // bits of C or K in a direct (SIMT) step
 constexpr int kMaxBatch = 8;    // bitstring batch bits
+constexpr int kMaxOpen = 12;    // open output qubits
 
 // Which group (slice, bitstring chunk) the launches of one group work on.
 // Read by the leaf builder and the accumulator; the accumulator advances it
@@ -91,10 +92,12 @@ struct PermuteArgs {
 
 struct AccumArgs {
   const void *root;           // complex64, or complex128 when dbl
-  double2 *acc;
+  double2 *acc;               // [row][2^m open values]
   GroupState *gs;
   int g;                      // batch bits
+  int m;                      // open output qubits
   int8_t beta_pos[kMaxBatch]; // root bit of batch bit j
+  int8_t open_pos[kMaxOpen];  // root bit of open bit j
   double scale_re, scale_im;
   int advance;                // 1: advance gs to the next group
   int dbl;                    // root is complex128
@@ -158,6 +161,9 @@ size_t cgemm_tc_scratch_bytes(int precision, int64_t batch, int64_t M, int64_t N
 // split; scatter outputs never split).
 int cgemm_tc_launches(int precision, int64_t batch, int64_t M, int64_t N, int64_t K, bool scatter, int ksplit = 0);
 cudaError_t launch_accumulate(const AccumArgs &a, cudaStream_t s);
+// kernel launches of one launch_accumulate (2 when the root is too large for
+// one block: the group state then advances in a launch of its own)
+int accumulate_launches(int g, int m);
 cudaError_t launch_accumulate_plain(const float2 *part, double2 *acc, int64_t n, double sre, double sim,
                                     cudaStream_t s);
 

@@ -85,12 +85,23 @@ struct Builder {
 
 }  // namespace
 
-Network build_network(const Circuit &c, int batch_log2) {
+Network build_network(const Circuit &c, int batch_log2, const std::vector<int> &open_qubits) {
   if (batch_log2 < 0 || batch_log2 > 8) fail(TZ_EINVAL, "batch_log2 must be in 0..8");
   Builder b;
   b.net.n_qubits = c.n;
   b.net.batch_log2 = batch_log2;
   const int n = c.n;
+  std::vector<int> opened(open_qubits);
+  std::sort(opened.begin(), opened.end());
+  if ((int)opened.size() > kMaxOpenQubits)
+    fail(TZ_EINVAL, "at most " + std::to_string(kMaxOpenQubits) + " open output qubits");
+  for (size_t j = 0; j < opened.size(); j++) {
+    if (opened[j] < 0 || opened[j] >= n) fail(TZ_EINVAL, "open qubit out of range");
+    if (j && opened[j] == opened[j - 1]) fail(TZ_EINVAL, "open qubit listed twice");
+  }
+  if (n > 0 && (int)opened.size() >= n) fail(TZ_EINVAL, "at least one output qubit must stay closed");
+  std::vector<char> is_opened(n, 0);
+  for (int q : opened) is_opened[q] = 1;
   std::vector<int> cur(n), seg(n, 0);
   for (int q = 0; q < n; q++) {
     cur[q] = b.add_index(q, 0);
@@ -125,9 +136,13 @@ Network build_network(const Circuit &c, int batch_log2) {
       cur[q] = nw;
     }
   }
+  // An open output qubit has no output tensor: its last wire index stays
+  // open to the end, and its value is the qubit's output bit.
+  for (size_t j = 0; j < opened.size(); j++) b.net.indices[cur[opened[j]]] = Index{-2, (int)j};
   std::vector<int> beta;
   for (int k = 0; k < batch_log2; k++) beta.push_back(b.add_index(-1, k));
   for (int q = 0; q < n; q++) {
+    if (is_opened[q]) continue;
     Leaf L;
     L.kind = LEAF_OUTPUT;
     L.qubit = q;
@@ -167,6 +182,7 @@ Network build_network(const Circuit &c, int batch_log2) {
         if (best < 0 || key(p) < key(best)) best = p;
       }
       if (best < 0) {  // index held by nobody else: sum it out
+        if (b.net.is_open(i)) continue;  // unless it is open: the factor stays
         b.net.scalar *= L.data[0] + L.data[1];
         b.kill(id);
         changed = true;
@@ -225,6 +241,8 @@ Network build_network(const Circuit &c, int batch_log2) {
   Network out;
   out.n_qubits = n;
   out.batch_log2 = batch_log2;
+  out.n_open = (int)opened.size();
+  out.open_qubits = opened;
   out.scalar = b.net.scalar;
   std::vector<int> remap(b.net.indices.size(), -1);
   auto map_index = [&](int i) {

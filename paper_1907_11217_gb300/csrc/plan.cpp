@@ -579,7 +579,7 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
           j.e_dst_pos = pos_of(dst.lay, e);
       }
       for (int i : lf.idx) {
-        if (!net.is_open(i)) continue;
+        if (!net.is_batch(i)) continue;
         j.beta_dst_pos[net.indices[i].segment] = (int8_t)pos_of(dst.lay, i);
       }
       for (int x = 0; x < 2 * (1 << lf.rc) && x < 4; x++) {
@@ -621,7 +621,7 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
   p->s_bits = so;
   so = align256(so + (size_t)p->max_rows * net.n_qubits);
   p->s_acc = so;
-  so = align256(so + (size_t)p->max_rows * 16);
+  so = align256(so + ((size_t)p->max_rows * 16 << net.n_open));
   p->s_arena = so;
   p->arena_bytes = (size_t)std::max(arena_peak, arena_const_peak);
   so = align256(so + p->arena_bytes);
@@ -633,6 +633,7 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
   stt.n_steps = NS;
   stt.k = (int)sliced.size();
   stt.batch_log2 = g;
+  stt.n_open = net.n_open;
   stt.max_log2 = ti.max_bits;
   for (int s = 0; s < NS; s++) {
     const StepInfo &st = ti.steps[s];
@@ -664,6 +665,8 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
       const PStep &ps = p->S[it.a];
       if (ps.tc)
         n = dev::cgemm_tc_launches(p->opts.precision, ps.batch, ps.M, ps.N, ps.K, !ps.row_major);
+    } else if (it.kind == IT_ACCUM) {
+      n = dev::accumulate_launches(net.batch_log2, net.n_open);
     }
     stt.n_launches_per_group += n;
   }
@@ -742,7 +745,8 @@ std::string plan_describe(const tz_plan *p) {
   bool first = true;
   for (size_t i = 0; i < p->net.indices.size(); i++)
     if (p->net.is_open((int)i)) {
-      o << (first ? "" : ",") << "[" << i << "," << p->net.indices[i].segment << "]";
+      o << (first ? "" : ",") << "[" << i << "," << p->net.indices[i].qubit << "," << p->net.indices[i].segment
+        << "]";
       first = false;
     }
   o << "]}";
@@ -924,10 +928,15 @@ static void run_items(tz_plan *p, const std::vector<Item> &items, const RunCtx &
         a.acc = reinterpret_cast<double2 *>(ctx.scratch + p->s_acc);
         a.gs = gs;
         a.g = p->net.batch_log2;
+        a.m = p->net.n_open;
         for (int j = 0; j < dev::kMaxBatch; j++) a.beta_pos[j] = -1;
+        for (int j = 0; j < dev::kMaxOpen; j++) a.open_pos[j] = -1;
         for (size_t q = 0; q < p->T[p->root].lay.size(); q++) {
           int i = p->T[p->root].lay[q];
-          a.beta_pos[p->net.indices[i].segment] = (int8_t)q;
+          if (p->net.is_batch(i))
+            a.beta_pos[p->net.indices[i].segment] = (int8_t)q;
+          else
+            a.open_pos[p->net.indices[i].segment] = (int8_t)q;
         }
         a.scale_re = p->net.scalar.real();
         a.scale_im = p->net.scalar.imag();
@@ -1044,6 +1053,8 @@ static void autotune_tc_steps(tz_plan *p) {
     if (it.kind == IT_GEMM && p->S[it.a].tc) {
       const PStep &ps = p->S[it.a];
       c = dev::cgemm_tc_launches(p->opts.precision, ps.batch, ps.M, ps.N, ps.K, !ps.row_major, ps.tc_ksplit);
+    } else if (it.kind == IT_ACCUM) {
+      c = dev::accumulate_launches(p->net.batch_log2, p->net.n_open);
     }
     n += c;
   }
@@ -1142,7 +1153,9 @@ void plan_run(tz_plan *p, const RunCtx &ctx, int64_t n_rows, int64_t lo, int64_t
   cuda_check(cudaSetDevice(p->opts.device), "cudaSetDevice");
   cudaStream_t s = ctx.stream;
   auto *gs = reinterpret_cast<dev::GroupState *>(ctx.scratch + p->s_gs);
-  if (fresh) cuda_check(cudaMemsetAsync(ctx.scratch + p->s_acc, 0, (size_t)n_rows * 16, s), "clear accumulator");
+  if (fresh)
+    cuda_check(cudaMemsetAsync(ctx.scratch + p->s_acc, 0, (size_t)n_rows * 16 << p->net.n_open, s),
+               "clear accumulator");
   cuda_check(dev::launch_init_state(gs, lo, hi, n_rows, s, fresh ? 0 : 1), "init group state");
   const int64_t chunk = int64_t(1) << p->net.batch_log2;
   const int64_t n_chunks = (n_rows + chunk - 1) / chunk;

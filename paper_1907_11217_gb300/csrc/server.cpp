@@ -127,8 +127,9 @@ struct tz_server {
     char *scratch = static_cast<char *>(opts.arena) + q.arena_off;
     tz::RunCtx ctx{scratch, sl.stream};
     const bool first = q.next == q.lo;
+    const size_t n_out = (size_t)q.n << p->net.n_open;  // amplitudes of the query
     if (first) {
-      ensure_pinned(sl, (size_t)q.n * nq, (size_t)q.n * 16 + 16);
+      ensure_pinned(sl, (size_t)q.n * nq, n_out * 16 + 16);
       std::memcpy(sl.pin_in, q.bits.data(), (size_t)q.n * nq);
       tz::cuda_check(cudaMemcpyAsync(scratch + p->s_bits, sl.pin_in, (size_t)q.n * nq, cudaMemcpyHostToDevice,
                                      sl.stream),
@@ -140,12 +141,12 @@ struct tz_server {
     sl.last = hi == q.hi;
     if (sl.last) {
       // pinned out: the amplitudes, then the scratch part's error word
-      ensure_pinned(sl, (size_t)q.n * nq, (size_t)q.n * 16 + 16);
-      tz::cuda_check(cudaMemcpyAsync(sl.pin_out, scratch + p->s_acc, (size_t)q.n * 16, cudaMemcpyDeviceToHost,
+      ensure_pinned(sl, (size_t)q.n * nq, n_out * 16 + 16);
+      tz::cuda_check(cudaMemcpyAsync(sl.pin_out, scratch + p->s_acc, n_out * 16, cudaMemcpyDeviceToHost,
                                      sl.stream),
                      "query amplitudes out");
       const auto *gs = reinterpret_cast<const tz::dev::GroupState *>(scratch + p->s_gs);
-      tz::cuda_check(cudaMemcpyAsync(sl.pin_out + 2 * q.n, &gs->tc_error, sizeof(int), cudaMemcpyDeviceToHost,
+      tz::cuda_check(cudaMemcpyAsync(sl.pin_out + 2 * n_out, &gs->tc_error, sizeof(int), cudaMemcpyDeviceToHost,
                                      sl.stream),
                      "query error word out");
     }
@@ -199,12 +200,13 @@ struct tz_server {
         continue;
       }
       int tc_error = 0;
-      std::memcpy(&tc_error, sl.pin_out + 2 * q.n, sizeof(int));
+      const size_t n_out = (size_t)q.n << q.plan->net.n_open;
+      std::memcpy(&tc_error, sl.pin_out + 2 * n_out, sizeof(int));
       if (tc_error) {
         fail_query(q, TZ_ETIMEOUT, "a tensor-core product of this query timed out in a bounded wait");
         continue;
       }
-      q.out.assign(sl.pin_out, sl.pin_out + 2 * q.n);
+      q.out.assign(sl.pin_out, sl.pin_out + 2 * n_out);
       q.state = Q_DONE;
       q.t_done = Clock::now();
       latencies.push_back(std::chrono::duration<double>(q.t_done - q.t_submit).count());

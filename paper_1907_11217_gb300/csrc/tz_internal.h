@@ -34,8 +34,8 @@ std::string circuit_spec(const Circuit &c);
 
 // ------------------------------------------------------------------ networks
 struct Index {
-  int qubit;    // -1 for a batch (bitstring) index
-  int segment;  // wire segment, or batch bit number
+  int qubit;    // -1 for a batch (bitstring) index, -2 for an open output qubit
+  int segment;  // wire segment, batch bit number, or open bit number
 };
 enum LeafKind { LEAF_CONST = 0, LEAF_OUTPUT = 1 };
 struct Leaf {
@@ -52,12 +52,20 @@ struct Leaf {
 };
 struct Network {
   int n_qubits = 0, batch_log2 = 0;
+  // Open output qubits: bit j of an amplitude's open value is the output bit
+  // of qubit open_qubits[j] (ascending); every bitstring yields 2^n_open
+  // amplitudes, its own bits on those qubits ignored.
+  int n_open = 0;
+  std::vector<int> open_qubits;
   std::vector<Index> indices;
   std::vector<Leaf> leaves;
   cd scalar{1.0, 0.0};  // global factor of the amplitude
+  // kept to the end of the contraction: batch indices and open output qubits
   bool is_open(int i) const { return indices[i].qubit < 0; }
+  bool is_batch(int i) const { return indices[i].qubit == -1; }
 };
-Network build_network(const Circuit &c, int batch_log2);
+constexpr int kMaxOpenQubits = 12;
+Network build_network(const Circuit &c, int batch_log2, const std::vector<int> &open_qubits = {});
 
 // ------------------------------------------------------- trees and analysis
 using Pairs = std::vector<std::pair<int, int>>;

@@ -19,11 +19,11 @@ def rel_err(got, ref, n_qubits):
 
 
 def make_plan(tz, spec, batch_log2=0, log2_max=0, precision="c64", small_log2=0, restarts=4, seed=1,
-              use_graph=False, stream=None, k_max=8, max_bitstrings=0, slice_bits=0):
+              use_graph=False, stream=None, k_max=8, max_bitstrings=0, slice_bits=0, open_qubits=()):
     """log2_max > 0: slice down to that size; slice_bits > 0: slice until the
     largest intermediate is slice_bits below the unsliced one."""
     c = tz.tz_circuit_from_spec(spec)
-    net = tz.tz_network_from_circuit(c, batch_log2)
+    net = tz.tz_network_from_circuit(c, batch_log2, open_qubits)
     tree = tz.tz_path_greedy(net, restarts=restarts, seed=seed, log2_max_intermediate=log2_max, precision=precision)
     if slice_bits > 0:
         full = tz.tz_plan_create(net, tree, []).stats()["max_log2"]
@@ -44,3 +44,16 @@ def rel_err_partial(got, ref, n_qubits, k):
     of random circuits sit near 2^(-(n+k)/2) (2^k terms of random phase add
     up to an amplitude of 2^(-n/2)), which is the floor here."""
     return rel_err(got, ref, n_qubits + k)
+
+
+def expand_open(bits, open_qubits):
+    """Every bitstring with each assignment of the open qubits: row
+    r * 2^m + o has bit j of o on the j-th smallest open qubit (the order of
+    the amplitudes a plan with open output qubits returns)."""
+    oq = sorted(open_qubits)
+    m = len(oq)
+    out = np.repeat(np.asarray(bits, dtype=np.uint8), 1 << m, axis=0)
+    o = np.tile(np.arange(1 << m), len(bits))
+    for j, q in enumerate(oq):
+        out[:, q] = (o >> j) & 1
+    return out

@@ -236,3 +236,91 @@ def test_contract_empty_and_oversized_batches(tz):
     with pytest.raises(tz.TzError) as e:
         tz.tz_contract_amplitudes(plan, np.zeros((5, 16), dtype=np.uint8))
     assert e.value.code == -1
+
+
+def _contract_described(desc, bits, open_order):
+    """Contract the network a plan describes, for one bitstring (batch of 1),
+    by pairwise einsum in numpy, keeping the open indices; returns the
+    tensor over the open indices in `open_order` (a test helper, no oracle)."""
+    items = []
+    for lf in desc["leaves"]:
+        data = np.array([complex(re_, im_) for re_, im_ in lf["data"]])
+        if lf["kind"] == 1:  # output tensor: row x of M[x * 2^rc + e]
+            rc = lf["rc"]
+            x = int(bits[lf["qubit"]])
+            arr = data[x << rc:(x + 1) << rc]
+            labels = lf["idx"][:rc]
+        else:
+            arr = data
+            labels = lf["idx"]
+        r = len(labels)
+        items.append((arr.reshape((2,) * r) if r else arr.reshape(()), list(reversed(labels))))
+    keep = set(open_order)
+    while len(items) > 1:
+        best = None
+        for a in range(len(items)):
+            for b in range(a + 1, len(items)):
+                la, lb = items[a][1], items[b][1]
+                if not set(la) & set(lb) and best is not None:
+                    continue
+                others = set()
+                for c, (_, lc) in enumerate(items):
+                    if c != a and c != b:
+                        others |= set(lc)
+                out = [e for e in dict.fromkeys(la + lb) if e in others or e in keep]
+                if best is None or len(out) < best[0]:
+                    best = (len(out), a, b, out)
+        _, a, b, out = best
+        (xa, la), (xb, lb) = items[a], items[b]
+        names = {e: chr(97 + k) for k, e in enumerate(dict.fromkeys(la + lb))}
+        sub = "".join(names[e] for e in la) + "," + "".join(names[e] for e in lb) + "->" + \
+            "".join(names[e] for e in out)
+        xc = np.einsum(sub, xa, xb)
+        items = [it for c, it in enumerate(items) if c not in (a, b)] + [(xc, out)]
+    x, labels = items[0]
+    return np.transpose(x, [labels.index(e) for e in open_order]) * complex(*desc["scalar"])
+
+
+@pytest.mark.parametrize("spec_kind, open_q", [("grid3x3", (0, 4, 8)), ("grid3x3", (2,)),
+                                               ("idle", (1, 2)), ("idle", (0,))])
+def test_open_output_qubits_network_matches_statevector(tz, spec_kind, open_q):
+    """A network with open output qubits, contracted on the host from the
+    plan's own description, gives the state-vector amplitudes of every
+    assignment of the open qubits (Sec. 2: several amplitudes from one
+    contraction). "idle": qubit 1 has only diagonal gates after |0>, qubit 2
+    none at all, so their open index sits on the input tensor."""
+    import json
+    from oracle import statevector
+    if spec_kind == "grid3x3":
+        spec = ti.circuit_to_spec(9, ti.generate_circuit(ti.grid(3, 3), 8, 5))
+        n = 9
+    else:
+        spec = "3\n0 h 0\n1 cz 0 1\n2 t 1\n3 x_1_2 0\n"
+        n = 3
+    net = tz.tz_network_from_circuit(tz.tz_circuit_from_spec(spec), 0, open_q)
+    infos = [net.index_info(i) for i in range(net.n_indices)]
+    open_idx = sorted((s, i) for i, (q, s) in enumerate(infos) if q == -2)
+    assert [s for s, _ in open_idx] == list(range(len(open_q)))
+    tree = tz.tz_path_greedy(net, restarts=4, seed=1, log2_max_intermediate=20, precision="c64")
+    plan = tz.tz_plan_create(net, tree, [], precision="c64")
+    assert plan.n_open == len(open_q)
+    desc = json.loads(plan.describe())
+    assert sorted(i for i, q, s in desc["open"] if q == -2) == sorted(i for _, i in open_idx)
+    rng = np.random.default_rng(3)
+    oq = sorted(open_q)
+    for _ in range(3):
+        bits = rng.integers(0, 2, n).astype(np.uint8)
+        got = _contract_described(desc, bits, [i for _, i in open_idx]).reshape(-1, order="F")
+        expanded = np.repeat(bits[None, :], 1 << len(oq), axis=0)
+        for o in range(1 << len(oq)):
+            for j, q in enumerate(oq):
+                expanded[o, q] = (o >> j) & 1
+        want = statevector.amplitudes(spec, expanded)
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * max(1.0, np.abs(want).max()))
+
+
+def test_open_output_qubits_rejected(tz):
+    c = tz.tz_circuit_generate_grid(3, 3, 8, 1)
+    for bad in [(9,), (-1,), (2, 2), tuple(range(9)), tuple(range(13))]:
+        with pytest.raises(tz.TzError):
+            tz.tz_network_from_circuit(c, 0, bad)
