@@ -422,7 +422,12 @@ struct TcSmem {
   static constexpr uint32_t TOTAL = STAGES * STAGE + STAGING + BARS + COLOFF + XEXP + 1024;  // + alignment
   static constexpr uint32_t ACC_COLS = BNP < 32 ? 32 : BNP;
   static constexpr uint32_t TMEM_COLS = 512;
-  static constexpr int ASLOTS = 4;
+  // the split warps cannot run more than STAGES k-blocks ahead (they read A
+  // from a stage), so more slots than stages would stay unused
+  static constexpr int ASLOTS = STAGES < 4 ? STAGES : 4;
+  // one slot per stage: the products of a k-block release its stage and its
+  // A slot together, on the stage's barrier (one commit instead of two)
+  static constexpr bool SLOT_IS_STAGE = ASLOTS == STAGES;
   static constexpr uint32_t A_COL0 = TMEM_COLS - ASLOTS * SLOT_COLS;
   static constexpr int NBUF = A_COL0 / ACC_COLS;
   static_assert(BNP <= 128, "an epilogue thread holds half a row of the tile in registers");
@@ -462,8 +467,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t *tfull = empty + STAGES;     // [NBUF] accumulator ready for the epilogue
   uint64_t *tempty = tfull + L::NBUF;   // [NBUF] accumulator drained by the epilogue
   uint64_t *drain = tempty + L::NBUF;   // all products retired
-  uint64_t *aempty = drain + 1;         // [ASLOTS] TMEM A slot read by its products
-  uint64_t *xfull = aempty + L::ASLOTS;  // [XR] FP16: exponent ring entry written
+  uint64_t *aempty_own = drain + 1;     // [ASLOTS] TMEM A slot read by its products
+  uint64_t *aempty = L::SLOT_IS_STAGE ? empty : aempty_own;
+  uint64_t *xfull = aempty_own + L::ASLOTS;  // [XR] FP16: exponent ring entry written
   uint64_t *stall = xfull + L::XR;       // test stall: nothing ever arrives here
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(stall + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -516,7 +522,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&tempty[b], CG == 2 ? 16 : 256);
     }
     mbar_init(drain, 1);
-    for (int b = 0; b < L::ASLOTS; b++) mbar_init(&aempty[b], 1);
+    if (!L::SLOT_IS_STAGE)
+      for (int b = 0; b < L::ASLOTS; b++) mbar_init(&aempty_own[b], 1);
     for (int b = 0; b < L::XR; b++) mbar_init(&xfull[b], 128);
     mbar_init(stall, 1);
     *abort_flag = 0;
@@ -683,7 +690,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
             }
             commit(&empty[s]);
-            commit(&aempty[slot]);
+            if (!L::SLOT_IS_STAGE) commit(&aempty[slot]);
           }
           if (!ok) break;
           commit(&tfull[buf]);
