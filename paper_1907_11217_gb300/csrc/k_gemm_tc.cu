@@ -63,7 +63,15 @@ template <int MODE>
 __host__ __device__ constexpr int stage_k() { return MODE == 0 ? 32 : 64; }
 // TMA, MMA, 4 split warps, 8 epilogue warps; registers are granted to warps
 // in groups of four, so 14 warps leave 128 registers a thread
-constexpr int kThreads = 448;
+// warps: 0 TMA, 1 MMA issuer, 2..5 A split, 6..13 epilogue, 14 readiness
+// waiter (hands the k-blocks over to the MMA warp through named barriers)
+constexpr int kThreads = 480;
+constexpr int kWaiterWarp = 14;
+// named barriers of the MMA and waiter warps (64 threads): k-block g ready
+// (kBarReady + g % kAhead), k-block g issued (kBarIssued + g % kAhead), and
+// the status reduction at the end of each tile (kBarTile)
+constexpr int kAhead = 2;
+constexpr int kBarReady = 1, kBarIssued = kBarReady + kAhead, kBarTile = kBarIssued + kAhead;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait (default)
 // Waits that let copies and products in flight finish before the CTA exits
 // (after an abort) always use this limit, never the adjustable one.
@@ -459,6 +467,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   // who waits for a drained accumulator before a range's products: the split
   // warps when a range spans several k-blocks, else the MMA issuer
   constexpr bool kSplitWaitsDrain = fold_k<MODE>() / stage_k<MODE>() > 1;
+  // who waits for each k-block's split A before its products: a waiter warp
+  // that hands the k-blocks over (pairs and TF32: their products are bound
+  // by the issuing thread, and a wait on it stalls the tensor pipe), or the
+  // issuing thread itself (single-CTA BF16 / FP16: bound by the split warps,
+  // where the extra hand-over only adds latency; measured 3-12 % slower with
+  // the waiter, against 2-6 % faster for the others)
+  constexpr bool kWaiter = CG == 2 || MODE == MODE_TF32;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * L::STAGE + L::STAGING);
@@ -556,6 +571,19 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const unsigned long long wait_ns = g_wait_ns;
+  // named barriers of the MMA and waiter warps (64 threads, both whole warps)
+  auto named_sync = [](int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); };
+  auto named_arrive = [](int id) { asm volatile("bar.arrive %0, 64;" ::"r"(id) : "memory"); };
+  // both warps meet; true when both pass ok_in true
+  auto named_all = [](int id, bool ok_in) {
+    uint32_t all;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.b32 q, %1, 0;\n bar.red.and.pred p, %2, 64, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(all)
+        : "r"((uint32_t)ok_in), "r"(id)
+        : "memory");
+    return all != 0;
+  };
   // a wait that gives up (timeout, or an abort) also stops the peer CTA
   auto wait = [&](uint64_t *bar, uint32_t parity) {
     const bool ok = mbar_wait_t<CG == 2>(bar, parity, abort_flag, wait_ns);
@@ -615,11 +643,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (warp == 1) {
-    if (lane == 0 && CG == 2 && rank != 0) {
+    if (CG == 2 && rank != 0) {
       // the pair's second CTA issues no products: it waits until the first
       // CTA's products (which use its tensor and shared memory) have retired
-      mbar_wait_t<true>(drain, 0, abort_flag, kDrainNs, false);
-    } else if (lane == 0) {
+      if (lane == 0) mbar_wait_t<true>(drain, 0, abort_flag, kDrainNs, false);
+    } else {
       constexpr uint32_t idesc = MODE == MODE_TF32   ? idesc_tf32(BNP)
                                  : MODE == MODE_BF16 ? idesc_bf16(BNP, BM * CG)
                                                      : idesc_f16(BNP, BM * CG);
@@ -637,69 +665,139 @@ __global__ void __launch_bounds__(kThreads, 1)
       // 8 TMEM columns of A)
       constexpr int kSteps = stage_k<MODE>() / (MODE == MODE_TF32 ? 8 : 16);
       constexpr int kFoldKb = fold_k<MODE>() / stage_k<MODE>();  // k-blocks per accumulation range
-      int64_t g = 0, rg = 0;  // k-blocks and accumulation ranges issued
-      // test stall: a bounded wait on a barrier nothing arrives at
-      bool ok = !g_stall || wait(stall, 0);
-      for (int64_t t = walker; t < n_tiles && ok; t += n_walkers) {
-        const Tile d = decode(t);
-        const int nkb = d.kb1 - d.kb0;
-        for (int r0 = 0; r0 < nkb; r0 += kFoldKb, rg++) {
-          // ranges of several k-blocks: the split warps waited for this
-          // range's accumulator to be drained before releasing its first
-          // k-block (a wait on this thread stalls the tensor pipe until the
-          // products in flight finish; measured 3-13 % faster). Ranges of one
-          // k-block (FP16) wait here, which measured faster for them.
-          const int buf = (int)(rg % L::NBUF);
-          if (!kSplitWaitsDrain) {
-            const int64_t use = rg / L::NBUF;
-            if (use > 0 && !wait(&tempty[buf], (uint32_t)((use - 1) & 1))) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-          }
-          const uint32_t d_acc = tmem + (uint32_t)(buf * L::ACC_COLS);
-          const int r1 = min(nkb, r0 + kFoldKb);
-          for (int kb = r0; kb < r1; kb++, g++) {
-            const int s = (int)(g % STAGES);
-            if (!wait(&conv[s], (uint32_t)((g / STAGES) & 1))) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            const int slot = (int)(g % L::ASLOTS);
-            const uint32_t ah = tmem + L::A_COL0 + (uint32_t)(slot * L::SLOT_COLS), al = ah + L::SLOT_COLS / 2;
-            const uint32_t bh = smem_u32(B_hi(s)), bl = smem_u32(B_lo(s));
+      // the products of k-block g (the kb - r0-th of its range) into d_acc,
+      // then the release of its stage and A slot (one thread)
+      auto issue = [&](int64_t g, int kr, uint32_t d_acc) {
+        const int s = (int)(g % STAGES);
+        const int slot = (int)(g % L::ASLOTS);
+        const uint32_t ah = tmem + L::A_COL0 + (uint32_t)(slot * L::SLOT_COLS), al = ah + L::SLOT_COLS / 2;
+        const uint32_t bh = smem_u32(B_hi(s)), bl = smem_u32(B_lo(s));
 #pragma unroll
-            for (int kk = 0; kk < kSteps; kk++) {
-              // 8 TMEM columns and 32 bytes of each B row per instruction
-              const uint64_t dbh = sw128_desc(bh + kk * 32), dbl = sw128_desc(bl + kk * 32);
-              const uint32_t acc = ((kb - r0) | kk) != 0;
-              if (MODE == MODE_TF32) {
-                umma_tf32_ts(d_acc, ah + kk * 8, dbh, idesc, acc);
-                umma_tf32_ts(d_acc, ah + kk * 8, dbl, idesc, 1);
-                umma_tf32_ts(d_acc, al + kk * 8, dbh, idesc, 1);
-              } else if (CG == 2) {
-                umma_f16_ts_pair(d_acc, ah + kk * 8, dbh, idesc, acc);
-                umma_f16_ts_pair(d_acc, ah + kk * 8, dbl, idesc, 1);
-                umma_f16_ts_pair(d_acc, al + kk * 8, dbh, idesc, 1);
-              } else {
-                umma_f16_ts(d_acc, ah + kk * 8, dbh, idesc, acc);
-                umma_f16_ts(d_acc, ah + kk * 8, dbl, idesc, 1);
-                umma_f16_ts(d_acc, al + kk * 8, dbh, idesc, 1);
-              }
-            }
-            commit(&empty[s]);
-            if (!L::SLOT_IS_STAGE) commit(&aempty[slot]);
+        for (int kk = 0; kk < kSteps; kk++) {
+          // 8 TMEM columns and 32 bytes of each B row per instruction
+          const uint64_t dbh = sw128_desc(bh + kk * 32), dbl = sw128_desc(bl + kk * 32);
+          const uint32_t acc = (kr | kk) != 0;
+          if (MODE == MODE_TF32) {
+            umma_tf32_ts(d_acc, ah + kk * 8, dbh, idesc, acc);
+            umma_tf32_ts(d_acc, ah + kk * 8, dbl, idesc, 1);
+            umma_tf32_ts(d_acc, al + kk * 8, dbh, idesc, 1);
+          } else if (CG == 2) {
+            umma_f16_ts_pair(d_acc, ah + kk * 8, dbh, idesc, acc);
+            umma_f16_ts_pair(d_acc, ah + kk * 8, dbl, idesc, 1);
+            umma_f16_ts_pair(d_acc, al + kk * 8, dbh, idesc, 1);
+          } else {
+            umma_f16_ts(d_acc, ah + kk * 8, dbh, idesc, acc);
+            umma_f16_ts(d_acc, ah + kk * 8, dbl, idesc, 1);
+            umma_f16_ts(d_acc, al + kk * 8, dbh, idesc, 1);
           }
-          if (!ok) break;
-          commit(&tfull[buf]);
+        }
+        commit(&empty[s]);
+        if (!L::SLOT_IS_STAGE) commit(&aempty[slot]);
+      };
+      int64_t g = 0, rg = 0;  // k-blocks and accumulation ranges issued
+      if constexpr (kWaiter) {
+        // No wait on the issuing thread: the waiter warp waits, up to kAhead
+        // k-blocks ahead, and releases each k-block through a named barrier.
+        // The whole warp runs the loop (named barriers count whole warps);
+        // lane 0 issues. A wait of the waiter that gave up ends both warps at
+        // the end of the tile (the products issued meanwhile read buffers that
+        // may not be ready: their results are discarded with the call's error
+        // status).
+        for (int64_t t = walker; t < n_tiles; t += n_walkers) {
+          const Tile d = decode(t);
+          const int nkb = d.kb1 - d.kb0;
+          for (int r0 = 0; r0 < nkb; r0 += kFoldKb, rg++) {
+            const int buf = (int)(rg % L::NBUF);
+            const uint32_t d_acc = tmem + (uint32_t)(buf * L::ACC_COLS);
+            const int r1 = min(nkb, r0 + kFoldKb);
+            for (int kb = r0; kb < r1; kb++, g++) {
+              named_sync(kBarReady + (int)(g % kAhead));
+              tc_fence_after();
+              if (lane == 0) issue(g, kb - r0, d_acc);
+              __syncwarp();
+              named_arrive(kBarIssued + (int)(g % kAhead));
+            }
+            if (lane == 0) commit(&tfull[buf]);
+            __syncwarp();
+          }
+          if (!named_all(kBarTile, true)) break;
+        }
+      } else if (lane == 0) {
+        // the issuing thread waits itself
+        bool ok = !g_stall || wait(stall, 0);  // test stall: nothing arrives there
+        for (int64_t t = walker; t < n_tiles && ok; t += n_walkers) {
+          const Tile d = decode(t);
+          const int nkb = d.kb1 - d.kb0;
+          for (int r0 = 0; r0 < nkb; r0 += kFoldKb, rg++) {
+            const int buf = (int)(rg % L::NBUF);
+            if (!kSplitWaitsDrain) {
+              const int64_t use = rg / L::NBUF;
+              if (use > 0 && !wait(&tempty[buf], (uint32_t)((use - 1) & 1))) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+            }
+            const uint32_t d_acc = tmem + (uint32_t)(buf * L::ACC_COLS);
+            const int r1 = min(nkb, r0 + kFoldKb);
+            for (int kb = r0; kb < r1; kb++, g++) {
+              if (!wait(&conv[(int)(g % STAGES)], (uint32_t)((g / STAGES) & 1))) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              issue(g, kb - r0, d_acc);
+            }
+            if (!ok) break;
+            commit(&tfull[buf]);
+          }
         }
       }
       // every product issued by this thread has retired once this fires
       // (for a pair, in both CTAs)
-      commit(drain);
-      mbar_wait_t<CG == 2>(drain, 0, abort_flag, kDrainNs, false);
+      if (lane == 0) {
+        commit(drain);
+        mbar_wait_t<CG == 2>(drain, 0, abort_flag, kDrainNs, false);
+      }
+      __syncwarp();
+    }
+  } else if (warp == kWaiterWarp) {
+    // readiness waiter of the issuing CTA: for each k-block it waits for the
+    // split A (and, at a range's start, for the accumulator to be drained
+    // where the split warps do not wait for that), then releases the k-block
+    // to the MMA warp; it runs at most kAhead k-blocks ahead, so its waits
+    // overlap the products of the k-blocks before. After a wait gives up it
+    // waits no more and releases the rest of the tile at once; the status
+    // reduction at the tile's end then stops both warps.
+    if (kWaiter && (CG == 1 || rank == 0)) {
+      constexpr int kFoldKb = fold_k<MODE>() / stage_k<MODE>();
+      int64_t g = 0, rg = 0;
+      bool ok = true;
+      // test stall: a bounded wait on a barrier nothing arrives at
+      if (lane == 0 && g_stall) ok = wait(stall, 0);
+      for (int64_t t = walker; t < n_tiles; t += n_walkers) {
+        const Tile d = decode(t);
+        const int nkb = d.kb1 - d.kb0;
+        for (int r0 = 0; r0 < nkb; r0 += kFoldKb, rg++) {
+          const int r1 = min(nkb, r0 + kFoldKb);
+          for (int kb = r0; kb < r1; kb++, g++) {
+            if (lane == 0 && ok) {
+              if (!kSplitWaitsDrain && kb == r0 && rg >= L::NBUF)
+                ok = wait(&tempty[rg % L::NBUF], (uint32_t)(((rg / L::NBUF) - 1) & 1));
+              if (ok) ok = wait(&conv[(int)(g % STAGES)], (uint32_t)((g / STAGES) & 1));
+            }
+            __syncwarp();
+            // k-block g - kAhead issued: its ready barrier may be reused
+            if (g >= kAhead) named_sync(kBarIssued + (int)(g % kAhead));
+            named_arrive(kBarReady + (int)(g % kAhead));
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, (int)ok, 0) != 0;
+        if (!named_all(kBarTile, ok)) break;
+      }
+      // take the last "issued" arrivals, so that every barrier generation
+      // completes before the CTA exits
+      for (int64_t q = g > kAhead ? g - kAhead : 0; q < g; q++) named_sync(kBarIssued + (int)(q % kAhead));
     }
   } else if (warp < 6) {
     // split warps: warp w takes TMEM lane quarter w % 4, one row of A a thread
@@ -729,7 +827,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           rg++;
         }
-        if ((use > 0 && !wait(&aempty[slot], (uint32_t)((use - 1) & 1))) ||
+        // the A slot is free once the products of k-block g - ASLOTS have
+        // retired; with one slot per stage the stage's TMA load waited for
+        // exactly that before it was issued, so its landing implies it
+        if ((!L::SLOT_IS_STAGE && use > 0 && !wait(&aempty[slot], (uint32_t)((use - 1) & 1))) ||
             !wait(&full[s], (uint32_t)((g / STAGES) & 1))) {
           ok = false;
           break;
