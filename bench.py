@@ -232,7 +232,7 @@ def plan_roofline(plan, precision, ms_per_group):
             fl = 8.0 * st["batch"] * st["M"] * st["N"] * st["K"]
         else:
             fl = 8.0 * (1 << len(lay[a] | lay[b]))
-        if st["gemm"] and st["tc"] and tc:
+        if st["gemm"] and st["tc"] and not st.get("tc_simt") and tc:
             tf = 3 * fl / (tc * 1e12)
         else:
             tf = fl / ((fp64 if precision == "c128" else simt) * 1e12)

@@ -410,6 +410,11 @@ int tz_op_cgemm_static_status(void *stream);
  * Graph replays captured earlier pick both up (they are read on the device). */
 int tz_debug_set_wait_limit(int64_t ns);
 int tz_debug_stall_tensor_core(int on);
+/* Test hook (process-wide): with on = 1, plans autotuned afterwards run every
+ * tensor-core step with at most 32 complex K values on the CUDA-core
+ * complex64 kernel, whichever is faster (the autotuner otherwise takes that
+ * kernel only where it measured faster); clears the autotuner's cache. */
+int tz_debug_tune_force_simt(int on);
 
 /* Process-wide default of how the split BF16 / FP16 products run where the
  * shape allows pairs (128-column tiles, m a multiple of 256): 1 on pairs of

@@ -125,6 +125,7 @@ SIGNATURES = {
     "tz_debug_stall_tensor_core": (c_int, [c_int]),
     "tz_tune_tc_pairs": (c_int, [c_int]),
     "tz_tune_tc_prefetch": (c_int, [c_int]),
+    "tz_debug_tune_force_simt": (c_int, [c_int]),
 }
 
 _lib = None

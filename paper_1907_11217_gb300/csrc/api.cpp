@@ -601,6 +601,12 @@ int tz_tune_tc_prefetch(int kblocks) {
   TZ_CATCH
 }
 
+int tz_debug_tune_force_simt(int on) {
+  TZ_TRY
+  tz::tune_force_simt(on);
+  TZ_CATCH
+}
+
 int tz_debug_stall_tensor_core(int on) {
   TZ_TRY
   tz::cuda_check(tz::dev::tc_set_stall(on), "set stall switch");

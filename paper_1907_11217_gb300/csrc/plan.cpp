@@ -7,6 +7,7 @@
 #include <cstring>
 #include <map>
 #include <tuple>
+#include <atomic>
 #include <mutex>
 #include <memory>
 #include <sstream>
@@ -696,7 +697,7 @@ std::string plan_describe(const tz_plan *p) {
       << ",\"M\":" << x.M << ",\"N\":" << x.N << ",\"K\":" << x.K << ",\"batch\":" << x.batch
       << ",\"level\":" << x.level << ",\"dstep\":" << x.dstep << ",\"permX\":" << x.permX << ",\"permY\":" << x.permY
       << ",\"row_major\":" << x.row_major << ",\"c_nat\":" << x.c_nat << ",\"skinny\":" << x.skinny
-      << ",\"tc_pair\":" << x.tc_pair << ",\"tc_ksplit\":" << x.tc_ksplit;
+      << ",\"tc_pair\":" << x.tc_pair << ",\"tc_ksplit\":" << x.tc_ksplit << ",\"tc_simt\":" << x.tc_simt;
     auto arr = [&](const char *name, const int8_t *v, int n) {
       o << ",\"" << name << "\":[";
       for (int j = 0; j < n; j++) o << (j ? "," : "") << (int)v[j];
@@ -828,7 +829,7 @@ static void item_cost(const tz_plan *p, const Item &it, int *kind, double *flops
     case IT_GEMM: {
       const PStep &ps = p->S[it.a];
       const bool dot = ps.M * ps.N <= 64 && ps.K >= 64 && (ps.K % 2) == 0;
-      *kind = ps.tc ? 4 : ps.skinny ? 6 : dot ? 7 : 3;
+      *kind = ps.tc && !ps.tc_simt ? 4 : ps.skinny ? 6 : dot ? 7 : 3;
       *flops = 8.0 * ps.batch * (double)ps.M * (double)ps.N * (double)ps.K;
       *bytes = (double)p->esz * ps.batch * ((double)ps.M * ps.K + (double)ps.N * ps.K + (double)ps.M * ps.N);
       break;
@@ -908,7 +909,7 @@ static void run_items(tz_plan *p, const std::vector<Item> &items, const RunCtx &
         } else if (ps.skinny) {
           cuda_check(dev::launch_cgemm_skinny_gather(X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.gather, sc, s),
                      "skinny gemm");
-        } else if (ps.tc) {
+        } else if (ps.tc && !ps.tc_simt) {
           void *scr = abase + ps.tc_scratch_off;
           cuda_check(dev::launch_cgemm_tc(p->opts.precision, X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.M * ps.K,
                                           ps.N * ps.K, ps.M * ps.N, sc, scr, (size_t)ps.tc_scratch, &gs->tc_error,
@@ -971,12 +972,23 @@ struct TuneKey {
   }
 };
 struct TuneChoice {
-  int pair, ksplit;
+  int pair, ksplit, simt;
   float ms;
 };
+// products with at most this many complex K values also try the CUDA-core
+// complex64 kernel (FP32 FMA: at least as accurate as the split products);
+// with so few terms per output they are bound by writing C
+constexpr int64_t kTuneSimtMaxK = 32;
+std::atomic<int> g_tune_force_simt{0};  // test hook: take that kernel wherever allowed
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneChoice> g_tune_cache;
 }  // namespace
+
+void tune_force_simt(int on) {
+  g_tune_force_simt.store(on ? 1 : 0);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache.clear();  // choices made under the other setting are not reused
+}
 
 static void autotune_tc_steps(tz_plan *p) {
   cudaStream_t s = p->stream;
@@ -1001,6 +1013,7 @@ static void autotune_tc_steps(tz_plan *p) {
         if (f != g_tune_cache.end()) {
           ps.tc_pair = f->second.pair;
           ps.tc_ksplit = f->second.ksplit;
+          ps.tc_simt = f->second.simt;
           tuned++;
           continue;
         }
@@ -1014,26 +1027,38 @@ static void autotune_tc_steps(tz_plan *p) {
       float2 *C = (float2 *)tensor_ptr(p, ctx, ps.c_nat >= 0 ? ps.c_nat : ps.c);
       const dev::CScatter *sc = ps.row_major ? nullptr : &ps.scatter;
       void *scr = abase + ps.tc_scratch_off;
-      TuneChoice best{-1, 0, 1e30f};
+      TuneChoice best{-1, 0, 0, 1e30f};
+      auto time_it = [&](auto launch) {
+        launch();  // warm-up
+        cuda_check(cudaEventRecord(e0, s), "event");
+        for (int r = 0; r < 3; r++) launch();
+        cuda_check(cudaEventRecord(e1, s), "event");
+        cuda_check(cudaEventSynchronize(e1), "event");
+        float ms = 0;
+        cuda_check(cudaEventElapsedTime(&ms, e0, e1), "event");
+        return ms;
+      };
       for (int pr : pairs)
         for (int ks : splits) {
-          auto launch = [&] {
+          const float ms = time_it([&] {
             cuda_check(dev::launch_cgemm_tc(p->opts.precision, X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.M * ps.K,
                                             ps.N * ps.K, ps.M * ps.N, sc, scr, (size_t)ps.tc_scratch, &gs->tc_error,
                                             s, pr, ks),
                        "autotune launch");
-          };
-          launch();  // warm-up
-          cuda_check(cudaEventRecord(e0, s), "event");
-          for (int r = 0; r < 3; r++) launch();
-          cuda_check(cudaEventRecord(e1, s), "event");
-          cuda_check(cudaEventSynchronize(e1), "event");
-          float ms = 0;
-          cuda_check(cudaEventElapsedTime(&ms, e0, e1), "event");
-          if (ms < best.ms) best = TuneChoice{pr, ks, ms};
+          });
+          if (ms < best.ms) best = TuneChoice{pr, ks, 0, ms};
         }
+      if (ps.K <= kTuneSimtMaxK) {
+        const float ms = time_it([&] {
+          cuda_check(dev::launch_cgemm_simt(X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.M * ps.K, ps.N * ps.K,
+                                            ps.M * ps.N, sc, s),
+                     "autotune launch");
+        });
+        if (ms < best.ms || g_tune_force_simt.load()) best = TuneChoice{-1, 0, 1, ms};
+      }
       ps.tc_pair = best.pair;
       ps.tc_ksplit = best.ksplit;
+      ps.tc_simt = best.simt;
       tuned++;
       std::lock_guard<std::mutex> lk(g_tune_mu);
       g_tune_cache[key] = best;
@@ -1050,7 +1075,7 @@ static void autotune_tc_steps(tz_plan *p) {
   int n = 0;
   for (const Item &it : p->var_items) {
     int c = 1;
-    if (it.kind == IT_GEMM && p->S[it.a].tc) {
+    if (it.kind == IT_GEMM && p->S[it.a].tc && !p->S[it.a].tc_simt) {
       const PStep &ps = p->S[it.a];
       c = dev::cgemm_tc_launches(p->opts.precision, ps.batch, ps.M, ps.N, ps.K, !ps.row_major, ps.tc_ksplit);
     } else if (it.kind == IT_ACCUM) {

@@ -35,6 +35,8 @@ struct PStep {
   int64_t tc_scratch_off = -1;
   int tc_pair = -1;           // tensor-core launch choice (autotuned at bind): pairs of
   int tc_ksplit = 0;          // CTAs (1/0, -1 default) and K split (1 none, 0 default)
+  int tc_simt = 0;            // 1: the autotuner found the CUDA-core complex64 kernel
+                              // faster for this (small-K) step
   dev::CScatter scatter{};    // where the GEMM writes its result
   bool row_major = false;     // scatter is the plain row-major order
   int c_nat = -1;             // tensor the GEMM writes in row-major order when a
@@ -127,6 +129,8 @@ void plan_run(tz_plan *p, const RunCtx &ctx, int64_t n_rows, int64_t lo, int64_t
 // call on it (or of the bind-time steps) timed out in a bounded wait.
 // Synchronous (reads device memory); call after the stream has finished.
 int read_tc_error(const tz_plan *p, const RunCtx &ctx);
+// test hook: autotuned steps with small K take the CUDA-core kernel
+void tune_force_simt(int on);
 void plan_destroy(tz_plan *p);
 void plan_profile_collect(tz_plan *p);
 void item_cost_public(const tz_plan *p, int var_item, int *kind, double *flops, double *bytes);

@@ -221,3 +221,31 @@ def test_autotuned_plan_matches_oracle(tz, prec):
     got = tz.tz_contract_amplitudes(plan, bits)
     ref = np.array([tn.Contractor(spec, max_log2=24).amplitude(x) for x in bits[:16]])
     assert rel_err(got[:16], ref, 49) <= (3e-5 if prec == "bf16x3" else TOL_C64)
+
+
+def test_autotuned_small_k_steps_on_cuda_cores(tz):
+    """The autotuner may run a small-K tensor-core step on the CUDA-core
+    complex64 kernel, through the output layout chosen for the tensor-core
+    product (the test hook forces that choice wherever it is allowed); the
+    amplitudes still match the oracle."""
+    import json
+    spec = grid_spec(7, 7, 16, 2)
+    bits = ti.random_bitstrings(49, 64, 77)
+    net = tz.tz_network_from_circuit(tz.tz_circuit_from_spec(spec), 6)
+    tree = tz.tz_path_greedy(net, restarts=16, seed=7, algorithm="elimination", precision="fp16x3")
+    tz.tz_debug_tune_force_simt(True)
+    try:
+        plan = tz.tz_plan_create(net, tree, [], precision="fp16x3", max_bitstrings=64, autotune=True)
+        plan.bind()
+    finally:
+        tz.tz_debug_tune_force_simt(False)
+    steps = [s for s in json.loads(plan.describe())["steps"] if s.get("var") and s.get("gemm") and s.get("tc")]
+    small = [s for s in steps if s["K"] <= 32]
+    assert small and all(s["tc_simt"] == 1 for s in small)
+    assert all(s["tc_simt"] == 0 for s in steps if s["K"] > 32)
+    plan.profile_enable(True)
+    got = tz.tz_contract_amplitudes(plan, bits)
+    prof = plan.profile()
+    assert prof["gemm_simt"]["launches"] >= len(small)
+    ref = np.array([tn.Contractor(spec, max_log2=24).amplitude(x) for x in bits[:16]])
+    assert rel_err(got[:16], ref, 49) <= TOL_C64

@@ -300,8 +300,10 @@ PARTIAL_TOL = {"c64": 1e-5, "tf32x3": 1e-5, "fp16x3": 1e-5, "bf16x3": 3e-5, "c12
 
 def _partials(tz, net, tree, sliced, prec, bits, slices):
     import torch
+    # autotuned as in the bench: the steps run in the launch forms and on the
+    # kernels the autotuner picks
     plan = tz.tz_plan_create(net, tree, sliced, precision=prec, stream=torch.cuda.Stream(), use_graph=True,
-                             max_bitstrings=len(bits))
+                             max_bitstrings=len(bits), autotune=True)
     plan.bind()
     out = {}
     for s in slices:
