@@ -204,8 +204,9 @@ def test_slice_farm_ledger_resume_on_gpu(tz, tmp_path):
 @pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
 def test_autotuned_plan_matches_oracle(tz, prec):
     """A plan bound with autotune: every tensor-core step gets a timed
-    launch choice (pairs of CTAs or single CTAs; K split or not), recorded
-    in the plan description, and the amplitudes still match the oracle."""
+    launch choice (pairs of CTAs or single CTAs; K split or not; the
+    CUDA-core kernel for small K), recorded in the plan description, and the
+    amplitudes still match the oracle."""
     import json
     spec = grid_spec(7, 7, 16, 2)
     bits = ti.random_bitstrings(49, 64, 77)
@@ -216,8 +217,11 @@ def test_autotuned_plan_matches_oracle(tz, prec):
     st = plan.stats()
     steps = [s for s in json.loads(plan.describe())["steps"] if s.get("var") and s.get("gemm") and s.get("tc")]
     assert steps and st["n_tuned_steps"] == len(steps)
-    assert all(s["tc_pair"] in (0, 1) and s["tc_ksplit"] in (0, 1) for s in steps)
-    print(f"{prec}: tuned {len(steps)} steps, pairs chosen for {sum(s['tc_pair'] for s in steps)}")
+    # each step: a tensor-core launch form, or (K <= 32) the CUDA-core kernel
+    assert all((s["tc_simt"] == 0 and s["tc_pair"] in (0, 1) and s["tc_ksplit"] in (0, 1)) or
+               (s["tc_simt"] == 1 and s["K"] <= 32) for s in steps)
+    print(f"{prec}: tuned {len(steps)} steps, pairs chosen for {sum(s['tc_pair'] == 1 for s in steps)}, "
+          f"CUDA cores for {sum(s['tc_simt'] for s in steps)}")
     got = tz.tz_contract_amplitudes(plan, bits)
     ref = np.array([tn.Contractor(spec, max_log2=24).amplitude(x) for x in bits[:16]])
     assert rel_err(got[:16], ref, 49) <= (3e-5 if prec == "bf16x3" else TOL_C64)
