@@ -90,6 +90,12 @@ def parse():
     ap.add_argument("--autotune", type=int, default=1,
                     help="1: time each tensor-core step's launch choices when the plan is bound (untimed "
                          "preprocessing) and keep the fastest; 0: built-in defaults")
+    ap.add_argument("--direct-levels", type=int, default=0,
+                    help="0: each run of small direct steps between products is one persistent queue launch; "
+                         "1: one launch per dependency level")
+    ap.add_argument("--compare-direct", type=int, default=0,
+                    help="rounds of an interleaved comparison with the other direct-step launch form (same "
+                         "tree, same autotuned products, same slice windows; 0: off)")
     ap.add_argument("--tree-seed", type=int, default=7)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
@@ -132,7 +138,7 @@ def build_plan(tz, spec, args, precision, stream, device, log2_max, max_rows=0):
         sliced = tz.tz_slice_select(net, tree, log2_max, 40) if log2_max > 0 else []
     plan = tz.tz_plan_create(net, tree, sliced, precision=precision, device=device, stream=stream, use_graph=True,
                              max_bitstrings=max_rows or args.bitstrings or 1 << max(args.batch_log2, 0),
-                             autotune=bool(args.autotune))
+                             autotune=bool(args.autotune), direct_levels=bool(args.direct_levels))
     prep_s = time.perf_counter() - t0
     return plan, sliced, prep_s
 
@@ -672,7 +678,36 @@ def main():
     rl = roofline(prof, precision, args.workload)
     rl["plan_roofline"] = plan_roofline(plan, precision, ms / S / chunks)
     per_launch = {k: v["launches"] for k, v in prof.items()}
+    per_kind_ms = {k: v["ms"] for k, v in prof.items()}
     launches_per_call = 1 + S * chunks * st["n_launches_per_group"]
+
+    # the other direct-step launch form on the same tree and slice windows,
+    # interleaved step by step with this plan (the autotuner's cached choices
+    # make the products identical), so that drifts in clock and power hit both
+    direct_compare = None
+    if args.compare_direct > 0 and world == 1:
+        p3, _, _ = build_plan(tz, spec, argparse.Namespace(**{**vars(args), "direct_levels": 1 - args.direct_levels}),
+                              precision, stream, device, log2_max)
+        p3.bind()
+        t_one, t_other = [], []
+        for r in range(args.compare_direct):
+            for pl, acc in ((plan, t_one), (p3, t_other)):
+                lo, hi = slice_range(r)
+                pl.set_slice_range(lo, hi)
+                tz.tz_contract_amplitudes_device(pl, d_bits, d_out)   # warm: the window's first run
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                tz.tz_contract_amplitudes_device(pl, d_bits, d_out)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                acc.append(e0.elapsed_time(e1) / (hi - lo))
+        names = ("per dependency level", "queue") if args.direct_levels else ("queue", "per dependency level")
+        direct_compare = {"ms_per_slice": {names[0]: statistics.median(t_one), names[1]: statistics.median(t_other)},
+                          "launches_per_slice": {names[0]: st["n_launches_per_group"],
+                                                 names[1]: p3.stats()["n_launches_per_group"]},
+                          "rounds": args.compare_direct, "slices_per_round": S}
+        p3.close()
 
     # the same workload in the other modes (split precision against complex64),
     # each with its own tree and plan, timed over the same slice windows
@@ -741,14 +776,17 @@ def main():
                  "gemm_steps": st["n_gemm_steps"], "launches_per_slice": st["n_launches_per_group"],
                  "workspace_gb": st["workspace_bytes"] / 1e9,
                  "const_steps": st["n_const_steps"], "const_flops": st["const_flops"],
-                 "bind_ms": plan_bind_ms, "autotuned_steps": n_tuned},
+                 "bind_ms": plan_bind_ms, "autotuned_steps": n_tuned,
+                 "direct_launch": "per dependency level" if args.direct_levels else "queue"},
         "e2e": {"value": e2e_s, "unit": "s/amplitude", "h2d_bytes_per_step": int(bits.nbytes),
                 "d2h_bytes_per_step": 16 * A},
         "roofline": rl,
         "compare": compare,
+        "direct_compare": direct_compare,
         "cpu_baseline": cpu,
         "gpu_launches": args.steps * launches_per_call,
         "profiled_launches_per_kind": per_launch,
+        "profiled_ms_per_kind": per_kind_ms,
         "clocks": clk.summary(),
     }
     print(json.dumps(line))

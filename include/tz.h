@@ -210,6 +210,11 @@ typedef struct {
                             not) on the plan's own buffers and keep the fastest; choices
                             are cached per device, precision, shape and output kind.
                             0: the built-in defaults                                  */
+  int direct_levels;     /* 0: each run of direct (small) steps between two products or
+                            permutes is one persistent launch over a device work queue,
+                            each step placed at the earliest point its inputs exist
+                            (blocks wait, bounded, for the steps they read);
+                            1: one launch per dependency level                         */
 } tz_plan_opts;
 
 typedef struct {
@@ -270,15 +275,16 @@ int tz_contract_amplitudes(tz_plan *plan, const uint8_t *bitstrings, int64_t n, 
 /* Same with device pointers; asynchronous on the plan's stream (no host
  * synchronisation). d_bitstrings: n x n_qubits uint8; d_out: 2n doubles
  * (2n * 2^n_open with open output qubits).
- * If a tensor-core product of the call times out in one of its bounded
- * waits, the amplitudes it could have affected are written as NaN, and
+ * If a tensor-core product or a direct-step queue launch of the call times
+ * out in one of its bounded waits, the amplitudes it could have affected
+ * are written as NaN, and
  * tz_plan_status reports TZ_ETIMEOUT. (tz_contract_amplitudes returns
  * TZ_ETIMEOUT itself.) */
 int tz_contract_amplitudes_device(tz_plan *plan, const uint8_t *d_bitstrings, int64_t n, double *d_out);
 /* Synchronise the plan's stream and report how its last call (on the plan's
- * own workspace) ended: TZ_ETIMEOUT if a tensor-core product timed out in a
- * bounded wait (its amplitudes are then NaN), else TZ_OK. Each call starts
- * with a clear status. */
+ * own workspace) ended: TZ_ETIMEOUT if a tensor-core product or a direct-step
+ * queue launch ran out of time in a bounded wait (its amplitudes are then
+ * NaN), else TZ_OK. Each call starts with a clear status. */
 int tz_plan_status(tz_plan *plan);
 void tz_plan_destroy(tz_plan *plan);
 
@@ -400,16 +406,21 @@ int tz_op_cgemm_static(int precision, int64_t batch, int64_t m, int64_t n, int64
  * timed out in a bounded wait. */
 int tz_op_cgemm_static_status(void *stream);
 
-/* Test hooks (current device; they change no result of a product that
- * completes). tz_debug_set_wait_limit: the time limit of the tensor-core
- * products' bounded waits, in ns (0 restores the default 2 s); waits that let
- * copies in flight land before a stopped product exits always keep 2 s.
+/* Test hooks (current device; they change no result of a launch that
+ * completes). tz_debug_set_wait_limit: the time limit of the bounded waits of
+ * the tensor-core products and of the direct-step queue launches, in ns (0
+ * restores the default 2 s); waits that let copies in flight land before a
+ * stopped product exits always keep 2 s.
  * tz_debug_stall_tensor_core(1): every tensor-core product launched while it
  * is on first waits on a barrier that nothing arrives at, so the wait runs
  * out after the limit and the product reports TZ_ETIMEOUT; (0) turns it off.
- * Graph replays captured earlier pick both up (they are read on the device). */
+ * tz_debug_stall_direct_queue(1): likewise, the first block of every
+ * direct-step queue launch waits on a counter that nothing increments; the
+ * launch stops and the plan's call reports TZ_ETIMEOUT.
+ * Graph replays captured earlier pick these up (they are read on the device). */
 int tz_debug_set_wait_limit(int64_t ns);
 int tz_debug_stall_tensor_core(int on);
+int tz_debug_stall_direct_queue(int on);
 /* Test hook (process-wide): with on = 1, plans autotuned afterwards run every
  * tensor-core step with at most 32 complex K values on the CUDA-core
  * complex64 kernel, whichever is faster (the autotuner otherwise takes that

@@ -27,7 +27,7 @@ __all__ = [
     "tz_tree_from_pairs", "tz_slice_select", "tz_plan_create", "tz_contract_amplitudes",
     "tz_contract_amplitudes_device", "tz_op_permute", "tz_op_cgemm", "tz_op_accumulate", "PRECISIONS",
     "tz_plan_status", "tz_op_cgemm_status", "tz_op_cgemm_static_status", "tz_debug_set_wait_limit",
-    "tz_debug_stall_tensor_core", "tz_tune_tc_pairs", "tz_tune_tc_prefetch", "tz_debug_tune_force_simt",
+    "tz_debug_stall_tensor_core", "tz_debug_stall_direct_queue", "tz_tune_tc_pairs", "tz_tune_tc_prefetch", "tz_debug_tune_force_simt",
     "TZ_C64_SIMT", "TZ_TF32X3", "TZ_BF16X3", "TZ_FP16X3",
 ]
 
@@ -259,10 +259,10 @@ class Plan(_Handle):
 
 
 def tz_plan_create(net: Network, tree: Tree, sliced=(), precision="c64", device=0, stream=None, small_log2=0,
-                   use_graph=False, max_bitstrings=0, autotune=False) -> Plan:
+                   use_graph=False, max_bitstrings=0, autotune=False, direct_levels=False) -> Plan:
     arr = np.ascontiguousarray(np.asarray(list(sliced), dtype=np.int32))
     o = tz_plan_opts(PRECISIONS.get(precision, precision), device, _stream(stream), small_log2, int(use_graph),
-                     max_bitstrings, int(autotune))
+                     max_bitstrings, int(autotune), int(direct_levels))
     h = ctypes.c_void_p()
     ptr = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if len(arr) else None
     check(lib().tz_plan_create(net.handle, tree.handle, ptr, len(arr), ctypes.byref(o), ctypes.byref(h)))
@@ -338,6 +338,13 @@ def tz_debug_stall_tensor_core(on: bool):
     """Test hook: while on, every tensor-core product on the current device
     first waits on a barrier nothing arrives at, so its bounded wait runs out."""
     check(lib().tz_debug_stall_tensor_core(1 if on else 0))
+
+
+def tz_debug_stall_direct_queue(on: bool):
+    """Test hook: while on, the first block of every direct-step queue launch
+    on the current device waits on a counter nothing increments, so its
+    bounded wait runs out."""
+    check(lib().tz_debug_stall_direct_queue(1 if on else 0))
 
 
 def tz_tune_tc_pairs(mode: int):

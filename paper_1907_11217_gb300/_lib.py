@@ -41,7 +41,7 @@ class tz_path_opts(ctypes.Structure):
 class tz_plan_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("device", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("small_log2", ctypes.c_int), ("use_graph", ctypes.c_int), ("max_bitstrings", ctypes.c_int64),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("direct_levels", ctypes.c_int)]
 
 
 class tz_plan_stats(ctypes.Structure):
@@ -123,6 +123,7 @@ SIGNATURES = {
     "tz_op_cgemm_static_status": (c_int, [P]),
     "tz_debug_set_wait_limit": (c_int, [c_int64]),
     "tz_debug_stall_tensor_core": (c_int, [c_int]),
+    "tz_debug_stall_direct_queue": (c_int, [c_int]),
     "tz_tune_tc_pairs": (c_int, [c_int]),
     "tz_tune_tc_prefetch": (c_int, [c_int]),
     "tz_debug_tune_force_simt": (c_int, [c_int]),

@@ -417,8 +417,8 @@ int tz_contract_amplitudes(tz_plan *plan, const uint8_t *bitstrings, int64_t n, 
                                  cudaMemcpyDeviceToHost, s),
                  "copy amplitudes out");
   tz::cuda_check(cudaStreamSynchronize(s), "contract");
-  if (is_tc_precision(plan->opts.precision) && tz::read_tc_error(plan, ctx))
-    tz::fail(TZ_ETIMEOUT, "a tensor-core product timed out in a bounded wait; the amplitudes are invalid (NaN)");
+  if (tz::read_tc_error(plan, ctx))
+    tz::fail(TZ_ETIMEOUT, "a bounded wait (tensor-core product or direct-step queue) ran out; the amplitudes are invalid (NaN)");
   TZ_CATCH
 }
 
@@ -429,8 +429,8 @@ int tz_plan_status(tz_plan *plan) {
   tz::cuda_check(cudaSetDevice(plan->opts.device), "cudaSetDevice");
   const tz::RunCtx ctx = tz::default_ctx(plan);
   tz::cuda_check(cudaStreamSynchronize(ctx.stream), "synchronise the plan's stream");
-  if (is_tc_precision(plan->opts.precision) && tz::read_tc_error(plan, ctx))
-    tz::fail(TZ_ETIMEOUT, "a tensor-core product of the last call timed out in a bounded wait; its amplitudes are NaN");
+  if (tz::read_tc_error(plan, ctx))
+    tz::fail(TZ_ETIMEOUT, "a bounded wait (tensor-core product or direct-step queue) of the last call ran out; its amplitudes are NaN");
   TZ_CATCH
 }
 
@@ -586,6 +586,7 @@ int tz_debug_set_wait_limit(int64_t ns) {
   TZ_TRY
   REQUIRE(ns >= 0, "wait limit must be >= 0");
   tz::cuda_check(tz::dev::tc_set_wait_limit((unsigned long long)ns), "set wait limit");
+  tz::cuda_check(tz::dev::direct_queue_set_wait_limit((unsigned long long)ns), "set queue wait limit");
   TZ_CATCH
 }
 
@@ -610,6 +611,12 @@ int tz_debug_tune_force_simt(int on) {
 int tz_debug_stall_tensor_core(int on) {
   TZ_TRY
   tz::cuda_check(tz::dev::tc_set_stall(on), "set stall switch");
+  TZ_CATCH
+}
+
+int tz_debug_stall_direct_queue(int on) {
+  TZ_TRY
+  tz::cuda_check(tz::dev::direct_queue_set_stall(on), "set queue stall switch");
   TZ_CATCH
 }
 

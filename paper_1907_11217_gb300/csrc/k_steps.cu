@@ -1,5 +1,8 @@
 // Per-group kernels: leaf builder, direct small-step contraction, FP64
 // accumulation of partial amplitudes.
+#include <algorithm>
+#include <mutex>
+
 #include "kernels.h"
 
 namespace tz {
@@ -95,34 +98,27 @@ cudaError_t launch_leaf_build(const LeafJob *jobs, int n_jobs, const GroupState 
   return cudaGetLastError();
 }
 
-// Direct contraction of small steps, several independent steps per launch.
-// Each output element is summed by 2^split consecutive threads, each walking
-// its share of the contracted bits in Gray-code order (one offset update per
-// term), then reduced.
-template <typename T>
-__global__ void __launch_bounds__(256) direct_kernel(const DStep *steps, int n_steps, const char *cbase,
-                                                     char *abase) {
-  __shared__ int s_idx;
-  __shared__ T red[256];
-  const int64_t blk = blockIdx.x;
-  if (threadIdx.x == 0) {
-    int lo = 0, hi = n_steps - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (steps[mid].block_begin <= blk)
-        lo = mid;
-      else
-        hi = mid - 1;
-    }
-    s_idx = lo;
-  }
-  __syncthreads();
-  const DStep &st = steps[s_idx];
+// Direct contraction of small steps. Each output element is summed by
+// 2^split consecutive threads, each walking its share of the contracted bits
+// in Gray-code order (one offset update per term), then reduced. blk is the
+// block's number within its step. kCG reads the operands through L2 only
+// (ld.global.cg): in a queue launch they may have been written by other
+// blocks of the same launch, after this SM last cached those addresses.
+template <typename T, bool kCG>
+__device__ __forceinline__ T load_op(const T *p) {
+  if constexpr (kCG)
+    return __ldcg(p);
+  else
+    return *p;
+}
+
+template <typename T, bool kCG>
+__device__ __forceinline__ void direct_block(const DStep &st, int64_t blk, const char *cbase, char *abase, T *red) {
   const T *__restrict__ Ap = region_ptr<T>(st.A, cbase, abase);
   const T *__restrict__ Bp = region_ptr<T>(st.B, cbase, abase);
   T *Cp = const_cast<T *>(region_ptr<T>(st.C, cbase, abase));
   const int split = st.split;
-  const int64_t item = (blk - st.block_begin) * 256 + threadIdx.x;
+  const int64_t item = blk * 256 + threadIdx.x;
   const int64_t c = item >> split;
   const int part = (int)(item & ((1 << split) - 1));
   const bool active = c < (int64_t(1) << st.nC);
@@ -140,7 +136,7 @@ __global__ void __launch_bounds__(256) direct_kernel(const DStep *steps, int n_s
         oa += int64_t(1) << st.a_k[nlow + q];
         ob += int64_t(1) << st.b_k[nlow + q];
       }
-    acc = cmul(Ap[oa], Bp[ob]);
+    acc = cmul(load_op<T, kCG>(Ap + oa), load_op<T, kCG>(Bp + ob));
     const int64_t nt = int64_t(1) << nlow;
     for (int64_t t = 1; t < nt; t++) {
       const int q = __ffsll(t) - 1;
@@ -148,7 +144,7 @@ __global__ void __launch_bounds__(256) direct_kernel(const DStep *steps, int n_s
       const int64_t da = int64_t(1) << st.a_k[q], db = int64_t(1) << st.b_k[q];
       oa += on ? da : -da;
       ob += on ? db : -db;
-      acc = cfma(Ap[oa], Bp[ob], acc);
+      acc = cfma(load_op<T, kCG>(Ap + oa), load_op<T, kCG>(Bp + ob), acc);
     }
   }
   if (split > 0) {
@@ -165,6 +161,32 @@ __global__ void __launch_bounds__(256) direct_kernel(const DStep *steps, int n_s
   if (active && part == 0) Cp[c] = acc;
 }
 
+// One launch per dependency level: block b of the launch belongs to the step
+// whose block range holds b.
+__device__ __forceinline__ int step_of_block(const DStep *steps, int n_steps, int64_t blk) {
+  int lo = 0, hi = n_steps - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (steps[mid].block_begin <= blk)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) direct_kernel(const DStep *steps, int n_steps, const char *cbase,
+                                                     char *abase) {
+  __shared__ int s_idx;
+  __shared__ T red[256];
+  const int64_t blk = blockIdx.x;
+  if (threadIdx.x == 0) s_idx = step_of_block(steps, n_steps, blk);
+  __syncthreads();
+  const DStep &st = steps[s_idx];
+  direct_block<T, false>(st, blk - st.block_begin, cbase, abase, red);
+}
+
 cudaError_t launch_direct(const DStep *steps, int n_steps, int64_t total_blocks, const char *cbase, char *abase,
                           int dbl, cudaStream_t s) {
   if (n_steps <= 0) return cudaSuccess;
@@ -174,6 +196,153 @@ cudaError_t launch_direct(const DStep *steps, int n_steps, int64_t total_blocks,
   else
     direct_kernel<float2><<<(unsigned)total_blocks, 256, 0, s>>>(steps, n_steps, cbase, abase);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- queue
+// The persistent form. ctrl[0] hands out tickets (the launch's blocks in
+// order), ctrl[1] counts blocks that have left, ctrl[2] is the stop flag,
+// ctrl[3] is a counter nothing increments (the test stall waits on it), and
+// ctrl[4 + j] counts the finished blocks of step j.
+//
+// Progress: a step's blocks come after the blocks of the steps it reads
+// (DStep::dep < own index, tickets in block order). A block holding a
+// ticket is resident, so the lowest unfinished ticket always has all of its
+// inputs done and runs to the end; no wait can close a cycle, whatever the
+// grid size. Every wait is still bounded.
+constexpr unsigned long long kQueueWaitNs = 2000000000ull;  // 2 s (default)
+__device__ unsigned long long g_dq_wait_ns = kQueueWaitNs;
+__device__ int g_dq_stall;
+
+__device__ __forceinline__ unsigned long long dq_globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Wait until *cnt >= target: 1 when it is, 0 when the launch was stopped or
+// the wait ran out (then the error word and the stop flag are set).
+__device__ bool dq_wait(const unsigned *cnt, unsigned target, unsigned *stop, int *err,
+                        unsigned long long limit) {
+  const unsigned long long t0 = dq_globaltimer();
+  for (unsigned polls = 0;; polls++) {
+    if (ld_acquire(cnt) >= target) return true;
+    if (ld_acquire(stop)) return false;
+    if ((polls & 15) == 15) {
+      if (dq_globaltimer() - t0 > limit) {
+        atomicExch(err, 1);
+        atomicExch(stop, 1u);
+        return false;
+      }
+      __nanosleep(64);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) direct_queue_kernel(const DStep *steps, int n_steps, int64_t total,
+                                                           const char *cbase, char *abase, unsigned *ctrl,
+                                                           int *err) {
+  __shared__ int s_idx, s_go, s_last;
+  __shared__ int64_t s_blk;
+  __shared__ T red[256];
+  unsigned *done = ctrl + 4;
+  const unsigned long long limit = g_dq_wait_ns;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int64_t t = atomicAdd(&ctrl[0], 1u);
+      int go = t < total;
+      int idx = 0;
+      if (go) {
+        idx = step_of_block(steps, n_steps, t);
+        if (g_dq_stall && t == 0) go = dq_wait(&ctrl[3], 1u, &ctrl[2], err, limit);
+        for (int k = 0; k < 2 && go; k++) {
+          const int d = steps[idx].dep[k];
+          if (d >= 0) go = dq_wait(&done[d], (unsigned)steps[d].nblk, &ctrl[2], err, limit);
+        }
+      }
+      s_idx = idx;
+      s_blk = t;
+      s_go = go;
+    }
+    __syncthreads();
+    if (!s_go) break;
+    const DStep &st = steps[s_idx];
+    direct_block<T, true>(st, s_blk - st.block_begin, cbase, abase, red);
+    __syncthreads();  // every result of this block is written
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&done[s_idx], 1u);
+    }
+  }
+  // the last block to leave zeroes the counters for the next launch
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&ctrl[1], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    for (int j = threadIdx.x; j < n_steps; j += blockDim.x) done[j] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      ctrl[0] = 0;
+      ctrl[2] = 0;
+      ctrl[3] = 0;
+      __threadfence();
+      ctrl[1] = 0;
+    }
+  }
+}
+
+namespace {
+// resident blocks of the queue kernel per device (blocks per SM x SMs)
+std::mutex g_dq_mu;
+int g_dq_resident[2][64];
+}  // namespace
+
+template <typename T>
+static int dq_resident(int dbl) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  std::lock_guard<std::mutex> lk(g_dq_mu);
+  int &r = g_dq_resident[dbl][dev];
+  if (r == 0) {
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, direct_queue_kernel<T>, 256, 0) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return 0;
+    r = std::max(1, per_sm) * std::max(1, sms);
+  }
+  return r;
+}
+
+cudaError_t launch_direct_queue(const DStep *steps, int n_steps, int64_t total_blocks, const char *cbase,
+                                char *abase, unsigned *ctrl, int *err, int dbl, cudaStream_t s) {
+  if (n_steps <= 0) return cudaSuccess;
+  if (total_blocks > 0x7fffffffLL || !ctrl || !err) return cudaErrorInvalidValue;
+  const int resident = dbl ? dq_resident<double2>(1) : dq_resident<float2>(0);
+  if (resident <= 0) return cudaErrorInvalidDevice;
+  const unsigned grid = (unsigned)std::min<int64_t>(total_blocks, resident);
+  if (dbl)
+    direct_queue_kernel<double2><<<grid, 256, 0, s>>>(steps, n_steps, total_blocks, cbase, abase, ctrl, err);
+  else
+    direct_queue_kernel<float2><<<grid, 256, 0, s>>>(steps, n_steps, total_blocks, cbase, abase, ctrl, err);
+  return cudaGetLastError();
+}
+
+cudaError_t direct_queue_set_wait_limit(unsigned long long ns) {
+  const unsigned long long v = ns ? ns : kQueueWaitNs;
+  return cudaMemcpyToSymbol(g_dq_wait_ns, &v, sizeof(v));
+}
+
+cudaError_t direct_queue_set_stall(int on) {
+  const int v = on ? 1 : 0;
+  return cudaMemcpyToSymbol(g_dq_stall, &v, sizeof(v));
 }
 
 // acc[row][o] += scale * root[beta, o] in FP64 for the current chunk (o the

@@ -21,8 +21,9 @@ struct GroupState {
   int64_t lo, hi;        // slice range
   int64_t n_rows;        // bitstrings in the call
   int64_t groups_done;
-  int tc_error;          // set by a tensor-core product whose bounded wait ran
-                         // out; cleared when a call starts
+  int tc_error;          // set by a tensor-core product or a direct-step queue
+                         // launch whose bounded wait ran out; cleared when a
+                         // call starts
   int pad0;
   int64_t pad[1];
 };
@@ -62,7 +63,10 @@ struct DStep {
   int64_t A, B, C;      // region-relative offsets
   int64_t block_begin;  // first block of this step within its launch
   int nC, nK, split;    // output bits, contracted bits, log2 threads per output
-  int pad0;
+  int nblk;             // blocks of this step
+  int dep[2];           // queue launches: the steps of the same launch (indices
+                        // from its first step) whose results A and B are, -1 none
+  int pad0, pad1;
   int8_t a_c[kMaxDirect], b_c[kMaxDirect];  // C bit -> A / B bit (-1 absent)
   int8_t a_k[kMaxDirect], b_k[kMaxDirect];  // K bit -> A / B bit
 };
@@ -111,6 +115,23 @@ cudaError_t launch_leaf_build(const LeafJob *jobs, int n_jobs, const GroupState 
                               int g, const char *cbase, char *abase, int dbl, cudaStream_t s);
 cudaError_t launch_direct(const DStep *steps, int n_steps, int64_t total_blocks, const char *cbase, char *abase,
                           int dbl, cudaStream_t s);
+// The same steps in one persistent launch over a device work queue: blocks
+// take the launch's blocks in order from a ticket counter, and a block whose
+// step reads the result of an earlier step of the same launch (DStep::dep)
+// first waits, bounded, until every block of that step has finished. So a
+// run of dependent levels needs one launch instead of one per level.
+// ctrl: direct_queue_ctrl_words(n_steps) zeroed words of device memory,
+// owned by the caller; the launch leaves them zeroed again when it ends. A
+// wait that runs out sets *err to 1 and stops the launch (the steps' results
+// are then invalid).
+cudaError_t launch_direct_queue(const DStep *steps, int n_steps, int64_t total_blocks, const char *cbase,
+                                char *abase, unsigned *ctrl, int *err, int dbl, cudaStream_t s);
+inline int64_t direct_queue_ctrl_words(int n_steps) { return 4 + (int64_t)n_steps; }
+// Test hooks for the current device: the limit of the queue's bounded waits
+// in ns (0 restores the default 2 s), and a switch that makes the first block
+// of every queue launch wait on a counter that nothing increments.
+cudaError_t direct_queue_set_wait_limit(unsigned long long ns);
+cudaError_t direct_queue_set_stall(int on);
 cudaError_t launch_permute(const float2 *in, float2 *out, const PermuteArgs &a, cudaStream_t s);
 cudaError_t launch_permute_z(const double2 *in, double2 *out, const PermuteArgs &a, cudaStream_t s);
 // complex128 products (FP64 FMA): tiled, skinny in place, long-k dot

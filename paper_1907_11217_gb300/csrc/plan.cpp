@@ -403,6 +403,67 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
     }
   }
 
+  // ------------------------------------------------- direct-step queues
+  // Each group's direct steps move to the earliest point where their inputs
+  // exist: right after the last product or permute whose result they read
+  // (through other direct steps, too). The direct steps that share such a
+  // point form one queue launch, in their level order, which is a
+  // topological order. A direct step only moves earlier, and a product reads
+  // a direct step's result at a later point than before, so every item
+  // still runs after its inputs.
+  if (p->opts.direct_levels == 0) {
+    std::vector<Item> &items = p->var_items;
+    std::vector<int> phase(p->T.size(), 0);  // point after which a tensor exists
+    std::vector<Item> bars;                  // the other items, in order
+    std::vector<std::vector<int>> at;        // direct steps per point
+    int v0 = -1;
+    for (const Item &it : items) {
+      if (it.kind == IT_DIRECT) {
+        for (int d = it.first; d < it.first + it.count; d++) {
+          if (v0 < 0) v0 = d;
+          const int a = p->dstep_tensors[3 * d], b = p->dstep_tensors[3 * d + 1], c = p->dstep_tensors[3 * d + 2];
+          const int ph = std::max(phase[a], phase[b]);
+          at[ph].push_back(d);
+          phase[c] = ph;
+        }
+        continue;
+      }
+      const int bi = (int)bars.size();
+      bars.push_back(it);
+      at.resize(bars.size());
+      if (it.kind == IT_PERMUTE) phase[it.b] = bi;
+      if (it.kind == IT_GEMM) {
+        const PStep &ps = p->S[it.a];
+        phase[ps.c_nat >= 0 ? ps.c_nat : ps.c] = bi;
+      }
+    }
+    if (v0 >= 0) {
+      std::vector<dev::DStep> nd(p->dsteps.begin(), p->dsteps.begin() + v0);
+      std::vector<int> nt(p->dstep_tensors.begin(), p->dstep_tensors.begin() + 3 * (size_t)v0);
+      std::vector<int> remap(p->dsteps.size(), -1);
+      std::vector<Item> out;
+      for (size_t bi = 0; bi < bars.size(); bi++) {
+        out.push_back(bars[bi]);
+        if (at[bi].empty()) continue;
+        Item q{IT_DIRECT};
+        q.queue = true;
+        q.first = (int)nd.size();
+        for (int d : at[bi]) {
+          remap[d] = (int)nd.size();
+          nd.push_back(p->dsteps[d]);
+          nt.insert(nt.end(), {p->dstep_tensors[3 * d], p->dstep_tensors[3 * d + 1], p->dstep_tensors[3 * d + 2]});
+        }
+        q.count = (int)nd.size() - q.first;
+        out.push_back(q);
+      }
+      for (PStep &ps : p->S)
+        if (ps.dstep >= v0) ps.dstep = remap[ps.dstep];
+      p->dsteps.swap(nd);
+      p->dstep_tensors.swap(nt);
+      items.swap(out);
+    }
+  }
+
   // ---------------------------------------------------------------- memory
   // lifetimes in item time; const tensors consumed by var work are persistent
   const int NT = (int)p->T.size();
@@ -538,24 +599,29 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
     int want = std::max(0, 12 - ds.nC);
     ds.split = std::min({ds.nK, want, 8});
   }
-  for (Item &it : p->var_items) {
-    if (it.kind != IT_DIRECT) continue;
-    int64_t b = 0;
-    for (int d = it.first; d < it.first + it.count; d++) {
-      p->dsteps[d].block_begin = b;
-      b += std::max<int64_t>(1, ((int64_t(1) << (p->dsteps[d].nC + p->dsteps[d].split)) + 255) / 256);
+  int64_t queue_words = 0;
+  for (std::vector<Item> *items : {&p->var_items, &p->const_items})
+    for (Item &it : *items) {
+      if (it.kind != IT_DIRECT) continue;
+      int64_t b = 0;
+      for (int d = it.first; d < it.first + it.count; d++) {
+        dev::DStep &ds = p->dsteps[d];
+        ds.block_begin = b;
+        ds.nblk = (int)std::max<int64_t>(1, ((int64_t(1) << (ds.nC + ds.split)) + 255) / 256);
+        ds.dep[0] = ds.dep[1] = -1;
+        b += ds.nblk;
+        if (!it.queue) continue;
+        // steps of the same launch whose results this step reads
+        for (int k = 0; k < 2; k++)
+          for (int e = it.first; e < d; e++)
+            if (p->dstep_tensors[3 * e + 2] == p->dstep_tensors[3 * d + k]) ds.dep[k] = e - it.first;
+      }
+      it.blocks = b;
+      if (it.queue) {
+        it.ctrl_off = queue_words * 4;
+        queue_words += dev::direct_queue_ctrl_words(it.count);
+      }
     }
-    it.blocks = b;
-  }
-  for (Item &it : p->const_items) {
-    if (it.kind != IT_DIRECT) continue;
-    int64_t b = 0;
-    for (int d = it.first; d < it.first + it.count; d++) {
-      p->dsteps[d].block_begin = b;
-      b += std::max<int64_t>(1, ((int64_t(1) << (p->dsteps[d].nC + p->dsteps[d].split)) + 255) / 256);
-    }
-    it.blocks = b;
-  }
   // leaf jobs
   for (int l = 0; l < L; l++) {
     if (!p->T[l].var) continue;
@@ -623,6 +689,9 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
   so = align256(so + (size_t)p->max_rows * net.n_qubits);
   p->s_acc = so;
   so = align256(so + ((size_t)p->max_rows * 16 << net.n_open));
+  p->s_queue = so;
+  p->queue_bytes = (size_t)queue_words * 4;
+  so = align256(so + p->queue_bytes);
   p->s_arena = so;
   p->arena_bytes = (size_t)std::max(arena_peak, arena_const_peak);
   so = align256(so + p->arena_bytes);
@@ -721,9 +790,14 @@ std::string plan_describe(const tz_plan *p) {
     o << "[";
     for (size_t i = 0; i < v.size(); i++)
       o << (i ? "," : "") << "[" << v[i].kind << "," << v[i].a << "," << v[i].b << "," << v[i].first << ","
-        << v[i].count << "," << v[i].blocks << "]";
+        << v[i].count << "," << v[i].blocks << "," << (v[i].queue ? 1 : 0) << "]";
     o << "]";
   };
+  o << "],\"dsteps\":[";
+  for (size_t d = 0; d < p->dsteps.size(); d++)
+    o << (d ? "," : "") << "[" << p->dstep_tensors[3 * d] << "," << p->dstep_tensors[3 * d + 1] << ","
+      << p->dstep_tensors[3 * d + 2] << "," << p->dsteps[d].nblk << "," << p->dsteps[d].dep[0] << ","
+      << p->dsteps[d].dep[1] << "]";
   o << "],\"var_items\":";
   items(p->var_items);
   o << ",\"const_items\":";
@@ -871,9 +945,16 @@ static void run_items(tz_plan *p, const std::vector<Item> &items, const RunCtx &
                      "leaf build");
         break;
       case IT_DIRECT:
-        cuda_check(dev::launch_direct(reinterpret_cast<const dev::DStep *>(p->ws + p->off_dsteps) + it.first,
-                                      it.count, it.blocks, cbase, abase, p->esz == 16, s),
-                   "direct steps");
+        if (it.queue)
+          cuda_check(dev::launch_direct_queue(reinterpret_cast<const dev::DStep *>(p->ws + p->off_dsteps) + it.first,
+                                              it.count, it.blocks, cbase, abase,
+                                              reinterpret_cast<unsigned *>(ctx.scratch + p->s_queue + it.ctrl_off),
+                                              &gs->tc_error, p->esz == 16, s),
+                     "direct step queue");
+        else
+          cuda_check(dev::launch_direct(reinterpret_cast<const dev::DStep *>(p->ws + p->off_dsteps) + it.first,
+                                        it.count, it.blocks, cbase, abase, p->esz == 16, s),
+                     "direct steps");
         break;
       case IT_PERMUTE: {
         dev::PermuteArgs a{};
@@ -1181,6 +1262,10 @@ void plan_run(tz_plan *p, const RunCtx &ctx, int64_t n_rows, int64_t lo, int64_t
   if (fresh)
     cuda_check(cudaMemsetAsync(ctx.scratch + p->s_acc, 0, (size_t)n_rows * 16 << p->net.n_open, s),
                "clear accumulator");
+  // queue launches leave their counters zeroed; this covers a scratch part
+  // the plan has not run on before
+  if (p->queue_bytes)
+    cuda_check(cudaMemsetAsync(ctx.scratch + p->s_queue, 0, p->queue_bytes, s), "clear queue counters");
   cuda_check(dev::launch_init_state(gs, lo, hi, n_rows, s, fresh ? 0 : 1), "init group state");
   const int64_t chunk = int64_t(1) << p->net.batch_log2;
   const int64_t n_chunks = (n_rows + chunk - 1) / chunk;

@@ -50,6 +50,8 @@ struct Item {
   int a = -1, b = -1;         // PERMUTE: src, dst tensors; GEMM: step
   int first = 0, count = 0;   // DIRECT: dsteps range
   int64_t blocks = 0;         // DIRECT: total blocks
+  bool queue = false;         // DIRECT: one queue launch over dependent steps
+  int64_t ctrl_off = -1;      // DIRECT queue: its counters in the scratch part's queue area
 };
 
 }  // namespace tz
@@ -76,6 +78,7 @@ struct tz_plan {
   // accumulator | group arena]; a query can also run in another scratch part
   size_t off_dsteps = 0, off_jobs = 0, off_const = 0, off_scratch = 0;
   size_t s_gs = 0, s_bits = 0, s_acc = 0, s_arena = 0;  // offsets within a scratch part
+  size_t s_queue = 0, queue_bytes = 0;  // counters of the direct-step queue launches
   size_t const_bytes = 0, arena_bytes = 0, resident_bytes = 0, scratch_bytes = 0, total_bytes = 0;
   // device state
   char *ws = nullptr;

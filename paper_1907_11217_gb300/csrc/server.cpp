@@ -203,7 +203,7 @@ struct tz_server {
       const size_t n_out = (size_t)q.n << q.plan->net.n_open;
       std::memcpy(&tc_error, sl.pin_out + 2 * n_out, sizeof(int));
       if (tc_error) {
-        fail_query(q, TZ_ETIMEOUT, "a tensor-core product of this query timed out in a bounded wait");
+        fail_query(q, TZ_ETIMEOUT, "a bounded wait (tensor-core product or direct-step queue) of this query ran out");
         continue;
       }
       q.out.assign(sl.pin_out, sl.pin_out + 2 * n_out);

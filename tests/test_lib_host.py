@@ -1,6 +1,7 @@
 """Host-side checks of the library (no GPU): the C ABI loads and exports
 every declared symbol, the C++ circuit generator matches the seeded input
 generator, and the network/tree/slicing/plan logic keeps its invariants."""
+import json
 import os
 import re
 
@@ -324,3 +325,65 @@ def test_open_output_qubits_rejected(tz):
     for bad in [(9,), (-1,), (2, 2), tuple(range(9)), tuple(range(13))]:
         with pytest.raises(tz.TzError):
             tz.tz_network_from_circuit(c, 0, bad)
+
+
+def _producers(desc):
+    """Item index producing each tensor of a plan's group (None: exists
+    before the group starts: constants and bind-time results)."""
+    prod = {}
+    for i, it in enumerate(desc["var_items"]):
+        kind = it[0]
+        if kind == 0:
+            for t in desc["tensors"]:
+                if t["var"] and t["leaf"] >= 0 and not t["full"]:
+                    prod[t["id"]] = (i, -1)
+        elif kind == 1:
+            for d in range(it[3], it[3] + it[4]):
+                prod[desc["dsteps"][d][2]] = (i, d)
+        elif kind == 2:
+            prod[it[2]] = (i, -1)
+        elif kind == 3:
+            st = desc["steps"][it[1]]
+            prod[st["c_nat"] if st["c_nat"] >= 0 else st["c"]] = (i, -1)
+    return prod
+
+
+@pytest.mark.parametrize("rows,cols,t,seed,small,prec", [
+    (4, 5, 16, 4, 10, "c64"), (5, 5, 14, 2, 8, "fp16x3"), (7, 7, 16, 5, 12, "fp16x3"), (4, 4, 20, 6, 20, "c64")])
+def test_direct_queue_schedule(tz, rows, cols, t, seed, small, prec):
+    """Queue launches (the default): every direct step runs after the items
+    whose results it reads, or, inside its queue launch, after the steps it
+    waits for (dep = their index in the launch); each product and permute
+    still runs after its inputs; blocks add up; the launch count per group
+    is at most that of one launch per dependency level, over the same steps."""
+    spec = ti.circuit_to_spec(rows * cols, ti.generate_circuit(ti.grid(rows, cols), t, seed))
+    net = tz.tz_network_from_circuit(tz.tz_circuit_from_spec(spec), 2)
+    tree = tz.tz_path_greedy(net, restarts=4, seed=1, precision=prec)
+    descs, stats = {}, {}
+    for levels in (0, 1):
+        plan = tz.tz_plan_create(net, tree, [], precision=prec, small_log2=small, direct_levels=levels)
+        descs[levels], stats[levels] = json.loads(plan.describe()), plan.stats()
+    q, lv = descs[0], descs[1]
+    assert stats[0]["n_launches_per_group"] <= stats[1]["n_launches_per_group"]
+    directs = [it for it in q["var_items"] if it[0] == 1]
+    assert directs and all(it[6] == 1 for it in directs)
+    assert all(it[6] == 0 for it in lv["var_items"] if it[0] == 1)
+    assert sorted(tuple(d[:3]) for d in q["dsteps"]) == sorted(tuple(d[:3]) for d in lv["dsteps"])
+    prod = _producers(q)
+    for i, it in enumerate(q["var_items"]):
+        if it[0] == 1:
+            assert it[5] == sum(q["dsteps"][d][3] for d in range(it[3], it[3] + it[4]))
+            for d in range(it[3], it[3] + it[4]):
+                a, b, c, nblk, dep0, dep1 = q["dsteps"][d]
+                for x, dep in ((a, dep0), (b, dep1)):
+                    pi, pd = prod.get(x, (None, -1))
+                    if pi == i:          # made in this launch: wait for it
+                        assert it[3] <= pd < d and dep == pd - it[3]
+                    else:
+                        assert dep == -1 and (pi is None or pi < i)
+        elif it[0] in (2, 3):
+            st = q["steps"][it[1]] if it[0] == 3 else None
+            ins = [it[1]] if it[0] == 2 else [st["opX"], st["opY"]]
+            for x in ins:
+                pi, _ = prod.get(x, (None, -1))
+                assert pi is None or pi < i
