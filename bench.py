@@ -90,9 +90,9 @@ def parse():
     ap.add_argument("--autotune", type=int, default=1,
                     help="1: time each tensor-core step's launch choices when the plan is bound (untimed "
                          "preprocessing) and keep the fastest; 0: built-in defaults")
-    ap.add_argument("--direct-levels", type=int, default=0,
-                    help="0: each run of small direct steps between products is one persistent queue launch; "
-                         "1: one launch per dependency level")
+    ap.add_argument("--direct-queue", type=int, default=0,
+                    help="1: each run of small direct steps between products is one persistent queue launch; "
+                         "0: one launch per dependency level (measured no slower)")
     ap.add_argument("--compare-direct", type=int, default=0,
                     help="rounds of an interleaved comparison with the other direct-step launch form (same "
                          "tree, same autotuned products, same slice windows; 0: off)")
@@ -138,7 +138,7 @@ def build_plan(tz, spec, args, precision, stream, device, log2_max, max_rows=0):
         sliced = tz.tz_slice_select(net, tree, log2_max, 40) if log2_max > 0 else []
     plan = tz.tz_plan_create(net, tree, sliced, precision=precision, device=device, stream=stream, use_graph=True,
                              max_bitstrings=max_rows or args.bitstrings or 1 << max(args.batch_log2, 0),
-                             autotune=bool(args.autotune), direct_levels=bool(args.direct_levels))
+                             autotune=bool(args.autotune), direct_queue=bool(args.direct_queue))
     prep_s = time.perf_counter() - t0
     return plan, sliced, prep_s
 
@@ -601,6 +601,8 @@ def main():
     # (the default tree has none) they are replicas instead: each contracts
     # whole amplitudes of its own bitstrings, and nothing is reduced
     replicas = dist and n_slices < world
+    from paper_1907_11217_gb300 import shard
+
     # slices per step: ~3 s of estimated work (a fixed 2^12 when that is smaller), at least 1
     S = args.slices
     if S <= 0:
@@ -611,9 +613,8 @@ def main():
         stream.synchronize()
         one = time.perf_counter() - t0
         S = int(max(1, min(4096, n_slices // (1 if replicas else world), 3.0 / max(one, 1e-6))))
-    S = min(S, max(1, n_slices // (1 if replicas else world)))
-
-    from paper_1907_11217_gb300 import shard
+    # a power of two that divides the slice range: every step's window is whole
+    S = shard.window_size(n_slices, 1 if replicas else world, S)
 
     def slice_range(step):
         if replicas:
@@ -686,7 +687,7 @@ def main():
     # make the products identical), so that drifts in clock and power hit both
     direct_compare = None
     if args.compare_direct > 0 and world == 1:
-        p3, _, _ = build_plan(tz, spec, argparse.Namespace(**{**vars(args), "direct_levels": 1 - args.direct_levels}),
+        p3, _, _ = build_plan(tz, spec, argparse.Namespace(**{**vars(args), "direct_queue": 1 - args.direct_queue}),
                               precision, stream, device, log2_max)
         p3.bind()
         t_one, t_other = [], []
@@ -702,7 +703,7 @@ def main():
                 e1.record(stream)
                 torch.cuda.synchronize()
                 acc.append(e0.elapsed_time(e1) / (hi - lo))
-        names = ("per dependency level", "queue") if args.direct_levels else ("queue", "per dependency level")
+        names = ("queue", "per dependency level") if args.direct_queue else ("per dependency level", "queue")
         direct_compare = {"ms_per_slice": {names[0]: statistics.median(t_one), names[1]: statistics.median(t_other)},
                           "launches_per_slice": {names[0]: st["n_launches_per_group"],
                                                  names[1]: p3.stats()["n_launches_per_group"]},
@@ -777,7 +778,7 @@ def main():
                  "workspace_gb": st["workspace_bytes"] / 1e9,
                  "const_steps": st["n_const_steps"], "const_flops": st["const_flops"],
                  "bind_ms": plan_bind_ms, "autotuned_steps": n_tuned,
-                 "direct_launch": "per dependency level" if args.direct_levels else "queue"},
+                 "direct_launch": "queue" if args.direct_queue else "per dependency level"},
         "e2e": {"value": e2e_s, "unit": "s/amplitude", "h2d_bytes_per_step": int(bits.nbytes),
                 "d2h_bytes_per_step": 16 * A},
         "roofline": rl,

@@ -259,10 +259,10 @@ class Plan(_Handle):
 
 
 def tz_plan_create(net: Network, tree: Tree, sliced=(), precision="c64", device=0, stream=None, small_log2=0,
-                   use_graph=False, max_bitstrings=0, autotune=False, direct_levels=False) -> Plan:
+                   use_graph=False, max_bitstrings=0, autotune=False, direct_queue=False) -> Plan:
     arr = np.ascontiguousarray(np.asarray(list(sliced), dtype=np.int32))
     o = tz_plan_opts(PRECISIONS.get(precision, precision), device, _stream(stream), small_log2, int(use_graph),
-                     max_bitstrings, int(autotune), int(direct_levels))
+                     max_bitstrings, int(autotune), int(direct_queue))
     h = ctypes.c_void_p()
     ptr = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if len(arr) else None
     check(lib().tz_plan_create(net.handle, tree.handle, ptr, len(arr), ctypes.byref(o), ctypes.byref(h)))

@@ -41,7 +41,7 @@ class tz_path_opts(ctypes.Structure):
 class tz_plan_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("device", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("small_log2", ctypes.c_int), ("use_graph", ctypes.c_int), ("max_bitstrings", ctypes.c_int64),
-                ("autotune", ctypes.c_int), ("direct_levels", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("direct_queue", ctypes.c_int)]
 
 
 class tz_plan_stats(ctypes.Structure):

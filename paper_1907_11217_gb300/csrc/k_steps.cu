@@ -101,18 +101,8 @@ cudaError_t launch_leaf_build(const LeafJob *jobs, int n_jobs, const GroupState 
 // Direct contraction of small steps. Each output element is summed by
 // 2^split consecutive threads, each walking its share of the contracted bits
 // in Gray-code order (one offset update per term), then reduced. blk is the
-// block's number within its step. kCG reads the operands through L2 only
-// (ld.global.cg): in a queue launch they may have been written by other
-// blocks of the same launch, after this SM last cached those addresses.
-template <typename T, bool kCG>
-__device__ __forceinline__ T load_op(const T *p) {
-  if constexpr (kCG)
-    return __ldcg(p);
-  else
-    return *p;
-}
-
-template <typename T, bool kCG>
+// block's number within its step.
+template <typename T>
 __device__ __forceinline__ void direct_block(const DStep &st, int64_t blk, const char *cbase, char *abase, T *red) {
   const T *__restrict__ Ap = region_ptr<T>(st.A, cbase, abase);
   const T *__restrict__ Bp = region_ptr<T>(st.B, cbase, abase);
@@ -136,7 +126,7 @@ __device__ __forceinline__ void direct_block(const DStep &st, int64_t blk, const
         oa += int64_t(1) << st.a_k[nlow + q];
         ob += int64_t(1) << st.b_k[nlow + q];
       }
-    acc = cmul(load_op<T, kCG>(Ap + oa), load_op<T, kCG>(Bp + ob));
+    acc = cmul(Ap[oa], Bp[ob]);
     const int64_t nt = int64_t(1) << nlow;
     for (int64_t t = 1; t < nt; t++) {
       const int q = __ffsll(t) - 1;
@@ -144,7 +134,7 @@ __device__ __forceinline__ void direct_block(const DStep &st, int64_t blk, const
       const int64_t da = int64_t(1) << st.a_k[q], db = int64_t(1) << st.b_k[q];
       oa += on ? da : -da;
       ob += on ? db : -db;
-      acc = cfma(load_op<T, kCG>(Ap + oa), load_op<T, kCG>(Bp + ob), acc);
+      acc = cfma(Ap[oa], Bp[ob], acc);
     }
   }
   if (split > 0) {
@@ -184,7 +174,7 @@ __global__ void __launch_bounds__(256) direct_kernel(const DStep *steps, int n_s
   if (threadIdx.x == 0) s_idx = step_of_block(steps, n_steps, blk);
   __syncthreads();
   const DStep &st = steps[s_idx];
-  direct_block<T, false>(st, blk - st.block_begin, cbase, abase, red);
+  direct_block<T>(st, blk - st.block_begin, cbase, abase, red);
 }
 
 cudaError_t launch_direct(const DStep *steps, int n_steps, int64_t total_blocks, const char *cbase, char *abase,
@@ -208,7 +198,17 @@ cudaError_t launch_direct(const DStep *steps, int n_steps, int64_t total_blocks,
 // (DStep::dep < own index, tickets in block order). A block holding a
 // ticket is resident, so the lowest unfinished ticket always has all of its
 // inputs done and runs to the end; no wait can close a cycle, whatever the
-// grid size. Every wait is still bounded.
+// grid size. Every wait is still bounded. Block b's first ticket is b itself
+// (no atomic); later tickets come from ctrl[0], which starts at the grid size.
+//
+// Visibility: a producer block's threads write their results, meet at a
+// barrier, and one thread fences and counts the block done; a consumer's
+// waiting thread reads the count with acquire semantics at GPU scope before
+// its block's barrier, so the block's plain loads that follow see the
+// results (the acquire also keeps the SM's L1 from serving older copies).
+// Results of one launch never share a 128-byte line with anything else read
+// in it: the tensors of a queue launch all live through the whole launch, so
+// none reuses another's memory, and every tensor starts on 256 bytes.
 constexpr unsigned long long kQueueWaitNs = 2000000000ull;  // 2 s (default)
 __device__ unsigned long long g_dq_wait_ns = kQueueWaitNs;
 __device__ int g_dq_stall;
@@ -226,44 +226,50 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
 
 // Wait until *cnt >= target: 1 when it is, 0 when the launch was stopped or
 // the wait ran out (then the error word and the stop flag are set).
-__device__ bool dq_wait(const unsigned *cnt, unsigned target, unsigned *stop, int *err,
-                        unsigned long long limit) {
+__device__ __forceinline__ bool dq_wait(const unsigned *cnt, unsigned target, unsigned *stop, int *err,
+                                        unsigned long long limit) {
+  if (ld_acquire(cnt) >= target) return true;
   const unsigned long long t0 = dq_globaltimer();
-  for (unsigned polls = 0;; polls++) {
+  for (unsigned polls = 1;; polls++) {
     if (ld_acquire(cnt) >= target) return true;
-    if (ld_acquire(stop)) return false;
-    if ((polls & 15) == 15) {
+    if ((polls & 15) == 0) {
+      if (ld_acquire(stop)) return false;
       if (dq_globaltimer() - t0 > limit) {
         atomicExch(err, 1);
         atomicExch(stop, 1u);
         return false;
       }
-      __nanosleep(64);
+      if (polls >= 256) __nanosleep(32);
     }
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) direct_queue_kernel(const DStep *steps, int n_steps, int64_t total,
-                                                           const char *cbase, char *abase, unsigned *ctrl,
-                                                           int *err) {
+__global__ void __launch_bounds__(256) direct_queue_kernel(const DStep *steps, int n_steps, const int *bmap,
+                                                           int64_t total, const char *cbase, char *abase,
+                                                           unsigned *ctrl, int *err) {
   __shared__ int s_idx, s_go, s_last;
   __shared__ int64_t s_blk;
   __shared__ T red[256];
   unsigned *done = ctrl + 4;
   const unsigned long long limit = g_dq_wait_ns;
+  // thread 0 takes the block's next ticket as soon as it has passed the
+  // waits of the current one, so the atomic's latency hides behind the
+  // block's work (a block holds at most one ticket it has not started, and
+  // every ticket below it is finished or running: progress is unchanged)
+  int64_t t_next = blockIdx.x;
   for (;;) {
     if (threadIdx.x == 0) {
-      const int64_t t = atomicAdd(&ctrl[0], 1u);
+      const int64_t t = t_next;
       int go = t < total;
       int idx = 0;
       if (go) {
-        idx = step_of_block(steps, n_steps, t);
+        idx = bmap[t];
         if (g_dq_stall && t == 0) go = dq_wait(&ctrl[3], 1u, &ctrl[2], err, limit);
-        for (int k = 0; k < 2 && go; k++) {
-          const int d = steps[idx].dep[k];
-          if (d >= 0) go = dq_wait(&done[d], (unsigned)steps[d].nblk, &ctrl[2], err, limit);
-        }
+        const int4 dp = *reinterpret_cast<const int4 *>(steps[idx].dep);  // dep[2], dep_nblk[2]
+        if (go && dp.x >= 0) go = dq_wait(&done[dp.x], (unsigned)dp.z, &ctrl[2], err, limit);
+        if (go && dp.y >= 0) go = dq_wait(&done[dp.y], (unsigned)dp.w, &ctrl[2], err, limit);
+        if (go) t_next = (int64_t)gridDim.x + atomicAdd(&ctrl[0], 1u);
       }
       s_idx = idx;
       s_blk = t;
@@ -272,7 +278,7 @@ __global__ void __launch_bounds__(256) direct_queue_kernel(const DStep *steps, i
     __syncthreads();
     if (!s_go) break;
     const DStep &st = steps[s_idx];
-    direct_block<T, true>(st, s_blk - st.block_begin, cbase, abase, red);
+    direct_block<T>(st, s_blk - st.block_begin, cbase, abase, red);
     __syncthreads();  // every result of this block is written
     if (threadIdx.x == 0) {
       __threadfence();
@@ -321,17 +327,17 @@ static int dq_resident(int dbl) {
   return r;
 }
 
-cudaError_t launch_direct_queue(const DStep *steps, int n_steps, int64_t total_blocks, const char *cbase,
-                                char *abase, unsigned *ctrl, int *err, int dbl, cudaStream_t s) {
+cudaError_t launch_direct_queue(const DStep *steps, int n_steps, const int *bmap, int64_t total_blocks,
+                                const char *cbase, char *abase, unsigned *ctrl, int *err, int dbl, cudaStream_t s) {
   if (n_steps <= 0) return cudaSuccess;
-  if (total_blocks > 0x7fffffffLL || !ctrl || !err) return cudaErrorInvalidValue;
+  if (total_blocks > 0x7fffffffLL || !ctrl || !err || !bmap) return cudaErrorInvalidValue;
   const int resident = dbl ? dq_resident<double2>(1) : dq_resident<float2>(0);
   if (resident <= 0) return cudaErrorInvalidDevice;
   const unsigned grid = (unsigned)std::min<int64_t>(total_blocks, resident);
   if (dbl)
-    direct_queue_kernel<double2><<<grid, 256, 0, s>>>(steps, n_steps, total_blocks, cbase, abase, ctrl, err);
+    direct_queue_kernel<double2><<<grid, 256, 0, s>>>(steps, n_steps, bmap, total_blocks, cbase, abase, ctrl, err);
   else
-    direct_queue_kernel<float2><<<grid, 256, 0, s>>>(steps, n_steps, total_blocks, cbase, abase, ctrl, err);
+    direct_queue_kernel<float2><<<grid, 256, 0, s>>>(steps, n_steps, bmap, total_blocks, cbase, abase, ctrl, err);
   return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // Device-side descriptors and kernel launchers (host-callable).
 #pragma once
 #include <cuda_runtime.h>
+#include <cstddef>
 #include <cstdint>
 
 #include "tz.h"
@@ -66,10 +67,13 @@ struct DStep {
   int nblk;             // blocks of this step
   int dep[2];           // queue launches: the steps of the same launch (indices
                         // from its first step) whose results A and B are, -1 none
-  int pad0, pad1;
+  int dep_nblk[2];      // the blocks of those steps
   int8_t a_c[kMaxDirect], b_c[kMaxDirect];  // C bit -> A / B bit (-1 absent)
   int8_t a_k[kMaxDirect], b_k[kMaxDirect];  // K bit -> A / B bit
 };
+
+static_assert(offsetof(DStep, dep) % 16 == 0 && sizeof(DStep) % 16 == 0,
+              "the queue kernel reads dep and dep_nblk with one 16-byte load");
 
 // Where a GEMM writes its result: canonical element (z, m, n) of the
 // row-major [batch][m][n] product goes to offset Sb(z) + Sm(m) + Sn(n),
@@ -124,8 +128,9 @@ cudaError_t launch_direct(const DStep *steps, int n_steps, int64_t total_blocks,
 // owned by the caller; the launch leaves them zeroed again when it ends. A
 // wait that runs out sets *err to 1 and stops the launch (the steps' results
 // are then invalid).
-cudaError_t launch_direct_queue(const DStep *steps, int n_steps, int64_t total_blocks, const char *cbase,
-                                char *abase, unsigned *ctrl, int *err, int dbl, cudaStream_t s);
+// bmap: the step (index from the launch's first) of each of its blocks.
+cudaError_t launch_direct_queue(const DStep *steps, int n_steps, const int *bmap, int64_t total_blocks,
+                                const char *cbase, char *abase, unsigned *ctrl, int *err, int dbl, cudaStream_t s);
 inline int64_t direct_queue_ctrl_words(int n_steps) { return 4 + (int64_t)n_steps; }
 // Test hooks for the current device: the limit of the queue's bounded waits
 // in ns (0 restores the default 2 s), and a switch that makes the first block

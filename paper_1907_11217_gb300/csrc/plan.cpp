@@ -411,7 +411,7 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
   // topological order. A direct step only moves earlier, and a product reads
   // a direct step's result at a later point than before, so every item
   // still runs after its inputs.
-  if (p->opts.direct_levels == 0) {
+  if (p->opts.direct_queue) {
     std::vector<Item> &items = p->var_items;
     std::vector<int> phase(p->T.size(), 0);  // point after which a tensor exists
     std::vector<Item> bars;                  // the other items, in order
@@ -609,17 +609,24 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
         ds.block_begin = b;
         ds.nblk = (int)std::max<int64_t>(1, ((int64_t(1) << (ds.nC + ds.split)) + 255) / 256);
         ds.dep[0] = ds.dep[1] = -1;
+        ds.dep_nblk[0] = ds.dep_nblk[1] = 0;
         b += ds.nblk;
         if (!it.queue) continue;
         // steps of the same launch whose results this step reads
         for (int k = 0; k < 2; k++)
           for (int e = it.first; e < d; e++)
-            if (p->dstep_tensors[3 * e + 2] == p->dstep_tensors[3 * d + k]) ds.dep[k] = e - it.first;
+            if (p->dstep_tensors[3 * e + 2] == p->dstep_tensors[3 * d + k]) {
+              ds.dep[k] = e - it.first;
+              ds.dep_nblk[k] = p->dsteps[e].nblk;
+            }
       }
       it.blocks = b;
       if (it.queue) {
         it.ctrl_off = queue_words * 4;
         queue_words += dev::direct_queue_ctrl_words(it.count);
+        it.bmap_off = (int64_t)p->bmap.size() * 4;
+        for (int d = it.first; d < it.first + it.count; d++)
+          p->bmap.insert(p->bmap.end(), (size_t)p->dsteps[d].nblk, d - it.first);
       }
     }
   // leaf jobs
@@ -677,6 +684,8 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
   off = align256(off + sizeof(dev::DStep) * std::max<size_t>(1, p->dsteps.size()));
   p->off_jobs = off;
   off = align256(off + sizeof(dev::LeafJob) * std::max<size_t>(1, p->jobs.size()));
+  p->off_bmap = off;
+  off = align256(off + sizeof(int32_t) * p->bmap.size());
   p->off_const = off;
   p->const_bytes = (size_t)const_peak;
   off = align256(off + p->const_bytes);
@@ -947,7 +956,9 @@ static void run_items(tz_plan *p, const std::vector<Item> &items, const RunCtx &
       case IT_DIRECT:
         if (it.queue)
           cuda_check(dev::launch_direct_queue(reinterpret_cast<const dev::DStep *>(p->ws + p->off_dsteps) + it.first,
-                                              it.count, it.blocks, cbase, abase,
+                                              it.count,
+                                              reinterpret_cast<const int *>(p->ws + p->off_bmap + it.bmap_off),
+                                              it.blocks, cbase, abase,
                                               reinterpret_cast<unsigned *>(ctx.scratch + p->s_queue + it.ctrl_off),
                                               &gs->tc_error, p->esz == 16, s),
                      "direct step queue");
@@ -1208,6 +1219,10 @@ void plan_bind(tz_plan *p, void *ws, size_t bytes) {
     cuda_check(cudaMemcpyAsync(p->ws + p->off_jobs, js.data(), js.size() * sizeof(dev::LeafJob),
                                cudaMemcpyHostToDevice, s),
                "upload leaf tables");
+  if (!p->bmap.empty())
+    cuda_check(cudaMemcpyAsync(p->ws + p->off_bmap, p->bmap.data(), p->bmap.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, s),
+               "upload queue block maps");
   // constant leaves, in their planned storage order
   std::vector<float2> host;
   std::vector<double2> hostz;

@@ -17,14 +17,28 @@ def partition(n_slices: int, world: int, rank: int):
     return lo, lo + base + (1 if rank < extra else 0)
 
 
+def window_size(n_slices: int, world: int, target: int):
+    """Slices per rank and step: the largest power of two <= target (at
+    least 1) that lets every rank take a whole window of its own. Slice
+    counts are powers of two (2^k), so such windows tile the slice range and
+    no step is ever cut short at its end."""
+    per = max(1, min(int(target), max(1, n_slices // max(world, 1))))
+    return 1 << (per.bit_length() - 1)
+
+
 def step_window(n_slices: int, world: int, rank: int, per_rank: int, step: int):
     """Slices [lo, hi) a rank contracts in one timed step when every rank
     takes `per_rank` consecutive slices and successive steps move on through
-    the range (wrapping)."""
+    the range (wrapping). A window always holds min(per_rank, n_slices)
+    slices: one that would run past the end of the range is moved back to
+    end there (with window_size's windows that never happens)."""
     if per_rank < 1:
         raise ValueError("per_rank must be >= 1")
-    lo = ((step * world + rank) * per_rank) % max(n_slices, 1)
-    return lo, min(n_slices, lo + per_rank)
+    n = max(n_slices, 1)
+    per = min(per_rank, n)
+    lo = ((step * world + rank) * per) % n
+    lo = min(lo, n - per)
+    return lo, lo + per
 
 
 def reduce_partials(t):

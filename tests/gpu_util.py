@@ -20,7 +20,7 @@ def rel_err(got, ref, n_qubits):
 
 def make_plan(tz, spec, batch_log2=0, log2_max=0, precision="c64", small_log2=0, restarts=4, seed=1,
               use_graph=False, stream=None, k_max=8, max_bitstrings=0, slice_bits=0, open_qubits=(),
-              direct_levels=False):
+              direct_queue=False):
     """log2_max > 0: slice down to that size; slice_bits > 0: slice until the
     largest intermediate is slice_bits below the unsliced one."""
     c = tz.tz_circuit_from_spec(spec)
@@ -31,7 +31,7 @@ def make_plan(tz, spec, batch_log2=0, log2_max=0, precision="c64", small_log2=0,
         log2_max = full - slice_bits
     sl = tz.tz_slice_select(net, tree, log2_max, k_max) if log2_max > 0 else []
     plan = tz.tz_plan_create(net, tree, sl, precision=precision, small_log2=small_log2, use_graph=use_graph,
-                             stream=stream, max_bitstrings=max_bitstrings, direct_levels=direct_levels)
+                             stream=stream, max_bitstrings=max_bitstrings, direct_queue=direct_queue)
     plan.bind()
     return plan, net, tree, sl
 

@@ -1,7 +1,7 @@
-"""The direct-step queue launch on the GPU (C ABI): every run of small
-direct steps between two products is one persistent launch whose blocks
-take work from a device ticket counter and wait, bounded, for the steps they
-read. It must give bit-identical amplitudes to one launch per dependency
+"""The direct-step queue launch on the GPU (C ABI; tz_plan_opts.direct_queue):
+every run of small direct steps between two products is one persistent
+launch whose blocks take work from a device ticket counter and wait,
+bounded, for the steps they read. It must give bit-identical amplitudes to one launch per dependency
 level (the per-element arithmetic is the same), match the FP64 oracle, leave
 its counters ready for the next launch (many groups replayed from one
 captured graph, several calls in a row), and report a wait that runs out as
@@ -47,7 +47,7 @@ def test_queue_matches_levels_and_statevector(tz, rows, cols, t, seed, cut, g, s
     got = {}
     for levels in (False, True):
         plan, *_ = make_plan(tz, spec, batch_log2=g, slice_bits=cut, small_log2=small, precision=prec,
-                             use_graph=graph, direct_levels=levels, max_bitstrings=32)
+                             use_graph=graph, direct_queue=not levels, max_bitstrings=32)
         items = _queue_items(plan)
         assert items and all(it[6] == (0 if levels else 1) for it in items)
         # two calls in a row: the counters are left ready for the next launch
@@ -69,7 +69,7 @@ def test_queue_fewer_launches_same_result_7x7(tz):
     res, launches = {}, {}
     for levels in (False, True):
         plan, *_ = make_plan(tz, spec, batch_log2=6, small_log2=12, precision="fp16x3", use_graph=True,
-                             direct_levels=levels, max_bitstrings=64, restarts=8)
+                             direct_queue=not levels, max_bitstrings=64, restarts=8)
         launches[levels] = plan.stats()["n_launches_per_group"]
         res[levels] = tz.tz_contract_amplitudes(plan, bits)
         plan.close()
@@ -85,7 +85,8 @@ def test_queue_timeout_reports_then_recovers(tz, graph):
     from paper_1907_11217_gb300._lib import TZ_ETIMEOUT
     spec = grid_spec(4, 5, 16, 4)
     bits = ti.random_bitstrings(20, 8, 5)
-    plan, *_ = make_plan(tz, spec, batch_log2=1, slice_bits=3, small_log2=10, use_graph=graph, max_bitstrings=8)
+    plan, *_ = make_plan(tz, spec, batch_log2=1, slice_bits=3, small_log2=10, use_graph=graph, max_bitstrings=8,
+                         direct_queue=True)
     ref = sv.amplitudes(spec, bits)
     ok = tz.tz_contract_amplitudes(plan, bits)     # captures the graph before the stall
     assert rel_err(ok, ref, 20) <= TOL["c64"]

@@ -351,7 +351,7 @@ def _producers(desc):
 @pytest.mark.parametrize("rows,cols,t,seed,small,prec", [
     (4, 5, 16, 4, 10, "c64"), (5, 5, 14, 2, 8, "fp16x3"), (7, 7, 16, 5, 12, "fp16x3"), (4, 4, 20, 6, 20, "c64")])
 def test_direct_queue_schedule(tz, rows, cols, t, seed, small, prec):
-    """Queue launches (the default): every direct step runs after the items
+    """Queue launches (tz_plan_opts.direct_queue): every direct step runs after the items
     whose results it reads, or, inside its queue launch, after the steps it
     waits for (dep = their index in the launch); each product and permute
     still runs after its inputs; blocks add up; the launch count per group
@@ -361,7 +361,7 @@ def test_direct_queue_schedule(tz, rows, cols, t, seed, small, prec):
     tree = tz.tz_path_greedy(net, restarts=4, seed=1, precision=prec)
     descs, stats = {}, {}
     for levels in (0, 1):
-        plan = tz.tz_plan_create(net, tree, [], precision=prec, small_log2=small, direct_levels=levels)
+        plan = tz.tz_plan_create(net, tree, [], precision=prec, small_log2=small, direct_queue=not levels)
         descs[levels], stats[levels] = json.loads(plan.describe()), plan.stats()
     q, lv = descs[0], descs[1]
     assert stats[0]["n_launches_per_group"] <= stats[1]["n_launches_per_group"]

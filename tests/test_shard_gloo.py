@@ -37,6 +37,25 @@ def test_step_windows_of_ranks_are_disjoint_within_a_step():
             seen |= s
 
 
+@pytest.mark.parametrize("n,w,target", [(4096, 1, 1826), (4096, 1, 1977), (1024, 1, 1024), (1, 1, 3),
+                                         (4096, 4, 700), (64, 8, 100), (2, 4, 1)])
+def test_step_windows_are_whole(n, w, target):
+    """Every timed step contracts the same number of slices: a window that
+    ran past the end of the slice range would make the per-slice time look
+    shorter than it is."""
+    per = shard.window_size(n, w, target)
+    assert per & (per - 1) == 0 and 1 <= per <= max(1, target)
+    assert per * w <= n or per == 1
+    for step in range(12):
+        seen = set()
+        for r in range(w):
+            lo, hi = shard.step_window(n, w, r, per, step)
+            assert hi - lo == min(per, n) and 0 <= lo and hi <= n
+            if per * w <= n:
+                assert not (set(range(lo, hi)) & seen)
+                seen |= set(range(lo, hi))
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
