@@ -96,6 +96,9 @@ def parse():
     ap.add_argument("--compare-direct", type=int, default=0,
                     help="rounds of an interleaved comparison with the other direct-step launch form (same "
                          "tree, same autotuned products, same slice windows; 0: off)")
+    ap.add_argument("--tune-file", default="",
+                    help="load the autotuner's choices for the main plan from this .json if it exists, else save "
+                         "them there after binding (a profiler run then reproduces the timed run's plan)")
     ap.add_argument("--tree-seed", type=int, default=7)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
@@ -208,11 +211,12 @@ def measured_peaks():
 
 
 # DRAM bytes (read + write) per tensor-core product launch, averaged over the
-# 20 product launches of one step, from one ncu capture of the bench command
-# itself (dram__bytes_read.sum + dram__bytes_write.sum, one pass;
+# 14 product launches of one step, from one ncu capture of the bench command
+# itself with its autotuned choices fixed by --tune-file
+# (dram__bytes_read.sum + dram__bytes_write.sum, one pass;
 # profiles/launch_list_bristlecone70_d32_fp16x3.md), keyed by (precision,
 # workload). A mode or workload without an up-to-date capture reports null.
-TC_DRAM_BYTES_PER_LAUNCH = {("fp16x3", "bristlecone70_d32"): 1.4938e9}
+TC_DRAM_BYTES_PER_LAUNCH = {("fp16x3", "bristlecone70_d32"): 1.9341e9}
 
 
 def plan_roofline(plan, precision, ms_per_group):
@@ -248,6 +252,39 @@ def plan_roofline(plan, precision, ms_per_group):
             t += 2 * esz * size[it[1]] / (hbm * 1e9)
     return {"t_roof_ms": t * 1e3, "t_measured_ms": ms_per_group, "frac": t * 1e3 / ms_per_group,
             "peaks": f"{src}: HBM {hbm:.0f} GB/s, tensor {tc or 0:.0f} TF/s, FP32 {simt:.1f} TF/s"}
+
+
+def top_profiled_items(plan, precision, n=10):
+    """The n most expensive launch items of the profiled groups: kind, GEMM
+    shape, ms per group, achieved rates and the item's own roofline time
+    (max of algorithmic bytes / HBM peak and issued flops / its unit's peak)."""
+    hbm, tc, _, _, _ = measured_peaks()
+    if precision == "tf32x3":
+        tc *= 1.1 / 2.25
+    steps = json.loads(plan.describe())["steps"]
+    items = plan.profile_items()
+    groups = max([it["launches"] for it in items if it["kind"] == "leaves"] or [1])
+    out = []
+    for i, it in enumerate(items):
+        if it["ms"] <= 0:
+            continue
+        ms = it["ms"] / groups
+        rate = tc * (3 if precision in ("tf32x3", "bf16x3", "fp16x3") and it["kind"] == "gemm_tc" else 1)
+        if it["kind"] != "gemm_tc":
+            rate = 80.5 if precision != "c128" else 1.3   # CUDA-core FP32 (FP64) peak, TF/s
+        issued = it["flops"] * (3 if it["kind"] == "gemm_tc" and precision in ("tf32x3", "bf16x3", "fp16x3") else 1)
+        t_roof = max(it["bytes"] / (hbm * 1e9), issued / (tc * 1e12 if it["kind"] == "gemm_tc" else rate * 1e12))
+        e = {"item": i, "kind": it["kind"], "ms_per_group": ms, "gbs": it["bytes"] / (ms / 1e3) / 1e9,
+             "useful_tflops": it["flops"] / (ms / 1e3) / 1e12, "roofline_ms": t_roof * 1e3,
+             "frac": t_roof * 1e3 / ms}
+        if it["step"] >= 0:
+            st = steps[it["step"]]
+            e["shape"] = {"batch": st["batch"], "M": st["M"], "N": st["N"], "K": st["K"],
+                          "out": "row-major" if st["row_major"] else "scatter",
+                          "choice": "simt" if st["tc_simt"] else ("pairs" if st["tc_pair"] == 1 else "single")}
+        out.append(e)
+    out.sort(key=lambda e: -e["ms_per_group"])
+    return out[:n]
 
 
 def roofline(prof, precision, workload):
@@ -585,7 +622,15 @@ def main():
     stream = torch.cuda.Stream(device=device)
     plan, sliced, prep_s = build_plan(tz, spec, args, precision, stream, device, log2_max)
     st = plan.stats()
+    tune_loaded = bool(args.tune_file) and os.path.exists(args.tune_file)
+    if tune_loaded:
+        for e in json.load(open(args.tune_file)):
+            tz.tz_tune_preset(precision, *e)
     plan.bind()
+    if args.tune_file and not tune_loaded:
+        d = json.loads(plan.describe())
+        json.dump([[s["batch"], s["M"], s["N"], s["K"], 0 if s["row_major"] else 1, s["tc_pair"], s["tc_ksplit"],
+                    s["tc_simt"]] for s in d["steps"] if s["var"] and s["tc"]], open(args.tune_file, "w"))
     plan_bind_ms = plan.stats()["bind_ms"]
     n_tuned = plan.stats()["n_tuned_steps"]
     st = plan.stats()   # the launch count follows the autotuned choices
@@ -675,6 +720,7 @@ def main():
     plan.profile_enable(True)
     one_step(args.warmup + args.steps, reduce=False)
     prof = plan.profile()
+    top_items = top_profiled_items(plan, precision)
     plan.profile_enable(False)
     rl = roofline(prof, precision, args.workload)
     rl["plan_roofline"] = plan_roofline(plan, precision, ms / S / chunks)
@@ -788,6 +834,7 @@ def main():
         "gpu_launches": args.steps * launches_per_call,
         "profiled_launches_per_kind": per_launch,
         "profiled_ms_per_kind": per_kind_ms,
+        "profiled_top_items": top_items,
         "clocks": clk.summary(),
     }
     print(json.dumps(line))

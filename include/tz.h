@@ -428,6 +428,16 @@ int tz_debug_stall_direct_queue(int on);
  * complex64 kernel, whichever is faster (the autotuner otherwise takes that
  * kernel only where it measured faster); clears the autotuner's cache. */
 int tz_debug_tune_force_simt(int on);
+/* Preset one entry of the autotuner's cache on the current device: plans
+ * autotuned afterwards whose tensor-core step has this precision, shape
+ * (batch, m, n, k) and output kind (scatter = 0 row-major, 1 through the
+ * scatter map) take this launch choice without timing it: pair (1 pairs of
+ * CTAs, 0 single CTAs, -1 the process default), ksplit (1 never split K, 0
+ * the default split), simt (1 the CUDA-core complex64 kernel; allowed only
+ * for k <= 32). Lets a run reproduce the choices of an earlier one, e.g. a
+ * profiler run, whose own timings would differ. TZ_EINVAL for bad values. */
+int tz_tune_preset(int precision, int64_t batch, int64_t m, int64_t n, int64_t k, int scatter, int pair, int ksplit,
+                   int simt);
 
 /* Process-wide default of how the split BF16 / FP16 products run where the
  * shape allows pairs (128-column tiles, m a multiple of 256): 1 on pairs of

@@ -27,7 +27,7 @@ __all__ = [
     "tz_tree_from_pairs", "tz_slice_select", "tz_plan_create", "tz_contract_amplitudes",
     "tz_contract_amplitudes_device", "tz_op_permute", "tz_op_cgemm", "tz_op_accumulate", "PRECISIONS",
     "tz_plan_status", "tz_op_cgemm_status", "tz_op_cgemm_static_status", "tz_debug_set_wait_limit",
-    "tz_debug_stall_tensor_core", "tz_debug_stall_direct_queue", "tz_tune_tc_pairs", "tz_tune_tc_prefetch", "tz_debug_tune_force_simt",
+    "tz_debug_stall_tensor_core", "tz_debug_stall_direct_queue", "tz_tune_tc_pairs", "tz_tune_tc_prefetch", "tz_debug_tune_force_simt", "tz_tune_preset",
     "TZ_C64_SIMT", "TZ_TF32X3", "TZ_BF16X3", "TZ_FP16X3",
 ]
 
@@ -351,6 +351,12 @@ def tz_tune_tc_pairs(mode: int):
     """Process default for the split BF16 / FP16 products: 1 pairs of CTAs
     (cta_group::2) where the shape allows, 0 single CTAs, -1 initial default."""
     check(lib().tz_tune_tc_pairs(int(mode)))
+
+
+def tz_tune_preset(precision, batch, m, n, k, scatter, pair, ksplit, simt):
+    """Preset one autotuner cache entry on the current device (see tz.h)."""
+    check(lib().tz_tune_preset(PRECISIONS.get(precision, precision), int(batch), int(m), int(n), int(k),
+                               int(scatter), int(pair), int(ksplit), int(simt)))
 
 
 def tz_debug_tune_force_simt(on: bool):

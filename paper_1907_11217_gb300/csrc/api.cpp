@@ -602,6 +602,14 @@ int tz_tune_tc_prefetch(int kblocks) {
   TZ_CATCH
 }
 
+int tz_tune_preset(int precision, int64_t batch, int64_t m, int64_t n, int64_t k, int scatter, int pair, int ksplit,
+                   int simt) {
+  TZ_TRY
+  REQUIRE(is_tc_precision(precision), "presets are for the tensor-core precisions");
+  tz::tune_preset(precision, batch, m, n, k, scatter, pair, ksplit, simt);
+  TZ_CATCH
+}
+
 int tz_debug_tune_force_simt(int on) {
   TZ_TRY
   tz::tune_force_simt(on);

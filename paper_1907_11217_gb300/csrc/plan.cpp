@@ -1082,6 +1082,17 @@ void tune_force_simt(int on) {
   g_tune_cache.clear();  // choices made under the other setting are not reused
 }
 
+void tune_preset(int precision, int64_t batch, int64_t M, int64_t N, int64_t K, int scatter, int pair, int ksplit,
+                 int simt) {
+  if (batch < 1 || M < 1 || N < 1 || K < 1 || (scatter != 0 && scatter != 1) || pair < -1 || pair > 1 ||
+      (ksplit != 0 && ksplit != 1) || (simt != 0 && simt != 1) || (simt && K > kTuneSimtMaxK))
+    fail(TZ_EINVAL, "bad autotuner preset");
+  int dev = 0;
+  cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[TuneKey{dev, precision, batch, M, N, K, scatter}] = TuneChoice{simt ? -1 : pair, simt ? 0 : ksplit, simt, 0.f};
+}
+
 static void autotune_tc_steps(tz_plan *p) {
   cudaStream_t s = p->stream;
   const RunCtx ctx = default_ctx(p);

@@ -136,6 +136,9 @@ void plan_run(tz_plan *p, const RunCtx &ctx, int64_t n_rows, int64_t lo, int64_t
 int read_tc_error(const tz_plan *p, const RunCtx &ctx);
 // test hook: autotuned steps with small K take the CUDA-core kernel
 void tune_force_simt(int on);
+// one autotuner cache entry for the current device (tz_tune_preset)
+void tune_preset(int precision, int64_t batch, int64_t M, int64_t N, int64_t K, int scatter, int pair, int ksplit,
+                 int simt);
 void plan_destroy(tz_plan *p);
 void plan_profile_collect(tz_plan *p);
 void item_cost_public(const tz_plan *p, int var_item, int *kind, double *flops, double *bytes);

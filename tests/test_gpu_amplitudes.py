@@ -253,3 +253,42 @@ def test_autotuned_small_k_steps_on_cuda_cores(tz):
     assert prof["gemm_simt"]["launches"] >= len(small)
     ref = np.array([tn.Contractor(spec, max_log2=24).amplitude(x) for x in bits[:16]])
     assert rel_err(got[:16], ref, 49) <= TOL_C64
+
+
+def test_autotuner_presets_reproduce_choices(tz):
+    """Presets (tz_tune_preset) fill the autotuner's cache: a plan autotuned
+    afterwards takes the preset choice for every step it covers, here the
+    opposite of what a first plan measured, and its amplitudes match the
+    first plan's within the split products' error."""
+    import json
+    spec = grid_spec(7, 7, 16, 2)
+    bits = ti.random_bitstrings(49, 64, 77)
+    net = tz.tz_network_from_circuit(tz.tz_circuit_from_spec(spec), 6)
+    tree = tz.tz_path_greedy(net, restarts=16, seed=7, algorithm="elimination", precision="fp16x3")
+    tz.tz_debug_tune_force_simt(False)   # also clears the cache of earlier tests
+    p1 = tz.tz_plan_create(net, tree, [], precision="fp16x3", max_bitstrings=64, autotune=True)
+    p1.bind()
+    first = [s for s in json.loads(p1.describe())["steps"] if s["var"] and s["tc"]]
+    a1 = tz.tz_contract_amplitudes(p1, bits)
+    p1.close()
+    want = []
+    for s in first:
+        if s["K"] <= 32:
+            simt = 1 - s["tc_simt"]
+            pair = 0
+        else:
+            simt = 0
+            pair = 1 - s["tc_pair"] if s["tc_pair"] in (0, 1) else 0
+        want.append((s["batch"], s["M"], s["N"], s["K"], 0 if s["row_major"] else 1, pair, 0, simt))
+        tz.tz_tune_preset("fp16x3", *want[-1])
+    p2 = tz.tz_plan_create(net, tree, [], precision="fp16x3", max_bitstrings=64, autotune=True)
+    p2.bind()
+    second = [s for s in json.loads(p2.describe())["steps"] if s["var"] and s["tc"]]
+    for s, w in zip(second, want):
+        assert s["tc_simt"] == w[7] and (w[7] == 1 or (s["tc_pair"], s["tc_ksplit"]) == (w[5], w[6]))
+    a2 = tz.tz_contract_amplitudes(p2, bits)
+    p2.close()
+    tz.tz_debug_tune_force_simt(False)   # leave no presets behind
+    assert rel_err(a2, a1, 49) <= TOL_C64
+    with pytest.raises(tz.TzError):
+        tz.tz_tune_preset("fp16x3", 1, 128, 64, 64, 0, 0, 0, 1)   # the CUDA-core kernel only for k <= 32
