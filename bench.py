@@ -281,7 +281,9 @@ def top_profiled_items(plan, precision, n=10):
             st = steps[it["step"]]
             e["shape"] = {"batch": st["batch"], "M": st["M"], "N": st["N"], "K": st["K"],
                           "out": "row-major" if st["row_major"] else "scatter",
-                          "choice": "simt" if st["tc_simt"] else ("pairs" if st["tc_pair"] == 1 else "single")}
+                          "choice": {1: "simt", 2: "stream"}.get(st["tc_simt"],
+                                                                 ("pairs" if st["tc_pair"] == 1 else "single")
+                                                                 if st["tc"] else "simt")}
         out.append(e)
     out.sort(key=lambda e: -e["ms_per_group"])
     return out[:n]
@@ -630,7 +632,9 @@ def main():
     if args.tune_file and not tune_loaded:
         d = json.loads(plan.describe())
         json.dump([[s["batch"], s["M"], s["N"], s["K"], 0 if s["row_major"] else 1, s["tc_pair"], s["tc_ksplit"],
-                    s["tc_simt"]] for s in d["steps"] if s["var"] and s["tc"]], open(args.tune_file, "w"))
+                    s["tc_simt"]] for s in d["steps"]
+                   if s["var"] and s["gemm"] and (s["tc"] or (s["K"] <= 32 and not s["skinny"]))],
+                  open(args.tune_file, "w"))
     plan_bind_ms = plan.stats()["bind_ms"]
     n_tuned = plan.stats()["n_tuned_steps"]
     st = plan.stats()   # the launch count follows the autotuned choices

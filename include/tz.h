@@ -424,18 +424,21 @@ int tz_debug_set_wait_limit(int64_t ns);
 int tz_debug_stall_tensor_core(int on);
 int tz_debug_stall_direct_queue(int on);
 /* Test hook (process-wide): with on = 1, plans autotuned afterwards run every
- * tensor-core step with at most 32 complex K values on the CUDA-core
- * complex64 kernel, whichever is faster (the autotuner otherwise takes that
- * kernel only where it measured faster); clears the autotuner's cache. */
+ * tensor-core step with at most 32 complex K values on the tiled CUDA-core
+ * complex64 kernel, whichever is faster; with on = 2, every complex64 step
+ * with at most 32 complex K values that the stream kernel supports runs on
+ * it (the autotuner otherwise takes either only where it measured faster);
+ * 0 turns it off. Each call clears the autotuner's cache. */
 int tz_debug_tune_force_simt(int on);
 /* Preset one entry of the autotuner's cache on the current device: plans
- * autotuned afterwards whose tensor-core step has this precision, shape
- * (batch, m, n, k) and output kind (scatter = 0 row-major, 1 through the
- * scatter map) take this launch choice without timing it: pair (1 pairs of
- * CTAs, 0 single CTAs, -1 the process default), ksplit (1 never split K, 0
- * the default split), simt (1 the CUDA-core complex64 kernel; allowed only
- * for k <= 32). Lets a run reproduce the choices of an earlier one, e.g. a
- * profiler run, whose own timings would differ. TZ_EINVAL for bad values. */
+ * autotuned afterwards whose step has this precision (a complex64 one),
+ * shape (batch, m, n, k) and output kind (scatter = 0 row-major, 1 through
+ * the scatter map) take this launch choice without timing it: pair (1 pairs
+ * of CTAs, 0 single CTAs, -1 the process default), ksplit (1 never split K,
+ * 0 the default split), simt (0 the step's own kernel; for k <= 32 only: 1
+ * the tiled CUDA-core kernel, 2 the stream kernel). Lets a run reproduce the
+ * choices of an earlier one, e.g. a profiler run, whose own timings would
+ * differ. TZ_EINVAL for bad values. */
 int tz_tune_preset(int precision, int64_t batch, int64_t m, int64_t n, int64_t k, int scatter, int pair, int ksplit,
                    int simt);
 

@@ -359,10 +359,11 @@ def tz_tune_preset(precision, batch, m, n, k, scatter, pair, ksplit, simt):
                                int(scatter), int(pair), int(ksplit), int(simt)))
 
 
-def tz_debug_tune_force_simt(on: bool):
+def tz_debug_tune_force_simt(on):
     """Test hook: autotuned plans run every small-K tensor-core step on the
-    CUDA-core complex64 kernel."""
-    check(lib().tz_debug_tune_force_simt(int(bool(on))))
+    tiled CUDA-core complex64 kernel (on = True or 1), or every small-K
+    complex64 step the stream kernel supports on it (on = 2)."""
+    check(lib().tz_debug_tune_force_simt(2 if on == 2 else int(bool(on))))
 
 
 def tz_tune_tc_prefetch(kblocks: int):

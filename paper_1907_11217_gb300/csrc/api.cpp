@@ -605,7 +605,7 @@ int tz_tune_tc_prefetch(int kblocks) {
 int tz_tune_preset(int precision, int64_t batch, int64_t m, int64_t n, int64_t k, int scatter, int pair, int ksplit,
                    int simt) {
   TZ_TRY
-  REQUIRE(is_tc_precision(precision), "presets are for the tensor-core precisions");
+  REQUIRE(precision == TZ_C64_SIMT || is_tc_precision(precision), "presets are for the complex64 precisions");
   tz::tune_preset(precision, batch, m, n, k, scatter, pair, ksplit, simt);
   TZ_CATCH
 }

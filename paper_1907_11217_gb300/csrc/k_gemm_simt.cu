@@ -3,6 +3,8 @@
 // C[z] m x n, all row-major. This is the plain complex64 precision mode and
 // the baseline of the split-precision tensor-core modes.
 #include <algorithm>
+#include <utility>
+#include <vector>
 
 #include "kernels.h"
 
@@ -417,6 +419,260 @@ cudaError_t run_skinny_gather(const T *X, const T *Y, T *C, int64_t batch, int64
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- stream
+// Products with few summed values (K <= 32) write far more than they read,
+// and through a scatter map their outputs land wherever the consumer wants
+// them. This kernel is built around the writes: a tile is the set of
+// outputs whose local bits (the low bz bits of the batch index, bm of the row
+// index, bn of the column index) vary, chosen so that they cover the lowest
+// output positions. Its outputs are numbered ("ranks") in the order of
+// their output positions, so a warp's 32 consecutive ranks write consecutive
+// addresses; the tile's rows of A and B are staged in shared memory
+// (K padded to KMAX with zeros) and every output is a short dot product in
+// FP32 FMA, summed in k order like the tiled kernel.
+constexpr int kStreamMaxLocal = 16;
+struct StreamTile {
+  int bz, bm, bn, nl;               // local bits of batch, row, column; total
+  int8_t rsrc[kStreamMaxLocal];     // rank bit r: 0 batch, 1 row, 2 column
+  int8_t rbit[kStreamMaxLocal];     // its bit within that index
+  int8_t rpos[kStreamMaxLocal];     // its output position
+};
+
+template <int KMAX>
+__global__ void __launch_bounds__(256)
+    cgemm_stream_kernel(const float2 *__restrict__ A, const float2 *__restrict__ B, float2 *__restrict__ C,
+                        int64_t batch, int64_t M, int64_t N, int K, const __grid_constant__ CScatter sc,
+                        const __grid_constant__ StreamTile st) {
+  // rows in shared memory: KMAX / 2 chunks of 16 bytes each, and every block
+  // of rows with the same batch bits shifted by one more chunk, so that the
+  // rows a warp reads at once (different batch bits) sit in different banks
+  extern __shared__ float4 stream_smem[];
+  constexpr int CH = KMAX / 2;
+  const int rowsA = 1 << (st.bz + st.bm), rowsB = 1 << (st.bz + st.bn);
+  float4 *As4 = stream_smem;
+  float4 *Bs4 = As4 + (size_t)rowsA * CH + (1 << st.bz);
+  auto rowA = [&](int row) { return As4 + row * CH + (row >> st.bm); };
+  auto rowB = [&](int row) { return Bs4 + row * CH + (row >> st.bn); };
+  // the rank bits from 8 up, decoded once per launch: entry j holds the local
+  // batch, row and column bits and the output offset of rank j * 256
+  __shared__ int s_hz[1 << (kStreamMaxLocal - 8)], s_hm[1 << (kStreamMaxLocal - 8)],
+      s_hn[1 << (kStreamMaxLocal - 8)];
+  __shared__ int64_t s_ho[1 << (kStreamMaxLocal - 8)];
+  __shared__ int8_t s_pos[kMaxBits];      // output position of bit t of (batch, row, column)
+  __shared__ unsigned s_base[2][2];       // a tile's output base, OR-reduced by warps 0 and 1
+  const int gz = sc.nb, gm = sc.nm, gn = sc.nn, total = gz + gm + gn;
+  const int nhi = st.nl > 8 ? 1 << (st.nl - 8) : 1;
+  for (int j = threadIdx.x; j < nhi; j += 256) {
+    int hz = 0, hm = 0, hn = 0;
+    int64_t ho = 0;
+    for (int r = 8; r < st.nl; r++)
+      if ((j >> (r - 8)) & 1) {
+        const int v = 1 << st.rbit[r];
+        if (st.rsrc[r] == 0) hz |= v;
+        else if (st.rsrc[r] == 1) hm |= v;
+        else hn |= v;
+        ho |= int64_t(1) << st.rpos[r];
+      }
+    s_hz[j] = hz;
+    s_hm[j] = hm;
+    s_hn[j] = hn;
+    s_ho[j] = ho;
+  }
+  for (int t = threadIdx.x; t < total; t += 256)
+    s_pos[t] = t < gz ? sc.pb[t] : t < gz + gm ? sc.pm[t - gz] : sc.pn[t - gz - gm];
+  // the rank bits below 8 come from the thread
+  int tz0 = 0, tm0 = 0, tn0 = 0;
+  int64_t to0 = 0;
+  for (int r = 0; r < st.nl && r < 8; r++)
+    if ((threadIdx.x >> r) & 1) {
+      const int v = 1 << st.rbit[r];
+      if (st.rsrc[r] == 0) tz0 |= v;
+      else if (st.rsrc[r] == 1) tm0 |= v;
+      else tn0 |= v;
+      to0 |= int64_t(1) << st.rpos[r];
+    }
+  __syncthreads();
+  const int sn = gn - st.bn, sm = gm - st.bm;  // log2 of the column and row tiles
+  const int64_t tiles = (batch * M * N) >> st.nl;
+  const int R = 1 << st.nl;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t nt = tile & ((int64_t(1) << sn) - 1);
+    const int64_t mt = (tile >> sn) & ((int64_t(1) << sm) - 1);
+    const int64_t zt = tile >> (sn + sm);
+    const int64_t z0 = zt << st.bz, m0 = mt << st.bm, n0 = nt << st.bn;
+    if (threadIdx.x < 64) {
+      // bit t of (z0, m0, n0) contributes 1 << s_pos[t] to the tile's base
+      const int t = threadIdx.x;
+      int64_t c = 0;
+      if (t < total) {
+        const int64_t v = t < gz ? (z0 >> t) : t < gz + gm ? (m0 >> (t - gz)) : (n0 >> (t - gz - gm));
+        c = (v & 1) ? int64_t(1) << s_pos[t] : 0;
+      }
+      const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)c);
+      const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(c >> 32));
+      if ((t & 31) == 0) {
+        s_base[t >> 5][0] = lo;
+        s_base[t >> 5][1] = hi;
+      }
+    }
+    __syncthreads();  // the previous tile's rows are no longer read; base ready
+    const int64_t base = (int64_t)((uint64_t)(s_base[0][0] | s_base[1][0]) |
+                                   ((uint64_t)(s_base[0][1] | s_base[1][1]) << 32));
+    // rows (z0 + lz, m0 .. m0 + 2^bm) of A are one contiguous run of 2^bm K
+    // values; two complex values (16 bytes) per load where K is even
+    for (int i = threadIdx.x; i < rowsA * CH; i += 256) {
+      const int row = i / CH, c = i - row * CH;
+      const int lz = row >> st.bm, lm = row & ((1 << st.bm) - 1);
+      const float2 *src = A + ((z0 + lz) * M + m0 + lm) * K;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if ((K & 1) == 0) {
+        if (2 * c < K) v = *reinterpret_cast<const float4 *>(src + 2 * c);
+      } else {
+        if (2 * c < K) v.x = src[2 * c].x, v.y = src[2 * c].y;
+        if (2 * c + 1 < K) v.z = src[2 * c + 1].x, v.w = src[2 * c + 1].y;
+      }
+      rowA(row)[c] = v;
+    }
+    for (int i = threadIdx.x; i < rowsB * CH; i += 256) {
+      const int row = i / CH, c = i - row * CH;
+      const int lz = row >> st.bn, ln = row & ((1 << st.bn) - 1);
+      const float2 *src = B + ((z0 + lz) * N + n0 + ln) * K;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if ((K & 1) == 0) {
+        if (2 * c < K) v = *reinterpret_cast<const float4 *>(src + 2 * c);
+      } else {
+        if (2 * c < K) v.x = src[2 * c].x, v.y = src[2 * c].y;
+        if (2 * c + 1 < K) v.z = src[2 * c + 1].x, v.w = src[2 * c + 1].y;
+      }
+      rowB(row)[c] = v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x >= R) continue;
+    // (keeping a thread's rows in registers across its outputs measured
+    // slower: the registers cost more occupancy than the reads they save)
+    for (int rr = 0; rr < R; rr += 256) {
+      const int j = rr >> 8;
+      const int lz = tz0 | s_hz[j];
+      const float4 *a = rowA((lz << st.bm) + (tm0 | s_hm[j]));
+      const float4 *b = rowB((lz << st.bn) + (tn0 | s_hn[j]));
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < CH; k++) {
+        const float4 x = a[k], y = b[k];
+        cmac(acc, make_float2(x.x, x.y), make_float2(y.x, y.y));
+        cmac(acc, make_float2(x.z, x.w), make_float2(y.z, y.w));
+      }
+      __stcs(C + base + (to0 | s_ho[j]), acc);
+    }
+  }
+}
+
+// Tile of the stream kernel for this product, or false when it does not
+// apply (dimensions not powers of two, K above 32, or no tile within the
+// shared-memory budget). The output position of every index bit comes from
+// the scatter map (row-major: column bits lowest, then row, then batch).
+bool stream_tile(int64_t batch, int64_t M, int64_t N, int64_t K, const CScatter &sc, StreamTile *t, int *kmax) {
+  auto lg = [](int64_t v) { int b = 0; while ((int64_t(1) << b) < v) b++; return (int64_t(1) << b) == v ? b : -1; };
+  const int gz = lg(batch), gm = lg(M), gn = lg(N);
+  if (gz < 0 || gm < 0 || gn < 0 || K < 1 || K > 32) return false;
+  if (sc.nb != gz || sc.nm != gm || sc.nn != gn) return false;
+  const int total = gz + gm + gn;
+  if (total > kMaxBits) return false;
+  *kmax = K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
+  const int64_t budget = 40 * 1024 / 8;  // float2 values of dynamic shared memory (48 KB with the static part)
+  // owner of each output position
+  std::vector<std::pair<int, int>> owner(total, {-1, -1});
+  const int8_t *pos[3] = {sc.pb, sc.pm, sc.pn};
+  const int g[3] = {gz, gm, gn};
+  for (int x = 0; x < 3; x++)
+    for (int j = 0; j < g[x]; j++) {
+      if (pos[x][j] < 0 || pos[x][j] >= total || owner[pos[x][j]].first >= 0) return false;
+      owner[pos[x][j]] = {x, j};
+    }
+  auto fits = [&](const int *b) {
+    return ((int64_t(1) << (b[0] + b[1])) + (int64_t(1) << (b[0] + b[2]))) * *kmax + (int64_t(4) << b[0]) <= budget &&
+           b[0] + b[1] + b[2] <= kStreamMaxLocal;
+  };
+  int b[3] = {0, 0, 0};
+  for (int L = std::min(total, 6); L >= 0; L--) {
+    int c[3] = {0, 0, 0};
+    for (int p = 0; p < L; p++) c[owner[p].first] = std::max(c[owner[p].first], owner[p].second + 1);
+    if (fits(c)) {
+      std::copy(c, c + 3, b);
+      break;
+    }
+  }
+  // more rows and columns while they fit: each A row is then read by more
+  // columns and each B row by more rows (up to 4096 outputs a tile)
+  for (;;) {
+    if (b[0] + b[1] + b[2] >= 12) break;
+    int c[3] = {b[0], b[1], b[2]};
+    const int pick = (b[2] < g[2] && (b[2] <= b[1] || b[1] >= g[1])) ? 2 : 1;
+    if (c[pick] >= g[pick]) break;
+    c[pick]++;
+    if (!fits(c)) break;
+    std::copy(c, c + 3, b);
+  }
+  t->bz = b[0];
+  t->bm = b[1];
+  t->bn = b[2];
+  t->nl = b[0] + b[1] + b[2];
+  // ranks: the local bits in the order of their output positions
+  int r = 0;
+  for (int p = 0; p < total; p++) {
+    const int x = owner[p].first, j = owner[p].second;
+    if (j < b[x]) {
+      t->rsrc[r] = (int8_t)x;
+      t->rbit[r] = (int8_t)j;
+      t->rpos[r] = (int8_t)p;
+      r++;
+    }
+  }
+  return r == t->nl;
+}
+
+CScatter row_major_map(int64_t batch, int64_t M, int64_t N) {
+  auto lg = [](int64_t v) { int b = 0; while ((int64_t(1) << b) < v) b++; return b; };
+  CScatter sc{};
+  sc.nn = lg(N);
+  sc.nm = lg(M);
+  sc.nb = lg(batch);
+  for (int j = 0; j < sc.nn; j++) sc.pn[j] = (int8_t)j;
+  for (int j = 0; j < sc.nm; j++) sc.pm[j] = (int8_t)(sc.nn + j);
+  for (int j = 0; j < sc.nb; j++) sc.pb[j] = (int8_t)(sc.nn + sc.nm + j);
+  return sc;
+}
+
+}  // namespace
+
+bool cgemm_stream_supported(int64_t batch, int64_t M, int64_t N, int64_t K, const CScatter *sc) {
+  StreamTile t{};
+  int kmax = 0;
+  if (batch * M * N < 256) return false;
+  return stream_tile(batch, M, N, K, sc ? *sc : row_major_map(batch, M, N), &t, &kmax);
+}
+
+cudaError_t launch_cgemm_stream(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N,
+                                int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s) {
+  if (sA != M * K || sB != N * K || (!sc && sC != M * N)) return cudaErrorNotSupported;
+  const CScatter map = sc ? *sc : row_major_map(batch, M, N);
+  StreamTile t{};
+  int kmax = 0;
+  if (batch * M * N < 256 || !stream_tile(batch, M, N, K, map, &t, &kmax)) return cudaErrorNotSupported;
+  const size_t smem = ((((size_t)1 << (t.bz + t.bm)) + ((size_t)1 << (t.bz + t.bn))) * kmax / 2 +
+                       ((size_t)2 << t.bz)) * sizeof(float4);
+  const int64_t tiles = batch * M * N >> t.nl;
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, 152 * 8);
+  switch (kmax) {
+    case 4: cgemm_stream_kernel<4><<<grid, 256, smem, s>>>(A, B, C, batch, M, N, (int)K, map, t); break;
+    case 8: cgemm_stream_kernel<8><<<grid, 256, smem, s>>>(A, B, C, batch, M, N, (int)K, map, t); break;
+    case 16: cgemm_stream_kernel<16><<<grid, 256, smem, s>>>(A, B, C, batch, M, N, (int)K, map, t); break;
+    default: cgemm_stream_kernel<32><<<grid, 256, smem, s>>>(A, B, C, batch, M, N, (int)K, map, t); break;
+  }
+  return cudaGetLastError();
+}
+
+namespace {
 }  // namespace
 
 cudaError_t launch_cgemm_skinny_gather(const float2 *X, const float2 *Y, float2 *C, int64_t batch, int64_t M,

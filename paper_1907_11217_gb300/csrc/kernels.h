@@ -147,6 +147,15 @@ cudaError_t launch_zskinny_gather(const double2 *X, const double2 *Y, double2 *C
 // sc == nullptr: C row-major with batch stride sC.
 cudaError_t launch_cgemm_simt(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N,
                               int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s);
+// Products with K <= 32 complex values on CUDA cores, organised around their
+// writes: tiles of outputs that cover the lowest output positions, written in
+// address order (launch_cgemm_stream returns cudaErrorNotSupported where
+// cgemm_stream_supported is false: dimensions not powers of two, K above 32,
+// or fewer than 256 outputs). Same FP32 arithmetic and summation order as
+// launch_cgemm_simt's tiled kernel. sc == nullptr: C row-major (sC = M N).
+bool cgemm_stream_supported(int64_t batch, int64_t M, int64_t N, int64_t K, const CScatter *sc);
+cudaError_t launch_cgemm_stream(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N,
+                                int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s);
 // Skinny product (n <= 4, k <= 16) reading X and Y through gather maps and
 // writing C through sc (nullptr: row-major [batch][m][n]).
 cudaError_t launch_cgemm_skinny_gather(const float2 *X, const float2 *Y, float2 *C, int64_t batch, int64_t M,

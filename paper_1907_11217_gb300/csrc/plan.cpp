@@ -1001,6 +1001,10 @@ static void run_items(tz_plan *p, const std::vector<Item> &items, const RunCtx &
         } else if (ps.skinny) {
           cuda_check(dev::launch_cgemm_skinny_gather(X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.gather, sc, s),
                      "skinny gemm");
+        } else if (ps.tc_simt == 2) {
+          cuda_check(dev::launch_cgemm_stream(X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.M * ps.K, ps.N * ps.K,
+                                              ps.M * ps.N, sc, s),
+                     "stream gemm");
         } else if (ps.tc && !ps.tc_simt) {
           void *scr = abase + ps.tc_scratch_off;
           cuda_check(dev::launch_cgemm_tc(p->opts.precision, X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.M * ps.K,
@@ -1071,13 +1075,14 @@ struct TuneChoice {
 // complex64 kernel (FP32 FMA: at least as accurate as the split products);
 // with so few terms per output they are bound by writing C
 constexpr int64_t kTuneSimtMaxK = 32;
-std::atomic<int> g_tune_force_simt{0};  // test hook: take that kernel wherever allowed
+std::atomic<int> g_tune_force_simt{0};  // test hook: 1 the tiled CUDA-core kernel, 2 the
+                                        // stream kernel, wherever allowed
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneChoice> g_tune_cache;
 }  // namespace
 
 void tune_force_simt(int on) {
-  g_tune_force_simt.store(on ? 1 : 0);
+  g_tune_force_simt.store(on == 2 ? 2 : on ? 1 : 0);
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache.clear();  // choices made under the other setting are not reused
 }
@@ -1085,7 +1090,7 @@ void tune_force_simt(int on) {
 void tune_preset(int precision, int64_t batch, int64_t M, int64_t N, int64_t K, int scatter, int pair, int ksplit,
                  int simt) {
   if (batch < 1 || M < 1 || N < 1 || K < 1 || (scatter != 0 && scatter != 1) || pair < -1 || pair > 1 ||
-      (ksplit != 0 && ksplit != 1) || (simt != 0 && simt != 1) || (simt && K > kTuneSimtMaxK))
+      (ksplit != 0 && ksplit != 1) || simt < 0 || simt > 2 || (simt && K > kTuneSimtMaxK))
     fail(TZ_EINVAL, "bad autotuner preset");
   int dev = 0;
   cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
@@ -1108,12 +1113,19 @@ static void autotune_tc_steps(tz_plan *p) {
     for (const Item &it : p->var_items) {
       if (it.kind != IT_GEMM) continue;
       PStep &ps = p->S[it.a];
-      if (!ps.tc) continue;
+      const dev::CScatter *sc0 = ps.row_major ? nullptr : &ps.scatter;
+      // the stream kernel is a candidate for every complex64 product with
+      // few summed values that it supports, on the tensor-core path or not
+      const bool stream_ok = p->esz == 8 && !ps.skinny && ps.K <= kTuneSimtMaxK &&
+                             dev::cgemm_stream_supported(ps.batch, ps.M, ps.N, ps.K, sc0);
+      if (!ps.tc && !stream_ok) continue;
       const TuneKey key{dev, p->opts.precision, ps.batch, ps.M, ps.N, ps.K, ps.row_major ? 0 : 1};
       {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto f = g_tune_cache.find(key);
-        if (f != g_tune_cache.end()) {
+        // (a preset of the stream kernel for a product it does not support
+        // is not taken: the step is timed instead)
+        if (f != g_tune_cache.end() && (f->second.simt != 2 || stream_ok)) {
           ps.tc_pair = f->second.pair;
           ps.tc_ksplit = f->second.ksplit;
           ps.tc_simt = f->second.simt;
@@ -1121,10 +1133,12 @@ static void autotune_tc_steps(tz_plan *p) {
           continue;
         }
       }
-      std::vector<int> pairs = {0};
-      if (dev::tc_pair_supported(p->opts.precision, ps.M, ps.N)) pairs.push_back(1);
+      std::vector<int> pairs;
+      if (ps.tc) pairs.push_back(0);
+      if (ps.tc && dev::tc_pair_supported(p->opts.precision, ps.M, ps.N)) pairs.push_back(1);
       std::vector<int> splits = {0};
-      if (ps.row_major && dev::cgemm_tc_split(p->opts.precision, ps.batch, ps.M, ps.N, ps.K) > 1) splits.push_back(1);
+      if (ps.tc && ps.row_major && dev::cgemm_tc_split(p->opts.precision, ps.batch, ps.M, ps.N, ps.K) > 1)
+        splits.push_back(1);
       const float2 *X = (const float2 *)tensor_ptr(p, ctx, ps.opX);
       const float2 *Y = (const float2 *)tensor_ptr(p, ctx, ps.opY);
       float2 *C = (float2 *)tensor_ptr(p, ctx, ps.c_nat >= 0 ? ps.c_nat : ps.c);
@@ -1151,13 +1165,24 @@ static void autotune_tc_steps(tz_plan *p) {
           });
           if (ms < best.ms) best = TuneChoice{pr, ks, 0, ms};
         }
+      const int force = g_tune_force_simt.load();
       if (ps.K <= kTuneSimtMaxK) {
+        // the tiled CUDA-core kernel: simt = 1 on the tensor-core path, the
+        // step's own kernel (0) otherwise
         const float ms = time_it([&] {
           cuda_check(dev::launch_cgemm_simt(X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.M * ps.K, ps.N * ps.K,
                                             ps.M * ps.N, sc, s),
                      "autotune launch");
         });
-        if (ms < best.ms || g_tune_force_simt.load()) best = TuneChoice{-1, 0, 1, ms};
+        if (ms < best.ms || (force == 1 && ps.tc)) best = TuneChoice{-1, 0, ps.tc ? 1 : 0, ms};
+      }
+      if (stream_ok) {
+        const float ms = time_it([&] {
+          cuda_check(dev::launch_cgemm_stream(X, Y, C, ps.batch, ps.M, ps.N, ps.K, ps.M * ps.K, ps.N * ps.K,
+                                              ps.M * ps.N, sc, s),
+                     "autotune launch");
+        });
+        if ((ms < best.ms && force != 1) || force == 2) best = TuneChoice{-1, 0, 2, ms};
       }
       ps.tc_pair = best.pair;
       ps.tc_ksplit = best.ksplit;

@@ -35,8 +35,9 @@ struct PStep {
   int64_t tc_scratch_off = -1;
   int tc_pair = -1;           // tensor-core launch choice (autotuned at bind): pairs of
   int tc_ksplit = 0;          // CTAs (1/0, -1 default) and K split (1 none, 0 default)
-  int tc_simt = 0;            // 1: the autotuner found the CUDA-core complex64 kernel
-                              // faster for this (small-K) step
+  int tc_simt = 0;            // autotuned kernel of a small-K step: 1 the tiled CUDA-core
+                              // complex64 kernel (tensor-core steps), 2 the stream kernel
+                              // (any complex64 step it supports), 0 the step's own
   dev::CScatter scatter{};    // where the GEMM writes its result
   bool row_major = false;     // scatter is the plain row-major order
   int c_nat = -1;             // tensor the GEMM writes in row-major order when a

@@ -216,10 +216,11 @@ def test_autotuned_plan_matches_oracle(tz, prec):
     plan.bind()
     st = plan.stats()
     steps = [s for s in json.loads(plan.describe())["steps"] if s.get("var") and s.get("gemm") and s.get("tc")]
-    assert steps and st["n_tuned_steps"] == len(steps)
-    # each step: a tensor-core launch form, or (K <= 32) the CUDA-core kernel
+    # small-K CUDA-core steps are tuned too (tiled or stream kernel)
+    assert steps and st["n_tuned_steps"] >= len(steps)
+    # each step: a tensor-core launch form, or (K <= 32) a CUDA-core kernel
     assert all((s["tc_simt"] == 0 and s["tc_pair"] in (0, 1) and s["tc_ksplit"] in (0, 1)) or
-               (s["tc_simt"] == 1 and s["K"] <= 32) for s in steps)
+               (s["tc_simt"] in (1, 2) and s["K"] <= 32) for s in steps)
     print(f"{prec}: tuned {len(steps)} steps, pairs chosen for {sum(s['tc_pair'] == 1 for s in steps)}, "
           f"CUDA cores for {sum(s['tc_simt'] for s in steps)}")
     got = tz.tz_contract_amplitudes(plan, bits)
@@ -274,7 +275,7 @@ def test_autotuner_presets_reproduce_choices(tz):
     want = []
     for s in first:
         if s["K"] <= 32:
-            simt = 1 - s["tc_simt"]
+            simt = 1 if s["tc_simt"] != 1 else 0
             pair = 0
         else:
             simt = 0
@@ -292,3 +293,39 @@ def test_autotuner_presets_reproduce_choices(tz):
     assert rel_err(a2, a1, 49) <= TOL_C64
     with pytest.raises(tz.TzError):
         tz.tz_tune_preset("fp16x3", 1, 128, 64, 64, 0, 0, 0, 1)   # the CUDA-core kernel only for k <= 32
+
+
+@pytest.mark.parametrize("prec,rows,cols,t,seed,g", [("c64", 7, 7, 16, 2, 6), ("fp16x3", 7, 7, 16, 2, 6),
+                                                     ("c64", 6, 6, 18, 9, 4), ("fp16x3", 6, 6, 18, 9, 4),
+                                                     ("c64", 5, 5, 24, 3, 2)])
+def test_stream_kernel_matches_tiled_kernel(tz, prec, rows, cols, t, seed, g):
+    """The stream kernel for small-K products (K <= 32, outputs written in
+    address order) sums in the same order and FP32 arithmetic as the tiled
+    CUDA-core kernel: a plan autotuned with every small-K step forced onto it
+    gives bit-identical amplitudes to the same plan with those steps forced
+    onto the tiled kernel, and both match the oracle."""
+    import json
+    n = rows * cols
+    spec = grid_spec(rows, cols, t, seed)
+    bits = ti.random_bitstrings(n, 1 << g, 13)
+    net = tz.tz_network_from_circuit(tz.tz_circuit_from_spec(spec), g)
+    tree = tz.tz_path_greedy(net, restarts=16, seed=7, algorithm="elimination", precision=prec)
+    got, n_stream = {}, 0
+    try:
+        for force in (1, 2):
+            tz.tz_debug_tune_force_simt(force)
+            plan = tz.tz_plan_create(net, tree, [], precision=prec, max_bitstrings=1 << g, autotune=True)
+            plan.bind()
+            steps = [s for s in json.loads(plan.describe())["steps"] if s["var"] and s["gemm"]]
+            if force == 2:
+                n_stream = sum(s["tc_simt"] == 2 for s in steps)
+            else:
+                assert not any(s["tc_simt"] == 2 for s in steps)
+            got[force] = tz.tz_contract_amplitudes(plan, bits)
+            plan.close()
+    finally:
+        tz.tz_debug_tune_force_simt(0)
+    assert n_stream > 0
+    assert np.array_equal(got[1], got[2])
+    ref = np.array([tn.Contractor(spec, max_log2=24).amplitude(x) for x in bits[:8]])
+    assert rel_err(got[2][:8], ref, n) <= TOL_C64
