@@ -436,7 +436,14 @@ struct StreamTile {
   int8_t rsrc[kStreamMaxLocal];     // rank bit r: 0 batch, 1 row, 2 column
   int8_t rbit[kStreamMaxLocal];     // its bit within that index
   int8_t rpos[kStreamMaxLocal];     // its output position
+  int8_t lane_rank[32];             // rank (within its warp's 32) that lane l computes
 };
+// Shared-memory layout of the staged rows: a row of KMAX values takes
+// KMAX / 2 + 1 chunks of 16 bytes (an odd count, so 8 consecutive rows start
+// in 8 different banks), and each block of rows with the same batch bits is
+// shifted by one more chunk (rows that differ only in batch bits would
+// otherwise share banks). shift = log2 of the rows per batch value.
+__host__ __device__ inline int stream_row_chunk(int row, int ch, int shift) { return row * (ch + 1) + (row >> shift); }
 
 template <int KMAX>
 __global__ void __launch_bounds__(256)
@@ -450,9 +457,9 @@ __global__ void __launch_bounds__(256)
   constexpr int CH = KMAX / 2;
   const int rowsA = 1 << (st.bz + st.bm), rowsB = 1 << (st.bz + st.bn);
   float4 *As4 = stream_smem;
-  float4 *Bs4 = As4 + (size_t)rowsA * CH + (1 << st.bz);
-  auto rowA = [&](int row) { return As4 + row * CH + (row >> st.bm); };
-  auto rowB = [&](int row) { return Bs4 + row * CH + (row >> st.bn); };
+  float4 *Bs4 = As4 + (size_t)rowsA * (CH + 1) + (1 << st.bz);
+  auto rowA = [&](int row) { return As4 + stream_row_chunk(row, CH, st.bm); };
+  auto rowB = [&](int row) { return Bs4 + stream_row_chunk(row, CH, st.bn); };
   // the rank bits from 8 up, decoded once per launch: entry j holds the local
   // batch, row and column bits and the output offset of rank j * 256
   __shared__ int s_hz[1 << (kStreamMaxLocal - 8)], s_hm[1 << (kStreamMaxLocal - 8)],
@@ -481,10 +488,15 @@ __global__ void __launch_bounds__(256)
   for (int t = threadIdx.x; t < total; t += 256)
     s_pos[t] = t < gz ? sc.pb[t] : t < gz + gm ? sc.pm[t - gz] : sc.pn[t - gz - gm];
   // the rank bits below 8 come from the thread
+  // the thread's rank within its block of 256: the warp's 32 ranks are a
+  // fixed permutation of its lanes (chosen on the host so that the lanes a
+  // shared-memory phase serves read rows in different banks); the warp
+  // still writes one contiguous run
+  const int trank = (int)(threadIdx.x & ~31u) | st.lane_rank[threadIdx.x & 31];
   int tz0 = 0, tm0 = 0, tn0 = 0;
   int64_t to0 = 0;
   for (int r = 0; r < st.nl && r < 8; r++)
-    if ((threadIdx.x >> r) & 1) {
+    if ((trank >> r) & 1) {
       const int v = 1 << st.rbit[r];
       if (st.rsrc[r] == 0) tz0 |= v;
       else if (st.rsrc[r] == 1) tm0 |= v;
@@ -547,7 +559,7 @@ __global__ void __launch_bounds__(256)
       rowB(row)[c] = v;
     }
     __syncthreads();
-    if ((int)threadIdx.x >= R) continue;
+    if (trank >= R) continue;
     // (keeping a thread's rows in registers across its outputs measured
     // slower: the registers cost more occupancy than the reads they save)
     for (int rr = 0; rr < R; rr += 256) {
@@ -590,7 +602,8 @@ bool stream_tile(int64_t batch, int64_t M, int64_t N, int64_t K, const CScatter 
       owner[pos[x][j]] = {x, j};
     }
   auto fits = [&](const int *b) {
-    return ((int64_t(1) << (b[0] + b[1])) + (int64_t(1) << (b[0] + b[2]))) * *kmax + (int64_t(4) << b[0]) <= budget &&
+    return ((int64_t(1) << (b[0] + b[1])) + (int64_t(1) << (b[0] + b[2]))) * (*kmax + 2) + (int64_t(4) << b[0]) <=
+               budget &&
            b[0] + b[1] + b[2] <= kStreamMaxLocal;
   };
   int b[3] = {0, 0, 0};
@@ -628,7 +641,66 @@ bool stream_tile(int64_t batch, int64_t M, int64_t N, int64_t K, const CScatter 
       r++;
     }
   }
-  return r == t->nl;
+  if (r != t->nl) return false;
+  // lanes of a warp: a shared-memory phase of 128-bit loads serves 8
+  // consecutive lanes, and its cost is the largest number of different rows
+  // that fall in one 16-byte bank group. Ranks are dealt to lanes to keep
+  // that low for both operands (pairwise swaps while the cost drops); the
+  // pattern is the same in every warp and for every chunk of the rows.
+  for (int l = 0; l < 32; l++) t->lane_rank[l] = (int8_t)l;
+  if (t->nl >= 5) {
+    const int ch = *kmax / 2;
+    int slot[2][32], row[2][32];
+    for (int q = 0; q < 32; q++) {
+      int lz = 0, lm = 0, ln = 0;
+      for (int j = 0; j < 5; j++)
+        if ((q >> j) & 1) {
+          const int v = 1 << t->rbit[j];
+          if (t->rsrc[j] == 0) lz |= v;
+          else if (t->rsrc[j] == 1) lm |= v;
+          else ln |= v;
+        }
+      row[0][q] = (lz << t->bm) | lm;
+      row[1][q] = (lz << t->bn) | ln;
+      slot[0][q] = stream_row_chunk(row[0][q], ch, t->bm) & 7;
+      slot[1][q] = stream_row_chunk(row[1][q], ch, t->bn) & 7;
+    }
+    auto phase_cost = [&](int ph) {
+      int c = 0;
+      for (int o = 0; o < 2; o++) {
+        int worst = 0;
+        for (int sl = 0; sl < 8; sl++) {
+          int rows_here[8], nr = 0;
+          for (int l = 8 * ph; l < 8 * ph + 8; l++) {
+            const int q = t->lane_rank[l];
+            if (slot[o][q] != sl) continue;
+            bool seen = false;
+            for (int i = 0; i < nr; i++) seen |= rows_here[i] == row[o][q];
+            if (!seen) rows_here[nr++] = row[o][q];
+          }
+          worst = std::max(worst, nr);
+        }
+        c += worst;
+      }
+      return c;
+    };
+    for (int pass = 0; pass < 8; pass++) {
+      bool better = false;
+      for (int a = 0; a < 32; a++)
+        for (int b = a + 1; b < 32; b++) {
+          if ((a >> 3) == (b >> 3)) continue;
+          const int before = phase_cost(a >> 3) + phase_cost(b >> 3);
+          std::swap(t->lane_rank[a], t->lane_rank[b]);
+          if (phase_cost(a >> 3) + phase_cost(b >> 3) < before) {
+            better = true;
+          } else {
+            std::swap(t->lane_rank[a], t->lane_rank[b]);
+          }
+        }
+      if (!better) break;
+    }
+  }
+  return true;
 }
 
 CScatter row_major_map(int64_t batch, int64_t M, int64_t N) {
@@ -659,7 +731,7 @@ cudaError_t launch_cgemm_stream(const float2 *A, const float2 *B, float2 *C, int
   StreamTile t{};
   int kmax = 0;
   if (batch * M * N < 256 || !stream_tile(batch, M, N, K, map, &t, &kmax)) return cudaErrorNotSupported;
-  const size_t smem = ((((size_t)1 << (t.bz + t.bm)) + ((size_t)1 << (t.bz + t.bn))) * kmax / 2 +
+  const size_t smem = ((((size_t)1 << (t.bz + t.bm)) + ((size_t)1 << (t.bz + t.bn))) * (kmax / 2 + 1) +
                        ((size_t)2 << t.bz)) * sizeof(float4);
   const int64_t tiles = batch * M * N >> t.nl;
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, 152 * 8);
