@@ -298,7 +298,7 @@ def test_autotuner_presets_reproduce_choices(tz):
 @pytest.mark.parametrize("prec,rows,cols,t,seed,g", [("c64", 7, 7, 16, 2, 6), ("fp16x3", 7, 7, 16, 2, 6),
                                                      ("c64", 6, 6, 18, 9, 4), ("fp16x3", 6, 6, 18, 9, 4),
                                                      ("c64", 5, 5, 24, 3, 2)])
-def test_stream_kernel_matches_tiled_kernel(tz, prec, rows, cols, t, seed, g):
+def test_stream_kernel_matches_tiled_kernel(tz, prec, rows, cols, t, seed, g, small=0):
     """The stream kernel for small-K products (K <= 32, outputs written in
     address order) sums in the same order and FP32 arithmetic as the tiled
     CUDA-core kernel: a plan autotuned with every small-K step forced onto it
@@ -314,7 +314,8 @@ def test_stream_kernel_matches_tiled_kernel(tz, prec, rows, cols, t, seed, g):
     try:
         for force in (1, 2):
             tz.tz_debug_tune_force_simt(force)
-            plan = tz.tz_plan_create(net, tree, [], precision=prec, max_bitstrings=1 << g, autotune=True)
+            plan = tz.tz_plan_create(net, tree, [], precision=prec, max_bitstrings=1 << g, autotune=True,
+                                     small_log2=small)
             plan.bind()
             steps = [s for s in json.loads(plan.describe())["steps"] if s["var"] and s["gemm"]]
             if force == 2:
@@ -329,3 +330,14 @@ def test_stream_kernel_matches_tiled_kernel(tz, prec, rows, cols, t, seed, g):
     assert np.array_equal(got[1], got[2])
     ref = np.array([tn.Contractor(spec, max_log2=24).amplitude(x) for x in bits[:8]])
     assert rel_err(got[2][:8], ref, n) <= TOL_C64
+
+
+
+@pytest.mark.parametrize("prec,rows,cols,t,seed,g,small", [("c64", 5, 5, 16, 3, 3, 4), ("c64", 6, 6, 14, 2, 2, 6),
+                                                           ("fp16x3", 6, 6, 16, 4, 3, 6)])
+def test_stream_kernel_short_sums(tz, prec, rows, cols, t, seed, g, small):
+    """Plans cut with a low direct-step threshold hold many products with
+    K = 1, 2 and 4 (outer products and short sums; K = 1 takes the kernel's
+    element loads, since its rows are not 16-byte aligned): forced onto the
+    stream kernel they match the tiled kernel bit for bit and the oracle."""
+    test_stream_kernel_matches_tiled_kernel(tz, prec, rows, cols, t, seed, g, small)
