@@ -151,40 +151,35 @@ __device__ __forceinline__ void direct_block(const DStep &st, int64_t blk, const
   if (active && part == 0) Cp[c] = acc;
 }
 
-// One launch per dependency level: block b of the launch belongs to the step
-// whose block range holds b.
-__device__ __forceinline__ int step_of_block(const DStep *steps, int n_steps, int64_t blk) {
-  int lo = 0, hi = n_steps - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (steps[mid].block_begin <= blk)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
+// A block's step descriptor, staged in shared memory by 12 threads at once
+// (its fields are then read by every thread without further global loads).
+__device__ __forceinline__ void stage_step(DStep *dst, const DStep *src) {
+  static_assert(sizeof(DStep) % 16 == 0 && sizeof(DStep) / 16 <= 32, "DStep staged in 16-byte pieces");
+  if (threadIdx.x < sizeof(DStep) / 16)
+    reinterpret_cast<uint4 *>(dst)[threadIdx.x] = reinterpret_cast<const uint4 *>(src)[threadIdx.x];
 }
 
+// One launch per dependency level: block b of the launch belongs to step
+// bmap[b].
 template <typename T>
-__global__ void __launch_bounds__(256) direct_kernel(const DStep *steps, int n_steps, const char *cbase,
+__global__ void __launch_bounds__(256) direct_kernel(const DStep *steps, const int *bmap, const char *cbase,
                                                      char *abase) {
-  __shared__ int s_idx;
+  __shared__ __align__(16) DStep s_st;
   __shared__ T red[256];
   const int64_t blk = blockIdx.x;
-  if (threadIdx.x == 0) s_idx = step_of_block(steps, n_steps, blk);
+  stage_step(&s_st, steps + bmap[blk]);
   __syncthreads();
-  const DStep &st = steps[s_idx];
-  direct_block<T>(st, blk - st.block_begin, cbase, abase, red);
+  direct_block<T>(s_st, blk - s_st.block_begin, cbase, abase, red);
 }
 
-cudaError_t launch_direct(const DStep *steps, int n_steps, int64_t total_blocks, const char *cbase, char *abase,
-                          int dbl, cudaStream_t s) {
+cudaError_t launch_direct(const DStep *steps, int n_steps, const int *bmap, int64_t total_blocks, const char *cbase,
+                          char *abase, int dbl, cudaStream_t s) {
   if (n_steps <= 0) return cudaSuccess;
-  if (total_blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (total_blocks > 0x7fffffffLL || !bmap) return cudaErrorInvalidValue;
   if (dbl)
-    direct_kernel<double2><<<(unsigned)total_blocks, 256, 0, s>>>(steps, n_steps, cbase, abase);
+    direct_kernel<double2><<<(unsigned)total_blocks, 256, 0, s>>>(steps, bmap, cbase, abase);
   else
-    direct_kernel<float2><<<(unsigned)total_blocks, 256, 0, s>>>(steps, n_steps, cbase, abase);
+    direct_kernel<float2><<<(unsigned)total_blocks, 256, 0, s>>>(steps, bmap, cbase, abase);
   return cudaGetLastError();
 }
 
@@ -250,6 +245,7 @@ __global__ void __launch_bounds__(256) direct_queue_kernel(const DStep *steps, i
                                                            unsigned *ctrl, int *err) {
   __shared__ int s_idx, s_go, s_last;
   __shared__ int64_t s_blk;
+  __shared__ __align__(16) DStep s_st;
   __shared__ T red[256];
   unsigned *done = ctrl + 4;
   const unsigned long long limit = g_dq_wait_ns;
@@ -277,8 +273,9 @@ __global__ void __launch_bounds__(256) direct_queue_kernel(const DStep *steps, i
     }
     __syncthreads();
     if (!s_go) break;
-    const DStep &st = steps[s_idx];
-    direct_block<T>(st, s_blk - st.block_begin, cbase, abase, red);
+    stage_step(&s_st, steps + s_idx);
+    __syncthreads();
+    direct_block<T>(s_st, s_blk - s_st.block_begin, cbase, abase, red);
     __syncthreads();  // every result of this block is written
     if (threadIdx.x == 0) {
       __threadfence();

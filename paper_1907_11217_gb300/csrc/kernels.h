@@ -117,8 +117,9 @@ cudaError_t launch_init_state(GroupState *gs, int64_t lo, int64_t hi, int64_t n_
 // dbl: tensors are complex128 (else complex64)
 cudaError_t launch_leaf_build(const LeafJob *jobs, int n_jobs, const GroupState *gs, const uint8_t *bits, int nq,
                               int g, const char *cbase, char *abase, int dbl, cudaStream_t s);
-cudaError_t launch_direct(const DStep *steps, int n_steps, int64_t total_blocks, const char *cbase, char *abase,
-                          int dbl, cudaStream_t s);
+// bmap: the step (index from steps) of each of the launch's blocks.
+cudaError_t launch_direct(const DStep *steps, int n_steps, const int *bmap, int64_t total_blocks, const char *cbase,
+                          char *abase, int dbl, cudaStream_t s);
 // The same steps in one persistent launch over a device work queue: blocks
 // take the launch's blocks in order from a ticket counter, and a block whose
 // step reads the result of an earlier step of the same launch (DStep::dep)

@@ -621,12 +621,13 @@ tz_plan *plan_create(const Network &net, const Pairs &pairs, const std::vector<i
             }
       }
       it.blocks = b;
+      // the step of each block of the launch (one load instead of a search)
+      it.bmap_off = (int64_t)p->bmap.size() * 4;
+      for (int d = it.first; d < it.first + it.count; d++)
+        p->bmap.insert(p->bmap.end(), (size_t)p->dsteps[d].nblk, d - it.first);
       if (it.queue) {
         it.ctrl_off = queue_words * 4;
         queue_words += dev::direct_queue_ctrl_words(it.count);
-        it.bmap_off = (int64_t)p->bmap.size() * 4;
-        for (int d = it.first; d < it.first + it.count; d++)
-          p->bmap.insert(p->bmap.end(), (size_t)p->dsteps[d].nblk, d - it.first);
       }
     }
   // leaf jobs
@@ -964,7 +965,9 @@ static void run_items(tz_plan *p, const std::vector<Item> &items, const RunCtx &
                      "direct step queue");
         else
           cuda_check(dev::launch_direct(reinterpret_cast<const dev::DStep *>(p->ws + p->off_dsteps) + it.first,
-                                        it.count, it.blocks, cbase, abase, p->esz == 16, s),
+                                        it.count,
+                                        reinterpret_cast<const int *>(p->ws + p->off_bmap + it.bmap_off),
+                                        it.blocks, cbase, abase, p->esz == 16, s),
                      "direct steps");
         break;
       case IT_PERMUTE: {

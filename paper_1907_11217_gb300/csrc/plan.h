@@ -53,7 +53,7 @@ struct Item {
   int64_t blocks = 0;         // DIRECT: total blocks
   bool queue = false;         // DIRECT: one queue launch over dependent steps
   int64_t ctrl_off = -1;      // DIRECT queue: its counters in the scratch part's queue area
-  int64_t bmap_off = -1;      // DIRECT queue: its block -> step map (int32) in the resident bmap table
+  int64_t bmap_off = -1;      // DIRECT: its block -> step map (int32) in the resident bmap table
 };
 
 }  // namespace tz
@@ -79,7 +79,7 @@ struct tz_plan {
   // constants], then one scratch part [group state | bitstrings | FP64
   // accumulator | group arena]; a query can also run in another scratch part
   size_t off_dsteps = 0, off_jobs = 0, off_bmap = 0, off_const = 0, off_scratch = 0;
-  std::vector<int32_t> bmap;       // queue launches: step of each block, from the launch's first step
+  std::vector<int32_t> bmap;       // direct launches: step of each block, from the launch's first step
   size_t s_gs = 0, s_bits = 0, s_acc = 0, s_arena = 0;  // offsets within a scratch part
   size_t s_queue = 0, queue_bytes = 0;  // counters of the direct-step queue launches
   size_t const_bytes = 0, arena_bytes = 0, resident_bytes = 0, scratch_bytes = 0, total_bytes = 0;
