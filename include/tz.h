@@ -441,6 +441,16 @@ int tz_debug_tune_force_simt(int on);
  * differ. TZ_EINVAL for bad values. */
 int tz_tune_preset(int precision, int64_t batch, int64_t m, int64_t n, int64_t k, int scatter, int pair, int ksplit,
                    int simt);
+/* Test hook (host only, no device work): the tile the stream kernel would use
+ * for a product of batch x m x n with k summed values (dimensions powers of
+ * two), C row-major (scatter = 0) or written through the scatter map whose
+ * output positions of the batch, row and column bits are pb, pm, pn
+ * (log2 batch, log2 m, log2 n entries). *supported = 0 where the kernel does
+ * not apply; else out (86 int32) = {bz, bm, bn, nl, kmax, dynamic shared
+ * bytes; for each of 16 rank bits: source (0 batch, 1 row, 2 column, -1
+ * none), bit, output position; the rank of each of the 32 lanes}. */
+int tz_debug_stream_tile(int64_t batch, int64_t m, int64_t n, int64_t k, int scatter, const int8_t *pb,
+                         const int8_t *pm, const int8_t *pn, int32_t *out, int *supported);
 
 /* Process-wide default of how the split BF16 / FP16 products run where the
  * shape allows pairs (128-column tiles, m a multiple of 256): 1 on pairs of

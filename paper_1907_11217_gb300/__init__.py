@@ -27,7 +27,7 @@ __all__ = [
     "tz_tree_from_pairs", "tz_slice_select", "tz_plan_create", "tz_contract_amplitudes",
     "tz_contract_amplitudes_device", "tz_op_permute", "tz_op_cgemm", "tz_op_accumulate", "PRECISIONS",
     "tz_plan_status", "tz_op_cgemm_status", "tz_op_cgemm_static_status", "tz_debug_set_wait_limit",
-    "tz_debug_stall_tensor_core", "tz_debug_stall_direct_queue", "tz_tune_tc_pairs", "tz_tune_tc_prefetch", "tz_debug_tune_force_simt", "tz_tune_preset",
+    "tz_debug_stall_tensor_core", "tz_debug_stall_direct_queue", "tz_tune_tc_pairs", "tz_tune_tc_prefetch", "tz_debug_tune_force_simt", "tz_tune_preset", "tz_debug_stream_tile",
     "TZ_C64_SIMT", "TZ_TF32X3", "TZ_BF16X3", "TZ_FP16X3",
 ]
 
@@ -357,6 +357,25 @@ def tz_tune_preset(precision, batch, m, n, k, scatter, pair, ksplit, simt):
     """Preset one autotuner cache entry on the current device (see tz.h)."""
     check(lib().tz_tune_preset(PRECISIONS.get(precision, precision), int(batch), int(m), int(n), int(k),
                                int(scatter), int(pair), int(ksplit), int(simt)))
+
+
+def tz_debug_stream_tile(batch, m, n, k, pb=None, pm=None, pn=None):
+    """Test hook (host only): the stream kernel's tile for a product, as a
+    dict, or None where the kernel does not apply. pb, pm, pn: output
+    positions of the batch, row and column bits (None: C row-major)."""
+    out = (ctypes.c_int32 * 86)()
+    sup = ctypes.c_int()
+    scatter = pb is not None
+    arrs = [np.ascontiguousarray(np.asarray(x if x is not None else [0], dtype=np.int8)) for x in (pb, pm, pn)]
+    ptrs = [a.ctypes.data_as(ctypes.c_void_p) for a in arrs]
+    check(lib().tz_debug_stream_tile(int(batch), int(m), int(n), int(k), int(scatter), *ptrs,
+                                     ctypes.cast(out, ctypes.c_void_p), ctypes.byref(sup)))
+    if not sup.value:
+        return None
+    v = list(out)
+    ranks = [(v[6 + 3 * r], v[7 + 3 * r], v[8 + 3 * r]) for r in range(16) if v[6 + 3 * r] >= 0]
+    return {"bz": v[0], "bm": v[1], "bn": v[2], "nl": v[3], "kmax": v[4], "smem": v[5], "ranks": ranks,
+            "lane_rank": v[54:86]}
 
 
 def tz_debug_tune_force_simt(on):

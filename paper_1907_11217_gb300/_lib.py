@@ -128,6 +128,7 @@ SIGNATURES = {
     "tz_tune_tc_prefetch": (c_int, [c_int]),
     "tz_debug_tune_force_simt": (c_int, [c_int]),
     "tz_tune_preset": (c_int, [c_int, c_int64, c_int64, c_int64, c_int64, c_int, c_int, c_int, c_int]),
+    "tz_debug_stream_tile": (c_int, [c_int64, c_int64, c_int64, c_int64, c_int, P, P, P, P, P]),
 }
 
 _lib = None

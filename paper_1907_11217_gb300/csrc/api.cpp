@@ -610,6 +610,27 @@ int tz_tune_preset(int precision, int64_t batch, int64_t m, int64_t n, int64_t k
   TZ_CATCH
 }
 
+int tz_debug_stream_tile(int64_t batch, int64_t m, int64_t n, int64_t k, int scatter, const int8_t *pb,
+                         const int8_t *pm, const int8_t *pn, int32_t *out, int *supported) {
+  TZ_TRY
+  REQUIRE(out && supported, "NULL argument");
+  REQUIRE(batch >= 1 && m >= 1 && n >= 1 && k >= 1, "dimensions must be >= 1");
+  tz::dev::CScatter sc{};
+  if (scatter) {
+    REQUIRE(pb && pm && pn, "NULL scatter positions");
+    auto lg = [](int64_t v) { int b = 0; while ((int64_t(1) << b) < v) b++; return b; };
+    sc.nb = lg(batch);
+    sc.nm = lg(m);
+    sc.nn = lg(n);
+    REQUIRE(sc.nb + sc.nm + sc.nn <= tz::dev::kMaxBits, "too many index bits");
+    for (int j = 0; j < sc.nb; j++) sc.pb[j] = pb[j];
+    for (int j = 0; j < sc.nm; j++) sc.pm[j] = pm[j];
+    for (int j = 0; j < sc.nn; j++) sc.pn[j] = pn[j];
+  }
+  *supported = tz::dev::cgemm_stream_describe(batch, m, n, k, scatter ? &sc : nullptr, out);
+  TZ_CATCH
+}
+
 int tz_debug_tune_force_simt(int on) {
   TZ_TRY
   tz::tune_force_simt(on);

@@ -724,6 +724,26 @@ bool cgemm_stream_supported(int64_t batch, int64_t M, int64_t N, int64_t K, cons
   return stream_tile(batch, M, N, K, sc ? *sc : row_major_map(batch, M, N), &t, &kmax);
 }
 
+int cgemm_stream_describe(int64_t batch, int64_t M, int64_t N, int64_t K, const CScatter *sc, int32_t *out) {
+  StreamTile t{};
+  int kmax = 0;
+  if (batch * M * N < 256 || !stream_tile(batch, M, N, K, sc ? *sc : row_major_map(batch, M, N), &t, &kmax)) return 0;
+  out[0] = t.bz;
+  out[1] = t.bm;
+  out[2] = t.bn;
+  out[3] = t.nl;
+  out[4] = kmax;
+  out[5] = (int32_t)(((((int64_t)1 << (t.bz + t.bm)) + ((int64_t)1 << (t.bz + t.bn))) * (kmax / 2 + 1) +
+                      ((int64_t)2 << t.bz)) * 16);
+  for (int r = 0; r < kStreamMaxLocal; r++) {
+    out[6 + 3 * r] = r < t.nl ? t.rsrc[r] : -1;
+    out[7 + 3 * r] = r < t.nl ? t.rbit[r] : -1;
+    out[8 + 3 * r] = r < t.nl ? t.rpos[r] : -1;
+  }
+  for (int l = 0; l < 32; l++) out[6 + 3 * kStreamMaxLocal + l] = t.lane_rank[l];
+  return 1;
+}
+
 cudaError_t launch_cgemm_stream(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N,
                                 int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s) {
   if (sA != M * K || sB != N * K || (!sc && sC != M * N)) return cudaErrorNotSupported;

@@ -157,6 +157,11 @@ cudaError_t launch_cgemm_simt(const float2 *A, const float2 *B, float2 *C, int64
 bool cgemm_stream_supported(int64_t batch, int64_t M, int64_t N, int64_t K, const CScatter *sc);
 cudaError_t launch_cgemm_stream(const float2 *A, const float2 *B, float2 *C, int64_t batch, int64_t M, int64_t N,
                                 int64_t K, int64_t sA, int64_t sB, int64_t sC, const CScatter *sc, cudaStream_t s);
+// Host-side tile of the stream kernel (no device work): 1 and out[] =
+// {bz, bm, bn, nl, kmax, dynamic shared bytes, then per rank bit r < 16:
+// source (0 batch, 1 row, 2 column, -1 none), bit, output position; then the
+// 32 lanes' ranks}, or 0 where the kernel does not apply.
+int cgemm_stream_describe(int64_t batch, int64_t M, int64_t N, int64_t K, const CScatter *sc, int32_t *out);
 // Skinny product (n <= 4, k <= 16) reading X and Y through gather maps and
 // writing C through sc (nullptr: row-major [batch][m][n]).
 cudaError_t launch_cgemm_skinny_gather(const float2 *X, const float2 *Y, float2 *C, int64_t batch, int64_t M,

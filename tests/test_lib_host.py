@@ -387,3 +387,82 @@ def test_direct_queue_schedule(tz, rows, cols, t, seed, small, prec):
             for x in ins:
                 pi, _ = prod.get(x, (None, -1))
                 assert pi is None or pi < i
+
+
+
+def _stream_cases():
+    rng = np.random.default_rng(5)
+    cases = [(1024, 4096, 8, 4, None), (512, 2048, 256, 8, None), (32, 512, 128, 32, None), (1, 256, 1, 1, None)]
+    for _ in range(24):
+        gz, gm, gn = rng.integers(0, 7), rng.integers(1, 12), rng.integers(0, 9)
+        total = gz + gm + gn
+        pos = rng.permutation(total)
+        cases.append((1 << gz, 1 << gm, 1 << gn, int(rng.choice([1, 2, 4, 8, 16, 32])),
+                      (pos[:gz], pos[gz:gz + gm], pos[gz + gm:])))
+    return cases
+
+
+@pytest.mark.parametrize("case", range(28))
+def test_stream_tile_invariants(tz, case):
+    """Host side of the stream kernel for small-K products: its tile covers
+    the lowest output positions it can, ranks follow output positions, the
+    lanes get a permutation of the warp's ranks, shared memory stays within
+    40 KB, and (emulating the kernel's index arithmetic) every output of a
+    tile is written once, each warp's 32 outputs forming one contiguous run
+    when the 5 lowest positions are in the tile."""
+    batch, m, n, k, maps = _stream_cases()[case]
+    gz, gm, gn = (int(np.log2(x)) for x in (batch, m, n))
+    total = gz + gm + gn
+    if maps is None:
+        pb, pm, pn = (list(range(gn + gm, total)), list(range(gn, gn + gm)), list(range(gn)))
+        t = tz.tz_debug_stream_tile(batch, m, n, k)
+    else:
+        pb, pm, pn = (list(map(int, x)) for x in maps)
+        t = tz.tz_debug_stream_tile(batch, m, n, k, pb, pm, pn)
+    if batch * m * n < 256:
+        assert t is None
+        return
+    assert t is not None
+    pos_of = {0: pb, 1: pm, 2: pn}
+    local = {0: t["bz"], 1: t["bm"], 2: t["bn"]}
+    assert t["nl"] == sum(local.values()) == len(t["ranks"]) and t["smem"] <= 40 * 1024
+    assert t["kmax"] >= k and t["kmax"] in (4, 8, 16, 32)
+    # ranks: exactly the local bits, in increasing output position
+    assert sorted((s, b) for s, b, _ in t["ranks"]) == sorted((s, b) for s in range(3) for b in range(local[s]))
+    assert all(pos_of[s][b] == p for s, b, p in t["ranks"])
+    assert [p for _, _, p in t["ranks"]] == sorted(p for _, _, p in t["ranks"])
+    covered = 0
+    while covered < total and any(p == covered for _, _, p in t["ranks"]):
+        covered += 1
+    # covering one more of the 6 lowest positions would not fit in 40 KB
+    if covered < min(total, 6):
+        owner = {}
+        for s_, pos in pos_of.items():
+            for b, p in enumerate(pos):
+                owner[p] = (s_, b)
+        need = [0, 0, 0]
+        for p in range(covered + 1):
+            s_, b = owner[p]
+            need[s_] = max(need[s_], b + 1)
+        rows = (1 << (need[0] + need[1])) + (1 << (need[0] + need[2]))
+        assert rows * (t["kmax"] + 2) + (4 << need[0]) > 40 * 1024 // 8 or sum(need) > 16
+    assert sorted(t["lane_rank"]) == list(range(32)) if t["nl"] >= 5 else t["lane_rank"] == list(range(32))
+    # emulate one tile: thread rank, high rank bits, output offsets
+    R = 1 << t["nl"]
+    offs = []
+    for rr in range(0, max(R, 256), 256):
+        for w in range(8):
+            warp = []
+            for lane in range(32):
+                rank = w * 32 + t["lane_rank"][lane] + rr
+                if rank >= R:
+                    continue
+                o = sum(1 << p for r, (_, _, p) in enumerate(t["ranks"]) if (rank >> r) & 1)
+                warp.append(o)
+            offs += warp
+            if len(warp) == 32 and covered >= 5:
+                assert max(warp) - min(warp) == 31 and len(set(warp)) == 32
+    want = set()
+    for q in range(R):
+        want.add(sum(1 << p for r, (_, _, p) in enumerate(t["ranks"]) if (q >> r) & 1))
+    assert len(offs) == R and set(offs) == want
