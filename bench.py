@@ -211,12 +211,12 @@ def measured_peaks():
 
 
 # DRAM bytes (read + write) per tensor-core product launch, averaged over the
-# 12 product launches of one step, from one ncu capture of the bench command
+# 13 product launches of one step, from one ncu capture of the bench command
 # itself with its autotuned choices fixed by --tune-file
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass;
 # profiles/launch_list_bristlecone70_d32_fp16x3.md), keyed by (precision,
 # workload). A mode or workload without an up-to-date capture reports null.
-TC_DRAM_BYTES_PER_LAUNCH = {("fp16x3", "bristlecone70_d32"): 2.1944e9}
+TC_DRAM_BYTES_PER_LAUNCH = {("fp16x3", "bristlecone70_d32"): 2.0430e9}
 
 
 def plan_roofline(plan, precision, ms_per_group):
